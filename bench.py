@@ -1,0 +1,391 @@
+#!/usr/bin/env python
+"""Time-to-solve of one-reduce MGS-GMRES against plain MGS-GMRES on B300.
+
+Default workload: FP64 3D 7-point upwinded convection-diffusion on a 256^3
+grid (n = 16,777,216, nnz = 117,047,296), GMRES(50), relative residual 1e-8,
+x_true ~ U[-1, 1] from PCG64(0), b = A x_true, x0 = 0. One step is one
+complete solve (every Arnoldi step, restart and solution update on the GPU).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload 256|32] [--no-mgs] [--no-cpu-baseline]
+
+Prints one JSON line (rank 0). With N > 1 (torchrun) every rank solves its own
+replica of the system (no data-path collective); the time is the maximum
+over ranks. The reference arm (--impl reference) times the FP64 CPU oracle on
+a bounded sample of the same workload and scales it to a whole solve.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1809_05805_b300 import problems as P  # noqa: E402
+
+WORKLOADS = {
+    256: dict(N=256, m=50, tol=1e-8, max_iter=3000),
+    32: dict(N=32, m=30, tol=1e-8, max_iter=300),
+}
+METRIC = "time-to-solve (1e-8 rel. resid), one-reduce MGS-GMRES"
+FP64_DFMA_PER_CLK_SM = 2  # B300: 1.25 TFLOP/s nominal FP64 = 148 SMs x 2 DFMA/clk x 2 flop x ~2.1 GHz
+
+
+def workload_name(w):
+    N = w["N"]
+    return (f"3D 7-point convection-diffusion {N}^3 (n={N ** 3}, nnz={P.grid7_nnz(N)}), FP64 CSR, "
+            f"GMRES({w['m']}) one-reduce MGS vs plain MGS, tol {w['tol']:g}, x0=0")
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else ".",
+                                 f".clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        try:
+            with open(self.path) as f:
+                for line in f:
+                    p = [t.strip() for t in line.split(",")]
+                    if len(p) >= 9 and p[1].isdigit():
+                        rows.append(p)
+            os.remove(self.path)
+        except OSError:
+            pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = np.array([float(r[1]) for r in rows])
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(rows[0][2]), "samples": len(rows),
+                "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit()),
+                "reasons": reasons}
+
+
+# ----------------------------------------------------------------------------- helpers
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def alg_bytes_iteration(n, nnz, j):
+    """Algorithmic bytes of one-reduce step j (0-based in its cycle): fused SpMV + block dot + MAXPY."""
+    return 4.0 * (n + 1) + 12.0 * nnz + 8.0 * n * (j + 2) + 8.0 * n * (j + 3)
+
+
+def cycle_profile(total_iters, m):
+    """Columns per cycle of a solve with `total_iters` steps and restart m (all cycles full but the last)."""
+    ks = [m] * (total_iters // m)
+    if total_iters % m:
+        ks.append(total_iters % m)
+    return ks
+
+
+def solve_model_bytes(n, nnz, ks):
+    tot = 0.0
+    for k in ks:
+        tot += sum(alg_bytes_iteration(n, nnz, j) for j in range(k)) + 8.0 * n * (k + 1)  # + tail
+        tot += 4.0 * (n + 1) + 12.0 * nnz + 24.0 * n + 8.0 * n * (k + 2)  # residual + x update
+    return tot
+
+
+def cpu_baseline(A, b, w, ks_full, sample_iters):
+    """Time the FP64 oracle (1 thread) on the first `sample_iters` steps of the same
+    solve and scale to the whole solve by the algorithmic-bytes model."""
+    import oracle
+
+    n, nnz = len(A[0]) - 1, len(A[1])
+    o = oracle.get()
+    t0 = time.perf_counter()
+    r = o.gmres(A, b, variant=oracle.ONE_REDUCE, m=w["m"], tol=0.0, max_iter=sample_iters)
+    dt = time.perf_counter() - t0
+    sample_bytes = solve_model_bytes(n, nnz, [r.iters])
+    full_bytes = solve_model_bytes(n, nnz, ks_full)
+    est = dt * full_bytes / sample_bytes
+    return {"value": est, "unit": "s", "cores": 1, "kind": "oracle",
+            "sample": (f"first {r.iters} Arnoldi steps (+ tail, residual, update) of one-reduce GMRES({w['m']}) "
+                       f"on the same {w['N']}^3 system, FP64 C oracle on 1 host thread, {dt:.2f} s, scaled by "
+                       f"the algorithmic-bytes model to the full solve ({sum(ks_full)} steps, {len(ks_full)} cycles)"),
+            "sample_seconds": dt}
+
+
+def golden_profile(name):
+    path = os.path.join(ROOT, "tests", "golden", f"oracle_profile_{name}.txt")
+    if not os.path.exists(path):
+        return None
+    out = {}
+    with open(path) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip() or line.startswith("history"):
+                continue
+            k, v = line.split()
+            out[k] = float(v)
+    return out
+
+
+# ----------------------------------------------------------------------------- reference arm
+def run_reference(args, w, rank, world):
+    if rank != 0:
+        return 0
+    A = P.conv_diff_7pt(w["N"])
+    _, b = P.rhs(A, seed=0)
+    prof = golden_profile(f"c2_one_reduce" if w["N"] == 256 else "c1")
+    if prof is None:
+        print(json.dumps({"impl": "reference", "unavailable": "oracle iteration profile for this workload "
+                          "(tests/golden/oracle_profile_*.txt) has not been written"}))
+        return 0
+    ks = cycle_profile(int(prof["iters"]), w["m"])
+    sample = 6 if w["N"] == 256 else w["max_iter"]
+    vals = []
+    for s in range(args.warmup + args.steps):
+        cb = cpu_baseline(A, b, w, ks, sample)
+        if s >= args.warmup:
+            vals.append(cb)
+    v = float(np.mean([c["value"] for c in vals]))
+    cores = 1
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * v, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_name(w), "m": w["m"], "tol": w["tol"]},
+        "cpu_baseline": {"value": v, "unit": "s", "cores": cores, "kind": "oracle", "sample": vals[-1]["sample"]},
+        "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ----------------------------------------------------------------------------- our arm
+def timed_solves(torch, s, bd, x, steps, warmup, stream):
+    infos = []
+    for _ in range(warmup):
+        x.zero_()
+        s.solve(bd, x)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    ms = 0.0
+    prof = None
+    for _ in range(steps):
+        with torch.cuda.stream(stream):
+            x.zero_()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        infos.append(s.solve(bd, x))
+        e1.record(stream)
+        e1.synchronize()
+        ms += e0.elapsed_time(e1)
+        p = s.profile()
+        if prof is None:
+            prof = p
+        else:
+            for k in prof:
+                for f in prof[k]:
+                    prof[k][f] += p[k][f]
+    return ms / steps, infos, prof
+
+
+def run_ours(args, w, rank, world, dist):
+    import torch
+
+    from paper_1809_05805_b300 import lsgmres
+
+    lsgmres.load()  # fails loudly when the CUDA library is missing
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream()
+    A = P.conv_diff_7pt(w["N"])
+    _, b = P.rhs(A, seed=0)
+    n, nnz = len(A[0]) - 1, len(A[1])
+    peaks = load_peaks()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(v):
+        if dist is None:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    bd = torch.from_numpy(b).cuda()
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    s = lsgmres.Solver(A, m=w["m"], tol=w["tol"], ortho="one_reduce_mgs", max_iter=w["max_iter"], stream=stream)
+    s.set_profile(True)
+
+    barrier()
+    with ClockSampler(local) as clk:
+        ms, infos, prof = timed_solves(torch, s, bd, x, args.steps, args.warmup, stream)
+        barrier()
+    clocks = clk.summary()
+    ms = max_over_ranks(ms)
+    info = infos[-1]
+    xs = x.cpu().numpy()
+    true_rel = float(np.linalg.norm(b - P.to_scipy(A) @ xs) / np.linalg.norm(b))
+    hist_1r = s.history()
+
+    # plain MGS on the same kernels
+    mgs = None
+    if not args.no_mgs:
+        s.set(ortho="mgs", max_iter=w["max_iter"])
+        ms_m, infos_m, prof_m = timed_solves(torch, s, bd, x, max(1, min(args.steps, 2)), 1, stream)
+        ms_m = max_over_ranks(ms_m)
+        im = infos_m[-1]
+        mgs = {"time_to_solve_s": ms_m / 1e3, "iters": im.iters, "restarts": im.restarts,
+               "reductions": im.reductions, "kernel_launches": im.kernel_launches,
+               "rel_resid_true": im.rel_resid_true,
+               "alg_gbs": sum(v["bytes"] for v in prof_m.values()) / (sum(v["ms"] for v in prof_m.values()) * 1e6)
+               if prof_m else None}
+        s.set(ortho="one_reduce_mgs", max_iter=w["max_iter"])
+
+    # end to end through the host-buffer entry point (copies inside the call)
+    bh = torch.from_numpy(b).pin_memory().numpy()
+    xh = torch.zeros(n, dtype=torch.float64).pin_memory().numpy()
+    s.set_profile(False)
+    e2e_ms = 0.0
+    e2e_steps = max(1, min(args.steps, 2))
+    s.solve_host(bh, xh)  # warm the staging buffers
+    for _ in range(e2e_steps):
+        xh[:] = 0.0
+        t0 = time.perf_counter()
+        s.solve_host(bh, xh)
+        e2e_ms += (time.perf_counter() - t0) * 1e3
+    e2e_ms = max_over_ranks(e2e_ms / e2e_steps)
+    s.set_profile(True)
+
+    # roofline of the dominant kernel (the fused SpMV + block-dot step)
+    st = prof["one_reduce_step"]
+    mx = prof["arnoldi_maxpy"]
+    clk_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2032.0)
+    fp64_peak = 148 * FP64_DFMA_PER_CLK_SM * 2 * float(peaks.get("sm_max_mhz", 2032.0)) * 1e6 / 1e12
+    step_avg_ms = st["ms"] / max(st["launches"], 1)
+    step_tflops = st["flops"] / (st["ms"] * 1e-3) / 1e12 if st["ms"] else None
+    step_gbs = st["bytes"] / (st["ms"] * 1e-3) / 1e9 if st["ms"] else None
+    hbm = float(peaks.get("hbm_gbs", 6400.0))
+    roofline = {
+        "kernel": "k_one_reduce_step (fused CSR SpMV + block dot [V u]^T[u w] + epilogue)",
+        "bound": "alu", "achieved": step_tflops, "peak": fp64_peak, "unit": "TFLOP/s",
+        "frac": step_tflops / fp64_peak if step_tflops else None,
+        "peak_source": (f"FP64 pipe derived from unit counts and clock: 148 SMs x {FP64_DFMA_PER_CLK_SM} DFMA/clk x 2 "
+                        f"flop x {peaks.get('sm_max_mhz', 2032.0):g} MHz (nominal 1.25 TFLOP/s)"),
+        "traffic": None,
+        "launch_avg_ms": step_avg_ms, "launches": st["launches"],
+        "alg_flops_per_launch": st["flops"] / max(st["launches"], 1),
+        "alg_bytes_per_launch": st["bytes"] / max(st["launches"], 1),
+        "hbm_gbs": step_gbs, "hbm_frac_of_measured": step_gbs / hbm if step_gbs else None,
+        "maxpy": {"launch_avg_ms": mx["ms"] / max(mx["launches"], 1),
+                  "tflops": mx["flops"] / (mx["ms"] * 1e-3) / 1e12 if mx["ms"] else None,
+                  "hbm_gbs": mx["bytes"] / (mx["ms"] * 1e-3) / 1e9 if mx["ms"] else None},
+    }
+    total_bytes = sum(v["bytes"] for v in prof.values())
+    total_ms_prof = sum(v["ms"] for v in prof.values())
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        ks = cycle_profile(info.iters, w["m"])
+        sample = 12 if w["N"] == 256 else w["max_iter"]
+        cpu = cpu_baseline(A, b, w, ks, sample)
+
+    line = {
+        "metric": METRIC, "value": ms / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded stencil, x_true ~ U[-1,1])",
+        "config": {"workload": workload_name(w), "n": n, "nnz": nnz, "m": w["m"], "tol": w["tol"],
+                   "parallelism": "replicas" if world > 1 else "1 GPU",
+                   "l2": "inputs larger than L2 (Krylov basis %.1f GB >> 126 MB), no flush" % (8 * n * (w["m"] + 1) / 1e9)},
+        "iters": info.iters, "restarts": info.restarts, "reductions": info.reductions,
+        "grid_syncs": info.grid_syncs, "rel_resid_true": true_rel,
+        "solves_per_s": world / (ms / 1e3),
+        "alg_hbm_gbs_whole_solve": total_bytes / (total_ms_prof * 1e6) if total_ms_prof else None,
+        "mgs": mgs,
+        "speedup_vs_mgs": (mgs["time_to_solve_s"] / (ms / 1e3)) if mgs else None,
+        "e2e": {"value": e2e_ms / 1e3, "unit": "s", "h2d_bytes_per_step": 16 * n, "d2h_bytes_per_step": 8 * n},
+        "gpu_launches": int(sum(i.kernel_launches for i in infos)),
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "clocks": clocks,
+        "history_first": [float(h) for h in hist_1r[:3]],
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    s.close()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", type=int, choices=sorted(WORKLOADS), default=256)
+    ap.add_argument("--no-mgs", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    w = WORKLOADS[args.workload]
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist_mod
+
+        if args.impl == "reference":
+            dist = None  # the reference arm runs on rank 0 only
+        else:
+            import torch
+
+            torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+            dist_mod.init_process_group("nccl")
+            dist = dist_mod
+    try:
+        if args.impl == "reference":
+            return run_reference(args, w, rank, world)
+        return run_ours(args, w, rank, world, dist)
+    finally:
+        if dist is not None:
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

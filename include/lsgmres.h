@@ -1,0 +1,187 @@
+/*
+ * lsgmres.h: C ABI of the B300-native low-synchronization GMRES library.
+ *
+ * Solves A x = b for a square sparse A in CSR form with restarted GMRES(m)
+ * (Saad and Schultz), in one of two orthogonalization schemes:
+ *
+ *   GMRES_MGS             MGS-GMRES, Algorithm 6 of Swirydowicz, Langou,
+ *                         Ananthan, Yang and Thomas, "Low synchronization GMRES
+ *                         algorithms" (arXiv:1809.05805). Step i makes i+1
+ *                         inner products and one norm, each a separate
+ *                         grid-wide reduction (Section IV).
+ *   GMRES_ONE_REDUCE_MGS  one-synchronization MGS-GMRES with lagged
+ *                         normalization, Algorithm 7 built on the Level-2
+ *                         compact-WY MGS of Algorithm 4 (Sections II-III). Each
+ *                         step makes one grid-wide reduction: the block inner
+ *                         product [V_{j-1} u_j]^T [u_j  A u_j], which also
+ *                         carries the lagged norm of u_j.
+ *
+ * Both schemes run on the same kernels (CSR SpMV, multi-column dot, MAXPY) on
+ * one GPU. All arithmetic on the solve path is FP64.
+ *
+ * Conventions for every entry point:
+ *   - Every call returns a gmres_status; no call aborts or exits. After an
+ *     error, gmres_last_error(h) describes it.
+ *   - "device" pointers are CUDA global-memory addresses on the handle's device
+ *     (for example torch.Tensor.data_ptr() of a CUDA tensor); "host" pointers
+ *     are ordinary CPU memory. Vectors are contiguous FP64 arrays of length n.
+ *   - Work is ordered on the handle's stream (gmres_set_stream; default: the
+ *     legacy default stream). Calls that return results to the host
+ *     synchronize that stream before returning.
+ *   - The library owns its copy of A and all Krylov workspace; the caller owns
+ *     b and x and every buffer it passes in. No call retains a caller pointer.
+ *   - A handle is not thread-safe: one host thread at a time per handle.
+ */
+#ifndef LSGMRES_H
+#define LSGMRES_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  GMRES_OK = 0,              /* converged: ||b - A x|| / ||b|| <= tol */
+  GMRES_MAXITER = 1,         /* max_iter Arnoldi steps spent before convergence */
+  GMRES_BREAKDOWN_EXACT = 2, /* reserved: a vanishing Krylov direction ends a cycle; the
+                                solve restarts from the true residual, so it is not returned */
+  GMRES_ERR_ARG = -1,        /* invalid argument or invalid CSR structure */
+  GMRES_ERR_CUDA = -2,       /* a CUDA runtime call failed */
+  GMRES_ERR_NONFINITE = -3,  /* NaN or Inf in b, x0 or a reduction */
+  GMRES_ERR_OOM = -4,        /* device or pinned-host allocation failed */
+  GMRES_ERR_TIMEOUT = -5     /* reserved for bounded device-side waits */
+} gmres_status;
+
+typedef enum { GMRES_MGS = 0, GMRES_ONE_REDUCE_MGS = 1 } gmres_ortho;
+
+/* Arithmetic of the Krylov loop. Only GMRES_FP64 is implemented; the others
+ * are reserved for mixed-precision iterative refinement and are rejected. */
+typedef enum { GMRES_FP64 = 0, GMRES_IR_FP32 = 1, GMRES_IR_BF16 = 2 } gmres_prec;
+
+typedef struct gmres_ctx* gmres_handle;
+
+/* Square CSR matrix: row i holds entries rowptr[i] .. rowptr[i+1]-1 of col/val.
+ * rowptr[0] = 0, rowptr nondecreasing, rowptr[n] = nnz, 0 <= col < n.
+ * on_device = 0: the three arrays are host memory; 1: device memory.
+ * Either way gmres_create copies them; the caller may free them afterwards. */
+typedef struct {
+  int64_t n;
+  int64_t nnz;
+  const int32_t* rowptr;
+  const int32_t* col;
+  const double* val;
+  int on_device;
+} gmres_csr;
+
+typedef struct {
+  int iters;              /* Arnoldi steps (Hessenberg columns) over all cycles */
+  int restarts;           /* cycles run */
+  int status;             /* the gmres_status of the solve */
+  int breakdowns;         /* cycles ended by a vanishing new direction */
+  double rel_resid_true;  /* ||b - A x|| / ||b|| at exit, recomputed from x */
+  double rel_resid_est;   /* last Givens estimate |g_{k+1}| / ||b|| */
+  int64_t reductions;     /* grid-wide reductions executed on the device */
+  int64_t grid_syncs;     /* kernel boundaries that did work (one grid-wide sync each) */
+  int64_t kernel_launches;/* kernels launched by the solve */
+  double seconds;         /* wall time of the solve */
+} gmres_info;
+
+/* Create a solver for A with restart length m_restart (1 <= m <= 128) and
+ * relative tolerance tol >= 0. Validates A on the host (structure above; n > 0;
+ * nnz < 2^31), copies it to the device and allocates the Krylov basis
+ * ((m+1) columns of n doubles) and the small dense state. Defaults:
+ * GMRES_ONE_REDUCE_MGS, GMRES_FP64, max_iter = 10 * m, legacy default stream.
+ * Errors: GMRES_ERR_ARG, GMRES_ERR_OOM, GMRES_ERR_CUDA; *out is NULL then. */
+gmres_status gmres_create(const gmres_csr* A, int m_restart, double tol, gmres_handle* out);
+
+/* Select the orthogonalization scheme, the arithmetic and the iteration limit
+ * (max_iter >= 0 Arnoldi steps over all cycles). GMRES_ERR_ARG for an unknown
+ * scheme, a precision other than GMRES_FP64, or max_iter < 0. */
+gmres_status gmres_set(gmres_handle h, gmres_ortho ortho, gmres_prec prec, int max_iter);
+
+/* Change the tolerance (tol >= 0). */
+gmres_status gmres_set_tol(gmres_handle h, double tol);
+
+/* Order all later work of h on cuda_stream (a cudaStream_t; NULL = legacy default). */
+gmres_status gmres_set_stream(gmres_handle h, void* cuda_stream);
+
+/* Solve A x = b. b: device, n doubles, read only. x: device, n doubles, holds
+ * x0 on entry and the solution on exit. A cycle ends when the Givens residual
+ * estimate reaches tol; the solve ends when the recomputed true residual
+ * ||b - A x|| / ||b|| <= tol (GMRES_OK) or after max_iter steps
+ * (GMRES_MAXITER). b = 0 gives x = 0. info may be NULL. Synchronizes the stream.
+ * Errors: GMRES_ERR_ARG (NULL or misaligned pointer: b and x must be 8-byte
+ * aligned), GMRES_ERR_NONFINITE, GMRES_ERR_CUDA. */
+gmres_status gmres_solve(gmres_handle h, const double* b, double* x, gmres_info* info);
+
+/* As gmres_solve with b and x in host memory: copies b and x0 to the device,
+ * solves, and copies x back (the copies are part of the call). */
+gmres_status gmres_solve_host(gmres_handle h, const double* b_host, double* x_host,
+                              gmres_info* info);
+
+/* Copy the residual-estimate history of the last solve (one entry per
+ * Arnoldi step: |g_{k+1}| / ||b|| after column k completes) into host_buf
+ * (capacity cap). *len receives the full history length. */
+gmres_status gmres_history(gmres_handle h, double* host_buf, int cap, int* len);
+
+/* Release all device and host memory of h. NULL is accepted. */
+gmres_status gmres_destroy(gmres_handle h);
+
+/* Description of the last error on h (or of the last failed gmres_create when
+ * h is NULL). The string is owned by the library. */
+const char* gmres_last_error(gmres_handle h);
+
+/* Per-kernel timing. With on = 1, later solves bracket every kernel launch
+ * with CUDA events on the handle's stream (a few microseconds of host work
+ * per launch) and gmres_profile reports, per kernel class, the summed device
+ * time, the launch count and the algorithmic bytes and flops of the launches
+ * that did work (launches that found their cycle already finished are counted
+ * separately). Counters reset at the start of every solve.
+ * Classes: 0 one-reduce step (fused SpMV + block dot + epilogue), 1 Arnoldi
+ * MAXPY, 2 MGS SpMV + first dot, 3 MGS axpy + next dot, 4 residual / norm,
+ * 5 least squares, 6 solution update (MAXPY), 7 launches that did no work. */
+#define GMRES_PROFILE_CLASSES 8
+gmres_status gmres_set_profile(gmres_handle h, int on);
+gmres_status gmres_profile(gmres_handle h, int cls, double* total_ms, int64_t* launches,
+                           double* alg_bytes, double* alg_flops);
+
+/* ------------------------------------------------------------------------
+ * Single steps of the solve path, exposed for parity tests.
+ * ------------------------------------------------------------------------ */
+
+/* y = A x (device x, y; n doubles each). The CSR SpMV of the Arnoldi step
+ * (Section IV: the matvec partitions by rows). */
+gmres_status lsg_spmv(gmres_handle h, const double* x, double* y);
+
+/* The fused SpMV + block inner product of one one-reduce step (Algorithm 4's
+ * single reduction, Section IV's mass inner product): with V the first j
+ * columns of a column-major device array (leading dimension ldv >= n) and
+ * u a device vector, computes w = A u (written to device w) and the 2j+2 sums
+ *   X[0:j]   = V^T u,   X[j:2j] = V^T w,   X[2j] = u^T u,   X[2j+1] = u^T w
+ * into host X. If use_spmv is 0, w is an input (not overwritten) and the
+ * SpMV is skipped (the standalone QR form of Algorithm 4). 0 <= j <= m. */
+gmres_status lsg_block_dot(gmres_handle h, const double* V, int64_t ldv, int j,
+                           const double* u, double* w, int use_spmv, double* X);
+
+/* MAXPY (Section IV): y_out = alpha * y_in + sum_{k<K} c[k] * V[:, k] for
+ * device V (leading dimension ldv >= n, 16-byte aligned columns), device
+ * y_in and y_out (may alias), host c (K values), 0 <= K <= m + 1. */
+gmres_status lsg_maxpy(gmres_handle h, const double* V, int64_t ldv, int K, const double* c,
+                       double alpha, const double* y_in, double* y_out);
+
+/* Run one GMRES cycle of k Arnoldi steps (1 <= k <= m) from the device vector
+ * r0, with no convergence test, using the selected scheme. Returns the
+ * normalized basis V_out (device, n x (k+1), leading dimension n), the
+ * unrotated Hessenberg H_out (host, (k+1) x k, column-major) and, for the
+ * one-reduce scheme, T_out = (I + L)^{-1} (host, (k+1) x (k+1), lower;
+ * zeros for MGS). Any output pointer may be NULL. *k_done receives the
+ * number of columns completed (< k only after a breakdown). */
+gmres_status gmres_arnoldi(gmres_handle h, const double* r0, int k, double* V_out,
+                           double* H_out, double* T_out, int* k_done);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LSGMRES_H */

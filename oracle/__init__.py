@@ -66,6 +66,10 @@ class Oracle:
         lib = ctypes.CDLL(self.path)
         lib.orc_spmv.argtypes = [ctypes.c_int64, _P, _P, _P, _P, _P]
         lib.orc_spmv.restype = None
+        lib.orc_dot.argtypes = [ctypes.c_int64, _P, _P]
+        lib.orc_dot.restype = ctypes.c_double
+        lib.orc_maxpy.argtypes = [ctypes.c_int64, ctypes.c_int, _P, ctypes.c_int64, _P, ctypes.c_double, _P, _P]
+        lib.orc_maxpy.restype = None
         lib.orc_qr_mgs.argtypes = [ctypes.c_int64, ctypes.c_int, _P, _P, _P]
         lib.orc_qr_cgs.argtypes = [ctypes.c_int64, ctypes.c_int, _P, _P, _P, ctypes.c_int]
         lib.orc_qr_mgs_lvl2.argtypes = [ctypes.c_int64, ctypes.c_int, _P, _P, _P, _P]
@@ -86,6 +90,21 @@ class Oracle:
         y = np.empty(len(rowptr) - 1, dtype=np.float64)
         self.lib.orc_spmv(len(y), _ptr(rowptr), _ptr(col), _ptr(val), _ptr(x), _ptr(y))
         return y
+
+    def dot(self, x: np.ndarray, y: np.ndarray) -> float:
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        y = np.ascontiguousarray(y, dtype=np.float64)
+        return self.lib.orc_dot(len(x), _ptr(x), _ptr(y))
+
+    def maxpy(self, V: np.ndarray, c: np.ndarray, alpha: float, y: np.ndarray) -> np.ndarray:
+        """alpha * y + V @ c with V (n x K) column-major."""
+        V = np.asfortranarray(V, dtype=np.float64)
+        c = np.ascontiguousarray(c, dtype=np.float64)
+        y = np.ascontiguousarray(y, dtype=np.float64)
+        out = np.empty_like(y)
+        n, K = V.shape
+        self.lib.orc_maxpy(n, K, _ptr(V), n, _ptr(c), alpha, _ptr(y), _ptr(out))
+        return out
 
     def _qr(self, fn, A: np.ndarray, *extra, with_T=False):
         A = np.asfortranarray(A, dtype=np.float64)

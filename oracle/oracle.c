@@ -15,6 +15,8 @@
  *
  * Contents, each citing the passage it follows:
  *   orc_spmv          y = A x for CSR A (Section IV, CSR matvec)
+ *   orc_dot, orc_maxpy  the mass inner product and MAXPY of Section IV, one
+ *                     column at a time
  *   orc_qr_mgs        column MGS QR (Algorithm 2, one column at a time)
  *   orc_qr_cgs        classical GS QR, 1 or 2 passes (Algorithm 1)
  *   orc_qr_mgs_lvl2   Level-2 compact-WY MGS with lagged normalization
@@ -78,6 +80,21 @@ static double dot(int64_t n, const double* x, const double* y) {
 }
 
 static double nrm2(int64_t n, const double* x) { return sqrt(dot(n, x, x)); }
+
+/* Inner product x^T y, sequential (the plain definition behind the mass inner
+ * product of Section IV: one such sum per column). */
+double orc_dot(int64_t n, const double* x, const double* y) { return dot(n, x, y); }
+
+/* MAXPY of Section IV: y_out = alpha y_in + sum_{k<K} c[k] V(:, k), V column-major
+ * with leading dimension ldv, written term by term in column order. */
+void orc_maxpy(int64_t n, int K, const double* V, int64_t ldv, const double* c, double alpha,
+               const double* y_in, double* y_out) {
+  for (int64_t i = 0; i < n; ++i) {
+    double t = alpha * y_in[i];
+    for (int k = 0; k < K; ++k) t += c[k] * V[i + (size_t)k * ldv];
+    y_out[i] = t;
+  }
+}
 
 /* y = y + alpha x */
 static void axpy(int64_t n, double alpha, const double* x, double* y) {

@@ -1,0 +1,1298 @@
+// B300-native restarted GMRES(m) with plain MGS and one-reduce (lagged
+// normalization, compact-WY) MGS orthogonalization, FP64.
+//
+// Method: Swirydowicz, Langou, Ananthan, Yang, Thomas, "Low synchronization
+// GMRES algorithms" (arXiv:1809.05805): Algorithm 6 (MGS-GMRES), Algorithm 4
+// (Level-2 MGS with R normalization lag), Algorithm 7 (one-synchronization
+// MGS-GMRES), the compact-WY T recurrence of Section II, and the fused mass
+// inner product / MAXPY of Section IV.
+//
+// Design for sm_103a (B300):
+//  * FP64 issue rate, not HBM, bounds the FP64 Arnoldi step on this part
+//    (about 2 DFMA per clock per SM against ~6 TB/s of HBM), so the kernels
+//    spend DFMAs only on the method's own products, keep every scale factor
+//    out of the inner loops, and reduce across threads once per kernel.
+//  * The basis is stored unnormalized: column k holds u_k and scale[k] = 1/||u_k||,
+//    so v_k = scale[k] * u_k is never written. Scales are folded into the
+//    coefficients of the dot products and of the MAXPY.
+//  * One grid-wide reduction per kernel: per-CTA partial sums go to global
+//    memory, an atomic ticket elects the last CTA, which sums the partials in
+//    CTA order (deterministic) and runs the small dense epilogue (lagged norm,
+//    Givens rotation, T row, T s, MAXPY coefficients) in shared memory.
+//  * Kernels read the step index and the stop flag from device state, so a
+//    cycle is a fixed launch sequence; once the epilogue marks the cycle done,
+//    the remaining kernels of the cycle return immediately.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "lsgmres.h"
+
+namespace {
+
+constexpr int kThreads = 256;                // CTA size; also rows per tile
+constexpr int kWarps = kThreads / 32;        // 8
+constexpr int kRowsPerLane = kThreads / 32;  // rows of a tile handled by one lane in the dot phase
+constexpr int kMaxM = 128;                   // largest restart length
+constexpr double kEps = 2.220446049250313e-16;
+constexpr double kBreakdownFactor = 16.0;
+
+// --------------------------------------------------------------------------
+// device state
+// --------------------------------------------------------------------------
+struct DevState {
+  double bnorm;        // ||b|| (or ||r0|| for gmres_arnoldi)
+  double rnorm;        // last true-residual norm
+  double tol;
+  double est;          // last Givens estimate (relative)
+  int step;            // next Arnoldi step of the cycle
+  int inner;           // MGS: next inner-product index within the step
+  int kmax;            // steps allowed in this cycle
+  int k;               // Hessenberg columns completed in this cycle
+  int done;            // cycle finished
+  int converged;
+  int breakdown;
+  int nonfinite;
+  int maxpy_k;         // columns of the pending Arnoldi MAXPY
+  int total_iters;     // over all cycles
+  int restarts;
+  int breakdowns;
+  unsigned int ticket; // last-CTA election
+  int pad;
+  long long reductions;
+  long long grid_syncs;
+  double mgs_coef;     // MGS: coefficient of the pending axpy
+};
+
+// Device pointers into the small dense arrays (one allocation).
+struct Small {
+  DevState* st;
+  double* H;        // (m+1) x m, unrotated, column-major, ld = m+1
+  double* Rg;       // (m+1) x m, rotated
+  double* cs;       // m+1
+  double* sn;       // m+1
+  double* g;        // m+2
+  double* T;        // (m+1) x (m+1), lower, ld = m+1
+  double* scale;    // m+2: 1/||u_k||
+  double* coef;     // m+3: [alpha, c_0 .. c_m] of the pending Arnoldi MAXPY
+  double* coefx;    // m+3: [1, y_0 s_0 .. ] of the solution update
+  double* hist;     // hist_cap
+  double* partials; // P x nvmax
+  double* raw;      // nvmax: standalone block-dot output
+  int m;
+  int ldh;          // m + 1
+  int nvmax;        // 2 (m + 1) + 2
+  int hist_cap;
+};
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum one value over the CTA (fixed order); result valid in thread 0.
+__device__ __forceinline__ double block_sum(double v, double* sbuf /* kWarps */) {
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) sbuf[wid] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < kWarps; ++i) t += sbuf[i];
+  }
+  __syncthreads();
+  return t;
+}
+
+// Row i of A times x (CSR, FP64 FMA chain in column order).
+__device__ __forceinline__ double csr_row(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                                          const double* __restrict__ val, const double* __restrict__ x,
+                                          int64_t i) {
+  const int p0 = __ldg(rowptr + i), p1 = __ldg(rowptr + i + 1);
+  double s = 0.0;
+  for (int p = p0; p < p1; ++p) s = fma(__ldg(val + p), __ldg(x + __ldg(col + p)), s);
+  return s;
+}
+
+// Publish this CTA's partial sums and elect the last CTA. Returns true in every
+// thread of the last CTA, after which `red` holds the grid totals (summed in CTA
+// order) for values [0, nv).
+__device__ bool grid_reduce_last(Small s, double* red, int nv) {
+  __shared__ int s_last;
+  for (int v = threadIdx.x; v < nv; v += blockDim.x) s.partials[(size_t)blockIdx.x * s.nvmax + v] = red[v];
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = (atomicAdd(&s.st->ticket, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (!s_last) return false;
+  __threadfence();
+  for (int v = threadIdx.x; v < nv; v += blockDim.x) {
+    double t = 0.0;
+    for (int b = 0; b < (int)gridDim.x; ++b) t += __ldcg(s.partials + (size_t)b * s.nvmax + v);
+    red[v] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    s.st->ticket = 0u;
+    s.st->reductions += 1;
+  }
+  return true;
+}
+
+// Column j of H is complete (entries 0..j+1): rotate a copy by the stored
+// rotations, form rotation j, update g; returns |g_{j+1}|. Single thread.
+__device__ double rotate_column(Small s, int j) {
+  const int ld = s.ldh;
+  double* R = s.Rg + (size_t)j * ld;
+  const double* Hc = s.H + (size_t)j * ld;
+  for (int i = 0; i <= j + 1; ++i) R[i] = Hc[i];
+  for (int i = 0; i < j; ++i) {
+    const double c = s.cs[i], sn = s.sn[i];
+    const double t = c * R[i] + sn * R[i + 1];
+    R[i + 1] = -sn * R[i] + c * R[i + 1];
+    R[i] = t;
+  }
+  double c = 1.0, sn = 0.0;
+  if (R[j + 1] != 0.0) {
+    const double rho = hypot(R[j], R[j + 1]);
+    c = R[j] / rho;
+    sn = R[j + 1] / rho;
+  }
+  s.cs[j] = c;
+  s.sn[j] = sn;
+  R[j] = c * R[j] + sn * R[j + 1];
+  R[j + 1] = 0.0;
+  s.g[j + 1] = -sn * s.g[j];
+  s.g[j] = c * s.g[j];
+  return fabs(s.g[j + 1]);
+}
+
+__device__ double hcol_norm(Small s, int j) {
+  const double* Hc = s.H + (size_t)j * s.ldh;
+  double t = 0.0;
+  for (int i = 0; i <= j + 1; ++i) t += Hc[i] * Hc[i];
+  return sqrt(t);
+}
+
+// Column j of H has just received its subdiagonal entry h = H(j+1, j).
+// Rotate, record the estimate, and decide whether the cycle stops.
+// Returns 1 if the cycle is done. Single thread.
+__device__ int finish_column(Small s, int j, double h, bool last_allowed) {
+  DevState* st = s.st;
+  const double est = rotate_column(s, j) / st->bnorm;
+  const int it = st->total_iters + j;
+  if (it < s.hist_cap) s.hist[it] = est;
+  st->k = j + 1;
+  st->est = est;
+  if (!isfinite(est)) {
+    st->nonfinite = 1;
+    return 1;
+  }
+  if (h <= kBreakdownFactor * kEps * hcol_norm(s, j)) {
+    st->breakdown = 1;
+    return 1;
+  }
+  if (est <= st->tol) {
+    st->converged = 1;
+    return 1;
+  }
+  if (last_allowed) return 1;
+  return 0;
+}
+
+// --------------------------------------------------------------------------
+// one-reduce step: fused SpMV + block dot + epilogue
+// --------------------------------------------------------------------------
+// Step j of a cycle (u_j = column j, not yet normalized; V_{j} = columns 0..j-1):
+//   w = A u_j;
+//   X = [a = U_j^T u_j, c = U_j^T w, sigma = u_j^T u_j, d = u_j^T w]  (one reduction)
+// where U_j holds the unnormalized columns; the epilogue applies scale[k].
+// At j == kmax (the tail) the SpMV and c, d are skipped.
+// Standalone mode (raw_out != nullptr): j is j_arg, w may be an input
+// (use_spmv == 0), and the totals go to raw_out without the GMRES epilogue.
+template <int MAXC>
+__global__ void __launch_bounds__(kThreads, 2)
+k_one_reduce_step(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                  const double* __restrict__ val, const double* __restrict__ V, int64_t ldv,
+                  const double* __restrict__ u_arg, double* __restrict__ w, int64_t n, Small s,
+                  int j_arg, int use_spmv, double* raw_out) {
+  __shared__ double su[kThreads];
+  __shared__ double sw[kThreads];
+  __shared__ double red[2 * (kMaxM + 1) + 2];
+  __shared__ double sbuf[kWarps];
+  __shared__ int s_j, s_tail, s_skip;
+  DevState* st = s.st;
+  if (threadIdx.x == 0) {
+    if (raw_out) {
+      s_j = j_arg;
+      s_tail = 0;
+      s_skip = 0;
+    } else {
+      s_skip = __ldcg(&st->done);
+      s_j = __ldcg(&st->step);
+      s_tail = (s_j == __ldcg(&st->kmax));
+    }
+  }
+  __syncthreads();
+  if (s_skip) return;
+  const int j = s_j;
+  const bool tail = s_tail;
+  const bool spmv = raw_out ? (use_spmv != 0) : !tail;
+  const bool need_w = raw_out ? true : !tail;
+  const double* u = raw_out ? u_arg : V + (size_t)j * ldv;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+
+  double acc_a[MAXC], acc_c[MAXC];
+#pragma unroll
+  for (int c = 0; c < MAXC; ++c) acc_a[c] = acc_c[c] = 0.0;
+  double sig = 0.0, dd = 0.0;
+
+  const int64_t ntiles = (n + kThreads - 1) / kThreads;
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int64_t row = t * kThreads + threadIdx.x;
+    double ur = 0.0, wr = 0.0;
+    if (row < n) {
+      ur = u[row];
+      if (spmv) {
+        wr = csr_row(rowptr, col, val, u, row);
+        w[row] = wr;
+      } else if (need_w) {
+        wr = w[row];
+      }
+    }
+    sig = fma(ur, ur, sig);
+    dd = fma(ur, wr, dd);
+    su[threadIdx.x] = ur;
+    sw[threadIdx.x] = wr;
+    __syncthreads();
+    double ru[kRowsPerLane], rw[kRowsPerLane];
+#pragma unroll
+    for (int q = 0; q < kRowsPerLane; ++q) {
+      ru[q] = su[lane + 32 * q];
+      rw[q] = sw[lane + 32 * q];
+    }
+    const int64_t base = t * kThreads + lane;
+#pragma unroll
+    for (int c = 0; c < MAXC; ++c) {
+      const int k = wid + c * kWarps;
+      if (k < j) {
+        const double* vk = V + (size_t)k * ldv + base;
+        double x[kRowsPerLane];
+#pragma unroll
+        for (int q = 0; q < kRowsPerLane; ++q) x[q] = (base + 32 * q < n) ? __ldg(vk + 32 * q) : 0.0;
+#pragma unroll
+        for (int q = 0; q < kRowsPerLane; ++q) {
+          acc_a[c] = fma(x[q], ru[q], acc_a[c]);
+          acc_c[c] = fma(x[q], rw[q], acc_c[c]);
+        }
+      }
+    }
+    __syncthreads();
+  }
+
+  // CTA partials: red[0:j] = a, red[j:2j] = c, red[2j] = sigma, red[2j+1] = d
+#pragma unroll
+  for (int c = 0; c < MAXC; ++c) {
+    const int k = wid + c * kWarps;
+    if (k < j) {  // warp-uniform
+      const double a = warp_sum(acc_a[c]);
+      const double cc = warp_sum(acc_c[c]);
+      if (lane == 0) {
+        red[k] = a;
+        red[j + k] = cc;
+      }
+    }
+  }
+  const double sig_t = block_sum(sig, sbuf);
+  const double dd_t = block_sum(dd, sbuf);
+  if (threadIdx.x == 0) {
+    red[2 * j] = sig_t;
+    red[2 * j + 1] = dd_t;
+  }
+  __syncthreads();
+  const int nv = 2 * j + 2;
+  if (!grid_reduce_last(s, red, nv)) return;
+
+  if (raw_out) {
+    for (int v = threadIdx.x; v < nv; v += blockDim.x) raw_out[v] = red[v];
+    return;
+  }
+
+  // ---------------- epilogue (last CTA) ----------------
+  // stop: 0 = continue the cycle; 1 = cycle done after the T row (converged
+  // or tail); 2 = cycle done now (breakdown, zero or non-finite norm).
+  __shared__ double s_ib;
+  __shared__ int s_stop;
+  const int ld = s.ldh;
+  if (threadIdx.x == 0) {
+    st->grid_syncs += 1;
+    const double beta = sqrt(red[2 * j]);
+    int stop = 0;
+    if (!isfinite(beta)) {
+      st->nonfinite = 1;
+      stop = 2;
+    } else if (j == 0) {
+      if (beta == 0.0) stop = 2;  // r0 = 0: the host never starts such a cycle
+      else s.g[0] = beta;
+    } else {
+      s.H[(size_t)(j - 1) * ld + j] = beta;  // H(j, j-1): the lagged norm completes column j-1
+      const int fin = finish_column(s, j - 1, beta, tail);
+      if (st->breakdown || st->nonfinite) stop = 2;
+      else if (fin) stop = 1;
+    }
+    if (isfinite(beta) && beta != 0.0) s.scale[j] = 1.0 / beta;
+    s_ib = 1.0 / beta;
+    s_stop = stop;
+  }
+  __syncthreads();
+  if (s_stop == 2) {
+    if (threadIdx.x == 0) st->done = 1;
+    return;
+  }
+  const double ib = s_ib;
+  // ell = (U_j^T u_j) scaled to v_k^T v_j
+  for (int i = threadIdx.x; i < j; i += blockDim.x) red[i] = red[i] * s.scale[i] * ib;
+  __syncthreads();
+  // row j of T = (I + L)^{-1}: T(j, k) = -sum_{i=k}^{j-1} ell_i T(i, k)
+  for (int k = threadIdx.x; k < j; k += blockDim.x) {
+    double t = 0.0;
+    for (int i = k; i < j; ++i) t = fma(red[i], s.T[(size_t)k * ld + i], t);
+    s.T[(size_t)k * ld + j] = -t;
+  }
+  if (threadIdx.x == 0) s.T[(size_t)j * ld + j] = 1.0;
+  __syncthreads();
+  if (s_stop) {
+    if (threadIdx.x == 0) st->done = 1;
+    return;
+  }
+  // s = [c * scale / beta ; d / beta^2] stored over the c slots
+  __shared__ double sv[kMaxM + 1];
+  for (int i = threadIdx.x; i <= j; i += blockDim.x)
+    sv[i] = (i < j) ? red[j + i] * s.scale[i] * ib : red[2 * j + 1] * ib * ib;
+  __syncthreads();
+  // r = T s; H(0:j, j) = r; MAXPY coefficients
+  for (int i = threadIdx.x; i <= j; i += blockDim.x) {
+    double t = 0.0;
+    for (int k = 0; k <= i; ++k) t = fma(s.T[(size_t)k * ld + i], sv[k], t);
+    s.H[(size_t)j * ld + i] = t;
+    s.coef[1 + i] = -t * s.scale[i];
+  }
+  if (threadIdx.x == 0) {
+    s.coef[0] = ib;
+    st->maxpy_k = j + 1;
+    st->step = j + 1;
+  }
+}
+
+// --------------------------------------------------------------------------
+// MAXPY: out = alpha * y_in + sum_{k<K} c_k V[:, k]
+// --------------------------------------------------------------------------
+enum { MAXPY_ARNOLDI = 0, MAXPY_XUPDATE = 1, MAXPY_STANDALONE = 2 };
+
+__global__ void __launch_bounds__(kThreads)
+k_maxpy(const double* __restrict__ V, int64_t ldv, const double* y_in, double* y_out, int64_t n,
+        Small s, int mode, int K_arg) {
+  __shared__ double sc[kMaxM + 3];
+  __shared__ int sK, s_skip;
+  __shared__ double* s_out;
+  DevState* st = s.st;
+  if (threadIdx.x == 0) {
+    s_skip = 0;
+    if (mode == MAXPY_ARNOLDI) {
+      s_skip = __ldcg(&st->done);
+      sK = __ldcg(&st->maxpy_k);
+      s_out = const_cast<double*>(V) + (size_t)__ldcg(&st->step) * ldv;
+    } else if (mode == MAXPY_XUPDATE) {
+      sK = __ldcg(&st->k);
+      s_out = y_out;
+    } else {
+      sK = K_arg;
+      s_out = y_out;
+    }
+  }
+  __syncthreads();
+  if (s_skip) return;
+  const int K = sK;
+  const double* cf = (mode == MAXPY_XUPDATE) ? s.coefx : s.coef;
+  for (int i = threadIdx.x; i <= K; i += blockDim.x) sc[i] = __ldcg(cf + i);
+  __syncthreads();
+  if (mode == MAXPY_ARNOLDI && blockIdx.x == 0 && threadIdx.x == 0) st->grid_syncs += 1;
+  double* out = s_out;
+  const double alpha = sc[0];
+  const bool vec = ((reinterpret_cast<uintptr_t>(y_in) | reinterpret_cast<uintptr_t>(out) |
+                     reinterpret_cast<uintptr_t>(V)) & 15) == 0 && (ldv & 1) == 0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (vec) {
+    const int64_t n2 = n / 2;
+    for (int64_t i = gid; i < n2; i += stride) {
+      const double2 y = reinterpret_cast<const double2*>(y_in)[i];
+      double a0 = alpha * y.x, a1 = alpha * y.y;
+      for (int k = 0; k < K; ++k) {
+        const double2 v = __ldg(reinterpret_cast<const double2*>(V + (size_t)k * ldv) + i);
+        a0 = fma(sc[1 + k], v.x, a0);
+        a1 = fma(sc[1 + k], v.y, a1);
+      }
+      reinterpret_cast<double2*>(out)[i] = make_double2(a0, a1);
+    }
+    if ((n & 1) && gid == 0) {
+      const int64_t i = n - 1;
+      double a0 = alpha * y_in[i];
+      for (int k = 0; k < K; ++k) a0 = fma(sc[1 + k], V[(size_t)k * ldv + i], a0);
+      out[i] = a0;
+    }
+  } else {
+    for (int64_t i = gid; i < n; i += stride) {
+      double a0 = alpha * y_in[i];
+      for (int k = 0; k < K; ++k) a0 = fma(sc[1 + k], V[(size_t)k * ldv + i], a0);
+      out[i] = a0;
+    }
+  }
+}
+
+// --------------------------------------------------------------------------
+// MGS-GMRES kernels (Algorithm 6)
+// --------------------------------------------------------------------------
+// Step i, first kernel: w = A v_i = scale_i * (A u_i) written into column i+1,
+// fused with the first inner product p = u_0^T w; the epilogue sets
+// h_0 = scale_0 p = H(0, i).
+__global__ void __launch_bounds__(kThreads, 2)
+k_mgs_spmv(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+           const double* __restrict__ val, double* __restrict__ V, int64_t ldv, int64_t n, Small s) {
+  __shared__ double sbuf[kWarps];
+  __shared__ double red[2];
+  __shared__ int s_i, s_skip;
+  __shared__ double s_si;
+  DevState* st = s.st;
+  if (threadIdx.x == 0) {
+    s_skip = __ldcg(&st->done);
+    s_i = __ldcg(&st->step);
+    s_si = __ldcg(&s.scale[s_i]);
+  }
+  __syncthreads();
+  if (s_skip) return;
+  const int i = s_i;
+  const double si = s_si;
+  const double* u = V + (size_t)i * ldv;
+  double* w = V + (size_t)(i + 1) * ldv;
+  const double* u0 = V;
+  double acc = 0.0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride) {
+    const double wr = si * csr_row(rowptr, col, val, u, r);
+    w[r] = wr;
+    acc = fma(wr, u0[r], acc);
+  }
+  const double tot = block_sum(acc, sbuf);
+  if (threadIdx.x == 0) red[0] = tot;
+  __syncthreads();
+  if (!grid_reduce_last(s, red, 1)) return;
+  if (threadIdx.x == 0) {
+    st->grid_syncs += 1;
+    const double h = s.scale[0] * red[0];
+    s.H[(size_t)i * s.ldh + 0] = h;
+    st->mgs_coef = h * s.scale[0];
+    st->inner = 0;
+  }
+}
+
+// Step i, inner kernel k: w -= h_k v_k, fused with the next reduction:
+// h_{k+1} = v_{k+1}^T w (k < i) or ||w||^2 (k == i). The last inner kernel
+// completes column i of H, rotates it, tests convergence and stores
+// scale[i+1] = 1 / ||w||, so column i+1 becomes v_{i+1} without a rewrite.
+__global__ void __launch_bounds__(kThreads, 2)
+k_mgs_axpy_dot(double* __restrict__ V, int64_t ldv, int64_t n, Small s) {
+  __shared__ double sbuf[kWarps];
+  __shared__ double red[2];
+  __shared__ int s_i, s_k, s_skip;
+  __shared__ double s_cf;
+  DevState* st = s.st;
+  if (threadIdx.x == 0) {
+    s_skip = __ldcg(&st->done);
+    s_i = __ldcg(&st->step);
+    s_k = __ldcg(&st->inner);
+    s_cf = __ldcg(&st->mgs_coef);
+  }
+  __syncthreads();
+  if (s_skip) return;
+  const int i = s_i, k = s_k;
+  const double cf = s_cf;
+  double* w = V + (size_t)(i + 1) * ldv;
+  const double* uk = V + (size_t)k * ldv;
+  const bool last = (k == i);
+  const double* un = last ? w : V + (size_t)(k + 1) * ldv;
+  double acc = 0.0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride) {
+    const double wr = fma(-cf, uk[r], w[r]);
+    w[r] = wr;
+    acc = fma(wr, last ? wr : un[r], acc);
+  }
+  const double tot = block_sum(acc, sbuf);
+  if (threadIdx.x == 0) red[0] = tot;
+  __syncthreads();
+  if (!grid_reduce_last(s, red, 1)) return;
+  if (threadIdx.x == 0) {
+    st->grid_syncs += 1;
+    const int ld = s.ldh;
+    if (!last) {
+      const double h = s.scale[k + 1] * red[0];
+      s.H[(size_t)i * ld + k + 1] = h;
+      st->mgs_coef = h * s.scale[k + 1];
+      st->inner = k + 1;
+    } else {
+      const double hn = sqrt(red[0]);
+      s.H[(size_t)i * ld + i + 1] = hn;
+      s.scale[i + 1] = 1.0 / hn;
+      const int stop = finish_column(s, i, hn, i + 1 == st->kmax);
+      st->step = i + 1;
+      st->inner = 0;
+      if (stop) st->done = 1;
+    }
+  }
+}
+
+// --------------------------------------------------------------------------
+// residual, norms, least squares, export
+// --------------------------------------------------------------------------
+enum { RES_BNORM = 0, RES_RESIDUAL = 1, RES_START = 2 };
+
+// mode RES_BNORM:    ||b|| -> st->bnorm
+// mode RES_RESIDUAL: r = b - A x -> column 0, ||r|| -> st->rnorm, and the
+//                    cycle state is reset (x == nullptr means x = 0).
+// mode RES_START:    column 0 = b (a given start vector), ||b|| -> bnorm and rnorm.
+__global__ void __launch_bounds__(kThreads, 2)
+k_residual(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+           const double* __restrict__ val, const double* __restrict__ b, const double* __restrict__ x,
+           double* __restrict__ V0, int64_t n, Small s, int mode, int kmax) {
+  __shared__ double sbuf[kWarps];
+  __shared__ double red[2];
+  double acc = 0.0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride) {
+    double v = b[r];
+    if (mode == RES_RESIDUAL && x) v -= csr_row(rowptr, col, val, x, r);
+    if (mode != RES_BNORM) V0[r] = v;
+    acc = fma(v, v, acc);
+  }
+  const double tot = block_sum(acc, sbuf);
+  if (threadIdx.x == 0) red[0] = tot;
+  __syncthreads();
+  if (!grid_reduce_last(s, red, 1)) return;
+  if (threadIdx.x == 0) {
+    DevState* st = s.st;
+    st->grid_syncs += 1;
+    const double nr = sqrt(red[0]);
+    if (mode == RES_BNORM) {
+      st->bnorm = nr;
+      return;
+    }
+    if (mode == RES_START) st->bnorm = nr;
+    st->rnorm = nr;
+    st->step = 0;
+    st->inner = 0;
+    st->kmax = kmax;
+    st->k = 0;
+    st->done = 0;
+    st->converged = 0;
+    st->breakdown = 0;
+    st->nonfinite = isfinite(nr) ? 0 : 1;
+    st->maxpy_k = 0;
+    s.g[0] = nr;
+    s.scale[0] = 1.0 / nr;
+    for (int i = 1; i <= s.m + 1; ++i) s.g[i] = 0.0;
+  }
+}
+
+// Back substitution R(0:k,0:k) y = g(0:k) (column-oriented), then the
+// coefficients of x += V_k y in the unnormalized basis, and the cycle totals.
+__global__ void k_lsq(Small s) {
+  __shared__ double y[kMaxM + 1];
+  __shared__ int sk;
+  DevState* st = s.st;
+  if (threadIdx.x == 0) sk = st->k;
+  __syncthreads();
+  const int k = sk;
+  const int ld = s.ldh;
+  for (int l = threadIdx.x; l < k; l += blockDim.x) y[l] = s.g[l];
+  __syncthreads();
+  for (int i = k - 1; i >= 0; --i) {
+    if (threadIdx.x == 0) y[i] = y[i] / s.Rg[(size_t)i * ld + i];
+    __syncthreads();
+    const double yi = y[i];
+    for (int l = threadIdx.x; l < i; l += blockDim.x) y[l] = fma(-s.Rg[(size_t)i * ld + l], yi, y[l]);
+    __syncthreads();
+  }
+  for (int l = threadIdx.x; l < k; l += blockDim.x) s.coefx[1 + l] = y[l] * s.scale[l];
+  if (threadIdx.x == 0) {
+    s.coefx[0] = 1.0;
+    st->total_iters += k;
+    st->restarts += 1;
+    st->breakdowns += st->breakdown;
+  }
+}
+
+// V_out[:, k] = scale[k] * V[:, k] for k <= kk (normalized basis export).
+__global__ void k_export_basis(const double* __restrict__ V, int64_t ldv, double* __restrict__ Vo,
+                               int64_t n, int kk, Small s) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int k = 0; k <= kk; ++k) {
+    const double sc = s.scale[k];
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride)
+      Vo[(size_t)k * n + r] = sc * V[(size_t)k * ldv + r];
+  }
+}
+
+__global__ void k_spmv(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                       const double* __restrict__ val, const double* __restrict__ x, double* __restrict__ y,
+                       int64_t n) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride)
+    y[r] = csr_row(rowptr, col, val, x, r);
+}
+
+using StepKernel = void (*)(const int32_t*, const int32_t*, const double*, const double*, int64_t,
+                            const double*, double*, int64_t, Small, int, int, double*);
+
+StepKernel step_kernel_for(int m) {
+  if (m <= 1 * kWarps) return k_one_reduce_step<1>;
+  if (m <= 2 * kWarps) return k_one_reduce_step<2>;
+  if (m <= 4 * kWarps) return k_one_reduce_step<4>;
+  if (m <= 8 * kWarps) return k_one_reduce_step<8>;
+  return k_one_reduce_step<16>;
+}
+
+}  // namespace
+
+// ==========================================================================
+// host side
+// ==========================================================================
+struct gmres_ctx {
+  int64_t n = 0, nnz = 0;
+  int m = 0;
+  double tol = 0.0;
+  int max_iter = 0;
+  int ortho = GMRES_ONE_REDUCE_MGS;
+  int prec = GMRES_FP64;
+  int device = 0;
+  int nsm = 0;
+  int P = 0;          // CTAs of reduction kernels
+  int grid_stream = 0;// CTAs of streaming kernels
+  int32_t* rowptr = nullptr;
+  int32_t* col = nullptr;
+  double* val = nullptr;
+  double* V = nullptr;
+  int64_t ldv = 0;
+  double* w = nullptr;
+  char* small = nullptr;
+  Small s{};
+  DevState* h_st = nullptr;  // pinned mirror
+  cudaStream_t stream = nullptr;
+  StepKernel step = nullptr;
+  std::vector<double> hist;
+  int hist_len = 0;
+  double* h_b = nullptr;  // pinned staging for gmres_solve_host
+  double* h_x = nullptr;
+  double* d_b = nullptr;  // device staging for gmres_solve_host
+  double* d_x = nullptr;
+  int64_t launches = 0;
+  std::string err;
+  // per-kernel timing (gmres_set_profile)
+  struct ProfRec {
+    int cls, j, i;
+    cudaEvent_t a, b;
+  };
+  bool prof_on = false;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  std::vector<ProfRec> recs;
+  double prof_ms[GMRES_PROFILE_CLASSES] = {};
+  double prof_bytes[GMRES_PROFILE_CLASSES] = {};
+  double prof_flops[GMRES_PROFILE_CLASSES] = {};
+  int64_t prof_cnt[GMRES_PROFILE_CLASSES] = {};
+};
+
+namespace {
+
+std::string g_create_err;
+
+gmres_status fail(gmres_ctx* h, gmres_status st, const std::string& msg) {
+  if (h)
+    h->err = msg;
+  else
+    g_create_err = msg;
+  return st;
+}
+
+#define CUDA_TRY(h, call)                                                                        \
+  do {                                                                                           \
+    cudaError_t e_ = (call);                                                                     \
+    if (e_ != cudaSuccess)                                                                       \
+      return fail(h, e_ == cudaErrorMemoryAllocation ? GMRES_ERR_OOM : GMRES_ERR_CUDA,           \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                           \
+  } while (0)
+
+#define LAUNCH_CHECK(h)                                                                          \
+  do {                                                                                           \
+    cudaError_t e_ = cudaGetLastError();                                                         \
+    if (e_ != cudaSuccess) return fail(h, GMRES_ERR_CUDA, std::string("launch: ") + cudaGetErrorString(e_)); \
+  } while (0)
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+gmres_status alloc_small(gmres_ctx* h) {
+  const int m = h->m, ld = m + 1;
+  const int nvmax = 2 * (m + 1) + 2;
+  h->s.m = m;
+  h->s.ldh = ld;
+  h->s.nvmax = nvmax;
+  h->s.hist_cap = h->max_iter + m + 1;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off = align_up(off + bytes, 256);
+    return o;
+  };
+  const size_t o_st = take(sizeof(DevState));
+  const size_t o_H = take(sizeof(double) * ld * m);
+  const size_t o_R = take(sizeof(double) * ld * m);
+  const size_t o_cs = take(sizeof(double) * (m + 1));
+  const size_t o_sn = take(sizeof(double) * (m + 1));
+  const size_t o_g = take(sizeof(double) * (m + 2));
+  const size_t o_T = take(sizeof(double) * ld * ld);
+  const size_t o_sc = take(sizeof(double) * (m + 2));
+  const size_t o_cf = take(sizeof(double) * (m + 3));
+  const size_t o_cx = take(sizeof(double) * (m + 3));
+  const size_t o_hi = take(sizeof(double) * h->s.hist_cap);
+  const size_t o_pa = take(sizeof(double) * (size_t)h->P * nvmax);
+  const size_t o_raw = take(sizeof(double) * nvmax);
+  if (h->small) cudaFree(h->small);
+  h->small = nullptr;
+  CUDA_TRY(h, cudaMalloc(&h->small, off));
+  CUDA_TRY(h, cudaMemset(h->small, 0, off));
+  char* b = h->small;
+  h->s.st = reinterpret_cast<DevState*>(b + o_st);
+  h->s.H = reinterpret_cast<double*>(b + o_H);
+  h->s.Rg = reinterpret_cast<double*>(b + o_R);
+  h->s.cs = reinterpret_cast<double*>(b + o_cs);
+  h->s.sn = reinterpret_cast<double*>(b + o_sn);
+  h->s.g = reinterpret_cast<double*>(b + o_g);
+  h->s.T = reinterpret_cast<double*>(b + o_T);
+  h->s.scale = reinterpret_cast<double*>(b + o_sc);
+  h->s.coef = reinterpret_cast<double*>(b + o_cf);
+  h->s.coefx = reinterpret_cast<double*>(b + o_cx);
+  h->s.hist = reinterpret_cast<double*>(b + o_hi);
+  h->s.partials = reinterpret_cast<double*>(b + o_pa);
+  h->s.raw = reinterpret_cast<double*>(b + o_raw);
+  h->hist.assign(h->s.hist_cap, 0.0);
+  return GMRES_OK;
+}
+
+gmres_status read_state(gmres_ctx* h) {
+  CUDA_TRY(h, cudaMemcpyAsync(h->h_st, h->s.st, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  return GMRES_OK;
+}
+
+gmres_status write_state(gmres_ctx* h) {
+  CUDA_TRY(h, cudaMemcpyAsync(h->s.st, h->h_st, sizeof(DevState), cudaMemcpyHostToDevice, h->stream));
+  return GMRES_OK;
+}
+
+int prof_begin(gmres_ctx* h, int cls, int j, int i);
+void prof_end(gmres_ctx* h, int idx);
+
+// Launch the kernels of one cycle of kmax steps (the state was reset by the
+// residual kernel). Kernels past the end of the cycle return at once.
+gmres_status launch_cycle(gmres_ctx* h, int kmax) {
+  const int P = h->P;
+  if (h->ortho == GMRES_ONE_REDUCE_MGS) {
+    for (int j = 0; j <= kmax; ++j) {
+      int pr = prof_begin(h, 0, j, kmax);
+      h->step<<<P, kThreads, 0, h->stream>>>(h->rowptr, h->col, h->val, h->V, h->ldv, nullptr, h->w, h->n,
+                                            h->s, 0, 1, nullptr);
+      prof_end(h, pr);
+      ++h->launches;
+      if (j < kmax) {
+        pr = prof_begin(h, 1, j, 0);
+        k_maxpy<<<h->grid_stream, kThreads, 0, h->stream>>>(h->V, h->ldv, h->w, nullptr, h->n, h->s,
+                                                             MAXPY_ARNOLDI, 0);
+        prof_end(h, pr);
+        ++h->launches;
+      }
+    }
+  } else {
+    for (int i = 0; i < kmax; ++i) {
+      int pr = prof_begin(h, 2, i, 0);
+      k_mgs_spmv<<<P, kThreads, 0, h->stream>>>(h->rowptr, h->col, h->val, h->V, h->ldv, h->n, h->s);
+      prof_end(h, pr);
+      ++h->launches;
+      for (int k = 0; k <= i; ++k) {
+        pr = prof_begin(h, 3, i, k);
+        k_mgs_axpy_dot<<<P, kThreads, 0, h->stream>>>(h->V, h->ldv, h->n, h->s);
+        prof_end(h, pr);
+        ++h->launches;
+      }
+    }
+  }
+  LAUNCH_CHECK(h);
+  return GMRES_OK;
+}
+
+gmres_status check_ptr(gmres_ctx* h, const void* p, const char* what) {
+  if (!p) return fail(h, GMRES_ERR_ARG, std::string(what) + " is NULL");
+  if (reinterpret_cast<uintptr_t>(p) & 7) return fail(h, GMRES_ERR_ARG, std::string(what) + " is not 8-byte aligned");
+  return GMRES_OK;
+}
+
+enum { PC_STEP = 0, PC_MAXPY = 1, PC_MGS_SPMV = 2, PC_MGS_AXPY = 3, PC_RES = 4, PC_LSQ = 5, PC_XUPD = 6,
+       PC_NOOP = 7 };
+
+// Record an event pair around the next launch (no-op unless profiling).
+int prof_begin(gmres_ctx* h, int cls, int j, int i) {
+  if (!h->prof_on) return -1;
+  while (h->ev_used + 2 > h->ev_pool.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return -1;
+    h->ev_pool.push_back(e);
+  }
+  gmres_ctx::ProfRec r{cls, j, i, h->ev_pool[h->ev_used], h->ev_pool[h->ev_used + 1]};
+  h->ev_used += 2;
+  cudaEventRecord(r.a, h->stream);
+  h->recs.push_back(r);
+  return (int)h->recs.size() - 1;
+}
+
+void prof_end(gmres_ctx* h, int idx) {
+  if (idx >= 0) cudaEventRecord(h->recs[idx].b, h->stream);
+}
+
+// Algorithmic traffic and flops of one launch that did work (FP64: 8-byte
+// values, 4-byte indices; a vector read once counts once).
+void alg_model(const gmres_ctx* h, const gmres_ctx::ProfRec& r, int kx, double* bytes, double* flops) {
+  const double n = (double)h->n, nnz = (double)h->nnz;
+  const double csr = 4.0 * (n + 1) + 12.0 * nnz;
+  switch (r.cls) {
+    case PC_STEP:
+      if (r.j == r.i) {  // tail: u and V_j, no SpMV (r.i carries kmax)
+        *bytes = 8.0 * n * (r.j + 1);
+        *flops = 2.0 * n * (r.j + 1);
+      } else {
+        *bytes = csr + 8.0 * n * (r.j + 2);  // u (gathered), j basis columns, w written
+        *flops = 2.0 * nnz + 2.0 * n * (2.0 * r.j + 2.0);
+      }
+      break;
+    case PC_MAXPY:  // w, j+1 columns read, one column written
+      *bytes = 8.0 * n * (r.j + 3);
+      *flops = 2.0 * n * (r.j + 1) + n;
+      break;
+    case PC_MGS_SPMV:  // u_i gathered, u_0 read, w written
+      *bytes = csr + 24.0 * n;
+      *flops = 2.0 * nnz + 3.0 * n;
+      break;
+    case PC_MGS_AXPY:  // w read+written, u_k, u_{k+1} read (the last reads only u_k)
+      *bytes = (r.i == r.j) ? 24.0 * n : 32.0 * n;
+      *flops = 4.0 * n;
+      break;
+    case PC_RES:
+      *bytes = (r.j == 0) ? 8.0 * n : csr + 24.0 * n;
+      *flops = (r.j == 0) ? 2.0 * n : 2.0 * nnz + 3.0 * n;
+      break;
+    case PC_XUPD:
+      *bytes = 8.0 * n * (kx + 2);
+      *flops = 2.0 * n * kx + n;
+      break;
+    default:
+      *bytes = 0.0;
+      *flops = 0.0;
+  }
+}
+
+// After the stream is synchronized: attribute the recorded launches of one
+// cycle that completed k columns (work or no-op) and recycle the events.
+void prof_settle(gmres_ctx* h, int k) {
+  if (!h->prof_on) return;
+  for (const auto& r : h->recs) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, r.a, r.b);
+    bool work = true;
+    if (r.cls == PC_STEP) work = r.j <= k;
+    else if (r.cls == PC_MAXPY) work = r.j < k;
+    else if (r.cls == PC_MGS_SPMV || r.cls == PC_MGS_AXPY) work = r.j < k;
+    const int c = work ? r.cls : PC_NOOP;
+    h->prof_ms[c] += ms;
+    h->prof_cnt[c] += 1;
+    if (work) {
+      double by, fl;
+      alg_model(h, r, k, &by, &fl);
+      h->prof_bytes[c] += by;
+      h->prof_flops[c] += fl;
+    }
+  }
+  h->recs.clear();
+  h->ev_used = 0;
+}
+
+void prof_reset(gmres_ctx* h) {
+  for (int c = 0; c < GMRES_PROFILE_CLASSES; ++c) {
+    h->prof_ms[c] = h->prof_bytes[c] = h->prof_flops[c] = 0.0;
+    h->prof_cnt[c] = 0;
+  }
+  h->recs.clear();
+  h->ev_used = 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+gmres_status gmres_create(const gmres_csr* A, int m_restart, double tol, gmres_handle* out) {
+  if (!out) return fail(nullptr, GMRES_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!A || !A->rowptr || (A->nnz > 0 && (!A->col || !A->val)))
+    return fail(nullptr, GMRES_ERR_ARG, "A or its arrays are NULL");
+  if (A->n <= 0 || A->nnz < 0 || A->nnz >= (int64_t)INT32_MAX || A->n >= (int64_t)INT32_MAX)
+    return fail(nullptr, GMRES_ERR_ARG, "n must be in [1, 2^31) and nnz in [0, 2^31)");
+  if (m_restart < 1 || m_restart > kMaxM) return fail(nullptr, GMRES_ERR_ARG, "m_restart must be in [1, 128]");
+  if (!(tol >= 0.0)) return fail(nullptr, GMRES_ERR_ARG, "tol must be >= 0");
+  const int64_t n = A->n, nnz = A->nnz;
+  // host copies for validation
+  std::vector<int32_t> rp(n + 1), cl(nnz);
+  std::vector<double> vl(nnz);
+  if (A->on_device) {
+    if (cudaMemcpy(rp.data(), A->rowptr, sizeof(int32_t) * (n + 1), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        (nnz && cudaMemcpy(cl.data(), A->col, sizeof(int32_t) * nnz, cudaMemcpyDeviceToHost) != cudaSuccess) ||
+        (nnz && cudaMemcpy(vl.data(), A->val, sizeof(double) * nnz, cudaMemcpyDeviceToHost) != cudaSuccess))
+      return fail(nullptr, GMRES_ERR_CUDA, "cannot read device CSR arrays");
+  } else {
+    std::memcpy(rp.data(), A->rowptr, sizeof(int32_t) * (n + 1));
+    if (nnz) {
+      std::memcpy(cl.data(), A->col, sizeof(int32_t) * nnz);
+      std::memcpy(vl.data(), A->val, sizeof(double) * nnz);
+    }
+  }
+  if (rp[0] != 0 || rp[n] != nnz) return fail(nullptr, GMRES_ERR_ARG, "rowptr[0] must be 0 and rowptr[n] = nnz");
+  for (int64_t i = 0; i < n; ++i)
+    if (rp[i + 1] < rp[i]) return fail(nullptr, GMRES_ERR_ARG, "rowptr is not nondecreasing");
+  for (int64_t p = 0; p < nnz; ++p)
+    if (cl[p] < 0 || cl[p] >= n) return fail(nullptr, GMRES_ERR_ARG, "column index out of range");
+  for (int64_t p = 0; p < nnz; ++p)
+    if (!std::isfinite(vl[p])) return fail(nullptr, GMRES_ERR_NONFINITE, "non-finite matrix value");
+
+  gmres_ctx* h = new gmres_ctx();
+  h->n = n;
+  h->nnz = nnz;
+  h->m = m_restart;
+  h->tol = tol;
+  h->max_iter = 10 * m_restart;
+  auto bail = [&](gmres_status st) {
+    g_create_err = h->err;
+    gmres_destroy(h);
+    return st;
+  };
+#define CREATE_TRY(call)                                                               \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess) {                                                           \
+      h->err = std::string(#call) + ": " + cudaGetErrorString(e_);                     \
+      return bail(e_ == cudaErrorMemoryAllocation ? GMRES_ERR_OOM : GMRES_ERR_CUDA);   \
+    }                                                                                  \
+  } while (0)
+  CREATE_TRY(cudaGetDevice(&h->device));
+  CREATE_TRY(cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, h->device));
+  const int64_t ntiles = (n + kThreads - 1) / kThreads;
+  h->P = (int)std::min<int64_t>(2 * (int64_t)h->nsm, ntiles);
+  h->grid_stream = (int)std::min<int64_t>(4 * (int64_t)h->nsm, std::max<int64_t>(1, (n / 2 + kThreads - 1) / kThreads));
+  const int64_t nnz_pad = align_up(std::max<int64_t>(nnz, 1), 4);
+  CREATE_TRY(cudaMalloc(&h->rowptr, sizeof(int32_t) * (n + 1)));
+  CREATE_TRY(cudaMalloc(&h->col, sizeof(int32_t) * nnz_pad));
+  CREATE_TRY(cudaMalloc(&h->val, sizeof(double) * nnz_pad));
+  CREATE_TRY(cudaMemset(h->col, 0, sizeof(int32_t) * nnz_pad));
+  CREATE_TRY(cudaMemset(h->val, 0, sizeof(double) * nnz_pad));
+  CREATE_TRY(cudaMemcpy(h->rowptr, rp.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice));
+  if (nnz) {
+    CREATE_TRY(cudaMemcpy(h->col, cl.data(), sizeof(int32_t) * nnz, cudaMemcpyHostToDevice));
+    CREATE_TRY(cudaMemcpy(h->val, vl.data(), sizeof(double) * nnz, cudaMemcpyHostToDevice));
+  }
+  h->ldv = (int64_t)align_up((size_t)n, 32);
+  CREATE_TRY(cudaMalloc(&h->V, sizeof(double) * (size_t)h->ldv * (m_restart + 1)));
+  CREATE_TRY(cudaMemset(h->V, 0, sizeof(double) * (size_t)h->ldv * (m_restart + 1)));
+  CREATE_TRY(cudaMalloc(&h->w, sizeof(double) * (size_t)h->ldv));
+  CREATE_TRY(cudaMemset(h->w, 0, sizeof(double) * (size_t)h->ldv));
+  CREATE_TRY(cudaMallocHost(&h->h_st, sizeof(DevState)));
+  std::memset(h->h_st, 0, sizeof(DevState));
+  if (alloc_small(h) != GMRES_OK) return bail(GMRES_ERR_CUDA);
+  h->step = step_kernel_for(m_restart);
+  CREATE_TRY(cudaFuncSetAttribute(reinterpret_cast<const void*>(h->step),
+                                  cudaFuncAttributePreferredSharedMemoryCarveout, 50));
+#undef CREATE_TRY
+  *out = h;
+  return GMRES_OK;
+}
+
+gmres_status gmres_set(gmres_handle h, gmres_ortho ortho, gmres_prec prec, int max_iter) {
+  if (!h) return GMRES_ERR_ARG;
+  if (ortho != GMRES_MGS && ortho != GMRES_ONE_REDUCE_MGS) return fail(h, GMRES_ERR_ARG, "unknown ortho");
+  if (prec != GMRES_FP64) return fail(h, GMRES_ERR_ARG, "only GMRES_FP64 is implemented");
+  if (max_iter < 0) return fail(h, GMRES_ERR_ARG, "max_iter < 0");
+  h->ortho = ortho;
+  h->prec = prec;
+  if (max_iter != h->max_iter) {
+    h->max_iter = max_iter;
+    gmres_status st = alloc_small(h);
+    if (st != GMRES_OK) return st;
+  }
+  return GMRES_OK;
+}
+
+gmres_status gmres_set_tol(gmres_handle h, double tol) {
+  if (!h) return GMRES_ERR_ARG;
+  if (!(tol >= 0.0)) return fail(h, GMRES_ERR_ARG, "tol must be >= 0");
+  h->tol = tol;
+  return GMRES_OK;
+}
+
+gmres_status gmres_set_stream(gmres_handle h, void* stream) {
+  if (!h) return GMRES_ERR_ARG;
+  h->stream = reinterpret_cast<cudaStream_t>(stream);
+  return GMRES_OK;
+}
+
+gmres_status gmres_solve(gmres_handle h, const double* b, double* x, gmres_info* info) {
+  if (!h) return GMRES_ERR_ARG;
+  gmres_status st;
+  if ((st = check_ptr(h, b, "b")) != GMRES_OK) return st;
+  if ((st = check_ptr(h, x, "x")) != GMRES_OK) return st;
+  CUDA_TRY(h, cudaSetDevice(h->device));
+  const auto t0 = std::chrono::steady_clock::now();
+  h->launches = 0;
+  // fresh state
+  std::memset(h->h_st, 0, sizeof(DevState));
+  h->h_st->tol = h->tol;
+  if ((st = write_state(h)) != GMRES_OK) return st;
+  const int P = h->P;
+  prof_reset(h);
+  int pr = prof_begin(h, PC_RES, 0, 0);
+  k_residual<<<P, kThreads, 0, h->stream>>>(h->rowptr, h->col, h->val, b, nullptr, nullptr, h->n, h->s, RES_BNORM, 0);
+  prof_end(h, pr);
+  ++h->launches;
+  LAUNCH_CHECK(h);
+  if ((st = read_state(h)) != GMRES_OK) return st;
+  const double bnorm = h->h_st->bnorm;
+  gmres_status result = GMRES_OK;
+  h->hist_len = 0;
+  if (!std::isfinite(bnorm)) {
+    result = GMRES_ERR_NONFINITE;
+    fail(h, result, "b contains NaN or Inf");
+  } else if (bnorm == 0.0) {
+    CUDA_TRY(h, cudaMemsetAsync(x, 0, sizeof(double) * h->n, h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    h->h_st->rnorm = 0.0;
+  } else {
+    int prev_total = 0;
+    for (;;) {
+      pr = prof_begin(h, PC_RES, 1, 0);
+      k_residual<<<P, kThreads, 0, h->stream>>>(h->rowptr, h->col, h->val, b, x, h->V, h->n, h->s, RES_RESIDUAL, 0);
+      prof_end(h, pr);
+      ++h->launches;
+      LAUNCH_CHECK(h);
+      if ((st = read_state(h)) != GMRES_OK) return st;
+      const DevState& hs = *h->h_st;
+      prof_settle(h, hs.total_iters - prev_total);
+      prev_total = hs.total_iters;
+      if (!std::isfinite(hs.rnorm) || hs.nonfinite) {
+        result = GMRES_ERR_NONFINITE;
+        fail(h, result, "non-finite residual (NaN or Inf in x0 or the iteration)");
+        break;
+      }
+      if (hs.rnorm / bnorm <= h->tol) {
+        result = GMRES_OK;
+        break;
+      }
+      if (hs.total_iters >= h->max_iter) {
+        result = GMRES_MAXITER;
+        break;
+      }
+      const int kmax = std::min(h->m, h->max_iter - hs.total_iters);
+      h->h_st->kmax = kmax;
+      // only kmax changes on the host side; write it without touching the rest
+      CUDA_TRY(h, cudaMemcpyAsync(&h->s.st->kmax, &h->h_st->kmax, sizeof(int), cudaMemcpyHostToDevice, h->stream));
+      if ((st = launch_cycle(h, kmax)) != GMRES_OK) return st;
+      pr = prof_begin(h, PC_LSQ, 0, 0);
+      k_lsq<<<1, 128, 0, h->stream>>>(h->s);
+      prof_end(h, pr);
+      pr = prof_begin(h, PC_XUPD, 0, 0);
+      k_maxpy<<<h->grid_stream, kThreads, 0, h->stream>>>(h->V, h->ldv, x, x, h->n, h->s, MAXPY_XUPDATE, 0);
+      prof_end(h, pr);
+      h->launches += 2;
+      LAUNCH_CHECK(h);
+    }
+  }
+  if ((st = read_state(h)) != GMRES_OK) return st;
+  const DevState& hs = *h->h_st;
+  h->hist_len = std::min(hs.total_iters, h->s.hist_cap);
+  if (h->hist_len > 0)
+    CUDA_TRY(h, cudaMemcpy(h->hist.data(), h->s.hist, sizeof(double) * h->hist_len, cudaMemcpyDeviceToHost));
+  const auto t1 = std::chrono::steady_clock::now();
+  if (info) {
+    std::memset(info, 0, sizeof(*info));
+    info->iters = hs.total_iters;
+    info->restarts = hs.restarts;
+    info->status = result;
+    info->breakdowns = hs.breakdowns;
+    info->rel_resid_true = bnorm > 0.0 ? hs.rnorm / bnorm : 0.0;
+    info->rel_resid_est = hs.est;
+    info->reductions = hs.reductions;
+    info->grid_syncs = hs.grid_syncs;
+    info->kernel_launches = h->launches;
+    info->seconds = std::chrono::duration<double>(t1 - t0).count();
+  }
+  return result;
+}
+
+gmres_status gmres_solve_host(gmres_handle h, const double* b_host, double* x_host, gmres_info* info) {
+  if (!h) return GMRES_ERR_ARG;
+  if (!b_host || !x_host) return fail(h, GMRES_ERR_ARG, "b_host or x_host is NULL");
+  const size_t bytes = sizeof(double) * h->n;
+  if (!h->d_b) {
+    CUDA_TRY(h, cudaMalloc(&h->d_b, bytes));
+    CUDA_TRY(h, cudaMalloc(&h->d_x, bytes));
+  }
+  CUDA_TRY(h, cudaMemcpyAsync(h->d_b, b_host, bytes, cudaMemcpyHostToDevice, h->stream));
+  CUDA_TRY(h, cudaMemcpyAsync(h->d_x, x_host, bytes, cudaMemcpyHostToDevice, h->stream));
+  gmres_status st = gmres_solve(h, h->d_b, h->d_x, info);
+  CUDA_TRY(h, cudaMemcpyAsync(x_host, h->d_x, bytes, cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  return st;
+}
+
+gmres_status gmres_history(gmres_handle h, double* host_buf, int cap, int* len) {
+  if (!h) return GMRES_ERR_ARG;
+  if (len) *len = h->hist_len;
+  if (host_buf && cap > 0) std::memcpy(host_buf, h->hist.data(), sizeof(double) * std::min(cap, h->hist_len));
+  return GMRES_OK;
+}
+
+gmres_status gmres_destroy(gmres_handle h) {
+  if (!h) return GMRES_OK;
+  cudaFree(h->rowptr);
+  cudaFree(h->col);
+  cudaFree(h->val);
+  cudaFree(h->V);
+  cudaFree(h->w);
+  cudaFree(h->small);
+  cudaFree(h->d_b);
+  cudaFree(h->d_x);
+  if (h->h_st) cudaFreeHost(h->h_st);
+  for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+  delete h;
+  return GMRES_OK;
+}
+
+const char* gmres_last_error(gmres_handle h) { return h ? h->err.c_str() : g_create_err.c_str(); }
+
+gmres_status gmres_set_profile(gmres_handle h, int on) {
+  if (!h) return GMRES_ERR_ARG;
+  h->prof_on = on != 0;
+  prof_reset(h);
+  return GMRES_OK;
+}
+
+gmres_status gmres_profile(gmres_handle h, int cls, double* total_ms, int64_t* launches, double* alg_bytes,
+                           double* alg_flops) {
+  if (!h) return GMRES_ERR_ARG;
+  if (cls < 0 || cls >= GMRES_PROFILE_CLASSES) return fail(h, GMRES_ERR_ARG, "profile class out of range");
+  if (total_ms) *total_ms = h->prof_ms[cls];
+  if (launches) *launches = h->prof_cnt[cls];
+  if (alg_bytes) *alg_bytes = h->prof_bytes[cls];
+  if (alg_flops) *alg_flops = h->prof_flops[cls];
+  return GMRES_OK;
+}
+
+gmres_status lsg_spmv(gmres_handle h, const double* x, double* y) {
+  if (!h) return GMRES_ERR_ARG;
+  gmres_status st;
+  if ((st = check_ptr(h, x, "x")) != GMRES_OK) return st;
+  if ((st = check_ptr(h, y, "y")) != GMRES_OK) return st;
+  k_spmv<<<h->grid_stream, kThreads, 0, h->stream>>>(h->rowptr, h->col, h->val, x, y, h->n);
+  LAUNCH_CHECK(h);
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  return GMRES_OK;
+}
+
+gmres_status lsg_block_dot(gmres_handle h, const double* V, int64_t ldv, int j, const double* u, double* w,
+                           int use_spmv, double* X) {
+  if (!h) return GMRES_ERR_ARG;
+  if (j < 0 || j > h->m) return fail(h, GMRES_ERR_ARG, "j must be in [0, m]");
+  if ((j > 0 && (!V || ldv < h->n)) || !u || !w || !X) return fail(h, GMRES_ERR_ARG, "bad pointer or ldv");
+  h->step<<<h->P, kThreads, 0, h->stream>>>(h->rowptr, h->col, h->val, V, ldv, u, w, h->n, h->s, j, use_spmv,
+                                            h->s.raw);
+  LAUNCH_CHECK(h);
+  CUDA_TRY(h, cudaMemcpyAsync(X, h->s.raw, sizeof(double) * (2 * j + 2), cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  return GMRES_OK;
+}
+
+gmres_status lsg_maxpy(gmres_handle h, const double* V, int64_t ldv, int K, const double* c, double alpha,
+                       const double* y_in, double* y_out) {
+  if (!h) return GMRES_ERR_ARG;
+  if (K < 0 || K > h->m + 1) return fail(h, GMRES_ERR_ARG, "K must be in [0, m+1]");
+  if ((K > 0 && (!V || !c || ldv < h->n)) || !y_in || !y_out) return fail(h, GMRES_ERR_ARG, "bad pointer or ldv");
+  std::vector<double> cf(K + 1);
+  cf[0] = alpha;
+  for (int k = 0; k < K; ++k) cf[1 + k] = c[k];
+  CUDA_TRY(h, cudaMemcpyAsync(h->s.coef, cf.data(), sizeof(double) * (K + 1), cudaMemcpyHostToDevice, h->stream));
+  k_maxpy<<<h->grid_stream, kThreads, 0, h->stream>>>(V, ldv, y_in, y_out, h->n, h->s, MAXPY_STANDALONE, K);
+  LAUNCH_CHECK(h);
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  return GMRES_OK;
+}
+
+gmres_status gmres_arnoldi(gmres_handle h, const double* r0, int k, double* V_out, double* H_out, double* T_out,
+                           int* k_done) {
+  if (!h) return GMRES_ERR_ARG;
+  gmres_status st;
+  if ((st = check_ptr(h, r0, "r0")) != GMRES_OK) return st;
+  if (k < 1 || k > h->m) return fail(h, GMRES_ERR_ARG, "k must be in [1, m]");
+  CUDA_TRY(h, cudaSetDevice(h->device));
+  std::memset(h->h_st, 0, sizeof(DevState));
+  h->h_st->tol = 0.0;
+  if ((st = write_state(h)) != GMRES_OK) return st;
+  CUDA_TRY(h, cudaMemsetAsync(h->s.H, 0, sizeof(double) * h->s.ldh * h->m, h->stream));
+  CUDA_TRY(h, cudaMemsetAsync(h->s.T, 0, sizeof(double) * h->s.ldh * h->s.ldh, h->stream));
+  k_residual<<<h->P, kThreads, 0, h->stream>>>(h->rowptr, h->col, h->val, r0, nullptr, h->V, h->n, h->s, RES_START, k);
+  LAUNCH_CHECK(h);
+  if ((st = launch_cycle(h, k)) != GMRES_OK) return st;
+  if ((st = read_state(h)) != GMRES_OK) return st;
+  const int kk = h->h_st->k;
+  if (h->h_st->nonfinite) return fail(h, GMRES_ERR_NONFINITE, "non-finite value in the Arnoldi process");
+  if (k_done) *k_done = kk;
+  if (V_out) {
+    k_export_basis<<<h->grid_stream, kThreads, 0, h->stream>>>(h->V, h->ldv, V_out, h->n, kk, h->s);
+    LAUNCH_CHECK(h);
+  }
+  const int ld = h->s.ldh;
+  std::vector<double> Hd((size_t)ld * h->m), Td((size_t)ld * ld);
+  CUDA_TRY(h, cudaMemcpyAsync(Hd.data(), h->s.H, sizeof(double) * Hd.size(), cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(h, cudaMemcpyAsync(Td.data(), h->s.T, sizeof(double) * Td.size(), cudaMemcpyDeviceToHost, h->stream));
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  if (H_out)
+    for (int c = 0; c < k; ++c)
+      for (int r = 0; r <= k; ++r) H_out[r + (size_t)c * (k + 1)] = (c < kk) ? Hd[r + (size_t)c * ld] : 0.0;
+  if (T_out)
+    for (int c = 0; c <= k; ++c)
+      for (int r = 0; r <= k; ++r)
+        T_out[r + (size_t)c * (k + 1)] =
+            (h->ortho == GMRES_ONE_REDUCE_MGS && r <= kk && c <= kk) ? Td[r + (size_t)c * ld] : 0.0;
+  return GMRES_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,241 @@
+"""ctypes binding of the C ABI in include/lsgmres.h (argument marshalling only).
+
+Every numerical step runs in the CUDA library ``liblsgmres.so`` built from
+``csrc/lsgmres.cu``; this module converts torch tensors and numpy arrays to
+pointers and status codes to exceptions. There is no CPU fallback: importing
+fails loudly when the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblsgmres.so")
+
+OK, MAXITER, BREAKDOWN_EXACT = 0, 1, 2
+ERR_ARG, ERR_CUDA, ERR_NONFINITE, ERR_OOM, ERR_TIMEOUT = -1, -2, -3, -4, -5
+MGS, ONE_REDUCE_MGS = 0, 1
+FP64, IR_FP32, IR_BF16 = 0, 1, 2
+ORTHO = {"mgs": MGS, "one_reduce_mgs": ONE_REDUCE_MGS, "one_reduce": ONE_REDUCE_MGS}
+STATUS_NAMES = {0: "OK", 1: "MAXITER", 2: "BREAKDOWN_EXACT", -1: "ERR_ARG", -2: "ERR_CUDA",
+                -3: "ERR_NONFINITE", -4: "ERR_OOM", -5: "ERR_TIMEOUT"}
+
+
+class GmresError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class _Csr(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("nnz", ctypes.c_int64), ("rowptr", ctypes.c_void_p),
+                ("col", ctypes.c_void_p), ("val", ctypes.c_void_p), ("on_device", ctypes.c_int)]
+
+
+class _Info(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("restarts", ctypes.c_int), ("status", ctypes.c_int),
+                ("breakdowns", ctypes.c_int), ("rel_resid_true", ctypes.c_double),
+                ("rel_resid_est", ctypes.c_double), ("reductions", ctypes.c_int64),
+                ("grid_syncs", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
+                ("seconds", ctypes.c_double)]
+
+
+@dataclass
+class SolveInfo:
+    status: int
+    iters: int
+    restarts: int
+    breakdowns: int
+    rel_resid_true: float
+    rel_resid_est: float
+    reductions: int
+    grid_syncs: int
+    kernel_launches: int
+    seconds: float
+
+
+EXPORTS = ["gmres_create", "gmres_set", "gmres_set_tol", "gmres_set_stream", "gmres_solve",
+           "gmres_solve_host", "gmres_history", "gmres_destroy", "gmres_last_error", "lsg_spmv",
+           "lsg_block_dot", "lsg_maxpy", "gmres_arnoldi", "gmres_set_profile", "gmres_profile"]
+
+PROFILE_CLASSES = ["one_reduce_step", "arnoldi_maxpy", "mgs_spmv_dot", "mgs_axpy_dot", "residual",
+                   "least_squares", "x_update", "noop"]
+
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load the CUDA library (raises if it is missing: there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} not built; run `python -m paper_1809_05805_b300.build`")
+    lib = ctypes.CDLL(path)
+    P, I64, I, D = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+    sig = {
+        "gmres_create": ([ctypes.POINTER(_Csr), I, D, ctypes.POINTER(P)], I),
+        "gmres_set": ([P, I, I, I], I),
+        "gmres_set_tol": ([P, D], I),
+        "gmres_set_stream": ([P, P], I),
+        "gmres_solve": ([P, P, P, ctypes.POINTER(_Info)], I),
+        "gmres_solve_host": ([P, P, P, ctypes.POINTER(_Info)], I),
+        "gmres_history": ([P, P, I, ctypes.POINTER(I)], I),
+        "gmres_destroy": ([P], I),
+        "gmres_last_error": ([P], ctypes.c_char_p),
+        "lsg_spmv": ([P, P, P], I),
+        "lsg_block_dot": ([P, P, I64, I, P, P, I, P], I),
+        "lsg_maxpy": ([P, P, I64, I, P, D, P, P], I),
+        "gmres_arnoldi": ([P, P, I, P, P, P, ctypes.POINTER(I)], I),
+        "gmres_set_profile": ([P, I], I),
+        "gmres_profile": ([P, I, ctypes.POINTER(D), ctypes.POINTER(I64), ctypes.POINTER(D),
+                           ctypes.POINTER(D)], I),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes, f.restype = args, res
+    _lib = lib
+    return lib
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data
+    return t.data_ptr()  # torch tensor
+
+
+def _dev_f64(t, n: int, name: str):
+    import torch
+
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise TypeError(f"{name} must be a contiguous float64 CUDA tensor")
+    if t.numel() < n:
+        raise ValueError(f"{name} has {t.numel()} elements, need {n}")
+    return t
+
+
+class Solver:
+    """Restarted GMRES(m) on one GPU through the C ABI (gmres_create/solve/...)."""
+
+    def __init__(self, A, m: int, tol: float, *, ortho: str = "one_reduce_mgs", max_iter: int | None = None,
+                 stream=None):
+        lib = load()
+        self.lib = lib
+        rowptr, col, val = A
+        on_dev = not isinstance(rowptr, np.ndarray)
+        if not on_dev:
+            rowptr = np.ascontiguousarray(rowptr, dtype=np.int32)
+            col = np.ascontiguousarray(col, dtype=np.int32)
+            val = np.ascontiguousarray(val, dtype=np.float64)
+        self.n = int(len(rowptr) - 1 if not on_dev else rowptr.numel() - 1)
+        self.nnz = int(len(col) if not on_dev else col.numel())
+        self.m = m
+        csr = _Csr(self.n, self.nnz, _ptr(rowptr), _ptr(col), _ptr(val), int(on_dev))
+        h = ctypes.c_void_p()
+        st = lib.gmres_create(ctypes.byref(csr), m, tol, ctypes.byref(h))
+        if st != OK:
+            raise GmresError(st, lib.gmres_last_error(None).decode())
+        self.h = h
+        self.set(ortho=ortho, max_iter=max_iter if max_iter is not None else 10 * m)
+        if stream is not None:
+            self.set_stream(stream)
+
+    def _check(self, st: int, allow=(OK,)):
+        if st not in allow:
+            raise GmresError(st, self.lib.gmres_last_error(self.h).decode())
+        return st
+
+    def set(self, *, ortho: str | int = "one_reduce_mgs", prec: int = FP64, max_iter: int = 300):
+        o = ORTHO[ortho] if isinstance(ortho, str) else int(ortho)
+        self._check(self.lib.gmres_set(self.h, o, prec, max_iter))
+        self.ortho, self.max_iter = o, max_iter
+
+    def set_tol(self, tol: float):
+        self._check(self.lib.gmres_set_tol(self.h, tol))
+
+    def set_stream(self, stream):
+        self._check(self.lib.gmres_set_stream(self.h, ctypes.c_void_p(int(stream.cuda_stream))))
+
+    def solve(self, b, x, *, raise_on_maxiter: bool = False) -> SolveInfo:
+        """b, x: float64 CUDA tensors (x holds x0 on entry, the solution on exit)."""
+        _dev_f64(b, self.n, "b")
+        _dev_f64(x, self.n, "x")
+        info = _Info()
+        st = self.lib.gmres_solve(self.h, _ptr(b), _ptr(x), ctypes.byref(info))
+        self._check(st, (OK,) if raise_on_maxiter else (OK, MAXITER))
+        return _info(info)
+
+    def solve_host(self, b: np.ndarray, x: np.ndarray) -> SolveInfo:
+        """b, x: float64 numpy arrays (host); copies in, solves, copies x back."""
+        assert b.dtype == np.float64 and x.dtype == np.float64 and b.flags.c_contiguous and x.flags.c_contiguous
+        info = _Info()
+        st = self.lib.gmres_solve_host(self.h, _ptr(b), _ptr(x), ctypes.byref(info))
+        self._check(st, (OK, MAXITER))
+        return _info(info)
+
+    def history(self) -> np.ndarray:
+        n = ctypes.c_int(0)
+        self._check(self.lib.gmres_history(self.h, None, 0, ctypes.byref(n)))
+        buf = np.zeros(n.value, dtype=np.float64)
+        self._check(self.lib.gmres_history(self.h, _ptr(buf), n.value, ctypes.byref(n)))
+        return buf
+
+    # -- single steps, for parity tests ------------------------------------
+    def spmv(self, x, y):
+        self._check(self.lib.lsg_spmv(self.h, _ptr(x), _ptr(y)))
+
+    def block_dot(self, V, ldv: int, j: int, u, w, use_spmv: bool = True) -> np.ndarray:
+        X = np.zeros(2 * j + 2, dtype=np.float64)
+        self._check(self.lib.lsg_block_dot(self.h, _ptr(V), ldv, j, _ptr(u), _ptr(w), int(use_spmv), _ptr(X)))
+        return X
+
+    def maxpy(self, V, ldv: int, c: np.ndarray, alpha: float, y_in, y_out):
+        c = np.ascontiguousarray(c, dtype=np.float64)
+        self._check(self.lib.lsg_maxpy(self.h, _ptr(V), ldv, len(c), _ptr(c), alpha, _ptr(y_in), _ptr(y_out)))
+
+    def arnoldi(self, r0, k: int):
+        """k Arnoldi steps from r0 (CUDA tensor). Returns (V torch n x (k'+1), H (k'+1) x k', T, k')."""
+        import torch
+
+        V = torch.zeros((k + 1, self.n), dtype=torch.float64, device=r0.device)  # column-major n x (k+1)
+        H = np.zeros((k + 1, k), dtype=np.float64, order="F")
+        T = np.zeros((k + 1, k + 1), dtype=np.float64, order="F")
+        kd = ctypes.c_int(0)
+        self._check(self.lib.gmres_arnoldi(self.h, _ptr(r0), k, _ptr(V), _ptr(H), _ptr(T), ctypes.byref(kd)))
+        kk = kd.value
+        return V[: kk + 1].T, H[: kk + 1, :kk], T[: kk + 1, : kk + 1], kk
+
+    def set_profile(self, on: bool):
+        self._check(self.lib.gmres_set_profile(self.h, int(on)))
+
+    def profile(self) -> dict:
+        """Per kernel class of the last solve: device ms, launches, algorithmic bytes and flops."""
+        out = {}
+        for c, name in enumerate(PROFILE_CLASSES):
+            ms, cnt, by, fl = ctypes.c_double(), ctypes.c_int64(), ctypes.c_double(), ctypes.c_double()
+            self._check(self.lib.gmres_profile(self.h, c, ctypes.byref(ms), ctypes.byref(cnt), ctypes.byref(by),
+                                               ctypes.byref(fl)))
+            out[name] = dict(ms=ms.value, launches=cnt.value, bytes=by.value, flops=fl.value)
+        return out
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.gmres_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _info(i: _Info) -> SolveInfo:
+    return SolveInfo(i.status, i.iters, i.restarts, i.breakdowns, i.rel_resid_true, i.rel_resid_est,
+                     i.reductions, i.grid_syncs, i.kernel_launches, i.seconds)

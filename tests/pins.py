@@ -30,6 +30,23 @@ def pin_spmv_dense(orc):
         assert np.allclose(y, yd, rtol=1e-14, atol=1e-14 * np.abs(yd).max()), "spmv != dense"
 
 
+def pin_dot_maxpy(orc):
+    """orc_dot and orc_maxpy equal the exactly rounded results (math.fsum) within
+    the classical recursive-summation bound gamma_n * sum|terms|."""
+    import math
+    rng = np.random.default_rng(5)
+    n = 257
+    x, y = rng.standard_normal(n), rng.standard_normal(n)
+    exact = math.fsum(x * y)
+    assert abs(orc.dot(x, y) - exact) <= n * EPS * np.abs(x * y).sum()
+    V = rng.standard_normal((n, 5))
+    c = rng.standard_normal(5)
+    out = orc.maxpy(V, c, 0.5, y)
+    for i in (0, 100, n - 1):
+        terms = [0.5 * y[i]] + [c[k] * V[i, k] for k in range(5)]
+        assert abs(out[i] - math.fsum(terms)) <= 6 * EPS * sum(abs(t) for t in terms)
+
+
 # ---------------------------------------------------------------- QR kernels
 def pin_qr_reconstructs(orc):
     """Q R = A to rounding for all four Gram-Schmidt variants (backward stability)."""
@@ -241,6 +258,7 @@ def paige_S_norm(V):
 
 PINS = [
     pin_spmv_dense,
+    pin_dot_maxpy,
     pin_qr_reconstructs,
     pin_lvl2_equals_mgs,
     pin_arnoldi_relation,

@@ -48,6 +48,9 @@ MUTANTS = {
     "lvl2_z_unscaled": ("sv[j - 1] = z / beta;", "sv[j - 1] = z;"),
     "lvl2_T_sign": ("TT(j - 1, k) = -t;", "TT(j - 1, k) = t;"),
     "cgs_R_overwrite": ("R[i + (size_t)j * p] += s[i];", "R[i + (size_t)j * p] = s[i];"),
+    "maxpy_alpha": ("double t = alpha * y_in[i];", "double t = y_in[i];"),
+    "dot_square": ("double orc_dot(int64_t n, const double* x, const double* y) { return dot(n, x, y); }",
+                   "double orc_dot(int64_t n, const double* x, const double* y) { return dot(n, x, x); }"),
 }
 
 RUNNER = r"""
