@@ -32,6 +32,7 @@ from paper_1809_05805_b300 import problems as P  # noqa: E402
 
 WORKLOADS = {
     256: dict(N=256, m=50, tol=1e-8, max_iter=3000),
+    128: dict(N=128, m=50, tol=1e-8, max_iter=3000),  # profiling size (inputs still > L2)
     32: dict(N=32, m=30, tol=1e-8, max_iter=300),
 }
 METRIC = "time-to-solve (1e-8 rel. resid), one-reduce MGS-GMRES"

@@ -112,13 +112,30 @@ __device__ __forceinline__ double block_sum(double v, double* sbuf /* kWarps */)
   return t;
 }
 
-// Row i of A times x (CSR, FP64 FMA chain in column order).
+// Row i of A times x (CSR, FP64 FMA chain in column order). The loads of up
+// to 8 entries are issued together (predicated), so a stencil row costs two
+// dependent memory latencies (indices, then the gather) instead of two per entry.
 __device__ __forceinline__ double csr_row(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                                           const double* __restrict__ val, const double* __restrict__ x,
                                           int64_t i) {
+  constexpr int kW = 8;
   const int p0 = __ldg(rowptr + i), p1 = __ldg(rowptr + i + 1);
   double s = 0.0;
-  for (int p = p0; p < p1; ++p) s = fma(__ldg(val + p), __ldg(x + __ldg(col + p)), s);
+  for (int p = p0; p < p1; p += kW) {
+    int c[kW];
+    double v[kW], xv[kW];
+#pragma unroll
+    for (int e = 0; e < kW; ++e) {
+      const bool ok = p + e < p1;
+      c[e] = ok ? __ldg(col + p + e) : 0;
+      v[e] = ok ? __ldg(val + p + e) : 0.0;
+    }
+#pragma unroll
+    for (int e = 0; e < kW; ++e) xv[e] = (p + e < p1) ? __ldg(x + c[e]) : 0.0;
+#pragma unroll
+    for (int e = 0; e < kW; ++e)
+      if (p + e < p1) s = fma(v[e], xv[e], s);
+  }
   return s;
 }
 
@@ -134,10 +151,36 @@ __device__ bool grid_reduce_last(Small s, double* red, int nv) {
   __syncthreads();
   if (!s_last) return false;
   __threadfence();
-  for (int v = threadIdx.x; v < nv; v += blockDim.x) {
-    double t = 0.0;
-    for (int b = 0; b < (int)gridDim.x; ++b) t += __ldcg(s.partials + (size_t)b * s.nvmax + v);
-    red[v] = t;
+  // S threads per value (S a power of two, S * nv <= blockDim): thread (v, seg)
+  // sums partials seg, seg + S, ... in order; the S sums are then combined by a
+  // fixed xor tree (and, for S > 32, across warps in warp order). The order is
+  // independent of timing, so results are bitwise reproducible.
+  const int P = gridDim.x;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int S = 1;
+  while (2 * S * nv <= (int)blockDim.x && S < (int)blockDim.x) S *= 2;
+  const int Sw = S < 32 ? S : 32;
+  __shared__ double wred[kThreads / 32];
+  for (int base = 0; base < nv * S; base += blockDim.x) {
+    const int t = base + threadIdx.x;
+    const int v = t / S, seg = t % S;
+    double acc = 0.0;
+    if (v < nv) {
+#pragma unroll 8
+      for (int b = seg; b < P; b += S) acc += __ldcg(s.partials + (size_t)b * s.nvmax + v);
+    }
+    for (int o = Sw >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (S > 32) {  // one pass only (S * nv <= blockDim): combine the warps of each value
+      if (lane == 0) wred[wid] = acc;
+      __syncthreads();
+      if ((int)threadIdx.x < nv) {
+        double t2 = 0.0;
+        for (int w = threadIdx.x * (S / 32); w < ((int)threadIdx.x + 1) * (S / 32); ++w) t2 += wred[w];
+        red[threadIdx.x] = t2;
+      }
+    } else if (v < nv && seg == 0) {
+      red[v] = acc;
+    }
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -147,65 +190,70 @@ __device__ bool grid_reduce_last(Small s, double* red, int nv) {
   return true;
 }
 
-// Column j of H is complete (entries 0..j+1): rotate a copy by the stored
-// rotations, form rotation j, update g; returns |g_{j+1}|. Single thread.
-__device__ double rotate_column(Small s, int j) {
-  const int ld = s.ldh;
-  double* R = s.Rg + (size_t)j * ld;
-  const double* Hc = s.H + (size_t)j * ld;
-  for (int i = 0; i <= j + 1; ++i) R[i] = Hc[i];
-  for (int i = 0; i < j; ++i) {
-    const double c = s.cs[i], sn = s.sn[i];
-    const double t = c * R[i] + sn * R[i + 1];
-    R[i + 1] = -sn * R[i] + c * R[i + 1];
-    R[i] = t;
-  }
-  double c = 1.0, sn = 0.0;
-  if (R[j + 1] != 0.0) {
-    const double rho = hypot(R[j], R[j + 1]);
-    c = R[j] / rho;
-    sn = R[j + 1] / rho;
-  }
-  s.cs[j] = c;
-  s.sn[j] = sn;
-  R[j] = c * R[j] + sn * R[j + 1];
-  R[j + 1] = 0.0;
-  s.g[j + 1] = -sn * s.g[j];
-  s.g[j] = c * s.g[j];
-  return fabs(s.g[j + 1]);
-}
-
-__device__ double hcol_norm(Small s, int j) {
-  const double* Hc = s.H + (size_t)j * s.ldh;
-  double t = 0.0;
-  for (int i = 0; i <= j + 1; ++i) t += Hc[i] * Hc[i];
-  return sqrt(t);
-}
-
-// Column j of H has just received its subdiagonal entry h = H(j+1, j).
-// Rotate, record the estimate, and decide whether the cycle stops.
-// Returns 1 if the cycle is done. Single thread.
+// Column j of H is complete (entries 0..j+1 in global memory). Run by the
+// whole CTA: the column and the stored rotations are staged in shared memory
+// with parallel loads, then thread 0 rotates the column, forms rotation j,
+// updates g, records the residual estimate and decides whether the cycle
+// stops (breakdown, convergence, non-finite, or the last allowed column).
+// Returns the stop decision (0/1) in every thread.
 __device__ int finish_column(Small s, int j, double h, bool last_allowed) {
-  DevState* st = s.st;
-  const double est = rotate_column(s, j) / st->bnorm;
-  const int it = st->total_iters + j;
-  if (it < s.hist_cap) s.hist[it] = est;
-  st->k = j + 1;
-  st->est = est;
-  if (!isfinite(est)) {
-    st->nonfinite = 1;
-    return 1;
+  __shared__ double sh_col[kMaxM + 2], sh_c[kMaxM + 1], sh_s[kMaxM + 1];
+  __shared__ int s_res;
+  const int ld = s.ldh;
+  for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) sh_col[i] = s.H[(size_t)j * ld + i];
+  for (int i = threadIdx.x; i < j; i += blockDim.x) {
+    sh_c[i] = s.cs[i];
+    sh_s[i] = s.sn[i];
   }
-  if (h <= kBreakdownFactor * kEps * hcol_norm(s, j)) {
-    st->breakdown = 1;
-    return 1;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    DevState* st = s.st;
+    double hn2 = 0.0;  // ||Hbar(0:j+1, j)||^2 for the breakdown test
+    for (int i = 0; i <= j + 1; ++i) hn2 += sh_col[i] * sh_col[i];
+    double* R = sh_col;
+    for (int i = 0; i < j; ++i) {
+      const double c = sh_c[i], sn = sh_s[i];
+      const double t = c * R[i] + sn * R[i + 1];
+      R[i + 1] = -sn * R[i] + c * R[i + 1];
+      R[i] = t;
+    }
+    double c = 1.0, sn = 0.0;
+    if (R[j + 1] != 0.0) {
+      const double rho = hypot(R[j], R[j + 1]);
+      c = R[j] / rho;
+      sn = R[j + 1] / rho;
+    }
+    R[j] = c * R[j] + sn * R[j + 1];
+    R[j + 1] = 0.0;
+    double* Rg = s.Rg + (size_t)j * ld;
+    for (int i = 0; i <= j + 1; ++i) Rg[i] = R[i];
+    s.cs[j] = c;
+    s.sn[j] = sn;
+    const double gj = s.g[j];
+    s.g[j + 1] = -sn * gj;
+    s.g[j] = c * gj;
+    const double est = fabs(sn * gj) / st->bnorm;
+    const int it = st->total_iters + j;
+    if (it < s.hist_cap) s.hist[it] = est;
+    st->k = j + 1;
+    st->est = est;
+    int stop = 0;
+    if (!isfinite(est)) {
+      st->nonfinite = 1;
+      stop = 1;
+    } else if (h <= kBreakdownFactor * kEps * sqrt(hn2)) {
+      st->breakdown = 1;
+      stop = 1;
+    } else if (est <= st->tol) {
+      st->converged = 1;
+      stop = 1;
+    } else if (last_allowed) {
+      stop = 1;
+    }
+    s_res = stop;
   }
-  if (est <= st->tol) {
-    st->converged = 1;
-    return 1;
-  }
-  if (last_allowed) return 1;
-  return 0;
+  __syncthreads();
+  return s_res;
 }
 
 // --------------------------------------------------------------------------
@@ -250,9 +298,17 @@ k_one_reduce_step(const int32_t* __restrict__ rowptr, const int32_t* __restrict_
   const double* u = raw_out ? u_arg : V + (size_t)j * ldv;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 
+  // Work split of the block dot over a tile of 256 rows (8 row groups of 32):
+  // the first 8*J8 columns go to warps whole (warp w owns columns w, w+8, ...,
+  // all 8 row groups); the r8 = j mod 8 remaining columns are split by rows,
+  // each warp taking its own row group. Every warp issues the same DFMAs.
+  const int J8 = j / kWarps, r8 = j % kWarps;
   double acc_a[MAXC], acc_c[MAXC];
+  double rem_a[kWarps - 1], rem_c[kWarps - 1];
 #pragma unroll
   for (int c = 0; c < MAXC; ++c) acc_a[c] = acc_c[c] = 0.0;
+#pragma unroll
+  for (int c = 0; c < kWarps - 1; ++c) rem_a[c] = rem_c[c] = 0.0;
   double sig = 0.0, dd = 0.0;
 
   const int64_t ntiles = (n + kThreads - 1) / kThreads;
@@ -273,36 +329,39 @@ k_one_reduce_step(const int32_t* __restrict__ rowptr, const int32_t* __restrict_
     su[threadIdx.x] = ur;
     sw[threadIdx.x] = wr;
     __syncthreads();
-    double ru[kRowsPerLane], rw[kRowsPerLane];
-#pragma unroll
-    for (int q = 0; q < kRowsPerLane; ++q) {
-      ru[q] = su[lane + 32 * q];
-      rw[q] = sw[lane + 32 * q];
-    }
     const int64_t base = t * kThreads + lane;
 #pragma unroll
     for (int c = 0; c < MAXC; ++c) {
-      const int k = wid + c * kWarps;
-      if (k < j) {
+      if (c < J8) {  // warp-uniform
+        const int k = wid + c * kWarps;
         const double* vk = V + (size_t)k * ldv + base;
         double x[kRowsPerLane];
 #pragma unroll
         for (int q = 0; q < kRowsPerLane; ++q) x[q] = (base + 32 * q < n) ? __ldg(vk + 32 * q) : 0.0;
 #pragma unroll
         for (int q = 0; q < kRowsPerLane; ++q) {
-          acc_a[c] = fma(x[q], ru[q], acc_a[c]);
-          acc_c[c] = fma(x[q], rw[q], acc_c[c]);
+          acc_a[c] = fma(x[q], su[lane + 32 * q], acc_a[c]);
+          acc_c[c] = fma(x[q], sw[lane + 32 * q], acc_c[c]);
         }
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < kWarps - 1; ++c) {
+      if (c < r8) {  // block-uniform
+        const double x = (row < n) ? __ldg(V + (size_t)(J8 * kWarps + c) * ldv + row) : 0.0;
+        rem_a[c] = fma(x, ur, rem_a[c]);
+        rem_c[c] = fma(x, wr, rem_c[c]);
       }
     }
     __syncthreads();
   }
 
   // CTA partials: red[0:j] = a, red[j:2j] = c, red[2j] = sigma, red[2j+1] = d
+  __shared__ double srem[2][kWarps - 1][kWarps];
 #pragma unroll
   for (int c = 0; c < MAXC; ++c) {
-    const int k = wid + c * kWarps;
-    if (k < j) {  // warp-uniform
+    if (c < J8) {  // warp-uniform
+      const int k = wid + c * kWarps;
       const double a = warp_sum(acc_a[c]);
       const double cc = warp_sum(acc_c[c]);
       if (lane == 0) {
@@ -311,11 +370,28 @@ k_one_reduce_step(const int32_t* __restrict__ rowptr, const int32_t* __restrict_
       }
     }
   }
+#pragma unroll
+  for (int c = 0; c < kWarps - 1; ++c) {
+    if (c < r8) {
+      const double a = warp_sum(rem_a[c]);
+      const double cc = warp_sum(rem_c[c]);
+      if (lane == 0) {
+        srem[0][c][wid] = a;
+        srem[1][c][wid] = cc;
+      }
+    }
+  }
   const double sig_t = block_sum(sig, sbuf);
   const double dd_t = block_sum(dd, sbuf);
   if (threadIdx.x == 0) {
     red[2 * j] = sig_t;
     red[2 * j + 1] = dd_t;
+  }
+  if ((int)threadIdx.x < 2 * r8) {
+    const int half = threadIdx.x / r8, c = threadIdx.x % r8;
+    double t2 = 0.0;
+    for (int w2 = 0; w2 < kWarps; ++w2) t2 += srem[half][c][w2];
+    red[half * j + J8 * kWarps + c] = t2;
   }
   __syncthreads();
   const int nv = 2 * j + 2;
@@ -329,9 +405,19 @@ k_one_reduce_step(const int32_t* __restrict__ rowptr, const int32_t* __restrict_
   // ---------------- epilogue (last CTA) ----------------
   // stop: 0 = continue the cycle; 1 = cycle done after the T row (converged
   // or tail); 2 = cycle done now (breakdown, zero or non-finite norm).
-  __shared__ double s_ib;
-  __shared__ int s_stop;
+  // T (rows and columns 0..j-1) and scale[0..j-1] are staged in shared memory
+  // (dynamic, (m+1)^2 + (m+1) doubles) so the O(j^2) work reads no global memory.
+  extern __shared__ double dyn[];
   const int ld = s.ldh;
+  double* sT = dyn;                       // (m+1) x (m+1), column-major, ld
+  double* sScale = dyn + (size_t)ld * ld; // m+1
+  __shared__ double s_beta;
+  __shared__ int s_stop;
+  for (int e = threadIdx.x; e < j * j; e += blockDim.x) {
+    const int k = e / j, i = e % j;  // column k, row i
+    if (i >= k) sT[(size_t)k * ld + i] = s.T[(size_t)k * ld + i];
+  }
+  for (int i = threadIdx.x; i < j; i += blockDim.x) sScale[i] = s.scale[i];
   if (threadIdx.x == 0) {
     st->grid_syncs += 1;
     const double beta = sqrt(red[2 * j]);
@@ -344,46 +430,56 @@ k_one_reduce_step(const int32_t* __restrict__ rowptr, const int32_t* __restrict_
       else s.g[0] = beta;
     } else {
       s.H[(size_t)(j - 1) * ld + j] = beta;  // H(j, j-1): the lagged norm completes column j-1
-      const int fin = finish_column(s, j - 1, beta, tail);
-      if (st->breakdown || st->nonfinite) stop = 2;
-      else if (fin) stop = 1;
     }
     if (isfinite(beta) && beta != 0.0) s.scale[j] = 1.0 / beta;
-    s_ib = 1.0 / beta;
+    s_beta = beta;
     s_stop = stop;
   }
   __syncthreads();
+  if (s_stop == 0 && j > 0) {
+    const int fin = finish_column(s, j - 1, s_beta, tail);
+    if (threadIdx.x == 0) {
+      if (st->breakdown || st->nonfinite) s_stop = 2;
+      else if (fin) s_stop = 1;
+    }
+    __syncthreads();
+  }
   if (s_stop == 2) {
     if (threadIdx.x == 0) st->done = 1;
     return;
   }
-  const double ib = s_ib;
+  const double ib = 1.0 / s_beta;
+  if (threadIdx.x == 0) sScale[j] = ib;
   // ell = (U_j^T u_j) scaled to v_k^T v_j
-  for (int i = threadIdx.x; i < j; i += blockDim.x) red[i] = red[i] * s.scale[i] * ib;
+  for (int i = threadIdx.x; i < j; i += blockDim.x) red[i] = red[i] * sScale[i] * ib;
   __syncthreads();
   // row j of T = (I + L)^{-1}: T(j, k) = -sum_{i=k}^{j-1} ell_i T(i, k)
   for (int k = threadIdx.x; k < j; k += blockDim.x) {
     double t = 0.0;
-    for (int i = k; i < j; ++i) t = fma(red[i], s.T[(size_t)k * ld + i], t);
+    for (int i = k; i < j; ++i) t = fma(red[i], sT[(size_t)k * ld + i], t);
+    sT[(size_t)k * ld + j] = -t;
     s.T[(size_t)k * ld + j] = -t;
   }
-  if (threadIdx.x == 0) s.T[(size_t)j * ld + j] = 1.0;
+  if (threadIdx.x == 0) {
+    sT[(size_t)j * ld + j] = 1.0;
+    s.T[(size_t)j * ld + j] = 1.0;
+  }
   __syncthreads();
   if (s_stop) {
     if (threadIdx.x == 0) st->done = 1;
     return;
   }
-  // s = [c * scale / beta ; d / beta^2] stored over the c slots
+  // s = [c * scale / beta ; d / beta^2]
   __shared__ double sv[kMaxM + 1];
   for (int i = threadIdx.x; i <= j; i += blockDim.x)
-    sv[i] = (i < j) ? red[j + i] * s.scale[i] * ib : red[2 * j + 1] * ib * ib;
+    sv[i] = (i < j) ? red[j + i] * sScale[i] * ib : red[2 * j + 1] * ib * ib;
   __syncthreads();
   // r = T s; H(0:j, j) = r; MAXPY coefficients
   for (int i = threadIdx.x; i <= j; i += blockDim.x) {
     double t = 0.0;
-    for (int k = 0; k <= i; ++k) t = fma(s.T[(size_t)k * ld + i], sv[k], t);
+    for (int k = 0; k <= i; ++k) t = fma(sT[(size_t)k * ld + i], sv[k], t);
     s.H[(size_t)j * ld + i] = t;
-    s.coef[1 + i] = -t * s.scale[i];
+    s.coef[1 + i] = -t * sScale[i];
   }
   if (threadIdx.x == 0) {
     s.coef[0] = ib;
@@ -397,7 +493,7 @@ k_one_reduce_step(const int32_t* __restrict__ rowptr, const int32_t* __restrict_
 // --------------------------------------------------------------------------
 enum { MAXPY_ARNOLDI = 0, MAXPY_XUPDATE = 1, MAXPY_STANDALONE = 2 };
 
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 4)
 k_maxpy(const double* __restrict__ V, int64_t ldv, const double* y_in, double* y_out, int64_t n,
         Small s, int mode, int K_arg) {
   __shared__ double sc[kMaxM + 3];
@@ -436,7 +532,18 @@ k_maxpy(const double* __restrict__ V, int64_t ldv, const double* y_in, double* y
     for (int64_t i = gid; i < n2; i += stride) {
       const double2 y = reinterpret_cast<const double2*>(y_in)[i];
       double a0 = alpha * y.x, a1 = alpha * y.y;
-      for (int k = 0; k < K; ++k) {
+      int k = 0;
+      for (; k + 4 <= K; k += 4) {  // four independent loads in flight per thread
+        double2 v[4];
+#pragma unroll
+        for (int u2 = 0; u2 < 4; ++u2) v[u2] = __ldg(reinterpret_cast<const double2*>(V + (size_t)(k + u2) * ldv) + i);
+#pragma unroll
+        for (int u2 = 0; u2 < 4; ++u2) {
+          a0 = fma(sc[1 + k + u2], v[u2].x, a0);
+          a1 = fma(sc[1 + k + u2], v[u2].y, a1);
+        }
+      }
+      for (; k < K; ++k) {
         const double2 v = __ldg(reinterpret_cast<const double2*>(V + (size_t)k * ldv) + i);
         a0 = fma(sc[1 + k], v.x, a0);
         a1 = fma(sc[1 + k], v.y, a1);
@@ -540,23 +647,32 @@ k_mgs_axpy_dot(double* __restrict__ V, int64_t ldv, int64_t n, Small s) {
   if (threadIdx.x == 0) red[0] = tot;
   __syncthreads();
   if (!grid_reduce_last(s, red, 1)) return;
+  const int ld = s.ldh;
+  if (!last) {
+    if (threadIdx.x == 0) {
+      st->grid_syncs += 1;
+      const double sc = __ldcg(&s.scale[k + 1]);
+      const double h = sc * red[0];
+      s.H[(size_t)i * ld + k + 1] = h;
+      st->mgs_coef = h * sc;
+      st->inner = k + 1;
+    }
+    return;
+  }
+  __shared__ double s_hn;
   if (threadIdx.x == 0) {
     st->grid_syncs += 1;
-    const int ld = s.ldh;
-    if (!last) {
-      const double h = s.scale[k + 1] * red[0];
-      s.H[(size_t)i * ld + k + 1] = h;
-      st->mgs_coef = h * s.scale[k + 1];
-      st->inner = k + 1;
-    } else {
-      const double hn = sqrt(red[0]);
-      s.H[(size_t)i * ld + i + 1] = hn;
-      s.scale[i + 1] = 1.0 / hn;
-      const int stop = finish_column(s, i, hn, i + 1 == st->kmax);
-      st->step = i + 1;
-      st->inner = 0;
-      if (stop) st->done = 1;
-    }
+    const double hn = sqrt(red[0]);
+    s.H[(size_t)i * ld + i + 1] = hn;
+    s.scale[i + 1] = 1.0 / hn;
+    s_hn = hn;
+  }
+  __syncthreads();
+  const int stop = finish_column(s, i, s_hn, i + 1 == __ldcg(&st->kmax));
+  if (threadIdx.x == 0) {
+    st->step = i + 1;
+    st->inner = 0;
+    if (stop) st->done = 1;
   }
 }
 
@@ -614,7 +730,11 @@ k_residual(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
 
 // Back substitution R(0:k,0:k) y = g(0:k) (column-oriented), then the
 // coefficients of x += V_k y in the unnormalized basis, and the cycle totals.
+// The k x k triangle of the rotated Hessenberg is staged in shared memory
+// (dynamic, (m+1) x m doubles) so each of the k sequential steps is a
+// shared-memory update, not a global-memory round trip.
 __global__ void k_lsq(Small s) {
+  extern __shared__ double sR[];
   __shared__ double y[kMaxM + 1];
   __shared__ int sk;
   DevState* st = s.st;
@@ -622,13 +742,14 @@ __global__ void k_lsq(Small s) {
   __syncthreads();
   const int k = sk;
   const int ld = s.ldh;
+  for (int e = threadIdx.x; e < k * ld; e += blockDim.x) sR[e] = s.Rg[e];
   for (int l = threadIdx.x; l < k; l += blockDim.x) y[l] = s.g[l];
   __syncthreads();
   for (int i = k - 1; i >= 0; --i) {
-    if (threadIdx.x == 0) y[i] = y[i] / s.Rg[(size_t)i * ld + i];
+    if (threadIdx.x == 0) y[i] = y[i] / sR[(size_t)i * ld + i];
     __syncthreads();
     const double yi = y[i];
-    for (int l = threadIdx.x; l < i; l += blockDim.x) y[l] = fma(-s.Rg[(size_t)i * ld + l], yi, y[l]);
+    for (int l = threadIdx.x; l < i; l += blockDim.x) y[l] = fma(-sR[(size_t)i * ld + l], yi, y[l]);
     __syncthreads();
   }
   for (int l = threadIdx.x; l < k; l += blockDim.x) s.coefx[1 + l] = y[l] * s.scale[l];
@@ -662,12 +783,20 @@ __global__ void k_spmv(const int32_t* __restrict__ rowptr, const int32_t* __rest
 using StepKernel = void (*)(const int32_t*, const int32_t*, const double*, const double*, int64_t,
                             const double*, double*, int64_t, Small, int, int, double*);
 
+// MAXC = floor(m / 8) whole columns per warp (j <= m), at least 1.
 StepKernel step_kernel_for(int m) {
-  if (m <= 1 * kWarps) return k_one_reduce_step<1>;
-  if (m <= 2 * kWarps) return k_one_reduce_step<2>;
-  if (m <= 4 * kWarps) return k_one_reduce_step<4>;
-  if (m <= 8 * kWarps) return k_one_reduce_step<8>;
-  return k_one_reduce_step<16>;
+  switch (std::max(1, m / kWarps)) {
+    case 1: return k_one_reduce_step<1>;
+    case 2: return k_one_reduce_step<2>;
+    case 3: return k_one_reduce_step<3>;
+    case 4: return k_one_reduce_step<4>;
+    case 5: return k_one_reduce_step<5>;
+    case 6: return k_one_reduce_step<6>;
+    case 7: return k_one_reduce_step<7>;
+    case 8: return k_one_reduce_step<8>;
+    case 9: case 10: case 11: case 12: return k_one_reduce_step<12>;
+    default: return k_one_reduce_step<16>;
+  }
 }
 
 }  // namespace
@@ -697,6 +826,8 @@ struct gmres_ctx {
   DevState* h_st = nullptr;  // pinned mirror
   cudaStream_t stream = nullptr;
   StepKernel step = nullptr;
+  size_t step_smem = 0;  // dynamic shared memory of the step kernel (T and scales)
+  size_t lsq_smem = 0;   // dynamic shared memory of k_lsq (rotated Hessenberg)
   std::vector<double> hist;
   int hist_len = 0;
   double* h_b = nullptr;  // pinned staging for gmres_solve_host
@@ -817,8 +948,8 @@ gmres_status launch_cycle(gmres_ctx* h, int kmax) {
   if (h->ortho == GMRES_ONE_REDUCE_MGS) {
     for (int j = 0; j <= kmax; ++j) {
       int pr = prof_begin(h, 0, j, kmax);
-      h->step<<<P, kThreads, 0, h->stream>>>(h->rowptr, h->col, h->val, h->V, h->ldv, nullptr, h->w, h->n,
-                                            h->s, 0, 1, nullptr);
+      h->step<<<P, kThreads, h->step_smem, h->stream>>>(h->rowptr, h->col, h->val, h->V, h->ldv, nullptr, h->w,
+                                                        h->n, h->s, 0, 1, nullptr);
       prof_end(h, pr);
       ++h->launches;
       if (j < kmax) {
@@ -1031,8 +1162,12 @@ gmres_status gmres_create(const gmres_csr* A, int m_restart, double tol, gmres_h
   std::memset(h->h_st, 0, sizeof(DevState));
   if (alloc_small(h) != GMRES_OK) return bail(GMRES_ERR_CUDA);
   h->step = step_kernel_for(m_restart);
+  h->step_smem = sizeof(double) * ((size_t)(m_restart + 1) * (m_restart + 1) + (m_restart + 1));
+  h->lsq_smem = sizeof(double) * (size_t)(m_restart + 1) * m_restart;
   CREATE_TRY(cudaFuncSetAttribute(reinterpret_cast<const void*>(h->step),
-                                  cudaFuncAttributePreferredSharedMemoryCarveout, 50));
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->step_smem));
+  CREATE_TRY(cudaFuncSetAttribute(reinterpret_cast<const void*>(k_lsq),
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->lsq_smem));
 #undef CREATE_TRY
   *out = h;
   return GMRES_OK;
@@ -1127,7 +1262,7 @@ gmres_status gmres_solve(gmres_handle h, const double* b, double* x, gmres_info*
       CUDA_TRY(h, cudaMemcpyAsync(&h->s.st->kmax, &h->h_st->kmax, sizeof(int), cudaMemcpyHostToDevice, h->stream));
       if ((st = launch_cycle(h, kmax)) != GMRES_OK) return st;
       pr = prof_begin(h, PC_LSQ, 0, 0);
-      k_lsq<<<1, 128, 0, h->stream>>>(h->s);
+      k_lsq<<<1, 128, h->lsq_smem, h->stream>>>(h->s);
       prof_end(h, pr);
       pr = prof_begin(h, PC_XUPD, 0, 0);
       k_maxpy<<<h->grid_stream, kThreads, 0, h->stream>>>(h->V, h->ldv, x, x, h->n, h->s, MAXPY_XUPDATE, 0);
@@ -1233,8 +1368,8 @@ gmres_status lsg_block_dot(gmres_handle h, const double* V, int64_t ldv, int j, 
   if (!h) return GMRES_ERR_ARG;
   if (j < 0 || j > h->m) return fail(h, GMRES_ERR_ARG, "j must be in [0, m]");
   if ((j > 0 && (!V || ldv < h->n)) || !u || !w || !X) return fail(h, GMRES_ERR_ARG, "bad pointer or ldv");
-  h->step<<<h->P, kThreads, 0, h->stream>>>(h->rowptr, h->col, h->val, V, ldv, u, w, h->n, h->s, j, use_spmv,
-                                            h->s.raw);
+  h->step<<<h->P, kThreads, h->step_smem, h->stream>>>(h->rowptr, h->col, h->val, V, ldv, u, w, h->n, h->s, j,
+                                                        use_spmv, h->s.raw);
   LAUNCH_CHECK(h);
   CUDA_TRY(h, cudaMemcpyAsync(X, h->s.raw, sizeof(double) * (2 * j + 2), cudaMemcpyDeviceToHost, h->stream));
   CUDA_TRY(h, cudaStreamSynchronize(h->stream));
