@@ -164,6 +164,34 @@ gmres_status lsg_spmv(gmres_handle h, const double* x, double* y);
 gmres_status lsg_block_dot(gmres_handle h, const double* V, int64_t ldv, int j,
                            const double* u, double* w, int use_spmv, double* X);
 
+/* lsg_block_dot_noalloc: the fused SpMV + block inner product of lsg_block_dot
+ * for callers that cannot allocate device memory -- for example code running
+ * under a memory pool or arena that owns all device memory, a process whose
+ * allocator is locked for the duration of a solve, or a host library that may
+ * not call cudaMalloc/cudaFree in its calling context. It needs no handle and
+ * makes no allocation: the reduction scratch lives in a fixed array compiled
+ * into this library (about 300 KB, present on every device that loads the
+ * library until the process exits). The paper has no counterpart; it is an
+ * interface convenience.
+ *
+ * Inputs (all device memory, caller-owned): the CSR arrays rowptr/col/val of an
+ * n x n matrix (used when use_spmv != 0), V (first j columns of a column-major
+ * array, leading dimension ldv >= n), u (n doubles), w (n doubles: written
+ * with A u when use_spmv != 0, read otherwise). Output: X (device, 2j+2
+ * doubles) = [V^T u, V^T w, u^T u, u^T w], as in lsg_block_dot.
+ * Limits: 0 <= j <= 64 and 1 <= n < 2^31; larger j returns GMRES_ERR_ARG with
+ * the limit in gmres_last_error(NULL). Work is queued on cuda_stream (a
+ * cudaStream_t, NULL = legacy default) and the call does not synchronize.
+ * The first call on each device looks up the scratch array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before
+ * any stream capture. All calls share the one scratch array, so calls that
+ * could run at the same time on the GPU (different streams, threads) race and
+ * must be serialized by the caller. Errors are described by
+ * gmres_last_error(NULL). */
+gmres_status lsg_block_dot_noalloc(const int32_t* rowptr, const int32_t* col, const double* val, int64_t n,
+                                   const double* V, int64_t ldv, int j, const double* u, double* w,
+                                   int use_spmv, double* X, void* cuda_stream);
+
 /* MAXPY (Section IV): y_out = alpha * y_in + sum_{k<K} c[k] * V[:, k] for
  * device V (leading dimension ldv >= n, 16-byte aligned columns), device
  * y_in and y_out (may alias), host c (K values), 0 <= K <= m + 1. */

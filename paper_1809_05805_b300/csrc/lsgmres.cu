@@ -30,6 +30,7 @@
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -780,6 +781,24 @@ __global__ void k_spmv(const int32_t* __restrict__ rowptr, const int32_t* __rest
     y[r] = csr_row(rowptr, col, val, x, r);
 }
 
+
+// --------------------------------------------------------------------------
+// scratch for lsg_block_dot_noalloc
+// --------------------------------------------------------------------------
+// The grid reduction of the fused SpMV + block-dot kernel needs scratch: one
+// row of partial sums per CTA and the last-CTA ticket. gmres_create allocates
+// it per handle; lsg_block_dot_noalloc instead uses this fixed array, which is
+// part of the library image and so exists on every device that loads the
+// library, from load until process exit. Layout: a DevState (holds the ticket)
+// followed by kNoAllocMaxCtas rows of kNoAllocNv doubles.
+constexpr int kNoAllocMaxJ = 64;                       // largest j (block-dot columns)
+constexpr int kNoAllocMaxCtas = 296;                   // largest grid of the reduction
+constexpr int kNoAllocNv = 2 * kNoAllocMaxJ + 2;       // sums per CTA
+constexpr size_t kNoAllocStateBytes = 256;             // DevState, padded
+constexpr size_t kNoAllocBytes = kNoAllocStateBytes + sizeof(double) * (size_t)kNoAllocMaxCtas * kNoAllocNv;
+static_assert(sizeof(DevState) <= kNoAllocStateBytes, "DevState outgrew its slot");
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
 using StepKernel = void (*)(const int32_t*, const int32_t*, const double*, const double*, int64_t,
                             const double*, double*, int64_t, Small, int, int, double*);
 
@@ -854,6 +873,14 @@ struct gmres_ctx {
 namespace {
 
 std::string g_create_err;
+
+// Device address of g_noalloc_scratch, looked up once per device (the host
+// symbol is only a stand-in and must never be passed to a kernel).
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+int g_noalloc_nsm[kNoAllocMaxDevices] = {};
+
 
 gmres_status fail(gmres_ctx* h, gmres_status st, const std::string& msg) {
   if (h)
@@ -1388,6 +1415,55 @@ gmres_status lsg_maxpy(gmres_handle h, const double* V, int64_t ldv, int K, cons
   k_maxpy<<<h->grid_stream, kThreads, 0, h->stream>>>(V, ldv, y_in, y_out, h->n, h->s, MAXPY_STANDALONE, K);
   LAUNCH_CHECK(h);
   CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  return GMRES_OK;
+}
+
+gmres_status lsg_block_dot_noalloc(const int32_t* rowptr, const int32_t* col, const double* val, int64_t n,
+                                   const double* V, int64_t ldv, int j, const double* u, double* w,
+                                   int use_spmv, double* X, void* cuda_stream) {
+  if (n <= 0 || n >= (int64_t)INT32_MAX) return fail(nullptr, GMRES_ERR_ARG, "n must be in [1, 2^31)");
+  if (j < 0 || j > kNoAllocMaxJ)
+    return fail(nullptr, GMRES_ERR_ARG,
+                "lsg_block_dot_noalloc: j = " + std::to_string(j) + " exceeds the fixed scratch limit of " +
+                    std::to_string(kNoAllocMaxJ) + " columns");
+  if (!u || !w || !X || (use_spmv && (!rowptr || !col || !val)) || (j > 0 && (!V || ldv < n)))
+    return fail(nullptr, GMRES_ERR_ARG, "lsg_block_dot_noalloc: NULL pointer or ldv < n");
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices)
+    return fail(nullptr, GMRES_ERR_CUDA, "lsg_block_dot_noalloc: no usable current device");
+  void* scratch = nullptr;
+  int nsm = 0;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {  // first call on this device: look up the array's device address
+      cudaError_t e = cudaGetSymbolAddress(&g_noalloc_ptr[dev], g_noalloc_scratch);
+      if (e != cudaSuccess) {
+        g_noalloc_ptr[dev] = nullptr;
+        return fail(nullptr, GMRES_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+      }
+      e = cudaDeviceGetAttribute(&g_noalloc_nsm[dev], cudaDevAttrMultiProcessorCount, dev);
+      if (e != cudaSuccess) {
+        g_noalloc_ptr[dev] = nullptr;
+        return fail(nullptr, GMRES_ERR_CUDA, std::string("cudaDeviceGetAttribute: ") + cudaGetErrorString(e));
+      }
+    }
+    scratch = g_noalloc_ptr[dev];
+    nsm = g_noalloc_nsm[dev];
+  }
+  cudaStream_t stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+  Small sm{};
+  sm.st = reinterpret_cast<DevState*>(scratch);
+  sm.partials = reinterpret_cast<double*>(static_cast<unsigned char*>(scratch) + kNoAllocStateBytes);
+  sm.nvmax = kNoAllocNv;
+  const int64_t ntiles = (n + kThreads - 1) / kThreads;
+  const int P = (int)std::min<int64_t>(std::min<int64_t>(kNoAllocMaxCtas, 2 * (int64_t)nsm), ntiles);
+  // the ticket must start at zero; a memset allocates nothing
+  cudaError_t e = cudaMemsetAsync(scratch, 0, sizeof(DevState), stream);
+  if (e != cudaSuccess) return fail(nullptr, GMRES_ERR_CUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
+  k_one_reduce_step<kNoAllocMaxJ / kWarps><<<P, kThreads, 0, stream>>>(rowptr, col, val, V, ldv, u, w, n, sm, j,
+                                                                      use_spmv, X);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(nullptr, GMRES_ERR_CUDA, std::string("launch: ") + cudaGetErrorString(e));
   return GMRES_OK;
 }
 

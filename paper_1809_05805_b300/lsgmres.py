@@ -60,7 +60,8 @@ class SolveInfo:
 
 EXPORTS = ["gmres_create", "gmres_set", "gmres_set_tol", "gmres_set_stream", "gmres_solve",
            "gmres_solve_host", "gmres_history", "gmres_destroy", "gmres_last_error", "lsg_spmv",
-           "lsg_block_dot", "lsg_maxpy", "gmres_arnoldi", "gmres_set_profile", "gmres_profile"]
+           "lsg_block_dot", "lsg_maxpy", "gmres_arnoldi", "gmres_set_profile", "gmres_profile",
+           "lsg_block_dot_noalloc"]
 
 PROFILE_CLASSES = ["one_reduce_step", "arnoldi_maxpy", "mgs_spmv_dot", "mgs_axpy_dot", "residual",
                    "least_squares", "x_update", "noop"]
@@ -92,6 +93,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "lsg_maxpy": ([P, P, I64, I, P, D, P, P], I),
         "gmres_arnoldi": ([P, P, I, P, P, P, ctypes.POINTER(I)], I),
         "gmres_set_profile": ([P, I], I),
+        "lsg_block_dot_noalloc": ([P, P, P, I64, P, I64, I, P, P, I, P, P], I),
         "gmres_profile": ([P, I, ctypes.POINTER(D), ctypes.POINTER(I64), ctypes.POINTER(D),
                            ctypes.POINTER(D)], I),
     }
@@ -234,6 +236,19 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+
+def block_dot_noalloc(A_dev, n: int, V, ldv: int, j: int, u, w, X, use_spmv: bool = True, stream=None):
+    """lsg_block_dot_noalloc: the fused SpMV + block dot without a handle or any
+    allocation by the library. A_dev = (rowptr, col, val) as CUDA tensors; V, u,
+    w, X CUDA float64 tensors (X receives 2j+2 sums). Queued on `stream`
+    (a torch.cuda.Stream, default: the legacy default stream); not synchronized."""
+    lib = load()
+    rowptr, col, val = A_dev
+    st = lib.lsg_block_dot_noalloc(_ptr(rowptr), _ptr(col), _ptr(val), n, _ptr(V), ldv, j, _ptr(u), _ptr(w),
+                                   int(use_spmv), _ptr(X), None if stream is None else int(stream.cuda_stream))
+    if st != OK:
+        raise GmresError(st, lib.gmres_last_error(None).decode())
 
 
 def _info(i: _Info) -> SolveInfo:
