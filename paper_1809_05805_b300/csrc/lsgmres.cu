@@ -50,6 +50,7 @@ constexpr double kBreakdownFactor = 16.0;
 // --------------------------------------------------------------------------
 struct DevState {
   double bnorm;        // ||b|| (or ||r0|| for gmres_arnoldi)
+  double inv_bnorm;    // 1 / bnorm (the residual estimate multiplies; FP64 division is slow)
   double rnorm;        // last true-residual norm
   double tol;
   double est;          // last Givens estimate (relative)
@@ -220,9 +221,9 @@ __device__ int finish_column(Small s, int j, double h, bool last_allowed) {
     }
     double c = 1.0, sn = 0.0;
     if (R[j + 1] != 0.0) {
-      const double rho = hypot(R[j], R[j + 1]);
-      c = R[j] / rho;
-      sn = R[j + 1] / rho;
+      const double irho = 1.0 / hypot(R[j], R[j + 1]);
+      c = R[j] * irho;
+      sn = R[j + 1] * irho;
     }
     R[j] = c * R[j] + sn * R[j + 1];
     R[j + 1] = 0.0;
@@ -233,7 +234,7 @@ __device__ int finish_column(Small s, int j, double h, bool last_allowed) {
     const double gj = s.g[j];
     s.g[j + 1] = -sn * gj;
     s.g[j] = c * gj;
-    const double est = fabs(sn * gj) / st->bnorm;
+    const double est = fabs(sn * gj) * st->inv_bnorm;
     const int it = st->total_iters + j;
     if (it < s.hist_cap) s.hist[it] = est;
     st->k = j + 1;
@@ -437,7 +438,13 @@ k_one_reduce_step(const int32_t* __restrict__ rowptr, const int32_t* __restrict_
     s_stop = stop;
   }
   __syncthreads();
-  if (s_stop == 0 && j > 0) {
+  if (threadIdx.x == 0 && s_stop == 0 && j > 0 && s_beta == 0.0) s_stop = 2;  // exact breakdown: no 1/0
+  __syncthreads();
+  // Column j-1 is now complete. Except at the cycle's tail, its Givens
+  // rotation and the convergence test run in the following MAXPY launch (one
+  // extra CTA beside the streaming CTAs): they are a chain of dependent FP64
+  // operations at ~64 cycles each on this part and are not needed by the MAXPY.
+  if (s_stop == 0 && j > 0 && tail) {
     const int fin = finish_column(s, j - 1, s_beta, tail);
     if (threadIdx.x == 0) {
       if (st->breakdown || st->nonfinite) s_stop = 2;
@@ -454,12 +461,21 @@ k_one_reduce_step(const int32_t* __restrict__ rowptr, const int32_t* __restrict_
   // ell = (U_j^T u_j) scaled to v_k^T v_j
   for (int i = threadIdx.x; i < j; i += blockDim.x) red[i] = red[i] * sScale[i] * ib;
   __syncthreads();
-  // row j of T = (I + L)^{-1}: T(j, k) = -sum_{i=k}^{j-1} ell_i T(i, k)
+  // row j of T = (I + L)^{-1}: T(j, k) = -sum_{i=k}^{j-1} ell_i T(i, k). Each sum
+  // is split into 4 interleaved partial sums on different warps (shorter
+  // dependent FP64 chains), combined in a fixed order.
+  __shared__ double spart[4][kMaxM + 1];
+  for (int t = threadIdx.x; t < 4 * j; t += blockDim.x) {
+    const int seg = t / j, k = t % j;
+    double p = 0.0;
+    for (int i = k + seg; i < j; i += 4) p = fma(red[i], sT[(size_t)k * ld + i], p);
+    spart[seg][k] = p;
+  }
+  __syncthreads();
   for (int k = threadIdx.x; k < j; k += blockDim.x) {
-    double t = 0.0;
-    for (int i = k; i < j; ++i) t = fma(red[i], sT[(size_t)k * ld + i], t);
-    sT[(size_t)k * ld + j] = -t;
-    s.T[(size_t)k * ld + j] = -t;
+    const double t = -(((spart[0][k] + spart[1][k]) + spart[2][k]) + spart[3][k]);
+    sT[(size_t)k * ld + j] = t;
+    s.T[(size_t)k * ld + j] = t;
   }
   if (threadIdx.x == 0) {
     sT[(size_t)j * ld + j] = 1.0;
@@ -475,10 +491,16 @@ k_one_reduce_step(const int32_t* __restrict__ rowptr, const int32_t* __restrict_
   for (int i = threadIdx.x; i <= j; i += blockDim.x)
     sv[i] = (i < j) ? red[j + i] * sScale[i] * ib : red[2 * j + 1] * ib * ib;
   __syncthreads();
-  // r = T s; H(0:j, j) = r; MAXPY coefficients
+  // r = T s (4 interleaved partial sums per entry); H(0:j, j) = r; MAXPY coefficients
+  for (int t = threadIdx.x; t < 4 * (j + 1); t += blockDim.x) {
+    const int seg = t / (j + 1), i = t % (j + 1);
+    double p = 0.0;
+    for (int k = seg; k <= i; k += 4) p = fma(sT[(size_t)k * ld + i], sv[k], p);
+    spart[seg][i] = p;
+  }
+  __syncthreads();
   for (int i = threadIdx.x; i <= j; i += blockDim.x) {
-    double t = 0.0;
-    for (int k = 0; k <= i; ++k) t = fma(sT[(size_t)k * ld + i], sv[k], t);
+    const double t = ((spart[0][i] + spart[1][i]) + spart[2][i]) + spart[3][i];
     s.H[(size_t)j * ld + i] = t;
     s.coef[1 + i] = -t * sScale[i];
   }
@@ -521,12 +543,26 @@ k_maxpy(const double* __restrict__ V, int64_t ldv, const double* y_in, double* y
   const double* cf = (mode == MAXPY_XUPDATE) ? s.coefx : s.coef;
   for (int i = threadIdx.x; i <= K; i += blockDim.x) sc[i] = __ldcg(cf + i);
   __syncthreads();
-  if (mode == MAXPY_ARNOLDI && blockIdx.x == 0 && threadIdx.x == 0) st->grid_syncs += 1;
+  if (mode == MAXPY_ARNOLDI && blockIdx.x == gridDim.x - 1) {
+    // The last CTA of an Arnoldi MAXPY finishes column j-1 of H (Givens,
+    // residual estimate, stop decision) while the other CTAs stream.
+    const int j = __ldcg(&st->step) - 1;
+    if (j >= 1) {
+      const double h = __ldcg(&s.H[(size_t)(j - 1) * s.ldh + j]);
+      const int stop = finish_column(s, j - 1, h, false);
+      if (threadIdx.x == 0) {
+        st->grid_syncs += 1;
+        if (stop) st->done = 1;
+      }
+    }
+    return;
+  }
+  const int ndata = gridDim.x - (mode == MAXPY_ARNOLDI ? 1 : 0);  // CTAs that stream
   double* out = s_out;
   const double alpha = sc[0];
   const bool vec = ((reinterpret_cast<uintptr_t>(y_in) | reinterpret_cast<uintptr_t>(out) |
                      reinterpret_cast<uintptr_t>(V)) & 15) == 0 && (ldv & 1) == 0;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t stride = (int64_t)ndata * blockDim.x;
   const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (vec) {
     const int64_t n2 = n / 2;
@@ -710,9 +746,13 @@ k_residual(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
     const double nr = sqrt(red[0]);
     if (mode == RES_BNORM) {
       st->bnorm = nr;
+      st->inv_bnorm = 1.0 / nr;
       return;
     }
-    if (mode == RES_START) st->bnorm = nr;
+    if (mode == RES_START) {
+      st->bnorm = nr;
+      st->inv_bnorm = 1.0 / nr;
+    }
     st->rnorm = nr;
     st->step = 0;
     st->inner = 0;
@@ -744,10 +784,13 @@ __global__ void k_lsq(Small s) {
   const int k = sk;
   const int ld = s.ldh;
   for (int e = threadIdx.x; e < k * ld; e += blockDim.x) sR[e] = s.Rg[e];
+  __shared__ double rinv[kMaxM + 1];
   for (int l = threadIdx.x; l < k; l += blockDim.x) y[l] = s.g[l];
   __syncthreads();
+  for (int l = threadIdx.x; l < k; l += blockDim.x) rinv[l] = 1.0 / sR[(size_t)l * ld + l];
+  __syncthreads();
   for (int i = k - 1; i >= 0; --i) {
-    if (threadIdx.x == 0) y[i] = y[i] / sR[(size_t)i * ld + i];
+    if (threadIdx.x == 0) y[i] = y[i] * rinv[i];
     __syncthreads();
     const double yi = y[i];
     for (int l = threadIdx.x; l < i; l += blockDim.x) y[l] = fma(-sR[(size_t)i * ld + l], yi, y[l]);
@@ -864,6 +907,21 @@ struct gmres_ctx {
   std::vector<cudaEvent_t> ev_pool;
   size_t ev_used = 0;
   std::vector<ProfRec> recs;
+  // CUDA graphs of whole cycles (captured once per scheme, kmax and profiling
+  // mode; used when the handle has a non-default stream)
+  struct CycleGraph {
+    int ortho, kmax;
+    bool prof;
+    cudaGraphExec_t exec;
+    int64_t nlaunch;
+    std::vector<ProfRec> recs;
+    std::vector<cudaEvent_t> events;
+  };
+  std::vector<CycleGraph> graphs;
+  bool capturing = false;
+  bool graph_prof_ok = true;  // false once a capture with timing events has failed
+  CycleGraph* cap = nullptr;
+  size_t cap_ev_used = 0;
   double prof_ms[GMRES_PROFILE_CLASSES] = {};
   double prof_bytes[GMRES_PROFILE_CLASSES] = {};
   double prof_flops[GMRES_PROFILE_CLASSES] = {};
@@ -906,7 +964,10 @@ gmres_status fail(gmres_ctx* h, gmres_status st, const std::string& msg) {
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
+void destroy_graphs(gmres_ctx* h);
+
 gmres_status alloc_small(gmres_ctx* h) {
+  destroy_graphs(h);  // captured graphs hold pointers into the old block
   const int m = h->m, ld = m + 1;
   const int nvmax = 2 * (m + 1) + 2;
   h->s.m = m;
@@ -980,9 +1041,9 @@ gmres_status launch_cycle(gmres_ctx* h, int kmax) {
       prof_end(h, pr);
       ++h->launches;
       if (j < kmax) {
-        pr = prof_begin(h, 1, j, 0);
-        k_maxpy<<<h->grid_stream, kThreads, 0, h->stream>>>(h->V, h->ldv, h->w, nullptr, h->n, h->s,
-                                                             MAXPY_ARNOLDI, 0);
+        pr = prof_begin(h, 1, j, kmax);
+        k_maxpy<<<h->grid_stream + 1, kThreads, 0, h->stream>>>(h->V, h->ldv, h->w, nullptr, h->n, h->s,
+                                                                 MAXPY_ARNOLDI, 0);
         prof_end(h, pr);
         ++h->launches;
       }
@@ -1017,6 +1078,14 @@ enum { PC_STEP = 0, PC_MAXPY = 1, PC_MGS_SPMV = 2, PC_MGS_AXPY = 3, PC_RES = 4, 
 // Record an event pair around the next launch (no-op unless profiling).
 int prof_begin(gmres_ctx* h, int cls, int j, int i) {
   if (!h->prof_on) return -1;
+  if (h->capturing) {  // events pre-created for the graph being captured
+    if (h->cap_ev_used + 2 > h->cap->events.size()) return -1;
+    gmres_ctx::ProfRec r{cls, j, i, h->cap->events[h->cap_ev_used], h->cap->events[h->cap_ev_used + 1]};
+    h->cap_ev_used += 2;
+    cudaEventRecordWithFlags(r.a, h->stream, cudaEventRecordExternal);  // a timing node in the graph
+    h->cap->recs.push_back(r);
+    return (int)h->cap->recs.size() - 1;
+  }
   while (h->ev_used + 2 > h->ev_pool.size()) {
     cudaEvent_t e;
     if (cudaEventCreate(&e) != cudaSuccess) return -1;
@@ -1030,7 +1099,83 @@ int prof_begin(gmres_ctx* h, int cls, int j, int i) {
 }
 
 void prof_end(gmres_ctx* h, int idx) {
-  if (idx >= 0) cudaEventRecord(h->recs[idx].b, h->stream);
+  if (idx < 0) return;
+  if (h->capturing)
+    cudaEventRecordWithFlags(h->cap->recs[idx].b, h->stream, cudaEventRecordExternal);
+  else
+    cudaEventRecord(h->recs[idx].b, h->stream);
+}
+
+void destroy_graphs(gmres_ctx* h) {
+  for (auto& g : h->graphs) {
+    cudaGraphExecDestroy(g.exec);
+    for (cudaEvent_t e : g.events) cudaEventDestroy(e);
+  }
+  h->graphs.clear();
+}
+
+gmres_status launch_cycle(gmres_ctx* h, int kmax);
+
+// One cycle of kmax steps. With a non-default stream the cycle's fixed launch
+// sequence is captured once into a CUDA graph (per scheme, kmax and profiling
+// mode) and replayed; kernels read their step index from device state, so the
+// same graph serves every cycle. On the legacy default stream (which cannot be
+// captured) the kernels are launched one by one.
+gmres_status run_cycle(gmres_ctx* h, int kmax) {
+  if (h->stream == nullptr || (h->prof_on && !h->graph_prof_ok)) return launch_cycle(h, kmax);
+  gmres_ctx::CycleGraph* g = nullptr;
+  for (auto& c : h->graphs)
+    if (c.ortho == h->ortho && c.kmax == kmax && c.prof == h->prof_on) g = &c;
+  if (!g) {
+    h->graphs.emplace_back();
+    g = &h->graphs.back();
+    g->ortho = h->ortho;
+    g->kmax = kmax;
+    g->prof = h->prof_on;
+    g->exec = nullptr;
+    const int64_t nl = (h->ortho == GMRES_ONE_REDUCE_MGS) ? 2 * (int64_t)kmax + 1
+                                                          : (int64_t)kmax + (int64_t)kmax * (kmax + 1) / 2;
+    if (h->prof_on) {
+      g->events.resize(2 * nl);
+      for (auto& e : g->events) CUDA_TRY(h, cudaEventCreate(&e));
+    }
+    const int64_t before = h->launches;
+    h->capturing = true;
+    h->cap = g;
+    h->cap_ev_used = 0;
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
+    gmres_status st = GMRES_OK;
+    if (e == cudaSuccess) st = launch_cycle(h, kmax);
+    cudaError_t e2 = cudaStreamEndCapture(h->stream, &graph);
+    h->capturing = false;
+    h->cap = nullptr;
+    g->nlaunch = h->launches - before;
+    h->launches = before;
+    if (e != cudaSuccess || e2 != cudaSuccess || st != GMRES_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      for (cudaEvent_t ev : g->events) cudaEventDestroy(ev);
+      h->graphs.pop_back();
+      cudaGetLastError();
+      if (!h->prof_on)
+        return fail(h, GMRES_ERR_CUDA, std::string("cycle graph capture failed: ") +
+                                            cudaGetErrorString(e != cudaSuccess ? e : e2));
+      h->graph_prof_ok = false;  // timed launches are not capturable here: launch them directly
+      h->err.clear();
+      return launch_cycle(h, kmax);
+    }
+    e = cudaGraphInstantiate(&g->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      h->graphs.pop_back();
+      return fail(h, GMRES_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+    }
+  }
+  CUDA_TRY(h, cudaGraphLaunch(g->exec, h->stream));
+  h->launches += g->nlaunch;
+  if (h->prof_on)
+    for (const auto& r : g->recs) h->recs.push_back(r);
+  return GMRES_OK;
 }
 
 // Algorithmic traffic and flops of one launch that did work (FP64: 8-byte
@@ -1083,7 +1228,7 @@ void prof_settle(gmres_ctx* h, int k) {
     cudaEventElapsedTime(&ms, r.a, r.b);
     bool work = true;
     if (r.cls == PC_STEP) work = r.j <= k;
-    else if (r.cls == PC_MAXPY) work = r.j < k;
+    else if (r.cls == PC_MAXPY) work = r.j <= k && r.j < r.i;  // also runs after the stopping step
     else if (r.cls == PC_MGS_SPMV || r.cls == PC_MGS_AXPY) work = r.j < k;
     const int c = work ? r.cls : PC_NOOP;
     h->prof_ms[c] += ms;
@@ -1287,7 +1432,7 @@ gmres_status gmres_solve(gmres_handle h, const double* b, double* x, gmres_info*
       h->h_st->kmax = kmax;
       // only kmax changes on the host side; write it without touching the rest
       CUDA_TRY(h, cudaMemcpyAsync(&h->s.st->kmax, &h->h_st->kmax, sizeof(int), cudaMemcpyHostToDevice, h->stream));
-      if ((st = launch_cycle(h, kmax)) != GMRES_OK) return st;
+      if ((st = run_cycle(h, kmax)) != GMRES_OK) return st;
       pr = prof_begin(h, PC_LSQ, 0, 0);
       k_lsq<<<1, 128, h->lsq_smem, h->stream>>>(h->s);
       prof_end(h, pr);
@@ -1355,6 +1500,7 @@ gmres_status gmres_destroy(gmres_handle h) {
   cudaFree(h->d_x);
   if (h->h_st) cudaFreeHost(h->h_st);
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+  destroy_graphs(h);
   delete h;
   return GMRES_OK;
 }

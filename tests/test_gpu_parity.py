@@ -252,3 +252,52 @@ def test_invalid_csr_rejected(lsg):
     assert e.value.status == lsg.ERR_ARG
     with pytest.raises(lsg.GmresError):
         lsg.Solver((np.array([0, 1, 2], np.int32), np.array([0, 5], np.int32), np.ones(2)), m=2, tol=1e-8)
+
+
+@pytest.mark.parametrize("ortho", ["mgs", "one_reduce_mgs"])
+def test_stream_graph_path(torch_cuda, lsg, orc, ortho):
+    """On a non-default stream each cycle runs as a replayed CUDA graph. Results
+    equal the oracle's and, bitwise, the kernel-by-kernel path on the default
+    stream; max_iter = 70 with m = 30 also exercises a shorter last cycle."""
+    torch = torch_cuda
+    A = P.conv_diff_7pt(24)
+    _, b = P.rhs(A, seed=11)
+    n = len(b)
+    bd = dev(torch, b)
+    r = orc.gmres(A, b, variant=0 if ortho == "mgs" else 1, m=30, tol=1e-12, max_iter=70)
+    outs = []
+    for use_stream in (False, True):
+        s = lsg.Solver(A, m=30, tol=1e-12, ortho=ortho, max_iter=70)
+        stream = torch.cuda.Stream() if use_stream else None
+        if stream is not None:
+            s.set_stream(stream)
+        x = torch.zeros(n, dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        info = s.solve(bd, x)
+        outs.append((x.cpu().numpy(), s.history(), info))
+    for x, hist, info in outs:
+        assert info.iters == r.iters == 70 and info.restarts == r.restarts
+        k = 50
+        assert np.all(np.abs(hist[:k] - r.history[:k]) <= 1e-8 * r.history[:k])
+        assert np.linalg.norm(x - r.x) <= 1e-9 * np.linalg.norm(r.x)
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+
+
+def test_stream_graph_replay_twice(torch_cuda, lsg):
+    """Two solves on one handle and stream (graphs replayed) give identical results."""
+    torch = torch_cuda
+    A = P.conv_diff_7pt(16)
+    _, b = P.rhs(A, seed=12)
+    s = lsg.Solver(A, m=20, tol=1e-10)
+    stream = torch.cuda.Stream()
+    s.set_stream(stream)
+    bd = dev(torch, b)
+    res = []
+    for _ in range(2):
+        with torch.cuda.stream(stream):
+            x = torch.zeros(len(b), dtype=torch.float64, device="cuda")
+        stream.synchronize()
+        info = s.solve(bd, x)
+        res.append((x.cpu().numpy(), s.history(), info.kernel_launches))
+    assert np.array_equal(res[0][0], res[1][0]) and np.array_equal(res[0][1], res[1][1])
+    assert res[0][2] == res[1][2]
