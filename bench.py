@@ -37,6 +37,10 @@ WORKLOADS = {
 }
 METRIC = "time-to-solve (1e-8 rel. resid), one-reduce MGS-GMRES"
 FP64_DFMA_PER_CLK_SM = 2  # B300: 1.25 TFLOP/s nominal FP64 = 148 SMs x 2 DFMA/clk x 2 flop x ~2.1 GHz
+# DRAM bytes per step launch / algorithmic bytes, from the ncu capture summarized in
+# profiles/k_one_reduce_step_128cubed.md (dram__bytes_read.sum + dram__bytes_write.sum).
+# Valid only for the kernel build that capture measured; set to None when it changes.
+STEP_TRAFFIC_RATIO = 1.013
 
 
 def workload_name(w):
@@ -310,7 +314,9 @@ def run_ours(args, w, rank, world, dist):
         "frac": step_tflops / fp64_peak if step_tflops else None,
         "peak_source": (f"FP64 pipe derived from unit counts and clock: 148 SMs x {FP64_DFMA_PER_CLK_SM} DFMA/clk x 2 "
                         f"flop x {peaks.get('sm_max_mhz', 2032.0):g} MHz (nominal 1.25 TFLOP/s)"),
-        "traffic": None,
+        "traffic": (STEP_TRAFFIC_RATIO * st["bytes"] / max(st["launches"], 1)) if STEP_TRAFFIC_RATIO else None,
+        "traffic_source": "ncu dram bytes / algorithmic bytes at 128^3 (same kernel build), times this run's "
+                          "algorithmic bytes per launch",
         "launch_avg_ms": step_avg_ms, "launches": st["launches"],
         "alg_flops_per_launch": st["flops"] / max(st["launches"], 1),
         "alg_bytes_per_launch": st["bytes"] / max(st["launches"], 1),

@@ -100,6 +100,25 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+// Butterfly reduce-scatter of 32 per-lane values over the warp: 31 adds
+// (16 + 8 + 4 + 2 + 1), each lane keeping the half its lane bit selects at
+// every level. On return lane l holds the sum over the 32 lanes of slot l
+// (also returned). Fixed order: bitwise reproducible.
+__device__ __forceinline__ double warp_reduce_scatter32(double* v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) {
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int i = 0; i < o; ++i) {
+      const double send = up ? v[i] : v[i + o];
+      const double keep = up ? v[i + o] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+  return v[0];
+}
+
 // Sum one value over the CTA (fixed order); result valid in thread 0.
 __device__ __forceinline__ double block_sum(double v, double* sbuf /* kWarps */) {
   v = warp_sum(v);
@@ -139,6 +158,44 @@ __device__ __forceinline__ double csr_row(const int32_t* __restrict__ rowptr, co
       if (p + e < p1) s = fma(v[e], xv[e], s);
   }
   return s;
+}
+
+// Rows r0 and r1 of A times x with the loads of both rows in flight together
+// (rows of up to 8 entries; longer rows use csr_row). Rows >= n give 0.
+__device__ __forceinline__ void csr_row2(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                                         const double* __restrict__ val, const double* __restrict__ x,
+                                         int64_t r0, int64_t r1, int64_t n, double& y0, double& y1) {
+  constexpr int kW = 8;
+  const int a0 = r0 < n ? __ldg(rowptr + r0) : 0, b0 = r0 < n ? __ldg(rowptr + r0 + 1) : 0;
+  const int a1 = r1 < n ? __ldg(rowptr + r1) : 0, b1 = r1 < n ? __ldg(rowptr + r1 + 1) : 0;
+  if (b0 - a0 <= kW && b1 - a1 <= kW) {
+    int c0[kW], c1[kW];
+    double v0[kW], v1[kW];
+#pragma unroll
+    for (int e = 0; e < kW; ++e) {
+      c0[e] = (a0 + e < b0) ? __ldg(col + a0 + e) : 0;
+      v0[e] = (a0 + e < b0) ? __ldg(val + a0 + e) : 0.0;
+      c1[e] = (a1 + e < b1) ? __ldg(col + a1 + e) : 0;
+      v1[e] = (a1 + e < b1) ? __ldg(val + a1 + e) : 0.0;
+    }
+    double x0[kW], x1[kW];
+#pragma unroll
+    for (int e = 0; e < kW; ++e) {
+      x0[e] = (a0 + e < b0) ? __ldg(x + c0[e]) : 0.0;
+      x1[e] = (a1 + e < b1) ? __ldg(x + c1[e]) : 0.0;
+    }
+    double s0 = 0.0, s1 = 0.0;
+#pragma unroll
+    for (int e = 0; e < kW; ++e) {
+      if (a0 + e < b0) s0 = fma(v0[e], x0[e], s0);
+      if (a1 + e < b1) s1 = fma(v1[e], x1[e], s1);
+    }
+    y0 = s0;
+    y1 = s1;
+  } else {
+    y0 = r0 < n ? csr_row(rowptr, col, val, x, r0) : 0.0;
+    y1 = r1 < n ? csr_row(rowptr, col, val, x, r1) : 0.0;
+  }
 }
 
 // Publish this CTA's partial sums and elect the last CTA. Returns true in every
@@ -274,8 +331,8 @@ k_one_reduce_step(const int32_t* __restrict__ rowptr, const int32_t* __restrict_
                   const double* __restrict__ val, const double* __restrict__ V, int64_t ldv,
                   const double* __restrict__ u_arg, double* __restrict__ w, int64_t n, Small s,
                   int j_arg, int use_spmv, double* raw_out) {
-  __shared__ double su[kThreads];
-  __shared__ double sw[kThreads];
+  __shared__ double su[2 * kThreads];
+  __shared__ double sw[2 * kThreads];
   __shared__ double red[2 * (kMaxM + 1) + 2];
   __shared__ double sbuf[kWarps];
   __shared__ int s_j, s_tail, s_skip;
@@ -314,86 +371,171 @@ k_one_reduce_step(const int32_t* __restrict__ rowptr, const int32_t* __restrict_
   double sig = 0.0, dd = 0.0;
 
   const int64_t ntiles = (n + kThreads - 1) / kThreads;
-  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const int64_t row = t * kThreads + threadIdx.x;
-    double ur = 0.0, wr = 0.0;
-    if (row < n) {
-      ur = u[row];
+  // Large problems take tiles in pairs (the CSR loads of two rows per thread are
+  // in flight together, halving the latency-bound SpMV phases per row); small
+  // ones keep one tile per CTA iteration so that every SM gets work.
+  if (ntiles >= 4 * (int64_t)gridDim.x) {
+    const int64_t npairs = (ntiles + 1) / 2;
+    for (int64_t pp = blockIdx.x; pp < npairs; pp += gridDim.x) {
+      const int64_t row0 = pp * (2 * kThreads) + threadIdx.x, row1 = row0 + kThreads;
+      double ur0 = 0.0, wr0 = 0.0, ur1 = 0.0, wr1 = 0.0;
+      if (row0 < n) ur0 = u[row0];
+      if (row1 < n) ur1 = u[row1];
       if (spmv) {
-        wr = csr_row(rowptr, col, val, u, row);
-        w[row] = wr;
+        csr_row2(rowptr, col, val, u, row0, row1, n, wr0, wr1);
+        if (row0 < n) w[row0] = wr0;
+        if (row1 < n) w[row1] = wr1;
       } else if (need_w) {
-        wr = w[row];
+        if (row0 < n) wr0 = w[row0];
+        if (row1 < n) wr1 = w[row1];
       }
-    }
-    sig = fma(ur, ur, sig);
-    dd = fma(ur, wr, dd);
-    su[threadIdx.x] = ur;
-    sw[threadIdx.x] = wr;
-    __syncthreads();
-    const int64_t base = t * kThreads + lane;
-#pragma unroll
-    for (int c = 0; c < MAXC; ++c) {
-      if (c < J8) {  // warp-uniform
-        const int k = wid + c * kWarps;
-        const double* vk = V + (size_t)k * ldv + base;
-        double x[kRowsPerLane];
-#pragma unroll
-        for (int q = 0; q < kRowsPerLane; ++q) x[q] = (base + 32 * q < n) ? __ldg(vk + 32 * q) : 0.0;
-#pragma unroll
+      sig = fma(ur0, ur0, sig);
+      dd = fma(ur0, wr0, dd);
+      sig = fma(ur1, ur1, sig);
+      dd = fma(ur1, wr1, dd);
+      su[threadIdx.x] = ur0;
+      sw[threadIdx.x] = wr0;
+      su[kThreads + threadIdx.x] = ur1;
+      sw[kThreads + threadIdx.x] = wr1;
+      __syncthreads();
+  #pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int64_t base = pp * (2 * kThreads) + h * kThreads + lane;
+        double ru[kRowsPerLane], rw[kRowsPerLane];
+  #pragma unroll
         for (int q = 0; q < kRowsPerLane; ++q) {
-          acc_a[c] = fma(x[q], su[lane + 32 * q], acc_a[c]);
-          acc_c[c] = fma(x[q], sw[lane + 32 * q], acc_c[c]);
+          ru[q] = su[h * kThreads + lane + 32 * q];
+          rw[q] = sw[h * kThreads + lane + 32 * q];
+        }
+  #pragma unroll
+        for (int c = 0; c < MAXC; ++c) {
+          if (c < J8) {  // warp-uniform
+            const int k = wid + c * kWarps;
+            const double* vk = V + (size_t)k * ldv + base;
+            double x[kRowsPerLane];
+  #pragma unroll
+            for (int q = 0; q < kRowsPerLane; ++q) x[q] = (base + 32 * q < n) ? __ldg(vk + 32 * q) : 0.0;
+  #pragma unroll
+            for (int q = 0; q < kRowsPerLane; ++q) {
+              acc_a[c] = fma(x[q], ru[q], acc_a[c]);
+              acc_c[c] = fma(x[q], rw[q], acc_c[c]);
+            }
+          }
         }
       }
-    }
-#pragma unroll
-    for (int c = 0; c < kWarps - 1; ++c) {
-      if (c < r8) {  // block-uniform
-        const double x = (row < n) ? __ldg(V + (size_t)(J8 * kWarps + c) * ldv + row) : 0.0;
-        rem_a[c] = fma(x, ur, rem_a[c]);
-        rem_c[c] = fma(x, wr, rem_c[c]);
+  #pragma unroll
+      for (int c = 0; c < kWarps - 1; ++c) {
+        if (c < r8) {  // block-uniform
+          const double* vk = V + (size_t)(J8 * kWarps + c) * ldv;
+          const double x0 = (row0 < n) ? __ldg(vk + row0) : 0.0;
+          const double x1 = (row1 < n) ? __ldg(vk + row1) : 0.0;
+          rem_a[c] = fma(x0, ur0, rem_a[c]);
+          rem_c[c] = fma(x0, wr0, rem_c[c]);
+          rem_a[c] = fma(x1, ur1, rem_a[c]);
+          rem_c[c] = fma(x1, wr1, rem_c[c]);
+        }
       }
+      __syncthreads();
     }
-    __syncthreads();
+  } else {
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+      const int64_t row = t * kThreads + threadIdx.x;
+      double ur = 0.0, wr = 0.0;
+      if (row < n) {
+        ur = u[row];
+        if (spmv) {
+          wr = csr_row(rowptr, col, val, u, row);
+          w[row] = wr;
+        } else if (need_w) {
+          wr = w[row];
+        }
+      }
+      sig = fma(ur, ur, sig);
+      dd = fma(ur, wr, dd);
+      su[threadIdx.x] = ur;
+      sw[threadIdx.x] = wr;
+      __syncthreads();
+      const int64_t base = t * kThreads + lane;
+      double ru[kRowsPerLane], rw[kRowsPerLane];
+  #pragma unroll
+      for (int q = 0; q < kRowsPerLane; ++q) {
+        ru[q] = su[lane + 32 * q];
+        rw[q] = sw[lane + 32 * q];
+      }
+  #pragma unroll
+      for (int c = 0; c < MAXC; ++c) {
+        if (c < J8) {  // warp-uniform
+          const int k = wid + c * kWarps;
+          const double* vk = V + (size_t)k * ldv + base;
+          double x[kRowsPerLane];
+  #pragma unroll
+          for (int q = 0; q < kRowsPerLane; ++q) x[q] = (base + 32 * q < n) ? __ldg(vk + 32 * q) : 0.0;
+  #pragma unroll
+          for (int q = 0; q < kRowsPerLane; ++q) {
+            acc_a[c] = fma(x[q], ru[q], acc_a[c]);
+            acc_c[c] = fma(x[q], rw[q], acc_c[c]);
+          }
+        }
+      }
+  #pragma unroll
+      for (int c = 0; c < kWarps - 1; ++c) {
+        if (c < r8) {  // block-uniform
+          const double x = (row < n) ? __ldg(V + (size_t)(J8 * kWarps + c) * ldv + row) : 0.0;
+          rem_a[c] = fma(x, ur, rem_a[c]);
+          rem_c[c] = fma(x, wr, rem_c[c]);
+        }
+      }
+      __syncthreads();
+    }
   }
 
-  // CTA partials: red[0:j] = a, red[j:2j] = c, red[2j] = sigma, red[2j+1] = d
-  __shared__ double srem[2][kWarps - 1][kWarps];
+  // CTA partials: red[0:j] = a, red[j:2j] = c, red[2j] = sigma, red[2j+1] = d.
+  // Each lane's accumulators are packed into 32-slot chunks and reduced across
+  // the warp by a butterfly reduce-scatter (31 adds per chunk instead of 5 per
+  // value): lane l then holds the warp total of slot l.
+  constexpr int kSlots = 2 * MAXC + 2 * (kWarps - 1) + 2;
+  constexpr int kChunks = (kSlots + 31) / 32;
+  double v[kChunks * 32];
+#pragma unroll
+  for (int i = 0; i < kChunks * 32; ++i) v[i] = 0.0;
 #pragma unroll
   for (int c = 0; c < MAXC; ++c) {
-    if (c < J8) {  // warp-uniform
-      const int k = wid + c * kWarps;
-      const double a = warp_sum(acc_a[c]);
-      const double cc = warp_sum(acc_c[c]);
-      if (lane == 0) {
-        red[k] = a;
-        red[j + k] = cc;
-      }
-    }
+    v[c] = acc_a[c];
+    v[MAXC + c] = acc_c[c];
   }
 #pragma unroll
   for (int c = 0; c < kWarps - 1; ++c) {
-    if (c < r8) {
-      const double a = warp_sum(rem_a[c]);
-      const double cc = warp_sum(rem_c[c]);
-      if (lane == 0) {
-        srem[0][c][wid] = a;
-        srem[1][c][wid] = cc;
-      }
+    v[2 * MAXC + c] = rem_a[c];
+    v[2 * MAXC + kWarps - 1 + c] = rem_c[c];
+  }
+  v[kSlots - 2] = sig;
+  v[kSlots - 1] = dd;
+  __shared__ double scross[kSlots - 2 * MAXC][kWarps];  // slots summed across warps
+#pragma unroll
+  for (int ch = 0; ch < kChunks; ++ch) {
+    const double tot = warp_reduce_scatter32(v + 32 * ch);
+    const int slot = 32 * ch + lane;
+    if (slot < MAXC) {
+      if (slot < J8) red[wid + slot * kWarps] = tot;  // column wid + 8 slot belongs to this warp
+    } else if (slot < 2 * MAXC) {
+      if (slot - MAXC < J8) red[j + wid + (slot - MAXC) * kWarps] = tot;
+    } else if (slot < kSlots) {
+      scross[slot - 2 * MAXC][wid] = tot;
     }
   }
-  const double sig_t = block_sum(sig, sbuf);
-  const double dd_t = block_sum(dd, sbuf);
-  if (threadIdx.x == 0) {
-    red[2 * j] = sig_t;
-    red[2 * j + 1] = dd_t;
-  }
-  if ((int)threadIdx.x < 2 * r8) {
-    const int half = threadIdx.x / r8, c = threadIdx.x % r8;
+  __syncthreads();
+  // remainder columns and the two norms: sum the 8 warps in warp order
+  if ((int)threadIdx.x < kSlots - 2 * MAXC) {
+    const int q = threadIdx.x;
     double t2 = 0.0;
-    for (int w2 = 0; w2 < kWarps; ++w2) t2 += srem[half][c][w2];
-    red[half * j + J8 * kWarps + c] = t2;
+    for (int w2 = 0; w2 < kWarps; ++w2) t2 += scross[q][w2];
+    if (q < kWarps - 1) {
+      if (q < r8) red[J8 * kWarps + q] = t2;
+    } else if (q < 2 * (kWarps - 1)) {
+      if (q - (kWarps - 1) < r8) red[j + J8 * kWarps + q - (kWarps - 1)] = t2;
+    } else {
+      red[2 * j + (q - 2 * (kWarps - 1))] = t2;
+    }
   }
   __syncthreads();
   const int nv = 2 * j + 2;
