@@ -47,6 +47,9 @@ def run(name):
         f.write(f"status {r.status}\niters {r.iters}\nrestarts {r.restarts}\nreductions {r.reductions}\n")
         f.write(f"rel_resid_true {r.rel_resid_true!r}\n")
         f.write("history " + " ".join(repr(float(h)) for h in r.history) + "\n")
+        idx = np.sort(np.random.default_rng(123).choice(len(b), size=64, replace=False))
+        f.write("x_sample_idx " + " ".join(str(int(i)) for i in idx) + "\n")
+        f.write("x_sample " + " ".join(repr(float(r.x[i])) for i in idx) + "\n")
     print(name, r.status, r.iters, r.restarts, r.rel_resid_true, f"{dt:.1f}s", flush=True)
 
 
@@ -57,7 +60,8 @@ def load(name):
             if line.startswith("#") or not line.strip():
                 continue
             k, v = line.split(" ", 1)
-            vals[k] = np.array([float(t) for t in v.split()]) if k == "history" else float(v)
+            vals[k] = np.array([float(t) for t in v.split()]) if k in ("history", "x_sample_idx", "x_sample") \
+                else float(v)
     return vals
 
 

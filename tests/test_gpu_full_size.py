@@ -1,0 +1,63 @@
+"""Full-size parity: the 256^3 benchmark solve on the GPU, in the launch
+configuration bench.py times (a non-default stream, so cycles run as CUDA
+graphs), against the FP64 oracle's own complete solve of the same seeded system.
+
+The oracle's run (tests/golden/oracle_profile_c2_one_reduce.txt, written by
+tests/golden/make_oracle_profiles.py from the oracle alone, ~30 min on one CPU
+thread) records its iteration, restart and reduction counts, its residual
+history and 64 sampled entries of its solution.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from paper_1809_05805_b300 import problems as P
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "oracle_profile_c2_one_reduce.txt")
+
+
+def _golden():
+    vals = {}
+    with open(GOLDEN) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            k, v = line.split(" ", 1)
+            vals[k] = np.array([float(t) for t in v.split()]) if k in ("history", "x_sample_idx", "x_sample") \
+                else float(v)
+    return vals
+
+
+def test_256cubed_solve_matches_oracle_run():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1809_05805_b300 import lsgmres
+
+    g = _golden()
+    A = P.conv_diff_7pt(256)
+    _, b = P.rhs(A, seed=0)
+    n = len(b)
+    stream = torch.cuda.Stream()
+    s = lsgmres.Solver(A, m=50, tol=1e-8, ortho="one_reduce_mgs", max_iter=3000, stream=stream)
+    bd = torch.from_numpy(b).cuda()
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    info = s.solve(bd, x)
+    hist = s.history()
+    assert info.status == 0 and g["status"] == 0
+    assert info.iters == int(g["iters"]) and info.restarts == int(g["restarts"])
+    assert info.reductions == int(g["reductions"])
+    h = g["history"]
+    assert len(hist) == len(h)
+    assert np.all(np.abs(hist[:50] - h[:50]) <= 1e-8 * h[:50])
+    assert np.all(np.abs(hist - h) <= np.maximum(1e-6 * h, 1e-14))
+    xs = x.cpu().numpy()
+    true = np.linalg.norm(b - P.to_scipy(A) @ xs) / np.linalg.norm(b)
+    assert true <= 1e-8 and abs(true - g["rel_resid_true"]) <= 1e-3 * g["rel_resid_true"]
+    if "x_sample" in g:
+        idx = g["x_sample_idx"].astype(np.int64)
+        assert np.all(np.abs(xs[idx] - g["x_sample"]) <= 1e-9)
