@@ -24,7 +24,7 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 
 ORC_OK, ORC_MAXITER, ORC_BREAKDOWN = 0, 1, 2
 ORC_ERR_ARG, ORC_ERR_NONFINITE, ORC_ERR_OOM = -1, -3, -4
-MGS, ONE_REDUCE = 0, 1
+MGS, ONE_REDUCE, IR_FP32 = 0, 1, 2
 
 CFLAGS = ["-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-std=c99"]
 

@@ -25,6 +25,8 @@
  *                       variant 0: MGS-GMRES (Algorithm 6)
  *                       variant 1: one-synchronization MGS-GMRES with lagged
  *                                  normalization (Algorithm 7 built on Algorithm 4)
+ *                       variant 2: variant 1 with each cycle's vectors in FP32
+ *                                  inside FP64 restarts (GMRES-IR) [A13]
  *
  * What pins each function (tests/test_oracle_*.py, all CPU-only):
  *   the Arnoldi relation A V_k = V_{k+1} Hbar_k (Section III); the MGS /
@@ -54,6 +56,7 @@
 
 #define ORC_VARIANT_MGS 0
 #define ORC_VARIANT_ONE_REDUCE 1
+#define ORC_VARIANT_IR_FP32 2
 
 /* Breakdown threshold factor [A6]: the new direction is declared exhausted
  * when its norm is below BREAKDOWN_FACTOR * eps * ||Hbar(:, j)||. */
@@ -465,6 +468,117 @@ static cycle_out cycle_one_reduce(cycle_ws* ws, int kmax, double beta0, double b
   return out;
 }
 
+
+/* ------------------------------------------------------------------------- */
+/* GMRES-IR: the one-reduce cycle in FP32 inside FP64 restarts [A13].        */
+/* ------------------------------------------------------------------------- */
+/* Mixed-precision iterative refinement (an extension; the paper is FP64
+ * throughout). Every n-vector of a cycle -- the basis, A u with the matrix
+ * values rounded to FP32, the block inner products and the MAXPY -- is FP32,
+ * summed sequentially in FP32. The small dense arithmetic (beta, T, Givens,
+ * least squares) is FP64, and so are the restart residual b - A x, its norm and
+ * the correction x += V y (the FP32 basis widened exactly to FP64). */
+
+static void spmv_f32(int64_t n, const int32_t* rowptr, const int32_t* col, const float* val32,
+                     const float* x, float* y) {
+  for (int64_t i = 0; i < n; ++i) {
+    float s = 0.0f;
+    for (int64_t p = rowptr[i]; p < rowptr[i + 1]; ++p) s += val32[p] * x[col[p]];
+    y[i] = s;
+  }
+}
+
+static float dot_f32(int64_t n, const float* x, const float* y) {
+  float s = 0.0f;
+  for (int64_t i = 0; i < n; ++i) s += x[i] * y[i];
+  return s;
+}
+
+/* One cycle of cycle_one_reduce's steps with FP32 vectors. On entry V column 0
+ * (FP64) holds r0 = b - A x and beta0 = ||r0|| (FP64). On exit the cycle's FP32
+ * basis, widened, is in V (FP64) for the correction, and H, T, g as in FP64. */
+static cycle_out cycle_one_reduce_f32(cycle_ws* ws, float* V32, float* w32, const float* val32, int kmax,
+                                      double beta0, double bnorm, double tol, double* hist, int* hlen,
+                                      int hcap, int64_t* nred) {
+  cycle_out out = {0, 0, 0.0};
+  const int64_t n = ws->n;
+  const int ld = ws->m + 1;
+#define V32COL(k) (V32 + (size_t)(k) * n)
+  for (int64_t l = 0; l < n; ++l) V32COL(0)[l] = (float)(VCOL(ws, 0)[l] / beta0); /* v_0 */
+  memset(ws->g, 0, sizeof(double) * (size_t)ld);
+  ws->g[0] = beta0;
+  memset(ws->T, 0, sizeof(double) * (size_t)ld * ld);
+
+  /* step 0 */
+  spmv_f32(n, ws->rowptr, ws->col, val32, V32COL(0), w32);
+  double d0 = (double)dot_f32(n, V32COL(0), w32);
+  *nred += 1;
+  TL(ws, 0, 0) = 1.0;
+  HH(ws, 0, 0) = d0;
+  for (int64_t l = 0; l < n; ++l) V32COL(1)[l] = w32[l] - (float)d0 * V32COL(0)[l];
+
+  int kcols = 0;
+  for (int j = 1; j <= kmax; ++j) {
+    const int tail = (j == kmax);
+    float* u = V32COL(j);
+    if (!tail) spmv_f32(n, ws->rowptr, ws->col, val32, u, w32);
+    for (int i = 0; i < j; ++i) ws->a[i] = (double)dot_f32(n, V32COL(i), u);
+    double sigma = (double)dot_f32(n, u, u);
+    double d = 0.0;
+    if (!tail) {
+      for (int i = 0; i < j; ++i) ws->c[i] = (double)dot_f32(n, V32COL(i), w32);
+      d = (double)dot_f32(n, u, w32);
+    }
+    *nred += 1;
+
+    double beta = sqrt(sigma);
+    HH(ws, j, j - 1) = beta;
+    double est = rotate_column(ws, j - 1) / bnorm;
+    if (*hlen < hcap) hist[*hlen] = est;
+    *hlen += 1;
+    out.k = j;
+    out.est = est;
+    kcols = j;
+    if (beta <= BREAKDOWN_FACTOR * 2.220446049250313e-16 * hcol_norm(ws, j - 1)) {
+      out.breakdown = 1;
+      break;
+    }
+    const float ib = (float)(1.0 / beta);
+    for (int64_t l = 0; l < n; ++l) u[l] *= ib; /* v_j */
+
+    for (int i = 0; i < j; ++i) ws->a[i] /= beta;
+    for (int k = 0; k < j; ++k) {
+      double t = 0.0;
+      for (int i = k; i < j; ++i) t += ws->a[i] * TL(ws, i, k);
+      TL(ws, j, k) = -t;
+    }
+    TL(ws, j, j) = 1.0;
+    if (tail || est <= tol) break;
+
+    for (int i = 0; i < j; ++i) ws->s[i] = ws->c[i] / beta;
+    ws->s[j] = d / (beta * beta);
+    for (int i = 0; i <= j; ++i) {
+      double t = 0.0;
+      for (int k = 0; k <= i; ++k) t += TL(ws, i, k) * ws->s[k];
+      ws->r[i] = t;
+      HH(ws, i, j) = t;
+    }
+    float* un = V32COL(j + 1);
+    const float fb = (float)beta;
+    for (int64_t l = 0; l < n; ++l) un[l] = w32[l] / fb;
+    for (int i = 0; i <= j; ++i) {
+      const float ri = (float)ws->r[i];
+      const float* vi = V32COL(i);
+      for (int64_t l = 0; l < n; ++l) un[l] -= ri * vi[l];
+    }
+  }
+  /* widen the used basis for the FP64 correction (exact) */
+  for (int k = 0; k <= kcols && k <= ws->m; ++k)
+    for (int64_t l = 0; l < n; ++l) VCOL(ws, k)[l] = (double)V32COL(k)[l];
+#undef V32COL
+  return out;
+}
+
 static int all_finite(int64_t n, const double* v) {
   for (int64_t i = 0; i < n; ++i)
     if (!isfinite(v[i])) return 0;
@@ -485,7 +599,8 @@ int orc_gmres(int64_t n, const int32_t* rowptr, const int32_t* col, const double
               double* hist, int hist_cap, orc_info* info,
               double* V1, double* H1, double* T1, int* k1) {
   if (n <= 0 || m <= 0 || max_iter < 0 || !(tol >= 0.0) || !b || !x || !info) return ORC_ERR_ARG;
-  if (variant != ORC_VARIANT_MGS && variant != ORC_VARIANT_ONE_REDUCE) return ORC_ERR_ARG;
+  if (variant != ORC_VARIANT_MGS && variant != ORC_VARIANT_ONE_REDUCE && variant != ORC_VARIANT_IR_FP32)
+    return ORC_ERR_ARG;
   memset(info, 0, sizeof(*info));
   if (!all_finite(n, b) || !all_finite(n, x)) {
     info->status = ORC_ERR_NONFINITE;
@@ -514,7 +629,21 @@ int orc_gmres(int64_t n, const int32_t* rowptr, const int32_t* col, const double
   ws.s = (double*)calloc(ld, sizeof(double));
   ws.r = (double*)calloc(ld, sizeof(double));
   double* res = (double*)malloc(sizeof(double) * (size_t)n);
+  float* V32 = NULL;
+  float* w32 = NULL;
+  float* val32 = NULL;
   int status = ORC_OK;
+  if (variant == ORC_VARIANT_IR_FP32) {
+    const int64_t nnz = rowptr[n];
+    V32 = (float*)malloc(sizeof(float) * (size_t)n * ld);
+    w32 = (float*)malloc(sizeof(float) * (size_t)n);
+    val32 = (float*)malloc(sizeof(float) * (size_t)(nnz > 0 ? nnz : 1));
+    if (!V32 || !w32 || !val32) {
+      status = ORC_ERR_OOM;
+      goto done;
+    }
+    for (int64_t p = 0; p < nnz; ++p) val32[p] = (float)val[p];
+  }
   if (!ws.V || !ws.w || !ws.H || !ws.Rg || !ws.cs || !ws.sn || !ws.g || !ws.T || !ws.a ||
       !ws.c || !ws.s || !ws.r || !res) {
     status = ORC_ERR_OOM;
@@ -553,10 +682,14 @@ int orc_gmres(int64_t n, const int32_t* rowptr, const int32_t* col, const double
     if (kmax > mm) kmax = mm;
     memcpy(VCOL(&ws, 0), res, sizeof(double) * n);
     memset(ws.H, 0, sizeof(double) * ld * mm);
-    cycle_out co = (variant == ORC_VARIANT_MGS)
-                       ? cycle_mgs(&ws, kmax, beta0, bnorm, tol, hist, &hlen, hist_cap, &info->reductions)
-                       : cycle_one_reduce(&ws, kmax, beta0, bnorm, tol, hist, &hlen, hist_cap,
-                                          &info->reductions);
+    cycle_out co;
+    if (variant == ORC_VARIANT_MGS)
+      co = cycle_mgs(&ws, kmax, beta0, bnorm, tol, hist, &hlen, hist_cap, &info->reductions);
+    else if (variant == ORC_VARIANT_ONE_REDUCE)
+      co = cycle_one_reduce(&ws, kmax, beta0, bnorm, tol, hist, &hlen, hist_cap, &info->reductions);
+    else
+      co = cycle_one_reduce_f32(&ws, V32, w32, val32, kmax, beta0, bnorm, tol, hist, &hlen, hist_cap,
+                                &info->reductions);
     if (first) {
       if (V1) memcpy(V1, ws.V, sizeof(double) * (size_t)n * ld);
       if (H1) memcpy(H1, ws.H, sizeof(double) * ld * mm);
@@ -574,5 +707,6 @@ done:
   info->status = status;
   free(ws.V); free(ws.w); free(ws.H); free(ws.Rg); free(ws.cs); free(ws.sn); free(ws.g);
   free(ws.T); free(ws.a); free(ws.c); free(ws.s); free(ws.r); free(res);
+  free(V32); free(w32); free(val32);
   return status;
 }

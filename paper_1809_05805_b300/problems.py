@@ -71,6 +71,56 @@ def grid7_nnz(N: int) -> int:
 
 
 # --------------------------------------------------------------------------
+# 3D 27-point anisotropic diffusion (trilinear finite elements)
+# --------------------------------------------------------------------------
+def aniso_27pt(N: int, k=(1.0, 1.0, 1e-3)) -> CSR:
+    """Stiffness matrix of -div(diag(k) grad u) with trilinear (Q1) elements on a
+    uniform N^3 interior grid of the unit cube, Dirichlet boundary eliminated:
+
+        A = k_x T (x) M (x) M + k_y M (x) T (x) M + k_z M (x) M (x) T
+
+    (x fastest), with the 1D stiffness T = tridiag(-1, 2, -1) and the 1D mass
+    M = tridiag(1, 4, 1) / 6, the common factor h dropped. Symmetric positive
+    definite, 27 nonzeros per interior row, (3N - 2)^3 nonzeros in total.
+    """
+    N = int(N)
+    n = N ** 3
+    kx, ky, kz = (float(v) for v in k)
+    T = {-1: -1.0, 0: 2.0, 1: -1.0}
+    M = {-1: 1.0 / 6.0, 0: 4.0 / 6.0, 1: 1.0 / 6.0}
+    idx = np.arange(n, dtype=np.int64)
+    ix = idx % N
+    iy = (idx // N) % N
+    iz = idx // (N * N)
+    offs, vals, masks = [], [], []
+    for dz in (-1, 0, 1):  # ascending column order: dz, then dy, then dx
+        for dy in (-1, 0, 1):
+            for dx in (-1, 0, 1):
+                offs.append(dz * N * N + dy * N + dx)
+                vals.append(kx * T[dx] * M[dy] * M[dz] + ky * M[dx] * T[dy] * M[dz] + kz * M[dx] * M[dy] * T[dz])
+                ok = np.ones(n, dtype=bool)
+                for d, i in ((dx, ix), (dy, iy), (dz, iz)):
+                    if d < 0:
+                        ok &= i > 0
+                    elif d > 0:
+                        ok &= i < N - 1
+                masks.append(ok)
+    del ix, iy, iz
+    valid = np.stack(masks, axis=1)
+    del masks
+    counts = valid.sum(axis=1)
+    rowptr = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(counts, out=rowptr[1:])
+    cols = (idx[:, None] + np.array(offs, dtype=np.int64)[None, :])[valid].astype(np.int32)
+    v = np.broadcast_to(np.array(vals), (n, 27))[valid].astype(np.float64)
+    return rowptr.astype(np.int32), cols, v
+
+
+def grid27_nnz(N: int) -> int:
+    return (3 * N - 2) ** 3
+
+
+# --------------------------------------------------------------------------
 # right-hand sides and generic helpers
 # --------------------------------------------------------------------------
 def to_scipy(A: CSR) -> sp.csr_matrix:

@@ -13,7 +13,7 @@ import numpy as np
 from paper_1809_05805_b300 import problems as P
 
 EPS = np.finfo(np.float64).eps
-MGS, ONE_REDUCE = 0, 1
+MGS, ONE_REDUCE, IR_FP32 = 0, 1, 2
 
 
 def _dense(A):
@@ -242,6 +242,39 @@ def pin_reduction_counts(orc):
     assert r1.reductions == exp_1r, (r1.reductions, exp_1r)
 
 
+def pin_ir_refines_to_fp64_accuracy(orc):
+    """GMRES-IR (FP32 cycles, FP64 residual and update) reaches a true relative
+    residual of 1e-12 -- far below FP32 rounding -- and its x equals a dense LU
+    solve (numpy) within the conditioning bound."""
+    for A in (P.aniso_27pt(7), P.conv_diff_7pt(7)):
+        xt, b = P.rhs(A, seed=2)
+        D = _dense(A)
+        xref = np.linalg.solve(D, b)
+        kap = np.linalg.cond(D)
+        r = orc.gmres(A, b, variant=IR_FP32, m=30, tol=1e-12, max_iter=2000)
+        assert r.status == 0
+        true = np.linalg.norm(b - D @ r.x) / np.linalg.norm(b)
+        assert true <= 1e-12, true
+        assert np.linalg.norm(r.x - xref) <= 10 * kap * 1e-12 * np.linalg.norm(xref)
+
+
+def pin_ir_cycle_is_fp32(orc):
+    """The IR cycle runs in FP32: its first-cycle residual estimates and Arnoldi
+    relation agree with the FP64 one-reduce cycle at FP32 level (well above
+    FP64 rounding, well below the quantities themselves)."""
+    A = P.aniso_27pt(8)
+    _, b = P.rhs(A, seed=3)
+    m = 20
+    r64 = orc.gmres(A, b, variant=ONE_REDUCE, m=m, tol=0.0, max_iter=m, capture=True)
+    r32 = orc.gmres(A, b, variant=IR_FP32, m=m, tol=0.0, max_iter=m, capture=True)
+    rel = np.abs(r32.history - r64.history) / r64.history
+    assert 1e-10 < rel.max() < 1e-3, rel.max()
+    S = P.to_scipy(A)
+    AV = S @ r32.V[:, : r32.k]
+    err = np.linalg.norm(AV - r32.V @ r32.H) / np.linalg.norm(AV)
+    assert 1e-10 < err < 1e-5, err
+
+
 def simoncini_szyld_run(orc, variant):
     A, b = P.simoncini_szyld(100, seed=0)
     return orc.gmres(A, b, variant=variant, m=100, tol=0.0, max_iter=100, capture=True)
@@ -269,4 +302,6 @@ PINS = [
     pin_finite_termination,
     pin_explicit_residual,
     pin_reduction_counts,
+    pin_ir_refines_to_fp64_accuracy,
+    pin_ir_cycle_is_fp32,
 ]

@@ -96,3 +96,24 @@ def test_generator_stencil_structure():
     assert np.isclose(D[i, i - N], -1.25) and np.isclose(D[i, i - N * N], -1.125)
     off = D - np.diag(np.diag(D))
     assert np.all(off <= 0) and np.all(np.diag(D) >= -off.sum(axis=1))
+
+
+def test_generator_27pt_equals_kronecker_definition():
+    """The 27-point generator equals k_x T(x)M(x)M + k_y M(x)T(x)M + k_z M(x)M(x)T built
+    with scipy's Kronecker products; it is symmetric positive definite."""
+    import scipy.sparse as sp
+
+    N = 5
+    k = (1.0, 1.0, 1e-3)
+    A = P.aniso_27pt(N, k)
+    assert len(A[1]) == P.grid27_nnz(N)
+    Tm = sp.diags([-1.0, 2.0, -1.0], [-1, 0, 1], shape=(N, N))
+    Mm = sp.diags([1.0, 4.0, 1.0], [-1, 0, 1], shape=(N, N)) / 6.0
+    ref = (k[0] * sp.kron(sp.kron(Mm, Mm), Tm) + k[1] * sp.kron(sp.kron(Mm, Tm), Mm)
+           + k[2] * sp.kron(sp.kron(Tm, Mm), Mm)).toarray()
+    D = P.to_scipy(A).toarray()
+    assert np.allclose(D, ref, rtol=0, atol=1e-15)
+    assert np.allclose(D, D.T) and np.linalg.eigvalsh(D).min() > 0
+    for i in range(N ** 3):
+        c = A[1][A[0][i]:A[0][i + 1]]
+        assert np.all(np.diff(c) > 0)
