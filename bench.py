@@ -31,11 +31,19 @@ sys.path.insert(0, ROOT)
 from paper_1809_05805_b300 import problems as P  # noqa: E402
 
 WORKLOADS = {
-    256: dict(N=256, m=50, tol=1e-8, max_iter=3000),
-    128: dict(N=128, m=50, tol=1e-8, max_iter=3000),  # profiling size (inputs still > L2)
-    32: dict(N=32, m=30, tol=1e-8, max_iter=300),
+    # 7-point convection-diffusion, FP64 one-reduce against plain MGS on the same kernels
+    256: dict(N=256, m=50, tol=1e-8, max_iter=3000, stencil="7pt", prec="fp64", compare="mgs"),
+    128: dict(N=128, m=50, tol=1e-8, max_iter=3000, stencil="7pt", prec="fp64", compare="mgs"),  # profiling size
+    32: dict(N=32, m=30, tol=1e-8, max_iter=300, stencil="7pt", prec="fp64", compare="mgs"),
+    # 27-point anisotropic diffusion, GMRES-IR (FP32 cycles) against FP64 one-reduce
+    192: dict(N=192, m=40, tol=1e-10, max_iter=5000, stencil="27pt", prec="ir_fp32", compare="fp64"),
 }
 METRIC = "time-to-solve (1e-8 rel. resid), one-reduce MGS-GMRES"
+METRIC_IR = "time-to-solve (1e-10 rel. resid), GMRES-IR: one-reduce cycles in FP32, FP64 restarts"
+
+
+def make_problem(w):
+    return P.conv_diff_7pt(w["N"]) if w["stencil"] == "7pt" else P.aniso_27pt(w["N"])
 FP64_DFMA_PER_CLK_SM = 2  # B300: 1.25 TFLOP/s nominal FP64 = 148 SMs x 2 DFMA/clk x 2 flop x ~2.1 GHz
 # DRAM bytes per step launch / algorithmic bytes, from the ncu capture summarized in
 # profiles/k_one_reduce_step_128cubed.md (dram__bytes_read.sum + dram__bytes_write.sum).
@@ -45,6 +53,10 @@ STEP_TRAFFIC_RATIO = 1.013
 
 def workload_name(w):
     N = w["N"]
+    if w["stencil"] == "27pt":
+        return (f"3D 27-point anisotropic diffusion k=(1,1,1e-3) {N}^3 (n={N ** 3}, nnz={P.grid27_nnz(N)}), "
+                f"GMRES-IR: one-reduce GMRES({w['m']}) cycles in FP32 (FP32 basis, SpMV, dots, MAXPY) inside "
+                f"FP64 restarts, vs FP64 one-reduce, tol {w['tol']:g}, x0=0")
     return (f"3D 7-point convection-diffusion {N}^3 (n={N ** 3}, nnz={P.grid7_nnz(N)}), FP64 CSR, "
             f"GMRES({w['m']}) one-reduce MGS vs plain MGS, tol {w['tol']:g}, x0=0")
 
@@ -147,11 +159,13 @@ def cpu_baseline(A, b, w, ks_full, sample_iters):
     n, nnz = len(A[0]) - 1, len(A[1])
     o = oracle.get()
     t0 = time.perf_counter()
-    r = o.gmres(A, b, variant=oracle.ONE_REDUCE, m=w["m"], tol=0.0, max_iter=sample_iters)
+    variant = oracle.IR_FP32 if w["prec"] == "ir_fp32" else oracle.ONE_REDUCE
+    r = o.gmres(A, b, variant=variant, m=w["m"], tol=0.0, max_iter=sample_iters)
     dt = time.perf_counter() - t0
     est = dt * oracle_solve_bytes(n, nnz, ks_full) / oracle_solve_bytes(n, nnz, [r.iters])
     return {"value": est, "unit": "s", "cores": 1, "kind": "oracle",
-            "sample": (f"first {r.iters} Arnoldi steps (+ tail, residual, update) of one-reduce GMRES({w['m']}) "
+            "sample": (f"first {r.iters} Arnoldi steps (+ tail, residual, update) of "
+                       f"{'GMRES-IR' if w['prec'] == 'ir_fp32' else 'one-reduce GMRES'}({w['m']}) "
                        f"on the same {w['N']}^3 system, FP64 C oracle on 1 host thread, {dt:.2f} s, scaled to the "
                        f"full solve ({sum(ks_full)} steps, {len(ks_full)} cycles) by a model of the oracle's "
                        f"memory traffic"),
@@ -176,15 +190,15 @@ def golden_profile(name):
 def run_reference(args, w, rank, world):
     if rank != 0:
         return 0
-    A = P.conv_diff_7pt(w["N"])
+    A = make_problem(w)
     _, b = P.rhs(A, seed=0)
-    prof = golden_profile(f"c2_one_reduce" if w["N"] == 256 else "c1")
+    prof = golden_profile({256: "c2_one_reduce", 32: "c1", 192: "c3_ir"}.get(w["N"], "none"))
     if prof is None:
         print(json.dumps({"impl": "reference", "unavailable": "oracle iteration profile for this workload "
                           "(tests/golden/oracle_profile_*.txt) has not been written"}))
         return 0
     ks = cycle_profile(int(prof["iters"]), w["m"])
-    sample = 12 if w["N"] == 256 else w["max_iter"]
+    sample = 12 if w["N"] >= 128 else w["max_iter"]
     vals = []
     for s in range(args.warmup + args.steps):
         cb = cpu_baseline(A, b, w, ks, sample)
@@ -193,7 +207,7 @@ def run_reference(args, w, rank, world):
     v = float(np.mean([c["value"] for c in vals]))
     cores = 1
     line = {
-        "impl": "reference", "metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus,
+        "impl": "reference", "metric": METRIC_IR if w["prec"] == "ir_fp32" else METRIC, "value": v, "unit": "s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * v, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": workload_name(w), "m": w["m"], "tol": w["tol"]},
@@ -242,10 +256,11 @@ def run_ours(args, w, rank, world, dist):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     stream = torch.cuda.Stream()
-    A = P.conv_diff_7pt(w["N"])
+    A = make_problem(w)
     _, b = P.rhs(A, seed=0)
     n, nnz = len(A[0]) - 1, len(A[1])
     peaks = load_peaks()
+    ir = w["prec"] == "ir_fp32"
 
     def barrier():
         if dist is not None:
@@ -261,7 +276,8 @@ def run_ours(args, w, rank, world, dist):
 
     bd = torch.from_numpy(b).cuda()
     x = torch.zeros(n, dtype=torch.float64, device="cuda")
-    s = lsgmres.Solver(A, m=w["m"], tol=w["tol"], ortho="one_reduce_mgs", max_iter=w["max_iter"], stream=stream)
+    s = lsgmres.Solver(A, m=w["m"], tol=w["tol"], ortho="one_reduce_mgs", max_iter=w["max_iter"], stream=stream,
+                       prec=w["prec"])
     s.set_profile(True)
 
     barrier()
@@ -275,9 +291,23 @@ def run_ours(args, w, rank, world, dist):
     true_rel = float(np.linalg.norm(b - P.to_scipy(A) @ xs) / np.linalg.norm(b))
     hist_1r = s.history()
 
-    # plain MGS on the same kernels
+    # the comparison leg on the same kernels: plain MGS (FP64 workloads) or the
+    # FP64 one-reduce solve (GMRES-IR workload, which also gives IR's error)
     mgs = None
-    if not args.no_mgs:
+    fp64 = None
+    if not args.no_mgs and w["compare"] == "fp64":
+        s.set(ortho="one_reduce_mgs", prec="fp64", max_iter=w["max_iter"])
+        ms_f, infos_f, prof_f = timed_solves(torch, s, bd, x, max(1, min(args.steps, 2)), 1, stream)
+        ms_f = max_over_ranks(ms_f)
+        i64 = infos_f[-1]
+        x64 = x.cpu().numpy()
+        fp64 = {"time_to_solve_s": ms_f / 1e3, "iters": i64.iters, "restarts": i64.restarts,
+                "rel_resid_true": i64.rel_resid_true,
+                "ir_rel_error_vs_fp64": float(np.linalg.norm(xs - x64) / np.linalg.norm(x64)),
+                "step_tflops_fp64": prof_f["one_reduce_step"]["flops"] / (prof_f["one_reduce_step"]["ms"] * 1e9)
+                if prof_f["one_reduce_step"]["ms"] else None}
+        s.set(ortho="one_reduce_mgs", prec=w["prec"], max_iter=w["max_iter"])
+    if not args.no_mgs and w["compare"] == "mgs":
         s.set(ortho="mgs", max_iter=w["max_iter"])
         ms_m, infos_m, prof_m = timed_solves(torch, s, bd, x, max(1, min(args.steps, 2)), 1, stream)
         ms_m = max_over_ranks(ms_m)
@@ -313,45 +343,64 @@ def run_ours(args, w, rank, world, dist):
     step_tflops = st["flops"] / (st["ms"] * 1e-3) / 1e12 if st["ms"] else None
     step_gbs = st["bytes"] / (st["ms"] * 1e-3) / 1e9 if st["ms"] else None
     hbm = float(peaks.get("hbm_gbs", 6400.0))
-    roofline = {
-        "kernel": "k_one_reduce_step (fused CSR SpMV + block dot [V u]^T[u w] + epilogue)",
-        "bound": "alu", "achieved": step_tflops, "peak": fp64_peak, "unit": "TFLOP/s",
-        "frac": step_tflops / fp64_peak if step_tflops else None,
-        "peak_source": (f"FP64 pipe derived from unit counts and clock: 148 SMs x {FP64_DFMA_PER_CLK_SM} DFMA/clk x 2 "
-                        f"flop x {peaks.get('sm_max_mhz', 2032.0):g} MHz (nominal 1.25 TFLOP/s)"),
-        "traffic": (STEP_TRAFFIC_RATIO * st["bytes"] / max(st["launches"], 1)) if STEP_TRAFFIC_RATIO else None,
-        "traffic_source": "ncu dram bytes / algorithmic bytes at 128^3 (same kernel build), times this run's "
-                          "algorithmic bytes per launch",
-        "launch_avg_ms": step_avg_ms, "launches": st["launches"],
-        "alg_flops_per_launch": st["flops"] / max(st["launches"], 1),
-        "alg_bytes_per_launch": st["bytes"] / max(st["launches"], 1),
-        "hbm_gbs": step_gbs, "hbm_frac_of_measured": step_gbs / hbm if step_gbs else None,
-        "maxpy": {"launch_avg_ms": mx["ms"] / max(mx["launches"], 1),
-                  "tflops": mx["flops"] / (mx["ms"] * 1e-3) / 1e12 if mx["ms"] else None,
-                  "hbm_gbs": mx["bytes"] / (mx["ms"] * 1e-3) / 1e9 if mx["ms"] else None},
-    }
+    if ir:  # FP32 cycles: the step kernel streams at FP32 rates, HBM is the bound
+        roofline = {
+            "kernel": "k_one_reduce_step<float> (fused FP32 CSR SpMV + block dot + epilogue)",
+            "bound": "hbm", "achieved": step_gbs, "peak": hbm, "unit": "GB/s",
+            "frac": step_gbs / hbm if step_gbs else None,
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy bandwidth, of measured)",
+            "traffic": None,
+            "launch_avg_ms": step_avg_ms, "launches": st["launches"],
+            "alg_bytes_per_launch": st["bytes"] / max(st["launches"], 1),
+            "fp32_tflops": step_tflops,
+            "maxpy": {"launch_avg_ms": mx["ms"] / max(mx["launches"], 1),
+                      "hbm_gbs": mx["bytes"] / (mx["ms"] * 1e-3) / 1e9 if mx["ms"] else None,
+                      "hbm_frac_of_measured": (mx["bytes"] / (mx["ms"] * 1e-3) / 1e9) / hbm if mx["ms"] else None},
+        }
+    else:
+        roofline = {
+            "kernel": "k_one_reduce_step (fused CSR SpMV + block dot [V u]^T[u w] + epilogue)",
+            "bound": "alu", "achieved": step_tflops, "peak": fp64_peak, "unit": "TFLOP/s",
+            "frac": step_tflops / fp64_peak if step_tflops else None,
+            "peak_source": (f"FP64 pipe derived from unit counts and clock: 148 SMs x {FP64_DFMA_PER_CLK_SM} DFMA/clk x 2 "
+                            f"flop x {peaks.get('sm_max_mhz', 2032.0):g} MHz (nominal 1.25 TFLOP/s)"),
+            "traffic": (STEP_TRAFFIC_RATIO * st["bytes"] / max(st["launches"], 1)) if STEP_TRAFFIC_RATIO else None,
+            "traffic_source": "ncu dram bytes / algorithmic bytes at 128^3 (same kernel build), times this run's "
+                              "algorithmic bytes per launch",
+            "launch_avg_ms": step_avg_ms, "launches": st["launches"],
+            "alg_flops_per_launch": st["flops"] / max(st["launches"], 1),
+            "alg_bytes_per_launch": st["bytes"] / max(st["launches"], 1),
+            "hbm_gbs": step_gbs, "hbm_frac_of_measured": step_gbs / hbm if step_gbs else None,
+            "maxpy": {"launch_avg_ms": mx["ms"] / max(mx["launches"], 1),
+                      "tflops": mx["flops"] / (mx["ms"] * 1e-3) / 1e12 if mx["ms"] else None,
+                      "hbm_gbs": mx["bytes"] / (mx["ms"] * 1e-3) / 1e9 if mx["ms"] else None},
+        }
     total_bytes = sum(v["bytes"] for v in prof.values())
     total_ms_prof = sum(v["ms"] for v in prof.values())
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         ks = cycle_profile(info.iters, w["m"])
-        sample = 12 if w["N"] == 256 else w["max_iter"]
+        sample = 12 if w["N"] >= 128 else w["max_iter"]
         cpu = cpu_baseline(A, b, w, ks, sample)
 
     line = {
-        "metric": METRIC, "value": ms / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
+        "metric": METRIC_IR if ir else METRIC, "value": ms / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded stencil, x_true ~ U[-1,1])",
+        "vs_baseline": None, "dtype": "f32 cycles / f64 restarts" if ir else "f64",
+        "data": "synthetic (seeded stencil, x_true ~ U[-1,1])",
         "config": {"workload": workload_name(w), "n": n, "nnz": nnz, "m": w["m"], "tol": w["tol"],
                    "parallelism": "replicas" if world > 1 else "1 GPU",
-                   "l2": "inputs larger than L2 (Krylov basis %.1f GB >> 126 MB), no flush" % (8 * n * (w["m"] + 1) / 1e9)},
+                   "l2": "inputs larger than L2 (Krylov basis %.1f GB >> 126 MB), no flush"
+                         % ((4 if ir else 8) * n * (w["m"] + 1) / 1e9)},
         "iters": info.iters, "restarts": info.restarts, "reductions": info.reductions,
         "grid_syncs": info.grid_syncs, "rel_resid_true": true_rel,
         "solves_per_s": world / (ms / 1e3),
         "alg_hbm_gbs_whole_solve": total_bytes / (total_ms_prof * 1e6) if total_ms_prof else None,
         "mgs": mgs,
         "speedup_vs_mgs": (mgs["time_to_solve_s"] / (ms / 1e3)) if mgs else None,
+        "fp64_one_reduce": fp64,
+        "speedup_vs_fp64": (fp64["time_to_solve_s"] / (ms / 1e3)) if fp64 else None,
         "e2e": {"value": e2e_ms / 1e3, "unit": "s", "h2d_bytes_per_step": 16 * n, "d2h_bytes_per_step": 8 * n},
         "gpu_launches": int(sum(i.kernel_launches for i in infos)),
         "roofline": roofline,

@@ -55,8 +55,16 @@ typedef enum {
 
 typedef enum { GMRES_MGS = 0, GMRES_ONE_REDUCE_MGS = 1 } gmres_ortho;
 
-/* Arithmetic of the Krylov loop. Only GMRES_FP64 is implemented; the others
- * are reserved for mixed-precision iterative refinement and are rejected. */
+/* Arithmetic of the Krylov loop.
+ *   GMRES_FP64     everything in FP64.
+ *   GMRES_IR_FP32  GMRES-IR: every restart cycle runs the one-reduce Arnoldi
+ *                  steps with FP32 vectors (basis, A u with FP32 matrix values,
+ *                  block inner products and MAXPY, FP32 accumulation), while the
+ *                  residual b - A x, the small dense algebra and the correction
+ *                  x += V y stay FP64, so the solve still reaches FP64 residuals.
+ *                  One-reduce scheme only; gmres_set allocates the FP32 copies
+ *                  ((m+1) n + n + nnz floats, n doubles) on first use.
+ *   GMRES_IR_BF16  reserved (rejected). */
 typedef enum { GMRES_FP64 = 0, GMRES_IR_FP32 = 1, GMRES_IR_BF16 = 2 } gmres_prec;
 
 typedef struct gmres_ctx* gmres_handle;
@@ -97,7 +105,8 @@ gmres_status gmres_create(const gmres_csr* A, int m_restart, double tol, gmres_h
 
 /* Select the orthogonalization scheme, the arithmetic and the iteration limit
  * (max_iter >= 0 Arnoldi steps over all cycles). GMRES_ERR_ARG for an unknown
- * scheme, a precision other than GMRES_FP64, or max_iter < 0. */
+ * scheme, GMRES_IR_BF16, GMRES_IR_FP32 with GMRES_MGS, or max_iter < 0;
+ * GMRES_ERR_OOM if the FP32 copies cannot be allocated. */
 gmres_status gmres_set(gmres_handle h, gmres_ortho ortho, gmres_prec prec, int max_iter);
 
 /* Change the tolerance (tol >= 0). */

@@ -32,6 +32,7 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "lsgmres.h"
@@ -51,6 +52,7 @@ constexpr double kBreakdownFactor = 16.0;
 struct DevState {
   double bnorm;        // ||b|| (or ||r0|| for gmres_arnoldi)
   double inv_bnorm;    // 1 / bnorm (the residual estimate multiplies; FP64 division is slow)
+  double cycle_scale;  // norm the cycle's right-hand side was divided by (FP32 cycles), else 1
   double rnorm;        // last true-residual norm
   double tol;
   double est;          // last Givens estimate (relative)
@@ -104,15 +106,16 @@ __device__ __forceinline__ double warp_sum(double v) {
 // (16 + 8 + 4 + 2 + 1), each lane keeping the half its lane bit selects at
 // every level. On return lane l holds the sum over the 32 lanes of slot l
 // (also returned). Fixed order: bitwise reproducible.
-__device__ __forceinline__ double warp_reduce_scatter32(double* v) {
+template <typename T>
+__device__ __forceinline__ T warp_reduce_scatter32(T* v) {
   const int lane = threadIdx.x & 31;
 #pragma unroll
   for (int o = 16; o >= 1; o >>= 1) {
     const bool up = (lane & o) != 0;
 #pragma unroll
     for (int i = 0; i < o; ++i) {
-      const double send = up ? v[i] : v[i + o];
-      const double keep = up ? v[i + o] : v[i];
+      const T send = up ? v[i] : v[i + o];
+      const T keep = up ? v[i + o] : v[i];
       v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
     }
   }
@@ -136,23 +139,24 @@ __device__ __forceinline__ double block_sum(double v, double* sbuf /* kWarps */)
 // Row i of A times x (CSR, FP64 FMA chain in column order). The loads of up
 // to 8 entries are issued together (predicated), so a stencil row costs two
 // dependent memory latencies (indices, then the gather) instead of two per entry.
-__device__ __forceinline__ double csr_row(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-                                          const double* __restrict__ val, const double* __restrict__ x,
+template <typename VT>
+__device__ __forceinline__ VT csr_row(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                                          const VT* __restrict__ val, const VT* __restrict__ x,
                                           int64_t i) {
   constexpr int kW = 8;
   const int p0 = __ldg(rowptr + i), p1 = __ldg(rowptr + i + 1);
-  double s = 0.0;
+  VT s = VT(0);
   for (int p = p0; p < p1; p += kW) {
     int c[kW];
-    double v[kW], xv[kW];
+    VT v[kW], xv[kW];
 #pragma unroll
     for (int e = 0; e < kW; ++e) {
       const bool ok = p + e < p1;
       c[e] = ok ? __ldg(col + p + e) : 0;
-      v[e] = ok ? __ldg(val + p + e) : 0.0;
+      v[e] = ok ? __ldg(val + p + e) : VT(0);
     }
 #pragma unroll
-    for (int e = 0; e < kW; ++e) xv[e] = (p + e < p1) ? __ldg(x + c[e]) : 0.0;
+    for (int e = 0; e < kW; ++e) xv[e] = (p + e < p1) ? __ldg(x + c[e]) : VT(0);
 #pragma unroll
     for (int e = 0; e < kW; ++e)
       if (p + e < p1) s = fma(v[e], xv[e], s);
@@ -162,29 +166,30 @@ __device__ __forceinline__ double csr_row(const int32_t* __restrict__ rowptr, co
 
 // Rows r0 and r1 of A times x with the loads of both rows in flight together
 // (rows of up to 8 entries; longer rows use csr_row). Rows >= n give 0.
+template <typename VT>
 __device__ __forceinline__ void csr_row2(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-                                         const double* __restrict__ val, const double* __restrict__ x,
-                                         int64_t r0, int64_t r1, int64_t n, double& y0, double& y1) {
+                                         const VT* __restrict__ val, const VT* __restrict__ x,
+                                         int64_t r0, int64_t r1, int64_t n, VT& y0, VT& y1) {
   constexpr int kW = 8;
   const int a0 = r0 < n ? __ldg(rowptr + r0) : 0, b0 = r0 < n ? __ldg(rowptr + r0 + 1) : 0;
   const int a1 = r1 < n ? __ldg(rowptr + r1) : 0, b1 = r1 < n ? __ldg(rowptr + r1 + 1) : 0;
   if (b0 - a0 <= kW && b1 - a1 <= kW) {
     int c0[kW], c1[kW];
-    double v0[kW], v1[kW];
+    VT v0[kW], v1[kW];
 #pragma unroll
     for (int e = 0; e < kW; ++e) {
       c0[e] = (a0 + e < b0) ? __ldg(col + a0 + e) : 0;
-      v0[e] = (a0 + e < b0) ? __ldg(val + a0 + e) : 0.0;
+      v0[e] = (a0 + e < b0) ? __ldg(val + a0 + e) : VT(0);
       c1[e] = (a1 + e < b1) ? __ldg(col + a1 + e) : 0;
-      v1[e] = (a1 + e < b1) ? __ldg(val + a1 + e) : 0.0;
+      v1[e] = (a1 + e < b1) ? __ldg(val + a1 + e) : VT(0);
     }
-    double x0[kW], x1[kW];
+    VT x0[kW], x1[kW];
 #pragma unroll
     for (int e = 0; e < kW; ++e) {
-      x0[e] = (a0 + e < b0) ? __ldg(x + c0[e]) : 0.0;
-      x1[e] = (a1 + e < b1) ? __ldg(x + c1[e]) : 0.0;
+      x0[e] = (a0 + e < b0) ? __ldg(x + c0[e]) : VT(0);
+      x1[e] = (a1 + e < b1) ? __ldg(x + c1[e]) : VT(0);
     }
-    double s0 = 0.0, s1 = 0.0;
+    VT s0 = VT(0), s1 = VT(0);
 #pragma unroll
     for (int e = 0; e < kW; ++e) {
       if (a0 + e < b0) s0 = fma(v0[e], x0[e], s0);
@@ -193,8 +198,8 @@ __device__ __forceinline__ void csr_row2(const int32_t* __restrict__ rowptr, con
     y0 = s0;
     y1 = s1;
   } else {
-    y0 = r0 < n ? csr_row(rowptr, col, val, x, r0) : 0.0;
-    y1 = r1 < n ? csr_row(rowptr, col, val, x, r1) : 0.0;
+    y0 = r0 < n ? csr_row(rowptr, col, val, x, r0) : VT(0);
+    y1 = r1 < n ? csr_row(rowptr, col, val, x, r1) : VT(0);
   }
 }
 
@@ -291,7 +296,7 @@ __device__ int finish_column(Small s, int j, double h, bool last_allowed) {
     const double gj = s.g[j];
     s.g[j + 1] = -sn * gj;
     s.g[j] = c * gj;
-    const double est = fabs(sn * gj) * st->inv_bnorm;
+    const double est = fabs(sn * gj) * st->cycle_scale * st->inv_bnorm;
     const int it = st->total_iters + j;
     if (it < s.hist_cap) s.hist[it] = est;
     st->k = j + 1;
@@ -325,16 +330,15 @@ __device__ int finish_column(Small s, int j, double h, bool last_allowed) {
 // At j == kmax (the tail) the SpMV and c, d are skipped.
 // Standalone mode (raw_out != nullptr): j is j_arg, w may be an input
 // (use_spmv == 0), and the totals go to raw_out without the GMRES epilogue.
-template <int MAXC>
+template <int MAXC, typename VT>
 __global__ void __launch_bounds__(kThreads, 2)
 k_one_reduce_step(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-                  const double* __restrict__ val, const double* __restrict__ V, int64_t ldv,
-                  const double* __restrict__ u_arg, double* __restrict__ w, int64_t n, Small s,
+                  const VT* __restrict__ val, const VT* __restrict__ V, int64_t ldv,
+                  const VT* __restrict__ u_arg, VT* __restrict__ w, int64_t n, Small s,
                   int j_arg, int use_spmv, double* raw_out) {
-  __shared__ double su[2 * kThreads];
-  __shared__ double sw[2 * kThreads];
+  __shared__ VT su[2 * kThreads];
+  __shared__ VT sw[2 * kThreads];
   __shared__ double red[2 * (kMaxM + 1) + 2];
-  __shared__ double sbuf[kWarps];
   __shared__ int s_j, s_tail, s_skip;
   DevState* st = s.st;
   if (threadIdx.x == 0) {
@@ -354,7 +358,7 @@ k_one_reduce_step(const int32_t* __restrict__ rowptr, const int32_t* __restrict_
   const bool tail = s_tail;
   const bool spmv = raw_out ? (use_spmv != 0) : !tail;
   const bool need_w = raw_out ? true : !tail;
-  const double* u = raw_out ? u_arg : V + (size_t)j * ldv;
+  const VT* u = raw_out ? u_arg : V + (size_t)j * ldv;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 
   // Work split of the block dot over a tile of 256 rows (8 row groups of 32):
@@ -362,13 +366,13 @@ k_one_reduce_step(const int32_t* __restrict__ rowptr, const int32_t* __restrict_
   // all 8 row groups); the r8 = j mod 8 remaining columns are split by rows,
   // each warp taking its own row group. Every warp issues the same DFMAs.
   const int J8 = j / kWarps, r8 = j % kWarps;
-  double acc_a[MAXC], acc_c[MAXC];
-  double rem_a[kWarps - 1], rem_c[kWarps - 1];
+  VT acc_a[MAXC], acc_c[MAXC];
+  VT rem_a[kWarps - 1], rem_c[kWarps - 1];
 #pragma unroll
-  for (int c = 0; c < MAXC; ++c) acc_a[c] = acc_c[c] = 0.0;
+  for (int c = 0; c < MAXC; ++c) acc_a[c] = acc_c[c] = VT(0);
 #pragma unroll
-  for (int c = 0; c < kWarps - 1; ++c) rem_a[c] = rem_c[c] = 0.0;
-  double sig = 0.0, dd = 0.0;
+  for (int c = 0; c < kWarps - 1; ++c) rem_a[c] = rem_c[c] = VT(0);
+  VT sig = VT(0), dd = VT(0);
 
   const int64_t ntiles = (n + kThreads - 1) / kThreads;
   // Large problems take tiles in pairs (the CSR loads of two rows per thread are
@@ -378,7 +382,7 @@ k_one_reduce_step(const int32_t* __restrict__ rowptr, const int32_t* __restrict_
     const int64_t npairs = (ntiles + 1) / 2;
     for (int64_t pp = blockIdx.x; pp < npairs; pp += gridDim.x) {
       const int64_t row0 = pp * (2 * kThreads) + threadIdx.x, row1 = row0 + kThreads;
-      double ur0 = 0.0, wr0 = 0.0, ur1 = 0.0, wr1 = 0.0;
+      VT ur0 = VT(0), wr0 = VT(0), ur1 = VT(0), wr1 = VT(0);
       if (row0 < n) ur0 = u[row0];
       if (row1 < n) ur1 = u[row1];
       if (spmv) {
@@ -401,7 +405,7 @@ k_one_reduce_step(const int32_t* __restrict__ rowptr, const int32_t* __restrict_
   #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int64_t base = pp * (2 * kThreads) + h * kThreads + lane;
-        double ru[kRowsPerLane], rw[kRowsPerLane];
+        VT ru[kRowsPerLane], rw[kRowsPerLane];
   #pragma unroll
         for (int q = 0; q < kRowsPerLane; ++q) {
           ru[q] = su[h * kThreads + lane + 32 * q];
@@ -411,10 +415,10 @@ k_one_reduce_step(const int32_t* __restrict__ rowptr, const int32_t* __restrict_
         for (int c = 0; c < MAXC; ++c) {
           if (c < J8) {  // warp-uniform
             const int k = wid + c * kWarps;
-            const double* vk = V + (size_t)k * ldv + base;
-            double x[kRowsPerLane];
+            const VT* vk = V + (size_t)k * ldv + base;
+            VT x[kRowsPerLane];
   #pragma unroll
-            for (int q = 0; q < kRowsPerLane; ++q) x[q] = (base + 32 * q < n) ? __ldg(vk + 32 * q) : 0.0;
+            for (int q = 0; q < kRowsPerLane; ++q) x[q] = (base + 32 * q < n) ? __ldg(vk + 32 * q) : VT(0);
   #pragma unroll
             for (int q = 0; q < kRowsPerLane; ++q) {
               acc_a[c] = fma(x[q], ru[q], acc_a[c]);
@@ -426,9 +430,9 @@ k_one_reduce_step(const int32_t* __restrict__ rowptr, const int32_t* __restrict_
   #pragma unroll
       for (int c = 0; c < kWarps - 1; ++c) {
         if (c < r8) {  // block-uniform
-          const double* vk = V + (size_t)(J8 * kWarps + c) * ldv;
-          const double x0 = (row0 < n) ? __ldg(vk + row0) : 0.0;
-          const double x1 = (row1 < n) ? __ldg(vk + row1) : 0.0;
+          const VT* vk = V + (size_t)(J8 * kWarps + c) * ldv;
+          const VT x0 = (row0 < n) ? __ldg(vk + row0) : VT(0);
+          const VT x1 = (row1 < n) ? __ldg(vk + row1) : VT(0);
           rem_a[c] = fma(x0, ur0, rem_a[c]);
           rem_c[c] = fma(x0, wr0, rem_c[c]);
           rem_a[c] = fma(x1, ur1, rem_a[c]);
@@ -440,7 +444,7 @@ k_one_reduce_step(const int32_t* __restrict__ rowptr, const int32_t* __restrict_
   } else {
     for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
       const int64_t row = t * kThreads + threadIdx.x;
-      double ur = 0.0, wr = 0.0;
+      VT ur = VT(0), wr = VT(0);
       if (row < n) {
         ur = u[row];
         if (spmv) {
@@ -456,7 +460,7 @@ k_one_reduce_step(const int32_t* __restrict__ rowptr, const int32_t* __restrict_
       sw[threadIdx.x] = wr;
       __syncthreads();
       const int64_t base = t * kThreads + lane;
-      double ru[kRowsPerLane], rw[kRowsPerLane];
+      VT ru[kRowsPerLane], rw[kRowsPerLane];
   #pragma unroll
       for (int q = 0; q < kRowsPerLane; ++q) {
         ru[q] = su[lane + 32 * q];
@@ -466,10 +470,10 @@ k_one_reduce_step(const int32_t* __restrict__ rowptr, const int32_t* __restrict_
       for (int c = 0; c < MAXC; ++c) {
         if (c < J8) {  // warp-uniform
           const int k = wid + c * kWarps;
-          const double* vk = V + (size_t)k * ldv + base;
-          double x[kRowsPerLane];
+          const VT* vk = V + (size_t)k * ldv + base;
+          VT x[kRowsPerLane];
   #pragma unroll
-          for (int q = 0; q < kRowsPerLane; ++q) x[q] = (base + 32 * q < n) ? __ldg(vk + 32 * q) : 0.0;
+          for (int q = 0; q < kRowsPerLane; ++q) x[q] = (base + 32 * q < n) ? __ldg(vk + 32 * q) : VT(0);
   #pragma unroll
           for (int q = 0; q < kRowsPerLane; ++q) {
             acc_a[c] = fma(x[q], ru[q], acc_a[c]);
@@ -480,7 +484,7 @@ k_one_reduce_step(const int32_t* __restrict__ rowptr, const int32_t* __restrict_
   #pragma unroll
       for (int c = 0; c < kWarps - 1; ++c) {
         if (c < r8) {  // block-uniform
-          const double x = (row < n) ? __ldg(V + (size_t)(J8 * kWarps + c) * ldv + row) : 0.0;
+          const VT x = (row < n) ? __ldg(V + (size_t)(J8 * kWarps + c) * ldv + row) : VT(0);
           rem_a[c] = fma(x, ur, rem_a[c]);
           rem_c[c] = fma(x, wr, rem_c[c]);
         }
@@ -495,9 +499,9 @@ k_one_reduce_step(const int32_t* __restrict__ rowptr, const int32_t* __restrict_
   // value): lane l then holds the warp total of slot l.
   constexpr int kSlots = 2 * MAXC + 2 * (kWarps - 1) + 2;
   constexpr int kChunks = (kSlots + 31) / 32;
-  double v[kChunks * 32];
+  VT v[kChunks * 32];
 #pragma unroll
-  for (int i = 0; i < kChunks * 32; ++i) v[i] = 0.0;
+  for (int i = 0; i < kChunks * 32; ++i) v[i] = VT(0);
 #pragma unroll
   for (int c = 0; c < MAXC; ++c) {
     v[c] = acc_a[c];
@@ -510,10 +514,10 @@ k_one_reduce_step(const int32_t* __restrict__ rowptr, const int32_t* __restrict_
   }
   v[kSlots - 2] = sig;
   v[kSlots - 1] = dd;
-  __shared__ double scross[kSlots - 2 * MAXC][kWarps];  // slots summed across warps
+  __shared__ VT scross[kSlots - 2 * MAXC][kWarps];  // slots summed across warps
 #pragma unroll
   for (int ch = 0; ch < kChunks; ++ch) {
-    const double tot = warp_reduce_scatter32(v + 32 * ch);
+    const VT tot = warp_reduce_scatter32(v + 32 * ch);
     const int slot = 32 * ch + lane;
     if (slot < MAXC) {
       if (slot < J8) red[wid + slot * kWarps] = tot;  // column wid + 8 slot belongs to this warp
@@ -658,32 +662,51 @@ k_one_reduce_step(const int32_t* __restrict__ rowptr, const int32_t* __restrict_
 // --------------------------------------------------------------------------
 enum { MAXPY_ARNOLDI = 0, MAXPY_XUPDATE = 1, MAXPY_STANDALONE = 2 };
 
+template <typename T>
+struct Vec16;  // a 16-byte vector of T
+template <>
+struct Vec16<double> {
+  using type = double2;
+};
+template <>
+struct Vec16<float> {
+  using type = float4;
+};
+
+// VT: basis type, YT: type of y_in / y_out, CT: arithmetic type. Arnoldi mode
+// needs VT == YT (the output is a basis column); the FP32 solution update of
+// GMRES-IR uses VT = float, YT = CT = double.
+template <typename VT, typename YT, typename CT>
 __global__ void __launch_bounds__(kThreads, 4)
-k_maxpy(const double* __restrict__ V, int64_t ldv, const double* y_in, double* y_out, int64_t n,
-        Small s, int mode, int K_arg) {
+k_maxpy(const VT* __restrict__ V, int64_t ldv, const YT* y_in, YT* y_out, int64_t n, Small s, int mode,
+        int K_arg) {
   __shared__ double sc[kMaxM + 3];
+  __shared__ CT scc[kMaxM + 3];
   __shared__ int sK, s_skip;
-  __shared__ double* s_out;
+  __shared__ YT* s_out;
   DevState* st = s.st;
   if (threadIdx.x == 0) {
     s_skip = 0;
+    s_out = y_out;
     if (mode == MAXPY_ARNOLDI) {
       s_skip = __ldcg(&st->done);
       sK = __ldcg(&st->maxpy_k);
-      s_out = const_cast<double*>(V) + (size_t)__ldcg(&st->step) * ldv;
+      if constexpr (std::is_same<VT, YT>::value)
+        s_out = const_cast<VT*>(V) + (size_t)__ldcg(&st->step) * ldv;
     } else if (mode == MAXPY_XUPDATE) {
       sK = __ldcg(&st->k);
-      s_out = y_out;
     } else {
       sK = K_arg;
-      s_out = y_out;
     }
   }
   __syncthreads();
   if (s_skip) return;
   const int K = sK;
   const double* cf = (mode == MAXPY_XUPDATE) ? s.coefx : s.coef;
-  for (int i = threadIdx.x; i <= K; i += blockDim.x) sc[i] = __ldcg(cf + i);
+  for (int i = threadIdx.x; i <= K; i += blockDim.x) {
+    sc[i] = __ldcg(cf + i);
+    scc[i] = (CT)sc[i];
+  }
   __syncthreads();
   if (mode == MAXPY_ARNOLDI && blockIdx.x == gridDim.x - 1) {
     // The last CTA of an Arnoldi MAXPY finishes column j-1 of H (Givens,
@@ -700,47 +723,62 @@ k_maxpy(const double* __restrict__ V, int64_t ldv, const double* y_in, double* y
     return;
   }
   const int ndata = gridDim.x - (mode == MAXPY_ARNOLDI ? 1 : 0);  // CTAs that stream
-  double* out = s_out;
-  const double alpha = sc[0];
-  const bool vec = ((reinterpret_cast<uintptr_t>(y_in) | reinterpret_cast<uintptr_t>(out) |
-                     reinterpret_cast<uintptr_t>(V)) & 15) == 0 && (ldv & 1) == 0;
+  YT* out = s_out;
+  const CT alpha = scc[0];
   const int64_t stride = (int64_t)ndata * blockDim.x;
   const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (vec) {
-    const int64_t n2 = n / 2;
-    for (int64_t i = gid; i < n2; i += stride) {
-      const double2 y = reinterpret_cast<const double2*>(y_in)[i];
-      double a0 = alpha * y.x, a1 = alpha * y.y;
-      int k = 0;
-      for (; k + 4 <= K; k += 4) {  // four independent loads in flight per thread
-        double2 v[4];
+  int64_t done_rows = 0;
+  if constexpr (std::is_same<VT, YT>::value) {
+    constexpr int E = 16 / (int)sizeof(VT);
+    using V16 = typename Vec16<VT>::type;
+    union U {
+      V16 v;
+      VT e[E];
+    };
+    const bool vec = ((reinterpret_cast<uintptr_t>(y_in) | reinterpret_cast<uintptr_t>(out) |
+                       reinterpret_cast<uintptr_t>(V)) & 15) == 0 && (ldv % E) == 0;
+    if (vec) {
+      const int64_t nE = n / E;
+      for (int64_t i = gid; i < nE; i += stride) {
+        U y;
+        y.v = reinterpret_cast<const V16*>(y_in)[i];
+        CT a[E];
 #pragma unroll
-        for (int u2 = 0; u2 < 4; ++u2) v[u2] = __ldg(reinterpret_cast<const double2*>(V + (size_t)(k + u2) * ldv) + i);
+        for (int e = 0; e < E; ++e) a[e] = alpha * (CT)y.e[e];
+        int k = 0;
+        for (; k + 4 <= K; k += 4) {  // four independent loads in flight per thread
+          U v[4];
 #pragma unroll
-        for (int u2 = 0; u2 < 4; ++u2) {
-          a0 = fma(sc[1 + k + u2], v[u2].x, a0);
-          a1 = fma(sc[1 + k + u2], v[u2].y, a1);
+          for (int u2 = 0; u2 < 4; ++u2) v[u2].v = __ldg(reinterpret_cast<const V16*>(V + (size_t)(k + u2) * ldv) + i);
+#pragma unroll
+          for (int u2 = 0; u2 < 4; ++u2)
+#pragma unroll
+            for (int e = 0; e < E; ++e) a[e] = fma(scc[1 + k + u2], (CT)v[u2].e[e], a[e]);
         }
+        for (; k < K; ++k) {
+          U v;
+          v.v = __ldg(reinterpret_cast<const V16*>(V + (size_t)k * ldv) + i);
+#pragma unroll
+          for (int e = 0; e < E; ++e) a[e] = fma(scc[1 + k], (CT)v.e[e], a[e]);
+        }
+        U o;
+#pragma unroll
+        for (int e = 0; e < E; ++e) o.e[e] = (VT)a[e];
+        reinterpret_cast<V16*>(out)[i] = o.v;
       }
-      for (; k < K; ++k) {
-        const double2 v = __ldg(reinterpret_cast<const double2*>(V + (size_t)k * ldv) + i);
-        a0 = fma(sc[1 + k], v.x, a0);
-        a1 = fma(sc[1 + k], v.y, a1);
+      done_rows = nE * E;
+      for (int64_t i = done_rows + gid; i < n; i += stride) {  // ragged tail
+        CT a0 = alpha * (CT)y_in[i];
+        for (int k = 0; k < K; ++k) a0 = fma(scc[1 + k], (CT)V[(size_t)k * ldv + i], a0);
+        out[i] = (YT)a0;
       }
-      reinterpret_cast<double2*>(out)[i] = make_double2(a0, a1);
+      return;
     }
-    if ((n & 1) && gid == 0) {
-      const int64_t i = n - 1;
-      double a0 = alpha * y_in[i];
-      for (int k = 0; k < K; ++k) a0 = fma(sc[1 + k], V[(size_t)k * ldv + i], a0);
-      out[i] = a0;
-    }
-  } else {
-    for (int64_t i = gid; i < n; i += stride) {
-      double a0 = alpha * y_in[i];
-      for (int k = 0; k < K; ++k) a0 = fma(sc[1 + k], V[(size_t)k * ldv + i], a0);
-      out[i] = a0;
-    }
+  }
+  for (int64_t i = done_rows + gid; i < n; i += stride) {
+    CT a0 = alpha * (CT)y_in[i];
+    for (int k = 0; k < K; ++k) a0 = fma(scc[1 + k], (CT)V[(size_t)k * ldv + i], a0);
+    out[i] = (YT)a0;
   }
 }
 
@@ -896,6 +934,7 @@ k_residual(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
       st->inv_bnorm = 1.0 / nr;
     }
     st->rnorm = nr;
+    st->cycle_scale = 1.0;
     st->step = 0;
     st->inner = 0;
     st->kmax = kmax;
@@ -909,6 +948,23 @@ k_residual(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
     s.scale[0] = 1.0 / nr;
     for (int i = 1; i <= s.m + 1; ++i) s.g[i] = 0.0;
   }
+}
+
+// Start of an FP32 (GMRES-IR) cycle: column 0 of the FP32 basis = r / ||r||
+// rounded to FP32 (normalized in FP64 first, so the FP32 cycle works on a
+// unit-scale right-hand side); the estimate and the correction of this cycle
+// are scaled back by ||r||.
+__global__ void k_round_scaled(const double* __restrict__ r, float* __restrict__ out, int64_t n, Small s) {
+  const double rn = __ldcg(&s.st->rnorm);
+  const double ir = 1.0 / rn;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) out[i] = (float)(r[i] * ir);
+  if (blockIdx.x == 0 && threadIdx.x == 0) s.st->cycle_scale = rn;
+}
+
+__global__ void k_to_float(const double* __restrict__ a, float* __restrict__ out, int64_t n) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) out[i] = (float)a[i];
 }
 
 // Back substitution R(0:k,0:k) y = g(0:k) (column-oriented), then the
@@ -938,7 +994,8 @@ __global__ void k_lsq(Small s) {
     for (int l = threadIdx.x; l < i; l += blockDim.x) y[l] = fma(-sR[(size_t)i * ld + l], yi, y[l]);
     __syncthreads();
   }
-  for (int l = threadIdx.x; l < k; l += blockDim.x) s.coefx[1 + l] = y[l] * s.scale[l];
+  const double cs = st->cycle_scale;
+  for (int l = threadIdx.x; l < k; l += blockDim.x) s.coefx[1 + l] = y[l] * s.scale[l] * cs;
   if (threadIdx.x == 0) {
     s.coefx[0] = 1.0;
     st->total_iters += k;
@@ -984,22 +1041,24 @@ constexpr size_t kNoAllocBytes = kNoAllocStateBytes + sizeof(double) * (size_t)k
 static_assert(sizeof(DevState) <= kNoAllocStateBytes, "DevState outgrew its slot");
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
-using StepKernel = void (*)(const int32_t*, const int32_t*, const double*, const double*, int64_t,
-                            const double*, double*, int64_t, Small, int, int, double*);
+template <typename VT>
+using StepKernel = void (*)(const int32_t*, const int32_t*, const VT*, const VT*, int64_t, const VT*, VT*, int64_t,
+                            Small, int, int, double*);
 
 // MAXC = floor(m / 8) whole columns per warp (j <= m), at least 1.
-StepKernel step_kernel_for(int m) {
+template <typename VT>
+StepKernel<VT> step_kernel_for(int m) {
   switch (std::max(1, m / kWarps)) {
-    case 1: return k_one_reduce_step<1>;
-    case 2: return k_one_reduce_step<2>;
-    case 3: return k_one_reduce_step<3>;
-    case 4: return k_one_reduce_step<4>;
-    case 5: return k_one_reduce_step<5>;
-    case 6: return k_one_reduce_step<6>;
-    case 7: return k_one_reduce_step<7>;
-    case 8: return k_one_reduce_step<8>;
-    case 9: case 10: case 11: case 12: return k_one_reduce_step<12>;
-    default: return k_one_reduce_step<16>;
+    case 1: return k_one_reduce_step<1, VT>;
+    case 2: return k_one_reduce_step<2, VT>;
+    case 3: return k_one_reduce_step<3, VT>;
+    case 4: return k_one_reduce_step<4, VT>;
+    case 5: return k_one_reduce_step<5, VT>;
+    case 6: return k_one_reduce_step<6, VT>;
+    case 7: return k_one_reduce_step<7, VT>;
+    case 8: return k_one_reduce_step<8, VT>;
+    case 9: case 10: case 11: case 12: return k_one_reduce_step<12, VT>;
+    default: return k_one_reduce_step<16, VT>;
   }
 }
 
@@ -1029,7 +1088,14 @@ struct gmres_ctx {
   Small s{};
   DevState* h_st = nullptr;  // pinned mirror
   cudaStream_t stream = nullptr;
-  StepKernel step = nullptr;
+  StepKernel<double> step = nullptr;
+  StepKernel<float> step32 = nullptr;
+  // GMRES-IR (FP32 cycles): FP32 basis, SpMV result and matrix values, and the
+  // FP64 restart residual; allocated by gmres_set(GMRES_IR_FP32)
+  float* V32 = nullptr;
+  float* w32 = nullptr;
+  float* val32 = nullptr;
+  double* r64 = nullptr;
   size_t step_smem = 0;  // dynamic shared memory of the step kernel (T and scales)
   size_t lsq_smem = 0;   // dynamic shared memory of k_lsq (rotated Hessenberg)
   std::vector<double> hist;
@@ -1052,7 +1118,7 @@ struct gmres_ctx {
   // CUDA graphs of whole cycles (captured once per scheme, kmax and profiling
   // mode; used when the handle has a non-default stream)
   struct CycleGraph {
-    int ortho, kmax;
+    int ortho, prec, kmax;
     bool prof;
     cudaGraphExec_t exec;
     int64_t nlaunch;
@@ -1178,14 +1244,22 @@ gmres_status launch_cycle(gmres_ctx* h, int kmax) {
   if (h->ortho == GMRES_ONE_REDUCE_MGS) {
     for (int j = 0; j <= kmax; ++j) {
       int pr = prof_begin(h, 0, j, kmax);
-      h->step<<<P, kThreads, h->step_smem, h->stream>>>(h->rowptr, h->col, h->val, h->V, h->ldv, nullptr, h->w,
-                                                        h->n, h->s, 0, 1, nullptr);
+      if (h->prec == GMRES_IR_FP32)
+        h->step32<<<P, kThreads, h->step_smem, h->stream>>>(h->rowptr, h->col, h->val32, h->V32, h->ldv, nullptr,
+                                                            h->w32, h->n, h->s, 0, 1, nullptr);
+      else
+        h->step<<<P, kThreads, h->step_smem, h->stream>>>(h->rowptr, h->col, h->val, h->V, h->ldv, nullptr, h->w,
+                                                          h->n, h->s, 0, 1, nullptr);
       prof_end(h, pr);
       ++h->launches;
       if (j < kmax) {
         pr = prof_begin(h, 1, j, kmax);
-        k_maxpy<<<h->grid_stream + 1, kThreads, 0, h->stream>>>(h->V, h->ldv, h->w, nullptr, h->n, h->s,
-                                                                 MAXPY_ARNOLDI, 0);
+        if (h->prec == GMRES_IR_FP32)
+          k_maxpy<float, float, float><<<h->grid_stream + 1, kThreads, 0, h->stream>>>(
+              h->V32, h->ldv, h->w32, nullptr, h->n, h->s, MAXPY_ARNOLDI, 0);
+        else
+          k_maxpy<double, double, double><<<h->grid_stream + 1, kThreads, 0, h->stream>>>(
+              h->V, h->ldv, h->w, nullptr, h->n, h->s, MAXPY_ARNOLDI, 0);
         prof_end(h, pr);
         ++h->launches;
       }
@@ -1267,11 +1341,12 @@ gmres_status run_cycle(gmres_ctx* h, int kmax) {
   if (h->stream == nullptr || (h->prof_on && !h->graph_prof_ok)) return launch_cycle(h, kmax);
   gmres_ctx::CycleGraph* g = nullptr;
   for (auto& c : h->graphs)
-    if (c.ortho == h->ortho && c.kmax == kmax && c.prof == h->prof_on) g = &c;
+    if (c.ortho == h->ortho && c.prec == h->prec && c.kmax == kmax && c.prof == h->prof_on) g = &c;
   if (!g) {
     h->graphs.emplace_back();
     g = &h->graphs.back();
     g->ortho = h->ortho;
+    g->prec = h->prec;
     g->kmax = kmax;
     g->prof = h->prof_on;
     g->exec = nullptr;
@@ -1324,19 +1399,21 @@ gmres_status run_cycle(gmres_ctx* h, int kmax) {
 // values, 4-byte indices; a vector read once counts once).
 void alg_model(const gmres_ctx* h, const gmres_ctx::ProfRec& r, int kx, double* bytes, double* flops) {
   const double n = (double)h->n, nnz = (double)h->nnz;
-  const double csr = 4.0 * (n + 1) + 12.0 * nnz;
+  const bool f32 = h->prec == GMRES_IR_FP32;          // FP32 cycle: 4-byte vectors and values
+  const double vb = f32 ? 4.0 : 8.0;
+  const double csr = 4.0 * (n + 1) + (4.0 + (f32 && (r.cls == PC_STEP) ? 4.0 : 8.0)) * nnz;
   switch (r.cls) {
     case PC_STEP:
       if (r.j == r.i) {  // tail: u and V_j, no SpMV (r.i carries kmax)
-        *bytes = 8.0 * n * (r.j + 1);
+        *bytes = vb * n * (r.j + 1);
         *flops = 2.0 * n * (r.j + 1);
       } else {
-        *bytes = csr + 8.0 * n * (r.j + 2);  // u (gathered), j basis columns, w written
+        *bytes = csr + vb * n * (r.j + 2);  // u (gathered), j basis columns, w written
         *flops = 2.0 * nnz + 2.0 * n * (2.0 * r.j + 2.0);
       }
       break;
     case PC_MAXPY:  // w, j+1 columns read, one column written
-      *bytes = 8.0 * n * (r.j + 3);
+      *bytes = vb * n * (r.j + 3);
       *flops = 2.0 * n * (r.j + 1) + n;
       break;
     case PC_MGS_SPMV:  // u_i gathered, u_0 read, w written
@@ -1351,8 +1428,8 @@ void alg_model(const gmres_ctx* h, const gmres_ctx::ProfRec& r, int kx, double* 
       *bytes = (r.j == 0) ? 8.0 * n : csr + 24.0 * n;
       *flops = (r.j == 0) ? 2.0 * n : 2.0 * nnz + 3.0 * n;
       break;
-    case PC_XUPD:
-      *bytes = 8.0 * n * (kx + 2);
+    case PC_XUPD:  // x read and written (FP64), kx basis columns
+      *bytes = 16.0 * n + vb * n * kx;
       *flops = 2.0 * n * kx + n;
       break;
     default:
@@ -1475,10 +1552,13 @@ gmres_status gmres_create(const gmres_csr* A, int m_restart, double tol, gmres_h
   CREATE_TRY(cudaMallocHost(&h->h_st, sizeof(DevState)));
   std::memset(h->h_st, 0, sizeof(DevState));
   if (alloc_small(h) != GMRES_OK) return bail(GMRES_ERR_CUDA);
-  h->step = step_kernel_for(m_restart);
+  h->step = step_kernel_for<double>(m_restart);
+  h->step32 = step_kernel_for<float>(m_restart);
   h->step_smem = sizeof(double) * ((size_t)(m_restart + 1) * (m_restart + 1) + (m_restart + 1));
   h->lsq_smem = sizeof(double) * (size_t)(m_restart + 1) * m_restart;
   CREATE_TRY(cudaFuncSetAttribute(reinterpret_cast<const void*>(h->step),
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->step_smem));
+  CREATE_TRY(cudaFuncSetAttribute(reinterpret_cast<const void*>(h->step32),
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->step_smem));
   CREATE_TRY(cudaFuncSetAttribute(reinterpret_cast<const void*>(k_lsq),
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->lsq_smem));
@@ -1490,8 +1570,25 @@ gmres_status gmres_create(const gmres_csr* A, int m_restart, double tol, gmres_h
 gmres_status gmres_set(gmres_handle h, gmres_ortho ortho, gmres_prec prec, int max_iter) {
   if (!h) return GMRES_ERR_ARG;
   if (ortho != GMRES_MGS && ortho != GMRES_ONE_REDUCE_MGS) return fail(h, GMRES_ERR_ARG, "unknown ortho");
-  if (prec != GMRES_FP64) return fail(h, GMRES_ERR_ARG, "only GMRES_FP64 is implemented");
+  if (prec != GMRES_FP64 && prec != GMRES_IR_FP32)
+    return fail(h, GMRES_ERR_ARG, "precision must be GMRES_FP64 or GMRES_IR_FP32");
+  if (prec == GMRES_IR_FP32 && ortho != GMRES_ONE_REDUCE_MGS)
+    return fail(h, GMRES_ERR_ARG, "GMRES_IR_FP32 runs the one-reduce scheme only");
   if (max_iter < 0) return fail(h, GMRES_ERR_ARG, "max_iter < 0");
+  if (prec == GMRES_IR_FP32 && !h->V32) {  // FP32 copies for the inner cycles
+    CUDA_TRY(h, cudaSetDevice(h->device));
+    const int64_t nnz_pad = (int64_t)align_up((size_t)std::max<int64_t>(h->nnz, 1), 4);
+    CUDA_TRY(h, cudaMalloc(&h->V32, sizeof(float) * (size_t)h->ldv * (h->m + 1)));
+    CUDA_TRY(h, cudaMemset(h->V32, 0, sizeof(float) * (size_t)h->ldv * (h->m + 1)));
+    CUDA_TRY(h, cudaMalloc(&h->w32, sizeof(float) * (size_t)h->ldv));
+    CUDA_TRY(h, cudaMemset(h->w32, 0, sizeof(float) * (size_t)h->ldv));
+    CUDA_TRY(h, cudaMalloc(&h->val32, sizeof(float) * (size_t)nnz_pad));
+    CUDA_TRY(h, cudaMemset(h->val32, 0, sizeof(float) * (size_t)nnz_pad));
+    CUDA_TRY(h, cudaMalloc(&h->r64, sizeof(double) * (size_t)h->ldv));
+    k_to_float<<<h->grid_stream, kThreads>>>(h->val, h->val32, h->nnz);
+    LAUNCH_CHECK(h);
+    CUDA_TRY(h, cudaDeviceSynchronize());
+  }
   h->ortho = ortho;
   h->prec = prec;
   if (max_iter != h->max_iter) {
@@ -1549,7 +1646,9 @@ gmres_status gmres_solve(gmres_handle h, const double* b, double* x, gmres_info*
     int prev_total = 0;
     for (;;) {
       pr = prof_begin(h, PC_RES, 1, 0);
-      k_residual<<<P, kThreads, 0, h->stream>>>(h->rowptr, h->col, h->val, b, x, h->V, h->n, h->s, RES_RESIDUAL, 0);
+      k_residual<<<P, kThreads, 0, h->stream>>>(h->rowptr, h->col, h->val, b, x,
+                                                 h->prec == GMRES_IR_FP32 ? h->r64 : h->V, h->n, h->s,
+                                                 RES_RESIDUAL, 0);
       prof_end(h, pr);
       ++h->launches;
       LAUNCH_CHECK(h);
@@ -1574,12 +1673,22 @@ gmres_status gmres_solve(gmres_handle h, const double* b, double* x, gmres_info*
       h->h_st->kmax = kmax;
       // only kmax changes on the host side; write it without touching the rest
       CUDA_TRY(h, cudaMemcpyAsync(&h->s.st->kmax, &h->h_st->kmax, sizeof(int), cudaMemcpyHostToDevice, h->stream));
+      if (h->prec == GMRES_IR_FP32) {
+        k_round_scaled<<<h->grid_stream, kThreads, 0, h->stream>>>(h->r64, h->V32, h->n, h->s);
+        ++h->launches;
+        LAUNCH_CHECK(h);
+      }
       if ((st = run_cycle(h, kmax)) != GMRES_OK) return st;
       pr = prof_begin(h, PC_LSQ, 0, 0);
       k_lsq<<<1, 128, h->lsq_smem, h->stream>>>(h->s);
       prof_end(h, pr);
       pr = prof_begin(h, PC_XUPD, 0, 0);
-      k_maxpy<<<h->grid_stream, kThreads, 0, h->stream>>>(h->V, h->ldv, x, x, h->n, h->s, MAXPY_XUPDATE, 0);
+      if (h->prec == GMRES_IR_FP32)
+        k_maxpy<float, double, double><<<h->grid_stream, kThreads, 0, h->stream>>>(h->V32, h->ldv, x, x, h->n, h->s,
+                                                                                  MAXPY_XUPDATE, 0);
+      else
+        k_maxpy<double, double, double><<<h->grid_stream, kThreads, 0, h->stream>>>(h->V, h->ldv, x, x, h->n, h->s,
+                                                                                   MAXPY_XUPDATE, 0);
       prof_end(h, pr);
       h->launches += 2;
       LAUNCH_CHECK(h);
@@ -1640,6 +1749,10 @@ gmres_status gmres_destroy(gmres_handle h) {
   cudaFree(h->small);
   cudaFree(h->d_b);
   cudaFree(h->d_x);
+  cudaFree(h->V32);
+  cudaFree(h->w32);
+  cudaFree(h->val32);
+  cudaFree(h->r64);
   if (h->h_st) cudaFreeHost(h->h_st);
   for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
   destroy_graphs(h);
@@ -1700,7 +1813,8 @@ gmres_status lsg_maxpy(gmres_handle h, const double* V, int64_t ldv, int K, cons
   cf[0] = alpha;
   for (int k = 0; k < K; ++k) cf[1 + k] = c[k];
   CUDA_TRY(h, cudaMemcpyAsync(h->s.coef, cf.data(), sizeof(double) * (K + 1), cudaMemcpyHostToDevice, h->stream));
-  k_maxpy<<<h->grid_stream, kThreads, 0, h->stream>>>(V, ldv, y_in, y_out, h->n, h->s, MAXPY_STANDALONE, K);
+  k_maxpy<double, double, double><<<h->grid_stream, kThreads, 0, h->stream>>>(V, ldv, y_in, y_out, h->n, h->s,
+                                                                               MAXPY_STANDALONE, K);
   LAUNCH_CHECK(h);
   CUDA_TRY(h, cudaStreamSynchronize(h->stream));
   return GMRES_OK;
@@ -1748,7 +1862,7 @@ gmres_status lsg_block_dot_noalloc(const int32_t* rowptr, const int32_t* col, co
   // the ticket must start at zero; a memset allocates nothing
   cudaError_t e = cudaMemsetAsync(scratch, 0, sizeof(DevState), stream);
   if (e != cudaSuccess) return fail(nullptr, GMRES_ERR_CUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
-  k_one_reduce_step<kNoAllocMaxJ / kWarps><<<P, kThreads, 0, stream>>>(rowptr, col, val, V, ldv, u, w, n, sm, j,
+  k_one_reduce_step<kNoAllocMaxJ / kWarps, double><<<P, kThreads, 0, stream>>>(rowptr, col, val, V, ldv, u, w, n, sm, j,
                                                                       use_spmv, X);
   e = cudaGetLastError();
   if (e != cudaSuccess) return fail(nullptr, GMRES_ERR_CUDA, std::string("launch: ") + cudaGetErrorString(e));
@@ -1761,6 +1875,7 @@ gmres_status gmres_arnoldi(gmres_handle h, const double* r0, int k, double* V_ou
   gmres_status st;
   if ((st = check_ptr(h, r0, "r0")) != GMRES_OK) return st;
   if (k < 1 || k > h->m) return fail(h, GMRES_ERR_ARG, "k must be in [1, m]");
+  if (h->prec != GMRES_FP64) return fail(h, GMRES_ERR_ARG, "gmres_arnoldi runs the FP64 cycle only");
   CUDA_TRY(h, cudaSetDevice(h->device));
   std::memset(h->h_st, 0, sizeof(DevState));
   h->h_st->tol = 0.0;

@@ -21,6 +21,7 @@ ERR_ARG, ERR_CUDA, ERR_NONFINITE, ERR_OOM, ERR_TIMEOUT = -1, -2, -3, -4, -5
 MGS, ONE_REDUCE_MGS = 0, 1
 FP64, IR_FP32, IR_BF16 = 0, 1, 2
 ORTHO = {"mgs": MGS, "one_reduce_mgs": ONE_REDUCE_MGS, "one_reduce": ONE_REDUCE_MGS}
+PREC = {"fp64": FP64, "ir_fp32": IR_FP32, "ir_bf16": IR_BF16}
 STATUS_NAMES = {0: "OK", 1: "MAXITER", 2: "BREAKDOWN_EXACT", -1: "ERR_ARG", -2: "ERR_CUDA",
                 -3: "ERR_NONFINITE", -4: "ERR_OOM", -5: "ERR_TIMEOUT"}
 
@@ -126,7 +127,7 @@ class Solver:
     """Restarted GMRES(m) on one GPU through the C ABI (gmres_create/solve/...)."""
 
     def __init__(self, A, m: int, tol: float, *, ortho: str = "one_reduce_mgs", max_iter: int | None = None,
-                 stream=None):
+                 stream=None, prec: str | int = "fp64"):
         lib = load()
         self.lib = lib
         rowptr, col, val = A
@@ -144,7 +145,7 @@ class Solver:
         if st != OK:
             raise GmresError(st, lib.gmres_last_error(None).decode())
         self.h = h
-        self.set(ortho=ortho, max_iter=max_iter if max_iter is not None else 10 * m)
+        self.set(ortho=ortho, max_iter=max_iter if max_iter is not None else 10 * m, prec=prec)
         if stream is not None:
             self.set_stream(stream)
 
@@ -153,10 +154,11 @@ class Solver:
             raise GmresError(st, self.lib.gmres_last_error(self.h).decode())
         return st
 
-    def set(self, *, ortho: str | int = "one_reduce_mgs", prec: int = FP64, max_iter: int = 300):
+    def set(self, *, ortho: str | int = "one_reduce_mgs", prec: str | int = FP64, max_iter: int = 300):
         o = ORTHO[ortho] if isinstance(ortho, str) else int(ortho)
-        self._check(self.lib.gmres_set(self.h, o, prec, max_iter))
-        self.ortho, self.max_iter = o, max_iter
+        pr = PREC[prec] if isinstance(prec, str) else int(prec)
+        self._check(self.lib.gmres_set(self.h, o, pr, max_iter))
+        self.ortho, self.prec, self.max_iter = o, pr, max_iter
 
     def set_tol(self, tol: float):
         self._check(self.lib.gmres_set_tol(self.h, tol))
