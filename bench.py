@@ -37,6 +37,7 @@ WORKLOADS = {
     32: dict(N=32, m=30, tol=1e-8, max_iter=300, stencil="7pt", prec="fp64", compare="mgs"),
     # 27-point anisotropic diffusion, GMRES-IR (FP32 cycles) against FP64 one-reduce
     192: dict(N=192, m=40, tol=1e-10, max_iter=5000, stencil="27pt", prec="ir_fp32", compare="fp64"),
+    144: dict(N=144, m=40, tol=1e-10, max_iter=5000, stencil="27pt", prec="ir_fp32", compare="fp64"),  # profiling
 }
 METRIC = "time-to-solve (1e-8 rel. resid), one-reduce MGS-GMRES"
 METRIC_IR = "time-to-solve (1e-10 rel. resid), GMRES-IR: one-reduce cycles in FP32, FP64 restarts"
