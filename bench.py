@@ -7,7 +7,14 @@ x_true ~ U[-1, 1] from PCG64(0), b = A x_true, x0 = 0. One step is one
 complete solve (every Arnoldi step, restart and solution update on the GPU).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload 256|32] [--no-mgs] [--no-cpu-baseline]
+                  [--workload 256|128|32|192|144|batch512|batch64] [--no-mgs]
+                  [--no-cpu-baseline]
+
+--workload batch512: 512 independent 2D 9-point variable-coefficient
+convection-diffusion systems (grid side log-uniform in 32..256, cell diffusion
+log-uniform in [0.1, 10], cell Peclet U[0, 2], seeded), GMRES(30) to 1e-8, all
+solved together by the batched solver against the same systems solved one
+after another.
 
 Prints one JSON line (rank 0). With N > 1 (torchrun) every rank solves its own
 replica of the system (no data-path collective); the time is the maximum
@@ -39,6 +46,13 @@ WORKLOADS = {
     192: dict(N=192, m=40, tol=1e-10, max_iter=5000, stencil="27pt", prec="ir_fp32", compare="fp64"),
     144: dict(N=144, m=40, tol=1e-10, max_iter=5000, stencil="27pt", prec="ir_fp32", compare="fp64"),  # profiling
 }
+# batched uneven solves: 2D 9-point variable-coefficient convection-diffusion
+# systems, grid side log-uniform in `side`, all solved together
+BATCH_WORKLOADS = {
+    "batch512": dict(count=512, side=(32, 256), m=30, tol=1e-8, max_iter=20000, seed=0),
+    "batch64": dict(count=64, side=(32, 256), m=30, tol=1e-8, max_iter=20000, seed=0),  # profiling size
+}
+METRIC_BATCH = "time-to-solve (1e-8 rel. resid) of a batch of uneven systems, batched one-reduce MGS-GMRES"
 METRIC = "time-to-solve (1e-8 rel. resid), one-reduce MGS-GMRES"
 METRIC_IR = "time-to-solve (1e-10 rel. resid), GMRES-IR: one-reduce cycles in FP32, FP64 restarts"
 
@@ -415,17 +429,257 @@ def run_ours(args, w, rank, world, dist):
     return 0
 
 
+# ----------------------------------------------------------------------------- batched workload
+def batch_problem(w):
+    pars = P.batch_2d_params(w["count"], seed=w["seed"], side=w["side"])
+    mats, rhs = [], []
+    for i, par in enumerate(pars):
+        A = P.batch_2d_system(par)
+        mats.append(A)
+        rhs.append(P.rhs(A, seed=i)[1])
+    return pars, mats, rhs
+
+
+def batch_workload_name(w, mats):
+    n = sum(len(A[0]) - 1 for A in mats)
+    nnz = sum(len(A[1]) for A in mats)
+    return (f"{w['count']} independent 2D 9-point variable-coefficient convection-diffusion systems, grid side "
+            f"log-uniform {w['side'][0]}..{w['side'][1]} (total n={n}, nnz={nnz}), kappa log-uniform [0.1,10], "
+            f"cell Peclet U[0,2], FP64 CSR, batched one-reduce GMRES({w['m']}) vs the same systems solved one "
+            f"after another, tol {w['tol']:g}, x0=0")
+
+
+def batch_cpu_baseline(mats, rhs, w, iters, budget_s=20.0):
+    """Time the FP64 oracle (1 thread) on complete solves of a sample of the
+    systems (every 16th, in order, until `budget_s`), scaled to the whole batch
+    by the ratio of sum(n_i * iters_i) over all systems to that over the sample."""
+    from oracle import Oracle
+
+    orc = Oracle()
+    t_tot, work_s, names = 0.0, 0.0, []
+    for i in range(0, len(mats), 16):
+        t0 = time.perf_counter()
+        r = orc.gmres(mats[i], rhs[i], variant=1, m=w["m"], tol=w["tol"], max_iter=w["max_iter"])
+        t_tot += time.perf_counter() - t0
+        work_s += (len(mats[i][0]) - 1) * r.iters
+        names.append(i)
+        if t_tot >= budget_s:
+            break
+    work_all = sum((len(A[0]) - 1) * k for A, k in zip(mats, iters))
+    v = t_tot * work_all / work_s
+    return {"value": v, "unit": "s", "cores": 1, "kind": "oracle",
+            "sample": f"complete oracle solves of {len(names)} of the {len(mats)} systems (every 16th), "
+                      f"{t_tot:.1f} s, scaled by sum(n_i * iters_i) over all systems / over the sample"}
+
+
+def run_batch_reference(args, w, rank):
+    if rank != 0:
+        return 0
+    _, mats, rhs = batch_problem(w)
+    from oracle import Oracle
+
+    orc = Oracle()
+    # every 32nd system per step (sizes are drawn independently, so the sample
+    # is representative), scaled to the batch by total n / sample n
+    vals = []
+    for s in range(args.warmup + args.steps):
+        t_tot, work_s, cnt = 0.0, 0.0, 0
+        for i in range(0, len(mats), 32):
+            t0 = time.perf_counter()
+            r = orc.gmres(mats[i], rhs[i], variant=1, m=w["m"], tol=w["tol"], max_iter=w["max_iter"])
+            t_tot += time.perf_counter() - t0
+            work_s += len(mats[i][0]) - 1
+            cnt += 1
+            if t_tot >= 8.0:
+                break
+        v = t_tot * sum(len(A[0]) - 1 for A in mats) / work_s
+        if s >= args.warmup:
+            vals.append(v)
+    v = float(np.mean(vals))
+    line = {
+        "impl": "reference", "metric": METRIC_BATCH, "value": v, "unit": "s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * v, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": batch_workload_name(w, mats), "m": w["m"], "tol": w["tol"]},
+        "cpu_baseline": {"value": v, "unit": "s", "cores": 1, "kind": "oracle",
+                         "sample": f"complete oracle solves of {cnt} systems (every 32nd) per step, scaled by "
+                                   f"total n / sample n"},
+        "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def run_batch(args, w, rank, world, dist):
+    import torch
+
+    from paper_1809_05805_b300 import lsgmres
+
+    lsgmres.load()  # fails loudly when the CUDA library is missing
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream()
+    pars, mats, rhs = batch_problem(w)
+    S = len(mats)
+    ntot = sum(len(A[0]) - 1 for A in mats)
+    peaks = load_peaks()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(v):
+        if dist is None:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    t0 = time.perf_counter()
+    bs = lsgmres.BatchSolver(mats, m=w["m"], tol=w["tol"], max_iter=w["max_iter"], stream=stream)
+    create_s = time.perf_counter() - t0
+    bd = [torch.from_numpy(b).cuda() for b in rhs]
+    xd = [torch.zeros(len(b), dtype=torch.float64, device="cuda") for b in rhs]
+    bs.set_profile(True)
+
+    def one_solve():
+        with torch.cuda.stream(stream):
+            for x in xd:
+                x.zero_()
+        return bs.solve(bd, xd)
+
+    for _ in range(args.warmup):
+        one_solve()
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    ms, prof, launches = 0.0, None, 0
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            torch.cuda.synchronize()
+            e0.record(stream)
+            infos = one_solve()
+            e1.record(stream)
+            e1.synchronize()
+            ms += e0.elapsed_time(e1)
+            launches += infos[0].kernel_launches
+            p = bs.profile()
+            if prof is None:
+                prof = p
+            else:
+                for k in prof:
+                    for f in prof[k]:
+                        prof[k][f] += p[k][f]
+        barrier()
+    clocks = clk.summary()
+    ms = max_over_ranks(ms / args.steps)
+    xs = [x.cpu().numpy() for x in xd]
+    true_rel = [float(np.linalg.norm(b - P.to_scipy(A) @ x) / np.linalg.norm(b)) for A, b, x in zip(mats, rhs, xs)]
+    iters = [i.iters for i in infos]
+
+    # the comparison leg: the same systems solved one after another by the
+    # single-system solver (same kernels, graphs on the same stream)
+    seq = None
+    if not args.no_mgs:
+        seq_ms, seq_iters = 0.0, []
+        for A, b in zip(mats, bd):
+            s1 = lsgmres.Solver(A, m=w["m"], tol=w["tol"], ortho="one_reduce_mgs", max_iter=w["max_iter"],
+                                stream=stream)
+            x1 = torch.zeros(len(b), dtype=torch.float64, device="cuda")
+            s1.solve(b, x1)  # captures its graphs
+            x1.zero_()
+            torch.cuda.synchronize()
+            e0.record(stream)
+            inf1 = s1.solve(b, x1)
+            e1.record(stream)
+            e1.synchronize()
+            seq_ms += e0.elapsed_time(e1)
+            seq_iters.append(inf1.iters)
+            s1.close()
+        seq = {"time_to_solve_s": seq_ms / 1e3, "iters_equal_to_batched": int(sum(a == b for a, b in
+                                                                                 zip(seq_iters, iters))),
+               "systems": S}
+
+    # end to end through the host-buffer entry point (copies inside the call)
+    bh = [torch.from_numpy(b).pin_memory().numpy() for b in rhs]
+    xh = [torch.zeros(len(b), dtype=torch.float64).pin_memory().numpy() for b in rhs]
+    bs.set_profile(False)
+    bs.solve_host(bh, xh)
+    e2e_steps = max(1, min(args.steps, 2))
+    e2e_ms = 0.0
+    for _ in range(e2e_steps):
+        for x in xh:
+            x[:] = 0.0
+        t0 = time.perf_counter()
+        bs.solve_host(bh, xh)
+        e2e_ms += (time.perf_counter() - t0) * 1e3
+    e2e_ms = max_over_ranks(e2e_ms / e2e_steps)
+
+    st = prof["one_reduce_step"]
+    mx = prof["arnoldi_maxpy"]
+    fp64_peak = 148 * FP64_DFMA_PER_CLK_SM * 2 * float(peaks.get("sm_max_mhz", 2032.0)) * 1e6 / 1e12
+    hbm = float(peaks.get("hbm_gbs", 6400.0))
+    step_tflops = st["flops"] / (st["ms"] * 1e-3) / 1e12 if st["ms"] else None
+    step_gbs = st["bytes"] / (st["ms"] * 1e-3) / 1e9 if st["ms"] else None
+    roofline = {
+        "kernel": "kb_step (batched fused CSR SpMV + block dot + per-system epilogue)",
+        "bound": "alu", "achieved": step_tflops, "peak": fp64_peak, "unit": "TFLOP/s",
+        "frac": step_tflops / fp64_peak if step_tflops else None,
+        "peak_source": (f"FP64 pipe derived from unit counts and clock: 148 SMs x {FP64_DFMA_PER_CLK_SM} DFMA/clk x 2 "
+                        f"flop x {peaks.get('sm_max_mhz', 2032.0):g} MHz (nominal 1.25 TFLOP/s)"),
+        "traffic": None,
+        "launch_avg_ms": st["ms"] / max(st["launches"], 1), "launches": st["launches"],
+        "alg_flops_per_launch": st["flops"] / max(st["launches"], 1),
+        "alg_bytes_per_launch": st["bytes"] / max(st["launches"], 1),
+        "hbm_gbs": step_gbs, "hbm_frac_of_measured": step_gbs / hbm if step_gbs else None,
+        "noop_launches": prof["noop"]["launches"],
+        "maxpy": {"launch_avg_ms": mx["ms"] / max(mx["launches"], 1),
+                  "tflops": mx["flops"] / (mx["ms"] * 1e-3) / 1e12 if mx["ms"] else None,
+                  "hbm_gbs": mx["bytes"] / (mx["ms"] * 1e-3) / 1e9 if mx["ms"] else None},
+    }
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = batch_cpu_baseline(mats, rhs, w, iters)
+    line = {
+        "metric": METRIC_BATCH, "value": ms / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded 2D stencils, x_true ~ U[-1,1])",
+        "config": {"workload": batch_workload_name(w, mats), "systems": S, "n_total": ntot, "m": w["m"],
+                   "tol": w["tol"], "grid_ctas": bs.grid, "create_s": create_s,
+                   "parallelism": "replicas" if world > 1 else "1 GPU",
+                   "l2": "inputs larger than L2 (batch Krylov basis %.1f GB >> 126 MB), no flush"
+                         % (8 * ntot * (w["m"] + 1) / 1e9)},
+        "iters_max": max(iters), "iters_median": float(np.median(iters)),
+        "all_converged": all(i.status == 0 for i in infos), "max_rel_resid_true": max(true_rel),
+        "solves_per_s": world * S / (ms / 1e3),
+        "sequential": seq,
+        "speedup_vs_sequential": (seq["time_to_solve_s"] / (ms / 1e3)) if seq else None,
+        "e2e": {"value": e2e_ms / 1e3, "unit": "s", "h2d_bytes_per_step": 16 * ntot, "d2h_bytes_per_step": 8 * ntot},
+        "gpu_launches": int(launches),
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "clocks": clocks,
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    bs.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", type=int, choices=sorted(WORKLOADS), default=256)
+    ap.add_argument("--workload", choices=[str(k) for k in sorted(WORKLOADS)] + sorted(BATCH_WORKLOADS),
+                    default="256")
     ap.add_argument("--no-mgs", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
-    w = WORKLOADS[args.workload]
+    batch = args.workload in BATCH_WORKLOADS
+    w = BATCH_WORKLOADS[args.workload] if batch else WORKLOADS[int(args.workload)]
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     dist = None
@@ -441,6 +695,10 @@ def main():
             dist_mod.init_process_group("nccl")
             dist = dist_mod
     try:
+        if batch:
+            if args.impl == "reference":
+                return run_batch_reference(args, w, rank)
+            return run_batch(args, w, rank, world, dist)
         if args.impl == "reference":
             return run_reference(args, w, rank, world)
         return run_ours(args, w, rank, world, dist)

@@ -156,6 +156,74 @@ gmres_status gmres_profile(gmres_handle h, int cls, double* total_ms, int64_t* l
                            double* alg_bytes, double* alg_flops);
 
 /* ------------------------------------------------------------------------
+ * Batched solves: many independent systems, one launch per Arnoldi step.
+ * ------------------------------------------------------------------------
+ * The paper defines the method for one system (Algorithm 7, Sections III-IV);
+ * batching is this library's addition and changes no system's arithmetic.
+ * A batch holds `count` square CSR systems of any sizes. Its solve runs
+ * restarted one-reduce MGS-GMRES(m) (FP64) on all of them in lock-step cycles:
+ * the systems' rows are concatenated (each padded to whole 256-row tiles) into
+ * one block-diagonal matrix and one Krylov basis, and each Arnoldi step of the
+ * cycle is one fused SpMV + block-inner-product launch and one MAXPY launch
+ * for every system still iterating, with a separate grid reduction and
+ * epilogue per system. A system leaves its cycle when its own residual
+ * estimate reaches tol and the batch when its true residual does (or after
+ * max_iter steps); results equal those of solving each system alone. The
+ * grid size of the batched kernels is chosen by a timing autotuner at create.
+ */
+typedef struct gmres_batch_ctx* gmres_batch;
+
+/* Create a batch from `count` >= 1 host CSR matrices (A[i].on_device must be
+ * 0; the arrays are copied), restart length 1 <= m <= 128, tol >= 0,
+ * max_iter >= 0 steps per system. Errors: GMRES_ERR_ARG, GMRES_ERR_OOM,
+ * GMRES_ERR_CUDA (details in gmres_batch_last_error(NULL)). */
+gmres_status gmres_batch_create(const gmres_csr* A, int count, int m_restart, double tol, int max_iter,
+                                gmres_batch* out);
+
+/* Order the batch's work on cuda_stream (cudaStream_t; NULL = legacy default;
+ * a non-default stream lets each cycle run as a replayed CUDA graph). */
+gmres_status gmres_batch_set_stream(gmres_batch bt, void* cuda_stream);
+
+/* Grid of the batched reduction kernels (CTAs; CTA c takes the contiguous
+ * range of 256-row tiles [c T / ctas, (c+1) T / ctas) of the T tiles of the
+ * batch). ctas = 0 re-runs the autotuner; otherwise 1 <= ctas <= min(T, 8 x
+ * the SM count), else GMRES_ERR_ARG. Results are deterministic for a given
+ * grid; the grid changes only the order of the partial sums. */
+gmres_status gmres_batch_set_grid(gmres_batch bt, int ctas);
+gmres_status gmres_batch_get_grid(gmres_batch bt, int* ctas);
+
+/* Solve all systems: b[i] and x[i] are device pointers (host array of `count`
+ * pointers) to system i's right-hand side and its x0 / solution. info may be
+ * NULL or a host array of `count` entries (per system). Returns GMRES_OK if
+ * every system converged, GMRES_MAXITER if some hit max_iter, or the first
+ * error. Errors: GMRES_ERR_ARG (NULL arrays, a NULL or not 8-byte-aligned
+ * pointer), GMRES_ERR_CUDA; a system whose b or x0 holds NaN/Inf reports
+ * GMRES_ERR_NONFINITE in its info entry while the others are solved.
+ * The b[i] are read-only; each x[i] is written once, at the end. Synchronizes
+ * the stream. */
+gmres_status gmres_batch_solve(gmres_batch bt, const double* const* b, double* const* x, gmres_info* info);
+
+/* As gmres_batch_solve with b[i] and x[i] in host memory (pinned or
+ * pageable): the copies into and out of the device are part of the call. */
+gmres_status gmres_batch_solve_host(gmres_batch bt, const double* const* b_host, double* const* x_host,
+                                    gmres_info* info);
+
+/* Per-launch timing of batch solves (as gmres_set_profile / gmres_profile;
+ * classes 0, 1, 4, 5, 6 and 7 occur). Each launch's algorithmic bytes and
+ * flops are summed over the systems it did work for. */
+gmres_status gmres_batch_set_profile(gmres_batch bt, int on);
+gmres_status gmres_batch_profile(gmres_batch bt, int cls, double* total_ms, int64_t* launches,
+                                 double* alg_bytes, double* alg_flops);
+
+/* Residual-estimate history of system i in the last batch solve (as gmres_history). */
+gmres_status gmres_batch_history(gmres_batch bt, int i, double* host_buf, int cap, int* len);
+
+gmres_status gmres_batch_destroy(gmres_batch bt);
+
+/* Description of the last error on bt (or of the last failed gmres_batch_create when NULL). */
+const char* gmres_batch_last_error(gmres_batch bt);
+
+/* ------------------------------------------------------------------------
  * Single steps of the solve path, exposed for parity tests.
  * ------------------------------------------------------------------------ */
 

@@ -62,7 +62,9 @@ class SolveInfo:
 EXPORTS = ["gmres_create", "gmres_set", "gmres_set_tol", "gmres_set_stream", "gmres_solve",
            "gmres_solve_host", "gmres_history", "gmres_destroy", "gmres_last_error", "lsg_spmv",
            "lsg_block_dot", "lsg_maxpy", "gmres_arnoldi", "gmres_set_profile", "gmres_profile",
-           "lsg_block_dot_noalloc"]
+           "lsg_block_dot_noalloc", "gmres_batch_create", "gmres_batch_set_grid", "gmres_batch_get_grid", "gmres_batch_set_stream", "gmres_batch_solve",
+           "gmres_batch_solve_host", "gmres_batch_set_profile", "gmres_batch_profile",
+           "gmres_batch_history", "gmres_batch_destroy", "gmres_batch_last_error"]
 
 PROFILE_CLASSES = ["one_reduce_step", "arnoldi_maxpy", "mgs_spmv_dot", "mgs_axpy_dot", "residual",
                    "least_squares", "x_update", "noop"]
@@ -97,6 +99,18 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "lsg_block_dot_noalloc": ([P, P, P, I64, P, I64, I, P, P, I, P, P], I),
         "gmres_profile": ([P, I, ctypes.POINTER(D), ctypes.POINTER(I64), ctypes.POINTER(D),
                            ctypes.POINTER(D)], I),
+        "gmres_batch_create": ([ctypes.POINTER(_Csr), I, I, D, I, ctypes.POINTER(P)], I),
+        "gmres_batch_set_stream": ([P, P], I),
+        "gmres_batch_set_grid": ([P, I], I),
+        "gmres_batch_get_grid": ([P, ctypes.POINTER(I)], I),
+        "gmres_batch_solve": ([P, P, P, ctypes.POINTER(_Info)], I),
+        "gmres_batch_history": ([P, I, P, I, ctypes.POINTER(I)], I),
+        "gmres_batch_solve_host": ([P, P, P, ctypes.POINTER(_Info)], I),
+        "gmres_batch_set_profile": ([P, I], I),
+        "gmres_batch_profile": ([P, I, ctypes.POINTER(D), ctypes.POINTER(I64), ctypes.POINTER(D),
+                                 ctypes.POINTER(D)], I),
+        "gmres_batch_destroy": ([P], I),
+        "gmres_batch_last_error": ([P], ctypes.c_char_p),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -251,6 +265,113 @@ def block_dot_noalloc(A_dev, n: int, V, ldv: int, j: int, u, w, X, use_spmv: boo
                                    int(use_spmv), _ptr(X), None if stream is None else int(stream.cuda_stream))
     if st != OK:
         raise GmresError(st, lib.gmres_last_error(None).decode())
+
+
+class BatchSolver:
+    """Many independent systems solved together (gmres_batch_*): one-reduce
+    MGS-GMRES(m) in FP64, lock-step cycles, one launch per Arnoldi step."""
+
+    def __init__(self, mats, m: int, tol: float, *, max_iter: int | None = None, stream=None):
+        lib = load()
+        self.lib = lib
+        self._keep = []
+        csrs = (_Csr * len(mats))()
+        self.n = []
+        for i, (rowptr, col, val) in enumerate(mats):
+            rowptr = np.ascontiguousarray(rowptr, dtype=np.int32)
+            col = np.ascontiguousarray(col, dtype=np.int32)
+            val = np.ascontiguousarray(val, dtype=np.float64)
+            self._keep += [rowptr, col, val]
+            n = len(rowptr) - 1
+            csrs[i] = _Csr(n, len(col), _ptr(rowptr), _ptr(col), _ptr(val), 0)
+            self.n.append(n)
+        self.count, self.m = len(mats), m
+        self.max_iter = max_iter if max_iter is not None else 10 * m
+        h = ctypes.c_void_p()
+        st = lib.gmres_batch_create(csrs, len(mats), m, tol, self.max_iter, ctypes.byref(h))
+        self._keep = None
+        if st != OK:
+            raise GmresError(st, lib.gmres_batch_last_error(None).decode())
+        self.h = h
+        if stream is not None:
+            self.set_stream(stream)
+
+    def _check(self, st: int, allow=(OK,)):
+        if st not in allow:
+            raise GmresError(st, self.lib.gmres_batch_last_error(self.h).decode())
+        return st
+
+    def set_stream(self, stream):
+        self._check(self.lib.gmres_batch_set_stream(self.h, ctypes.c_void_p(int(stream.cuda_stream))))
+
+    @property
+    def grid(self) -> int:
+        g = ctypes.c_int(0)
+        self._check(self.lib.gmres_batch_get_grid(self.h, ctypes.byref(g)))
+        return g.value
+
+    def set_grid(self, ctas: int):
+        """Pin the grid of the batched kernels (0: autotune again)."""
+        self._check(self.lib.gmres_batch_set_grid(self.h, int(ctas)))
+
+    def solve(self, bs, xs, *, allow=(OK, MAXITER)) -> list[SolveInfo]:
+        """bs, xs: lists of float64 CUDA tensors (xs hold x0 on entry, solutions on exit)."""
+        if len(bs) != self.count or len(xs) != self.count:
+            raise ValueError(f"need {self.count} right-hand sides and solution vectors")
+        for i in range(self.count):
+            _dev_f64(bs[i], self.n[i], f"b[{i}]")
+            _dev_f64(xs[i], self.n[i], f"x[{i}]")
+        bp = (ctypes.c_void_p * self.count)(*[_ptr(t) for t in bs])
+        xp = (ctypes.c_void_p * self.count)(*[_ptr(t) for t in xs])
+        infos = (_Info * self.count)()
+        self._check(self.lib.gmres_batch_solve(self.h, bp, xp, infos), allow)
+        return [_info(i) for i in infos]
+
+    def solve_host(self, bs, xs, *, allow=(OK, MAXITER)) -> list[SolveInfo]:
+        """bs, xs: lists of float64 numpy arrays (host; pinned for speed); x holds x0 on entry."""
+        if len(bs) != self.count or len(xs) != self.count:
+            raise ValueError(f"need {self.count} right-hand sides and solution vectors")
+        for i in range(self.count):
+            for a, nm in ((bs[i], "b"), (xs[i], "x")):
+                if not (isinstance(a, np.ndarray) and a.dtype == np.float64 and a.flags.c_contiguous
+                        and a.size >= self.n[i]):
+                    raise TypeError(f"{nm}[{i}] must be a contiguous float64 numpy array of {self.n[i]} entries")
+        bp = (ctypes.c_void_p * self.count)(*[_ptr(a) for a in bs])
+        xp = (ctypes.c_void_p * self.count)(*[_ptr(a) for a in xs])
+        infos = (_Info * self.count)()
+        self._check(self.lib.gmres_batch_solve_host(self.h, bp, xp, infos), allow)
+        return [_info(i) for i in infos]
+
+    def set_profile(self, on: bool):
+        self._check(self.lib.gmres_batch_set_profile(self.h, int(on)))
+
+    def profile(self) -> dict:
+        """Per kernel class of the last batch solve: device ms, launches, algorithmic bytes and flops."""
+        out = {}
+        for c, name in enumerate(PROFILE_CLASSES):
+            ms, cnt, by, fl = ctypes.c_double(), ctypes.c_int64(), ctypes.c_double(), ctypes.c_double()
+            self._check(self.lib.gmres_batch_profile(self.h, c, ctypes.byref(ms), ctypes.byref(cnt), ctypes.byref(by),
+                                                     ctypes.byref(fl)))
+            out[name] = dict(ms=ms.value, launches=cnt.value, bytes=by.value, flops=fl.value)
+        return out
+
+    def history(self, i: int) -> np.ndarray:
+        n = ctypes.c_int(0)
+        self._check(self.lib.gmres_batch_history(self.h, i, None, 0, ctypes.byref(n)))
+        buf = np.zeros(n.value, dtype=np.float64)
+        self._check(self.lib.gmres_batch_history(self.h, i, _ptr(buf), n.value, ctypes.byref(n)))
+        return buf
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.gmres_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def _info(i: _Info) -> SolveInfo:

@@ -121,6 +121,86 @@ def grid27_nnz(N: int) -> int:
 
 
 # --------------------------------------------------------------------------
+# 2D 9-point variable-coefficient convection-diffusion (batched workload)
+# --------------------------------------------------------------------------
+# Bilinear (Q1) element stiffness of -div(kappa grad u) on a unit square cell
+# with constant kappa, corners ordered (0,0), (1,0), (1,1), (0,1).
+_Q1_K = np.array([[4.0, -1.0, -2.0, -1.0],
+                  [-1.0, 4.0, -1.0, -2.0],
+                  [-2.0, -1.0, 4.0, -1.0],
+                  [-1.0, -2.0, -1.0, 4.0]]) / 6.0
+
+
+def conv_diff_9pt_2d(N: int, kappa_cells: np.ndarray, peclet: float, theta: float) -> CSR:
+    """-div(kappa grad u) + b . grad(u) on the N x N interior nodes of a uniform
+    grid of the unit square, Dirichlet boundary eliminated. Diffusion: bilinear
+    (Q1) elements with one kappa per cell ((N+1) x (N+1) cells, kappa_cells[cy, cx]),
+    giving a 9-point stencil. Convection: first-order upwinding of a constant
+    velocity with cell Peclet number `peclet` in direction theta, added as
+    (|p_a|) on the diagonal and -|p_a| on the upwind neighbour along each axis,
+    p = peclet * (cos theta, sin theta). Nodes are ordered x fastest."""
+    import scipy.sparse as sparse
+
+    N = int(N)
+    n = N * N
+    kc = np.asarray(kappa_cells, dtype=np.float64)
+    assert kc.shape == (N + 1, N + 1)
+    cy, cx = np.meshgrid(np.arange(N + 1), np.arange(N + 1), indexing="ij")
+    cx, cy, kk = cx.ravel(), cy.ravel(), kc.ravel()
+    # node coordinates (0..N+1) of the 4 corners, interior nodes are 1..N
+    corners = [(cx, cy), (cx + 1, cy), (cx + 1, cy + 1), (cx, cy + 1)]
+    rows, cols, vals = [], [], []
+    for a in range(4):
+        xa, ya = corners[a]
+        ia_ok = (xa >= 1) & (xa <= N) & (ya >= 1) & (ya <= N)
+        ia = (ya - 1) * N + (xa - 1)
+        for b in range(4):
+            xb, yb = corners[b]
+            ok = ia_ok & (xb >= 1) & (xb <= N) & (yb >= 1) & (yb <= N)
+            ib = (yb - 1) * N + (xb - 1)
+            rows.append(ia[ok])
+            cols.append(ib[ok])
+            vals.append(kk[ok] * _Q1_K[a, b])
+    # upwind convection
+    px, py = peclet * np.cos(theta), peclet * np.sin(theta)
+    idx = np.arange(n)
+    ix, iy = idx % N, idx // N
+    rows.append(idx)
+    cols.append(idx)
+    vals.append(np.full(n, abs(px) + abs(py)))
+    for p, shift, pos in ((px, 1, ix), (py, N, iy)):
+        if p > 0:  # flow in +axis: upwind neighbour is the lower one
+            ok = pos > 0
+            rows.append(idx[ok]); cols.append(idx[ok] - shift); vals.append(np.full(ok.sum(), -abs(p)))
+        elif p < 0:
+            ok = pos < N - 1
+            rows.append(idx[ok]); cols.append(idx[ok] + shift); vals.append(np.full(ok.sum(), -abs(p)))
+    S = sparse.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(n, n)).tocsr()
+    S.sum_duplicates()
+    S.sort_indices()
+    return S.indptr.astype(np.int32), S.indices.astype(np.int32), S.data.astype(np.float64)
+
+
+def batch_2d_params(count: int, seed: int = 0, side=(32, 256)):
+    """Seeded parameters of the batched workload: per system a grid side
+    log-uniform in `side`, cell diffusion coefficients log-uniform in [0.1, 10],
+    a cell Peclet number U[0, 2] and a flow direction U[0, 2 pi)."""
+    rng = _rng(seed)
+    out = []
+    for _ in range(count):
+        N = int(round(np.exp(rng.uniform(np.log(side[0]), np.log(side[1])))))
+        out.append(dict(N=N, kseed=int(rng.integers(1 << 31)), peclet=float(rng.uniform(0.0, 2.0)),
+                        theta=float(rng.uniform(0.0, 2 * np.pi))))
+    return out
+
+
+def batch_2d_system(par) -> CSR:
+    N = par["N"]
+    kc = np.exp(_rng(par["kseed"]).uniform(np.log(0.1), np.log(10.0), (N + 1, N + 1)))
+    return conv_diff_9pt_2d(N, kc, par["peclet"], par["theta"])
+
+
+# --------------------------------------------------------------------------
 # right-hand sides and generic helpers
 # --------------------------------------------------------------------------
 def to_scipy(A: CSR) -> sp.csr_matrix:

@@ -170,7 +170,7 @@ def test_solve_c1(torch_cuda, lsg, orc, ortho):
 
 
 @pytest.mark.parametrize("ortho", ["mgs", "one_reduce_mgs"])
-@pytest.mark.parametrize("case", ["m1", "ragged_restarts", "maxiter", "x0", "direct"])
+@pytest.mark.parametrize("case", ["m1", "ragged_restarts", "maxiter", "x0", "direct", "exact_breakdown"])
 def test_solve_edge_cases(torch_cuda, lsg, orc, ortho, case):
     torch = torch_cuda
     if case == "m1":  # GMRES(1): one column per cycle
@@ -189,6 +189,12 @@ def test_solve_edge_cases(torch_cuda, lsg, orc, ortho, case):
         A = P.conv_diff_7pt(9)
         _, b = P.rhs(A, 4)
         args = dict(m=10, tol=1e-9, max_iter=300)
+    elif case == "exact_breakdown":  # A = 2 I, b = e_0: u_1 = 0 exactly at step 1
+        n = 300
+        A = (np.arange(n + 1, dtype=np.int32), np.arange(n, dtype=np.int32), np.full(n, 2.0))
+        b = np.zeros(n)
+        b[0] = 1.0
+        args = dict(m=5, tol=1e-12, max_iter=50)
     else:  # GMRES(n) on a small dense system: exact termination
         M = P.random_dense(13, seed=2)
         A = P.from_dense(M)

@@ -117,3 +117,24 @@ def test_generator_27pt_equals_kronecker_definition():
     for i in range(N ** 3):
         c = A[1][A[0][i]:A[0][i + 1]]
         assert np.all(np.diff(c) > 0)
+
+
+def test_generator_9pt_2d():
+    """With kappa = 1 and no convection the 2D generator is the bilinear stiffness
+    T (x) M + M (x) T (scipy Kronecker products); the full operator has at most 9
+    entries per row, sorted columns, and a positive definite symmetric part."""
+    import scipy.sparse as sp
+
+    N = 6
+    A = P.conv_diff_9pt_2d(N, np.ones((N + 1, N + 1)), 0.0, 0.3)
+    Tm = sp.diags([-1.0, 2.0, -1.0], [-1, 0, 1], shape=(N, N))
+    Mm = sp.diags([1.0, 4.0, 1.0], [-1, 0, 1], shape=(N, N)) / 6.0
+    ref = (sp.kron(Mm, Tm) + sp.kron(Tm, Mm)).toarray()
+    assert np.allclose(P.to_scipy(A).toarray(), ref, atol=1e-15)
+    par = P.batch_2d_params(3, seed=1, side=(16, 20))[0]
+    B = P.batch_2d_system(par)
+    assert np.diff(B[0]).max() <= 9
+    D = P.to_scipy(B).toarray()
+    assert np.linalg.eigvalsh(0.5 * (D + D.T)).min() > 0
+    for i in range(len(B[0]) - 1):
+        assert np.all(np.diff(B[1][B[0][i]:B[0][i + 1]]) > 0)
