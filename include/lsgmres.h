@@ -192,6 +192,13 @@ gmres_status gmres_batch_set_stream(gmres_batch bt, void* cuda_stream);
 gmres_status gmres_batch_set_grid(gmres_batch bt, int ctas);
 gmres_status gmres_batch_get_grid(gmres_batch bt, int* ctas);
 
+/* Rows per thread of the batched step kernel: 1 (one 256-row tile per CTA
+ * iteration) or 2 (two consecutive tiles of one system together, so the CSR
+ * loads of two rows are in flight at once); chosen by the autotuner with the
+ * grid (gmres_batch_set_grid(bt, 0)). Other values: GMRES_ERR_ARG. */
+gmres_status gmres_batch_set_rows_per_thread(gmres_batch bt, int rows);
+gmres_status gmres_batch_get_rows_per_thread(gmres_batch bt, int* rows);
+
 /* Solve all systems: b[i] and x[i] are device pointers (host array of `count`
  * pointers) to system i's right-hand side and its x0 / solution. info may be
  * NULL or a host array of `count` entries (per system). Returns GMRES_OK if
@@ -214,6 +221,14 @@ gmres_status gmres_batch_solve_host(gmres_batch bt, const double* const* b_host,
 gmres_status gmres_batch_set_profile(gmres_batch bt, int on);
 gmres_status gmres_batch_profile(gmres_batch bt, int cls, double* total_ms, int64_t* launches,
                                  double* alg_bytes, double* alg_flops);
+
+/* Launch-by-launch record of the last profiled batch solve, in launch order:
+ * class (as gmres_profile), step index j (step and MAXPY launches; 0/1 for
+ * the norm and residual launches), tiles of 256 rows in the active list at the
+ * launch, device ms, algorithmic flops. Any output may be NULL; at most cap
+ * entries are written; *count receives the total. */
+gmres_status gmres_batch_launch_log(gmres_batch bt, int cap, int* cls, int* step, int64_t* active_tiles,
+                                    float* ms, double* alg_flops, int* count);
 
 /* Residual-estimate history of system i in the last batch solve (as gmres_history). */
 gmres_status gmres_batch_history(gmres_batch bt, int i, double* host_buf, int cap, int* len);

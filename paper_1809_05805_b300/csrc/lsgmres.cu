@@ -384,9 +384,10 @@ __device__ __forceinline__ void tile_block_dot(int64_t t, int64_t n, const int32
 #pragma unroll
       for (int q = 0; q < kRowsPerLane; ++q) x[q] = (base + 32 * q < n) ? __ldg(vk + 32 * q) : VT(0);
 #pragma unroll
-      for (int q = 0; q < kRowsPerLane; ++q) {
-        acc_a[c] = fma(x[q], ru[q], acc_a[c]);
-        acc_c[c] = fma(x[q], rw[q], acc_c[c]);
+      for (int q = 0; q < kRowsPerLane; ++q) acc_a[c] = fma(x[q], ru[q], acc_a[c]);
+      if (need_w) {  // the cycle's tail needs only V^T u
+#pragma unroll
+        for (int q = 0; q < kRowsPerLane; ++q) acc_c[c] = fma(x[q], rw[q], acc_c[c]);
       }
     }
   }
@@ -395,7 +396,84 @@ __device__ __forceinline__ void tile_block_dot(int64_t t, int64_t n, const int32
     if (c < r8) {  // block-uniform
       const VT x = (row < n) ? __ldg(V + (size_t)(J8 * kWarps + c) * ldv + row) : VT(0);
       rem_a[c] = fma(x, ur, rem_a[c]);
-      rem_c[c] = fma(x, wr, rem_c[c]);
+      if (need_w) rem_c[c] = fma(x, wr, rem_c[c]);
+    }
+  }
+  __syncthreads();
+}
+
+// Tiles 2 pp and 2 pp + 1 (rows 512 pp .. 512 pp + 511) of the fused SpMV +
+// block dot, two rows per thread: the CSR loads of both rows are in flight
+// together, halving the latency-bound SpMV phases per row. su, sw hold 512
+// values.
+template <int MAXC, typename VT>
+__device__ __forceinline__ void tile_pair_block_dot(int64_t pp, int64_t n, const int32_t* __restrict__ rowptr,
+                                                    const int32_t* __restrict__ col, const VT* __restrict__ val,
+                                                    const VT* __restrict__ V, int64_t ldv, const VT* __restrict__ u,
+                                                    VT* __restrict__ w, bool spmv, bool need_w, int J8, int r8,
+                                                    VT* su, VT* sw, VT (&acc_a)[MAXC], VT (&acc_c)[MAXC],
+                                                    VT (&rem_a)[kWarps - 1], VT (&rem_c)[kWarps - 1], VT& sig,
+                                                    VT& dd) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t row0 = pp * (2 * kThreads) + threadIdx.x, row1 = row0 + kThreads;
+  VT ur0 = VT(0), wr0 = VT(0), ur1 = VT(0), wr1 = VT(0);
+  if (row0 < n) ur0 = u[row0];
+  if (row1 < n) ur1 = u[row1];
+  if (spmv) {
+    csr_row2(rowptr, col, val, u, row0, row1, n, wr0, wr1);
+    if (row0 < n) w[row0] = wr0;
+    if (row1 < n) w[row1] = wr1;
+  } else if (need_w) {
+    if (row0 < n) wr0 = w[row0];
+    if (row1 < n) wr1 = w[row1];
+  }
+  sig = fma(ur0, ur0, sig);
+  dd = fma(ur0, wr0, dd);
+  sig = fma(ur1, ur1, sig);
+  dd = fma(ur1, wr1, dd);
+  su[threadIdx.x] = ur0;
+  sw[threadIdx.x] = wr0;
+  su[kThreads + threadIdx.x] = ur1;
+  sw[kThreads + threadIdx.x] = wr1;
+  __syncthreads();
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int64_t base = pp * (2 * kThreads) + h * kThreads + lane;
+    VT ru[kRowsPerLane], rw[kRowsPerLane];
+#pragma unroll
+    for (int q = 0; q < kRowsPerLane; ++q) {
+      ru[q] = su[h * kThreads + lane + 32 * q];
+      rw[q] = sw[h * kThreads + lane + 32 * q];
+    }
+#pragma unroll
+    for (int c = 0; c < MAXC; ++c) {
+      if (c < J8) {  // warp-uniform
+        const int k = wid + c * kWarps;
+        const VT* vk = V + (size_t)k * ldv + base;
+        VT x[kRowsPerLane];
+#pragma unroll
+        for (int q = 0; q < kRowsPerLane; ++q) x[q] = (base + 32 * q < n) ? __ldg(vk + 32 * q) : VT(0);
+#pragma unroll
+        for (int q = 0; q < kRowsPerLane; ++q) acc_a[c] = fma(x[q], ru[q], acc_a[c]);
+        if (need_w) {  // the cycle's tail needs only V^T u
+#pragma unroll
+          for (int q = 0; q < kRowsPerLane; ++q) acc_c[c] = fma(x[q], rw[q], acc_c[c]);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < kWarps - 1; ++c) {
+    if (c < r8) {  // block-uniform
+      const VT* vk = V + (size_t)(J8 * kWarps + c) * ldv;
+      const VT x0 = (row0 < n) ? __ldg(vk + row0) : VT(0);
+      const VT x1 = (row1 < n) ? __ldg(vk + row1) : VT(0);
+      rem_a[c] = fma(x0, ur0, rem_a[c]);
+      rem_a[c] = fma(x1, ur1, rem_a[c]);
+      if (need_w) {
+        rem_c[c] = fma(x0, wr0, rem_c[c]);
+        rem_c[c] = fma(x1, wr1, rem_c[c]);
+      }
     }
   }
   __syncthreads();
@@ -624,67 +702,9 @@ k_one_reduce_step(const int32_t* __restrict__ rowptr, const int32_t* __restrict_
   // ones keep one tile per CTA iteration so that every SM gets work.
   if (ntiles >= 4 * (int64_t)gridDim.x) {
     const int64_t npairs = (ntiles + 1) / 2;
-    for (int64_t pp = blockIdx.x; pp < npairs; pp += gridDim.x) {
-      const int64_t row0 = pp * (2 * kThreads) + threadIdx.x, row1 = row0 + kThreads;
-      VT ur0 = VT(0), wr0 = VT(0), ur1 = VT(0), wr1 = VT(0);
-      if (row0 < n) ur0 = u[row0];
-      if (row1 < n) ur1 = u[row1];
-      if (spmv) {
-        csr_row2(rowptr, col, val, u, row0, row1, n, wr0, wr1);
-        if (row0 < n) w[row0] = wr0;
-        if (row1 < n) w[row1] = wr1;
-      } else if (need_w) {
-        if (row0 < n) wr0 = w[row0];
-        if (row1 < n) wr1 = w[row1];
-      }
-      sig = fma(ur0, ur0, sig);
-      dd = fma(ur0, wr0, dd);
-      sig = fma(ur1, ur1, sig);
-      dd = fma(ur1, wr1, dd);
-      su[threadIdx.x] = ur0;
-      sw[threadIdx.x] = wr0;
-      su[kThreads + threadIdx.x] = ur1;
-      sw[kThreads + threadIdx.x] = wr1;
-      __syncthreads();
-  #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int64_t base = pp * (2 * kThreads) + h * kThreads + lane;
-        VT ru[kRowsPerLane], rw[kRowsPerLane];
-  #pragma unroll
-        for (int q = 0; q < kRowsPerLane; ++q) {
-          ru[q] = su[h * kThreads + lane + 32 * q];
-          rw[q] = sw[h * kThreads + lane + 32 * q];
-        }
-  #pragma unroll
-        for (int c = 0; c < MAXC; ++c) {
-          if (c < J8) {  // warp-uniform
-            const int k = wid + c * kWarps;
-            const VT* vk = V + (size_t)k * ldv + base;
-            VT x[kRowsPerLane];
-  #pragma unroll
-            for (int q = 0; q < kRowsPerLane; ++q) x[q] = (base + 32 * q < n) ? __ldg(vk + 32 * q) : VT(0);
-  #pragma unroll
-            for (int q = 0; q < kRowsPerLane; ++q) {
-              acc_a[c] = fma(x[q], ru[q], acc_a[c]);
-              acc_c[c] = fma(x[q], rw[q], acc_c[c]);
-            }
-          }
-        }
-      }
-  #pragma unroll
-      for (int c = 0; c < kWarps - 1; ++c) {
-        if (c < r8) {  // block-uniform
-          const VT* vk = V + (size_t)(J8 * kWarps + c) * ldv;
-          const VT x0 = (row0 < n) ? __ldg(vk + row0) : VT(0);
-          const VT x1 = (row1 < n) ? __ldg(vk + row1) : VT(0);
-          rem_a[c] = fma(x0, ur0, rem_a[c]);
-          rem_c[c] = fma(x0, wr0, rem_c[c]);
-          rem_a[c] = fma(x1, ur1, rem_a[c]);
-          rem_c[c] = fma(x1, wr1, rem_c[c]);
-        }
-      }
-      __syncthreads();
-    }
+    for (int64_t pp = blockIdx.x; pp < npairs; pp += gridDim.x)
+      tile_pair_block_dot<MAXC, VT>(pp, n, rowptr, col, val, V, ldv, u, w, spmv, need_w, J8, r8, su, sw, acc_a, acc_c,
+                                    rem_a, rem_c, sig, dd);
   } else {
     for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x)
       tile_block_dot<MAXC, VT>(t, n, rowptr, col, val, V, ldv, u, w, spmv, need_w, J8, r8, su, sw, acc_a, acc_c, rem_a,
@@ -1110,6 +1130,7 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 // cycle (or the solve) are skipped.
 struct BatchDev {
   const int32_t* tile_sys;   // T: system of each tile
+  const int32_t* sys_tile1;  // S: one past the last tile of each system
   const int32_t* act_tiles;  // Ta: tiles of the active systems, system by system
   const int64_t* n_act;      // Ta (device scalar)
   const int32_t* sys_b0;     // S: first CTA whose tile range touches the system
@@ -1135,13 +1156,15 @@ __device__ __forceinline__ void cta_tile_range(const BatchDev& bd, int64_t& lo, 
   hi = ((int64_t)blockIdx.x + 1) * Ta / Pe;
 }
 
-// Step j of the current cycle for every active system of the batch.
-template <int MAXC>
+// Step j of the current cycle for every active system of the batch. PAIRS:
+// two consecutive tiles of one system are processed together (two rows per
+// thread) wherever the CTA's range allows.
+template <int MAXC, bool PAIRS>
 __global__ void __launch_bounds__(kThreads, 2)
 kb_step(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col, const double* __restrict__ val,
         const double* __restrict__ V, int64_t ldv, double* __restrict__ w, int64_t NT, BatchDev bd, int j) {
-  __shared__ double su[kThreads];
-  __shared__ double sw[kThreads];
+  __shared__ double su[PAIRS ? 2 * kThreads : kThreads];
+  __shared__ double sw[PAIRS ? 2 * kThreads : kThreads];
   __shared__ double red[2 * (kMaxM + 1) + 2];
   __shared__ int s_active, s_tail;
   const int J8 = j / kWarps, r8 = j % kWarps;
@@ -1152,7 +1175,7 @@ kb_step(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col, con
   cta_tile_range(bd, lo, hi);
   if (lo >= hi) return;  // no tiles (fewer active tiles than CTAs): no slot, no ticket
   int cur = -1;
-  for (int64_t it = lo; it <= hi; ++it) {
+  for (int64_t it = lo; it <= hi;) {
     const int64_t t = (it < hi) ? bd.act_tiles[it] : -1;
     const int snext = (it < hi) ? __ldg(bd.tile_sys + t) : -1;
     if (snext != cur) {  // CTA-uniform
@@ -1183,15 +1206,27 @@ kb_step(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col, con
       for (int c = 0; c < kWarps - 1; ++c) rem_a[c] = rem_c[c] = 0.0;
       sig = dd = 0.0;
     }
+    // a system's tiles are consecutive in the list and in memory: tiles t and
+    // t + 1 form the pair t / 2 when t is even
+    if (PAIRS && (t & 1) == 0 && it + 1 < hi && __ldg(bd.tile_sys + t + 1) == cur) {
+      if (s_active)
+        tile_pair_block_dot<MAXC, double>(t >> 1, NT, rowptr, col, val, V, ldv, u, w, !s_tail, !s_tail, J8, r8, su,
+                                          sw, acc_a, acc_c, rem_a, rem_c, sig, dd);
+      it += 2;
+      continue;
+    }
     if (s_active)
       tile_block_dot<MAXC, double>(t, NT, rowptr, col, val, V, ldv, u, w, !s_tail, !s_tail, J8, r8, su, sw, acc_a,
                                    acc_c, rem_a, rem_c, sig, dd);
+    ++it;
   }
 }
 
-// Arnoldi MAXPY of step j for every active system (one row per thread, a tile
-// per CTA iteration, the system's coefficients staged in shared memory), plus
-// one CTA per system (block index >= ndata) that finishes column j-1 of that
+// Arnoldi MAXPY of step j for every active system: the first Pe = min(ndata,
+// Ta) CTAs take contiguous ranges of the active-tile list and stream each run
+// of one system's tiles (consecutive rows) with 16-byte loads, four basis
+// columns in flight, the system's coefficients staged in shared memory once per
+// run. One CTA per system (block index >= ndata) finishes column j-1 of that
 // system's Hessenberg matrix while the others stream.
 __global__ void __launch_bounds__(kThreads, 4)
 kb_maxpy(double* __restrict__ V, int64_t ldv, const double* __restrict__ w, BatchDev bd, int j, int ndata) {
@@ -1212,12 +1247,21 @@ kb_maxpy(double* __restrict__ V, int64_t ldv, const double* __restrict__ w, Batc
     }
     return;
   }
-  double* out = V + (size_t)(j + 1) * ldv;
   const int64_t Ta = *bd.n_act;
-  for (int64_t it = blockIdx.x; it < Ta; it += ndata) {
-    const int64_t t = bd.act_tiles[it];
+  const int64_t Pe = Ta < (int64_t)ndata ? Ta : (int64_t)ndata;
+  if ((int64_t)blockIdx.x >= Pe) return;
+  const int64_t lo = (int64_t)blockIdx.x * Ta / Pe, hi = ((int64_t)blockIdx.x + 1) * Ta / Pe;
+  const double2* w2 = reinterpret_cast<const double2*>(w);
+  double2* out2 = reinterpret_cast<double2*>(V + (size_t)(j + 1) * ldv);
+  const int64_t ldv2 = ldv / 2;
+  const double2* V2 = reinterpret_cast<const double2*>(V);
+  for (int64_t it = lo; it < hi;) {
+    const int64_t t0 = bd.act_tiles[it];
+    const int sy = __ldg(bd.tile_sys + t0);
+    const int64_t run = min(hi - it, (int64_t)__ldg(bd.sys_tile1 + sy) - t0);  // this system's tiles in range
+    __syncthreads();  // every warp is done with the previous run's flags and coefficients
     if (threadIdx.x == 0) {
-      const Small sm = bd.smalls[__ldg(bd.tile_sys + t)];
+      const Small sm = bd.smalls[sy];
       s_on = !__ldcg(&sm.st->done) && j < __ldcg(&sm.st->kmax);
       sK = __ldcg(&sm.st->maxpy_k);
       s_coef = sm.coef;
@@ -1227,20 +1271,30 @@ kb_maxpy(double* __restrict__ V, int64_t ldv, const double* __restrict__ w, Batc
       const int K = sK;
       for (int i = threadIdx.x; i <= K; i += blockDim.x) sc[i] = __ldcg(s_coef + i);
       __syncthreads();
-      const int64_t row = t * kThreads + threadIdx.x;
-      double a = sc[0] * w[row];
-      int k = 0;
-      for (; k + 4 <= K; k += 4) {
-        double v[4];
+      const int64_t e0 = t0 * (kThreads / 2), e1 = (t0 + run) * (kThreads / 2);  // double2 elements
+      for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+        const double2 y = w2[e];
+        double a0 = sc[0] * y.x, a1 = sc[0] * y.y;
+        int k = 0;
+        for (; k + 4 <= K; k += 4) {
+          double2 v[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) v[q] = __ldg(V + (size_t)(k + q) * ldv + row);
+          for (int q = 0; q < 4; ++q) v[q] = __ldg(V2 + (size_t)(k + q) * ldv2 + e);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) a = fma(sc[1 + k + q], v[q], a);
+          for (int q = 0; q < 4; ++q) {
+            a0 = fma(sc[1 + k + q], v[q].x, a0);
+            a1 = fma(sc[1 + k + q], v[q].y, a1);
+          }
+        }
+        for (; k < K; ++k) {
+          const double2 v = __ldg(V2 + (size_t)k * ldv2 + e);
+          a0 = fma(sc[1 + k], v.x, a0);
+          a1 = fma(sc[1 + k], v.y, a1);
+        }
+        out2[e] = make_double2(a0, a1);
       }
-      for (; k < K; ++k) a = fma(sc[1 + k], __ldg(V + (size_t)k * ldv + row), a);
-      out[row] = a;
     }
-    __syncthreads();
+    it += run;
   }
 }
 
@@ -1332,19 +1386,24 @@ kb_xupdate(const double* __restrict__ V, int64_t ldv, double* __restrict__ x, Ba
 using BatchStepKernel = void (*)(const int32_t*, const int32_t*, const double*, const double*, int64_t, double*,
                                  int64_t, BatchDev, int);
 
-BatchStepKernel batch_step_kernel_for(int m) {
+template <bool PAIRS>
+BatchStepKernel batch_step_kernel_sel(int m) {
   switch (std::max(1, m / kWarps)) {
-    case 1: return kb_step<1>;
-    case 2: return kb_step<2>;
-    case 3: return kb_step<3>;
-    case 4: return kb_step<4>;
-    case 5: return kb_step<5>;
-    case 6: return kb_step<6>;
-    case 7: return kb_step<7>;
-    case 8: return kb_step<8>;
-    case 9: case 10: case 11: case 12: return kb_step<12>;
-    default: return kb_step<16>;
+    case 1: return kb_step<1, PAIRS>;
+    case 2: return kb_step<2, PAIRS>;
+    case 3: return kb_step<3, PAIRS>;
+    case 4: return kb_step<4, PAIRS>;
+    case 5: return kb_step<5, PAIRS>;
+    case 6: return kb_step<6, PAIRS>;
+    case 7: return kb_step<7, PAIRS>;
+    case 8: return kb_step<8, PAIRS>;
+    case 9: case 10: case 11: case 12: return kb_step<12, PAIRS>;
+    default: return kb_step<16, PAIRS>;
   }
+}
+
+BatchStepKernel batch_step_kernel_for(int m, bool pairs) {
+  return pairs ? batch_step_kernel_sel<true>(m) : batch_step_kernel_sel<false>(m);
 }
 
 template <typename VT>
@@ -2242,6 +2301,7 @@ struct gmres_batch_ctx {
   double* bcat = nullptr;
   double* xcat = nullptr;
   int32_t* tile_sys = nullptr;
+  int32_t* sys_tile1 = nullptr;
   // device layout: active-tile list and per-system reduction slots
   int32_t* act_tiles = nullptr;
   int64_t* n_act = nullptr;
@@ -2265,13 +2325,22 @@ struct gmres_batch_ctx {
   size_t small_stride = 0;
   size_t step_smem = 0, lsq_smem = 0;
   BatchStepKernel step = nullptr;
+  bool pairs = false;  // step kernel takes tile pairs (two rows per thread)
   cudaStream_t stream = nullptr;
   // profiling (events around each launch; graphs captured with timing nodes)
   struct Rec {
     int cls, j;
     cudaEvent_t a, b;
     double bytes, flops;  // bytes < 0: attributed when the cycle's columns are known
+    int64_t tiles;        // active tiles at launch
   };
+  struct LogEntry {
+    int cls, j;
+    int64_t tiles;
+    float ms;
+    double bytes, flops;
+  };
+  std::vector<LogEntry> log;  // every launch of the last profiled solve
   struct G {
     int kmax;
     bool prof;
@@ -2328,6 +2397,7 @@ int batch_stream_grid(const gmres_batch_ctx* b) { return (int)std::min<int64_t>(
 BatchDev batch_dev(gmres_batch_ctx* b) {
   BatchDev d{};
   d.tile_sys = b->tile_sys;
+  d.sys_tile1 = b->sys_tile1;
   d.act_tiles = b->act_tiles;
   d.n_act = b->n_act;
   d.sys_b0 = b->sys_b0;
@@ -2398,7 +2468,7 @@ void batch_drop_graphs(gmres_batch_ctx* b) {
 // ---- profiling: an event pair around a launch (no-op unless profiling)
 int batch_prof_begin(gmres_batch_ctx* b, int cls, int j, double bytes = -1.0, double flops = -1.0) {
   if (!b->prof_on) return -1;
-  gmres_batch_ctx::Rec r{cls, j, nullptr, nullptr, bytes, flops};
+  gmres_batch_ctx::Rec r{cls, j, nullptr, nullptr, bytes, flops, *b->h_nact};
   if (b->cap) {  // timing nodes of the graph being captured
     gmres_batch_ctx::G* g = b->cap;
     const size_t u = 2 * g->recs.size();
@@ -2479,14 +2549,17 @@ void batch_prof_settle(gmres_batch_ctx* b) {
     b->prof_cnt[c] += 1;
     b->prof_bytes[c] += by;
     b->prof_flops[c] += fl;
+    b->log.push_back({c, r.j, r.tiles, ms, by, fl});
   }
   b->pending.clear();
   b->ev_used = 0;
   std::fill(b->cyc_kmax.begin(), b->cyc_kmax.end(), -1);
 }
 
-gmres_status batch_set_grid(gmres_batch_ctx* b, int P) {
+gmres_status batch_set_grid(gmres_batch_ctx* b, int P, bool pairs) {
   b->P = P;
+  b->pairs = pairs;
+  b->step = batch_step_kernel_for(b->m, pairs);
   b->layout_active.clear();  // the next solve lays out again
   batch_drop_graphs(b);
   return GMRES_OK;
@@ -2541,30 +2614,37 @@ gmres_status batch_run_cycle(gmres_batch_ctx* b, int KM) {
     }
   }
   BCUDA(b, cudaGraphLaunch(hit->exec, b->stream));
-  if (b->prof_on) b->pending.insert(b->pending.end(), hit->recs.begin(), hit->recs.end());
+  if (b->prof_on)
+    for (auto r : hit->recs) {
+      r.tiles = *b->h_nact;
+      b->pending.push_back(r);
+    }
   return GMRES_OK;
 }
 
-// Pick the grid of the batched reduction kernels: time one mid-cycle batched
-// step (all systems active, on the zeroed basis) for grids of 1, 2 and 3 CTAs
-// per SM (clamped to the tile count), best of two timed repeats each. The
-// states it dirties are reset by every solve.
+// Pick the launch shape of the batched step kernel: time one mid-cycle
+// batched step (all systems active, on the zeroed basis) for grids of 1, 2
+// and 3 CTAs per SM (clamped to the tile count), each with one and with two
+// rows per thread, best of two timed repeats each. The states it dirties are
+// reset by every solve.
 gmres_status batch_autotune(gmres_batch_ctx* b) {
-  std::vector<int> cand;
-  for (int k = 1; k <= 3; ++k) {
-    const int P = (int)std::min<int64_t>((int64_t)k * b->nsm, b->T);
-    if (cand.empty() || cand.back() != P) cand.push_back(P);
-  }
+  std::vector<std::pair<int, bool>> cand;
+  for (int pr = 0; pr < 2; ++pr)
+    for (int k = 1; k <= 3; ++k) {
+      const int P = (int)std::min<int64_t>((int64_t)k * b->nsm, b->T);
+      if (cand.empty() || cand.back() != std::make_pair(P, pr == 1)) cand.emplace_back(P, pr == 1);
+    }
   cudaEvent_t e0, e1;
   BCUDA(b, cudaEventCreate(&e0));
   BCUDA(b, cudaEventCreate(&e1));
   const int j = std::max(1, b->m / 2);
   const std::vector<char> all(b->S, 1);
   float best = 1e30f;
-  int bestP = cand.front();
+  auto bestc = cand.front();
   gmres_status st = GMRES_OK;
-  for (int P : cand) {
-    batch_set_grid(b, P);
+  for (auto c : cand) {
+    const int P = c.first;
+    batch_set_grid(b, P, c.second);
     if ((st = batch_layout(b, all, 0)) != GMRES_OK) break;
     float t_best = 1e30f;
     for (int rep = 0; rep < 3 && st == GMRES_OK; ++rep) {
@@ -2590,13 +2670,13 @@ gmres_status batch_autotune(gmres_batch_ctx* b) {
     if (st != GMRES_OK) break;
     if (t_best < best) {
       best = t_best;
-      bestP = P;
+      bestc = c;
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (st != GMRES_OK) return st;
-  return batch_set_grid(b, bestP);
+  return batch_set_grid(b, bestc.first, bestc.second);
 }
 
 }  // namespace
@@ -2614,6 +2694,7 @@ gmres_status gmres_batch_destroy(gmres_batch b) {
   cudaFree(b->bcat);
   cudaFree(b->xcat);
   cudaFree(b->tile_sys);
+  cudaFree(b->sys_tile1);
   cudaFree(b->act_tiles);
   cudaFree(b->n_act);
   cudaFree(b->sys_b0);
@@ -2734,6 +2815,12 @@ gmres_status gmres_batch_create(const gmres_csr* A, int count, int m_restart, do
   }
   BTRY(cudaMalloc(&b->tile_sys, sizeof(int32_t) * b->T));
   BTRY(cudaMemcpy(b->tile_sys, b->h_tile_sys.data(), sizeof(int32_t) * b->T, cudaMemcpyHostToDevice));
+  {
+    std::vector<int32_t> t1(count);
+    for (int i = 0; i < count; ++i) t1[i] = (int32_t)(b->tile0[i] + b->ntile[i]);
+    BTRY(cudaMalloc(&b->sys_tile1, sizeof(int32_t) * count));
+    BTRY(cudaMemcpy(b->sys_tile1, t1.data(), sizeof(int32_t) * count, cudaMemcpyHostToDevice));
+  }
   BTRY(cudaMalloc(&b->act_tiles, sizeof(int32_t) * b->T));
   BTRY(cudaMalloc(&b->n_act, sizeof(int64_t)));
   BTRY(cudaMalloc(&b->sys_b0, sizeof(int32_t) * count));
@@ -2798,11 +2885,11 @@ gmres_status gmres_batch_create(const gmres_csr* A, int count, int m_restart, do
   }
   BTRY(cudaMalloc(&b->smalls_dev, sizeof(Small) * count));
   BTRY(cudaMemcpy(b->smalls_dev, b->smalls.data(), sizeof(Small) * count, cudaMemcpyHostToDevice));
-  b->step = batch_step_kernel_for(m);
   b->step_smem = sizeof(double) * ((size_t)ld * ld + ld);
   b->lsq_smem = sizeof(double) * (size_t)ld * m;
-  BTRY(cudaFuncSetAttribute(reinterpret_cast<const void*>(b->step), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                            (int)b->step_smem));
+  for (bool pr : {false, true})
+    BTRY(cudaFuncSetAttribute(reinterpret_cast<const void*>(batch_step_kernel_for(m, pr)),
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->step_smem));
   BTRY(cudaFuncSetAttribute(reinterpret_cast<const void*>(kb_lsq), cudaFuncAttributeMaxDynamicSharedMemorySize,
                             (int)b->lsq_smem));
 #undef BTRY
@@ -2820,7 +2907,19 @@ gmres_status gmres_batch_set_grid(gmres_batch b, int ctas) {
   if (ctas == 0) return batch_autotune(b);
   if (ctas < 0 || ctas > batch_max_grid(b))
     return bfail(b, GMRES_ERR_ARG, "ctas must be in [0, " + std::to_string(batch_max_grid(b)) + "]");
-  return batch_set_grid(b, ctas);
+  return batch_set_grid(b, ctas, b->pairs);
+}
+
+gmres_status gmres_batch_set_rows_per_thread(gmres_batch b, int rows) {
+  if (!b) return GMRES_ERR_ARG;
+  if (rows != 1 && rows != 2) return bfail(b, GMRES_ERR_ARG, "rows per thread must be 1 or 2");
+  return batch_set_grid(b, b->P, rows == 2);
+}
+
+gmres_status gmres_batch_get_rows_per_thread(gmres_batch b, int* rows) {
+  if (!b || !rows) return GMRES_ERR_ARG;
+  *rows = b->pairs ? 2 : 1;
+  return GMRES_OK;
 }
 
 gmres_status gmres_batch_get_grid(gmres_batch b, int* ctas) {
@@ -2861,6 +2960,7 @@ gmres_status batch_solve(gmres_batch b, const double* const* bv, double* const* 
     b->prof_ms[c] = b->prof_bytes[c] = b->prof_flops[c] = 0.0;
     b->prof_cnt[c] = 0;
   }
+  b->log.clear();
   // gather b and x0 into the padded layout (padding rows stay 0 throughout)
   BCUDA(b, cudaMemsetAsync(b->bcat, 0, sizeof(double) * b->NT, sm));
   BCUDA(b, cudaMemsetAsync(b->xcat, 0, sizeof(double) * b->NT, sm));
@@ -3019,6 +3119,22 @@ gmres_status gmres_batch_solve_host(gmres_batch b, const double* const* bv, doub
 gmres_status gmres_batch_set_profile(gmres_batch b, int on) {
   if (!b) return GMRES_ERR_ARG;
   b->prof_on = on != 0;
+  return GMRES_OK;
+}
+
+gmres_status gmres_batch_launch_log(gmres_batch b, int cap, int* cls, int* step, int64_t* active_tiles, float* ms,
+                                    double* alg_flops, int* count) {
+  if (!b || cap < 0) return GMRES_ERR_ARG;
+  if (count) *count = (int)b->log.size();
+  const int k = std::min<int>(cap, (int)b->log.size());
+  for (int i = 0; i < k; ++i) {
+    const auto& e = b->log[i];
+    if (cls) cls[i] = e.cls;
+    if (step) step[i] = e.j;
+    if (active_tiles) active_tiles[i] = e.tiles;
+    if (ms) ms[i] = e.ms;
+    if (alg_flops) alg_flops[i] = e.flops;
+  }
   return GMRES_OK;
 }
 

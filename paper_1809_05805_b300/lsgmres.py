@@ -62,8 +62,9 @@ class SolveInfo:
 EXPORTS = ["gmres_create", "gmres_set", "gmres_set_tol", "gmres_set_stream", "gmres_solve",
            "gmres_solve_host", "gmres_history", "gmres_destroy", "gmres_last_error", "lsg_spmv",
            "lsg_block_dot", "lsg_maxpy", "gmres_arnoldi", "gmres_set_profile", "gmres_profile",
-           "lsg_block_dot_noalloc", "gmres_batch_create", "gmres_batch_set_grid", "gmres_batch_get_grid", "gmres_batch_set_stream", "gmres_batch_solve",
-           "gmres_batch_solve_host", "gmres_batch_set_profile", "gmres_batch_profile",
+           "lsg_block_dot_noalloc", "gmres_batch_create", "gmres_batch_set_grid", "gmres_batch_get_grid",
+           "gmres_batch_set_rows_per_thread", "gmres_batch_get_rows_per_thread", "gmres_batch_set_stream", "gmres_batch_solve",
+           "gmres_batch_solve_host", "gmres_batch_set_profile", "gmres_batch_profile", "gmres_batch_launch_log",
            "gmres_batch_history", "gmres_batch_destroy", "gmres_batch_last_error"]
 
 PROFILE_CLASSES = ["one_reduce_step", "arnoldi_maxpy", "mgs_spmv_dot", "mgs_axpy_dot", "residual",
@@ -103,10 +104,13 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "gmres_batch_set_stream": ([P, P], I),
         "gmres_batch_set_grid": ([P, I], I),
         "gmres_batch_get_grid": ([P, ctypes.POINTER(I)], I),
+        "gmres_batch_set_rows_per_thread": ([P, I], I),
+        "gmres_batch_get_rows_per_thread": ([P, ctypes.POINTER(I)], I),
         "gmres_batch_solve": ([P, P, P, ctypes.POINTER(_Info)], I),
         "gmres_batch_history": ([P, I, P, I, ctypes.POINTER(I)], I),
         "gmres_batch_solve_host": ([P, P, P, ctypes.POINTER(_Info)], I),
         "gmres_batch_set_profile": ([P, I], I),
+        "gmres_batch_launch_log": ([P, I, P, P, P, P, P, ctypes.POINTER(I)], I),
         "gmres_batch_profile": ([P, I, ctypes.POINTER(D), ctypes.POINTER(I64), ctypes.POINTER(D),
                                  ctypes.POINTER(D)], I),
         "gmres_batch_destroy": ([P], I),
@@ -311,8 +315,17 @@ class BatchSolver:
         return g.value
 
     def set_grid(self, ctas: int):
-        """Pin the grid of the batched kernels (0: autotune again)."""
+        """Pin the grid of the batched kernels (0: autotune grid and rows per thread again)."""
         self._check(self.lib.gmres_batch_set_grid(self.h, int(ctas)))
+
+    @property
+    def rows_per_thread(self) -> int:
+        r = ctypes.c_int(0)
+        self._check(self.lib.gmres_batch_get_rows_per_thread(self.h, ctypes.byref(r)))
+        return r.value
+
+    def set_rows_per_thread(self, rows: int):
+        self._check(self.lib.gmres_batch_set_rows_per_thread(self.h, int(rows)))
 
     def solve(self, bs, xs, *, allow=(OK, MAXITER)) -> list[SolveInfo]:
         """bs, xs: lists of float64 CUDA tensors (xs hold x0 on entry, solutions on exit)."""
@@ -354,6 +367,21 @@ class BatchSolver:
                                                      ctypes.byref(fl)))
             out[name] = dict(ms=ms.value, launches=cnt.value, bytes=by.value, flops=fl.value)
         return out
+
+    def launch_log(self) -> dict:
+        """Per launch of the last profiled solve: class name, step j, active tiles, ms, algorithmic flops."""
+        cnt = ctypes.c_int(0)
+        self._check(self.lib.gmres_batch_launch_log(self.h, 0, None, None, None, None, None, ctypes.byref(cnt)))
+        k = cnt.value
+        cls = np.zeros(k, np.int32)
+        step = np.zeros(k, np.int32)
+        tiles = np.zeros(k, np.int64)
+        ms = np.zeros(k, np.float32)
+        fl = np.zeros(k, np.float64)
+        self._check(self.lib.gmres_batch_launch_log(self.h, k, _ptr(cls), _ptr(step), _ptr(tiles), _ptr(ms), _ptr(fl),
+                                                    ctypes.byref(cnt)))
+        return dict(cls=np.array(PROFILE_CLASSES)[cls] if k else np.array([], dtype=str), step=step, tiles=tiles,
+                    ms=ms, flops=fl)
 
     def history(self, i: int) -> np.ndarray:
         n = ctypes.c_int(0)

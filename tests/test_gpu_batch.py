@@ -48,10 +48,12 @@ def _systems(count, seed, side):
     return mats, rhs
 
 
-def _solve_batch(torch, lsg, mats, rhs, m, tol, max_iter, grid=None, stream=None, x0s=None, allow=None):
+def _solve_batch(torch, lsg, mats, rhs, m, tol, max_iter, grid=None, stream=None, x0s=None, allow=None, rows=None):
     bs = lsg.BatchSolver(mats, m=m, tol=tol, max_iter=max_iter, stream=stream)
     if grid is not None:
         bs.set_grid(grid)
+    if rows is not None:
+        bs.set_rows_per_thread(rows)
     bd = [torch.from_numpy(b).cuda() for b in rhs]
     xd = [torch.zeros(len(b), dtype=torch.float64, device="cuda") if x0s is None or x0s[i] is None
           else torch.from_numpy(x0s[i]).cuda() for i, b in enumerate(rhs)]
@@ -72,16 +74,20 @@ def _check_against_oracle(orc, A, b, info, x, hist, m, tol, max_iter, x0=None):
     return r
 
 
-@pytest.mark.parametrize("grid", [None, 1, 5, "tiles"])
-def test_batch_matches_oracle_per_system(torch_cuda, lsg, orc, grid):
-    """Nine systems of 9^2 .. 70^2 rows (ragged tiles everywhere), GMRES(20)."""
+@pytest.mark.parametrize("grid,rows", [(None, None), (1, 1), (1, 2), (5, 2), (3, 1), ("tiles", 1)])
+def test_batch_matches_oracle_per_system(torch_cuda, lsg, orc, grid, rows):
+    """Nine systems of 9^2 .. 70^2 rows (ragged tiles everywhere), GMRES(20),
+    for the autotuned launch shape and for pinned grids with one or two rows
+    per thread (tile pairs inside a system, single tiles at odd boundaries)."""
     torch = torch_cuda
     mats, rhs = _systems(9, seed=11, side=(9, 70))
     ntiles = sum((len(A[0]) - 1 + 255) // 256 for A in mats)
     g = ntiles if grid == "tiles" else grid
-    bs, infos, xs, hists = _solve_batch(torch, lsg, mats, rhs, m=20, tol=1e-8, max_iter=3000, grid=g)
+    bs, infos, xs, hists = _solve_batch(torch, lsg, mats, rhs, m=20, tol=1e-8, max_iter=3000, grid=g, rows=rows)
     if g is not None:
         assert bs.grid == g
+    if rows is not None:
+        assert bs.rows_per_thread == rows
     for A, b, info, x, h in zip(mats, rhs, infos, xs, hists):
         assert info.status == 0
         _check_against_oracle(orc, A, b, info, x, h, 20, 1e-8, 3000)
@@ -96,7 +102,7 @@ def test_batch_many_systems_stream_graphs(torch_cuda, lsg, orc):
     torch = torch_cuda
     mats, rhs = _systems(64, seed=5, side=(6, 48))
     bs, infos, xs, hists = _solve_batch(torch, lsg, mats, rhs, m=16, tol=1e-9, max_iter=4000, grid=7,
-                                        stream=torch.cuda.Stream())
+                                        stream=torch.cuda.Stream(), rows=2)
     for i in range(0, 64, 6):
         _check_against_oracle(orc, mats[i], rhs[i], infos[i], xs[i], hists[i], 16, 1e-9, 4000)
     for A, b, info, x in zip(mats, rhs, infos, xs):
@@ -171,6 +177,9 @@ def test_batch_argument_checks(torch_cuda, lsg):
     bs = lsg.BatchSolver(mats, m=5, tol=1e-8)
     with pytest.raises(lsg.GmresError) as e:
         bs.set_grid(10 ** 6)
+    assert e.value.status == lsg.ERR_ARG
+    with pytest.raises(lsg.GmresError) as e:
+        bs.set_rows_per_thread(3)
     assert e.value.status == lsg.ERR_ARG
     with pytest.raises(ValueError):
         bs.solve([torch.zeros(1, dtype=torch.float64, device="cuda")], [])
