@@ -623,7 +623,7 @@ def run_batch(args, w, rank, world, dist):
     step_tflops = st["flops"] / (st["ms"] * 1e-3) / 1e12 if st["ms"] else None
     step_gbs = st["bytes"] / (st["ms"] * 1e-3) / 1e9 if st["ms"] else None
     roofline = {
-        "kernel": "kb_step (batched fused CSR SpMV + block dot + per-system epilogue)",
+        "kernel": "ke_step (batched fused CSR SpMV + block dot, per-group partial sums, per-system epilogue)",
         "bound": "alu", "achieved": step_tflops, "peak": fp64_peak, "unit": "TFLOP/s",
         "frac": step_tflops / fp64_peak if step_tflops else None,
         "peak_source": (f"FP64 pipe derived from unit counts and clock: 148 SMs x {FP64_DFMA_PER_CLK_SM} DFMA/clk x 2 "

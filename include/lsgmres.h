@@ -162,14 +162,19 @@ gmres_status gmres_profile(gmres_handle h, int cls, double* total_ms, int64_t* l
  * batching is this library's addition and changes no system's arithmetic.
  * A batch holds `count` square CSR systems of any sizes. Its solve runs
  * restarted one-reduce MGS-GMRES(m) (FP64) on all of them in lock-step cycles:
- * the systems' rows are concatenated (each padded to whole 256-row tiles) into
- * one block-diagonal matrix and one Krylov basis, and each Arnoldi step of the
- * cycle is one fused SpMV + block-inner-product launch and one MAXPY launch
- * for every system still iterating, with a separate grid reduction and
- * epilogue per system. A system leaves its cycle when its own residual
+ * each system's rows occupy a region of a shared row arena (padded to whole
+ * 512-row tile pairs) in every Krylov basis column, with its own CSR, and each
+ * Arnoldi step of the cycle is one fused SpMV + block-inner-product launch and
+ * one MAXPY launch for every system still iterating, with a grid reduction and
+ * an epilogue per system. A system's results match a solve of it alone up to
+ * the order of the partial sums of its reductions (which depends on the grid
+ * and on the other systems sharing the launches; for a given batch and grid it
+ * is fixed, so results are bitwise reproducible). A system leaves its cycle when its own residual
  * estimate reaches tol and the batch when its true residual does (or after
- * max_iter steps); results equal those of solving each system alone. The
- * grid size of the batched kernels is chosen by a timing autotuner at create.
+ * max_iter steps). Its first residual pass carries ||b|| in the same
+ * reduction as ||r0||, so a batched solve reports one reduction fewer than the
+ * single-system solver. The launch shape (grid, rows per thread) is chosen by
+ * a timing autotuner at create.
  */
 typedef struct gmres_batch_ctx* gmres_batch;
 
@@ -185,17 +190,18 @@ gmres_status gmres_batch_create(const gmres_csr* A, int count, int m_restart, do
 gmres_status gmres_batch_set_stream(gmres_batch bt, void* cuda_stream);
 
 /* Grid of the batched reduction kernels (CTAs; CTA c takes the contiguous
- * range of 256-row tiles [c T / ctas, (c+1) T / ctas) of the T tiles of the
- * batch). ctas = 0 re-runs the autotuner; otherwise 1 <= ctas <= min(T, 8 x
- * the SM count), else GMRES_ERR_ARG. Results are deterministic for a given
- * grid; the grid changes only the order of the partial sums. */
+ * range [c Ta / P, (c+1) Ta / P) of the Ta 256-row tiles of the systems still
+ * iterating, P = min(ctas, Ta)). ctas = 0 re-runs the autotuner; otherwise
+ * 1 <= ctas <= 8 x the SM count, else GMRES_ERR_ARG. The grid changes only
+ * the order of the partial sums. */
 gmres_status gmres_batch_set_grid(gmres_batch bt, int ctas);
 gmres_status gmres_batch_get_grid(gmres_batch bt, int* ctas);
 
 /* Rows per thread of the batched step kernel: 1 (one 256-row tile per CTA
  * iteration) or 2 (two consecutive tiles of one system together, so the CSR
- * loads of two rows are in flight at once); chosen by the autotuner with the
- * grid (gmres_batch_set_grid(bt, 0)). Other values: GMRES_ERR_ARG. */
+ * loads of two rows are in flight at once; the same sums in the same order);
+ * chosen by the autotuner with the grid (gmres_batch_set_grid(bt, 0)). Other
+ * values: GMRES_ERR_ARG. */
 gmres_status gmres_batch_set_rows_per_thread(gmres_batch bt, int rows);
 gmres_status gmres_batch_get_rows_per_thread(gmres_batch bt, int* rows);
 
@@ -223,10 +229,10 @@ gmres_status gmres_batch_profile(gmres_batch bt, int cls, double* total_ms, int6
                                  double* alg_bytes, double* alg_flops);
 
 /* Launch-by-launch record of the last profiled batch solve, in launch order:
- * class (as gmres_profile), step index j (step and MAXPY launches; 0/1 for
- * the norm and residual launches), tiles of 256 rows in the active list at the
- * launch, device ms, algorithmic flops. Any output may be NULL; at most cap
- * entries are written; *count receives the total. */
+ * class (as gmres_profile), step index j (step and MAXPY launches; 1 for the
+ * residual launches), 256-row tiles listed at the launch, device ms,
+ * algorithmic flops. Any output may be NULL; at most cap entries are written;
+ * *count receives the total. */
 gmres_status gmres_batch_launch_log(gmres_batch bt, int cap, int* cls, int* step, int64_t* active_tiles,
                                     float* ms, double* alg_flops, int* count);
 

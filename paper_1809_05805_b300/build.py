@@ -1,7 +1,9 @@
 """Build the CUDA library in-tree for sm_103a (B300).
 
-``python -m paper_1809_05805_b300.build`` compiles ``csrc/lsgmres.cu`` with nvcc
-into ``liblsgmres.so`` beside this file. The result travels with the source
+``python -m paper_1809_05805_b300.build`` compiles the translation units of
+``csrc/`` (``lsgmres.cu``: the single-system solver; ``batch.cu``: the batched
+engine and the serving loop; both include ``common.cuh``) with nvcc into one
+``liblsgmres.so`` beside this file. The result travels with the source
 tree; nothing is installed into site-packages or a JIT cache.
 """
 from __future__ import annotations
@@ -12,7 +14,7 @@ import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
-SRC = os.path.join(HERE, "csrc", "lsgmres.cu")
+SRCS = [os.path.join(HERE, "csrc", f) for f in ("lsgmres.cu", "batch.cu")]
 LIB = os.path.join(HERE, "liblsgmres.so")
 INCLUDE = os.path.join(ROOT, "include")
 
@@ -41,7 +43,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if not force and not stale():
         return LIB
     nvcc = os.environ.get("NVCC", "nvcc")
-    cmd = [nvcc, *NVCC_FLAGS, f"-I{INCLUDE}", SRC, "-o", LIB + ".tmp"]
+    cmd = [nvcc, *NVCC_FLAGS, f"-I{INCLUDE}", *SRCS, "-o", LIB + ".tmp"]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     p = subprocess.run(cmd, capture_output=True, text=True)

@@ -1,0 +1,713 @@
+// Device code shared by the single-system solver (lsgmres.cu) and the batched
+// engine (batch.cu): constants, the per-system state, CSR rows, the fused
+// tile block dot, the deterministic grid reduction, and the small dense
+// epilogues of one-reduce MGS-GMRES (Algorithm 7 on Algorithm 4, Sections II-IV
+// of Swirydowicz et al., arXiv:1809.05805). Internal linkage: each translation
+// unit gets its own copy.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+namespace {
+
+constexpr int kThreads = 256;                // CTA size; also rows per tile
+constexpr int kWarps = kThreads / 32;        // 8
+constexpr int kRowsPerLane = kThreads / 32;  // rows of a tile handled by one lane in the dot phase
+constexpr int kMaxM = 128;                   // largest restart length
+constexpr double kEps = 2.220446049250313e-16;
+constexpr double kBreakdownFactor = 16.0;
+
+// --------------------------------------------------------------------------
+// device state
+// --------------------------------------------------------------------------
+struct DevState {
+  double bnorm;        // ||b|| (or ||r0|| for gmres_arnoldi)
+  double inv_bnorm;    // 1 / bnorm (the residual estimate multiplies; FP64 division is slow)
+  double cycle_scale;  // norm the cycle's right-hand side was divided by (FP32 cycles), else 1
+  double rnorm;        // last true-residual norm
+  double tol;
+  double est;          // last Givens estimate (relative)
+  int step;            // next Arnoldi step of the cycle
+  int inner;           // MGS: next inner-product index within the step
+  int kmax;            // steps allowed in this cycle
+  int k;               // Hessenberg columns completed in this cycle
+  int done;            // cycle finished
+  int converged;
+  int breakdown;
+  int nonfinite;
+  int maxpy_k;         // columns of the pending Arnoldi MAXPY
+  int total_iters;     // over all cycles
+  int restarts;
+  int breakdowns;
+  unsigned int ticket; // last-CTA election
+  int fresh;           // batched engine: the next residual pass also sets bnorm
+  long long reductions;
+  long long grid_syncs;
+  double mgs_coef;     // MGS: coefficient of the pending axpy
+};
+
+// Device pointers into the small dense arrays (one allocation).
+struct Small {
+  DevState* st;
+  double* H;        // (m+1) x m, unrotated, column-major, ld = m+1
+  double* Rg;       // (m+1) x m, rotated
+  double* cs;       // m+1
+  double* sn;       // m+1
+  double* g;        // m+2
+  double* T;        // (m+1) x (m+1), lower, ld = m+1
+  double* scale;    // m+2: 1/||u_k||
+  double* coef;     // m+3: [alpha, c_0 .. c_m] of the pending Arnoldi MAXPY
+  double* coefx;    // m+3: [1, y_0 s_0 .. ] of the solution update
+  double* hist;     // hist_cap
+  double* partials; // P x nvmax
+  double* raw;      // nvmax: standalone block-dot output
+  int m;
+  int ldh;          // m + 1
+  int nvmax;        // 2 (m + 1) + 2
+  int hist_cap;
+};
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Butterfly reduce-scatter of 32 per-lane values over the warp: 31 adds
+// (16 + 8 + 4 + 2 + 1), each lane keeping the half its lane bit selects at
+// every level. On return lane l holds the sum over the 32 lanes of slot l
+// (also returned). Fixed order: bitwise reproducible.
+template <typename T>
+__device__ __forceinline__ T warp_reduce_scatter32(T* v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) {
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int i = 0; i < o; ++i) {
+      const T send = up ? v[i] : v[i + o];
+      const T keep = up ? v[i + o] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+  return v[0];
+}
+
+// Sum one value over the CTA (fixed order); result valid in thread 0.
+__device__ __forceinline__ double block_sum(double v, double* sbuf /* kWarps */) {
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) sbuf[wid] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < kWarps; ++i) t += sbuf[i];
+  }
+  __syncthreads();
+  return t;
+}
+
+// Row i of A times x (CSR, FP64 FMA chain in column order). The loads of up
+// to 8 entries are issued together (predicated), so a stencil row costs two
+// dependent memory latencies (indices, then the gather) instead of two per entry.
+template <typename VT>
+__device__ __forceinline__ VT csr_row(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                                          const VT* __restrict__ val, const VT* __restrict__ x,
+                                          int64_t i) {
+  constexpr int kW = 8;
+  const int p0 = __ldg(rowptr + i), p1 = __ldg(rowptr + i + 1);
+  VT s = VT(0);
+  for (int p = p0; p < p1; p += kW) {
+    int c[kW];
+    VT v[kW], xv[kW];
+#pragma unroll
+    for (int e = 0; e < kW; ++e) {
+      const bool ok = p + e < p1;
+      c[e] = ok ? __ldg(col + p + e) : 0;
+      v[e] = ok ? __ldg(val + p + e) : VT(0);
+    }
+#pragma unroll
+    for (int e = 0; e < kW; ++e) xv[e] = (p + e < p1) ? __ldg(x + c[e]) : VT(0);
+#pragma unroll
+    for (int e = 0; e < kW; ++e)
+      if (p + e < p1) s = fma(v[e], xv[e], s);
+  }
+  return s;
+}
+
+// Rows r0 and r1 of A times x with the loads of both rows in flight together
+// (rows of up to 8 entries; longer rows use csr_row). Rows >= n give 0.
+template <typename VT>
+__device__ __forceinline__ void csr_row2(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                                         const VT* __restrict__ val, const VT* __restrict__ x,
+                                         int64_t r0, int64_t r1, int64_t n, VT& y0, VT& y1) {
+  constexpr int kW = 8;
+  const int a0 = r0 < n ? __ldg(rowptr + r0) : 0, b0 = r0 < n ? __ldg(rowptr + r0 + 1) : 0;
+  const int a1 = r1 < n ? __ldg(rowptr + r1) : 0, b1 = r1 < n ? __ldg(rowptr + r1 + 1) : 0;
+  if (b0 - a0 <= kW && b1 - a1 <= kW) {
+    int c0[kW], c1[kW];
+    VT v0[kW], v1[kW];
+#pragma unroll
+    for (int e = 0; e < kW; ++e) {
+      c0[e] = (a0 + e < b0) ? __ldg(col + a0 + e) : 0;
+      v0[e] = (a0 + e < b0) ? __ldg(val + a0 + e) : VT(0);
+      c1[e] = (a1 + e < b1) ? __ldg(col + a1 + e) : 0;
+      v1[e] = (a1 + e < b1) ? __ldg(val + a1 + e) : VT(0);
+    }
+    VT x0[kW], x1[kW];
+#pragma unroll
+    for (int e = 0; e < kW; ++e) {
+      x0[e] = (a0 + e < b0) ? __ldg(x + c0[e]) : VT(0);
+      x1[e] = (a1 + e < b1) ? __ldg(x + c1[e]) : VT(0);
+    }
+    VT s0 = VT(0), s1 = VT(0);
+#pragma unroll
+    for (int e = 0; e < kW; ++e) {
+      if (a0 + e < b0) s0 = fma(v0[e], x0[e], s0);
+      if (a1 + e < b1) s1 = fma(v1[e], x1[e], s1);
+    }
+    y0 = s0;
+    y1 = s1;
+  } else {
+    y0 = r0 < n ? csr_row(rowptr, col, val, x, r0) : VT(0);
+    y1 = r1 < n ? csr_row(rowptr, col, val, x, r1) : VT(0);
+  }
+}
+
+// Sum nslot rows of partial sums (slots slot0 .. slot0+nslot-1, row stride
+// nvmax) into red[0 .. nv), all threads of the CTA: S threads per value (S a
+// power of two, S * nv <= blockDim) sum slots seg, seg + S, ... in order; the S
+// sums are combined by a fixed xor tree (and, for S > 32, across warps in warp
+// order). The order is independent of timing: results are bitwise reproducible.
+__device__ void reduce_slots(const double* partials, int64_t slot0, int nslot, int nvmax, double* red, int nv) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int S = 1;
+  while (2 * S * nv <= (int)blockDim.x && S < (int)blockDim.x) S *= 2;
+  const int Sw = S < 32 ? S : 32;
+  __shared__ double wred[kThreads / 32];
+  for (int base = 0; base < nv * S; base += blockDim.x) {
+    const int t = base + threadIdx.x;
+    const int v = t / S, seg = t % S;
+    double acc = 0.0;
+    if (v < nv) {
+#pragma unroll 8
+      for (int b = seg; b < nslot; b += S) acc += __ldcg(partials + (size_t)(slot0 + b) * nvmax + v);
+    }
+    for (int o = Sw >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (S > 32) {  // one pass only (S * nv <= blockDim): combine the warps of each value
+      if (lane == 0) wred[wid] = acc;
+      __syncthreads();
+      if ((int)threadIdx.x < nv) {
+        double t2 = 0.0;
+        for (int w = threadIdx.x * (S / 32); w < ((int)threadIdx.x + 1) * (S / 32); ++w) t2 += wred[w];
+        red[threadIdx.x] = t2;
+      }
+    } else if (v < nv && seg == 0) {
+      red[v] = acc;
+    }
+  }
+  __syncthreads();
+}
+
+// Publish this CTA's row `slot` of partial sums (red[0 .. nv)) and take a
+// ticket; returns true in every thread of the CTA that arrived last of
+// `expected`, after which red holds the totals over slots slot0 .. slot0 +
+// expected - 1, and the ticket is reset for the next kernel.
+__device__ bool publish_and_reduce(double* partials, int nvmax, int64_t slot, int64_t slot0, int expected,
+                                   unsigned int* ticket, double* red, int nv) {
+  __shared__ int s_last;
+  for (int v = threadIdx.x; v < nv; v += blockDim.x) partials[(size_t)slot * nvmax + v] = red[v];
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = (atomicAdd(ticket, 1u) == (unsigned)expected - 1);
+  __syncthreads();
+  if (!s_last) return false;
+  __threadfence();
+  reduce_slots(partials, slot0, expected, nvmax, red, nv);
+  if (threadIdx.x == 0) *ticket = 0u;
+  return true;
+}
+
+// Grid-wide form: every CTA of the grid publishes one slot (its block index).
+__device__ bool grid_reduce_last(Small s, double* red, int nv) {
+  if (!publish_and_reduce(s.partials, s.nvmax, blockIdx.x, 0, gridDim.x, &s.st->ticket, red, nv)) return false;
+  if (threadIdx.x == 0) s.st->reductions += 1;
+  return true;
+}
+
+// Column j of H is complete (entries 0..j+1 in global memory). Run by the
+// whole CTA: the column and the stored rotations are staged in shared memory
+// with parallel loads, then thread 0 rotates the column, forms rotation j,
+// updates g, records the residual estimate and decides whether the cycle
+// stops (breakdown, convergence, non-finite, or the last allowed column).
+// Returns the stop decision (0/1) in every thread.
+__device__ int finish_column(Small s, int j, double h, bool last_allowed) {
+  __shared__ double sh_col[kMaxM + 2], sh_c[kMaxM + 1], sh_s[kMaxM + 1];
+  __shared__ int s_res;
+  const int ld = s.ldh;
+  for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) sh_col[i] = s.H[(size_t)j * ld + i];
+  for (int i = threadIdx.x; i < j; i += blockDim.x) {
+    sh_c[i] = s.cs[i];
+    sh_s[i] = s.sn[i];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    DevState* st = s.st;
+    double hn2 = 0.0;  // ||Hbar(0:j+1, j)||^2 for the breakdown test
+    for (int i = 0; i <= j + 1; ++i) hn2 += sh_col[i] * sh_col[i];
+    double* R = sh_col;
+    for (int i = 0; i < j; ++i) {
+      const double c = sh_c[i], sn = sh_s[i];
+      const double t = c * R[i] + sn * R[i + 1];
+      R[i + 1] = -sn * R[i] + c * R[i + 1];
+      R[i] = t;
+    }
+    double c = 1.0, sn = 0.0;
+    if (R[j + 1] != 0.0) {
+      const double irho = 1.0 / hypot(R[j], R[j + 1]);
+      c = R[j] * irho;
+      sn = R[j + 1] * irho;
+    }
+    R[j] = c * R[j] + sn * R[j + 1];
+    R[j + 1] = 0.0;
+    double* Rg = s.Rg + (size_t)j * ld;
+    for (int i = 0; i <= j + 1; ++i) Rg[i] = R[i];
+    s.cs[j] = c;
+    s.sn[j] = sn;
+    const double gj = s.g[j];
+    s.g[j + 1] = -sn * gj;
+    s.g[j] = c * gj;
+    const double est = fabs(sn * gj) * st->cycle_scale * st->inv_bnorm;
+    const int it = st->total_iters + j;
+    if (it < s.hist_cap) s.hist[it] = est;
+    st->k = j + 1;
+    st->est = est;
+    int stop = 0;
+    if (!isfinite(est)) {
+      st->nonfinite = 1;
+      stop = 1;
+    } else if (h <= kBreakdownFactor * kEps * sqrt(hn2)) {
+      st->breakdown = 1;
+      stop = 1;
+    } else if (est <= st->tol) {
+      st->converged = 1;
+      stop = 1;
+    } else if (last_allowed) {
+      stop = 1;
+    }
+    s_res = stop;
+  }
+  __syncthreads();
+  return s_res;
+}
+
+// --------------------------------------------------------------------------
+// one-reduce step: fused SpMV + block dot + epilogue
+// --------------------------------------------------------------------------
+// Step j of a cycle (u_j = column j, not yet normalized; V_{j} = columns 0..j-1):
+//   w = A u_j;
+//   X = [a = U_j^T u_j, c = U_j^T w, sigma = u_j^T u_j, d = u_j^T w]  (one reduction)
+// where U_j holds the unnormalized columns; the epilogue applies scale[k].
+// At j == kmax (the tail) the SpMV and c, d are skipped.
+// Standalone mode (raw_out != nullptr): j is j_arg, w may be an input
+// (use_spmv == 0), and the totals go to raw_out without the GMRES epilogue.
+// One 256-row tile t of the fused SpMV + block dot (one row per thread in the
+// SpMV, the block-dot work split over the 8 warps), accumulated into the
+// caller's per-thread sums. Rows >= n count as zero. Row i of the SpMV is
+// rowptr[i] .. rowptr[i+1] of col/val, gathering xg[col] (a single system
+// passes xg = u; a system stored at rows row0.. of a shared arena passes its
+// own CSR shifted by -row0 and xg = u + row0).
+template <int MAXC, typename VT>
+__device__ __forceinline__ void tile_block_dot(int64_t t, int64_t n, const int32_t* __restrict__ rowptr,
+                                               const int32_t* __restrict__ col, const VT* __restrict__ val,
+                                               const VT* __restrict__ V, int64_t ldv, const VT* __restrict__ u,
+                                               const VT* __restrict__ xg, VT* __restrict__ w, bool spmv,
+                                               bool need_w, int J8, int r8, VT* su,
+                                               VT* sw, VT (&acc_a)[MAXC], VT (&acc_c)[MAXC],
+                                               VT (&rem_a)[kWarps - 1], VT (&rem_c)[kWarps - 1], VT& sig,
+                                               VT& dd) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t row = t * kThreads + threadIdx.x;
+  VT ur = VT(0), wr = VT(0);
+  if (row < n) {
+    ur = u[row];
+    if (spmv) {
+      wr = csr_row(rowptr, col, val, xg, row);
+      w[row] = wr;
+    } else if (need_w) {
+      wr = w[row];
+    }
+  }
+  sig = fma(ur, ur, sig);
+  dd = fma(ur, wr, dd);
+  su[threadIdx.x] = ur;
+  sw[threadIdx.x] = wr;
+  __syncthreads();
+  const int64_t base = t * kThreads + lane;
+  VT ru[kRowsPerLane], rw[kRowsPerLane];
+#pragma unroll
+  for (int q = 0; q < kRowsPerLane; ++q) {
+    ru[q] = su[lane + 32 * q];
+    rw[q] = sw[lane + 32 * q];
+  }
+#pragma unroll
+  for (int c = 0; c < MAXC; ++c) {
+    if (c < J8) {  // warp-uniform
+      const int k = wid + c * kWarps;
+      const VT* vk = V + (size_t)k * ldv + base;
+      VT x[kRowsPerLane];
+#pragma unroll
+      for (int q = 0; q < kRowsPerLane; ++q) x[q] = (base + 32 * q < n) ? __ldg(vk + 32 * q) : VT(0);
+#pragma unroll
+      for (int q = 0; q < kRowsPerLane; ++q) acc_a[c] = fma(x[q], ru[q], acc_a[c]);
+      if (need_w) {  // the cycle's tail needs only V^T u
+#pragma unroll
+        for (int q = 0; q < kRowsPerLane; ++q) acc_c[c] = fma(x[q], rw[q], acc_c[c]);
+      }
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < kWarps - 1; ++c) {
+    if (c < r8) {  // block-uniform
+      const VT x = (row < n) ? __ldg(V + (size_t)(J8 * kWarps + c) * ldv + row) : VT(0);
+      rem_a[c] = fma(x, ur, rem_a[c]);
+      if (need_w) rem_c[c] = fma(x, wr, rem_c[c]);
+    }
+  }
+  __syncthreads();
+}
+
+// Tiles 2 pp and 2 pp + 1 (rows 512 pp .. 512 pp + 511) of the fused SpMV +
+// block dot, two rows per thread: the CSR loads of both rows are in flight
+// together, halving the latency-bound SpMV phases per row. su, sw hold 512
+// values.
+template <int MAXC, typename VT>
+__device__ __forceinline__ void tile_pair_block_dot(int64_t pp, int64_t n, const int32_t* __restrict__ rowptr,
+                                                    const int32_t* __restrict__ col, const VT* __restrict__ val,
+                                                    const VT* __restrict__ V, int64_t ldv, const VT* __restrict__ u,
+                                                    const VT* __restrict__ xg, VT* __restrict__ w, bool spmv,
+                                                    bool need_w, int J8, int r8,
+                                                    VT* su, VT* sw, VT (&acc_a)[MAXC], VT (&acc_c)[MAXC],
+                                                    VT (&rem_a)[kWarps - 1], VT (&rem_c)[kWarps - 1], VT& sig,
+                                                    VT& dd) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t row0 = pp * (2 * kThreads) + threadIdx.x, row1 = row0 + kThreads;
+  VT ur0 = VT(0), wr0 = VT(0), ur1 = VT(0), wr1 = VT(0);
+  if (row0 < n) ur0 = u[row0];
+  if (row1 < n) ur1 = u[row1];
+  if (spmv) {
+    csr_row2(rowptr, col, val, xg, row0, row1, n, wr0, wr1);
+    if (row0 < n) w[row0] = wr0;
+    if (row1 < n) w[row1] = wr1;
+  } else if (need_w) {
+    if (row0 < n) wr0 = w[row0];
+    if (row1 < n) wr1 = w[row1];
+  }
+  sig = fma(ur0, ur0, sig);
+  dd = fma(ur0, wr0, dd);
+  sig = fma(ur1, ur1, sig);
+  dd = fma(ur1, wr1, dd);
+  su[threadIdx.x] = ur0;
+  sw[threadIdx.x] = wr0;
+  su[kThreads + threadIdx.x] = ur1;
+  sw[kThreads + threadIdx.x] = wr1;
+  __syncthreads();
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int64_t base = pp * (2 * kThreads) + h * kThreads + lane;
+    VT ru[kRowsPerLane], rw[kRowsPerLane];
+#pragma unroll
+    for (int q = 0; q < kRowsPerLane; ++q) {
+      ru[q] = su[h * kThreads + lane + 32 * q];
+      rw[q] = sw[h * kThreads + lane + 32 * q];
+    }
+#pragma unroll
+    for (int c = 0; c < MAXC; ++c) {
+      if (c < J8) {  // warp-uniform
+        const int k = wid + c * kWarps;
+        const VT* vk = V + (size_t)k * ldv + base;
+        VT x[kRowsPerLane];
+#pragma unroll
+        for (int q = 0; q < kRowsPerLane; ++q) x[q] = (base + 32 * q < n) ? __ldg(vk + 32 * q) : VT(0);
+#pragma unroll
+        for (int q = 0; q < kRowsPerLane; ++q) acc_a[c] = fma(x[q], ru[q], acc_a[c]);
+        if (need_w) {  // the cycle's tail needs only V^T u
+#pragma unroll
+          for (int q = 0; q < kRowsPerLane; ++q) acc_c[c] = fma(x[q], rw[q], acc_c[c]);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < kWarps - 1; ++c) {
+    if (c < r8) {  // block-uniform
+      const VT* vk = V + (size_t)(J8 * kWarps + c) * ldv;
+      const VT x0 = (row0 < n) ? __ldg(vk + row0) : VT(0);
+      const VT x1 = (row1 < n) ? __ldg(vk + row1) : VT(0);
+      rem_a[c] = fma(x0, ur0, rem_a[c]);
+      rem_a[c] = fma(x1, ur1, rem_a[c]);
+      if (need_w) {
+        rem_c[c] = fma(x0, wr0, rem_c[c]);
+        rem_c[c] = fma(x1, wr1, rem_c[c]);
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// Reduce the per-thread block-dot sums of the CTA into red[0 .. 2j+2).
+template <int MAXC, typename VT>
+__device__ __forceinline__ void cta_partials(VT (&acc_a)[MAXC], VT (&acc_c)[MAXC], VT (&rem_a)[kWarps - 1],
+                                             VT (&rem_c)[kWarps - 1], VT sig, VT dd, int j, int J8, int r8,
+                                             double* red) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  // CTA partials: red[0:j] = a, red[j:2j] = c, red[2j] = sigma, red[2j+1] = d.
+  // Each lane's accumulators are packed into 32-slot chunks and reduced across
+  // the warp by a butterfly reduce-scatter (31 adds per chunk instead of 5 per
+  // value): lane l then holds the warp total of slot l.
+  constexpr int kSlots = 2 * MAXC + 2 * (kWarps - 1) + 2;
+  constexpr int kChunks = (kSlots + 31) / 32;
+  VT v[kChunks * 32];
+#pragma unroll
+  for (int i = 0; i < kChunks * 32; ++i) v[i] = VT(0);
+#pragma unroll
+  for (int c = 0; c < MAXC; ++c) {
+    v[c] = acc_a[c];
+    v[MAXC + c] = acc_c[c];
+  }
+#pragma unroll
+  for (int c = 0; c < kWarps - 1; ++c) {
+    v[2 * MAXC + c] = rem_a[c];
+    v[2 * MAXC + kWarps - 1 + c] = rem_c[c];
+  }
+  v[kSlots - 2] = sig;
+  v[kSlots - 1] = dd;
+  __shared__ VT scross[kSlots - 2 * MAXC][kWarps];  // slots summed across warps
+#pragma unroll
+  for (int ch = 0; ch < kChunks; ++ch) {
+    const VT tot = warp_reduce_scatter32(v + 32 * ch);
+    const int slot = 32 * ch + lane;
+    if (slot < MAXC) {
+      if (slot < J8) red[wid + slot * kWarps] = tot;  // column wid + 8 slot belongs to this warp
+    } else if (slot < 2 * MAXC) {
+      if (slot - MAXC < J8) red[j + wid + (slot - MAXC) * kWarps] = tot;
+    } else if (slot < kSlots) {
+      scross[slot - 2 * MAXC][wid] = tot;
+    }
+  }
+  __syncthreads();
+  // remainder columns and the two norms: sum the 8 warps in warp order
+  if ((int)threadIdx.x < kSlots - 2 * MAXC) {
+    const int q = threadIdx.x;
+    double t2 = 0.0;
+    for (int w2 = 0; w2 < kWarps; ++w2) t2 += scross[q][w2];
+    if (q < kWarps - 1) {
+      if (q < r8) red[J8 * kWarps + q] = t2;
+    } else if (q < 2 * (kWarps - 1)) {
+      if (q - (kWarps - 1) < r8) red[j + J8 * kWarps + q - (kWarps - 1)] = t2;
+    } else {
+      red[2 * j + (q - 2 * (kWarps - 1))] = t2;
+    }
+  }
+  __syncthreads();
+}
+
+// The one-reduce epilogue (last CTA), given the grid totals red[0 .. 2j+2) of
+// step j: lagged norm, completion of column j-1 at the tail, T row, r = T s,
+// the new Hessenberg column and the MAXPY coefficients.
+__device__ void epilogue_one_reduce(Small s, double* red, int j, bool tail) {
+  DevState* st = s.st;
+  // ---------------- epilogue (last CTA) ----------------
+  // stop: 0 = continue the cycle; 1 = cycle done after the T row (converged
+  // or tail); 2 = cycle done now (breakdown, zero or non-finite norm); 3 =
+  // exact breakdown found, column j-1 still to be finished (then 2).
+  // T (rows and columns 0..j-1) and scale[0..j-1] are staged in shared memory
+  // (dynamic, (m+1)^2 + (m+1) doubles) so the O(j^2) work reads no global memory.
+  extern __shared__ double dyn[];
+  const int ld = s.ldh;
+  double* sT = dyn;                       // (m+1) x (m+1), column-major, ld
+  double* sScale = dyn + (size_t)ld * ld; // m+1
+  __shared__ double s_beta;
+  __shared__ int s_stop;
+  for (int e = threadIdx.x; e < j * j; e += blockDim.x) {
+    const int k = e / j, i = e % j;  // column k, row i
+    if (i >= k) sT[(size_t)k * ld + i] = s.T[(size_t)k * ld + i];
+  }
+  for (int i = threadIdx.x; i < j; i += blockDim.x) sScale[i] = s.scale[i];
+  if (threadIdx.x == 0) {
+    st->grid_syncs += 1;
+    const double beta = sqrt(red[2 * j]);
+    int stop = 0;
+    if (!isfinite(beta)) {
+      st->nonfinite = 1;
+      stop = 2;
+    } else if (j == 0) {
+      if (beta == 0.0) stop = 2;  // r0 = 0: the host never starts such a cycle
+      else s.g[0] = beta;
+    } else {
+      s.H[(size_t)(j - 1) * ld + j] = beta;  // H(j, j-1): the lagged norm completes column j-1
+    }
+    if (isfinite(beta) && beta != 0.0) s.scale[j] = 1.0 / beta;
+    s_beta = beta;
+    s_stop = stop;
+  }
+  __syncthreads();
+  // exact breakdown (u_j = 0): column j-1 is still rotated (its h = 0 makes the
+  // estimate exact), then the cycle ends without forming v_j (no 1/0)
+  if (threadIdx.x == 0 && s_stop == 0 && j > 0 && s_beta == 0.0) s_stop = 3;
+  __syncthreads();
+  // Column j-1 is now complete. Except at the cycle's tail (or an exact
+  // breakdown), its Givens rotation and the convergence test run in the
+  // following MAXPY launch (one extra CTA beside the streaming CTAs): they are a
+  // chain of dependent FP64 operations at ~64 cycles each on this part and are
+  // not needed by the MAXPY.
+  if (j > 0 && (s_stop == 3 || (s_stop == 0 && tail))) {
+    const bool exact = (s_stop == 3);
+    const int fin = finish_column(s, j - 1, s_beta, tail);
+    if (threadIdx.x == 0) {
+      if (exact || st->breakdown || st->nonfinite) s_stop = 2;
+      else if (fin) s_stop = 1;
+    }
+    __syncthreads();
+  }
+  if (s_stop == 2) {
+    if (threadIdx.x == 0) st->done = 1;
+    return;
+  }
+  const double ib = 1.0 / s_beta;
+  if (threadIdx.x == 0) sScale[j] = ib;
+  // ell = (U_j^T u_j) scaled to v_k^T v_j
+  for (int i = threadIdx.x; i < j; i += blockDim.x) red[i] = red[i] * sScale[i] * ib;
+  __syncthreads();
+  // row j of T = (I + L)^{-1}: T(j, k) = -sum_{i=k}^{j-1} ell_i T(i, k). Each sum
+  // is split into 4 interleaved partial sums on different warps (shorter
+  // dependent FP64 chains), combined in a fixed order.
+  __shared__ double spart[4][kMaxM + 1];
+  for (int t = threadIdx.x; t < 4 * j; t += blockDim.x) {
+    const int seg = t / j, k = t % j;
+    double p = 0.0;
+    for (int i = k + seg; i < j; i += 4) p = fma(red[i], sT[(size_t)k * ld + i], p);
+    spart[seg][k] = p;
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < j; k += blockDim.x) {
+    const double t = -(((spart[0][k] + spart[1][k]) + spart[2][k]) + spart[3][k]);
+    sT[(size_t)k * ld + j] = t;
+    s.T[(size_t)k * ld + j] = t;
+  }
+  if (threadIdx.x == 0) {
+    sT[(size_t)j * ld + j] = 1.0;
+    s.T[(size_t)j * ld + j] = 1.0;
+  }
+  __syncthreads();
+  if (s_stop) {
+    if (threadIdx.x == 0) st->done = 1;
+    return;
+  }
+  // s = [c * scale / beta ; d / beta^2]
+  __shared__ double sv[kMaxM + 1];
+  for (int i = threadIdx.x; i <= j; i += blockDim.x)
+    sv[i] = (i < j) ? red[j + i] * sScale[i] * ib : red[2 * j + 1] * ib * ib;
+  __syncthreads();
+  // r = T s (4 interleaved partial sums per entry); H(0:j, j) = r; MAXPY coefficients
+  for (int t = threadIdx.x; t < 4 * (j + 1); t += blockDim.x) {
+    const int seg = t / (j + 1), i = t % (j + 1);
+    double p = 0.0;
+    for (int k = seg; k <= i; k += 4) p = fma(sT[(size_t)k * ld + i], sv[k], p);
+    spart[seg][i] = p;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i <= j; i += blockDim.x) {
+    const double t = ((spart[0][i] + spart[1][i]) + spart[2][i]) + spart[3][i];
+    s.H[(size_t)j * ld + i] = t;
+    s.coef[1 + i] = -t * sScale[i];
+  }
+  if (threadIdx.x == 0) {
+    s.coef[0] = ib;
+    st->maxpy_k = j + 1;
+    st->step = j + 1;
+  }}
+
+// --------------------------------------------------------------------------
+// residual, norms, least squares, export
+// --------------------------------------------------------------------------
+enum { RES_BNORM = 0, RES_RESIDUAL = 1, RES_START = 2 };
+
+// End of a residual / norm kernel for one system (thread 0): store the norm
+// and, for a cycle start, reset the cycle state.
+__device__ void residual_finish(Small s, double sumsq, int mode, int kmax) {
+  DevState* st = s.st;
+  st->grid_syncs += 1;
+  const double nr = sqrt(sumsq);
+  if (mode == RES_BNORM) {
+    st->bnorm = nr;
+    st->inv_bnorm = 1.0 / nr;
+    return;
+  }
+  if (mode == RES_START) {
+    st->bnorm = nr;
+    st->inv_bnorm = 1.0 / nr;
+  }
+  st->rnorm = nr;
+  st->cycle_scale = 1.0;
+  st->step = 0;
+  st->inner = 0;
+  st->kmax = kmax;
+  st->k = 0;
+  st->done = 0;
+  st->converged = 0;
+  st->breakdown = 0;
+  st->nonfinite = isfinite(nr) ? 0 : 1;
+  st->maxpy_k = 0;
+  s.g[0] = nr;
+  s.scale[0] = 1.0 / nr;
+  for (int i = 1; i <= s.m + 1; ++i) s.g[i] = 0.0;
+}
+
+// Back substitution R(0:k,0:k) y = g(0:k) (column-oriented), then the
+// coefficients of x += V_k y in the unnormalized basis, and the cycle totals.
+// The k x k triangle of the rotated Hessenberg is staged in shared memory
+// (dynamic, (m+1) x m doubles) so each of the k sequential steps is a
+// shared-memory update, not a global-memory round trip.
+__device__ void lsq_system(Small s) {
+  extern __shared__ double sR[];
+  __shared__ double y[kMaxM + 1];
+  __shared__ int sk;
+  DevState* st = s.st;
+  if (threadIdx.x == 0) sk = st->k;
+  __syncthreads();
+  const int k = sk;
+  const int ld = s.ldh;
+  for (int e = threadIdx.x; e < k * ld; e += blockDim.x) sR[e] = s.Rg[e];
+  __shared__ double rinv[kMaxM + 1];
+  for (int l = threadIdx.x; l < k; l += blockDim.x) y[l] = s.g[l];
+  __syncthreads();
+  for (int l = threadIdx.x; l < k; l += blockDim.x) rinv[l] = 1.0 / sR[(size_t)l * ld + l];
+  __syncthreads();
+  for (int i = k - 1; i >= 0; --i) {
+    if (threadIdx.x == 0) y[i] = y[i] * rinv[i];
+    __syncthreads();
+    const double yi = y[i];
+    for (int l = threadIdx.x; l < i; l += blockDim.x) y[l] = fma(-sR[(size_t)i * ld + l], yi, y[l]);
+    __syncthreads();
+  }
+  const double cs = st->cycle_scale;
+  for (int l = threadIdx.x; l < k; l += blockDim.x) s.coefx[1 + l] = y[l] * s.scale[l] * cs;
+  if (threadIdx.x == 0) {
+    s.coefx[0] = 1.0;
+    st->total_iters += k;
+    st->restarts += 1;
+    st->breakdowns += st->breakdown;
+  }
+}
+
+// Kernel classes of the per-launch profiles (gmres_profile, gmres_batch_profile).
+enum { PC_STEP = 0, PC_MAXPY = 1, PC_MGS_SPMV = 2, PC_MGS_AXPY = 3, PC_RES = 4, PC_LSQ = 5, PC_XUPD = 6,
+       PC_NOOP = 7 };
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+}  // namespace

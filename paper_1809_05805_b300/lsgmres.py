@@ -369,7 +369,7 @@ class BatchSolver:
         return out
 
     def launch_log(self) -> dict:
-        """Per launch of the last profiled solve: class name, step j, active tiles, ms, algorithmic flops."""
+        """Per launch of the last profiled solve: class name, step j, listed tiles, ms, algorithmic flops."""
         cnt = ctypes.c_int(0)
         self._check(self.lib.gmres_batch_launch_log(self.h, 0, None, None, None, None, None, ctypes.byref(cnt)))
         k = cnt.value
@@ -378,8 +378,8 @@ class BatchSolver:
         tiles = np.zeros(k, np.int64)
         ms = np.zeros(k, np.float32)
         fl = np.zeros(k, np.float64)
-        self._check(self.lib.gmres_batch_launch_log(self.h, k, _ptr(cls), _ptr(step), _ptr(tiles), _ptr(ms), _ptr(fl),
-                                                    ctypes.byref(cnt)))
+        self._check(self.lib.gmres_batch_launch_log(self.h, k, _ptr(cls), _ptr(step), _ptr(tiles), _ptr(ms),
+                                                    _ptr(fl), ctypes.byref(cnt)))
         return dict(cls=np.array(PROFILE_CLASSES)[cls] if k else np.array([], dtype=str), step=step, tiles=tiles,
                     ms=ms, flops=fl)
 
