@@ -7,14 +7,20 @@ x_true ~ U[-1, 1] from PCG64(0), b = A x_true, x0 = 0. One step is one
 complete solve (every Arnoldi step, restart and solution update on the GPU).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload 256|128|32|192|144|batch512|batch64] [--no-mgs]
-                  [--no-cpu-baseline]
+                  [--workload 256|128|32|192|144|batch512|batch64|serve|serve_small]
+                  [--no-mgs] [--no-cpu-baseline]
 
 --workload batch512: 512 independent 2D 9-point variable-coefficient
 convection-diffusion systems (grid side log-uniform in 32..256, cell diffusion
 log-uniform in [0.1, 10], cell Peclet U[0, 2], seeded), GMRES(30) to 1e-8, all
 solved together by the batched solver against the same systems solved one
 after another.
+
+--workload serve: 256 requests arriving as a Poisson stream at 2000 req/s
+(3D 7-point convection-diffusion, n log-uniform in 4k..2M, 70% FP64 / 30%
+GMRES-IR, each to 1e-8) served by one continuous-batching server; reports
+solves/s and p50/p99 latency, a run at half the measured capacity, and the
+same requests one at a time on the single-system solver.
 
 Prints one JSON line (rank 0). With N > 1 (torchrun) every rank solves its own
 replica of the system (no data-path collective); the time is the maximum
@@ -53,6 +59,16 @@ BATCH_WORKLOADS = {
     "batch64": dict(count=64, side=(32, 256), m=30, tol=1e-8, max_iter=20000, seed=0),  # profiling size
 }
 METRIC_BATCH = "time-to-solve (1e-8 rel. resid) of a batch of uneven systems, batched one-reduce MGS-GMRES"
+# serving: Poisson arrivals of 3D 7-point convection-diffusion solves, n
+# log-uniform in n_range (cube side rounded onto `sides` log-spaced values),
+# 70% FP64 / 30% GMRES-IR, each to 1e-8, one continuous-batching server
+SERVE_WORKLOADS = {
+    "serve": dict(rate=2000.0, requests=256, n_range=(4096, 2_000_000), sides=16, ir_frac=0.3, m=30, tol=1e-8,
+                  max_iter=3000, budget=64 << 30, max_requests=256, seed=0),
+    "serve_small": dict(rate=2000.0, requests=48, n_range=(4096, 262_144), sides=8, ir_frac=0.3, m=30, tol=1e-8,
+                        max_iter=3000, budget=16 << 30, max_requests=64, seed=0),  # profiling size
+}
+METRIC_SERVE = "solves/s at 2000 req/s offered (1e-8 rel. resid each), continuous-batching serving loop; p50/p99 latency"
 METRIC = "time-to-solve (1e-8 rel. resid), one-reduce MGS-GMRES"
 METRIC_IR = "time-to-solve (1e-10 rel. resid), GMRES-IR: one-reduce cycles in FP32, FP64 restarts"
 
@@ -667,19 +683,268 @@ def run_batch(args, w, rank, world, dist):
     return 0
 
 
+# ----------------------------------------------------------------------------- serving workload
+def serve_requests(w):
+    """Seeded request stream: arrival times, cube sides, precisions, and the
+    systems (one matrix per distinct side, b = A x_true per request)."""
+    rng = np.random.default_rng(w["seed"])
+    k = w["requests"]
+    arrivals = np.cumsum(rng.exponential(1.0 / w["rate"], k))
+    arrivals -= arrivals[0]
+    lo, hi = w["n_range"]
+    n = np.exp(rng.uniform(np.log(lo), np.log(hi), k))
+    grid = np.unique(np.round(np.exp(np.linspace(np.log(lo ** (1 / 3)), np.log(hi ** (1 / 3)), w["sides"]))))
+    sides = grid[np.abs(np.log(grid)[None, :] - np.log(np.cbrt(n))[:, None]).argmin(axis=1)].astype(int)
+    precs = np.where(rng.random(k) < w["ir_frac"], "ir_fp32", "fp64")
+    mats = {N: P.conv_diff_7pt(int(N)) for N in np.unique(sides)}
+    reqs = []
+    for i in range(k):
+        A = mats[int(sides[i])]
+        reqs.append(dict(A=A, b=P.rhs(A, seed=1000 + i)[1], prec=str(precs[i]), t=float(arrivals[i]),
+                         n=int(sides[i]) ** 3))
+    return reqs
+
+
+def serve_run(lsgmres, sv, reqs, w, time_scale=1.0):
+    """Submit the requests at their arrival times (multiplied by time_scale)
+    from one thread, wait for all; returns wall time, latencies and the
+    solutions."""
+    import threading
+
+    xs = [np.zeros(r["n"]) for r in reqs]
+    ids = [None] * len(reqs)
+    slip = np.zeros(len(reqs))
+    t0 = time.perf_counter()
+
+    def feed():
+        for i, r in enumerate(reqs):
+            due = t0 + r["t"] * time_scale
+            dt = due - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+            slip[i] = max(0.0, time.perf_counter() - due)
+            ids[i] = sv.submit(r["A"], r["b"], xs[i], tol=w["tol"], prec=r["prec"], max_iter=w["max_iter"])
+
+    th = threading.Thread(target=feed)
+    th.start()
+    th.join()
+    sv.drain(timeout=900)
+    wall = time.perf_counter() - t0
+    infos = [sv.wait(i, timeout=10) for i in ids]
+    # latency from the scheduled arrival: the submit thread's delay plus the
+    # server's submit-to-completion time
+    lat = np.array([i.seconds for i in infos]) + slip
+    for i in ids:
+        sv.release(i)
+    return wall, lat, infos, xs
+
+
+def run_serve(args, w, rank, world, dist):
+    import torch
+
+    from paper_1809_05805_b300 import lsgmres
+
+    lsgmres.load()  # fails loudly when the CUDA library is missing
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    peaks = load_peaks()
+    reqs = serve_requests(w)
+    k = len(reqs)
+    sv = lsgmres.Server(m=w["m"], max_iter=w["max_iter"], max_requests=w["max_requests"],
+                        hbm_budget_bytes=w["budget"], ir_share=w["ir_frac"])
+    # warm-up: graph capture of the cycle shapes and first-touch costs
+    for _ in range(max(1, args.warmup)):
+        serve_run(lsgmres, sv, reqs[: min(16, k)], w)
+    sv.set_profile(True)
+    with ClockSampler(local) as clk:
+        walls, lats, all_infos, xs_last = [], [], None, None
+        for _ in range(args.steps):
+            wall, lat, infos, xs = serve_run(lsgmres, sv, reqs, w)
+            walls.append(wall)
+            lats.append(lat)
+            all_infos, xs_last = infos, xs
+    clocks = clk.summary()
+    st = sv.stats()
+    prof = [sv.profile(0), sv.profile(1)]
+    lat = np.concatenate(lats)
+    wall = float(np.mean(walls))
+    thr = k / wall
+    true_rel = [float(np.linalg.norm(r["b"] - P.to_scipy(r["A"]) @ x) / np.linalg.norm(r["b"]))
+                for r, x in zip(reqs, xs_last)]
+    # sustainable load: half the measured throughput, same requests
+    sv.set_profile(False)
+    rate_s = 0.5 * thr
+    wall_s, lat_s, _, _ = serve_run(lsgmres, sv, reqs, w, time_scale=w["rate"] / rate_s)
+    sv.close()
+
+    # baseline: the same requests one at a time in arrival order by the
+    # single-system solver (FIFO queue simulated from the measured solve times)
+    seq = None
+    if not args.no_mgs:
+        stream = torch.cuda.Stream()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        solo = []
+        cache = {}
+        for r in reqs:
+            key = (r["n"], r["prec"])
+            if key not in cache:
+                cache[key] = lsgmres.Solver(r["A"], m=w["m"], tol=w["tol"], max_iter=w["max_iter"], stream=stream,
+                                            prec=r["prec"])
+            s1 = cache[key]
+            bd = torch.from_numpy(r["b"]).cuda()
+            x1 = torch.zeros(r["n"], dtype=torch.float64, device="cuda")
+            s1.solve(bd, x1)  # graph capture for this shape
+            x1.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            s1.solve(bd, x1)
+            x1.cpu()
+            solo.append(time.perf_counter() - t0)
+        for s1 in cache.values():
+            s1.close()
+        arr = np.array([r["t"] for r in reqs])
+        end = 0.0
+        lat_q = []
+        for a, d in zip(arr, solo):
+            end = max(end, a) + d
+            lat_q.append(end - a)
+        seq = {"solves_per_s": k / end, "latency_p50_s": float(np.percentile(lat_q, 50)),
+               "latency_p99_s": float(np.percentile(lat_q, 99)), "solo_solve_s_sum": float(np.sum(solo)),
+               "note": "each request alone on the single-system solver (graphs on one stream), FIFO in arrival "
+                       "order; queueing simulated from the measured solve times"}
+
+    st0, st1 = prof[0]["one_reduce_step"], prof[1]["one_reduce_step"]
+    fp64_peak = 148 * FP64_DFMA_PER_CLK_SM * 2 * float(peaks.get("sm_max_mhz", 2032.0)) * 1e6 / 1e12
+    hbm = float(peaks.get("hbm_gbs", 6400.0))
+    tf0 = st0["flops"] / (st0["ms"] * 1e-3) / 1e12 if st0["ms"] else None
+    gbs1 = st1["bytes"] / (st1["ms"] * 1e-3) / 1e9 if st1["ms"] else None
+    roofline = {
+        "kernel": "ke_step<double> (FP64 engine: fused CSR SpMV + block dot + per-request epilogue)",
+        "bound": "alu", "achieved": tf0, "peak": fp64_peak, "unit": "TFLOP/s",
+        "frac": tf0 / fp64_peak if tf0 else None,
+        "peak_source": (f"FP64 pipe derived from unit counts and clock: 148 SMs x {FP64_DFMA_PER_CLK_SM} DFMA/clk x 2 "
+                        f"flop x {peaks.get('sm_max_mhz', 2032.0):g} MHz (nominal 1.25 TFLOP/s)"),
+        "traffic": None, "launch_avg_ms": st0["ms"] / max(st0["launches"], 1), "launches": st0["launches"],
+        "hbm_gbs": st0["bytes"] / (st0["ms"] * 1e-3) / 1e9 if st0["ms"] else None,
+        "ir_engine_step": {"kernel": "ke_step<float>", "bound": "hbm", "achieved_gbs": gbs1, "peak_gbs": hbm,
+                           "frac": gbs1 / hbm if gbs1 else None, "launches": st1["launches"]},
+    }
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        from oracle import Oracle
+
+        orc = Oracle()
+        t_tot, work_s, cnt = 0.0, 0.0, 0
+        for i in range(0, k, 4):
+            r = reqs[i]
+            if r["n"] > 300_000:  # keep the sample to seconds; the scaling below accounts for size
+                continue
+            t0 = time.perf_counter()
+            ro = orc.gmres(r["A"], r["b"], variant=1 if r["prec"] == "fp64" else 2, m=w["m"], tol=w["tol"],
+                           max_iter=w["max_iter"])
+            t_tot += time.perf_counter() - t0
+            work_s += r["n"] * ro.iters
+            cnt += 1
+            if t_tot >= 15.0:
+                break
+        work_all = sum(r["n"] * i.iters for r, i in zip(reqs, all_infos))
+        cpu_s = t_tot * work_all / work_s
+        cpu = {"value": k / cpu_s, "unit": "solves/s", "cores": 1, "kind": "oracle",
+               "sample": f"complete oracle solves of {cnt} requests (every 4th with n <= 300k, until 15 s: "
+                         f"{t_tot:.1f} s), scaled to all {k} requests by sum(n_i * iters_i)"}
+    ntot = sum(r["n"] for r in reqs)
+    line = {
+        "metric": METRIC_SERVE, "value": thr, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * wall, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64 / f32 cycles (GMRES-IR)",
+        "data": "synthetic (seeded 3D 7-point stencils, x_true ~ U[-1,1], Poisson arrivals)",
+        "config": {"workload": (f"{k} requests, Poisson arrivals at {w['rate']:g}/s, 3D 7-point convection-diffusion, "
+                                f"n log-uniform {w['n_range'][0]}..{w['n_range'][1]} (cube side on {w['sides']} "
+                                f"log-spaced values), {int(100 * (1 - w['ir_frac']))}% FP64 / "
+                                f"{int(100 * w['ir_frac'])}% GMRES-IR, GMRES({w['m']}) to {w['tol']:g} each"),
+                   "requests": k, "total_unknowns": ntot, "hbm_budget_bytes": w["budget"],
+                   "max_requests_per_engine": w["max_requests"], "parallelism": "1 GPU, 2 engines / streams",
+                   "l2": "each engine's arena and bases exceed L2; no flush",
+                   "timing": "host wall clock from the first arrival to the last completion (requests from host "
+                             "buffers, solutions back to host buffers)"},
+        "latency_p50_s": float(np.percentile(lat, 50)), "latency_p99_s": float(np.percentile(lat, 99)),
+        "makespan_s": wall,
+        "sustained": {"offered_rate": rate_s, "solves_per_s": k / wall_s,
+                      "latency_p50_s": float(np.percentile(lat_s, 50)),
+                      "latency_p99_s": float(np.percentile(lat_s, 99))},
+        "all_converged": all(i.status == 0 for i in all_infos), "max_rel_resid_true": max(true_rel),
+        "server": {"peak_running": st["peak_running"], "cycles": st["cycles"], "engine_bytes": st["engine_bytes"],
+                   "peak_bytes_in_use": st["peak_bytes_in_use"]},
+        "sequential": seq,
+        "speedup_vs_sequential": (thr / seq["solves_per_s"]) if seq else None,
+        "e2e": {"value": thr, "unit": "solves/s", "h2d_bytes_per_step": int(sum(8 * r["n"] + 12 * len(r["A"][1])
+                                                                            for r in reqs)),
+                "d2h_bytes_per_step": int(8 * ntot)},
+        "gpu_launches": int(sum(st["kernel_launches"])),
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "clocks": clocks,
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    return 0
+
+
+def run_serve_reference(args, w, rank):
+    if rank != 0:
+        return 0
+    reqs = serve_requests(w)
+    from oracle import Oracle
+
+    orc = Oracle()
+    vals = []
+    cnt = 0
+    for s in range(args.warmup + args.steps):
+        t_tot, n_s = 0.0, 0.0
+        cnt = 0
+        for i in range(0, len(reqs), 16):
+            r = reqs[i]
+            t0 = time.perf_counter()
+            orc.gmres(r["A"], r["b"], variant=1 if r["prec"] == "fp64" else 2, m=w["m"], tol=w["tol"],
+                      max_iter=w["max_iter"])
+            t_tot += time.perf_counter() - t0
+            n_s += r["n"]
+            cnt += 1
+            if t_tot >= 8.0:
+                break
+        total_s = t_tot * sum(r["n"] for r in reqs) / n_s
+        if s >= args.warmup:
+            vals.append(len(reqs) / total_s)
+    v = float(np.mean(vals))
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC_SERVE, "value": v, "unit": "solves/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * len(reqs) / v, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{len(reqs)} requests of the serving stream, solved one after another by the oracle"},
+        "cpu_baseline": {"value": v, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                         "sample": f"complete oracle solves of {cnt} requests (every 16th) per step, scaled by "
+                                   f"total n / sample n"},
+        "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=[str(k) for k in sorted(WORKLOADS)] + sorted(BATCH_WORKLOADS),
-                    default="256")
+    ap.add_argument("--workload", choices=[str(k) for k in sorted(WORKLOADS)] + sorted(BATCH_WORKLOADS)
+                    + sorted(SERVE_WORKLOADS), default="256")
     ap.add_argument("--no-mgs", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     batch = args.workload in BATCH_WORKLOADS
-    w = BATCH_WORKLOADS[args.workload] if batch else WORKLOADS[int(args.workload)]
+    serve = args.workload in SERVE_WORKLOADS
+    w = (BATCH_WORKLOADS[args.workload] if batch else SERVE_WORKLOADS[args.workload] if serve
+         else WORKLOADS[int(args.workload)])
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     dist = None
@@ -695,6 +960,10 @@ def main():
             dist_mod.init_process_group("nccl")
             dist = dist_mod
     try:
+        if serve:
+            if args.impl == "reference":
+                return run_serve_reference(args, w, rank)
+            return run_serve(args, w, rank, world, dist)
         if batch:
             if args.impl == "reference":
                 return run_batch_reference(args, w, rank)

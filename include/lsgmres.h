@@ -245,6 +245,100 @@ gmres_status gmres_batch_destroy(gmres_batch bt);
 const char* gmres_batch_last_error(gmres_batch bt);
 
 /* ------------------------------------------------------------------------
+ * Serving loop: continuous batching of independent solves.
+ * ------------------------------------------------------------------------
+ * Not in the paper (which defines the method for one system); each request is
+ * solved by the paper's one-reduce MGS-GMRES (Algorithm 7), FP64 or with FP32
+ * cycles inside FP64 restarts (GMRES_IR_FP32), exactly as a batch would.
+ * A server owns two batched engines, one per precision, each with its own
+ * CUDA stream and host worker thread, so their launches overlap on the
+ * device. Each engine's device memory (Krylov bases and vectors for a fixed
+ * number of arena rows, a CSR pool, per-request state) is allocated once at
+ * create from its share of hbm_budget_bytes. A worker runs lock-step restart
+ * cycles over its iterating requests; at every cycle boundary it completes
+ * the requests whose true residual reached their tol (copying x to x_out) and,
+ * while the next cycle runs, admits queued requests first come first served
+ * as long as arena rows, CSR pool space and a request slot are free. A request
+ * thus starts at the next cycle boundary of its engine after room frees up,
+ * and its Krylov basis stays on the device until it completes. Results equal a
+ * solve of the request alone up to the order of the partial sums of its
+ * reductions (which depends on the requests sharing its launches). */
+typedef struct gmres_server_ctx* gmres_server;
+
+typedef struct {
+  int m_restart;             /* restart length of every request, 1..128 */
+  int max_iter;              /* largest per-request max_iter accepted (sizes the histories) */
+  int max_requests;          /* request slots per engine (requests iterating at once) */
+  int64_t hbm_budget_bytes;  /* device bytes of both engines together */
+  double ir_share;           /* fraction of the budget for the GMRES_IR_FP32 engine, 0..1 */
+  int64_t nnz_per_row_hint;  /* expected nonzeros per row: splits an engine's bytes between arena rows and CSR */
+} gmres_server_config;
+
+typedef struct {
+  int64_t submitted, rejected;       /* all requests; rejected at submit (too large for their engine) */
+  int64_t admitted[2], completed[2]; /* per engine: [0] FP64, [1] GMRES_IR_FP32 */
+  int64_t queued[2], running[2], peak_running[2], cycles[2];
+  int64_t engine_bytes[2];           /* device bytes the engine holds (arena + CSR pool) */
+  int64_t peak_bytes_in_use[2];      /* largest arena + CSR bytes occupied by admitted requests */
+  int64_t arena_rows[2];
+  int64_t kernel_launches[2];        /* engine kernel launches since create */
+  double busy_seconds[2];            /* worker time with requests in flight */
+  double wall_seconds;               /* since create */
+} gmres_server_counters;
+
+/* Create a server on the current device and start its workers. Errors:
+ * GMRES_ERR_ARG (a field out of range), GMRES_ERR_OOM (the budget does not fit
+ * on the device), GMRES_ERR_CUDA; details in gmres_server_last_error(NULL). */
+gmres_status gmres_server_create(const gmres_server_config* cfg, gmres_server* out);
+
+/* Queue a request (O(1): the full CSR check runs when the request is admitted,
+ * and a request failing it completes with GMRES_ERR_ARG): A is a host CSR,
+ * b and x0 (may be NULL:
+ * zero) host or device vectors of A->n doubles, x_out where the solution is
+ * written at completion (host or device). A, b, x0 and x_out are borrowed:
+ * they must stay valid and unchanged until the request completes. prec is
+ * GMRES_FP64 or GMRES_IR_FP32; 0 <= max_iter <= cfg.max_iter. *id receives the
+ * request's id. Errors: GMRES_ERR_ARG, GMRES_ERR_OOM (larger than its
+ * engine's whole share of the budget: the request is rejected). */
+gmres_status gmres_server_submit(gmres_server sv, const gmres_csr* A, const double* b, const double* x0,
+                                 double* x_out, double tol, int prec, int max_iter, int64_t* id);
+
+/* Completion of request id: *done = 1 when x_out holds its result; then info
+ * (may be NULL) receives its counts, status and info.seconds = its latency
+ * from submit to completion. */
+gmres_status gmres_server_poll(gmres_server sv, int64_t id, int* done, gmres_info* info);
+
+/* Block until request id completes (returns its status if negative, else
+ * GMRES_OK) or timeout_s passes (GMRES_ERR_TIMEOUT). */
+gmres_status gmres_server_wait(gmres_server sv, int64_t id, double timeout_s, gmres_info* info);
+
+/* Block until every submitted request has completed (or GMRES_ERR_TIMEOUT). */
+gmres_status gmres_server_drain(gmres_server sv, double timeout_s);
+
+/* Forget a completed request (its id becomes unknown). */
+gmres_status gmres_server_release(gmres_server sv, int64_t id);
+
+gmres_status gmres_server_stats(gmres_server sv, gmres_server_counters* st);
+
+/* Per-launch timing of the engines' kernels (as gmres_set_profile /
+ * gmres_profile; engine 0 = FP64, 1 = GMRES_IR_FP32). Switching is allowed
+ * only while no request is queued or running (GMRES_ERR_ARG otherwise) and
+ * resets the totals. */
+gmres_status gmres_server_set_profile(gmres_server sv, int on);
+gmres_status gmres_server_profile(gmres_server sv, int engine, int cls, double* total_ms, int64_t* launches,
+                                  double* alg_bytes, double* alg_flops);
+
+/* Latencies (seconds, submit to completion) of the completed requests, in
+ * completion order; at most cap written, *len receives the total. */
+gmres_status gmres_server_latencies(gmres_server sv, double* buf, int cap, int* len);
+
+/* Stop: queued requests are dropped (never complete); requests already
+ * admitted run to completion first. */
+gmres_status gmres_server_destroy(gmres_server sv);
+
+const char* gmres_server_last_error(gmres_server sv);
+
+/* ------------------------------------------------------------------------
  * Single steps of the solve path, exposed for parity tests.
  * ------------------------------------------------------------------------ */
 

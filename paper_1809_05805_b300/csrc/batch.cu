@@ -1086,14 +1086,14 @@ struct Engine {
   }
 
   // One cycle boundary for every active slot: (re)list, residual pass, and
-  // the decisions. Slots whose solve ended are marked finished (their x is
-  // final in the arena) and returned in `ended`. If any slot goes on, its
-  // cycle, least squares and solution update are queued (not synchronized).
-  gmres_status boundary(std::vector<int>& ended, bool* any_active) {
+  // the decisions (synchronizes the stream). Slots whose solve ended are
+  // marked finished (their x is final in the arena) and returned in `ended`;
+  // the others, with their step budgets set, in `go`.
+  gmres_status residual_decide(std::vector<int>& ended, std::vector<int>& go) {
     ended.clear();
+    go.clear();
     std::vector<int> act;
     active_slots(act);
-    *any_active = false;
     if (act.empty()) return GMRES_OK;
     gmres_status st;
     if (listing_dirty || act != listed) {
@@ -1115,8 +1115,6 @@ struct Engine {
     ETRY(cudaMemcpyAsync(h_states, d_states, sizeof(DevState) * slot.size(), cudaMemcpyDeviceToHost, stream));
     ETRY(cudaStreamSynchronize(stream));
     prof_settle();
-    int KM = 0;
-    std::vector<int> go;
     for (int s : act) {
       Slot& sl = slot[s];
       DevState& hs = h_states[s];
@@ -1146,18 +1144,26 @@ struct Engine {
         ended.push_back(s);
       } else {
         hs.kmax = std::min(cfg.m, sl.max_iter - hs.total_iters);
-        KM = std::max(KM, hs.kmax);
         sl.it_prev = hs.total_iters;
         cyc_kmax[s] = hs.kmax;
         cyc_it0[s] = hs.total_iters;
         go.push_back(s);
       }
     }
-    if (go.empty()) return GMRES_OK;
-    *any_active = true;
     // the stream is idle and h_states mirrors the device: write back the
     // host's decisions (kmax, done) in one copy
     ETRY(cudaMemcpyAsync(d_states, h_states, sizeof(DevState) * slot.size(), cudaMemcpyHostToDevice, stream));
+    return GMRES_OK;
+  }
+
+  // Queue the cycle of the slots in `go` (as returned by residual_decide, the
+  // stream not used since): listing, FP32 start vector, the cycle's steps,
+  // least squares and solution update. Not synchronized.
+  gmres_status launch_next(const std::vector<int>& go) {
+    if (go.empty()) return GMRES_OK;
+    gmres_status st;
+    int KM = 0;
+    for (int s : go) KM = std::max(KM, h_states[s].kmax);
     if (go != listed && (st = write_listing(go)) != GMRES_OK) return st;
     const EngDev d2 = dev();
     const int ng = stream_grid();
@@ -1166,7 +1172,7 @@ struct Engine {
       ++launches;
     }
     if ((st = run_cycle(KM)) != GMRES_OK) return st;
-    pr = prof_begin(PC_LSQ, 0, 0.0, 0.0);
+    int pr = prof_begin(PC_LSQ, 0, 0.0, 0.0);
     ke_lsq<<<(int)slot.size(), 128, lsq_smem, stream>>>(d2);
     prof_end(pr);
     pr = prof_begin(PC_XUPD, 0);
@@ -1343,10 +1349,11 @@ gmres_status batch_solve(gmres_batch b, const double* const* bv, double* const* 
   gmres_status st;
   for (int i = 0; i < b->S; ++i)
     if ((st = beng(b, e.activate(b->slots[i], bv[i], xv[i], b->tol, b->max_iter))) != GMRES_OK) return st;
-  std::vector<int> ended;
-  bool more = true;
-  while (more)
-    if ((st = beng(b, e.boundary(ended, &more))) != GMRES_OK) return st;
+  std::vector<int> ended, go;
+  do {
+    if ((st = beng(b, e.residual_decide(ended, go))) != GMRES_OK) return st;
+    if ((st = beng(b, e.launch_next(go))) != GMRES_OK) return st;
+  } while (!go.empty());
   for (int i = 0; i < b->S; ++i) {
     const Engine::Slot& sl = e.slot[b->slots[i]];
     if (cudaMemcpyAsync(xv[i], e.xv + sl.row0, 8 * (size_t)sl.n, cudaMemcpyDefault, e.stream) != cudaSuccess)
@@ -1518,6 +1525,406 @@ gmres_status gmres_batch_history(gmres_batch b, int i, double* buf, int cap, int
   const auto& h = b->hist[i];
   if (len) *len = (int)h.size();
   if (buf && cap > 0) std::memcpy(buf, h.data(), sizeof(double) * std::min<size_t>(cap, h.size()));
+  return GMRES_OK;
+}
+
+}  // extern "C"
+
+// ==========================================================================
+// serving loop
+// ==========================================================================
+// Two engines (FP64 cycles, FP32 cycles inside FP64 restarts), each with its
+// own stream and worker thread, so their launches overlap on the device. A
+// worker repeats: residual pass and decisions for its iterating requests;
+// copy the finished ones' solutions out and complete them; queue the next
+// cycle; then, while that cycle runs, admit queued requests (first come,
+// first served) as long as its arena rows, CSR pool and slots allow: they join
+// at the next cycle boundary. The device footprint of each engine is fixed at
+// create from the byte budget, so admission never allocates.
+namespace {
+
+struct Request {
+  int64_t id = 0;
+  gmres_csr A{};
+  const double* b = nullptr;
+  const double* x0 = nullptr;
+  double* x_out = nullptr;
+  double tol = 0.0;
+  int prec = GMRES_FP64;
+  int max_iter = 0;
+  int slot = -1;
+  bool done = false;
+  gmres_info info{};
+  std::chrono::steady_clock::time_point t_submit, t_admit, t_done;
+};
+
+struct Worker {
+  Engine eng;
+  std::thread th;
+  std::deque<Request*> queue;
+  std::vector<Request*> running;  // by slot
+  int64_t admitted = 0, completed = 0, cycles = 0, peak_rows = 0, peak_csr_units = 0, peak_running = 0;
+  double busy_s = 0.0;
+};
+
+}  // namespace
+
+struct gmres_server_ctx {
+  gmres_server_config cfg{};
+  Worker w[2];  // 0: FP64, 1: GMRES-IR FP32
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  bool stop = false;
+  int64_t next_id = 1, submitted = 0, rejected = 0;
+  std::map<int64_t, std::unique_ptr<Request>> reqs;
+  std::vector<double> latencies;  // seconds, completion order
+  std::string err, worker_err;
+  int device = 0;
+  std::chrono::steady_clock::time_point t0;
+};
+
+namespace {
+
+std::string g_server_err;
+
+gmres_status sfail(gmres_server_ctx* sv, gmres_status st, const std::string& m) {
+  if (sv)
+    sv->err = m;
+  else
+    g_server_err = m;
+  return st;
+}
+
+// Admit queued requests of worker k, first come first served, while the head
+// fits (called by the worker with the lock released; only the worker touches
+// its engine). The full CSR check runs here, off the submitting thread.
+void admit(gmres_server_ctx* sv, int k) {
+  Worker& W = sv->w[k];
+  Engine& e = W.eng;
+  for (;;) {
+    Request* r;
+    {
+      std::lock_guard<std::mutex> lk(sv->mu);
+      if (W.queue.empty()) break;
+      r = W.queue.front();
+      if (!e.fits_now(r->A.n, r->A.nnz)) break;  // wait for room
+      W.queue.pop_front();
+    }
+    const std::string bad = validate_csr(r->A, 0);
+    int s = -1;
+    gmres_status st = GMRES_ERR_ARG;
+    if (bad.empty()) {
+      s = e.add(r->A);
+      st = s < 0 ? GMRES_ERR_CUDA : e.activate(s, r->b, r->x0, r->tol, r->max_iter);
+    }
+    std::lock_guard<std::mutex> lk(sv->mu);
+    if (st != GMRES_OK) {
+      if (s >= 0) e.remove(s);
+      if (!bad.empty()) sv->err = bad;
+      r->info.status = st;
+      r->done = true;
+      r->t_done = std::chrono::steady_clock::now();
+      sv->cv_done.notify_all();
+      continue;
+    }
+    r->slot = s;
+    r->t_admit = std::chrono::steady_clock::now();
+    W.running[s] = r;
+    ++W.admitted;
+    W.peak_rows = std::max(W.peak_rows, e.rows.used());
+    W.peak_csr_units = std::max(W.peak_csr_units, e.csr.used());
+    int64_t nrun = 0;
+    for (Request* q : W.running) nrun += q != nullptr;
+    W.peak_running = std::max(W.peak_running, nrun);
+  }
+}
+
+void worker_loop(gmres_server_ctx* sv, int k) {
+  Worker& W = sv->w[k];
+  Engine& e = W.eng;
+  cudaSetDevice(sv->device);
+  std::vector<int> ended, go;
+  for (;;) {
+    admit(sv, k);
+    {
+      std::unique_lock<std::mutex> lk(sv->mu);
+      bool any = false;
+      for (Request* q : W.running) any |= q != nullptr;
+      if (!any) {
+        if (sv->stop) return;
+        sv->cv_work.wait(lk, [&] { return sv->stop || !W.queue.empty(); });
+        continue;
+      }
+    }
+    const auto tb = std::chrono::steady_clock::now();
+    gmres_status st = e.residual_decide(ended, go);
+    // solutions of the finished requests go out before the next cycle is queued
+    for (int s : ended) {
+      Request* r = W.running[s];
+      cudaMemcpyAsync(r->x_out, e.xv + e.slot[s].row0, 8 * (size_t)e.slot[s].n, cudaMemcpyDefault, e.stream);
+    }
+    if (!ended.empty()) cudaStreamSynchronize(e.stream);
+    const auto td = std::chrono::steady_clock::now();
+    if (st == GMRES_OK) st = e.launch_next(go);
+    {
+      std::lock_guard<std::mutex> lk(sv->mu);
+      for (int s : ended) {
+        Request* r = W.running[s];
+        e.info_of(s, &r->info);
+        r->t_done = td;
+        r->info.seconds = std::chrono::duration<double>(td - r->t_submit).count();
+        r->done = true;
+        sv->latencies.push_back(r->info.seconds);
+        W.running[s] = nullptr;
+        e.remove(s);
+        ++W.completed;
+      }
+      if (!go.empty()) ++W.cycles;
+      if (st != GMRES_OK) {  // a CUDA failure ends every request of this engine
+        sv->worker_err = e.err;
+        for (Request*& q : W.running)
+          if (q) {
+            q->info.status = st;
+            q->done = true;
+            e.remove(q->slot);
+            q = nullptr;
+          }
+      }
+      W.busy_s += std::chrono::duration<double>(std::chrono::steady_clock::now() - tb).count();
+    }
+    sv->cv_done.notify_all();
+    // the loop's next admit() runs while the queued cycle executes (its copies
+    // are ordered after the cycle on the engine's stream)
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* gmres_server_last_error(gmres_server sv) { return sv ? sv->err.c_str() : g_server_err.c_str(); }
+
+gmres_status gmres_server_destroy(gmres_server sv) {
+  if (!sv) return GMRES_OK;
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    sv->stop = true;
+    for (Worker& W : sv->w) W.queue.clear();
+  }
+  sv->cv_work.notify_all();
+  for (Worker& W : sv->w)
+    if (W.th.joinable()) W.th.join();
+  for (Worker& W : sv->w)
+    if (W.eng.stream) cudaStreamDestroy(W.eng.stream);
+  delete sv;
+  return GMRES_OK;
+}
+
+gmres_status gmres_server_create(const gmres_server_config* cfg, gmres_server* out) {
+  if (!out) return sfail(nullptr, GMRES_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!cfg) return sfail(nullptr, GMRES_ERR_ARG, "cfg is NULL");
+  if (cfg->m_restart < 1 || cfg->m_restart > kMaxM) return sfail(nullptr, GMRES_ERR_ARG, "m_restart must be in [1, 128]");
+  if (cfg->max_iter < 1 || cfg->max_requests < 1 || cfg->hbm_budget_bytes <= 0 || !(cfg->ir_share >= 0.0) ||
+      cfg->ir_share > 1.0 || cfg->nnz_per_row_hint < 1)
+    return sfail(nullptr, GMRES_ERR_ARG,
+                 "need max_iter >= 1, max_requests >= 1, hbm_budget_bytes > 0, 0 <= ir_share <= 1, "
+                 "nnz_per_row_hint >= 1");
+  gmres_server_ctx* sv = new gmres_server_ctx();
+  sv->cfg = *cfg;
+  sv->t0 = std::chrono::steady_clock::now();
+  int nsm = 0;
+  if (cudaGetDevice(&sv->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, sv->device) != cudaSuccess) {
+    delete sv;
+    return sfail(nullptr, GMRES_ERR_CUDA, "no CUDA device");
+  }
+  for (int k = 0; k < 2; ++k) {
+    const double share = k == 0 ? 1.0 - cfg->ir_share : cfg->ir_share;
+    const int64_t budget = (int64_t)(share * (double)cfg->hbm_budget_bytes);
+    EngineConfig c;
+    c.m = cfg->m_restart;
+    c.prec = k == 0 ? GMRES_FP64 : GMRES_IR_FP32;
+    c.max_systems = cfg->max_requests;
+    c.max_iter_cap = cfg->max_iter;
+    // fixed per-slot state, then rows and CSR in proportion to a row's needs
+    const int ld = c.m + 1;
+    const int64_t per_slot = 8 * (int64_t)(2 * ld * c.m + ld * ld + 6 * ld + c.max_iter_cap + ld) + 256 * 12;
+    const int64_t vb = k == 0 ? 8 : 4;
+    const int64_t per_row = vb * (c.m + 2) + 16 + (k == 1 ? 8 : 0);
+    const int64_t csr_row = 4 + cfg->nnz_per_row_hint * (12 + (k == 1 ? 4 : 0));
+    // reduction slots: (largest grid + slots) rows of 2 (m+1) + 2 partial sums
+    const int64_t partials = 8 * ((int64_t)kMaxGridPerSm * nsm + c.max_systems + 1) * (2 * ld + 2);
+    const int64_t avail = budget - per_slot * c.max_systems - partials;
+    if (share > 0.0 && avail > (per_row + csr_row) * kPairRows) {
+      c.rows = avail / (per_row + csr_row) / kPairRows * kPairRows;
+      c.csr_bytes = c.rows * csr_row;
+    } else {
+      c.rows = 0;  // this engine takes no requests
+    }
+    Worker& W = sv->w[k];
+    if (c.rows > 0) {
+      if (W.eng.init(c) != GMRES_OK) {
+        g_server_err = "engine " + std::to_string(k) + ": " + W.eng.err;
+        gmres_server_destroy(sv);
+        return GMRES_ERR_OOM;
+      }
+      cudaStreamCreateWithFlags(&W.eng.stream, cudaStreamNonBlocking);
+      W.running.assign(c.max_systems, nullptr);
+      W.th = std::thread(worker_loop, sv, k);
+    }
+  }
+  *out = sv;
+  return GMRES_OK;
+}
+
+gmres_status gmres_server_submit(gmres_server sv, const gmres_csr* A, const double* b, const double* x0,
+                                 double* x_out, double tol, int prec, int max_iter, int64_t* id) {
+  if (!sv) return GMRES_ERR_ARG;
+  if (!A || !b || !x_out || !id) return sfail(sv, GMRES_ERR_ARG, "A, b, x_out and id must not be NULL");
+  if (prec != GMRES_FP64 && prec != GMRES_IR_FP32) return sfail(sv, GMRES_ERR_ARG, "prec must be FP64 or IR_FP32");
+  if (!(tol >= 0.0) || max_iter < 0 || max_iter > sv->cfg.max_iter)
+    return sfail(sv, GMRES_ERR_ARG, "need tol >= 0 and 0 <= max_iter <= the server's max_iter");
+  // O(1) checks here; the full CSR scan runs at admission, on the worker
+  if (A->on_device || !A->rowptr || A->n <= 0 || A->nnz < 0 || (A->nnz > 0 && (!A->col || !A->val)) ||
+      A->n >= (int64_t)INT32_MAX || A->nnz >= (int64_t)INT32_MAX || A->rowptr[0] != 0 || A->rowptr[A->n] != A->nnz)
+    return sfail(sv, GMRES_ERR_ARG, "need a host CSR with n > 0, rowptr[0] = 0 and rowptr[n] = nnz");
+  const int k = prec == GMRES_FP64 ? 0 : 1;
+  Worker& W = sv->w[k];
+  if (W.eng.R == 0 || !W.eng.fits_ever(A->n, A->nnz)) {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    ++sv->rejected;
+    return sfail(sv, GMRES_ERR_OOM, "request larger than its engine's share of the byte budget");
+  }
+  auto r = std::make_unique<Request>();
+  r->A = *A;
+  r->b = b;
+  r->x0 = x0;
+  r->x_out = x_out;
+  r->tol = tol;
+  r->prec = prec;
+  r->max_iter = max_iter;
+  r->t_submit = std::chrono::steady_clock::now();
+  {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    r->id = sv->next_id++;
+    *id = r->id;
+    W.queue.push_back(r.get());
+    sv->reqs[r->id] = std::move(r);
+    ++sv->submitted;
+  }
+  sv->cv_work.notify_all();
+  return GMRES_OK;
+}
+
+gmres_status gmres_server_poll(gmres_server sv, int64_t id, int* done, gmres_info* info) {
+  if (!sv || !done) return GMRES_ERR_ARG;
+  std::lock_guard<std::mutex> lk(sv->mu);
+  auto it = sv->reqs.find(id);
+  if (it == sv->reqs.end()) return sfail(sv, GMRES_ERR_ARG, "unknown request id");
+  *done = it->second->done;
+  if (*done && info) *info = it->second->info;
+  return GMRES_OK;
+}
+
+gmres_status gmres_server_wait(gmres_server sv, int64_t id, double timeout_s, gmres_info* info) {
+  if (!sv) return GMRES_ERR_ARG;
+  std::unique_lock<std::mutex> lk(sv->mu);
+  auto it = sv->reqs.find(id);
+  if (it == sv->reqs.end()) return sfail(sv, GMRES_ERR_ARG, "unknown request id");
+  Request* r = it->second.get();
+  const auto until = std::chrono::steady_clock::now() + std::chrono::duration_cast<std::chrono::steady_clock::duration>(
+                                                            std::chrono::duration<double>(std::max(0.0, timeout_s)));
+  if (!sv->cv_done.wait_until(lk, until, [&] { return r->done; })) return GMRES_ERR_TIMEOUT;
+  if (info) *info = r->info;
+  return (gmres_status)(r->info.status < 0 ? r->info.status : GMRES_OK);
+}
+
+gmres_status gmres_server_drain(gmres_server sv, double timeout_s) {
+  if (!sv) return GMRES_ERR_ARG;
+  std::unique_lock<std::mutex> lk(sv->mu);
+  const auto until = std::chrono::steady_clock::now() + std::chrono::duration_cast<std::chrono::steady_clock::duration>(
+                                                            std::chrono::duration<double>(std::max(0.0, timeout_s)));
+  const bool ok = sv->cv_done.wait_until(lk, until, [&] {
+    for (auto& kv : sv->reqs)
+      if (!kv.second->done) return false;
+    return true;
+  });
+  return ok ? GMRES_OK : GMRES_ERR_TIMEOUT;
+}
+
+gmres_status gmres_server_release(gmres_server sv, int64_t id) {
+  if (!sv) return GMRES_ERR_ARG;
+  std::lock_guard<std::mutex> lk(sv->mu);
+  auto it = sv->reqs.find(id);
+  if (it == sv->reqs.end()) return sfail(sv, GMRES_ERR_ARG, "unknown request id");
+  if (!it->second->done) return sfail(sv, GMRES_ERR_ARG, "request still in flight");
+  sv->reqs.erase(it);
+  return GMRES_OK;
+}
+
+gmres_status gmres_server_stats(gmres_server sv, gmres_server_counters* st) {
+  if (!sv || !st) return GMRES_ERR_ARG;
+  std::lock_guard<std::mutex> lk(sv->mu);
+  std::memset(st, 0, sizeof(*st));
+  st->submitted = sv->submitted;
+  st->rejected = sv->rejected;
+  for (int k = 0; k < 2; ++k) {
+    const Worker& W = sv->w[k];
+    const Engine& e = W.eng;
+    st->admitted[k] = W.admitted;
+    st->completed[k] = W.completed;
+    st->queued[k] = (int64_t)W.queue.size();
+    int64_t nrun = 0;
+    for (Request* q : W.running) nrun += q != nullptr;
+    st->running[k] = nrun;
+    st->peak_running[k] = W.peak_running;
+    st->cycles[k] = W.cycles;
+    st->busy_seconds[k] = W.busy_s;
+    st->kernel_launches[k] = e.launches;
+    const int64_t row_bytes = (int64_t)e.vb * (e.cfg.m + 2) + 16 + (k == 1 ? 8 : 0);
+    st->engine_bytes[k] = e.R > 0 ? (int64_t)Engine::footprint(e.cfg) : 0;
+    st->peak_bytes_in_use[k] = W.peak_rows * kPairRows * row_bytes + W.peak_csr_units * 256;
+    st->arena_rows[k] = e.R;
+  }
+  st->wall_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - sv->t0).count();
+  return GMRES_OK;
+}
+
+gmres_status gmres_server_set_profile(gmres_server sv, int on) {
+  if (!sv) return GMRES_ERR_ARG;
+  std::lock_guard<std::mutex> lk(sv->mu);
+  for (Worker& W : sv->w) {
+    bool busy = !W.queue.empty();
+    for (Request* q : W.running) busy |= q != nullptr;
+    if (busy) return sfail(sv, GMRES_ERR_ARG, "profiling can be switched only while the server is idle");
+  }
+  for (Worker& W : sv->w) {
+    W.eng.prof_on = on != 0;
+    W.eng.prof_reset();
+  }
+  return GMRES_OK;
+}
+
+gmres_status gmres_server_profile(gmres_server sv, int engine, int cls, double* total_ms, int64_t* launches,
+                                  double* alg_bytes, double* alg_flops) {
+  if (!sv || engine < 0 || engine > 1) return GMRES_ERR_ARG;
+  if (cls < 0 || cls >= GMRES_PROFILE_CLASSES) return sfail(sv, GMRES_ERR_ARG, "profile class out of range");
+  std::lock_guard<std::mutex> lk(sv->mu);
+  const Engine& e = sv->w[engine].eng;
+  if (total_ms) *total_ms = e.prof_ms[cls];
+  if (launches) *launches = e.prof_cnt[cls];
+  if (alg_bytes) *alg_bytes = e.prof_bytes[cls];
+  if (alg_flops) *alg_flops = e.prof_flops[cls];
+  return GMRES_OK;
+}
+
+gmres_status gmres_server_latencies(gmres_server sv, double* buf, int cap, int* len) {
+  if (!sv) return GMRES_ERR_ARG;
+  std::lock_guard<std::mutex> lk(sv->mu);
+  if (len) *len = (int)sv->latencies.size();
+  if (buf && cap > 0)
+    std::memcpy(buf, sv->latencies.data(), sizeof(double) * std::min<size_t>(cap, sv->latencies.size()));
   return GMRES_OK;
 }
 

@@ -45,6 +45,23 @@ class _Info(ctypes.Structure):
                 ("seconds", ctypes.c_double)]
 
 
+class _ServerConfig(ctypes.Structure):
+    _fields_ = [("m_restart", ctypes.c_int), ("max_iter", ctypes.c_int), ("max_requests", ctypes.c_int),
+                ("hbm_budget_bytes", ctypes.c_int64), ("ir_share", ctypes.c_double),
+                ("nnz_per_row_hint", ctypes.c_int64)]
+
+
+_I64x2 = ctypes.c_int64 * 2
+
+
+class _ServerCounters(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("rejected", ctypes.c_int64), ("admitted", _I64x2),
+                ("completed", _I64x2), ("queued", _I64x2), ("running", _I64x2), ("peak_running", _I64x2),
+                ("cycles", _I64x2), ("engine_bytes", _I64x2), ("peak_bytes_in_use", _I64x2),
+                ("arena_rows", _I64x2), ("kernel_launches", _I64x2), ("busy_seconds", ctypes.c_double * 2),
+                ("wall_seconds", ctypes.c_double)]
+
+
 @dataclass
 class SolveInfo:
     status: int
@@ -65,7 +82,10 @@ EXPORTS = ["gmres_create", "gmres_set", "gmres_set_tol", "gmres_set_stream", "gm
            "lsg_block_dot_noalloc", "gmres_batch_create", "gmres_batch_set_grid", "gmres_batch_get_grid",
            "gmres_batch_set_rows_per_thread", "gmres_batch_get_rows_per_thread", "gmres_batch_set_stream", "gmres_batch_solve",
            "gmres_batch_solve_host", "gmres_batch_set_profile", "gmres_batch_profile", "gmres_batch_launch_log",
-           "gmres_batch_history", "gmres_batch_destroy", "gmres_batch_last_error"]
+           "gmres_batch_history", "gmres_batch_destroy", "gmres_batch_last_error", "gmres_server_create",
+           "gmres_server_submit", "gmres_server_poll", "gmres_server_wait", "gmres_server_drain",
+           "gmres_server_release", "gmres_server_stats", "gmres_server_latencies", "gmres_server_destroy",
+           "gmres_server_last_error", "gmres_server_set_profile", "gmres_server_profile"]
 
 PROFILE_CLASSES = ["one_reduce_step", "arnoldi_maxpy", "mgs_spmv_dot", "mgs_axpy_dot", "residual",
                    "least_squares", "x_update", "noop"]
@@ -115,6 +135,19 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
                                  ctypes.POINTER(D)], I),
         "gmres_batch_destroy": ([P], I),
         "gmres_batch_last_error": ([P], ctypes.c_char_p),
+        "gmres_server_create": ([ctypes.POINTER(_ServerConfig), ctypes.POINTER(P)], I),
+        "gmres_server_submit": ([P, ctypes.POINTER(_Csr), P, P, P, D, I, I, ctypes.POINTER(I64)], I),
+        "gmres_server_poll": ([P, I64, ctypes.POINTER(I), ctypes.POINTER(_Info)], I),
+        "gmres_server_wait": ([P, I64, D, ctypes.POINTER(_Info)], I),
+        "gmres_server_drain": ([P, D], I),
+        "gmres_server_release": ([P, I64], I),
+        "gmres_server_stats": ([P, ctypes.POINTER(_ServerCounters)], I),
+        "gmres_server_latencies": ([P, P, I, ctypes.POINTER(I)], I),
+        "gmres_server_destroy": ([P], I),
+        "gmres_server_last_error": ([P], ctypes.c_char_p),
+        "gmres_server_set_profile": ([P, I], I),
+        "gmres_server_profile": ([P, I, I, ctypes.POINTER(D), ctypes.POINTER(I64), ctypes.POINTER(D),
+                                  ctypes.POINTER(D)], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -394,6 +427,118 @@ class BatchSolver:
         if getattr(self, "h", None):
             self.lib.gmres_batch_destroy(self.h)
             self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching solve server (gmres_server_*): requests of any size,
+    FP64 or GMRES-IR, are admitted at cycle boundaries under a device byte
+    budget and iterate together; one worker thread and CUDA stream per
+    precision."""
+
+    def __init__(self, *, m: int = 30, max_iter: int = 3000, max_requests: int = 256,
+                 hbm_budget_bytes: int = 16 << 30, ir_share: float = 0.3, nnz_per_row_hint: int = 7):
+        lib = load()
+        self.lib = lib
+        cfg = _ServerConfig(m, max_iter, max_requests, int(hbm_budget_bytes), float(ir_share), int(nnz_per_row_hint))
+        h = ctypes.c_void_p()
+        st = lib.gmres_server_create(ctypes.byref(cfg), ctypes.byref(h))
+        if st != OK:
+            raise GmresError(st, lib.gmres_server_last_error(None).decode())
+        self.h = h
+        self.m, self.max_iter = m, max_iter
+        self._refs = {}
+
+    def _check(self, st: int, allow=(OK,)):
+        if st not in allow:
+            raise GmresError(st, self.lib.gmres_server_last_error(self.h).decode())
+        return st
+
+    def submit(self, A, b, x_out, *, tol: float, prec: str | int = "fp64", max_iter: int | None = None,
+               x0=None) -> int:
+        """A = (rowptr, col, val) host arrays; b, x0, x_out float64 numpy arrays or CUDA tensors. The arrays
+        are kept referenced here until the request is waited for or released."""
+        rowptr = np.ascontiguousarray(A[0], dtype=np.int32)
+        col = np.ascontiguousarray(A[1], dtype=np.int32)
+        val = np.ascontiguousarray(A[2], dtype=np.float64)
+        n = len(rowptr) - 1
+        for a, nm in ((b, "b"), (x_out, "x_out"), (x0, "x0")):
+            if a is None:
+                continue
+            if isinstance(a, np.ndarray):
+                if not (a.dtype == np.float64 and a.flags.c_contiguous and a.size >= n):
+                    raise TypeError(f"{nm} must be a contiguous float64 array of {n} entries")
+            else:
+                _dev_f64(a, n, nm)
+        csr = _Csr(n, len(col), _ptr(rowptr), _ptr(col), _ptr(val), 0)
+        pr = PREC[prec] if isinstance(prec, str) else int(prec)
+        rid = ctypes.c_int64(0)
+        self._check(self.lib.gmres_server_submit(self.h, ctypes.byref(csr), _ptr(b), _ptr(x0), _ptr(x_out), tol, pr,
+                                                 self.max_iter if max_iter is None else int(max_iter),
+                                                 ctypes.byref(rid)))
+        self._refs[rid.value] = (rowptr, col, val, b, x0, x_out)
+        return rid.value
+
+    def poll(self, rid: int):
+        done = ctypes.c_int(0)
+        info = _Info()
+        self._check(self.lib.gmres_server_poll(self.h, rid, ctypes.byref(done), ctypes.byref(info)))
+        return bool(done.value), (_info(info) if done.value else None)
+
+    def wait(self, rid: int, timeout: float = 600.0) -> SolveInfo:
+        info = _Info()
+        st = self.lib.gmres_server_wait(self.h, rid, timeout, ctypes.byref(info))
+        if st == ERR_TIMEOUT:
+            raise TimeoutError(f"request {rid} not done after {timeout} s")
+        return _info(info)
+
+    def drain(self, timeout: float = 600.0):
+        if self.lib.gmres_server_drain(self.h, timeout) == ERR_TIMEOUT:
+            raise TimeoutError(f"requests still in flight after {timeout} s")
+
+    def release(self, rid: int):
+        self._check(self.lib.gmres_server_release(self.h, rid))
+        self._refs.pop(rid, None)
+
+    def stats(self) -> dict:
+        c = _ServerCounters()
+        self._check(self.lib.gmres_server_stats(self.h, ctypes.byref(c)))
+        out = {}
+        for name, _ in _ServerCounters._fields_:
+            v = getattr(c, name)
+            out[name] = list(v) if hasattr(v, "__len__") else v
+        return out
+
+    def set_profile(self, on: bool):
+        self._check(self.lib.gmres_server_set_profile(self.h, int(on)))
+
+    def profile(self, engine: int) -> dict:
+        """Per kernel class since profiling was switched on: device ms, launches, algorithmic bytes and flops."""
+        out = {}
+        for c, name in enumerate(PROFILE_CLASSES):
+            ms, cnt, by, fl = ctypes.c_double(), ctypes.c_int64(), ctypes.c_double(), ctypes.c_double()
+            self._check(self.lib.gmres_server_profile(self.h, engine, c, ctypes.byref(ms), ctypes.byref(cnt),
+                                                      ctypes.byref(by), ctypes.byref(fl)))
+            out[name] = dict(ms=ms.value, launches=cnt.value, bytes=by.value, flops=fl.value)
+        return out
+
+    def latencies(self) -> np.ndarray:
+        n = ctypes.c_int(0)
+        self._check(self.lib.gmres_server_latencies(self.h, None, 0, ctypes.byref(n)))
+        buf = np.zeros(n.value, dtype=np.float64)
+        self._check(self.lib.gmres_server_latencies(self.h, _ptr(buf), n.value, ctypes.byref(n)))
+        return buf[: n.value]
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.gmres_server_destroy(self.h)
+            self.h = None
+            self._refs.clear()
 
     def __del__(self):
         try:
