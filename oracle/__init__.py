@@ -24,7 +24,7 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 
 ORC_OK, ORC_MAXITER, ORC_BREAKDOWN = 0, 1, 2
 ORC_ERR_ARG, ORC_ERR_NONFINITE, ORC_ERR_OOM = -1, -3, -4
-MGS, ONE_REDUCE, IR_FP32 = 0, 1, 2
+MGS, ONE_REDUCE, IR_FP32, CGS2, PIPE2 = 0, 1, 2, 3, 4
 
 CFLAGS = ["-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-std=c99"]
 
@@ -73,7 +73,8 @@ class Oracle:
         lib.orc_qr_mgs.argtypes = [ctypes.c_int64, ctypes.c_int, _P, _P, _P]
         lib.orc_qr_cgs.argtypes = [ctypes.c_int64, ctypes.c_int, _P, _P, _P, ctypes.c_int]
         lib.orc_qr_mgs_lvl2.argtypes = [ctypes.c_int64, ctypes.c_int, _P, _P, _P, _P]
-        for f in (lib.orc_qr_mgs, lib.orc_qr_cgs, lib.orc_qr_mgs_lvl2):
+        lib.orc_qr_cgs2_lvl2.argtypes = [ctypes.c_int64, ctypes.c_int, _P, _P, _P, _P]
+        for f in (lib.orc_qr_mgs, lib.orc_qr_cgs, lib.orc_qr_mgs_lvl2, lib.orc_qr_cgs2_lvl2):
             f.restype = ctypes.c_int
         lib.orc_gmres.argtypes = [
             ctypes.c_int64, _P, _P, _P, _P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_double,
@@ -131,6 +132,10 @@ class Oracle:
     def qr_mgs_lvl2(self, A):
         """Level-2 compact-WY MGS with lagged normalization (Algorithm 4); returns Q, R, T."""
         return self._qr(self.lib.orc_qr_mgs_lvl2, A, with_T=True)
+
+    def qr_cgs2_lvl2(self, A):
+        """Level-2 iterated CGS with lagged normalization (Algorithm 5); returns Q, R, T."""
+        return self._qr(self.lib.orc_qr_cgs2_lvl2, A, with_T=True)
 
     # -- solver ------------------------------------------------------------
     def gmres(self, A, b, *, variant: int, m: int, tol: float, max_iter: int, x0=None,

@@ -21,12 +21,25 @@
  *   orc_qr_cgs        classical GS QR, 1 or 2 passes (Algorithm 1)
  *   orc_qr_mgs_lvl2   Level-2 compact-WY MGS with lagged normalization
  *                     (Algorithm 4, with the T recurrence of Section II)
+ *   orc_qr_cgs2_lvl2  Level-2 iterated CGS with lagged normalization
+ *                     (Algorithm 5): Algorithm 4's step, then a second
+ *                     classical projection with a second reduction [A16]
  *   orc_gmres         restarted GMRES(m) with
  *                       variant 0: MGS-GMRES (Algorithm 6)
  *                       variant 1: one-synchronization MGS-GMRES with lagged
  *                                  normalization (Algorithm 7 built on Algorithm 4)
  *                       variant 2: variant 1 with each cycle's vectors in FP32
  *                                  inside FP64 restarts (GMRES-IR) [A13]
+ *                       variant 3: variant 1 with the second (re-orthogonalizing)
+ *                                  projection of Algorithm 5: two reductions
+ *                                  per step [A16]
+ *                       variant 4: variant 1 with the Givens rotations applied
+ *                                  two columns at a time, the L = 2 pipeline
+ *                                  of Algorithm 8 [A17]
+ *
+ * Parity unpinned at rounding level: the second-pass coefficients that
+ * orc_qr_cgs2_lvl2 and variant 3 add to R and H are of the size of the rounding
+ * in those entries (eps ||a_j||), so no pin can tell whether they are added.
  *
  * What pins each function (tests/test_oracle_*.py, all CPU-only):
  *   the Arnoldi relation A V_k = V_{k+1} Hbar_k (Section III); the MGS /
@@ -57,6 +70,8 @@
 #define ORC_VARIANT_MGS 0
 #define ORC_VARIANT_ONE_REDUCE 1
 #define ORC_VARIANT_IR_FP32 2
+#define ORC_VARIANT_CGS2 3
+#define ORC_VARIANT_PIPE2 4
 
 /* Breakdown threshold factor [A6]: the new direction is declared exhausted
  * when its norm is below BREAKDOWN_FACTOR * eps * ||Hbar(:, j)||. */
@@ -248,6 +263,76 @@ int orc_qr_mgs_lvl2(int64_t n, int p, const double* A, double* Q, double* R, dou
   return ORC_OK;
 }
 
+/* Level-2 iterated classical Gram-Schmidt with lagged normalization,
+ * Algorithm 5, over the columns of A [A16]. When column j arrives, the first
+ * synchronization is exactly Algorithm 4's: one block reduction gives
+ * Q_{j-2}^T u_{j-1}, ||u_{j-1}||^2, Q_{j-2}^T a_j and u_{j-1}^T a_j; column j-1
+ * is normalized (the lag), the row of T is formed and the first projection
+ * r = T s gives u_j = a_j - Q_{j-1} r. The second synchronization is the
+ * re-orthogonalization of classical Gram-Schmidt applied twice:
+ * s2 = Q_{j-1}^T u_j, u_j = u_j - Q_{j-1} s2, and column j of R is r + s2.
+ * After the last column one more reduction normalizes it. T is returned as in
+ * orc_qr_mgs_lvl2. */
+int orc_qr_cgs2_lvl2(int64_t n, int p, const double* A, double* Q, double* R, double* T) {
+  if (n <= 0 || p <= 0 || p > n) return ORC_ERR_ARG;
+  memset(R, 0, sizeof(double) * (size_t)p * p);
+  memset(T, 0, sizeof(double) * (size_t)p * p);
+  double* x = (double*)malloc(sizeof(double) * (size_t)p);
+  double* y = (double*)malloc(sizeof(double) * (size_t)p);
+  double* sv = (double*)malloc(sizeof(double) * (size_t)p);
+  double* r = (double*)malloc(sizeof(double) * (size_t)p);
+  double* s2 = (double*)malloc(sizeof(double) * (size_t)p);
+  if (!x || !y || !sv || !r || !s2) {
+    free(x); free(y); free(sv); free(r); free(s2);
+    return ORC_ERR_OOM;
+  }
+#define QCOL(i) (Q + (size_t)(i) * n)
+#define TT(i, k) T[(i) + (size_t)(k) * p]
+  memcpy(QCOL(0), A, sizeof(double) * n);
+  TT(0, 0) = 1.0;
+  for (int j = 1; j <= p; ++j) {
+    const int last = (j == p);
+    double* u = QCOL(j - 1);
+    const double* a = last ? NULL : A + (size_t)j * n;
+    /* first synchronization: Algorithm 4's block reduction */
+    for (int i = 0; i < j - 1; ++i) x[i] = dot(n, QCOL(i), u);
+    double sigma = dot(n, u, u);
+    if (!last) {
+      for (int i = 0; i < j - 1; ++i) y[i] = dot(n, QCOL(i), a);
+    }
+    double z = last ? 0.0 : dot(n, u, a);
+    double beta = sqrt(sigma);
+    R[(j - 1) + (size_t)(j - 1) * p] = beta;
+    scal(n, 1.0 / beta, u);
+    for (int i = 0; i < j - 1; ++i) x[i] /= beta;
+    for (int k = 0; k < j - 1; ++k) {
+      double t = 0.0;
+      for (int i = k; i < j - 1; ++i) t += x[i] * TT(i, k);
+      TT(j - 1, k) = -t;
+    }
+    TT(j - 1, j - 1) = 1.0;
+    if (last) break;
+    for (int i = 0; i < j - 1; ++i) sv[i] = y[i];
+    sv[j - 1] = z / beta;
+    for (int i = 0; i < j; ++i) {
+      double t = 0.0;
+      for (int k = 0; k <= i; ++k) t += TT(i, k) * sv[k];
+      r[i] = t;
+    }
+    double* uj = QCOL(j);
+    memcpy(uj, a, sizeof(double) * n);
+    for (int i = 0; i < j; ++i) axpy(n, -r[i], QCOL(i), uj);
+    /* second synchronization: re-orthogonalize against q_0 .. q_{j-1} */
+    for (int i = 0; i < j; ++i) s2[i] = dot(n, QCOL(i), uj);
+    for (int i = 0; i < j; ++i) axpy(n, -s2[i], QCOL(i), uj);
+    for (int i = 0; i < j; ++i) R[i + (size_t)j * p] = r[i] + s2[i];
+  }
+#undef QCOL
+#undef TT
+  free(x); free(y); free(sv); free(r); free(s2);
+  return ORC_OK;
+}
+
 /* ------------------------------------------------------------------------- */
 /* Restarted GMRES(m), Section III.                                          */
 /* ------------------------------------------------------------------------- */
@@ -389,9 +474,20 @@ static cycle_out cycle_mgs(cycle_ws* ws, int kmax, double beta0, double bnorm, d
  * after the last step one extra reduction gives beta = ||u_kmax||, which
  *   completes column kmax-1 (the cycle's tail).
  * Only the tail pays a reduction that is not shared with a block product, so
- * a cycle of k steps makes k+1 reductions. */
+ * a cycle of k steps makes k+1 reductions.
+ *
+ * reorth (variant 3, Algorithm 5 in Arnoldi form [A16]): after u_{j+1} is
+ * formed, a second reduction s2 = V_{j+1}^T u_{j+1} and the projection
+ * u_{j+1} -= V_{j+1} s2 re-orthogonalize it, and H(0:j, j) = r + s2; a cycle
+ * of k steps makes 2k+1 reductions.
+ * pairs (variant 4, the L = 2 pipeline of Algorithm 8 [A17]): column 0 is
+ * rotated when it completes; afterwards columns are rotated two at a time,
+ * the odd column c-1 together with the even column c once c completes, and
+ * the convergence test runs only after a rotation. The cycle's tail and a
+ * breakdown rotate whatever is pending. V, H and every rotation are those of
+ * variant 1; only the step at which convergence is seen can come one later. */
 static cycle_out cycle_one_reduce(cycle_ws* ws, int kmax, double beta0, double bnorm, double tol,
-                                  double* hist, int* hlen, int hcap, int64_t* nred) {
+                                  double* hist, int* hlen, int hcap, int64_t* nred, int reorth, int pairs) {
   cycle_out out = {0, 0, 0.0};
   const int64_t n = ws->n;
   const int ld = ws->m + 1;
@@ -410,8 +506,15 @@ static cycle_out cycle_one_reduce(cycle_ws* ws, int kmax, double beta0, double b
     double* u1 = VCOL(ws, 1);
     memcpy(u1, ws->w, sizeof(double) * n);
     axpy(n, -d0, VCOL(ws, 0), u1);
+    if (reorth) {
+      double s2 = dot(n, VCOL(ws, 0), u1);
+      *nred += 1;
+      axpy(n, -s2, VCOL(ws, 0), u1);
+      HH(ws, 0, 0) += s2;
+    }
   }
 
+  int rotated = 0; /* columns rotated so far */
   for (int j = 1; j <= kmax; ++j) {
     const int tail = (j == kmax);
     double* u = VCOL(ws, j);
@@ -429,12 +532,21 @@ static cycle_out cycle_one_reduce(cycle_ws* ws, int kmax, double beta0, double b
     /* lagged norm completes column j-1 */
     double beta = sqrt(sigma);
     HH(ws, j, j - 1) = beta;
-    double est = rotate_column(ws, j - 1) / bnorm;
-    if (*hlen < hcap) hist[*hlen] = est;
-    *hlen += 1;
+    const int brk = beta <= BREAKDOWN_FACTOR * 2.220446049250313e-16 * hcol_norm(ws, j - 1);
+    const int c = j - 1;
+    const int rotate_now = !pairs || c == 0 || c % 2 == 0 || tail || brk;
+    double est = out.est;
+    if (rotate_now) {
+      for (int q = rotated; q <= c; ++q) {
+        est = rotate_column(ws, q) / bnorm;
+        if (*hlen < hcap) hist[*hlen] = est;
+        *hlen += 1;
+      }
+      rotated = c + 1;
+    }
     out.k = j;
     out.est = est;
-    if (beta <= BREAKDOWN_FACTOR * 2.220446049250313e-16 * hcol_norm(ws, j - 1)) {
+    if (brk) {
       out.breakdown = 1;
       if (beta != 0.0) scal(n, 1.0 / beta, u);
       break;
@@ -449,7 +561,7 @@ static cycle_out cycle_one_reduce(cycle_ws* ws, int kmax, double beta0, double b
       TL(ws, j, k) = -t;
     }
     TL(ws, j, j) = 1.0;
-    if (tail || est <= tol) break;
+    if (tail || (rotate_now && est <= tol)) break;
 
     /* s = [c / beta; d / beta^2], r = T s, H(0:j, j) = r */
     for (int i = 0; i < j; ++i) ws->s[i] = ws->c[i] / beta;
@@ -464,6 +576,14 @@ static cycle_out cycle_one_reduce(cycle_ws* ws, int kmax, double beta0, double b
     double* un = VCOL(ws, j + 1);
     for (int64_t l = 0; l < n; ++l) un[l] = ws->w[l] / beta;
     for (int i = 0; i <= j; ++i) axpy(n, -ws->r[i], VCOL(ws, i), un);
+    if (reorth) { /* second reduction: s2 = V_j^T u_{j+1} (a is free now) */
+      for (int i = 0; i <= j; ++i) ws->a[i] = dot(n, VCOL(ws, i), un);
+      *nred += 1;
+      for (int i = 0; i <= j; ++i) {
+        axpy(n, -ws->a[i], VCOL(ws, i), un);
+        HH(ws, i, j) += ws->a[i];
+      }
+    }
   }
   return out;
 }
@@ -599,7 +719,8 @@ int orc_gmres(int64_t n, const int32_t* rowptr, const int32_t* col, const double
               double* hist, int hist_cap, orc_info* info,
               double* V1, double* H1, double* T1, int* k1) {
   if (n <= 0 || m <= 0 || max_iter < 0 || !(tol >= 0.0) || !b || !x || !info) return ORC_ERR_ARG;
-  if (variant != ORC_VARIANT_MGS && variant != ORC_VARIANT_ONE_REDUCE && variant != ORC_VARIANT_IR_FP32)
+  if (variant != ORC_VARIANT_MGS && variant != ORC_VARIANT_ONE_REDUCE && variant != ORC_VARIANT_IR_FP32 &&
+      variant != ORC_VARIANT_CGS2 && variant != ORC_VARIANT_PIPE2)
     return ORC_ERR_ARG;
   memset(info, 0, sizeof(*info));
   if (!all_finite(n, b) || !all_finite(n, x)) {
@@ -685,8 +806,9 @@ int orc_gmres(int64_t n, const int32_t* rowptr, const int32_t* col, const double
     cycle_out co;
     if (variant == ORC_VARIANT_MGS)
       co = cycle_mgs(&ws, kmax, beta0, bnorm, tol, hist, &hlen, hist_cap, &info->reductions);
-    else if (variant == ORC_VARIANT_ONE_REDUCE)
-      co = cycle_one_reduce(&ws, kmax, beta0, bnorm, tol, hist, &hlen, hist_cap, &info->reductions);
+    else if (variant == ORC_VARIANT_ONE_REDUCE || variant == ORC_VARIANT_CGS2 || variant == ORC_VARIANT_PIPE2)
+      co = cycle_one_reduce(&ws, kmax, beta0, bnorm, tol, hist, &hlen, hist_cap, &info->reductions,
+                            variant == ORC_VARIANT_CGS2, variant == ORC_VARIANT_PIPE2);
     else
       co = cycle_one_reduce_f32(&ws, V32, w32, val32, kmax, beta0, bnorm, tol, hist, &hlen, hist_cap,
                                 &info->reductions);

@@ -13,7 +13,7 @@ import numpy as np
 from paper_1809_05805_b300 import problems as P
 
 EPS = np.finfo(np.float64).eps
-MGS, ONE_REDUCE, IR_FP32 = 0, 1, 2
+MGS, ONE_REDUCE, IR_FP32, CGS2, PIPE2 = 0, 1, 2, 3, 4
 
 
 def _dense(A):
@@ -51,7 +51,8 @@ def pin_dot_maxpy(orc):
 def pin_qr_reconstructs(orc):
     """Q R = A to rounding for all four Gram-Schmidt variants (backward stability)."""
     A = P.tall_skinny(300, 12, 1e4, seed=2)
-    for Q, R in (orc.qr_mgs(A), orc.qr_cgs(A, 1), orc.qr_cgs(A, 2), orc.qr_mgs_lvl2(A)[:2]):
+    for Q, R in (orc.qr_mgs(A), orc.qr_cgs(A, 1), orc.qr_cgs(A, 2), orc.qr_mgs_lvl2(A)[:2],
+                 orc.qr_cgs2_lvl2(A)[:2]):
         assert np.linalg.norm(Q @ R - A) <= 1e-13 * np.linalg.norm(A), "QR != A"
         assert np.allclose(R, np.triu(R)), "R not upper triangular"
         assert np.all(np.diag(R) > 0), "R diagonal not positive"
@@ -167,7 +168,7 @@ def pin_direct_solve(orc):
         b = np.random.default_rng(seed).standard_normal(n)
         xref = np.linalg.solve(M, b)
         kap = np.linalg.cond(M)
-        for var in (MGS, ONE_REDUCE):
+        for var in (MGS, ONE_REDUCE, CGS2, PIPE2):
             r = orc.gmres(A, b, variant=var, m=n, tol=1e-15, max_iter=n)
             err = np.linalg.norm(r.x - xref) / np.linalg.norm(xref)
             assert err <= 1e-12 * kap, f"n={n} var={var} err={err}"
@@ -193,7 +194,7 @@ def pin_krylov_minimum(orc):
         y, *_ = np.linalg.lstsq(M @ Qk, b, rcond=None)
         ref.append(np.linalg.norm(b - M @ (Qk @ y)) / np.linalg.norm(b))
     ref = np.array(ref)
-    for var in (MGS, ONE_REDUCE):
+    for var in (MGS, ONE_REDUCE, CGS2, PIPE2):
         r = orc.gmres(A, b, variant=var, m=kmax, tol=0.0, max_iter=kmax)
         assert np.allclose(r.history[:kmax], ref, rtol=1e-9, atol=1e-15), f"var {var}: {r.history} vs {ref}"
         # the solution after the cycle realizes the last minimum
@@ -206,7 +207,7 @@ def pin_finite_termination(orc):
     M = P.distinct_eigs(40, [1.0, 2.5, 4.0], seed=2)
     A = P.from_dense(M)
     b = np.random.default_rng(3).standard_normal(40)
-    for var in (MGS, ONE_REDUCE):
+    for var in (MGS, ONE_REDUCE, CGS2, PIPE2):
         r = orc.gmres(A, b, variant=var, m=10, tol=1e-12, max_iter=10)
         assert r.iters == 3, f"var {var}: {r.iters} steps"
         assert r.history[1] > 1e-6 and r.rel_resid_true <= 1e-12
@@ -275,6 +276,85 @@ def pin_ir_cycle_is_fp32(orc):
     assert 1e-10 < err < 1e-5, err
 
 
+def pin_cgs2_lvl2_qr(orc):
+    """Algorithm 5 (iterated CGS with lagged normalization): the paper states its
+    columns are orthogonal to machine precision; so ||I - Q^T Q|| stays O(eps)
+    for kappa up to 1e12 while MGS loses eps*kappa. Q R = A to rounding; on a
+    well-conditioned matrix Q and R equal column MGS's (exact-arithmetic
+    identity of the two projections), and T = inv(I + L) is the identity to
+    rounding because the re-orthogonalized columns are orthogonal."""
+    for kap in (1e2, 1e6, 1e10, 1e12):
+        A = P.tall_skinny(1000, 30, kap, seed=11)
+        Q, R, T = orc.qr_cgs2_lvl2(A)
+        assert _lo(Q) <= 1e-13, f"kappa {kap}: loss {_lo(Q)}"
+        assert np.linalg.norm(Q @ R - A) <= 1e-13 * np.linalg.norm(A)
+        assert np.abs(T - np.eye(30)).max() <= 1e-12
+    assert _lo(orc.qr_mgs(P.tall_skinny(1000, 30, 1e12, seed=11))[0]) >= 1e-6  # the contrast
+    A = P.tall_skinny(400, 15, 1e3, seed=5)
+    Qm, Rm = orc.qr_mgs(A)
+    Q2, R2, _ = orc.qr_cgs2_lvl2(A)
+    assert np.abs(Q2 - Qm).max() <= 1e-11 and np.abs(R2 - Rm).max() <= 1e-11 * np.abs(Rm).max()
+
+
+def pin_cgs2_gmres(orc):
+    """GMRES with Algorithm 5's two-reduction orthogonalization: on the
+    Simoncini-Szyld problem, where one-reduce loses orthogonality completely by
+    step 80, its basis stays orthonormal to 1e-13, its Hessenberg equals
+    V^T A V_k (the Galerkin identity of an orthonormal Arnoldi basis) and the
+    Arnoldi relation holds; on a well-conditioned problem it coincides with
+    MGS-GMRES; a cycle of k steps makes 2k + 1 reductions."""
+    A, b = P.simoncini_szyld(100, seed=0)
+    M = _dense(A)
+    r = orc.gmres(A, b, variant=CGS2, m=80, tol=0.0, max_iter=80, capture=True)
+    r1 = orc.gmres(A, b, variant=ONE_REDUCE, m=80, tol=0.0, max_iter=80, capture=True)
+    V = r.V[:, : r.k]
+    assert _lo(V) <= 1e-13, _lo(V)
+    assert _lo(r1.V[:, : r1.k]) >= 1e-3  # the contrast
+    G = r.V.T @ M @ V
+    assert np.abs(G - r.H).max() <= 1e-13 * np.abs(r.H).max()
+    assert np.linalg.norm(M @ V - r.V @ r.H) <= 1e-12 * np.linalg.norm(M @ V)
+    A = P.conv_diff_7pt(12)
+    _, b = P.rhs(A, seed=6)
+    rm = orc.gmres(A, b, variant=MGS, m=20, tol=1e-10, max_iter=200)
+    rc = orc.gmres(A, b, variant=CGS2, m=20, tol=1e-10, max_iter=200)
+    assert rm.iters == rc.iters and rm.restarts == rc.restarts
+    assert np.all(np.abs(rm.history[:20] - rc.history[:20]) <= 1e-12 * rm.history[:20])
+    A = P.conv_diff_7pt(8)
+    _, b = P.rhs(A, seed=1)
+    rc = orc.gmres(A, b, variant=CGS2, m=7, tol=0.0, max_iter=20)
+    cycles = [7, 7, 6]
+    assert rc.reductions == 1 + (len(cycles) + 1) + sum(2 * k + 1 for k in cycles), rc.reductions
+
+
+def pin_pipeline(orc):
+    """The L = 2 pipeline (Algorithm 8) changes only when the Givens rotations
+    are applied: with a fixed step count its basis, Hessenberg, T and residual
+    estimates are bit for bit those of one-reduce; with a tolerance it sees
+    convergence only after an even column (or column 0), so a single-cycle
+    solve that one-reduce ends after k steps ends after k steps when k - 1 is
+    even and after k + 1 steps otherwise."""
+    A = P.conv_diff_7pt(10)
+    _, b = P.rhs(A, seed=4)
+    r1 = orc.gmres(A, b, variant=ONE_REDUCE, m=25, tol=0.0, max_iter=25, capture=True)
+    rp = orc.gmres(A, b, variant=PIPE2, m=25, tol=0.0, max_iter=25, capture=True)
+    for a, c in ((r1.V, rp.V), (r1.H, rp.H), (r1.T, rp.T), (r1.history, rp.history)):
+        assert np.array_equal(a, c), "pipeline changed the arithmetic"
+    seen_odd = False
+    for seed in range(8):
+        A = P.conv_diff_7pt(9)
+        _, b = P.rhs(A, seed=seed)
+        tol = 10.0 ** (-4 - seed % 4)
+        r1 = orc.gmres(A, b, variant=ONE_REDUCE, m=200, tol=tol, max_iter=200)
+        rp = orc.gmres(A, b, variant=PIPE2, m=200, tol=tol, max_iter=200)
+        assert r1.restarts == rp.restarts == 1
+        k1 = r1.iters
+        want = k1 if (k1 - 1) % 2 == 0 or k1 == 1 else k1 + 1
+        seen_odd |= want != k1
+        assert rp.iters == want, (seed, k1, rp.iters)
+        assert rp.rel_resid_true <= tol
+    assert seen_odd, "no case where the pipeline needs the extra step"
+
+
 def simoncini_szyld_run(orc, variant):
     A, b = P.simoncini_szyld(100, seed=0)
     return orc.gmres(A, b, variant=variant, m=100, tol=0.0, max_iter=100, capture=True)
@@ -304,4 +384,7 @@ PINS = [
     pin_reduction_counts,
     pin_ir_refines_to_fp64_accuracy,
     pin_ir_cycle_is_fp32,
+    pin_cgs2_lvl2_qr,
+    pin_cgs2_gmres,
+    pin_pipeline,
 ]

@@ -57,6 +57,14 @@ MUTANTS = {
                       "for (int64_t l = 0; l < n; ++l) un[l] = w32[l];"),
     "ir_cycle_fp64_spmv": ("if (!tail) spmv_f32(n, ws->rowptr, ws->col, val32, u, w32);",
                            "if (!tail) spmv_f32(n, ws->rowptr, ws->col, val32, u, w32), w32[0] *= 1.5f;"),
+    # Algorithm 5 (second projection) and the L = 2 pipeline (Algorithm 8). Dropping
+    # the second-pass coefficients from H / R is not planted: they are of the size
+    # of the rounding in H itself (eps ||A v_j||), invisible to any pin.
+    "cgs2_reorth_sign": ("axpy(n, -ws->a[i], VCOL(ws, i), un);", "axpy(n, ws->a[i], VCOL(ws, i), un);"),
+    "qr_cgs2_second_pass_sign": ("for (int i = 0; i < j; ++i) axpy(n, -s2[i], QCOL(i), uj);",
+                                 "for (int i = 0; i < j; ++i) axpy(n, s2[i], QCOL(i), uj);"),
+    "pipe_pairs_shifted": ("c == 0 || c % 2 == 0 || tail || brk;", "c == 0 || c % 2 == 1 || tail || brk;"),
+    "pipe_skip_pending": ("for (int q = rotated; q <= c; ++q) {", "for (int q = c; q <= c; ++q) {"),
     "dot_square": ("double orc_dot(int64_t n, const double* x, const double* y) { return dot(n, x, y); }",
                    "double orc_dot(int64_t n, const double* x, const double* y) { return dot(n, x, x); }"),
 }
