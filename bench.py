@@ -350,6 +350,20 @@ def run_ours(args, w, rank, world, dist):
                if prof_m else None}
         s.set(ortho="one_reduce_mgs", max_iter=w["max_iter"])
 
+    # the paper's sibling schemes on the same kernels (Algorithm 5: two reductions
+    # per step; Algorithm 8: Givens rotations on column pairs)
+    siblings = None
+    if not args.no_mgs and w["compare"] == "mgs":
+        siblings = {}
+        for ortho in ("cgs2_lvl2", "one_reduce_pipe2"):
+            s.set(ortho=ortho, max_iter=w["max_iter"])
+            ms_s, infos_s, prof_s = timed_solves(torch, s, bd, x, 1, 1, stream)
+            isb = infos_s[-1]
+            siblings[ortho] = {"time_to_solve_s": max_over_ranks(ms_s) / 1e3, "iters": isb.iters,
+                               "restarts": isb.restarts, "reductions": isb.reductions,
+                               "rel_resid_true": isb.rel_resid_true}
+        s.set(ortho="one_reduce_mgs", max_iter=w["max_iter"])
+
     # end to end through the host-buffer entry point (copies inside the call)
     bh = torch.from_numpy(b).pin_memory().numpy()
     xh = torch.zeros(n, dtype=torch.float64).pin_memory().numpy()
@@ -430,6 +444,7 @@ def run_ours(args, w, rank, world, dist):
         "alg_hbm_gbs_whole_solve": total_bytes / (total_ms_prof * 1e6) if total_ms_prof else None,
         "mgs": mgs,
         "speedup_vs_mgs": (mgs["time_to_solve_s"] / (ms / 1e3)) if mgs else None,
+        "siblings": siblings,
         "fp64_one_reduce": fp64,
         "speedup_vs_fp64": (fp64["time_to_solve_s"] / (ms / 1e3)) if fp64 else None,
         "e2e": {"value": e2e_ms / 1e3, "unit": "s", "h2d_bytes_per_step": 16 * n, "d2h_bytes_per_step": 8 * n},

@@ -2,7 +2,7 @@
  * lsgmres.h: C ABI of the B300-native low-synchronization GMRES library.
  *
  * Solves A x = b for a square sparse A in CSR form with restarted GMRES(m)
- * (Saad and Schultz), in one of two orthogonalization schemes:
+ * (Saad and Schultz), in one of four orthogonalization schemes:
  *
  *   GMRES_MGS             MGS-GMRES, Algorithm 6 of Swirydowicz, Langou,
  *                         Ananthan, Yang and Thomas, "Low synchronization GMRES
@@ -15,9 +15,18 @@
  *                         step makes one grid-wide reduction: the block inner
  *                         product [V_{j-1} u_j]^T [u_j  A u_j], which also
  *                         carries the lagged norm of u_j.
+ *   GMRES_CGS2_LVL2       two-synchronization GMRES on the Level-2 iterated
+ *                         classical Gram-Schmidt of Algorithm 5: the one-reduce
+ *                         step, then a second block reduction V_{j+1}^T u_{j+1}
+ *                         and projection that re-orthogonalize the new vector
+ *                         (basis orthogonal to machine precision).
+ *   GMRES_ONE_REDUCE_PIPE2  the one-reduce scheme with the Givens rotations
+ *                         applied two columns at a time (the L = 2 pipeline of
+ *                         Algorithm 8); the same basis and Hessenberg, the
+ *                         convergence test after every second column.
  *
- * Both schemes run on the same kernels (CSR SpMV, multi-column dot, MAXPY) on
- * one GPU. All arithmetic on the solve path is FP64.
+ * All schemes run on the same kernels (CSR SpMV, multi-column dot, MAXPY) on
+ * one GPU. All arithmetic on the solve path is FP64 (except GMRES_IR_FP32).
  *
  * Conventions for every entry point:
  *   - Every call returns a gmres_status; no call aborts or exits. After an
@@ -53,7 +62,7 @@ typedef enum {
   GMRES_ERR_TIMEOUT = -5     /* reserved for bounded device-side waits */
 } gmres_status;
 
-typedef enum { GMRES_MGS = 0, GMRES_ONE_REDUCE_MGS = 1 } gmres_ortho;
+typedef enum { GMRES_MGS = 0, GMRES_ONE_REDUCE_MGS = 1, GMRES_CGS2_LVL2 = 2, GMRES_ONE_REDUCE_PIPE2 = 3 } gmres_ortho;
 
 /* Arithmetic of the Krylov loop.
  *   GMRES_FP64     everything in FP64.
@@ -105,7 +114,8 @@ gmres_status gmres_create(const gmres_csr* A, int m_restart, double tol, gmres_h
 
 /* Select the orthogonalization scheme, the arithmetic and the iteration limit
  * (max_iter >= 0 Arnoldi steps over all cycles). GMRES_ERR_ARG for an unknown
- * scheme, GMRES_IR_BF16, GMRES_IR_FP32 with GMRES_MGS, or max_iter < 0;
+ * scheme, GMRES_IR_BF16, GMRES_IR_FP32 with a scheme other than
+ * GMRES_ONE_REDUCE_MGS, or max_iter < 0;
  * GMRES_ERR_OOM if the FP32 copies cannot be allocated. */
 gmres_status gmres_set(gmres_handle h, gmres_ortho ortho, gmres_prec prec, int max_iter);
 
@@ -149,8 +159,10 @@ const char* gmres_last_error(gmres_handle h);
  * separately). Counters reset at the start of every solve.
  * Classes: 0 one-reduce step (fused SpMV + block dot + epilogue), 1 Arnoldi
  * MAXPY, 2 MGS SpMV + first dot, 3 MGS axpy + next dot, 4 residual / norm,
- * 5 least squares, 6 solution update (MAXPY), 7 launches that did no work. */
-#define GMRES_PROFILE_CLASSES 8
+ * 5 least squares, 6 solution update (MAXPY), 7 launches that did no work,
+ * 8 second (re-orthogonalizing) block reduction of GMRES_CGS2_LVL2, 9 its
+ * in-place MAXPY. */
+#define GMRES_PROFILE_CLASSES 10
 gmres_status gmres_set_profile(gmres_handle h, int on);
 gmres_status gmres_profile(gmres_handle h, int cls, double* total_ms, int64_t* launches,
                            double* alg_bytes, double* alg_flops);

@@ -44,6 +44,7 @@ struct DevState {
   int breakdowns;
   unsigned int ticket; // last-CTA election
   int fresh;           // batched engine: the next residual pass also sets bnorm
+  int pipe2;           // Givens rotations on column pairs (the L = 2 pipeline)
   long long reductions;
   long long grid_syncs;
   double mgs_coef;     // MGS: coefficient of the pending axpy
@@ -302,6 +303,39 @@ __device__ int finish_column(Small s, int j, double h, bool last_allowed) {
   }
   __syncthreads();
   return s_res;
+}
+
+// Column c of H is complete (h = H(c+1, c)). Normally it is rotated at once
+// (finish_column). In the L = 2 pipeline (Algorithm 8, st->pipe2) column 0 is
+// rotated alone and afterwards columns are rotated in pairs: an odd column
+// waits for the next even one, unless it is the cycle's last (tail) or its
+// new direction vanished (breakdown test on the unrotated column), in which
+// case everything pending is rotated now. Returns the stop decision of the
+// last rotation (0 when nothing was rotated). Run by the whole CTA.
+__device__ int finish_completed(Small s, int c, double h, bool tail) {
+  DevState* st = s.st;
+  if (!__ldcg(&st->pipe2)) return finish_column(s, c, h, tail);
+  __shared__ double sbuf[kWarps];
+  __shared__ int s_rot, s_first;
+  double v = 0.0;
+  for (int i = threadIdx.x; i <= c + 1; i += blockDim.x) {
+    const double x = (i == c + 1) ? h : s.H[(size_t)c * s.ldh + i];
+    v = fma(x, x, v);
+  }
+  const double hn2 = block_sum(v, sbuf);
+  if (threadIdx.x == 0) {
+    const bool brk = h <= kBreakdownFactor * kEps * sqrt(hn2);
+    s_rot = (c == 0 || (c & 1) == 0 || tail || brk);
+    s_first = st->k;  // columns rotated so far in this cycle
+  }
+  __syncthreads();
+  if (!s_rot) return 0;
+  int stop = 0;
+  for (int q = s_first; q <= c; ++q) {
+    const double hq = (q == c) ? h : __ldcg(&s.H[(size_t)q * s.ldh + q + 1]);
+    stop |= finish_column(s, q, hq, tail && q == c);
+  }
+  return stop;
 }
 
 // --------------------------------------------------------------------------
@@ -566,7 +600,7 @@ __device__ void epilogue_one_reduce(Small s, double* red, int j, bool tail) {
   // not needed by the MAXPY.
   if (j > 0 && (s_stop == 3 || (s_stop == 0 && tail))) {
     const bool exact = (s_stop == 3);
-    const int fin = finish_column(s, j - 1, s_beta, tail);
+    const int fin = finish_completed(s, j - 1, s_beta, tail);
     if (threadIdx.x == 0) {
       if (exact || st->breakdown || st->nonfinite) s_stop = 2;
       else if (fin) s_stop = 1;
@@ -706,7 +740,7 @@ __device__ void lsq_system(Small s) {
 
 // Kernel classes of the per-launch profiles (gmres_profile, gmres_batch_profile).
 enum { PC_STEP = 0, PC_MAXPY = 1, PC_MGS_SPMV = 2, PC_MGS_AXPY = 3, PC_RES = 4, PC_LSQ = 5, PC_XUPD = 6,
-       PC_NOOP = 7 };
+       PC_NOOP = 7, PC_REORTH = 8, PC_REORTH_MAXPY = 9 };
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 

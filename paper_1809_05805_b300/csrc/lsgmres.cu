@@ -112,9 +112,66 @@ k_one_reduce_step(const int32_t* __restrict__ rowptr, const int32_t* __restrict_
 }
 
 // --------------------------------------------------------------------------
+// Second projection of Algorithm 5 (cgs2_lvl2) in Arnoldi form
+// --------------------------------------------------------------------------
+// After step j and its MAXPY, column j+1 holds z = A v_j - V_{j+1} r. One more
+// grid reduction gives a_k = u_k^T z (k <= j) with the same fused tile block
+// dot (no SpMV); the last CTA forms s2_k = v_k^T z = scale_k a_k, adds s2 to
+// H(0:j, j) and writes the coefficients of z -= V_{j+1} s2, which the in-place
+// MAXPY (MAXPY_REORTH) applies.
+template <int MAXC>
+__global__ void __launch_bounds__(kThreads, 2)
+k_reorth(const double* __restrict__ V, int64_t ldv, int64_t n, Small s) {
+  __shared__ double su[2 * kThreads];
+  __shared__ double sw[2 * kThreads];
+  __shared__ double red[2 * (kMaxM + 1) + 2];
+  __shared__ int s_jj, s_skip;
+  DevState* st = s.st;
+  if (threadIdx.x == 0) {
+    s_skip = __ldcg(&st->done);
+    s_jj = __ldcg(&st->step);  // j + 1: z is column j + 1, projected on columns 0..j
+  }
+  __syncthreads();
+  if (s_skip) return;
+  const int jj = s_jj;
+  const double* z = V + (size_t)jj * ldv;
+  const int J8 = jj / kWarps, r8 = jj % kWarps;
+  double acc_a[MAXC], acc_c[MAXC], rem_a[kWarps - 1], rem_c[kWarps - 1];
+#pragma unroll
+  for (int c = 0; c < MAXC; ++c) acc_a[c] = acc_c[c] = 0.0;
+#pragma unroll
+  for (int c = 0; c < kWarps - 1; ++c) rem_a[c] = rem_c[c] = 0.0;
+  double sig = 0.0, dd = 0.0;
+  const int64_t ntiles = (n + kThreads - 1) / kThreads;
+  if (ntiles >= 4 * (int64_t)gridDim.x) {
+    const int64_t npairs = (ntiles + 1) / 2;
+    for (int64_t pp = blockIdx.x; pp < npairs; pp += gridDim.x)
+      tile_pair_block_dot<MAXC, double>(pp, n, nullptr, nullptr, nullptr, V, ldv, z, z, nullptr, false, false, J8,
+                                        r8, su, sw, acc_a, acc_c, rem_a, rem_c, sig, dd);
+  } else {
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x)
+      tile_block_dot<MAXC, double>(t, n, nullptr, nullptr, nullptr, V, ldv, z, z, nullptr, false, false, J8, r8, su,
+                                   sw, acc_a, acc_c, rem_a, rem_c, sig, dd);
+  }
+  cta_partials<MAXC, double>(acc_a, acc_c, rem_a, rem_c, sig, dd, jj, J8, r8, red);
+  if (!grid_reduce_last(s, red, 2 * jj + 2)) return;
+  const int ld = s.ldh;
+  for (int k = threadIdx.x; k < jj; k += blockDim.x) {
+    const double sk = __ldcg(&s.scale[k]);
+    const double s2 = red[k] * sk;
+    s.H[(size_t)(jj - 1) * ld + k] += s2;
+    s.coef[1 + k] = -s2 * sk;
+  }
+  if (threadIdx.x == 0) {
+    s.coef[0] = 1.0;
+    st->grid_syncs += 1;
+  }
+}
+
+// --------------------------------------------------------------------------
 // MAXPY: out = alpha * y_in + sum_{k<K} c_k V[:, k]
 // --------------------------------------------------------------------------
-enum { MAXPY_ARNOLDI = 0, MAXPY_XUPDATE = 1, MAXPY_STANDALONE = 2 };
+enum { MAXPY_ARNOLDI = 0, MAXPY_XUPDATE = 1, MAXPY_STANDALONE = 2, MAXPY_REORTH = 3 };
 
 template <typename T>
 struct Vec16;  // a 16-byte vector of T
@@ -129,7 +186,9 @@ struct Vec16<float> {
 
 // VT: basis type, YT: type of y_in / y_out, CT: arithmetic type. Arnoldi mode
 // needs VT == YT (the output is a basis column); the FP32 solution update of
-// GMRES-IR uses VT = float, YT = CT = double.
+// GMRES-IR uses VT = float, YT = CT = double. MAXPY_REORTH (the second
+// projection of Algorithm 5) updates the new basis column in place:
+// u_{j+1} += sum_k c_k u_k (y_in and y_out are that column; no Givens CTA).
 template <typename VT, typename YT, typename CT>
 __global__ void __launch_bounds__(kThreads, 4)
 k_maxpy(const VT* __restrict__ V, int64_t ldv, const YT* y_in, YT* y_out, int64_t n, Small s, int mode,
@@ -142,7 +201,7 @@ k_maxpy(const VT* __restrict__ V, int64_t ldv, const YT* y_in, YT* y_out, int64_
   if (threadIdx.x == 0) {
     s_skip = 0;
     s_out = y_out;
-    if (mode == MAXPY_ARNOLDI) {
+    if (mode == MAXPY_ARNOLDI || mode == MAXPY_REORTH) {
       s_skip = __ldcg(&st->done);
       sK = __ldcg(&st->maxpy_k);
       if constexpr (std::is_same<VT, YT>::value)
@@ -168,7 +227,7 @@ k_maxpy(const VT* __restrict__ V, int64_t ldv, const YT* y_in, YT* y_out, int64_
     const int j = __ldcg(&st->step) - 1;
     if (j >= 1) {
       const double h = __ldcg(&s.H[(size_t)(j - 1) * s.ldh + j]);
-      const int stop = finish_column(s, j - 1, h, false);
+      const int stop = finish_completed(s, j - 1, h, false);
       if (threadIdx.x == 0) {
         st->grid_syncs += 1;
         if (stop) st->done = 1;
@@ -178,6 +237,7 @@ k_maxpy(const VT* __restrict__ V, int64_t ldv, const YT* y_in, YT* y_out, int64_
   }
   const int ndata = gridDim.x - (mode == MAXPY_ARNOLDI ? 1 : 0);  // CTAs that stream
   YT* out = s_out;
+  if (mode == MAXPY_REORTH) y_in = out;  // in place: each element is read, then written, by one thread
   const CT alpha = scc[0];
   const int64_t stride = (int64_t)ndata * blockDim.x;
   const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -432,6 +492,23 @@ template <typename VT>
 using StepKernel = void (*)(const int32_t*, const int32_t*, const VT*, const VT*, int64_t, const VT*, VT*, int64_t,
                             Small, int, int, double*);
 
+using ReorthKernel = void (*)(const double*, int64_t, int64_t, Small);
+
+ReorthKernel reorth_kernel_for(int m) {
+  switch (std::max(1, m / kWarps)) {
+    case 1: return k_reorth<1>;
+    case 2: return k_reorth<2>;
+    case 3: return k_reorth<3>;
+    case 4: return k_reorth<4>;
+    case 5: return k_reorth<5>;
+    case 6: return k_reorth<6>;
+    case 7: return k_reorth<7>;
+    case 8: return k_reorth<8>;
+    case 9: case 10: case 11: case 12: return k_reorth<12>;
+    default: return k_reorth<16>;
+  }
+}
+
 // MAXC = floor(m / 8) whole columns per warp (j <= m), at least 1.
 template <typename VT>
 StepKernel<VT> step_kernel_for(int m) {
@@ -476,6 +553,7 @@ struct gmres_ctx {
   DevState* h_st = nullptr;  // pinned mirror
   cudaStream_t stream = nullptr;
   StepKernel<double> step = nullptr;
+  ReorthKernel reorth = nullptr;
   StepKernel<float> step32 = nullptr;
   // GMRES-IR (FP32 cycles): FP32 basis, SpMV result and matrix values, and the
   // FP64 restart residual; allocated by gmres_set(GMRES_IR_FP32)
@@ -627,7 +705,7 @@ void prof_end(gmres_ctx* h, int idx);
 // residual kernel). Kernels past the end of the cycle return at once.
 gmres_status launch_cycle(gmres_ctx* h, int kmax) {
   const int P = h->P;
-  if (h->ortho == GMRES_ONE_REDUCE_MGS) {
+  if (h->ortho != GMRES_MGS) {  // one-reduce, its L = 2 pipeline, and cgs2_lvl2
     for (int j = 0; j <= kmax; ++j) {
       int pr = prof_begin(h, 0, j, kmax);
       if (h->prec == GMRES_IR_FP32)
@@ -648,6 +726,16 @@ gmres_status launch_cycle(gmres_ctx* h, int kmax) {
               h->V, h->ldv, h->w, nullptr, h->n, h->s, MAXPY_ARNOLDI, 0);
         prof_end(h, pr);
         ++h->launches;
+        if (h->ortho == GMRES_CGS2_LVL2) {  // Algorithm 5's second reduction and projection
+          pr = prof_begin(h, PC_REORTH, j, kmax);
+          h->reorth<<<P, kThreads, 0, h->stream>>>(h->V, h->ldv, h->n, h->s);
+          prof_end(h, pr);
+          pr = prof_begin(h, PC_REORTH_MAXPY, j, kmax);
+          k_maxpy<double, double, double><<<h->grid_stream, kThreads, 0, h->stream>>>(
+              h->V, h->ldv, nullptr, nullptr, h->n, h->s, MAXPY_REORTH, 0);
+          prof_end(h, pr);
+          h->launches += 2;
+        }
       }
     }
   } else {
@@ -734,8 +822,9 @@ gmres_status run_cycle(gmres_ctx* h, int kmax) {
     g->kmax = kmax;
     g->prof = h->prof_on;
     g->exec = nullptr;
-    const int64_t nl = (h->ortho == GMRES_ONE_REDUCE_MGS) ? 2 * (int64_t)kmax + 1
-                                                          : (int64_t)kmax + (int64_t)kmax * (kmax + 1) / 2;
+    const int64_t nl = (h->ortho == GMRES_MGS)         ? (int64_t)kmax + (int64_t)kmax * (kmax + 1) / 2
+                       : (h->ortho == GMRES_CGS2_LVL2) ? 4 * (int64_t)kmax + 1
+                                                       : 2 * (int64_t)kmax + 1;
     if (h->prof_on) {
       g->events.resize(2 * nl);
       for (auto& e : g->events) CUDA_TRY(h, cudaEventCreate(&e));
@@ -800,6 +889,14 @@ void alg_model(const gmres_ctx* h, const gmres_ctx::ProfRec& r, int kx, double* 
       *bytes = vb * n * (r.j + 3);
       *flops = 2.0 * n * (r.j + 1) + n;
       break;
+    case PC_REORTH:  // z and j+1 basis columns read
+      *bytes = 8.0 * n * (r.j + 2);
+      *flops = 2.0 * n * (r.j + 2);
+      break;
+    case PC_REORTH_MAXPY:  // z and j+1 columns read, z written
+      *bytes = 8.0 * n * (r.j + 3);
+      *flops = 2.0 * n * (r.j + 1) + n;
+      break;
     case PC_MGS_SPMV:  // u_i gathered, u_0 read, w written
       *bytes = csr + 24.0 * n;
       *flops = 2.0 * nnz + 3.0 * n;
@@ -832,7 +929,8 @@ void prof_settle(gmres_ctx* h, int k) {
     bool work = true;
     if (r.cls == PC_STEP) work = r.j <= k;
     else if (r.cls == PC_MAXPY) work = r.j <= k && r.j < r.i;  // also runs after the stopping step
-    else if (r.cls == PC_MGS_SPMV || r.cls == PC_MGS_AXPY) work = r.j < k;
+    else if (r.cls == PC_MGS_SPMV || r.cls == PC_MGS_AXPY || r.cls == PC_REORTH || r.cls == PC_REORTH_MAXPY)
+      work = r.j < k;
     const int c = work ? r.cls : PC_NOOP;
     h->prof_ms[c] += ms;
     h->prof_cnt[c] += 1;
@@ -937,6 +1035,7 @@ gmres_status gmres_create(const gmres_csr* A, int m_restart, double tol, gmres_h
   std::memset(h->h_st, 0, sizeof(DevState));
   if (alloc_small(h) != GMRES_OK) return bail(GMRES_ERR_CUDA);
   h->step = step_kernel_for<double>(m_restart);
+  h->reorth = reorth_kernel_for(m_restart);
   h->step32 = step_kernel_for<float>(m_restart);
   h->step_smem = sizeof(double) * ((size_t)(m_restart + 1) * (m_restart + 1) + (m_restart + 1));
   h->lsq_smem = sizeof(double) * (size_t)(m_restart + 1) * m_restart;
@@ -953,7 +1052,9 @@ gmres_status gmres_create(const gmres_csr* A, int m_restart, double tol, gmres_h
 
 gmres_status gmres_set(gmres_handle h, gmres_ortho ortho, gmres_prec prec, int max_iter) {
   if (!h) return GMRES_ERR_ARG;
-  if (ortho != GMRES_MGS && ortho != GMRES_ONE_REDUCE_MGS) return fail(h, GMRES_ERR_ARG, "unknown ortho");
+  if (ortho != GMRES_MGS && ortho != GMRES_ONE_REDUCE_MGS && ortho != GMRES_CGS2_LVL2 &&
+      ortho != GMRES_ONE_REDUCE_PIPE2)
+    return fail(h, GMRES_ERR_ARG, "unknown ortho");
   if (prec != GMRES_FP64 && prec != GMRES_IR_FP32)
     return fail(h, GMRES_ERR_ARG, "precision must be GMRES_FP64 or GMRES_IR_FP32");
   if (prec == GMRES_IR_FP32 && ortho != GMRES_ONE_REDUCE_MGS)
@@ -1007,6 +1108,7 @@ gmres_status gmres_solve(gmres_handle h, const double* b, double* x, gmres_info*
   // fresh state
   std::memset(h->h_st, 0, sizeof(DevState));
   h->h_st->tol = h->tol;
+  h->h_st->pipe2 = h->ortho == GMRES_ONE_REDUCE_PIPE2;
   if ((st = write_state(h)) != GMRES_OK) return st;
   const int P = h->P;
   prof_reset(h);
@@ -1269,6 +1371,7 @@ gmres_status gmres_arnoldi(gmres_handle h, const double* r0, int k, double* V_ou
   CUDA_TRY(h, cudaSetDevice(h->device));
   std::memset(h->h_st, 0, sizeof(DevState));
   h->h_st->tol = 0.0;
+  h->h_st->pipe2 = h->ortho == GMRES_ONE_REDUCE_PIPE2;
   if ((st = write_state(h)) != GMRES_OK) return st;
   CUDA_TRY(h, cudaMemsetAsync(h->s.H, 0, sizeof(double) * h->s.ldh * h->m, h->stream));
   CUDA_TRY(h, cudaMemsetAsync(h->s.T, 0, sizeof(double) * h->s.ldh * h->s.ldh, h->stream));
@@ -1295,7 +1398,7 @@ gmres_status gmres_arnoldi(gmres_handle h, const double* r0, int k, double* V_ou
     for (int c = 0; c <= k; ++c)
       for (int r = 0; r <= k; ++r)
         T_out[r + (size_t)c * (k + 1)] =
-            (h->ortho == GMRES_ONE_REDUCE_MGS && r <= kk && c <= kk) ? Td[r + (size_t)c * ld] : 0.0;
+            (h->ortho != GMRES_MGS && r <= kk && c <= kk) ? Td[r + (size_t)c * ld] : 0.0;
   return GMRES_OK;
 }
 

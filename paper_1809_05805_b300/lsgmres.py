@@ -18,9 +18,10 @@ LIB_PATH = os.path.join(_HERE, "liblsgmres.so")
 
 OK, MAXITER, BREAKDOWN_EXACT = 0, 1, 2
 ERR_ARG, ERR_CUDA, ERR_NONFINITE, ERR_OOM, ERR_TIMEOUT = -1, -2, -3, -4, -5
-MGS, ONE_REDUCE_MGS = 0, 1
+MGS, ONE_REDUCE_MGS, CGS2_LVL2, ONE_REDUCE_PIPE2 = 0, 1, 2, 3
 FP64, IR_FP32, IR_BF16 = 0, 1, 2
-ORTHO = {"mgs": MGS, "one_reduce_mgs": ONE_REDUCE_MGS, "one_reduce": ONE_REDUCE_MGS}
+ORTHO = {"mgs": MGS, "one_reduce_mgs": ONE_REDUCE_MGS, "one_reduce": ONE_REDUCE_MGS, "cgs2_lvl2": CGS2_LVL2,
+         "one_reduce_pipe2": ONE_REDUCE_PIPE2}
 PREC = {"fp64": FP64, "ir_fp32": IR_FP32, "ir_bf16": IR_BF16}
 STATUS_NAMES = {0: "OK", 1: "MAXITER", 2: "BREAKDOWN_EXACT", -1: "ERR_ARG", -2: "ERR_CUDA",
                 -3: "ERR_NONFINITE", -4: "ERR_OOM", -5: "ERR_TIMEOUT"}
@@ -88,7 +89,7 @@ EXPORTS = ["gmres_create", "gmres_set", "gmres_set_tol", "gmres_set_stream", "gm
            "gmres_server_last_error", "gmres_server_set_profile", "gmres_server_profile"]
 
 PROFILE_CLASSES = ["one_reduce_step", "arnoldi_maxpy", "mgs_spmv_dot", "mgs_axpy_dot", "residual",
-                   "least_squares", "x_update", "noop"]
+                   "least_squares", "x_update", "noop", "reorth_dot", "reorth_maxpy"]
 
 _lib = None
 
