@@ -337,6 +337,18 @@ def run_ours(args, w, rank, world, dist):
                 "ir_rel_error_vs_fp64": float(np.linalg.norm(xs - x64) / np.linalg.norm(x64)),
                 "step_tflops_fp64": prof_f["one_reduce_step"]["flops"] / (prof_f["one_reduce_step"]["ms"] * 1e9)
                 if prof_f["one_reduce_step"]["ms"] else None}
+        # BF16 basis storage (FP32 arithmetic): the other GMRES-IR storage option
+        s.set(ortho="one_reduce_mgs", prec="ir_bf16", max_iter=w["max_iter"])
+        ms_b, infos_b, prof_b = timed_solves(torch, s, bd, x, max(1, min(args.steps, 2)), 1, stream)
+        ib16 = infos_b[-1]
+        xb = x.cpu().numpy()
+        fp64["ir_bf16"] = {"time_to_solve_s": max_over_ranks(ms_b) / 1e3, "iters": ib16.iters,
+                           "restarts": ib16.restarts, "rel_resid_true": ib16.rel_resid_true,
+                           "rel_error_vs_fp64": float(np.linalg.norm(xb - x64) / np.linalg.norm(x64)),
+                           "step_hbm_gbs": prof_b["one_reduce_step"]["bytes"] / (prof_b["one_reduce_step"]["ms"] * 1e6)
+                           if prof_b["one_reduce_step"]["ms"] else None,
+                           "maxpy_hbm_gbs": prof_b["arnoldi_maxpy"]["bytes"] / (prof_b["arnoldi_maxpy"]["ms"] * 1e6)
+                           if prof_b["arnoldi_maxpy"]["ms"] else None}
         s.set(ortho="one_reduce_mgs", prec=w["prec"], max_iter=w["max_iter"])
     if not args.no_mgs and w["compare"] == "mgs":
         s.set(ortho="mgs", max_iter=w["max_iter"])

@@ -73,7 +73,14 @@ typedef enum { GMRES_MGS = 0, GMRES_ONE_REDUCE_MGS = 1, GMRES_CGS2_LVL2 = 2, GMR
  *                  x += V y stay FP64, so the solve still reaches FP64 residuals.
  *                  One-reduce scheme only; gmres_set allocates the FP32 copies
  *                  ((m+1) n + n + nnz floats, n doubles) on first use.
- *   GMRES_IR_BF16  reserved (rejected). */
+ *   GMRES_IR_BF16  GMRES_IR_FP32 with the basis stored in BF16: each new basis
+ *                  vector is rounded to BF16 (nearest, ties to even) as the
+ *                  MAXPY stores it, and widened exactly on every load; all
+ *                  arithmetic and accumulation stay FP32 (w and the matrix
+ *                  values too). Halves the basis traffic of the cycles; each
+ *                  cycle reduces the residual less, so a solve takes more
+ *                  steps. One-reduce scheme only; gmres_set allocates
+ *                  (m+1) n BF16 values plus the FP32 copies on first use. */
 typedef enum { GMRES_FP64 = 0, GMRES_IR_FP32 = 1, GMRES_IR_BF16 = 2 } gmres_prec;
 
 typedef struct gmres_ctx* gmres_handle;
@@ -114,7 +121,7 @@ gmres_status gmres_create(const gmres_csr* A, int m_restart, double tol, gmres_h
 
 /* Select the orthogonalization scheme, the arithmetic and the iteration limit
  * (max_iter >= 0 Arnoldi steps over all cycles). GMRES_ERR_ARG for an unknown
- * scheme, GMRES_IR_BF16, GMRES_IR_FP32 with a scheme other than
+ * scheme, GMRES_IR_FP32 or GMRES_IR_BF16 with a scheme other than
  * GMRES_ONE_REDUCE_MGS, or max_iter < 0;
  * GMRES_ERR_OOM if the FP32 copies cannot be allocated. */
 gmres_status gmres_set(gmres_handle h, gmres_ortho ortho, gmres_prec prec, int max_iter);

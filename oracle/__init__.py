@@ -24,7 +24,7 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 
 ORC_OK, ORC_MAXITER, ORC_BREAKDOWN = 0, 1, 2
 ORC_ERR_ARG, ORC_ERR_NONFINITE, ORC_ERR_OOM = -1, -3, -4
-MGS, ONE_REDUCE, IR_FP32, CGS2, PIPE2 = 0, 1, 2, 3, 4
+MGS, ONE_REDUCE, IR_FP32, CGS2, PIPE2, IR_BF16 = 0, 1, 2, 3, 4, 5
 
 CFLAGS = ["-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-std=c99"]
 
@@ -82,6 +82,8 @@ class Oracle:
             ctypes.POINTER(ctypes.c_int),
         ]
         lib.orc_gmres.restype = ctypes.c_int
+        lib.orc_round_bf16.argtypes = [ctypes.c_float]
+        lib.orc_round_bf16.restype = ctypes.c_float
         self.lib = lib
 
     # -- kernels -----------------------------------------------------------
@@ -136,6 +138,11 @@ class Oracle:
     def qr_cgs2_lvl2(self, A):
         """Level-2 iterated CGS with lagged normalization (Algorithm 5); returns Q, R, T."""
         return self._qr(self.lib.orc_qr_cgs2_lvl2, A, with_T=True)
+
+    def round_bf16(self, x: np.ndarray) -> np.ndarray:
+        """The oracle's FP32 -> BF16 rounding (as FP32 values), element by element."""
+        return np.array([self.lib.orc_round_bf16(float(v)) for v in np.asarray(x, dtype=np.float32)],
+                        dtype=np.float32)
 
     # -- solver ------------------------------------------------------------
     def gmres(self, A, b, *, variant: int, m: int, tol: float, max_iter: int, x0=None,

@@ -36,6 +36,8 @@
  *                       variant 4: variant 1 with the Givens rotations applied
  *                                  two columns at a time, the L = 2 pipeline
  *                                  of Algorithm 8 [A17]
+ *                       variant 5: variant 2 with the basis stored in BF16
+ *                                  (FP32 arithmetic and accumulation) [A18]
  *
  * Parity unpinned at rounding level: the second-pass coefficients that
  * orc_qr_cgs2_lvl2 and variant 3 add to R and H are of the size of the rounding
@@ -52,8 +54,8 @@
  *   limiting-accuracy stall of the Simoncini-Szyld diagonal problem
  *   (Section V-A); and source-level mutants of this file that each pin catches.
  *
- * Readings of passages that are ambiguous or garbled in the paper are listed
- * where they are used, tagged [A1]..[A9].
+ * Readings of passages that are ambiguous or garbled in the paper (and of the
+ * extensions beyond it) are listed where they are used, tagged [A1]..[A18].
  */
 #include <math.h>
 #include <stdint.h>
@@ -72,6 +74,7 @@
 #define ORC_VARIANT_IR_FP32 2
 #define ORC_VARIANT_CGS2 3
 #define ORC_VARIANT_PIPE2 4
+#define ORC_VARIANT_IR_BF16 5
 
 /* Breakdown threshold factor [A6]: the new direction is declared exhausted
  * when its norm is below BREAKDOWN_FACTOR * eps * ||Hbar(:, j)||. */
@@ -614,17 +617,42 @@ static float dot_f32(int64_t n, const float* x, const float* y) {
   return s;
 }
 
-/* One cycle of cycle_one_reduce's steps with FP32 vectors. On entry V column 0
+/* Round an FP32 value to the nearest BF16 value (8 significant bits, ties to
+ * even), returned as the FP32 number it represents [A18]. BF16 is the upper
+ * half of an FP32 word; NaN stays NaN. */
+static float round_bf16(float f) {
+  uint32_t u;
+  memcpy(&u, &f, 4);
+  if ((u & 0x7f800000u) == 0x7f800000u) return f; /* Inf / NaN */
+  const uint32_t lsb = (u >> 16) & 1u;
+  u = (u + 0x7fffu + lsb) & 0xffff0000u;
+  float r;
+  memcpy(&r, &u, 4);
+  return r;
+}
+
+/* Exported for the pin that compares the rounding with an independent BF16 conversion. */
+float orc_round_bf16(float f) { return round_bf16(f); }
+
+static void round_bf16_vec(int64_t n, float* x, int on) {
+  if (!on) return;
+  for (int64_t i = 0; i < n; ++i) x[i] = round_bf16(x[i]);
+}
+
+/* One cycle of cycle_one_reduce's steps with FP32 vectors. With bf16 set, each
+ * basis vector v_j is stored in BF16: rounded once, when it is normalized
+ * (v_0 when it is formed) [A18]. On entry V column 0
  * (FP64) holds r0 = b - A x and beta0 = ||r0|| (FP64). On exit the cycle's FP32
  * basis, widened, is in V (FP64) for the correction, and H, T, g as in FP64. */
 static cycle_out cycle_one_reduce_f32(cycle_ws* ws, float* V32, float* w32, const float* val32, int kmax,
                                       double beta0, double bnorm, double tol, double* hist, int* hlen,
-                                      int hcap, int64_t* nred) {
+                                      int hcap, int64_t* nred, int bf16) {
   cycle_out out = {0, 0, 0.0};
   const int64_t n = ws->n;
   const int ld = ws->m + 1;
 #define V32COL(k) (V32 + (size_t)(k) * n)
   for (int64_t l = 0; l < n; ++l) V32COL(0)[l] = (float)(VCOL(ws, 0)[l] / beta0); /* v_0 */
+  round_bf16_vec(n, V32COL(0), bf16);
   memset(ws->g, 0, sizeof(double) * (size_t)ld);
   ws->g[0] = beta0;
   memset(ws->T, 0, sizeof(double) * (size_t)ld * ld);
@@ -665,6 +693,7 @@ static cycle_out cycle_one_reduce_f32(cycle_ws* ws, float* V32, float* w32, cons
     }
     const float ib = (float)(1.0 / beta);
     for (int64_t l = 0; l < n; ++l) u[l] *= ib; /* v_j */
+    round_bf16_vec(n, u, bf16);
 
     for (int i = 0; i < j; ++i) ws->a[i] /= beta;
     for (int k = 0; k < j; ++k) {
@@ -720,7 +749,7 @@ int orc_gmres(int64_t n, const int32_t* rowptr, const int32_t* col, const double
               double* V1, double* H1, double* T1, int* k1) {
   if (n <= 0 || m <= 0 || max_iter < 0 || !(tol >= 0.0) || !b || !x || !info) return ORC_ERR_ARG;
   if (variant != ORC_VARIANT_MGS && variant != ORC_VARIANT_ONE_REDUCE && variant != ORC_VARIANT_IR_FP32 &&
-      variant != ORC_VARIANT_CGS2 && variant != ORC_VARIANT_PIPE2)
+      variant != ORC_VARIANT_CGS2 && variant != ORC_VARIANT_PIPE2 && variant != ORC_VARIANT_IR_BF16)
     return ORC_ERR_ARG;
   memset(info, 0, sizeof(*info));
   if (!all_finite(n, b) || !all_finite(n, x)) {
@@ -754,7 +783,7 @@ int orc_gmres(int64_t n, const int32_t* rowptr, const int32_t* col, const double
   float* w32 = NULL;
   float* val32 = NULL;
   int status = ORC_OK;
-  if (variant == ORC_VARIANT_IR_FP32) {
+  if (variant == ORC_VARIANT_IR_FP32 || variant == ORC_VARIANT_IR_BF16) {
     const int64_t nnz = rowptr[n];
     V32 = (float*)malloc(sizeof(float) * (size_t)n * ld);
     w32 = (float*)malloc(sizeof(float) * (size_t)n);
@@ -811,7 +840,7 @@ int orc_gmres(int64_t n, const int32_t* rowptr, const int32_t* col, const double
                             variant == ORC_VARIANT_CGS2, variant == ORC_VARIANT_PIPE2);
     else
       co = cycle_one_reduce_f32(&ws, V32, w32, val32, kmax, beta0, bnorm, tol, hist, &hlen, hist_cap,
-                                &info->reductions);
+                                &info->reductions, variant == ORC_VARIANT_IR_BF16);
     if (first) {
       if (V1) memcpy(V1, ws.V, sizeof(double) * (size_t)n * ld);
       if (H1) memcpy(H1, ws.H, sizeof(double) * ld * mm);

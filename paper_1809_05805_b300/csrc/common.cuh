@@ -6,6 +6,7 @@
 // unit gets its own copy.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <cstddef>
@@ -111,12 +112,24 @@ __device__ __forceinline__ double block_sum(double v, double* sbuf /* kWarps */)
   return t;
 }
 
-// Row i of A times x (CSR, FP64 FMA chain in column order). The loads of up
-// to 8 entries are issued together (predicated), so a stencil row costs two
-// dependent memory latencies (indices, then the gather) instead of two per entry.
-template <typename VT>
+// Load a stored value through the read-only path, widened to the compute type
+// CT (the identity when the storage type is CT; BF16 storage widens exactly).
+template <typename CT, typename ST>
+__device__ __forceinline__ CT ld_as(const ST* p) {
+  return (CT)__ldg(p);
+}
+template <>
+__device__ __forceinline__ float ld_as<float, __nv_bfloat16>(const __nv_bfloat16* p) {
+  return __bfloat162float(__ldg(p));
+}
+
+// Row i of A times x (CSR, FMA chain in column order, in the type of val; x
+// may be stored narrower). The loads of up to 8 entries are issued together
+// (predicated), so a stencil row costs two dependent memory latencies
+// (indices, then the gather) instead of two per entry.
+template <typename VT, typename XT>
 __device__ __forceinline__ VT csr_row(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-                                          const VT* __restrict__ val, const VT* __restrict__ x,
+                                          const VT* __restrict__ val, const XT* __restrict__ x,
                                           int64_t i) {
   constexpr int kW = 8;
   const int p0 = __ldg(rowptr + i), p1 = __ldg(rowptr + i + 1);
@@ -131,7 +144,7 @@ __device__ __forceinline__ VT csr_row(const int32_t* __restrict__ rowptr, const 
       v[e] = ok ? __ldg(val + p + e) : VT(0);
     }
 #pragma unroll
-    for (int e = 0; e < kW; ++e) xv[e] = (p + e < p1) ? __ldg(x + c[e]) : VT(0);
+    for (int e = 0; e < kW; ++e) xv[e] = (p + e < p1) ? ld_as<VT>(x + c[e]) : VT(0);
 #pragma unroll
     for (int e = 0; e < kW; ++e)
       if (p + e < p1) s = fma(v[e], xv[e], s);
@@ -141,9 +154,9 @@ __device__ __forceinline__ VT csr_row(const int32_t* __restrict__ rowptr, const 
 
 // Rows r0 and r1 of A times x with the loads of both rows in flight together
 // (rows of up to 8 entries; longer rows use csr_row). Rows >= n give 0.
-template <typename VT>
+template <typename VT, typename XT>
 __device__ __forceinline__ void csr_row2(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-                                         const VT* __restrict__ val, const VT* __restrict__ x,
+                                         const VT* __restrict__ val, const XT* __restrict__ x,
                                          int64_t r0, int64_t r1, int64_t n, VT& y0, VT& y1) {
   constexpr int kW = 8;
   const int a0 = r0 < n ? __ldg(rowptr + r0) : 0, b0 = r0 < n ? __ldg(rowptr + r0 + 1) : 0;
@@ -161,8 +174,8 @@ __device__ __forceinline__ void csr_row2(const int32_t* __restrict__ rowptr, con
     VT x0[kW], x1[kW];
 #pragma unroll
     for (int e = 0; e < kW; ++e) {
-      x0[e] = (a0 + e < b0) ? __ldg(x + c0[e]) : VT(0);
-      x1[e] = (a1 + e < b1) ? __ldg(x + c1[e]) : VT(0);
+      x0[e] = (a0 + e < b0) ? ld_as<VT>(x + c0[e]) : VT(0);
+      x1[e] = (a1 + e < b1) ? ld_as<VT>(x + c1[e]) : VT(0);
     }
     VT s0 = VT(0), s1 = VT(0);
 #pragma unroll
@@ -354,11 +367,11 @@ __device__ int finish_completed(Small s, int c, double h, bool tail) {
 // rowptr[i] .. rowptr[i+1] of col/val, gathering xg[col] (a single system
 // passes xg = u; a system stored at rows row0.. of a shared arena passes its
 // own CSR shifted by -row0 and xg = u + row0).
-template <int MAXC, typename VT>
+template <int MAXC, typename SV, typename VT = SV>
 __device__ __forceinline__ void tile_block_dot(int64_t t, int64_t n, const int32_t* __restrict__ rowptr,
                                                const int32_t* __restrict__ col, const VT* __restrict__ val,
-                                               const VT* __restrict__ V, int64_t ldv, const VT* __restrict__ u,
-                                               const VT* __restrict__ xg, VT* __restrict__ w, bool spmv,
+                                               const SV* __restrict__ V, int64_t ldv, const SV* __restrict__ u,
+                                               const SV* __restrict__ xg, VT* __restrict__ w, bool spmv,
                                                bool need_w, int J8, int r8, VT* su,
                                                VT* sw, VT (&acc_a)[MAXC], VT (&acc_c)[MAXC],
                                                VT (&rem_a)[kWarps - 1], VT (&rem_c)[kWarps - 1], VT& sig,
@@ -367,7 +380,7 @@ __device__ __forceinline__ void tile_block_dot(int64_t t, int64_t n, const int32
   const int64_t row = t * kThreads + threadIdx.x;
   VT ur = VT(0), wr = VT(0);
   if (row < n) {
-    ur = u[row];
+    ur = ld_as<VT>(u + row);
     if (spmv) {
       wr = csr_row(rowptr, col, val, xg, row);
       w[row] = wr;
@@ -391,10 +404,10 @@ __device__ __forceinline__ void tile_block_dot(int64_t t, int64_t n, const int32
   for (int c = 0; c < MAXC; ++c) {
     if (c < J8) {  // warp-uniform
       const int k = wid + c * kWarps;
-      const VT* vk = V + (size_t)k * ldv + base;
+      const SV* vk = V + (size_t)k * ldv + base;
       VT x[kRowsPerLane];
 #pragma unroll
-      for (int q = 0; q < kRowsPerLane; ++q) x[q] = (base + 32 * q < n) ? __ldg(vk + 32 * q) : VT(0);
+      for (int q = 0; q < kRowsPerLane; ++q) x[q] = (base + 32 * q < n) ? ld_as<VT>(vk + 32 * q) : VT(0);
 #pragma unroll
       for (int q = 0; q < kRowsPerLane; ++q) acc_a[c] = fma(x[q], ru[q], acc_a[c]);
       if (need_w) {  // the cycle's tail needs only V^T u
@@ -406,7 +419,7 @@ __device__ __forceinline__ void tile_block_dot(int64_t t, int64_t n, const int32
 #pragma unroll
   for (int c = 0; c < kWarps - 1; ++c) {
     if (c < r8) {  // block-uniform
-      const VT x = (row < n) ? __ldg(V + (size_t)(J8 * kWarps + c) * ldv + row) : VT(0);
+      const VT x = (row < n) ? ld_as<VT>(V + (size_t)(J8 * kWarps + c) * ldv + row) : VT(0);
       rem_a[c] = fma(x, ur, rem_a[c]);
       if (need_w) rem_c[c] = fma(x, wr, rem_c[c]);
     }
@@ -418,11 +431,11 @@ __device__ __forceinline__ void tile_block_dot(int64_t t, int64_t n, const int32
 // block dot, two rows per thread: the CSR loads of both rows are in flight
 // together, halving the latency-bound SpMV phases per row. su, sw hold 512
 // values.
-template <int MAXC, typename VT>
+template <int MAXC, typename SV, typename VT = SV>
 __device__ __forceinline__ void tile_pair_block_dot(int64_t pp, int64_t n, const int32_t* __restrict__ rowptr,
                                                     const int32_t* __restrict__ col, const VT* __restrict__ val,
-                                                    const VT* __restrict__ V, int64_t ldv, const VT* __restrict__ u,
-                                                    const VT* __restrict__ xg, VT* __restrict__ w, bool spmv,
+                                                    const SV* __restrict__ V, int64_t ldv, const SV* __restrict__ u,
+                                                    const SV* __restrict__ xg, VT* __restrict__ w, bool spmv,
                                                     bool need_w, int J8, int r8,
                                                     VT* su, VT* sw, VT (&acc_a)[MAXC], VT (&acc_c)[MAXC],
                                                     VT (&rem_a)[kWarps - 1], VT (&rem_c)[kWarps - 1], VT& sig,
@@ -430,8 +443,8 @@ __device__ __forceinline__ void tile_pair_block_dot(int64_t pp, int64_t n, const
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int64_t row0 = pp * (2 * kThreads) + threadIdx.x, row1 = row0 + kThreads;
   VT ur0 = VT(0), wr0 = VT(0), ur1 = VT(0), wr1 = VT(0);
-  if (row0 < n) ur0 = u[row0];
-  if (row1 < n) ur1 = u[row1];
+  if (row0 < n) ur0 = ld_as<VT>(u + row0);
+  if (row1 < n) ur1 = ld_as<VT>(u + row1);
   if (spmv) {
     csr_row2(rowptr, col, val, xg, row0, row1, n, wr0, wr1);
     if (row0 < n) w[row0] = wr0;
@@ -462,10 +475,10 @@ __device__ __forceinline__ void tile_pair_block_dot(int64_t pp, int64_t n, const
     for (int c = 0; c < MAXC; ++c) {
       if (c < J8) {  // warp-uniform
         const int k = wid + c * kWarps;
-        const VT* vk = V + (size_t)k * ldv + base;
+        const SV* vk = V + (size_t)k * ldv + base;
         VT x[kRowsPerLane];
 #pragma unroll
-        for (int q = 0; q < kRowsPerLane; ++q) x[q] = (base + 32 * q < n) ? __ldg(vk + 32 * q) : VT(0);
+        for (int q = 0; q < kRowsPerLane; ++q) x[q] = (base + 32 * q < n) ? ld_as<VT>(vk + 32 * q) : VT(0);
 #pragma unroll
         for (int q = 0; q < kRowsPerLane; ++q) acc_a[c] = fma(x[q], ru[q], acc_a[c]);
         if (need_w) {  // the cycle's tail needs only V^T u
@@ -478,9 +491,9 @@ __device__ __forceinline__ void tile_pair_block_dot(int64_t pp, int64_t n, const
 #pragma unroll
   for (int c = 0; c < kWarps - 1; ++c) {
     if (c < r8) {  // block-uniform
-      const VT* vk = V + (size_t)(J8 * kWarps + c) * ldv;
-      const VT x0 = (row0 < n) ? __ldg(vk + row0) : VT(0);
-      const VT x1 = (row1 < n) ? __ldg(vk + row1) : VT(0);
+      const SV* vk = V + (size_t)(J8 * kWarps + c) * ldv;
+      const VT x0 = (row0 < n) ? ld_as<VT>(vk + row0) : VT(0);
+      const VT x1 = (row1 < n) ? ld_as<VT>(vk + row1) : VT(0);
       rem_a[c] = fma(x0, ur0, rem_a[c]);
       rem_a[c] = fma(x1, ur1, rem_a[c]);
       if (need_w) {

@@ -40,11 +40,13 @@
 
 namespace {
 
-template <int MAXC, typename VT>
+// VT: arithmetic type (and of A's values and w); SV: storage type of the
+// basis (VT, or BF16 for GMRES-IR with BF16 storage, widened exactly on load).
+template <int MAXC, typename VT, typename SV = VT>
 __global__ void __launch_bounds__(kThreads, 2)
 k_one_reduce_step(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-                  const VT* __restrict__ val, const VT* __restrict__ V, int64_t ldv,
-                  const VT* __restrict__ u_arg, VT* __restrict__ w, int64_t n, Small s,
+                  const VT* __restrict__ val, const SV* __restrict__ V, int64_t ldv,
+                  const SV* __restrict__ u_arg, VT* __restrict__ w, int64_t n, Small s,
                   int j_arg, int use_spmv, double* raw_out) {
   __shared__ VT su[2 * kThreads];
   __shared__ VT sw[2 * kThreads];
@@ -68,7 +70,7 @@ k_one_reduce_step(const int32_t* __restrict__ rowptr, const int32_t* __restrict_
   const bool tail = s_tail;
   const bool spmv = raw_out ? (use_spmv != 0) : !tail;
   const bool need_w = raw_out ? true : !tail;
-  const VT* u = raw_out ? u_arg : V + (size_t)j * ldv;
+  const SV* u = raw_out ? u_arg : V + (size_t)j * ldv;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 
   // Work split of the block dot over a tile of 256 rows (8 row groups of 32):
@@ -91,12 +93,12 @@ k_one_reduce_step(const int32_t* __restrict__ rowptr, const int32_t* __restrict_
   if (ntiles >= 4 * (int64_t)gridDim.x) {
     const int64_t npairs = (ntiles + 1) / 2;
     for (int64_t pp = blockIdx.x; pp < npairs; pp += gridDim.x)
-      tile_pair_block_dot<MAXC, VT>(pp, n, rowptr, col, val, V, ldv, u, u, w, spmv, need_w, J8, r8, su, sw, acc_a,
-                                    acc_c, rem_a, rem_c, sig, dd);
+      tile_pair_block_dot<MAXC, SV, VT>(pp, n, rowptr, col, val, V, ldv, u, u, w, spmv, need_w, J8, r8, su, sw,
+                                        acc_a, acc_c, rem_a, rem_c, sig, dd);
   } else {
     for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x)
-      tile_block_dot<MAXC, VT>(t, n, rowptr, col, val, V, ldv, u, u, w, spmv, need_w, J8, r8, su, sw, acc_a, acc_c,
-                               rem_a, rem_c, sig, dd);
+      tile_block_dot<MAXC, SV, VT>(t, n, rowptr, col, val, V, ldv, u, u, w, spmv, need_w, J8, r8, su, sw, acc_a,
+                                   acc_c, rem_a, rem_c, sig, dd);
   }
 
   cta_partials<MAXC, VT>(acc_a, acc_c, rem_a, rem_c, sig, dd, j, J8, r8, red);
@@ -146,11 +148,11 @@ k_reorth(const double* __restrict__ V, int64_t ldv, int64_t n, Small s) {
   if (ntiles >= 4 * (int64_t)gridDim.x) {
     const int64_t npairs = (ntiles + 1) / 2;
     for (int64_t pp = blockIdx.x; pp < npairs; pp += gridDim.x)
-      tile_pair_block_dot<MAXC, double>(pp, n, nullptr, nullptr, nullptr, V, ldv, z, z, nullptr, false, false, J8,
+      tile_pair_block_dot<MAXC, double, double>(pp, n, nullptr, nullptr, nullptr, V, ldv, z, z, nullptr, false, false, J8,
                                         r8, su, sw, acc_a, acc_c, rem_a, rem_c, sig, dd);
   } else {
     for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x)
-      tile_block_dot<MAXC, double>(t, n, nullptr, nullptr, nullptr, V, ldv, z, z, nullptr, false, false, J8, r8, su,
+      tile_block_dot<MAXC, double, double>(t, n, nullptr, nullptr, nullptr, V, ldv, z, z, nullptr, false, false, J8, r8, su,
                                    sw, acc_a, acc_c, rem_a, rem_c, sig, dd);
   }
   cta_partials<MAXC, double>(acc_a, acc_c, rem_a, rem_c, sig, dd, jj, J8, r8, red);
@@ -296,6 +298,78 @@ k_maxpy(const VT* __restrict__ V, int64_t ldv, const YT* y_in, YT* y_out, int64_
   }
 }
 
+// Arnoldi MAXPY of GMRES-IR with BF16 basis storage: u_{j+1} = alpha w +
+// sum_k c_k u_k computed in FP32 (w in FP32, the basis widened from BF16, the
+// coefficients rounded to FP32) and rounded to BF16 (nearest, ties to even)
+// as it is stored; eight BF16 values per 16-byte access. The last CTA
+// finishes column j-1 of H as in k_maxpy.
+__global__ void __launch_bounds__(kThreads, 4)
+k_maxpy_bf16(__nv_bfloat16* __restrict__ V, int64_t ldv, const float* __restrict__ w, int64_t n, Small s) {
+  __shared__ float scc[kMaxM + 3];
+  __shared__ int sK, s_skip, s_step;
+  DevState* st = s.st;
+  if (threadIdx.x == 0) {
+    s_skip = __ldcg(&st->done);
+    sK = __ldcg(&st->maxpy_k);
+    s_step = __ldcg(&st->step);
+  }
+  __syncthreads();
+  if (s_skip) return;
+  const int K = sK;
+  for (int i = threadIdx.x; i <= K; i += blockDim.x) scc[i] = (float)__ldcg(s.coef + i);
+  __syncthreads();
+  if (blockIdx.x == gridDim.x - 1) {
+    const int j = s_step - 1;
+    if (j >= 1) {
+      const double h = __ldcg(&s.H[(size_t)(j - 1) * s.ldh + j]);
+      const int stop = finish_completed(s, j - 1, h, false);
+      if (threadIdx.x == 0) {
+        st->grid_syncs += 1;
+        if (stop) st->done = 1;
+      }
+    }
+    return;
+  }
+  __nv_bfloat16* out = V + (size_t)s_step * ldv;
+  const int ndata = gridDim.x - 1;
+  const int64_t stride = (int64_t)ndata * blockDim.x;
+  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const float alpha = scc[0];
+  const int64_t n8 = n / 8;  // columns start on 16-byte boundaries (ldv is a multiple of 32)
+  for (int64_t i = gid; i < n8; i += stride) {
+    const float4 w0 = reinterpret_cast<const float4*>(w)[2 * i];
+    const float4 w1 = reinterpret_cast<const float4*>(w)[2 * i + 1];
+    float a[8] = {alpha * w0.x, alpha * w0.y, alpha * w0.z, alpha * w0.w,
+                  alpha * w1.x, alpha * w1.y, alpha * w1.z, alpha * w1.w};
+    for (int k = 0; k < K; ++k) {
+      union {
+        uint4 v;
+        __nv_bfloat162 h[4];
+      } x;
+      x.v = __ldg(reinterpret_cast<const uint4*>(V + (size_t)k * ldv) + i);
+      const float c = scc[1 + k];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float2 f = __bfloat1622float2(x.h[q]);
+        a[2 * q] = fmaf(c, f.x, a[2 * q]);
+        a[2 * q + 1] = fmaf(c, f.y, a[2 * q + 1]);
+      }
+    }
+    union {
+      uint4 v;
+      __nv_bfloat162 h[4];
+    } o;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) o.h[q] = __floats2bfloat162_rn(a[2 * q], a[2 * q + 1]);
+    reinterpret_cast<uint4*>(out)[i] = o.v;
+  }
+  for (int64_t i = 8 * n8 + gid; i < n; i += stride) {  // ragged tail
+    float a0 = alpha * w[i];
+    for (int k = 0; k < K; ++k) a0 = fmaf(scc[1 + k], __bfloat162float(V[(size_t)k * ldv + i]), a0);
+    out[i] = __float2bfloat16_rn(a0);
+  }
+}
+
 // --------------------------------------------------------------------------
 // MGS-GMRES kernels (Algorithm 6)
 // --------------------------------------------------------------------------
@@ -432,15 +506,19 @@ k_residual(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
   if (threadIdx.x == 0) residual_finish(s, red[0], mode, kmax);
 }
 
-// Start of an FP32 (GMRES-IR) cycle: column 0 of the FP32 basis = r / ||r||
-// rounded to FP32 (normalized in FP64 first, so the FP32 cycle works on a
-// unit-scale right-hand side); the estimate and the correction of this cycle
-// are scaled back by ||r||.
-__global__ void k_round_scaled(const double* __restrict__ r, float* __restrict__ out, int64_t n, Small s) {
+// Start of an FP32 (GMRES-IR) cycle: column 0 of the FP32 (or BF16) basis =
+// r / ||r|| rounded to FP32 (then BF16) (normalized in FP64 first, so the FP32
+// cycle works on a unit-scale right-hand side); the estimate and the
+// correction of this cycle are scaled back by ||r||.
+__device__ __forceinline__ void store_narrow(float* p, double x) { *p = (float)x; }
+__device__ __forceinline__ void store_narrow(__nv_bfloat16* p, double x) { *p = __float2bfloat16_rn((float)x); }
+
+template <typename OT>
+__global__ void k_round_scaled(const double* __restrict__ r, OT* __restrict__ out, int64_t n, Small s) {
   const double rn = __ldcg(&s.st->rnorm);
   const double ir = 1.0 / rn;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) out[i] = (float)(r[i] * ir);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) store_narrow(out + i, r[i] * ir);
   if (blockIdx.x == 0 && threadIdx.x == 0) s.st->cycle_scale = rn;
 }
 
@@ -488,8 +566,8 @@ constexpr size_t kNoAllocBytes = kNoAllocStateBytes + sizeof(double) * (size_t)k
 static_assert(sizeof(DevState) <= kNoAllocStateBytes, "DevState outgrew its slot");
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
-template <typename VT>
-using StepKernel = void (*)(const int32_t*, const int32_t*, const VT*, const VT*, int64_t, const VT*, VT*, int64_t,
+template <typename VT, typename SV = VT>
+using StepKernel = void (*)(const int32_t*, const int32_t*, const VT*, const SV*, int64_t, const SV*, VT*, int64_t,
                             Small, int, int, double*);
 
 using ReorthKernel = void (*)(const double*, int64_t, int64_t, Small);
@@ -510,19 +588,19 @@ ReorthKernel reorth_kernel_for(int m) {
 }
 
 // MAXC = floor(m / 8) whole columns per warp (j <= m), at least 1.
-template <typename VT>
-StepKernel<VT> step_kernel_for(int m) {
+template <typename VT, typename SV = VT>
+StepKernel<VT, SV> step_kernel_for(int m) {
   switch (std::max(1, m / kWarps)) {
-    case 1: return k_one_reduce_step<1, VT>;
-    case 2: return k_one_reduce_step<2, VT>;
-    case 3: return k_one_reduce_step<3, VT>;
-    case 4: return k_one_reduce_step<4, VT>;
-    case 5: return k_one_reduce_step<5, VT>;
-    case 6: return k_one_reduce_step<6, VT>;
-    case 7: return k_one_reduce_step<7, VT>;
-    case 8: return k_one_reduce_step<8, VT>;
-    case 9: case 10: case 11: case 12: return k_one_reduce_step<12, VT>;
-    default: return k_one_reduce_step<16, VT>;
+    case 1: return k_one_reduce_step<1, VT, SV>;
+    case 2: return k_one_reduce_step<2, VT, SV>;
+    case 3: return k_one_reduce_step<3, VT, SV>;
+    case 4: return k_one_reduce_step<4, VT, SV>;
+    case 5: return k_one_reduce_step<5, VT, SV>;
+    case 6: return k_one_reduce_step<6, VT, SV>;
+    case 7: return k_one_reduce_step<7, VT, SV>;
+    case 8: return k_one_reduce_step<8, VT, SV>;
+    case 9: case 10: case 11: case 12: return k_one_reduce_step<12, VT, SV>;
+    default: return k_one_reduce_step<16, VT, SV>;
   }
 }
 
@@ -555,9 +633,11 @@ struct gmres_ctx {
   StepKernel<double> step = nullptr;
   ReorthKernel reorth = nullptr;
   StepKernel<float> step32 = nullptr;
-  // GMRES-IR (FP32 cycles): FP32 basis, SpMV result and matrix values, and the
-  // FP64 restart residual; allocated by gmres_set(GMRES_IR_FP32)
+  StepKernel<float, __nv_bfloat16> step16 = nullptr;
+  // GMRES-IR (FP32 cycles): FP32 (or BF16) basis, FP32 SpMV result and matrix
+  // values, and the FP64 restart residual; allocated by gmres_set
   float* V32 = nullptr;
+  __nv_bfloat16* V16 = nullptr;
   float* w32 = nullptr;
   float* val32 = nullptr;
   double* r64 = nullptr;
@@ -711,6 +791,9 @@ gmres_status launch_cycle(gmres_ctx* h, int kmax) {
       if (h->prec == GMRES_IR_FP32)
         h->step32<<<P, kThreads, h->step_smem, h->stream>>>(h->rowptr, h->col, h->val32, h->V32, h->ldv, nullptr,
                                                             h->w32, h->n, h->s, 0, 1, nullptr);
+      else if (h->prec == GMRES_IR_BF16)
+        h->step16<<<P, kThreads, h->step_smem, h->stream>>>(h->rowptr, h->col, h->val32, h->V16, h->ldv, nullptr,
+                                                            h->w32, h->n, h->s, 0, 1, nullptr);
       else
         h->step<<<P, kThreads, h->step_smem, h->stream>>>(h->rowptr, h->col, h->val, h->V, h->ldv, nullptr, h->w,
                                                           h->n, h->s, 0, 1, nullptr);
@@ -721,6 +804,8 @@ gmres_status launch_cycle(gmres_ctx* h, int kmax) {
         if (h->prec == GMRES_IR_FP32)
           k_maxpy<float, float, float><<<h->grid_stream + 1, kThreads, 0, h->stream>>>(
               h->V32, h->ldv, h->w32, nullptr, h->n, h->s, MAXPY_ARNOLDI, 0);
+        else if (h->prec == GMRES_IR_BF16)
+          k_maxpy_bf16<<<h->grid_stream + 1, kThreads, 0, h->stream>>>(h->V16, h->ldv, h->w32, h->n, h->s);
         else
           k_maxpy<double, double, double><<<h->grid_stream + 1, kThreads, 0, h->stream>>>(
               h->V, h->ldv, h->w, nullptr, h->n, h->s, MAXPY_ARNOLDI, 0);
@@ -872,8 +957,10 @@ gmres_status run_cycle(gmres_ctx* h, int kmax) {
 // values, 4-byte indices; a vector read once counts once).
 void alg_model(const gmres_ctx* h, const gmres_ctx::ProfRec& r, int kx, double* bytes, double* flops) {
   const double n = (double)h->n, nnz = (double)h->nnz;
-  const bool f32 = h->prec == GMRES_IR_FP32;          // FP32 cycle: 4-byte vectors and values
-  const double vb = f32 ? 4.0 : 8.0;
+  // FP32 cycles: 4-byte values and w; basis vectors 4 bytes (FP32) or 2 (BF16)
+  const bool f32 = h->prec == GMRES_IR_FP32 || h->prec == GMRES_IR_BF16;
+  const double wb = f32 ? 4.0 : 8.0;
+  const double vb = h->prec == GMRES_IR_BF16 ? 2.0 : wb;
   const double csr = 4.0 * (n + 1) + (4.0 + (f32 && (r.cls == PC_STEP) ? 4.0 : 8.0)) * nnz;
   switch (r.cls) {
     case PC_STEP:
@@ -881,12 +968,12 @@ void alg_model(const gmres_ctx* h, const gmres_ctx::ProfRec& r, int kx, double* 
         *bytes = vb * n * (r.j + 1);
         *flops = 2.0 * n * (r.j + 1);
       } else {
-        *bytes = csr + vb * n * (r.j + 2);  // u (gathered), j basis columns, w written
+        *bytes = csr + vb * n * (r.j + 1) + wb * n;  // u (gathered), j basis columns, w written
         *flops = 2.0 * nnz + 2.0 * n * (2.0 * r.j + 2.0);
       }
       break;
-    case PC_MAXPY:  // w, j+1 columns read, one column written
-      *bytes = vb * n * (r.j + 3);
+    case PC_MAXPY:  // w and j+1 columns read, one column written
+      *bytes = wb * n + vb * n * (r.j + 2);
       *flops = 2.0 * n * (r.j + 1) + n;
       break;
     case PC_REORTH:  // z and j+1 basis columns read
@@ -1037,11 +1124,14 @@ gmres_status gmres_create(const gmres_csr* A, int m_restart, double tol, gmres_h
   h->step = step_kernel_for<double>(m_restart);
   h->reorth = reorth_kernel_for(m_restart);
   h->step32 = step_kernel_for<float>(m_restart);
+  h->step16 = step_kernel_for<float, __nv_bfloat16>(m_restart);
   h->step_smem = sizeof(double) * ((size_t)(m_restart + 1) * (m_restart + 1) + (m_restart + 1));
   h->lsq_smem = sizeof(double) * (size_t)(m_restart + 1) * m_restart;
   CREATE_TRY(cudaFuncSetAttribute(reinterpret_cast<const void*>(h->step),
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->step_smem));
   CREATE_TRY(cudaFuncSetAttribute(reinterpret_cast<const void*>(h->step32),
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->step_smem));
+  CREATE_TRY(cudaFuncSetAttribute(reinterpret_cast<const void*>(h->step16),
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->step_smem));
   CREATE_TRY(cudaFuncSetAttribute(reinterpret_cast<const void*>(k_lsq),
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->lsq_smem));
@@ -1055,16 +1145,24 @@ gmres_status gmres_set(gmres_handle h, gmres_ortho ortho, gmres_prec prec, int m
   if (ortho != GMRES_MGS && ortho != GMRES_ONE_REDUCE_MGS && ortho != GMRES_CGS2_LVL2 &&
       ortho != GMRES_ONE_REDUCE_PIPE2)
     return fail(h, GMRES_ERR_ARG, "unknown ortho");
-  if (prec != GMRES_FP64 && prec != GMRES_IR_FP32)
-    return fail(h, GMRES_ERR_ARG, "precision must be GMRES_FP64 or GMRES_IR_FP32");
-  if (prec == GMRES_IR_FP32 && ortho != GMRES_ONE_REDUCE_MGS)
-    return fail(h, GMRES_ERR_ARG, "GMRES_IR_FP32 runs the one-reduce scheme only");
+  if (prec != GMRES_FP64 && prec != GMRES_IR_FP32 && prec != GMRES_IR_BF16)
+    return fail(h, GMRES_ERR_ARG, "precision must be GMRES_FP64, GMRES_IR_FP32 or GMRES_IR_BF16");
+  if (prec != GMRES_FP64 && ortho != GMRES_ONE_REDUCE_MGS)
+    return fail(h, GMRES_ERR_ARG, "GMRES-IR runs the one-reduce scheme only");
   if (max_iter < 0) return fail(h, GMRES_ERR_ARG, "max_iter < 0");
-  if (prec == GMRES_IR_FP32 && !h->V32) {  // FP32 copies for the inner cycles
+  if (prec == GMRES_IR_BF16 && !h->V16) {  // BF16 basis
     CUDA_TRY(h, cudaSetDevice(h->device));
-    const int64_t nnz_pad = (int64_t)align_up((size_t)std::max<int64_t>(h->nnz, 1), 4);
+    CUDA_TRY(h, cudaMalloc(&h->V16, sizeof(__nv_bfloat16) * (size_t)h->ldv * (h->m + 1)));
+    CUDA_TRY(h, cudaMemset(h->V16, 0, sizeof(__nv_bfloat16) * (size_t)h->ldv * (h->m + 1)));
+  }
+  if (prec == GMRES_IR_FP32 && !h->V32) {  // FP32 basis
+    CUDA_TRY(h, cudaSetDevice(h->device));
     CUDA_TRY(h, cudaMalloc(&h->V32, sizeof(float) * (size_t)h->ldv * (h->m + 1)));
     CUDA_TRY(h, cudaMemset(h->V32, 0, sizeof(float) * (size_t)h->ldv * (h->m + 1)));
+  }
+  if (prec != GMRES_FP64 && !h->w32) {  // FP32 values, SpMV result and the FP64 restart residual
+    CUDA_TRY(h, cudaSetDevice(h->device));
+    const int64_t nnz_pad = (int64_t)align_up((size_t)std::max<int64_t>(h->nnz, 1), 4);
     CUDA_TRY(h, cudaMalloc(&h->w32, sizeof(float) * (size_t)h->ldv));
     CUDA_TRY(h, cudaMemset(h->w32, 0, sizeof(float) * (size_t)h->ldv));
     CUDA_TRY(h, cudaMalloc(&h->val32, sizeof(float) * (size_t)nnz_pad));
@@ -1133,7 +1231,7 @@ gmres_status gmres_solve(gmres_handle h, const double* b, double* x, gmres_info*
     for (;;) {
       pr = prof_begin(h, PC_RES, 1, 0);
       k_residual<<<P, kThreads, 0, h->stream>>>(h->rowptr, h->col, h->val, b, x,
-                                                 h->prec == GMRES_IR_FP32 ? h->r64 : h->V, h->n, h->s,
+                                                 h->prec != GMRES_FP64 ? h->r64 : h->V, h->n, h->s,
                                                  RES_RESIDUAL, 0);
       prof_end(h, pr);
       ++h->launches;
@@ -1165,7 +1263,11 @@ gmres_status gmres_solve(gmres_handle h, const double* b, double* x, gmres_info*
       h->h_st->kmax = kmax;
       // only kmax changes on the host side; write it without touching the rest
       CUDA_TRY(h, cudaMemcpyAsync(&h->s.st->kmax, &h->h_st->kmax, sizeof(int), cudaMemcpyHostToDevice, h->stream));
-      if (h->prec == GMRES_IR_FP32) {
+      if (h->prec == GMRES_IR_BF16) {
+        k_round_scaled<<<h->grid_stream, kThreads, 0, h->stream>>>(h->r64, h->V16, h->n, h->s);
+        ++h->launches;
+        LAUNCH_CHECK(h);
+      } else if (h->prec == GMRES_IR_FP32) {
         k_round_scaled<<<h->grid_stream, kThreads, 0, h->stream>>>(h->r64, h->V32, h->n, h->s);
         ++h->launches;
         LAUNCH_CHECK(h);
@@ -1175,7 +1277,11 @@ gmres_status gmres_solve(gmres_handle h, const double* b, double* x, gmres_info*
       k_lsq<<<1, 128, h->lsq_smem, h->stream>>>(h->s);
       prof_end(h, pr);
       pr = prof_begin(h, PC_XUPD, 0, 0);
-      if (h->prec == GMRES_IR_FP32)
+      if (h->prec == GMRES_IR_BF16)
+        k_maxpy<__nv_bfloat16, double, double><<<h->grid_stream, kThreads, 0, h->stream>>>(h->V16, h->ldv, x, x,
+                                                                                           h->n, h->s,
+                                                                                           MAXPY_XUPDATE, 0);
+      else if (h->prec == GMRES_IR_FP32)
         k_maxpy<float, double, double><<<h->grid_stream, kThreads, 0, h->stream>>>(h->V32, h->ldv, x, x, h->n, h->s,
                                                                                   MAXPY_XUPDATE, 0);
       else
@@ -1242,6 +1348,7 @@ gmres_status gmres_destroy(gmres_handle h) {
   cudaFree(h->d_b);
   cudaFree(h->d_x);
   cudaFree(h->V32);
+  cudaFree(h->V16);
   cudaFree(h->w32);
   cudaFree(h->val32);
   cudaFree(h->r64);

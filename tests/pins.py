@@ -13,7 +13,7 @@ import numpy as np
 from paper_1809_05805_b300 import problems as P
 
 EPS = np.finfo(np.float64).eps
-MGS, ONE_REDUCE, IR_FP32, CGS2, PIPE2 = 0, 1, 2, 3, 4
+MGS, ONE_REDUCE, IR_FP32, CGS2, PIPE2, IR_BF16 = 0, 1, 2, 3, 4, 5
 
 
 def _dense(A):
@@ -355,6 +355,49 @@ def pin_pipeline(orc):
     assert seen_odd, "no case where the pipeline needs the extra step"
 
 
+def pin_bf16_rounding(orc):
+    """The oracle's FP32 -> BF16 rounding equals torch's (round to nearest,
+    ties to even) on random values, exact ties, powers of two and values near
+    the largest finite BF16."""
+    import torch
+
+    rng = np.random.default_rng(13)
+    x = np.concatenate([rng.standard_normal(4000).astype(np.float32) * np.float32(10.0) ** rng.integers(-8, 8, 4000),
+                        np.array([1.0 + 2.0 ** -8, 1.0 + 3 * 2.0 ** -8, -(1.0 + 2.0 ** -8), 2.0 ** -126, 0.0,
+                                  3.3895e38, -1.5], dtype=np.float32)])
+    ref = torch.from_numpy(x).to(torch.bfloat16).to(torch.float32).numpy()
+    got = orc.round_bf16(x)
+    assert np.array_equal(got.view(np.uint32), ref.view(np.uint32)), "BF16 rounding differs"
+
+
+def pin_ir_bf16(orc):
+    """GMRES-IR with the basis stored in BF16: every stored basis value is a
+    BF16 number (low 16 bits of its FP32 word zero); the solve still reaches a
+    true relative residual of 1e-10 with x equal to a dense LU solve within
+    the conditioning bound; and the first steps' residual estimates agree with
+    FP64 at BF16 level (well above FP32 rounding, below 1%)."""
+    A = P.aniso_27pt(8)
+    _, b = P.rhs(A, seed=3)
+    m = 20
+    r64 = orc.gmres(A, b, variant=ONE_REDUCE, m=m, tol=0.0, max_iter=m, capture=True)
+    r16 = orc.gmres(A, b, variant=IR_BF16, m=m, tol=0.0, max_iter=m, capture=True)
+    V = r16.V.astype(np.float32)
+    assert np.array_equal(V.astype(np.float64), r16.V), "basis not FP32-representable"
+    assert np.all((V.view(np.uint32) & 0xFFFF) == 0), "basis value not a BF16 number"
+    # over the first 8 steps (before BF16 rounding in the basis dominates the
+    # small residual): above FP32 rounding (~1e-6 here), below 1%
+    rel = np.abs(r16.history[:8] - r64.history[:8]) / r64.history[:8]
+    assert 2e-5 < rel.max() < 1e-2, rel.max()
+    for A in (P.aniso_27pt(7), P.conv_diff_7pt(7)):
+        _, b = P.rhs(A, seed=2)
+        D = _dense(A)
+        xref = np.linalg.solve(D, b)
+        r = orc.gmres(A, b, variant=IR_BF16, m=30, tol=1e-10, max_iter=3000)
+        assert r.status == 0
+        assert np.linalg.norm(b - D @ r.x) / np.linalg.norm(b) <= 1e-10
+        assert np.linalg.norm(r.x - xref) <= 10 * np.linalg.cond(D) * 1e-10 * np.linalg.norm(xref)
+
+
 def simoncini_szyld_run(orc, variant):
     A, b = P.simoncini_szyld(100, seed=0)
     return orc.gmres(A, b, variant=variant, m=100, tol=0.0, max_iter=100, capture=True)
@@ -387,4 +430,6 @@ PINS = [
     pin_cgs2_lvl2_qr,
     pin_cgs2_gmres,
     pin_pipeline,
+    pin_bf16_rounding,
+    pin_ir_bf16,
 ]

@@ -65,6 +65,11 @@ MUTANTS = {
                                  "for (int i = 0; i < j; ++i) axpy(n, s2[i], QCOL(i), uj);"),
     "pipe_pairs_shifted": ("c == 0 || c % 2 == 0 || tail || brk;", "c == 0 || c % 2 == 1 || tail || brk;"),
     "pipe_skip_pending": ("for (int q = rotated; q <= c; ++q) {", "for (int q = c; q <= c; ++q) {"),
+    # GMRES-IR with BF16 basis storage
+    "bf16_no_tie_even": ("const uint32_t lsb = (u >> 16) & 1u;", "const uint32_t lsb = 0u;"),
+    "bf16_truncate": ("u = (u + 0x7fffu + lsb) & 0xffff0000u;", "u = u & 0xffff0000u;"),
+    "bf16_normalized_unrounded": ("    for (int64_t l = 0; l < n; ++l) u[l] *= ib; /* v_j */\n    round_bf16_vec(n, u, bf16);",
+                                  "    for (int64_t l = 0; l < n; ++l) u[l] *= ib; /* v_j */"),
     "dot_square": ("double orc_dot(int64_t n, const double* x, const double* y) { return dot(n, x, y); }",
                    "double orc_dot(int64_t n, const double* x, const double* y) { return dot(n, x, x); }"),
 }
