@@ -76,10 +76,11 @@ METRIC_IR = "time-to-solve (1e-10 rel. resid), GMRES-IR: one-reduce cycles in FP
 def make_problem(w):
     return P.conv_diff_7pt(w["N"]) if w["stencil"] == "7pt" else P.aniso_27pt(w["N"])
 FP64_DFMA_PER_CLK_SM = 2  # B300: 1.25 TFLOP/s nominal FP64 = 148 SMs x 2 DFMA/clk x 2 flop x ~2.1 GHz
-# DRAM bytes per step launch / algorithmic bytes, from the ncu capture summarized in
-# profiles/k_one_reduce_step_128cubed.md (dram__bytes_read.sum + dram__bytes_write.sum).
-# Valid only for the kernel build that capture measured; set to None when it changes.
-STEP_TRAFFIC_RATIO = 1.013
+# DRAM bytes per step launch / algorithmic bytes, from an ncu capture of the
+# step kernel on the 128^3 workload (dram__bytes_read.sum + dram__bytes_write.sum
+# over the launch's algorithmic bytes, at j = 8 and 9). Valid only for the kernel
+# build that capture measured; set to None when the kernel changes.
+STEP_TRAFFIC_RATIO = 1.047
 
 
 def workload_name(w):
