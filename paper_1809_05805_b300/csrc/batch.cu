@@ -119,7 +119,7 @@ __device__ __forceinline__ const float* desc_val<float>(const SysDesc& d) {
 // publishes that system's sums, and the CTA completing a system runs the
 // system's reduction and epilogue.
 template <int MAXC, bool PAIRS, typename VT>
-__global__ void __launch_bounds__(kThreads, 2)
+__global__ void __launch_bounds__(kThreads, sizeof(VT) == 4 ? 3 : 2)
 ke_step(const VT* __restrict__ V, int64_t ldv, VT* __restrict__ w, EngDev e, int j) {
   __shared__ VT su[PAIRS ? 2 * kThreads : kThreads];
   __shared__ VT sw[PAIRS ? 2 * kThreads : kThreads];
@@ -710,7 +710,7 @@ struct Engine {
     }
     ETRY(cudaFuncSetAttribute(reinterpret_cast<const void*>(ke_lsq), cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)lsq_smem));
-    P = 2 * nsm;
+    P = (ir() ? 3 : 2) * nsm;  // resident CTAs per SM of the step kernel
     pairs = true;
     return GMRES_OK;
   }
@@ -1227,7 +1227,7 @@ struct Engine {
     ETRY(cudaEventCreate(&e0));
     ETRY(cudaEventCreate(&e1));
     float best = 1e30f;
-    int bestP = 2 * nsm;
+    int bestP = (ir() ? 3 : 2) * nsm;
     bool bestPairs = true;
     st = GMRES_OK;
     for (int pr = 0; pr < 2 && st == GMRES_OK; ++pr)
