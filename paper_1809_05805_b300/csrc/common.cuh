@@ -126,28 +126,44 @@ __device__ __forceinline__ float ld_as<float, __nv_bfloat16>(const __nv_bfloat16
 // Row i of A times x (CSR, FMA chain in column order, in the type of val; x
 // may be stored narrower). The loads of up to 8 entries are issued together
 // (predicated), so a stencil row costs two dependent memory latencies
-// (indices, then the gather) instead of two per entry.
+// (indices, then the gather) instead of two per entry. Longer rows are taken
+// in rounds of 8 with the index and value loads of the next round issued
+// beside the gathers of the current one, so that a row of R rounds costs R + 1
+// latencies instead of 2 R.
 template <typename VT, typename XT>
 __device__ __forceinline__ VT csr_row(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                                           const VT* __restrict__ val, const XT* __restrict__ x,
                                           int64_t i) {
   constexpr int kW = 8;
   const int p0 = __ldg(rowptr + i), p1 = __ldg(rowptr + i + 1);
+  int c[kW];
+  VT v[kW];
+#pragma unroll
+  for (int e = 0; e < kW; ++e) {
+    const bool ok = p0 + e < p1;
+    c[e] = ok ? __ldg(col + p0 + e) : 0;
+    v[e] = ok ? __ldg(val + p0 + e) : VT(0);
+  }
   VT s = VT(0);
   for (int p = p0; p < p1; p += kW) {
-    int c[kW];
-    VT v[kW], xv[kW];
+    VT xv[kW], vc[kW];
 #pragma unroll
     for (int e = 0; e < kW; ++e) {
-      const bool ok = p + e < p1;
-      c[e] = ok ? __ldg(col + p + e) : 0;
-      v[e] = ok ? __ldg(val + p + e) : VT(0);
+      xv[e] = (p + e < p1) ? ld_as<VT>(x + c[e]) : VT(0);
+      vc[e] = v[e];
+    }
+    const int q = p + kW;
+    if (q < p1) {  // next round's indices and values, in flight with this round's gathers
+#pragma unroll
+      for (int e = 0; e < kW; ++e) {
+        const bool ok = q + e < p1;
+        c[e] = ok ? __ldg(col + q + e) : 0;
+        v[e] = ok ? __ldg(val + q + e) : VT(0);
+      }
     }
 #pragma unroll
-    for (int e = 0; e < kW; ++e) xv[e] = (p + e < p1) ? ld_as<VT>(x + c[e]) : VT(0);
-#pragma unroll
     for (int e = 0; e < kW; ++e)
-      if (p + e < p1) s = fma(v[e], xv[e], s);
+      if (p + e < p1) s = fma(vc[e], xv[e], s);
   }
   return s;
 }
