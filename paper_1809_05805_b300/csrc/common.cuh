@@ -17,6 +17,7 @@ namespace {
 constexpr int kThreads = 256;                // CTA size; also rows per tile
 constexpr int kWarps = kThreads / 32;        // 8
 constexpr int kRowsPerLane = kThreads / 32;  // rows of a tile handled by one lane in the dot phase
+constexpr int kRemBatch = 4;                 // remainder columns of the block dot loaded together
 constexpr int kMaxM = 128;                   // largest restart length
 constexpr double kEps = 2.220446049250313e-16;
 constexpr double kBreakdownFactor = 16.0;
@@ -432,12 +433,25 @@ __device__ __forceinline__ void tile_block_dot(int64_t t, int64_t n, const int32
       }
     }
   }
+  // The r8 remainder columns, four at a time: their loads are issued together
+  // (one memory latency per four columns instead of one per column).
 #pragma unroll
-  for (int c = 0; c < kWarps - 1; ++c) {
-    if (c < r8) {  // block-uniform
-      const VT x = (row < n) ? ld_as<VT>(V + (size_t)(J8 * kWarps + c) * ldv + row) : VT(0);
-      rem_a[c] = fma(x, ur, rem_a[c]);
-      if (need_w) rem_c[c] = fma(x, wr, rem_c[c]);
+  for (int c0 = 0; c0 < kWarps - 1; c0 += kRemBatch) {
+    if (c0 < r8) {  // block-uniform
+      VT x[kRemBatch];
+#pragma unroll
+      for (int b = 0; b < kRemBatch; ++b) {
+        const int c = c0 + b;
+        x[b] = (c < r8 && row < n) ? ld_as<VT>(V + (size_t)(J8 * kWarps + c) * ldv + row) : VT(0);
+      }
+#pragma unroll
+      for (int b = 0; b < kRemBatch; ++b) {
+        const int c = c0 + b;
+        if (c < kWarps - 1 && c < r8) {
+          rem_a[c] = fma(x[b], ur, rem_a[c]);
+          if (need_w) rem_c[c] = fma(x[b], wr, rem_c[c]);
+        }
+      }
     }
   }
   __syncthreads();
@@ -504,17 +518,29 @@ __device__ __forceinline__ void tile_pair_block_dot(int64_t pp, int64_t n, const
       }
     }
   }
+  // The r8 remainder columns, four at a time (loads issued together).
 #pragma unroll
-  for (int c = 0; c < kWarps - 1; ++c) {
-    if (c < r8) {  // block-uniform
-      const SV* vk = V + (size_t)(J8 * kWarps + c) * ldv;
-      const VT x0 = (row0 < n) ? ld_as<VT>(vk + row0) : VT(0);
-      const VT x1 = (row1 < n) ? ld_as<VT>(vk + row1) : VT(0);
-      rem_a[c] = fma(x0, ur0, rem_a[c]);
-      rem_a[c] = fma(x1, ur1, rem_a[c]);
-      if (need_w) {
-        rem_c[c] = fma(x0, wr0, rem_c[c]);
-        rem_c[c] = fma(x1, wr1, rem_c[c]);
+  for (int c0 = 0; c0 < kWarps - 1; c0 += kRemBatch) {
+    if (c0 < r8) {  // block-uniform
+      VT x0[kRemBatch], x1[kRemBatch];
+#pragma unroll
+      for (int b = 0; b < kRemBatch; ++b) {
+        const int c = c0 + b;
+        const SV* vk = V + (size_t)(J8 * kWarps + c) * ldv;
+        x0[b] = (c < r8 && row0 < n) ? ld_as<VT>(vk + row0) : VT(0);
+        x1[b] = (c < r8 && row1 < n) ? ld_as<VT>(vk + row1) : VT(0);
+      }
+#pragma unroll
+      for (int b = 0; b < kRemBatch; ++b) {
+        const int c = c0 + b;
+        if (c < kWarps - 1 && c < r8) {
+          rem_a[c] = fma(x0[b], ur0, rem_a[c]);
+          rem_a[c] = fma(x1[b], ur1, rem_a[c]);
+          if (need_w) {
+            rem_c[c] = fma(x0[b], wr0, rem_c[c]);
+            rem_c[c] = fma(x1[b], wr1, rem_c[c]);
+          }
+        }
       }
     }
   }
