@@ -47,6 +47,7 @@ struct DevState {
   unsigned int ticket; // last-CTA election
   int fresh;           // batched engine: the next residual pass also sets bnorm
   int pipe2;           // Givens rotations on column pairs (the L = 2 pipeline)
+  int stalled;         // a bounded device-side wait for staged CSR data gave up
   long long reductions;
   long long grid_syncs;
   double mgs_coef;     // MGS: coefficient of the pending axpy
@@ -167,6 +168,129 @@ __device__ __forceinline__ VT csr_row(const int32_t* __restrict__ rowptr, const 
       if (p + e < p1) s = fma(vc[e], xv[e], s);
   }
   return s;
+}
+
+// ---------------------------------------------------------------------------
+// CSR staging in shared memory: the bulk-copy (TMA) engine moves a tile's
+// rowptr slice, column indices and values into shared memory while the CTA
+// works on the previous tile; completion is signalled on an mbarrier
+// (transaction bytes). Every wait is bounded.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+// Global -> shared bulk copy (16-byte aligned addresses, size a multiple of 16).
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Wait for the phase of the given parity to complete; false after ~1 s
+// (2^31 SM clocks) without completion.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity))
+    if (clock64() - t0 > (1LL << 31)) return false;
+  return true;
+}
+
+// A CTA's staging buffer for the CSR of one unit of U rows (a tile, U = 256,
+// or a tile pair, U = 512): rp holds rowptr[U u .. U u + U + 4), col and val
+// hold entries [lo, hi) with lo = rowptr[U u] rounded down and hi =
+// rowptr[U u + U] rounded up to a multiple of 4 (16-byte copies), at most cap
+// entries. rowptr must be readable up to U * units + 4 entries (padded with
+// nnz past n) and col, val up to nnz rounded up to 4. A unit with more than
+// cap entries copies rowptr only and is read from global memory.
+template <typename VT>
+struct CsrStage {
+  int32_t* rp;
+  int32_t* col;
+  VT* val;
+  uint64_t* bar;
+  int cap;
+  int U;
+  __device__ static int lo_of(int p) { return p & ~3; }
+  __device__ static int hi_of(int p) { return (p + 3) & ~3; }
+  // Thread 0: start the copies of unit u with entry range [lo, hi).
+  __device__ void issue(const int32_t* g_rp, const int32_t* g_col, const VT* g_val, int64_t u, int lo,
+                        int hi) const {
+    // order this CTA's earlier shared-memory reads of the buffer before the
+    // asynchronous writes into it
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    const uint32_t brp = (uint32_t)(U + 4) * 4;
+    const bool fits = hi - lo <= cap;
+    const uint32_t bcol = fits ? (uint32_t)(hi - lo) * 4u : 0u;
+    const uint32_t bval = fits ? (uint32_t)(hi - lo) * (uint32_t)sizeof(VT) : 0u;
+    mbar_arrive_expect_tx(bar, brp + bcol + bval);
+    bulk_g2s(rp, g_rp + u * U, brp, bar);
+    if (bcol) {
+      bulk_g2s(col, g_col + lo, bcol, bar);
+      bulk_g2s(val, g_val + lo, bval, bar);
+    }
+  }
+};
+
+// Row of A times x from staged entries p0 .. p1 (relative to the staged base):
+// gathers in rounds of kW issued together, FMA chain in column order (the
+// same sums as csr_row).
+template <int kW, typename VT, typename XT>
+__device__ __forceinline__ VT csr_row_staged(const int32_t* s_col, const VT* s_val, const XT* __restrict__ x,
+                                             int p0, int p1) {
+  VT s = VT(0);
+  for (int p = p0; p < p1; p += kW) {
+    VT xv[kW];
+#pragma unroll
+    for (int e = 0; e < kW; ++e) xv[e] = (p + e < p1) ? ld_as<VT>(x + s_col[p + e]) : VT(0);
+#pragma unroll
+    for (int e = 0; e < kW; ++e)
+      if (p + e < p1) s = fma(s_val[p + e], xv[e], s);
+  }
+  return s;
+}
+
+// Two staged rows with the gathers of both in flight together (rows of up to
+// kW entries each; longer rows one after the other).
+template <int kW, typename VT, typename XT>
+__device__ __forceinline__ void csr_row2_staged(const int32_t* s_col, const VT* s_val, const XT* __restrict__ x,
+                                                int a0, int b0, int a1, int b1, VT& y0, VT& y1) {
+  if (b0 - a0 <= kW && b1 - a1 <= kW) {
+    VT x0[kW], x1[kW];
+#pragma unroll
+    for (int e = 0; e < kW; ++e) {
+      x0[e] = (a0 + e < b0) ? ld_as<VT>(x + s_col[a0 + e]) : VT(0);
+      x1[e] = (a1 + e < b1) ? ld_as<VT>(x + s_col[a1 + e]) : VT(0);
+    }
+    VT s0 = VT(0), s1 = VT(0);
+#pragma unroll
+    for (int e = 0; e < kW; ++e) {
+      if (a0 + e < b0) s0 = fma(s_val[a0 + e], x0[e], s0);
+      if (a1 + e < b1) s1 = fma(s_val[a1 + e], x1[e], s1);
+    }
+    y0 = s0;
+    y1 = s1;
+  } else {
+    y0 = csr_row_staged<kW>(s_col, s_val, x, a0, b0);
+    y1 = csr_row_staged<kW>(s_col, s_val, x, a1, b1);
+  }
 }
 
 // Rows r0 and r1 of A times x with the loads of both rows in flight together
@@ -378,38 +502,29 @@ __device__ int finish_completed(Small s, int c, double h, bool tail) {
 // At j == kmax (the tail) the SpMV and c, d are skipped.
 // Standalone mode (raw_out != nullptr): j is j_arg, w may be an input
 // (use_spmv == 0), and the totals go to raw_out without the GMRES epilogue.
-// One 256-row tile t of the fused SpMV + block dot (one row per thread in the
-// SpMV, the block-dot work split over the 8 warps), accumulated into the
-// caller's per-thread sums. Rows >= n count as zero. Row i of the SpMV is
-// rowptr[i] .. rowptr[i+1] of col/val, gathering xg[col] (a single system
-// passes xg = u; a system stored at rows row0.. of a shared arena passes its
-// own CSR shifted by -row0 and xg = u + row0).
-template <int MAXC, typename SV, typename VT = SV>
-__device__ __forceinline__ void tile_block_dot(int64_t t, int64_t n, const int32_t* __restrict__ rowptr,
-                                               const int32_t* __restrict__ col, const VT* __restrict__ val,
-                                               const SV* __restrict__ V, int64_t ldv, const SV* __restrict__ u,
-                                               const SV* __restrict__ xg, VT* __restrict__ w, bool spmv,
-                                               bool need_w, int J8, int r8, VT* su,
-                                               VT* sw, VT (&acc_a)[MAXC], VT (&acc_c)[MAXC],
-                                               VT (&rem_a)[kWarps - 1], VT (&rem_c)[kWarps - 1], VT& sig,
-                                               VT& dd) {
+// The block-dot half of one 256-row tile t, given this thread's row values
+// ur = u[row], wr = w[row] (zero for rows >= n): accumulates sigma and d,
+// stages u and w of the tile in shared memory, calls hook() once every thread
+// of the CTA is past its SpMV (the staged CSR of the tile is no longer read),
+// then splits the block dot over the 8 warps: warp w owns columns w, w+8, ...
+// over all 8 row groups, and the r8 = j mod 8 remainder columns are split by
+// rows.
+struct NoHook {
+  __device__ void operator()() const {}
+};
+template <int MAXC, typename SV, typename VT, typename Hook>
+__device__ __forceinline__ void tile_dot_rows(int64_t t, int64_t n, const SV* __restrict__ V, int64_t ldv,
+                                              bool need_w, int J8, int r8, VT ur, VT wr, VT* su, VT* sw,
+                                              VT (&acc_a)[MAXC], VT (&acc_c)[MAXC], VT (&rem_a)[kWarps - 1],
+                                              VT (&rem_c)[kWarps - 1], VT& sig, VT& dd, Hook hook) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int64_t row = t * kThreads + threadIdx.x;
-  VT ur = VT(0), wr = VT(0);
-  if (row < n) {
-    ur = ld_as<VT>(u + row);
-    if (spmv) {
-      wr = csr_row(rowptr, col, val, xg, row);
-      w[row] = wr;
-    } else if (need_w) {
-      wr = w[row];
-    }
-  }
   sig = fma(ur, ur, sig);
   dd = fma(ur, wr, dd);
   su[threadIdx.x] = ur;
   sw[threadIdx.x] = wr;
   __syncthreads();
+  hook();
   const int64_t base = t * kThreads + lane;
   VT ru[kRowsPerLane], rw[kRowsPerLane];
 #pragma unroll
@@ -457,32 +572,17 @@ __device__ __forceinline__ void tile_block_dot(int64_t t, int64_t n, const int32
   __syncthreads();
 }
 
-// Tiles 2 pp and 2 pp + 1 (rows 512 pp .. 512 pp + 511) of the fused SpMV +
-// block dot, two rows per thread: the CSR loads of both rows are in flight
-// together, halving the latency-bound SpMV phases per row. su, sw hold 512
-// values.
-template <int MAXC, typename SV, typename VT = SV>
-__device__ __forceinline__ void tile_pair_block_dot(int64_t pp, int64_t n, const int32_t* __restrict__ rowptr,
-                                                    const int32_t* __restrict__ col, const VT* __restrict__ val,
-                                                    const SV* __restrict__ V, int64_t ldv, const SV* __restrict__ u,
-                                                    const SV* __restrict__ xg, VT* __restrict__ w, bool spmv,
-                                                    bool need_w, int J8, int r8,
-                                                    VT* su, VT* sw, VT (&acc_a)[MAXC], VT (&acc_c)[MAXC],
-                                                    VT (&rem_a)[kWarps - 1], VT (&rem_c)[kWarps - 1], VT& sig,
-                                                    VT& dd) {
+// The block-dot half of the tile pair pp (rows 512 pp .. 512 pp + 511, two
+// per thread: row0 = 512 pp + tid and row1 = row0 + 256), as tile_dot_rows.
+// su, sw hold 512 values.
+template <int MAXC, typename SV, typename VT, typename Hook>
+__device__ __forceinline__ void tile_pair_dot_rows(int64_t pp, int64_t n, const SV* __restrict__ V, int64_t ldv,
+                                                   bool need_w, int J8, int r8, VT ur0, VT wr0, VT ur1, VT wr1,
+                                                   VT* su, VT* sw, VT (&acc_a)[MAXC], VT (&acc_c)[MAXC],
+                                                   VT (&rem_a)[kWarps - 1], VT (&rem_c)[kWarps - 1], VT& sig,
+                                                   VT& dd, Hook hook) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int64_t row0 = pp * (2 * kThreads) + threadIdx.x, row1 = row0 + kThreads;
-  VT ur0 = VT(0), wr0 = VT(0), ur1 = VT(0), wr1 = VT(0);
-  if (row0 < n) ur0 = ld_as<VT>(u + row0);
-  if (row1 < n) ur1 = ld_as<VT>(u + row1);
-  if (spmv) {
-    csr_row2(rowptr, col, val, xg, row0, row1, n, wr0, wr1);
-    if (row0 < n) w[row0] = wr0;
-    if (row1 < n) w[row1] = wr1;
-  } else if (need_w) {
-    if (row0 < n) wr0 = w[row0];
-    if (row1 < n) wr1 = w[row1];
-  }
   sig = fma(ur0, ur0, sig);
   dd = fma(ur0, wr0, dd);
   sig = fma(ur1, ur1, sig);
@@ -492,6 +592,7 @@ __device__ __forceinline__ void tile_pair_block_dot(int64_t pp, int64_t n, const
   su[kThreads + threadIdx.x] = ur1;
   sw[kThreads + threadIdx.x] = wr1;
   __syncthreads();
+  hook();
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
     const int64_t base = pp * (2 * kThreads) + h * kThreads + lane;
@@ -545,6 +646,64 @@ __device__ __forceinline__ void tile_pair_block_dot(int64_t pp, int64_t n, const
     }
   }
   __syncthreads();
+}
+
+// One 256-row tile t of the fused SpMV + block dot (one row per thread in the
+// SpMV), accumulated into the caller's per-thread sums. Rows >= n count as
+// zero. Row i of the SpMV is rowptr[i] .. rowptr[i+1] of col/val, gathering
+// xg[col] (a single system passes xg = u; a system stored at rows row0.. of a
+// shared arena passes its own CSR shifted by -row0 and xg = u + row0).
+template <int MAXC, typename SV, typename VT = SV>
+__device__ __forceinline__ void tile_block_dot(int64_t t, int64_t n, const int32_t* __restrict__ rowptr,
+                                               const int32_t* __restrict__ col, const VT* __restrict__ val,
+                                               const SV* __restrict__ V, int64_t ldv, const SV* __restrict__ u,
+                                               const SV* __restrict__ xg, VT* __restrict__ w, bool spmv,
+                                               bool need_w, int J8, int r8, VT* su,
+                                               VT* sw, VT (&acc_a)[MAXC], VT (&acc_c)[MAXC],
+                                               VT (&rem_a)[kWarps - 1], VT (&rem_c)[kWarps - 1], VT& sig,
+                                               VT& dd) {
+  const int64_t row = t * kThreads + threadIdx.x;
+  VT ur = VT(0), wr = VT(0);
+  if (row < n) {
+    ur = ld_as<VT>(u + row);
+    if (spmv) {
+      wr = csr_row(rowptr, col, val, xg, row);
+      w[row] = wr;
+    } else if (need_w) {
+      wr = w[row];
+    }
+  }
+  tile_dot_rows<MAXC, SV, VT>(t, n, V, ldv, need_w, J8, r8, ur, wr, su, sw, acc_a, acc_c, rem_a, rem_c, sig, dd,
+                              NoHook{});
+}
+
+// Tiles 2 pp and 2 pp + 1 (rows 512 pp .. 512 pp + 511) of the fused SpMV +
+// block dot, two rows per thread: the CSR loads of both rows are in flight
+// together, halving the latency-bound SpMV phases per row. su, sw hold 512
+// values.
+template <int MAXC, typename SV, typename VT = SV>
+__device__ __forceinline__ void tile_pair_block_dot(int64_t pp, int64_t n, const int32_t* __restrict__ rowptr,
+                                                    const int32_t* __restrict__ col, const VT* __restrict__ val,
+                                                    const SV* __restrict__ V, int64_t ldv, const SV* __restrict__ u,
+                                                    const SV* __restrict__ xg, VT* __restrict__ w, bool spmv,
+                                                    bool need_w, int J8, int r8,
+                                                    VT* su, VT* sw, VT (&acc_a)[MAXC], VT (&acc_c)[MAXC],
+                                                    VT (&rem_a)[kWarps - 1], VT (&rem_c)[kWarps - 1], VT& sig,
+                                                    VT& dd) {
+  const int64_t row0 = pp * (2 * kThreads) + threadIdx.x, row1 = row0 + kThreads;
+  VT ur0 = VT(0), wr0 = VT(0), ur1 = VT(0), wr1 = VT(0);
+  if (row0 < n) ur0 = ld_as<VT>(u + row0);
+  if (row1 < n) ur1 = ld_as<VT>(u + row1);
+  if (spmv) {
+    csr_row2(rowptr, col, val, xg, row0, row1, n, wr0, wr1);
+    if (row0 < n) w[row0] = wr0;
+    if (row1 < n) w[row1] = wr1;
+  } else if (need_w) {
+    if (row0 < n) wr0 = w[row0];
+    if (row1 < n) wr1 = w[row1];
+  }
+  tile_pair_dot_rows<MAXC, SV, VT>(pp, n, V, ldv, need_w, J8, r8, ur0, wr0, ur1, wr1, su, sw, acc_a, acc_c, rem_a,
+                                   rem_c, sig, dd, NoHook{});
 }
 
 // Reduce the per-thread block-dot sums of the CTA into red[0 .. 2j+2).
@@ -615,7 +774,7 @@ __device__ void epilogue_one_reduce(Small s, double* red, int j, bool tail) {
   // exact breakdown found, column j-1 still to be finished (then 2).
   // T (rows and columns 0..j-1) and scale[0..j-1] are staged in shared memory
   // (dynamic, (m+1)^2 + (m+1) doubles) so the O(j^2) work reads no global memory.
-  extern __shared__ double dyn[];
+  extern __shared__ __align__(16) double dyn[];
   const int ld = s.ldh;
   double* sT = dyn;                       // (m+1) x (m+1), column-major, ld
   double* sScale = dyn + (size_t)ld * ld; // m+1
@@ -762,7 +921,7 @@ __device__ void residual_finish(Small s, double sumsq, int mode, int kmax) {
 // (dynamic, (m+1) x m doubles) so each of the k sequential steps is a
 // shared-memory update, not a global-memory round trip.
 __device__ void lsq_system(Small s) {
-  extern __shared__ double sR[];
+  extern __shared__ __align__(16) double sR[];
   __shared__ double y[kMaxM + 1];
   __shared__ int sk;
   DevState* st = s.st;

@@ -46,16 +46,17 @@ namespace {
 // memory latency, and the extra resident warps hide more of it (measured on
 // the 192^3 27-point GMRES-IR solve: 2.9 -> 3.4 TB/s; four per SM spill and
 // lose).
-template <int MAXC, typename VT, typename SV = VT>
+template <int MAXC, typename VT, typename SV = VT, int STAGE = 0>
 __global__ void __launch_bounds__(kThreads, sizeof(VT) == 4 ? 3 : 2)
 k_one_reduce_step(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                   const VT* __restrict__ val, const SV* __restrict__ V, int64_t ldv,
                   const SV* __restrict__ u_arg, VT* __restrict__ w, int64_t n, Small s,
-                  int j_arg, int use_spmv, double* raw_out) {
+                  int j_arg, int use_spmv, double* raw_out, int stage, int stage_cap) {
   __shared__ VT su[2 * kThreads];
   __shared__ VT sw[2 * kThreads];
   __shared__ double red[2 * (kMaxM + 1) + 2];
-  __shared__ int s_j, s_tail, s_skip;
+  __shared__ int s_j, s_tail, s_skip, s_stage_off;
+  __shared__ uint64_t s_bar;
   DevState* st = s.st;
   if (threadIdx.x == 0) {
     if (raw_out) {
@@ -91,10 +92,119 @@ k_one_reduce_step(const int32_t* __restrict__ rowptr, const int32_t* __restrict_
   VT sig = VT(0), dd = VT(0);
 
   const int64_t ntiles = (n + kThreads - 1) / kThreads;
-  // Large problems take tiles in pairs (the CSR loads of two rows per thread are
-  // in flight together, halving the latency-bound SpMV phases per row); small
-  // ones keep one tile per CTA iteration so that every SM gets work.
-  if (ntiles >= 4 * (int64_t)gridDim.x) {
+  if constexpr (STAGE != 0) {
+    // Staged CSR (STAGE 1: one tile per unit, 2: tile pairs): the bulk-copy
+    // engine fetches the next unit's rowptr slice, indices and values into
+    // shared memory while this one's block dot runs. The global CSR is never
+    // read by this instantiation: a unit whose copy did not arrive in time, or
+    // that does not fit the buffer (the host sizes it for the largest unit),
+    // sets the stalled flag and contributes a zero SpMV.
+    const int U = STAGE == 2 ? 2 * kThreads : kThreads;
+    const int64_t units = (n + U - 1) / U;
+    if (spmv) {
+      extern __shared__ __align__(16) double dyn[];
+      constexpr int kWs = 8;  // gathers in flight per staged row
+      CsrStage<VT> cs;
+      cs.rp = reinterpret_cast<int32_t*>(dyn);
+      cs.col = cs.rp + (U + 4);
+      cs.val = reinterpret_cast<VT*>(cs.col + stage_cap);
+      cs.bar = &s_bar;
+      cs.cap = stage_cap;
+      cs.U = U;
+      if (threadIdx.x == 0) {
+        s_stage_off = 0;
+        mbar_init(&s_bar, 1);
+      }
+      __syncthreads();
+      uint32_t phase = 0, pend_phase = 0;
+      bool pending = false;  // thread 0: a copy was issued and not yet seen complete (phase pend_phase)
+      int64_t unit = blockIdx.x;
+      if (threadIdx.x == 0 && unit < units) {
+        cs.issue(rowptr, col, val, unit, CsrStage<VT>::lo_of(__ldg(rowptr + unit * U)),
+                 CsrStage<VT>::hi_of(__ldg(rowptr + unit * U + U)));
+        pending = true;
+      }
+      for (; unit < units; unit += gridDim.x) {
+        const int64_t nx = unit + gridDim.x;
+        int nlo = 0, nhi = 0;  // thread 0: the next unit's entry range, loaded ahead of its use
+        if (threadIdx.x == 0 && nx < units) {
+          nlo = CsrStage<VT>::lo_of(__ldg(rowptr + nx * U));
+          nhi = CsrStage<VT>::hi_of(__ldg(rowptr + nx * U + U));
+        }
+        const int64_t row0 = unit * U + threadIdx.x, row1 = row0 + kThreads;
+        VT ur0 = VT(0), ur1 = VT(0), wr0 = VT(0), wr1 = VT(0);
+        if (row0 < n) ur0 = ld_as<VT>(u + row0);
+        if (STAGE == 2 && row1 < n) ur1 = ld_as<VT>(u + row1);
+        bool staged = !s_stage_off;
+        if (staged) {
+          staged = mbar_wait_bounded(&s_bar, phase);
+          if (!staged) s_stage_off = 1;
+        }
+        if (threadIdx.x == 0) {
+          if (staged) pending = false;
+          else if (pending) pend_phase = phase;
+        }
+        phase ^= 1u;
+        int lo = 0;
+        if (staged) {
+          lo = CsrStage<VT>::lo_of(cs.rp[0]);
+          staged = CsrStage<VT>::hi_of(cs.rp[U]) - lo <= stage_cap;
+        }
+        if (!staged) atomicExch(&st->stalled, 1);
+        if (STAGE == 2) {
+          if (staged)
+            csr_row2_staged<kWs>(cs.col, cs.val, u, cs.rp[threadIdx.x] - lo, cs.rp[threadIdx.x + 1] - lo,
+                                 cs.rp[kThreads + threadIdx.x] - lo, cs.rp[kThreads + threadIdx.x + 1] - lo, wr0,
+                                 wr1);
+          if (row0 < n) w[row0] = wr0;
+          if (row1 < n) w[row1] = wr1;
+        } else if (row0 < n) {
+          if (staged)
+            wr0 = csr_row_staged<kWs>(cs.col, cs.val, u, cs.rp[threadIdx.x] - lo, cs.rp[threadIdx.x + 1] - lo);
+          w[row0] = wr0;
+        }
+        // once every thread is past its SpMV, the buffer takes the next unit
+        auto next = [&]() {
+          if (threadIdx.x == 0 && nx < units && !s_stage_off) {
+            cs.issue(rowptr, col, val, nx, nlo, nhi);
+            pending = true;
+          }
+        };
+        if (STAGE == 2)
+          tile_pair_dot_rows<MAXC, SV, VT>(unit, n, V, ldv, need_w, J8, r8, ur0, wr0, ur1, wr1, su, sw, acc_a,
+                                           acc_c, rem_a, rem_c, sig, dd, next);
+        else
+          tile_dot_rows<MAXC, SV, VT>(unit, n, V, ldv, need_w, J8, r8, ur0, wr0, su, sw, acc_a, acc_c, rem_a,
+                                      rem_c, sig, dd, next);
+      }
+      // no copy may still be landing in shared memory when the CTA moves on
+      if (threadIdx.x == 0 && pending) mbar_wait_bounded(&s_bar, pend_phase);
+      __syncthreads();
+    } else {
+      // no SpMV (the cycle's tail, or a standalone block dot with w given)
+      for (int64_t unit = blockIdx.x; unit < units; unit += gridDim.x) {
+        const int64_t row0 = unit * U + threadIdx.x, row1 = row0 + kThreads;
+        VT ur0 = VT(0), ur1 = VT(0), wr0 = VT(0), wr1 = VT(0);
+        if (row0 < n) {
+          ur0 = ld_as<VT>(u + row0);
+          if (need_w) wr0 = w[row0];
+        }
+        if (STAGE == 2 && row1 < n) {
+          ur1 = ld_as<VT>(u + row1);
+          if (need_w) wr1 = w[row1];
+        }
+        if (STAGE == 2)
+          tile_pair_dot_rows<MAXC, SV, VT>(unit, n, V, ldv, need_w, J8, r8, ur0, wr0, ur1, wr1, su, sw, acc_a,
+                                           acc_c, rem_a, rem_c, sig, dd, NoHook{});
+        else
+          tile_dot_rows<MAXC, SV, VT>(unit, n, V, ldv, need_w, J8, r8, ur0, wr0, su, sw, acc_a, acc_c, rem_a,
+                                      rem_c, sig, dd, NoHook{});
+      }
+    }
+  } else if (ntiles >= 4 * (int64_t)gridDim.x) {
+    // Large problems take tiles in pairs (the CSR loads of two rows per thread
+    // are in flight together, halving the latency-bound SpMV phases per row);
+    // small ones keep one tile per CTA iteration so that every SM gets work.
     const int64_t npairs = (ntiles + 1) / 2;
     for (int64_t pp = blockIdx.x; pp < npairs; pp += gridDim.x)
       tile_pair_block_dot<MAXC, SV, VT>(pp, n, rowptr, col, val, V, ldv, u, u, w, spmv, need_w, J8, r8, su, sw,
@@ -572,7 +682,7 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 template <typename VT, typename SV = VT>
 using StepKernel = void (*)(const int32_t*, const int32_t*, const VT*, const SV*, int64_t, const SV*, VT*, int64_t,
-                            Small, int, int, double*);
+                            Small, int, int, double*, int, int);
 
 using ReorthKernel = void (*)(const double*, int64_t, int64_t, Small);
 
@@ -591,21 +701,27 @@ ReorthKernel reorth_kernel_for(int m) {
   }
 }
 
-// MAXC = floor(m / 8) whole columns per warp (j <= m), at least 1.
-template <typename VT, typename SV = VT>
-StepKernel<VT, SV> step_kernel_for(int m) {
+// MAXC = floor(m / 8) whole columns per warp (j <= m), at least 1; STAGE as
+// in k_one_reduce_step.
+template <typename VT, typename SV, int STAGE>
+StepKernel<VT, SV> step_kernel_staged(int m) {
   switch (std::max(1, m / kWarps)) {
-    case 1: return k_one_reduce_step<1, VT, SV>;
-    case 2: return k_one_reduce_step<2, VT, SV>;
-    case 3: return k_one_reduce_step<3, VT, SV>;
-    case 4: return k_one_reduce_step<4, VT, SV>;
-    case 5: return k_one_reduce_step<5, VT, SV>;
-    case 6: return k_one_reduce_step<6, VT, SV>;
-    case 7: return k_one_reduce_step<7, VT, SV>;
-    case 8: return k_one_reduce_step<8, VT, SV>;
-    case 9: case 10: case 11: case 12: return k_one_reduce_step<12, VT, SV>;
-    default: return k_one_reduce_step<16, VT, SV>;
+    case 1: return k_one_reduce_step<1, VT, SV, STAGE>;
+    case 2: return k_one_reduce_step<2, VT, SV, STAGE>;
+    case 3: return k_one_reduce_step<3, VT, SV, STAGE>;
+    case 4: return k_one_reduce_step<4, VT, SV, STAGE>;
+    case 5: return k_one_reduce_step<5, VT, SV, STAGE>;
+    case 6: return k_one_reduce_step<6, VT, SV, STAGE>;
+    case 7: return k_one_reduce_step<7, VT, SV, STAGE>;
+    case 8: return k_one_reduce_step<8, VT, SV, STAGE>;
+    case 9: case 10: case 11: case 12: return k_one_reduce_step<12, VT, SV, STAGE>;
+    default: return k_one_reduce_step<16, VT, SV, STAGE>;
   }
+}
+template <typename VT, typename SV = VT>
+StepKernel<VT, SV> step_kernel_for(int m, int stage = 0) {
+  return stage == 2 ? step_kernel_staged<VT, SV, 2>(m)
+                    : stage == 1 ? step_kernel_staged<VT, SV, 1>(m) : step_kernel_staged<VT, SV, 0>(m);
 }
 
 }  // namespace
@@ -647,6 +763,10 @@ struct gmres_ctx {
   float* val32 = nullptr;
   double* r64 = nullptr;
   size_t step_smem = 0;  // dynamic shared memory of the step kernel (T and scales)
+  // Staged CSR of the step kernels (FP64 cycles; FP32 cycles): mode 0 off,
+  // 1 tiles, 2 tile pairs; entry capacity; dynamic shared memory at launch.
+  int stage64 = 0, cap64 = 0, stage32 = 0, cap32 = 0, stage16 = 0, cap16 = 0;
+  size_t smem64 = 0, smem32 = 0, smem16 = 0;
   size_t lsq_smem = 0;   // dynamic shared memory of k_lsq (rotated Hessenberg)
   std::vector<double> hist;
   int hist_len = 0;
@@ -794,14 +914,16 @@ gmres_status launch_cycle(gmres_ctx* h, int kmax) {
     for (int j = 0; j <= kmax; ++j) {
       int pr = prof_begin(h, 0, j, kmax);
       if (h->prec == GMRES_IR_FP32)
-        h->step32<<<h->P32, kThreads, h->step_smem, h->stream>>>(h->rowptr, h->col, h->val32, h->V32, h->ldv,
-                                                                 nullptr, h->w32, h->n, h->s, 0, 1, nullptr);
+        h->step32<<<h->P32, kThreads, h->smem32, h->stream>>>(h->rowptr, h->col, h->val32, h->V32, h->ldv, nullptr,
+                                                              h->w32, h->n, h->s, 0, 1, nullptr, h->stage32,
+                                                              h->cap32);
       else if (h->prec == GMRES_IR_BF16)
-        h->step16<<<h->P32, kThreads, h->step_smem, h->stream>>>(h->rowptr, h->col, h->val32, h->V16, h->ldv,
-                                                                 nullptr, h->w32, h->n, h->s, 0, 1, nullptr);
+        h->step16<<<h->P32, kThreads, h->smem16, h->stream>>>(h->rowptr, h->col, h->val32, h->V16, h->ldv, nullptr,
+                                                              h->w32, h->n, h->s, 0, 1, nullptr, h->stage16,
+                                                              h->cap16);
       else
-        h->step<<<P, kThreads, h->step_smem, h->stream>>>(h->rowptr, h->col, h->val, h->V, h->ldv, nullptr, h->w,
-                                                          h->n, h->s, 0, 1, nullptr);
+        h->step<<<P, kThreads, h->smem64, h->stream>>>(h->rowptr, h->col, h->val, h->V, h->ldv, nullptr, h->w, h->n,
+                                                       h->s, 0, 1, nullptr, h->stage64, h->cap64);
       prof_end(h, pr);
       ++h->launches;
       if (j < kmax) {
@@ -1050,6 +1172,60 @@ void prof_reset(gmres_ctx* h) {
 
 extern "C" {
 
+extern "C++" {
+// Largest staged entry range of a 256-row tile and of a 512-row tile pair
+// (the range [rowptr[first] rounded down, rowptr[last + 1] rounded up to 4),
+// as the step kernel copies it). rp is padded past n with nnz.
+static void csr_stage_caps(const std::vector<int32_t>& rp, int64_t n, int& cap_tile, int& cap_pair) {
+  cap_tile = cap_pair = 0;
+  for (int U : {kThreads, 2 * kThreads}) {
+    int64_t best = 0;
+    for (int64_t r = 0; r < n; r += U) {
+      const int64_t lo = rp[r] & ~3, hi = ((int64_t)rp[r + U] + 3) & ~3;
+      best = std::max(best, hi - lo);
+    }
+    (U == kThreads ? cap_tile : cap_pair) = (int)std::min<int64_t>(best, 1 << 30);
+  }
+}
+
+// Staging of a step kernel with values of vb bytes, launched on P CTAs of
+// which `per_sm` must stay resident per SM: tile pairs when the unstaged kernel
+// would take pairs (ntiles >= 4 P) and their buffer fits, else single tiles if
+// theirs fits, else off. kernel_for(stage) gives the kernel of a mode; the
+// dynamic shared memory is the larger of the epilogue's (t_smem) and the
+// staging buffer's. Sets the kernel's shared-memory limit.
+template <typename KernelFor>
+static gmres_status choose_stage(KernelFor kernel_for, size_t vb, int per_sm, int P, int64_t ntiles, int cap_tile,
+                                 int cap_pair, size_t t_smem, int& mode, int& cap, size_t& smem) {
+  const bool pairs = ntiles >= 4 * (int64_t)P;
+  for (int cand : {2, 1}) {
+    if (cand == 2 && !pairs) continue;
+    const int U = cand == 2 ? 2 * kThreads : kThreads;
+    const int c = cand == 2 ? cap_pair : cap_tile;
+    const size_t need = std::max(t_smem, (size_t)(U + 4) * 4 + (size_t)c * (4 + vb));
+    if (need > 200 * 1024) continue;
+    const void* k = reinterpret_cast<const void*>(kernel_for(cand));
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need) != cudaSuccess)
+      return GMRES_ERR_CUDA;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, kThreads, need) != cudaSuccess) return GMRES_ERR_CUDA;
+    if (nb >= per_sm) {
+      mode = cand;
+      cap = c;
+      smem = need;
+      return GMRES_OK;
+    }
+  }
+  mode = 0;
+  cap = 0;
+  smem = t_smem;
+  if (cudaFuncSetAttribute(reinterpret_cast<const void*>(kernel_for(0)), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)t_smem) != cudaSuccess)
+    return GMRES_ERR_CUDA;
+  return GMRES_OK;
+}
+}  // extern "C++"
+
 gmres_status gmres_create(const gmres_csr* A, int m_restart, double tol, gmres_handle* out) {
   if (!out) return fail(nullptr, GMRES_ERR_ARG, "out is NULL");
   *out = nullptr;
@@ -1109,12 +1285,16 @@ gmres_status gmres_create(const gmres_csr* A, int m_restart, double tol, gmres_h
   h->P32 = (int)std::min<int64_t>(3 * (int64_t)h->nsm, ntiles);
   h->grid_stream = (int)std::min<int64_t>(4 * (int64_t)h->nsm, std::max<int64_t>(1, (n / 2 + kThreads - 1) / kThreads));
   const int64_t nnz_pad = align_up(std::max<int64_t>(nnz, 1), 4);
-  CREATE_TRY(cudaMalloc(&h->rowptr, sizeof(int32_t) * (n + 1)));
+  // rowptr is padded with nnz to a whole number of 512-row tile pairs + 8, so
+  // that a staged unit's rowptr slice (U + 4 entries) is always in bounds
+  const int64_t rp_len = (int64_t)align_up((size_t)n, 2 * kThreads) + 8;
+  rp.resize(rp_len, (int32_t)nnz);
+  CREATE_TRY(cudaMalloc(&h->rowptr, sizeof(int32_t) * rp_len));
   CREATE_TRY(cudaMalloc(&h->col, sizeof(int32_t) * nnz_pad));
   CREATE_TRY(cudaMalloc(&h->val, sizeof(double) * nnz_pad));
   CREATE_TRY(cudaMemset(h->col, 0, sizeof(int32_t) * nnz_pad));
   CREATE_TRY(cudaMemset(h->val, 0, sizeof(double) * nnz_pad));
-  CREATE_TRY(cudaMemcpy(h->rowptr, rp.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice));
+  CREATE_TRY(cudaMemcpy(h->rowptr, rp.data(), sizeof(int32_t) * rp_len, cudaMemcpyHostToDevice));
   if (nnz) {
     CREATE_TRY(cudaMemcpy(h->col, cl.data(), sizeof(int32_t) * nnz, cudaMemcpyHostToDevice));
     CREATE_TRY(cudaMemcpy(h->val, vl.data(), sizeof(double) * nnz, cudaMemcpyHostToDevice));
@@ -1127,18 +1307,29 @@ gmres_status gmres_create(const gmres_csr* A, int m_restart, double tol, gmres_h
   CREATE_TRY(cudaMallocHost(&h->h_st, sizeof(DevState)));
   std::memset(h->h_st, 0, sizeof(DevState));
   if (alloc_small(h) != GMRES_OK) return bail(GMRES_ERR_CUDA);
-  h->step = step_kernel_for<double>(m_restart);
   h->reorth = reorth_kernel_for(m_restart);
-  h->step32 = step_kernel_for<float>(m_restart);
-  h->step16 = step_kernel_for<float, __nv_bfloat16>(m_restart);
   h->step_smem = sizeof(double) * ((size_t)(m_restart + 1) * (m_restart + 1) + (m_restart + 1));
   h->lsq_smem = sizeof(double) * (size_t)(m_restart + 1) * m_restart;
-  CREATE_TRY(cudaFuncSetAttribute(reinterpret_cast<const void*>(h->step),
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->step_smem));
-  CREATE_TRY(cudaFuncSetAttribute(reinterpret_cast<const void*>(h->step32),
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->step_smem));
-  CREATE_TRY(cudaFuncSetAttribute(reinterpret_cast<const void*>(h->step16),
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->step_smem));
+  {
+    int cap_tile = 0, cap_pair = 0;
+    csr_stage_caps(rp, n, cap_tile, cap_pair);
+    const int m = m_restart;
+    gmres_status sst = choose_stage([m](int sg) { return step_kernel_for<double>(m, sg); }, sizeof(double), 2,
+                                    h->P, ntiles, cap_tile, cap_pair, h->step_smem, h->stage64, h->cap64, h->smem64);
+    if (sst == GMRES_OK)
+      sst = choose_stage([m](int sg) { return step_kernel_for<float>(m, sg); }, sizeof(float), 3, h->P32, ntiles,
+                         cap_tile, cap_pair, h->step_smem, h->stage32, h->cap32, h->smem32);
+    if (sst == GMRES_OK)
+      sst = choose_stage([m](int sg) { return step_kernel_for<float, __nv_bfloat16>(m, sg); }, sizeof(float), 3,
+                         h->P32, ntiles, cap_tile, cap_pair, h->step_smem, h->stage16, h->cap16, h->smem16);
+    if (sst != GMRES_OK) {
+      h->err = "cudaFuncSetAttribute / occupancy query of the step kernels failed";
+      return bail(GMRES_ERR_CUDA);
+    }
+    h->step = step_kernel_for<double>(m, h->stage64);
+    h->step32 = step_kernel_for<float>(m, h->stage32);
+    h->step16 = step_kernel_for<float, __nv_bfloat16>(m, h->stage16);
+  }
   CREATE_TRY(cudaFuncSetAttribute(reinterpret_cast<const void*>(k_lsq),
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->lsq_smem));
 #undef CREATE_TRY
@@ -1252,6 +1443,11 @@ gmres_status gmres_solve(gmres_handle h, const double* b, double* x, gmres_info*
       }
       prev_total = hs.total_iters;
       ++cycles;
+      if (hs.stalled) {
+        result = GMRES_ERR_TIMEOUT;
+        fail(h, result, "a bounded device-side wait for staged CSR data gave up");
+        break;
+      }
       if (!std::isfinite(hs.rnorm) || hs.nonfinite) {
         result = GMRES_ERR_NONFINITE;
         fail(h, result, "non-finite residual (NaN or Inf in x0 or the iteration)");
@@ -1401,8 +1597,8 @@ gmres_status lsg_block_dot(gmres_handle h, const double* V, int64_t ldv, int j, 
   if (!h) return GMRES_ERR_ARG;
   if (j < 0 || j > h->m) return fail(h, GMRES_ERR_ARG, "j must be in [0, m]");
   if ((j > 0 && (!V || ldv < h->n)) || !u || !w || !X) return fail(h, GMRES_ERR_ARG, "bad pointer or ldv");
-  h->step<<<h->P, kThreads, h->step_smem, h->stream>>>(h->rowptr, h->col, h->val, V, ldv, u, w, h->n, h->s, j,
-                                                        use_spmv, h->s.raw);
+  h->step<<<h->P, kThreads, h->smem64, h->stream>>>(h->rowptr, h->col, h->val, V, ldv, u, w, h->n, h->s, j,
+                                                     use_spmv, h->s.raw, h->stage64, h->cap64);
   LAUNCH_CHECK(h);
   CUDA_TRY(h, cudaMemcpyAsync(X, h->s.raw, sizeof(double) * (2 * j + 2), cudaMemcpyDeviceToHost, h->stream));
   CUDA_TRY(h, cudaStreamSynchronize(h->stream));
@@ -1468,7 +1664,7 @@ gmres_status lsg_block_dot_noalloc(const int32_t* rowptr, const int32_t* col, co
   cudaError_t e = cudaMemsetAsync(scratch, 0, sizeof(DevState), stream);
   if (e != cudaSuccess) return fail(nullptr, GMRES_ERR_CUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
   k_one_reduce_step<kNoAllocMaxJ / kWarps, double><<<P, kThreads, 0, stream>>>(rowptr, col, val, V, ldv, u, w, n, sm, j,
-                                                                      use_spmv, X);
+                                                                      use_spmv, X, 0, 0);
   e = cudaGetLastError();
   if (e != cudaSuccess) return fail(nullptr, GMRES_ERR_CUDA, std::string("launch: ") + cudaGetErrorString(e));
   return GMRES_OK;
@@ -1493,6 +1689,7 @@ gmres_status gmres_arnoldi(gmres_handle h, const double* r0, int k, double* V_ou
   if ((st = launch_cycle(h, k)) != GMRES_OK) return st;
   if ((st = read_state(h)) != GMRES_OK) return st;
   const int kk = h->h_st->k;
+  if (h->h_st->stalled) return fail(h, GMRES_ERR_TIMEOUT, "a bounded device-side wait for staged CSR data gave up");
   if (h->h_st->nonfinite) return fail(h, GMRES_ERR_NONFINITE, "non-finite value in the Arnoldi process");
   if (k_done) *k_done = kk;
   if (V_out) {
