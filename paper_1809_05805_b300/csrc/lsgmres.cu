@@ -37,195 +37,9 @@
 
 #include "lsgmres.h"
 #include "common.cuh"
+#include "step.cuh"
 
 namespace {
-
-// VT: arithmetic type (and of A's values and w); SV: storage type of the
-// basis (VT, or BF16 for GMRES-IR with BF16 storage, widened exactly on load).
-// FP32 cycles run three CTAs per SM (FP64: two): the FP32 step is bound by
-// memory latency, and the extra resident warps hide more of it (measured on
-// the 192^3 27-point GMRES-IR solve: 2.9 -> 3.4 TB/s; four per SM spill and
-// lose).
-template <int MAXC, typename VT, typename SV = VT, int STAGE = 0>
-__global__ void __launch_bounds__(kThreads, sizeof(VT) == 4 ? 3 : 2)
-k_one_reduce_step(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-                  const VT* __restrict__ val, const SV* __restrict__ V, int64_t ldv,
-                  const SV* __restrict__ u_arg, VT* __restrict__ w, int64_t n, Small s,
-                  int j_arg, int use_spmv, double* raw_out, int stage, int stage_cap) {
-  __shared__ VT su[2 * kThreads];
-  __shared__ VT sw[2 * kThreads];
-  __shared__ double red[2 * (kMaxM + 1) + 2];
-  __shared__ int s_j, s_tail, s_skip, s_stage_off;
-  __shared__ uint64_t s_bar;
-  DevState* st = s.st;
-  if (threadIdx.x == 0) {
-    if (raw_out) {
-      s_j = j_arg;
-      s_tail = 0;
-      s_skip = 0;
-    } else {
-      s_skip = __ldcg(&st->done);
-      s_j = __ldcg(&st->step);
-      s_tail = (s_j == __ldcg(&st->kmax));
-    }
-  }
-  __syncthreads();
-  if (s_skip) return;
-  const int j = s_j;
-  const bool tail = s_tail;
-  const bool spmv = raw_out ? (use_spmv != 0) : !tail;
-  const bool need_w = raw_out ? true : !tail;
-  const SV* u = raw_out ? u_arg : V + (size_t)j * ldv;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-
-  // Work split of the block dot over a tile of 256 rows (8 row groups of 32):
-  // the first 8*J8 columns go to warps whole (warp w owns columns w, w+8, ...,
-  // all 8 row groups); the r8 = j mod 8 remaining columns are split by rows,
-  // each warp taking its own row group. Every warp issues the same DFMAs.
-  const int J8 = j / kWarps, r8 = j % kWarps;
-  VT acc_a[MAXC], acc_c[MAXC];
-  VT rem_a[kWarps - 1], rem_c[kWarps - 1];
-#pragma unroll
-  for (int c = 0; c < MAXC; ++c) acc_a[c] = acc_c[c] = VT(0);
-#pragma unroll
-  for (int c = 0; c < kWarps - 1; ++c) rem_a[c] = rem_c[c] = VT(0);
-  VT sig = VT(0), dd = VT(0);
-
-  const int64_t ntiles = (n + kThreads - 1) / kThreads;
-  if constexpr (STAGE != 0) {
-    // Staged CSR (STAGE 1: one tile per unit, 2: tile pairs): the bulk-copy
-    // engine fetches the next unit's rowptr slice, indices and values into
-    // shared memory while this one's block dot runs. The global CSR is never
-    // read by this instantiation: a unit whose copy did not arrive in time, or
-    // that does not fit the buffer (the host sizes it for the largest unit),
-    // sets the stalled flag and contributes a zero SpMV.
-    const int U = STAGE == 2 ? 2 * kThreads : kThreads;
-    const int64_t units = (n + U - 1) / U;
-    if (spmv) {
-      extern __shared__ __align__(16) double dyn[];
-      constexpr int kWs = 8;  // gathers in flight per staged row
-      CsrStage<VT> cs;
-      cs.rp = reinterpret_cast<int32_t*>(dyn);
-      cs.col = cs.rp + (U + 4);
-      cs.val = reinterpret_cast<VT*>(cs.col + stage_cap);
-      cs.bar = &s_bar;
-      cs.cap = stage_cap;
-      cs.U = U;
-      if (threadIdx.x == 0) {
-        s_stage_off = 0;
-        mbar_init(&s_bar, 1);
-      }
-      __syncthreads();
-      uint32_t phase = 0, pend_phase = 0;
-      bool pending = false;  // thread 0: a copy was issued and not yet seen complete (phase pend_phase)
-      int64_t unit = blockIdx.x;
-      if (threadIdx.x == 0 && unit < units) {
-        cs.issue(rowptr, col, val, unit, CsrStage<VT>::lo_of(__ldg(rowptr + unit * U)),
-                 CsrStage<VT>::hi_of(__ldg(rowptr + unit * U + U)));
-        pending = true;
-      }
-      for (; unit < units; unit += gridDim.x) {
-        const int64_t nx = unit + gridDim.x;
-        int nlo = 0, nhi = 0;  // thread 0: the next unit's entry range, loaded ahead of its use
-        if (threadIdx.x == 0 && nx < units) {
-          nlo = CsrStage<VT>::lo_of(__ldg(rowptr + nx * U));
-          nhi = CsrStage<VT>::hi_of(__ldg(rowptr + nx * U + U));
-        }
-        const int64_t row0 = unit * U + threadIdx.x, row1 = row0 + kThreads;
-        VT ur0 = VT(0), ur1 = VT(0), wr0 = VT(0), wr1 = VT(0);
-        if (row0 < n) ur0 = ld_as<VT>(u + row0);
-        if (STAGE == 2 && row1 < n) ur1 = ld_as<VT>(u + row1);
-        bool staged = !s_stage_off;
-        if (staged) {
-          staged = mbar_wait_bounded(&s_bar, phase);
-          if (!staged) s_stage_off = 1;
-        }
-        if (threadIdx.x == 0) {
-          if (staged) pending = false;
-          else if (pending) pend_phase = phase;
-        }
-        phase ^= 1u;
-        int lo = 0;
-        if (staged) {
-          lo = CsrStage<VT>::lo_of(cs.rp[0]);
-          staged = CsrStage<VT>::hi_of(cs.rp[U]) - lo <= stage_cap;
-        }
-        if (!staged) atomicExch(&st->stalled, 1);
-        if (STAGE == 2) {
-          if (staged)
-            csr_row2_staged<kWs>(cs.col, cs.val, u, cs.rp[threadIdx.x] - lo, cs.rp[threadIdx.x + 1] - lo,
-                                 cs.rp[kThreads + threadIdx.x] - lo, cs.rp[kThreads + threadIdx.x + 1] - lo, wr0,
-                                 wr1);
-          if (row0 < n) w[row0] = wr0;
-          if (row1 < n) w[row1] = wr1;
-        } else if (row0 < n) {
-          if (staged)
-            wr0 = csr_row_staged<kWs>(cs.col, cs.val, u, cs.rp[threadIdx.x] - lo, cs.rp[threadIdx.x + 1] - lo);
-          w[row0] = wr0;
-        }
-        // once every thread is past its SpMV, the buffer takes the next unit
-        auto next = [&]() {
-          if (threadIdx.x == 0 && nx < units && !s_stage_off) {
-            cs.issue(rowptr, col, val, nx, nlo, nhi);
-            pending = true;
-          }
-        };
-        if (STAGE == 2)
-          tile_pair_dot_rows<MAXC, SV, VT>(unit, n, V, ldv, need_w, J8, r8, ur0, wr0, ur1, wr1, su, sw, acc_a,
-                                           acc_c, rem_a, rem_c, sig, dd, next);
-        else
-          tile_dot_rows<MAXC, SV, VT>(unit, n, V, ldv, need_w, J8, r8, ur0, wr0, su, sw, acc_a, acc_c, rem_a,
-                                      rem_c, sig, dd, next);
-      }
-      // no copy may still be landing in shared memory when the CTA moves on
-      if (threadIdx.x == 0 && pending) mbar_wait_bounded(&s_bar, pend_phase);
-      __syncthreads();
-    } else {
-      // no SpMV (the cycle's tail, or a standalone block dot with w given)
-      for (int64_t unit = blockIdx.x; unit < units; unit += gridDim.x) {
-        const int64_t row0 = unit * U + threadIdx.x, row1 = row0 + kThreads;
-        VT ur0 = VT(0), ur1 = VT(0), wr0 = VT(0), wr1 = VT(0);
-        if (row0 < n) {
-          ur0 = ld_as<VT>(u + row0);
-          if (need_w) wr0 = w[row0];
-        }
-        if (STAGE == 2 && row1 < n) {
-          ur1 = ld_as<VT>(u + row1);
-          if (need_w) wr1 = w[row1];
-        }
-        if (STAGE == 2)
-          tile_pair_dot_rows<MAXC, SV, VT>(unit, n, V, ldv, need_w, J8, r8, ur0, wr0, ur1, wr1, su, sw, acc_a,
-                                           acc_c, rem_a, rem_c, sig, dd, NoHook{});
-        else
-          tile_dot_rows<MAXC, SV, VT>(unit, n, V, ldv, need_w, J8, r8, ur0, wr0, su, sw, acc_a, acc_c, rem_a,
-                                      rem_c, sig, dd, NoHook{});
-      }
-    }
-  } else if (ntiles >= 4 * (int64_t)gridDim.x) {
-    // Large problems take tiles in pairs (the CSR loads of two rows per thread
-    // are in flight together, halving the latency-bound SpMV phases per row);
-    // small ones keep one tile per CTA iteration so that every SM gets work.
-    const int64_t npairs = (ntiles + 1) / 2;
-    for (int64_t pp = blockIdx.x; pp < npairs; pp += gridDim.x)
-      tile_pair_block_dot<MAXC, SV, VT>(pp, n, rowptr, col, val, V, ldv, u, u, w, spmv, need_w, J8, r8, su, sw,
-                                        acc_a, acc_c, rem_a, rem_c, sig, dd);
-  } else {
-    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x)
-      tile_block_dot<MAXC, SV, VT>(t, n, rowptr, col, val, V, ldv, u, u, w, spmv, need_w, J8, r8, su, sw, acc_a,
-                                   acc_c, rem_a, rem_c, sig, dd);
-  }
-
-  cta_partials<MAXC, VT>(acc_a, acc_c, rem_a, rem_c, sig, dd, j, J8, r8, red);
-  const int nv = 2 * j + 2;
-  if (!grid_reduce_last(s, red, nv)) return;
-
-  if (raw_out) {
-    for (int v = threadIdx.x; v < nv; v += blockDim.x) raw_out[v] = red[v];
-    return;
-  }
-
-  epilogue_one_reduce(s, red, j, tail);
-}
 
 // --------------------------------------------------------------------------
 // Second projection of Algorithm 5 (cgs2_lvl2) in Arnoldi form
@@ -680,10 +494,6 @@ constexpr size_t kNoAllocBytes = kNoAllocStateBytes + sizeof(double) * (size_t)k
 static_assert(sizeof(DevState) <= kNoAllocStateBytes, "DevState outgrew its slot");
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
-template <typename VT, typename SV = VT>
-using StepKernel = void (*)(const int32_t*, const int32_t*, const VT*, const SV*, int64_t, const SV*, VT*, int64_t,
-                            Small, int, int, double*, int, int);
-
 using ReorthKernel = void (*)(const double*, int64_t, int64_t, Small);
 
 ReorthKernel reorth_kernel_for(int m) {
@@ -701,27 +511,16 @@ ReorthKernel reorth_kernel_for(int m) {
   }
 }
 
-// MAXC = floor(m / 8) whole columns per warp (j <= m), at least 1; STAGE as
-// in k_one_reduce_step.
-template <typename VT, typename SV, int STAGE>
-StepKernel<VT, SV> step_kernel_staged(int m) {
-  switch (std::max(1, m / kWarps)) {
-    case 1: return k_one_reduce_step<1, VT, SV, STAGE>;
-    case 2: return k_one_reduce_step<2, VT, SV, STAGE>;
-    case 3: return k_one_reduce_step<3, VT, SV, STAGE>;
-    case 4: return k_one_reduce_step<4, VT, SV, STAGE>;
-    case 5: return k_one_reduce_step<5, VT, SV, STAGE>;
-    case 6: return k_one_reduce_step<6, VT, SV, STAGE>;
-    case 7: return k_one_reduce_step<7, VT, SV, STAGE>;
-    case 8: return k_one_reduce_step<8, VT, SV, STAGE>;
-    case 9: case 10: case 11: case 12: return k_one_reduce_step<12, VT, SV, STAGE>;
-    default: return k_one_reduce_step<16, VT, SV, STAGE>;
-  }
+// Step kernels of a restart length m and staging mode (the instantiations
+// live in the step_<type>_s<stage>.cu translation units).
+StepKernel<double> step64_for(int m, int stage = 0) {
+  return reinterpret_cast<StepKernel<double>>(const_cast<void*>(lsg_steps::step_kernel_f64(m, stage)));
 }
-template <typename VT, typename SV = VT>
-StepKernel<VT, SV> step_kernel_for(int m, int stage = 0) {
-  return stage == 2 ? step_kernel_staged<VT, SV, 2>(m)
-                    : stage == 1 ? step_kernel_staged<VT, SV, 1>(m) : step_kernel_staged<VT, SV, 0>(m);
+StepKernel<float> step32_for(int m, int stage = 0) {
+  return reinterpret_cast<StepKernel<float>>(const_cast<void*>(lsg_steps::step_kernel_f32(m, stage)));
+}
+StepKernel<float, __nv_bfloat16> step16_for(int m, int stage = 0) {
+  return reinterpret_cast<StepKernel<float, __nv_bfloat16>>(const_cast<void*>(lsg_steps::step_kernel_bf16(m, stage)));
 }
 
 }  // namespace
@@ -1314,21 +1113,21 @@ gmres_status gmres_create(const gmres_csr* A, int m_restart, double tol, gmres_h
     int cap_tile = 0, cap_pair = 0;
     csr_stage_caps(rp, n, cap_tile, cap_pair);
     const int m = m_restart;
-    gmres_status sst = choose_stage([m](int sg) { return step_kernel_for<double>(m, sg); }, sizeof(double), 2,
+    gmres_status sst = choose_stage([m](int sg) { return step64_for(m, sg); }, sizeof(double), 2,
                                     h->P, ntiles, cap_tile, cap_pair, h->step_smem, h->stage64, h->cap64, h->smem64);
     if (sst == GMRES_OK)
-      sst = choose_stage([m](int sg) { return step_kernel_for<float>(m, sg); }, sizeof(float), 3, h->P32, ntiles,
+      sst = choose_stage([m](int sg) { return step32_for(m, sg); }, sizeof(float), 3, h->P32, ntiles,
                          cap_tile, cap_pair, h->step_smem, h->stage32, h->cap32, h->smem32);
     if (sst == GMRES_OK)
-      sst = choose_stage([m](int sg) { return step_kernel_for<float, __nv_bfloat16>(m, sg); }, sizeof(float), 3,
+      sst = choose_stage([m](int sg) { return step16_for(m, sg); }, sizeof(float), 3,
                          h->P32, ntiles, cap_tile, cap_pair, h->step_smem, h->stage16, h->cap16, h->smem16);
     if (sst != GMRES_OK) {
       h->err = "cudaFuncSetAttribute / occupancy query of the step kernels failed";
       return bail(GMRES_ERR_CUDA);
     }
-    h->step = step_kernel_for<double>(m, h->stage64);
-    h->step32 = step_kernel_for<float>(m, h->stage32);
-    h->step16 = step_kernel_for<float, __nv_bfloat16>(m, h->stage16);
+    h->step = step64_for(m, h->stage64);
+    h->step32 = step32_for(m, h->stage32);
+    h->step16 = step16_for(m, h->stage16);
   }
   CREATE_TRY(cudaFuncSetAttribute(reinterpret_cast<const void*>(k_lsq),
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->lsq_smem));
@@ -1663,8 +1462,7 @@ gmres_status lsg_block_dot_noalloc(const int32_t* rowptr, const int32_t* col, co
   // the ticket must start at zero; a memset allocates nothing
   cudaError_t e = cudaMemsetAsync(scratch, 0, sizeof(DevState), stream);
   if (e != cudaSuccess) return fail(nullptr, GMRES_ERR_CUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
-  k_one_reduce_step<kNoAllocMaxJ / kWarps, double><<<P, kThreads, 0, stream>>>(rowptr, col, val, V, ldv, u, w, n, sm, j,
-                                                                      use_spmv, X, 0, 0);
+  step64_for(kNoAllocMaxJ)<<<P, kThreads, 0, stream>>>(rowptr, col, val, V, ldv, u, w, n, sm, j, use_spmv, X, 0, 0);
   e = cudaGetLastError();
   if (e != cudaSuccess) return fail(nullptr, GMRES_ERR_CUDA, std::string("launch: ") + cudaGetErrorString(e));
   return GMRES_OK;
