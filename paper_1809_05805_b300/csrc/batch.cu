@@ -285,6 +285,10 @@ ke_xupdate(const VT* __restrict__ V, int64_t ldv, double* __restrict__ x, EngDev
   }
 }
 
+__global__ void ke_fill_i32(int32_t* __restrict__ a, int64_t n, int32_t v) {
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) a[i] = v;
+}
+
 __global__ void ke_to_float(const double* __restrict__ a, float* __restrict__ out, int64_t n) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) out[i] = (float)a[i];
@@ -415,6 +419,7 @@ struct Engine {
   // launch
   cudaStream_t stream = nullptr;
   size_t step_smem = 0, lsq_smem = 0;
+  int stage_cap = 0;  // entries of the step kernel's CSR staging buffer
   struct G {
     int kmax;
     bool prof;
@@ -557,12 +562,34 @@ struct Engine {
     for (int i = S - 1; i >= 0; --i) free_slots.push_back(i);
     cyc_kmax.assign(S, -1);
     cyc_it0.assign(S, 0);
-    step_smem = sizeof(double) * ((size_t)ld * ld + ld);
     lsq_smem = sizeof(double) * (size_t)ld * m;
-    for (bool pr : {false, true}) {
-      const void* f = ir() ? reinterpret_cast<const void*>(eng_step_for<float>(m, pr))
-                           : reinterpret_cast<const void*>(eng_step_for<double>(m, pr));
-      ETRY(cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)step_smem));
+    // The step kernel's dynamic shared memory: the CSR staging buffer (rowptr
+    // slice of a tile pair, then stage_cap indices and values) followed by the
+    // epilogue's T and scales. stage_cap is the largest multiple of 256 entries
+    // (at most 16,384) that keeps the kernel's resident CTAs per SM.
+    {
+      const size_t vb = ir() ? sizeof(float) : sizeof(double);
+      const size_t epi = sizeof(double) * ((size_t)ld * ld + ld);
+      const int per_sm = ir() ? 3 : 2;
+      stage_cap = 0;
+      for (int cap = 16384; cap >= 256 && stage_cap == 0; cap -= 256) {
+        const size_t need = (size_t)(2 * kThreads + 4) * 4 + (size_t)cap * (4 + vb) + epi;
+        bool ok = true;
+        for (bool pr : {false, true}) {
+          const void* f = ir() ? reinterpret_cast<const void*>(eng_step_for<float>(m, pr))
+                               : reinterpret_cast<const void*>(eng_step_for<double>(m, pr));
+          int nb = 0;
+          if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need) != cudaSuccess ||
+              cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, kThreads, need) != cudaSuccess || nb < per_sm)
+            ok = false;
+        }
+        if (ok) {
+          stage_cap = cap;
+          step_smem = need;
+        }
+      }
+      (void)cudaGetLastError();  // sizes above the per-block limit were refused; that is not an error here
+      if (stage_cap == 0) return fail(GMRES_ERR_CUDA, "no shared-memory size keeps the step kernel resident");
     }
     ETRY(cudaFuncSetAttribute(reinterpret_cast<const void*>(ke_lsq), cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)lsq_smem));
@@ -626,8 +653,11 @@ struct Engine {
   }
 
   int stream_grid() const { return 4 * nsm; }
+  // rowptr entries kept per system: padded with nnz to whole tile pairs + 8,
+  // so that every staged rowptr slice of the step kernel is in bounds
+  static int64_t rp_entries(int64_t n) { return (n + kPairRows - 1) / kPairRows * kPairRows + 8; }
   int64_t csr_bytes_for(int64_t n, int64_t nnz) const {
-    return (int64_t)align_up(4 * (size_t)(n + 1), 256) + (int64_t)align_up(4 * (size_t)std::max<int64_t>(nnz, 1), 256) +
+    return (int64_t)align_up(4 * (size_t)rp_entries(n), 256) + (int64_t)align_up(4 * (size_t)std::max<int64_t>(nnz, 1), 256) +
            (int64_t)align_up(8 * (size_t)std::max<int64_t>(nnz, 1), 256) +
            (ir() ? (int64_t)align_up(4 * (size_t)std::max<int64_t>(nnz, 1), 256) : 0);
   }
@@ -665,7 +695,7 @@ struct Engine {
     sl.csr_off = c0;
     sl.csr_units = units;
     char* base = csr_pool + 256 * (size_t)c0;
-    const size_t o_col = align_up(4 * (size_t)(a.n + 1), 256);
+    const size_t o_col = align_up(4 * (size_t)rp_entries(a.n), 256);
     const size_t o_val = o_col + align_up(4 * (size_t)std::max<int64_t>(a.nnz, 1), 256);
     const size_t o_v32 = o_val + align_up(8 * (size_t)std::max<int64_t>(a.nnz, 1), 256);
     SysDesc& d = h_desc[s];
@@ -677,6 +707,8 @@ struct Engine {
     d.n = a.n;
     const cudaMemcpyKind k = cudaMemcpyDefault;
     cudaMemcpyAsync((void*)d.rowptr, a.rowptr, 4 * (size_t)(a.n + 1), k, stream);
+    ke_fill_i32<<<1, kThreads, 0, stream>>>(const_cast<int32_t*>(d.rowptr) + a.n + 1, rp_entries(a.n) - (a.n + 1),
+                                           (int32_t)a.nnz);
     if (a.nnz > 0) {
       cudaMemcpyAsync((void*)d.col, a.col, 4 * (size_t)a.nnz, k, stream);
       cudaMemcpyAsync((void*)d.val, a.val, 8 * (size_t)a.nnz, k, stream);
@@ -884,10 +916,10 @@ struct Engine {
       int pr = prof_begin(PC_STEP, j);
       if (ir())
         eng_step_for<float>(cfg.m, pairs)<<<P, kThreads, step_smem, stream>>>(
-            static_cast<const float*>(V), ldv, static_cast<float*>(w), d, j);
+            static_cast<const float*>(V), ldv, static_cast<float*>(w), d, j, stage_cap);
       else
         eng_step_for<double>(cfg.m, pairs)<<<P, kThreads, step_smem, stream>>>(
-            static_cast<const double*>(V), ldv, static_cast<double*>(w), d, j);
+            static_cast<const double*>(V), ldv, static_cast<double*>(w), d, j, stage_cap);
       prof_end(pr);
       if (j < KM) {
         pr = prof_begin(PC_MAXPY, j);
@@ -1106,10 +1138,10 @@ struct Engine {
           if (e == cudaSuccess) {
             if (ir())
               eng_step_for<float>(cfg.m, pr == 1)<<<Pc, kThreads, step_smem, stream>>>(
-                  static_cast<const float*>(V), ldv, static_cast<float*>(w), dev(), j);
+                  static_cast<const float*>(V), ldv, static_cast<float*>(w), dev(), j, stage_cap);
             else
               eng_step_for<double>(cfg.m, pr == 1)<<<Pc, kThreads, step_smem, stream>>>(
-                  static_cast<const double*>(V), ldv, static_cast<double*>(w), dev(), j);
+                  static_cast<const double*>(V), ldv, static_cast<double*>(w), dev(), j, stage_cap);
             e = cudaGetLastError();
           }
           if (e == cudaSuccess) e = cudaEventRecord(e1, stream);
@@ -1267,7 +1299,7 @@ gmres_status gmres_batch_create(const gmres_csr* A, int count, int m_restart, do
   b->tol = tol;
   b->max_iter = max_iter;
   // CSR pool: exactly what the systems need
-  for (int i = 0; i < count; ++i) c.csr_bytes += (A[i].n + 1) * 4 + A[i].nnz * 12 + 3 * 256 + 256;
+  for (int i = 0; i < count; ++i) c.csr_bytes += Engine::rp_entries(A[i].n) * 4 + A[i].nnz * 12 + 3 * 256 + 256;
   if (b->eng.init(c) != GMRES_OK) {
     g_batch_err = b->eng.err;
     const gmres_status st = b->eng.err.find("cudaErrorMemoryAllocation") != std::string::npos ||

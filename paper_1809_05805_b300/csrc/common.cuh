@@ -233,15 +233,21 @@ struct CsrStage {
   // Thread 0: start the copies of unit u with entry range [lo, hi).
   __device__ void issue(const int32_t* g_rp, const int32_t* g_col, const VT* g_val, int64_t u, int lo,
                         int hi) const {
+    issue_at(g_rp + u * U, g_col, g_val, U, lo, hi);
+  }
+  // Thread 0: start the copies of a unit of nrows rows whose rowptr slice
+  // starts at rp_src (16-byte aligned), with entry range [lo, hi).
+  __device__ void issue_at(const int32_t* rp_src, const int32_t* g_col, const VT* g_val, int nrows, int lo,
+                           int hi) const {
     // order this CTA's earlier shared-memory reads of the buffer before the
     // asynchronous writes into it
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    const uint32_t brp = (uint32_t)(U + 4) * 4;
+    const uint32_t brp = (uint32_t)(nrows + 4) * 4;
     const bool fits = hi - lo <= cap;
     const uint32_t bcol = fits ? (uint32_t)(hi - lo) * 4u : 0u;
     const uint32_t bval = fits ? (uint32_t)(hi - lo) * (uint32_t)sizeof(VT) : 0u;
     mbar_arrive_expect_tx(bar, brp + bcol + bval);
-    bulk_g2s(rp, g_rp + u * U, brp, bar);
+    bulk_g2s(rp, rp_src, brp, bar);
     if (bcol) {
       bulk_g2s(col, g_col + lo, bcol, bar);
       bulk_g2s(val, g_val + lo, bval, bar);
@@ -766,18 +772,19 @@ __device__ __forceinline__ void cta_partials(VT (&acc_a)[MAXC], VT (&acc_c)[MAXC
 // The one-reduce epilogue (last CTA), given the grid totals red[0 .. 2j+2) of
 // step j: lagged norm, completion of column j-1 at the tail, T row, r = T s,
 // the new Hessenberg column and the MAXPY coefficients.
-__device__ void epilogue_one_reduce(Small s, double* red, int j, bool tail) {
+__device__ void epilogue_one_reduce(Small s, double* red, int j, bool tail, size_t dyn_off = 0) {
   DevState* st = s.st;
   // ---------------- epilogue (last CTA) ----------------
   // stop: 0 = continue the cycle; 1 = cycle done after the T row (converged
   // or tail); 2 = cycle done now (breakdown, zero or non-finite norm); 3 =
   // exact breakdown found, column j-1 still to be finished (then 2).
   // T (rows and columns 0..j-1) and scale[0..j-1] are staged in shared memory
-  // (dynamic, (m+1)^2 + (m+1) doubles) so the O(j^2) work reads no global memory.
+  // (dynamic, (m+1)^2 + (m+1) doubles from byte dyn_off on) so the O(j^2) work
+  // reads no global memory.
   extern __shared__ __align__(16) double dyn[];
   const int ld = s.ldh;
-  double* sT = dyn;                       // (m+1) x (m+1), column-major, ld
-  double* sScale = dyn + (size_t)ld * ld; // m+1
+  double* sT = dyn + dyn_off / sizeof(double);  // (m+1) x (m+1), column-major, ld
+  double* sScale = sT + (size_t)ld * ld;         // m+1
   __shared__ double s_beta;
   __shared__ int s_stop;
   for (int e = threadIdx.x; e < j * j; e += blockDim.x) {

@@ -80,6 +80,6 @@ __device__ __forceinline__ const float* desc_val<float>(const SysDesc& d) {
 }
 
 template <typename VT>
-using EngStepKernel = void (*)(const VT*, int64_t, VT*, EngDev, int);
+using EngStepKernel = void (*)(const VT*, int64_t, VT*, EngDev, int, int);
 
 }  // namespace

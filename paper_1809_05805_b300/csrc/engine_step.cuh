@@ -6,23 +6,96 @@
 
 namespace {
 
+// The copies of one staged unit: its rowptr slice, the system's indices and
+// values, the unit's rows and entry range.
+template <typename VT>
+struct StageCopy {
+  const int32_t* rp;
+  const int32_t* col;
+  const VT* val;
+  int nrows, lo, hi;
+};
+
+// Rows of one system's CSR times x, one entry at a time from global memory
+// (local row indices; the same FMA order as csr_row): the engine step's path
+// for a unit whose staged range exceeds the buffer.
+template <typename VT, typename XT>
+__device__ __noinline__ VT csr_row_plain(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                                         const VT* __restrict__ val, const XT* __restrict__ x, int64_t i) {
+  VT s = VT(0);
+  for (int p = __ldg(rowptr + i), e = __ldg(rowptr + i + 1); p < e; ++p) s = fma(__ldg(val + p), ld_as<VT>(x + __ldg(col + p)), s);
+  return s;
+}
+
 // Step j of the current cycle for every listed system: the CTA walks its
 // range of listed tiles (pairs of consecutive tiles of one system, two rows
 // per thread, when PAIRS); whenever the range moves to another system it
 // publishes that system's sums, and the CTA completing a system runs the
-// system's reduction and epilogue.
+// system's reduction and epilogue. Each unit's CSR (rowptr slice, indices,
+// values; per-system local indices) is staged in shared memory by bulk copies
+// issued while the previous unit's block dot runs (as in the single-system
+// step kernel); the epilogue's shared memory follows the staging buffer
+// (cap entries), since a system's epilogue can run while the next unit lands.
+// Each system's rowptr is padded with nnz to whole tile pairs + 8.
 template <int MAXC, bool PAIRS, typename VT>
 __global__ void __launch_bounds__(kThreads, sizeof(VT) == 4 ? 3 : 2)
-ke_step(const VT* __restrict__ V, int64_t ldv, VT* __restrict__ w, EngDev e, int j) {
+ke_step(const VT* __restrict__ V, int64_t ldv, VT* __restrict__ w, EngDev e, int j, int cap) {
   __shared__ VT su[PAIRS ? 2 * kThreads : kThreads];
   __shared__ VT sw[PAIRS ? 2 * kThreads : kThreads];
   __shared__ double red[2 * (kMaxM + 1) + 2];
-  __shared__ int s_active, s_tail;
+  __shared__ int s_active, s_tail, s_stage_off;
   __shared__ SysDesc s_d;
+  __shared__ uint64_t s_bar;
+  __shared__ StageCopy<VT> s_nc;
+  extern __shared__ __align__(16) double dyn[];
   int64_t lo, hi;
   if (!cta_tile_range(e, (int)gridDim.x, lo, hi)) return;
   const int J8 = j / kWarps, r8 = j % kWarps;
   const VT* u = V + (size_t)j * ldv;
+  constexpr int kRpRows = 2 * kThreads;  // the rowptr slice holds up to a tile pair
+  constexpr int kWs = 8;                 // gathers in flight per staged row
+  CsrStage<VT> cs;
+  cs.rp = reinterpret_cast<int32_t*>(dyn);
+  cs.col = cs.rp + (kRpRows + 4);
+  cs.val = reinterpret_cast<VT*>(cs.col + cap);
+  cs.bar = &s_bar;
+  cs.cap = cap;
+  cs.U = kRpRows;
+  const size_t epi_off = (size_t)(kRpRows + 4) * 4 + (size_t)cap * (4 + sizeof(VT));
+  if (threadIdx.x == 0) {
+    s_stage_off = 0;
+    mbar_init(&s_bar, 1);
+  }
+  __syncthreads();
+  // thread 0: the unit at list position p (a pair when PAIRS and the tile is
+  // even with its partner next in this CTA's range) and its copies
+  auto unit_at = [&](int64_t p, int64_t& t, int& sy, bool& pair) {
+    t = __ldg(e.act_tiles + p);
+    sy = __ldg(e.act_sys + p);
+    pair = PAIRS && (t & 1) == 0 && p + 1 < hi && __ldg(e.act_sys + p + 1) == sy;
+  };
+  auto copy_of = [&](int64_t t, int sy, bool pair) {
+    const SysDesc* d = e.desc + sy;
+    StageCopy<VT> c;
+    c.rp = d->rowptr + (t * kThreads - d->row0);
+    c.col = d->col;
+    c.val = desc_val<VT>(*d);
+    c.nrows = pair ? 2 * kThreads : kThreads;
+    c.lo = CsrStage<VT>::lo_of(__ldg(c.rp));
+    c.hi = CsrStage<VT>::hi_of(__ldg(c.rp + c.nrows));
+    return c;
+  };
+  uint32_t phase = 0, pend_phase = 0;
+  bool pending = false;  // thread 0: a copy was issued and not yet seen complete (phase pend_phase)
+  if (threadIdx.x == 0 && lo < hi) {
+    int64_t t0;
+    int sy0;
+    bool pr0;
+    unit_at(lo, t0, sy0, pr0);
+    const StageCopy<VT> c = copy_of(t0, sy0, pr0);
+    cs.issue_at(c.rp, c.col, c.val, c.nrows, c.lo, c.hi);
+    pending = true;
+  }
   VT acc_a[MAXC], acc_c[MAXC], rem_a[kWarps - 1], rem_c[kWarps - 1];
   VT sig = VT(0), dd = VT(0);
   int cur = -1;
@@ -30,12 +103,16 @@ ke_step(const VT* __restrict__ V, int64_t ldv, VT* __restrict__ w, EngDev e, int
     const int64_t t = (it < hi) ? __ldg(e.act_tiles + it) : -1;
     const int snext = (it < hi) ? __ldg(e.act_sys + it) : -1;
     if (snext != cur) {  // CTA-uniform
+      if (snext < 0) {   // end of the range: no copy may still land in the buffer
+        if (threadIdx.x == 0 && pending) mbar_wait_bounded(&s_bar, pend_phase);
+        __syncthreads();
+      }
       if (cur >= 0 && s_active) {  // done with system cur: publish its sums
         cta_partials<MAXC, VT>(acc_a, acc_c, rem_a, rem_c, sig, dd, j, J8, r8, red);
         if (sys_publish(e, cur, red, 2 * j + 2)) {
           const Small sm = e.smalls[cur];
           if (threadIdx.x == 0) sm.st->reductions += 1;
-          epilogue_one_reduce(sm, red, j, s_tail);
+          epilogue_one_reduce(sm, red, j, s_tail, epi_off);
         }
       }
       if (snext < 0) break;
@@ -56,23 +133,82 @@ ke_step(const VT* __restrict__ V, int64_t ldv, VT* __restrict__ w, EngDev e, int
       sig = dd = VT(0);
     }
     const bool tail = s_tail;
-    const int64_t lim = s_d.row0 + s_d.n;
-    const int32_t* rp = s_d.rowptr - s_d.row0;  // indexed by arena row
-    const VT* val = desc_val<VT>(s_d);
-    const VT* xg = u + s_d.row0;
     // a system's tiles are consecutive in the list and in the arena (its
     // region starts on a tile pair): tiles t, t + 1 form the pair t / 2
-    if (PAIRS && (t & 1) == 0 && it + 1 < hi && __ldg(e.act_sys + it + 1) == cur) {
-      if (s_active)
-        tile_pair_block_dot<MAXC, VT>(t >> 1, lim, rp, s_d.col, val, V, ldv, u, xg, w, !tail, !tail, J8, r8, su, sw,
-                                      acc_a, acc_c, rem_a, rem_c, sig, dd);
-      it += 2;
-      continue;
+    const bool pair = PAIRS && (t & 1) == 0 && it + 1 < hi && __ldg(e.act_sys + it + 1) == cur;
+    const int64_t it_next = it + (pair ? 2 : 1);
+    if (threadIdx.x == 0) {  // the next unit's copies, described ahead of their issue (kept in shared memory)
+      s_nc.nrows = 0;
+      if (it_next < hi) {
+        int64_t t1;
+        int sy1;
+        bool pr1;
+        unit_at(it_next, t1, sy1, pr1);
+        s_nc = copy_of(t1, sy1, pr1);
+      }
     }
-    if (s_active)
-      tile_block_dot<MAXC, VT>(t, lim, rp, s_d.col, val, V, ldv, u, xg, w, !tail, !tail, J8, r8, su, sw, acc_a, acc_c,
-                               rem_a, rem_c, sig, dd);
-    ++it;
+    bool staged = !s_stage_off;
+    if (staged) {
+      staged = mbar_wait_bounded(&s_bar, phase);
+      if (!staged) s_stage_off = 1;
+    }
+    if (threadIdx.x == 0) {
+      if (staged) pending = false;
+      else if (pending) pend_phase = phase;
+    }
+    phase ^= 1u;
+    // once every thread is past this unit's SpMV, the buffer takes the next unit
+    auto next = [&]() {
+      if (threadIdx.x == 0 && s_nc.nrows > 0 && !s_stage_off) {
+        cs.issue_at(s_nc.rp, s_nc.col, s_nc.val, s_nc.nrows, s_nc.lo, s_nc.hi);
+        pending = true;
+      }
+    };
+    if (s_active) {
+      const int64_t lim = s_d.row0 + s_d.n;
+      const VT* val = desc_val<VT>(s_d);
+      const VT* xg = u + s_d.row0;
+      const int U = pair ? 2 * kThreads : kThreads;
+      const int64_t row0 = t * kThreads + threadIdx.x, row1 = row0 + kThreads;  // arena rows
+      const int32_t* rpl = s_d.rowptr - s_d.row0;  // indexed by arena row
+      int slo = 0;
+      if (staged) {
+        slo = CsrStage<VT>::lo_of(cs.rp[0]);
+        staged = CsrStage<VT>::hi_of(cs.rp[U]) - slo <= cap;
+      }
+      VT ur0 = VT(0), ur1 = VT(0), wr0 = VT(0), wr1 = VT(0);
+      if (row0 < lim) ur0 = ld_as<VT>(u + row0);
+      if (pair && row1 < lim) ur1 = ld_as<VT>(u + row1);
+      if (!tail) {
+        if (pair) {
+          if (staged)
+            csr_row2_staged<kWs>(cs.col, cs.val, xg, cs.rp[threadIdx.x] - slo, cs.rp[threadIdx.x + 1] - slo,
+                                 cs.rp[kThreads + threadIdx.x] - slo, cs.rp[kThreads + threadIdx.x + 1] - slo, wr0,
+                                 wr1);
+          else {
+            if (row0 < lim) wr0 = csr_row_plain(rpl, s_d.col, val, xg, row0);
+            if (row1 < lim) wr1 = csr_row_plain(rpl, s_d.col, val, xg, row1);
+          }
+          if (row0 < lim) w[row0] = wr0;
+          if (row1 < lim) w[row1] = wr1;
+        } else if (row0 < lim) {
+          wr0 = staged ? csr_row_staged<kWs>(cs.col, cs.val, xg, cs.rp[threadIdx.x] - slo,
+                                             cs.rp[threadIdx.x + 1] - slo)
+                       : csr_row_plain(rpl, s_d.col, val, xg, row0);
+          w[row0] = wr0;
+        }
+      }
+      if (pair)
+        tile_pair_dot_rows<MAXC, VT, VT>(t >> 1, lim, V, ldv, !tail, J8, r8, ur0, wr0, ur1, wr1, su, sw, acc_a, acc_c,
+                                         rem_a, rem_c, sig, dd, next);
+      else
+        tile_dot_rows<MAXC, VT, VT>(t, lim, V, ldv, !tail, J8, r8, ur0, wr0, su, sw, acc_a, acc_c, rem_a, rem_c, sig,
+                                    dd, next);
+    } else {
+      __syncthreads();  // every thread is past its wait for this unit
+      next();
+    }
+    it = it_next;
   }
 }
 
