@@ -53,7 +53,7 @@ ke_step(const VT* __restrict__ V, int64_t ldv, VT* __restrict__ w, EngDev e, int
   const int J8 = j / kWarps, r8 = j % kWarps;
   const VT* u = V + (size_t)j * ldv;
   constexpr int kRpRows = 2 * kThreads;  // the rowptr slice holds up to a tile pair
-  constexpr int kWs = 8;                 // gathers in flight per staged row
+  constexpr int kWs = 10;                // gathers in flight per staged row
   CsrStage<VT> cs;
   cs.rp = reinterpret_cast<int32_t*>(dyn);
   cs.col = cs.rp + (kRpRows + 4);
