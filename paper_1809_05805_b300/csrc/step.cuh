@@ -99,7 +99,7 @@ k_one_reduce_step(const int32_t* __restrict__ rowptr, const int32_t* __restrict_
     const int64_t units = (n + U - 1) / U;
     if (spmv) {
       extern __shared__ __align__(16) double dyn[];
-      constexpr int kWs = 8;  // gathers in flight per staged row
+      constexpr int kWs = STAGE == 2 ? 8 : 14;  // gathers in flight per staged row
       CsrStage<VT> cs;
       cs.rp = reinterpret_cast<int32_t*>(dyn);
       cs.col = cs.rp + (U + 4);
