@@ -76,11 +76,14 @@ METRIC_IR = "time-to-solve (1e-10 rel. resid), GMRES-IR: one-reduce cycles in FP
 def make_problem(w):
     return P.conv_diff_7pt(w["N"]) if w["stencil"] == "7pt" else P.aniso_27pt(w["N"])
 FP64_DFMA_PER_CLK_SM = 2  # B300: 1.25 TFLOP/s nominal FP64 = 148 SMs x 2 DFMA/clk x 2 flop x ~2.1 GHz
-# DRAM bytes per step launch / algorithmic bytes, from an ncu capture of the
-# step kernel on the 128^3 workload (dram__bytes_read.sum + dram__bytes_write.sum
-# over the launch's algorithmic bytes, at j = 8 and 9). Valid only for the kernel
-# build that capture measured; set to None when the kernel changes.
-STEP_TRAFFIC_RATIO = 1.047
+# DRAM bytes per step launch / algorithmic bytes, from ncu captures of the
+# step kernels (dram__bytes_read.sum + dram__bytes_write.sum over the launch's
+# algorithmic bytes): the FP64 kernel with staged tile pairs on the 128^3
+# 7-point workload at j = 8 and 9, the FP32 kernel with staged tiles on the
+# 144^3 27-point GMRES-IR workload at j = 18 and 19. Valid only for the kernel
+# builds those captures measured; set to None when a kernel changes.
+STEP_TRAFFIC_RATIO = 1.049
+STEP32_TRAFFIC_RATIO = 1.016
 
 
 def workload_name(w):
@@ -407,7 +410,10 @@ def run_ours(args, w, rank, world, dist):
             "bound": "hbm", "achieved": step_gbs, "peak": hbm, "unit": "GB/s",
             "frac": step_gbs / hbm if step_gbs else None,
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy bandwidth, of measured)",
-            "traffic": None,
+            "traffic": ((STEP32_TRAFFIC_RATIO * st["bytes"] / max(st["launches"], 1))
+                        if STEP32_TRAFFIC_RATIO and w["prec"] == "ir_fp32" else None),
+            "traffic_source": "ncu dram bytes / algorithmic bytes of the FP32 step at 144^3 (same kernel build), "
+                              "times this run's algorithmic bytes per launch",
             "launch_avg_ms": step_avg_ms, "launches": st["launches"],
             "alg_bytes_per_launch": st["bytes"] / max(st["launches"], 1),
             "fp32_tflops": step_tflops,
