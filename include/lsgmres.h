@@ -174,6 +174,19 @@ gmres_status gmres_set_profile(gmres_handle h, int on);
 gmres_status gmres_profile(gmres_handle h, int cls, double* total_ms, int64_t* launches,
                            double* alg_bytes, double* alg_flops);
 
+/* Testing the bounded waits of the CSR staging. The step kernel brings each
+ * tile's CSR into shared memory with bulk copies whose completion it waits for
+ * on an mbarrier, for at most ~2^31 SM clocks (about one second); a wait that
+ * runs out marks the solve stalled, the kernel stops using staged data and
+ * returns, and the solve (or gmres_arnoldi) returns GMRES_ERR_TIMEOUT. With
+ * on = 1, later FP64 solves of this handle announce 16 bytes per copy that no
+ * copy delivers, so every such wait runs out (each step launch then takes about
+ * two seconds); on = 0 restores normal operation. *staged (may be NULL)
+ * receives whether the handle's FP64 step kernel stages its CSR at all (a
+ * matrix whose largest tile does not fit the shared memory is read from global
+ * memory, with no waits). Never errors on a valid handle. */
+gmres_status gmres_test_stall_staging(gmres_handle h, int on, int* staged);
+
 /* ------------------------------------------------------------------------
  * Batched solves: many independent systems, one launch per Arnoldi step.
  * ------------------------------------------------------------------------

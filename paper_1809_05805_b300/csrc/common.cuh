@@ -48,6 +48,7 @@ struct DevState {
   int fresh;           // batched engine: the next residual pass also sets bnorm
   int pipe2;           // Givens rotations on column pairs (the L = 2 pipeline)
   int stalled;         // a bounded device-side wait for staged CSR data gave up
+  int stall_test;      // testing: staged copies announce 16 bytes more than they bring
   long long reductions;
   long long grid_syncs;
   double mgs_coef;     // MGS: coefficient of the pending axpy
@@ -231,14 +232,16 @@ struct CsrStage {
   __device__ static int lo_of(int p) { return p & ~3; }
   __device__ static int hi_of(int p) { return (p + 3) & ~3; }
   // Thread 0: start the copies of unit u with entry range [lo, hi).
-  __device__ void issue(const int32_t* g_rp, const int32_t* g_col, const VT* g_val, int64_t u, int lo,
-                        int hi) const {
-    issue_at(g_rp + u * U, g_col, g_val, U, lo, hi);
+  __device__ void issue(const int32_t* g_rp, const int32_t* g_col, const VT* g_val, int64_t u, int lo, int hi,
+                        uint32_t extra = 0) const {
+    issue_at(g_rp + u * U, g_col, g_val, U, lo, hi, extra);
   }
   // Thread 0: start the copies of a unit of nrows rows whose rowptr slice
-  // starts at rp_src (16-byte aligned), with entry range [lo, hi).
-  __device__ void issue_at(const int32_t* rp_src, const int32_t* g_col, const VT* g_val, int nrows, int lo,
-                           int hi) const {
+  // starts at rp_src (16-byte aligned), with entry range [lo, hi). `extra`
+  // bytes are announced on top of the copies' (0 except in the test of the
+  // bounded waits, where they never arrive).
+  __device__ void issue_at(const int32_t* rp_src, const int32_t* g_col, const VT* g_val, int nrows, int lo, int hi,
+                           uint32_t extra = 0) const {
     // order this CTA's earlier shared-memory reads of the buffer before the
     // asynchronous writes into it
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -246,7 +249,7 @@ struct CsrStage {
     const bool fits = hi - lo <= cap;
     const uint32_t bcol = fits ? (uint32_t)(hi - lo) * 4u : 0u;
     const uint32_t bval = fits ? (uint32_t)(hi - lo) * (uint32_t)sizeof(VT) : 0u;
-    mbar_arrive_expect_tx(bar, brp + bcol + bval);
+    mbar_arrive_expect_tx(bar, brp + bcol + bval + extra);
     bulk_g2s(rp, rp_src, brp, bar);
     if (bcol) {
       bulk_g2s(col, g_col + lo, bcol, bar);

@@ -565,6 +565,7 @@ struct gmres_ctx {
   // Staged CSR of the step kernels (FP64 cycles; FP32 cycles): mode 0 off,
   // 1 tiles, 2 tile pairs; entry capacity; dynamic shared memory at launch.
   int stage64 = 0, cap64 = 0, stage32 = 0, cap32 = 0, stage16 = 0, cap16 = 0;
+  int stall_test = 0;  // gmres_test_stall_staging
   size_t smem64 = 0, smem32 = 0, smem16 = 0;
   size_t lsq_smem = 0;   // dynamic shared memory of k_lsq (rotated Hessenberg)
   std::vector<double> hist;
@@ -1203,6 +1204,7 @@ gmres_status gmres_solve(gmres_handle h, const double* b, double* x, gmres_info*
   std::memset(h->h_st, 0, sizeof(DevState));
   h->h_st->tol = h->tol;
   h->h_st->pipe2 = h->ortho == GMRES_ONE_REDUCE_PIPE2;
+  h->h_st->stall_test = h->stall_test;
   if ((st = write_state(h)) != GMRES_OK) return st;
   const int P = h->P;
   prof_reset(h);
@@ -1362,6 +1364,13 @@ gmres_status gmres_destroy(gmres_handle h) {
 
 const char* gmres_last_error(gmres_handle h) { return h ? h->err.c_str() : g_create_err.c_str(); }
 
+gmres_status gmres_test_stall_staging(gmres_handle h, int on, int* staged) {
+  if (!h) return GMRES_ERR_ARG;
+  h->stall_test = on ? 1 : 0;
+  if (staged) *staged = h->stage64 != 0;
+  return GMRES_OK;
+}
+
 gmres_status gmres_set_profile(gmres_handle h, int on) {
   if (!h) return GMRES_ERR_ARG;
   h->prof_on = on != 0;
@@ -1479,6 +1488,7 @@ gmres_status gmres_arnoldi(gmres_handle h, const double* r0, int k, double* V_ou
   std::memset(h->h_st, 0, sizeof(DevState));
   h->h_st->tol = 0.0;
   h->h_st->pipe2 = h->ortho == GMRES_ONE_REDUCE_PIPE2;
+  h->h_st->stall_test = h->stall_test;
   if ((st = write_state(h)) != GMRES_OK) return st;
   CUDA_TRY(h, cudaMemsetAsync(h->s.H, 0, sizeof(double) * h->s.ldh * h->m, h->stream));
   CUDA_TRY(h, cudaMemsetAsync(h->s.T, 0, sizeof(double) * h->s.ldh * h->s.ldh, h->stream));

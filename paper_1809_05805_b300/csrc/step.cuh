@@ -54,16 +54,19 @@ k_one_reduce_step(const int32_t* __restrict__ rowptr, const int32_t* __restrict_
   __shared__ double red[2 * (kMaxM + 1) + 2];
   __shared__ int s_j, s_tail, s_skip, s_stage_off;
   __shared__ uint64_t s_bar;
+  __shared__ uint32_t s_extra;
   DevState* st = s.st;
   if (threadIdx.x == 0) {
     if (raw_out) {
       s_j = j_arg;
       s_tail = 0;
       s_skip = 0;
+      s_extra = 0;
     } else {
       s_skip = __ldcg(&st->done);
       s_j = __ldcg(&st->step);
       s_tail = (s_j == __ldcg(&st->kmax));
+      s_extra = __ldcg(&st->stall_test) ? 16u : 0u;
     }
   }
   __syncthreads();
@@ -117,7 +120,7 @@ k_one_reduce_step(const int32_t* __restrict__ rowptr, const int32_t* __restrict_
       int64_t unit = blockIdx.x;
       if (threadIdx.x == 0 && unit < units) {
         cs.issue(rowptr, col, val, unit, CsrStage<VT>::lo_of(__ldg(rowptr + unit * U)),
-                 CsrStage<VT>::hi_of(__ldg(rowptr + unit * U + U)));
+                 CsrStage<VT>::hi_of(__ldg(rowptr + unit * U + U)), s_extra);
         pending = true;
       }
       for (; unit < units; unit += gridDim.x) {
@@ -162,7 +165,7 @@ k_one_reduce_step(const int32_t* __restrict__ rowptr, const int32_t* __restrict_
         // once every thread is past its SpMV, the buffer takes the next unit
         auto next = [&]() {
           if (threadIdx.x == 0 && nx < units && !s_stage_off) {
-            cs.issue(rowptr, col, val, nx, nlo, nhi);
+            cs.issue(rowptr, col, val, nx, nlo, nhi, s_extra);
             pending = true;
           }
         };

@@ -79,7 +79,7 @@ class SolveInfo:
 
 EXPORTS = ["gmres_create", "gmres_set", "gmres_set_tol", "gmres_set_stream", "gmres_solve",
            "gmres_solve_host", "gmres_history", "gmres_destroy", "gmres_last_error", "lsg_spmv",
-           "lsg_block_dot", "lsg_maxpy", "gmres_arnoldi", "gmres_set_profile", "gmres_profile",
+           "lsg_block_dot", "lsg_maxpy", "gmres_arnoldi", "gmres_set_profile", "gmres_profile", "gmres_test_stall_staging",
            "lsg_block_dot_noalloc", "gmres_batch_create", "gmres_batch_set_grid", "gmres_batch_get_grid",
            "gmres_batch_set_rows_per_thread", "gmres_batch_get_rows_per_thread", "gmres_batch_set_stream", "gmres_batch_solve",
            "gmres_batch_solve_host", "gmres_batch_set_profile", "gmres_batch_profile", "gmres_batch_launch_log",
@@ -118,6 +118,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "lsg_maxpy": ([P, P, I64, I, P, D, P, P], I),
         "gmres_arnoldi": ([P, P, I, P, P, P, ctypes.POINTER(I)], I),
         "gmres_set_profile": ([P, I], I),
+        "gmres_test_stall_staging": ([P, I, ctypes.POINTER(I)], I),
         "lsg_block_dot_noalloc": ([P, P, P, I64, P, I64, I, P, P, I, P, P], I),
         "gmres_profile": ([P, I, ctypes.POINTER(D), ctypes.POINTER(I64), ctypes.POINTER(D),
                            ctypes.POINTER(D)], I),
@@ -269,6 +270,13 @@ class Solver:
 
     def set_profile(self, on: bool):
         self._check(self.lib.gmres_set_profile(self.h, int(on)))
+
+    def test_stall_staging(self, on: bool) -> bool:
+        """Make the bounded waits of the CSR staging run out (testing); returns
+        whether the FP64 step kernel stages its CSR at all."""
+        staged = ctypes.c_int(0)
+        self._check(self.lib.gmres_test_stall_staging(self.h, int(on), ctypes.byref(staged)))
+        return bool(staged.value)
 
     def profile(self) -> dict:
         """Per kernel class of the last solve: device ms, launches, algorithmic bytes and flops."""

@@ -1,0 +1,100 @@
+"""GPU tests of the CSR staging of the step kernel (each tile's rowptr slice,
+indices and values brought into shared memory by bulk copies, completion
+waited for on an mbarrier with a bounded wait).
+
+* Matrices whose rows differ wildly in length (empty rows, one long row, a
+  ragged tail) go through the staged kernel and match the oracle at the
+  single-solve bar.
+* The bounded wait: with the test switch on, every copy announces 16 bytes
+  that never arrive, so every wait runs out (no fault, no hang: the waits are
+  bounded and no copy is left in flight); the solve must come back with
+  GMRES_ERR_TIMEOUT within seconds, and the same handle must solve normally
+  afterwards.
+"""
+import time
+
+import numpy as np
+import pytest
+
+from paper_1809_05805_b300 import problems as P
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+@pytest.fixture(scope="module")
+def lsg():
+    from paper_1809_05805_b300 import lsgmres
+
+    lsgmres.load()
+    return lsgmres
+
+
+def _ragged(n, seed):
+    """Diagonally dominant CSR with row lengths 0..40 except every 97th row
+    (length 300), and empty off-diagonal rows near the end: staged tiles of
+    very different sizes."""
+    rng = np.random.default_rng(seed)
+    rows, cols, vals = [], [], []
+    for i in range(n):
+        k = 300 if i % 97 == 5 else int(rng.integers(0, 41))
+        if i > n - 40:
+            k = 0
+        c = np.unique(rng.integers(0, n, k))
+        c = c[c != i]
+        v = rng.uniform(-1, 1, len(c)) / max(len(c), 1)
+        rows.extend([i] * (len(c) + 1))
+        cols.extend([i, *c.tolist()])
+        vals.extend([4.0, *v.tolist()])
+    order = np.lexsort((np.array(cols), np.array(rows)))
+    r = np.array(rows)[order]
+    rp = np.zeros(n + 1, np.int32)
+    np.add.at(rp, r + 1, 1)
+    return np.cumsum(rp).astype(np.int32), np.array(cols, np.int32)[order], np.array(vals)[order]
+
+
+@pytest.mark.parametrize("n", [1000, 5000, 40000])
+def test_staged_ragged_rows_match_oracle(torch_cuda, lsg, orc, n):
+    torch = torch_cuda
+    A = _ragged(n, seed=n)
+    b = np.random.default_rng(1).standard_normal(n)
+    s = lsg.Solver(A, m=20, tol=1e-10, max_iter=400)
+    assert s.test_stall_staging(False)  # the FP64 step kernel stages this matrix
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    info = s.solve(torch.from_numpy(b).cuda(), x)
+    r = orc.gmres(A, b, variant=1, m=20, tol=1e-10, max_iter=400)
+    assert info.status == r.status and info.iters == r.iters and info.restarts == r.restarts
+    hist = s.history()
+    k = min(50, len(hist))
+    assert np.all(np.abs(hist[:k] - r.history[:k]) <= 1e-8 * r.history[:k] + 1e-15)
+    assert np.linalg.norm(x.cpu().numpy() - r.x) <= 1e-9 * np.linalg.norm(r.x)
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_staging_wait_runs_out_and_reports_timeout(torch_cuda, lsg, graph):
+    torch = torch_cuda
+    A = P.conv_diff_7pt(24)
+    n = len(A[0]) - 1
+    _, b = P.rhs(A, seed=2)
+    bd = torch.from_numpy(b).cuda()
+    s = lsg.Solver(A, m=6, tol=1e-8, max_iter=300, stream=torch.cuda.Stream() if graph else None)
+    assert s.test_stall_staging(True)
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    t0 = time.time()
+    with pytest.raises(lsg.GmresError) as e:
+        s.solve(bd, x)
+    assert e.value.status == lsg.ERR_TIMEOUT
+    assert time.time() - t0 < 120
+    s.test_stall_staging(False)
+    x.zero_()
+    info = s.solve(bd, x)
+    assert info.status == 0
+    assert np.linalg.norm(b - P.to_scipy(A) @ x.cpu().numpy()) <= 1e-8 * np.linalg.norm(b)
