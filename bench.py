@@ -86,6 +86,33 @@ STEP_TRAFFIC_RATIO = 1.049
 STEP32_TRAFFIC_RATIO = 1.016
 
 
+def _rank_device(dist):
+    """Device of the collective tensors: CUDA under NCCL, the host under gloo."""
+    return "cuda" if dist.get_backend() == "nccl" else "cpu"
+
+
+def rank_barrier(dist):
+    """All ranks meet, then this rank's device work is done (the timing rule's
+    synchronization on both sides of the timed region)."""
+    import torch
+
+    if dist is not None:
+        dist.barrier()
+    if torch.cuda.is_available():
+        torch.cuda.synchronize()
+
+
+def rank_max(dist, v):
+    """Largest v over all ranks (a replicated step is as slow as its slowest rank)."""
+    if dist is None:
+        return v
+    import torch
+
+    t = torch.tensor([float(v)], dtype=torch.float64, device=_rank_device(dist))
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def workload_name(w):
     N = w["N"]
     if w["stencil"] == "27pt":
@@ -214,10 +241,10 @@ def golden_profile(name):
     out = {}
     with open(path) as f:
         for line in f:
-            if line.startswith("#") or not line.strip() or line.startswith("history"):
+            f_ = line.split()
+            if line.startswith("#") or len(f_) != 2:  # comments and the vector entries (history, x samples)
                 continue
-            k, v = line.split()
-            out[k] = float(v)
+            out[f_[0]] = float(f_[1])
     return out
 
 
@@ -298,16 +325,10 @@ def run_ours(args, w, rank, world, dist):
     ir = w["prec"] == "ir_fp32"
 
     def barrier():
-        if dist is not None:
-            dist.barrier()
-        torch.cuda.synchronize()
+        rank_barrier(dist)
 
     def max_over_ranks(v):
-        if dist is None:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return rank_max(dist, v)
 
     bd = torch.from_numpy(b).cuda()
     x = torch.zeros(n, dtype=torch.float64, device="cuda")
@@ -575,16 +596,10 @@ def run_batch(args, w, rank, world, dist):
     peaks = load_peaks()
 
     def barrier():
-        if dist is not None:
-            dist.barrier()
-        torch.cuda.synchronize()
+        rank_barrier(dist)
 
     def max_over_ranks(v):
-        if dist is None:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return rank_max(dist, v)
 
     t0 = time.perf_counter()
     bs = lsgmres.BatchSolver(mats, m=w["m"], tol=w["tol"], max_iter=w["max_iter"], stream=stream)
@@ -803,6 +818,9 @@ def run_serve(args, w, rank, world, dist):
     lat = np.concatenate(lats)
     wall = float(np.mean(walls))
     thr = k / wall
+    # replicas: every rank serves its own copy of the stream; the job's throughput
+    # is all ranks' requests over the slowest rank's makespan
+    job_thr = world * k / rank_max(dist, wall)
     true_rel = [float(np.linalg.norm(r["b"] - P.to_scipy(r["A"]) @ x) / np.linalg.norm(r["b"]))
                 for r, x in zip(reqs, xs_last)]
     # sustainable load: half the measured throughput, same requests
@@ -889,8 +907,8 @@ def run_serve(args, w, rank, world, dist):
                          f"{t_tot:.1f} s), scaled to all {k} requests by sum(n_i * iters_i)"}
     ntot = sum(r["n"] for r in reqs)
     line = {
-        "metric": METRIC_SERVE, "value": thr, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": 1e3 * wall, "higher_is_better": True, "scaling": "weak",
+        "metric": METRIC_SERVE, "value": job_thr, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * world * k / job_thr, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64 / f32 cycles (GMRES-IR)",
         "data": "synthetic (seeded 3D 7-point stencils, x_true ~ U[-1,1], Poisson arrivals)",
         "config": {"workload": (f"{k} requests, Poisson arrivals at {w['rate']:g}/s, 3D 7-point convection-diffusion, "
@@ -912,7 +930,7 @@ def run_serve(args, w, rank, world, dist):
                    "peak_bytes_in_use": st["peak_bytes_in_use"]},
         "sequential": seq,
         "speedup_vs_sequential": (thr / seq["solves_per_s"]) if seq else None,
-        "e2e": {"value": thr, "unit": "solves/s", "h2d_bytes_per_step": int(sum(8 * r["n"] + 12 * len(r["A"][1])
+        "e2e": {"value": job_thr, "unit": "solves/s", "h2d_bytes_per_step": int(sum(8 * r["n"] + 12 * len(r["A"][1])
                                                                             for r in reqs)),
                 "d2h_bytes_per_step": int(8 * ntot)},
         "gpu_launches": int(sum(st["kernel_launches"])),
