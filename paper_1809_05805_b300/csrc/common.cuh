@@ -18,6 +18,8 @@ constexpr int kThreads = 256;                // CTA size; also rows per tile
 constexpr int kWarps = kThreads / 32;        // 8
 constexpr int kRowsPerLane = kThreads / 32;  // rows of a tile handled by one lane in the dot phase
 constexpr int kRemBatch = 4;                 // remainder columns of the block dot loaded together
+constexpr int kGridGroup = 16;               // CTAs per group of a two-level grid reduction
+constexpr int kGridGroupsMax = 32;           // groups a two-level grid reduction supports (grids <= 512)
 constexpr int kMaxM = 128;                   // largest restart length
 constexpr double kEps = 2.220446049250313e-16;
 constexpr double kBreakdownFactor = 16.0;
@@ -45,6 +47,7 @@ struct DevState {
   int restarts;
   int breakdowns;
   unsigned int ticket; // last-CTA election
+  unsigned int gticket[kGridGroupsMax];  // per CTA group, two-level grid reductions
   int fresh;           // batched engine: the next residual pass also sets bnorm
   int pipe2;           // Givens rotations on column pairs (the L = 2 pipeline)
   int stalled;         // a bounded device-side wait for staged CSR data gave up
@@ -396,8 +399,26 @@ __device__ bool publish_and_reduce(double* partials, int nvmax, int64_t slot, in
 }
 
 // Grid-wide form: every CTA of the grid publishes one slot (its block index).
+// The last CTA sums the slots with S threads per value; when that leaves more
+// than 8 slots per thread (many CTAs and many values: each thread's loads come
+// in dependent rounds of 8, and the sums are one dependent FP64 chain), the
+// reduction takes two levels instead: the last CTA of each group of 16
+// consecutive CTAs sums its group's slots into row P + group, and the last
+// group sums the group rows. Both levels sum in a fixed order (deterministic
+// for a given grid). Needs P + ceil(P / 16) rows of partials.
 __device__ bool grid_reduce_last(Small s, double* red, int nv) {
-  if (!publish_and_reduce(s.partials, s.nvmax, blockIdx.x, 0, gridDim.x, &s.st->ticket, red, nv)) return false;
+  const int P = gridDim.x;
+  int S = 1;
+  while (2 * S * nv <= (int)blockDim.x && S < (int)blockDim.x) S *= 2;
+  const int NG = (P + kGridGroup - 1) / kGridGroup;
+  if ((P + S - 1) / S <= 8 || NG > kGridGroupsMax) {
+    if (!publish_and_reduce(s.partials, s.nvmax, blockIdx.x, 0, P, &s.st->ticket, red, nv)) return false;
+  } else {
+    const int g = (int)blockIdx.x / kGridGroup, g0 = g * kGridGroup;
+    const int gn = (P - g0 < kGridGroup) ? P - g0 : kGridGroup;
+    if (!publish_and_reduce(s.partials, s.nvmax, blockIdx.x, g0, gn, &s.st->gticket[g], red, nv)) return false;
+    if (!publish_and_reduce(s.partials, s.nvmax, P + g, P, NG, &s.st->ticket, red, nv)) return false;
+  }
   if (threadIdx.x == 0) s.st->reductions += 1;
   return true;
 }

@@ -489,8 +489,10 @@ __global__ void k_spmv(const int32_t* __restrict__ rowptr, const int32_t* __rest
 constexpr int kNoAllocMaxJ = 64;                       // largest j (block-dot columns)
 constexpr int kNoAllocMaxCtas = 296;                   // largest grid of the reduction
 constexpr int kNoAllocNv = 2 * kNoAllocMaxJ + 2;       // sums per CTA
-constexpr size_t kNoAllocStateBytes = 256;             // DevState, padded
-constexpr size_t kNoAllocBytes = kNoAllocStateBytes + sizeof(double) * (size_t)kNoAllocMaxCtas * kNoAllocNv;
+constexpr size_t kNoAllocStateBytes = 512;             // DevState, padded
+constexpr size_t kNoAllocBytes =
+    kNoAllocStateBytes +
+    sizeof(double) * (size_t)(kNoAllocMaxCtas + (kNoAllocMaxCtas + kGridGroup - 1) / kGridGroup) * kNoAllocNv;
 static_assert(sizeof(DevState) <= kNoAllocStateBytes, "DevState outgrew its slot");
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
@@ -668,7 +670,8 @@ gmres_status alloc_small(gmres_ctx* h) {
   const size_t o_cf = take(sizeof(double) * (m + 3));
   const size_t o_cx = take(sizeof(double) * (m + 3));
   const size_t o_hi = take(sizeof(double) * h->s.hist_cap);
-  const size_t o_pa = take(sizeof(double) * (size_t)std::max(h->P, h->P32) * nvmax);
+  const int Pmax = std::max(h->P, h->P32);  // rows: one per CTA, then one per group of 16 CTAs
+  const size_t o_pa = take(sizeof(double) * (size_t)(Pmax + (Pmax + kGridGroup - 1) / kGridGroup) * nvmax);
   const size_t o_raw = take(sizeof(double) * nvmax);
   if (h->small) cudaFree(h->small);
   h->small = nullptr;
