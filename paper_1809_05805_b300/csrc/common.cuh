@@ -11,6 +11,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <type_traits>
 
 namespace {
 
@@ -532,21 +533,52 @@ __device__ int finish_completed(Small s, int c, double h, bool tail) {
 // At j == kmax (the tail) the SpMV and c, d are skipped.
 // Standalone mode (raw_out != nullptr): j is j_arg, w may be an input
 // (use_spmv == 0), and the totals go to raw_out without the GMRES epilogue.
+// Where the block dot of a 256-row tile t reads basis column k: GlobalCols
+// reads the basis in global memory (row 256 t of column k at V + k ldv + r0);
+// SharedCols a copy of the tile's columns in shared memory (column k at
+// s + 256 k).
+// ld(k, i) reads entry i of the tile's slice of column k (global memory goes
+// through the read-only path, which takes global addresses only; shared
+// memory through plain loads).
+template <typename SV>
+struct GlobalCols {
+  const SV* V;
+  int64_t ldv;
+  int64_t r0;
+  template <typename VT>
+  __device__ VT ld(int k, int i) const {
+    return ld_as<VT>(V + (size_t)k * ldv + r0 + i);
+  }
+};
+template <typename SV>
+struct SharedCols {
+  const SV* s;
+  template <typename VT>
+  __device__ VT ld(int k, int i) const {
+    if constexpr (std::is_same<SV, __nv_bfloat16>::value)
+      return __bfloat162float(s[(size_t)k * kThreads + i]);
+    else
+      return (VT)s[(size_t)k * kThreads + i];
+  }
+};
+
 // The block-dot half of one 256-row tile t, given this thread's row values
 // ur = u[row], wr = w[row] (zero for rows >= n): accumulates sigma and d,
 // stages u and w of the tile in shared memory, calls hook() once every thread
-// of the CTA is past its SpMV (the staged CSR of the tile is no longer read),
-// then splits the block dot over the 8 warps: warp w owns columns w, w+8, ...
-// over all 8 row groups, and the r8 = j mod 8 remainder columns are split by
-// rows.
+// of the CTA is past its SpMV (the staged CSR of the tile is no longer read)
+// and before() ahead of the first basis read, then splits the block dot over
+// the 8 warps: warp w owns columns w, w+8, ... over all 8 row groups, and the
+// r8 = j mod 8 remainder columns are split by rows; after() runs once every
+// thread is done with the tile's basis columns.
 struct NoHook {
   __device__ void operator()() const {}
 };
-template <int MAXC, typename SV, typename VT, typename Hook>
-__device__ __forceinline__ void tile_dot_rows(int64_t t, int64_t n, const SV* __restrict__ V, int64_t ldv,
-                                              bool need_w, int J8, int r8, VT ur, VT wr, VT* su, VT* sw,
-                                              VT (&acc_a)[MAXC], VT (&acc_c)[MAXC], VT (&rem_a)[kWarps - 1],
-                                              VT (&rem_c)[kWarps - 1], VT& sig, VT& dd, Hook hook) {
+template <int MAXC, typename SV, typename VT, typename Cols, typename Hook, typename Before, typename After>
+__device__ __forceinline__ void tile_dot_rows_cols(int64_t t, int64_t n, Cols cols, bool need_w, int J8, int r8,
+                                                   VT ur, VT wr, VT* su, VT* sw, VT (&acc_a)[MAXC],
+                                                   VT (&acc_c)[MAXC], VT (&rem_a)[kWarps - 1],
+                                                   VT (&rem_c)[kWarps - 1], VT& sig, VT& dd, Hook hook,
+                                                   Before before, After after) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int64_t row = t * kThreads + threadIdx.x;
   sig = fma(ur, ur, sig);
@@ -555,6 +587,7 @@ __device__ __forceinline__ void tile_dot_rows(int64_t t, int64_t n, const SV* __
   sw[threadIdx.x] = wr;
   __syncthreads();
   hook();
+  before();
   const int64_t base = t * kThreads + lane;
   VT ru[kRowsPerLane], rw[kRowsPerLane];
 #pragma unroll
@@ -566,10 +599,10 @@ __device__ __forceinline__ void tile_dot_rows(int64_t t, int64_t n, const SV* __
   for (int c = 0; c < MAXC; ++c) {
     if (c < J8) {  // warp-uniform
       const int k = wid + c * kWarps;
-      const SV* vk = V + (size_t)k * ldv + base;
       VT x[kRowsPerLane];
 #pragma unroll
-      for (int q = 0; q < kRowsPerLane; ++q) x[q] = (base + 32 * q < n) ? ld_as<VT>(vk + 32 * q) : VT(0);
+      for (int q = 0; q < kRowsPerLane; ++q)
+        x[q] = (base + 32 * q < n) ? cols.template ld<VT>(k, lane + 32 * q) : VT(0);
 #pragma unroll
       for (int q = 0; q < kRowsPerLane; ++q) acc_a[c] = fma(x[q], ru[q], acc_a[c]);
       if (need_w) {  // the cycle's tail needs only V^T u
@@ -587,7 +620,7 @@ __device__ __forceinline__ void tile_dot_rows(int64_t t, int64_t n, const SV* __
 #pragma unroll
       for (int b = 0; b < kRemBatch; ++b) {
         const int c = c0 + b;
-        x[b] = (c < r8 && row < n) ? ld_as<VT>(V + (size_t)(J8 * kWarps + c) * ldv + row) : VT(0);
+        x[b] = (c < r8 && row < n) ? cols.template ld<VT>(J8 * kWarps + c, (int)threadIdx.x) : VT(0);
       }
 #pragma unroll
       for (int b = 0; b < kRemBatch; ++b) {
@@ -600,6 +633,17 @@ __device__ __forceinline__ void tile_dot_rows(int64_t t, int64_t n, const SV* __
     }
   }
   __syncthreads();
+  after();
+}
+
+// The block-dot half of one tile with the basis read from global memory.
+template <int MAXC, typename SV, typename VT, typename Hook>
+__device__ __forceinline__ void tile_dot_rows(int64_t t, int64_t n, const SV* __restrict__ V, int64_t ldv,
+                                              bool need_w, int J8, int r8, VT ur, VT wr, VT* su, VT* sw,
+                                              VT (&acc_a)[MAXC], VT (&acc_c)[MAXC], VT (&rem_a)[kWarps - 1],
+                                              VT (&rem_c)[kWarps - 1], VT& sig, VT& dd, Hook hook) {
+  tile_dot_rows_cols<MAXC, SV, VT>(t, n, GlobalCols<SV>{V, ldv, t * kThreads}, need_w, J8, r8, ur, wr, su, sw,
+                                   acc_a, acc_c, rem_a, rem_c, sig, dd, hook, NoHook{}, NoHook{});
 }
 
 // The block-dot half of the tile pair pp (rows 512 pp .. 512 pp + 511, two

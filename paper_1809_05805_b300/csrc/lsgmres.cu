@@ -540,7 +540,8 @@ struct gmres_ctx {
   int device = 0;
   int nsm = 0;
   int P = 0;          // CTAs of reduction kernels
-  int P32 = 0;        // CTAs of the FP32-cycle step kernel (3 resident per SM)
+  int P32 = 0;        // CTAs of the FP32-cycle step kernel (3 resident per SM; 2 in staging mode 3)
+  int P16 = 0;        // the same for the BF16-basis step kernel
   int grid_stream = 0;// CTAs of streaming kernels
   int32_t* rowptr = nullptr;
   int32_t* col = nullptr;
@@ -670,7 +671,7 @@ gmres_status alloc_small(gmres_ctx* h) {
   const size_t o_cf = take(sizeof(double) * (m + 3));
   const size_t o_cx = take(sizeof(double) * (m + 3));
   const size_t o_hi = take(sizeof(double) * h->s.hist_cap);
-  const int Pmax = std::max(h->P, h->P32);  // rows: one per CTA, then one per group of 16 CTAs
+  const int Pmax = std::max({h->P, h->P32, h->P16});  // rows: one per CTA, then one per group of 16 CTAs
   const size_t o_pa = take(sizeof(double) * (size_t)(Pmax + (Pmax + kGridGroup - 1) / kGridGroup) * nvmax);
   const size_t o_raw = take(sizeof(double) * nvmax);
   if (h->small) cudaFree(h->small);
@@ -721,7 +722,7 @@ gmres_status launch_cycle(gmres_ctx* h, int kmax) {
                                                               h->w32, h->n, h->s, 0, 1, nullptr, h->stage32,
                                                               h->cap32);
       else if (h->prec == GMRES_IR_BF16)
-        h->step16<<<h->P32, kThreads, h->smem16, h->stream>>>(h->rowptr, h->col, h->val32, h->V16, h->ldv, nullptr,
+        h->step16<<<h->P16, kThreads, h->smem16, h->stream>>>(h->rowptr, h->col, h->val32, h->V16, h->ldv, nullptr,
                                                               h->w32, h->n, h->s, 0, 1, nullptr, h->stage16,
                                                               h->cap16);
       else
@@ -994,28 +995,35 @@ static void csr_stage_caps(const std::vector<int32_t>& rp, int64_t n, int& cap_t
 // Staging of a step kernel with values of vb bytes, launched on P CTAs of
 // which `per_sm` must stay resident per SM: tile pairs when the unstaged kernel
 // would take pairs (ntiles >= 4 P) and their buffer fits, else single tiles if
-// theirs fits, else off. kernel_for(stage) gives the kernel of a mode; the
-// dynamic shared memory is the larger of the epilogue's (t_smem) and the
-// staging buffer's. Sets the kernel's shared-memory limit.
+// theirs fits, else off. With v3_bytes > 0 (the basis columns of a tile, FP32
+// cycles), mode 3 (single tiles with their basis columns staged too, two CTAs
+// per SM) is tried first; *P is then lowered to two CTAs per SM. kernel_for(stage)
+// gives the kernel of a mode; the dynamic shared memory is the larger of the
+// epilogue's (t_smem) and the staging buffer's. Sets the kernel's
+// shared-memory limit.
 template <typename KernelFor>
-static gmres_status choose_stage(KernelFor kernel_for, size_t vb, int per_sm, int P, int64_t ntiles, int cap_tile,
-                                 int cap_pair, size_t t_smem, int& mode, int& cap, size_t& smem) {
-  const bool pairs = ntiles >= 4 * (int64_t)P;
-  for (int cand : {2, 1}) {
+static gmres_status choose_stage(KernelFor kernel_for, size_t vb, int per_sm, int* P, int nsm, int64_t ntiles,
+                                 int cap_tile, int cap_pair, size_t t_smem, size_t v3_bytes, int& mode, int& cap,
+                                 size_t& smem) {
+  const bool pairs = ntiles >= 4 * (int64_t)*P;
+  for (int cand : {3, 2, 1}) {
+    if (cand == 3 && (v3_bytes == 0 || ntiles < 4 * 2 * (int64_t)nsm)) continue;
     if (cand == 2 && !pairs) continue;
     const int U = cand == 2 ? 2 * kThreads : kThreads;
     const int c = cand == 2 ? cap_pair : cap_tile;
-    const size_t need = std::max(t_smem, (size_t)(U + 4) * 4 + (size_t)c * (4 + vb));
+    const size_t need =
+        std::max(t_smem, (size_t)(U + 4) * 4 + (size_t)c * (4 + vb) + (cand == 3 ? v3_bytes : 0));
     if (need > 200 * 1024) continue;
     const void* k = reinterpret_cast<const void*>(kernel_for(cand));
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need) != cudaSuccess)
       return GMRES_ERR_CUDA;
     int nb = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, kThreads, need) != cudaSuccess) return GMRES_ERR_CUDA;
-    if (nb >= per_sm) {
+    if (nb >= (cand == 3 ? 2 : per_sm)) {
       mode = cand;
       cap = c;
       smem = need;
+      if (cand == 3) *P = (int)std::min<int64_t>(2 * (int64_t)nsm, ntiles);
       return GMRES_OK;
     }
   }
@@ -1086,6 +1094,7 @@ gmres_status gmres_create(const gmres_csr* A, int m_restart, double tol, gmres_h
   const int64_t ntiles = (n + kThreads - 1) / kThreads;
   h->P = (int)std::min<int64_t>(2 * (int64_t)h->nsm, ntiles);
   h->P32 = (int)std::min<int64_t>(3 * (int64_t)h->nsm, ntiles);
+  h->P16 = h->P32;
   h->grid_stream = (int)std::min<int64_t>(4 * (int64_t)h->nsm, std::max<int64_t>(1, (n / 2 + kThreads - 1) / kThreads));
   const int64_t nnz_pad = align_up(std::max<int64_t>(nnz, 1), 4);
   // rowptr is padded with nnz to a whole number of 512-row tile pairs + 8, so
@@ -1102,7 +1111,9 @@ gmres_status gmres_create(const gmres_csr* A, int m_restart, double tol, gmres_h
     CREATE_TRY(cudaMemcpy(h->col, cl.data(), sizeof(int32_t) * nnz, cudaMemcpyHostToDevice));
     CREATE_TRY(cudaMemcpy(h->val, vl.data(), sizeof(double) * nnz, cudaMemcpyHostToDevice));
   }
-  h->ldv = (int64_t)align_up((size_t)n, 32);
+  // whole tile pairs: a staged copy of a tile's slice of a basis column stays
+  // inside its column
+  h->ldv = (int64_t)align_up((size_t)n, 2 * kThreads);
   CREATE_TRY(cudaMalloc(&h->V, sizeof(double) * (size_t)h->ldv * (m_restart + 1)));
   CREATE_TRY(cudaMemset(h->V, 0, sizeof(double) * (size_t)h->ldv * (m_restart + 1)));
   CREATE_TRY(cudaMalloc(&h->w, sizeof(double) * (size_t)h->ldv));
@@ -1117,14 +1128,16 @@ gmres_status gmres_create(const gmres_csr* A, int m_restart, double tol, gmres_h
     int cap_tile = 0, cap_pair = 0;
     csr_stage_caps(rp, n, cap_tile, cap_pair);
     const int m = m_restart;
-    gmres_status sst = choose_stage([m](int sg) { return step64_for(m, sg); }, sizeof(double), 2,
-                                    h->P, ntiles, cap_tile, cap_pair, h->step_smem, h->stage64, h->cap64, h->smem64);
+    gmres_status sst = choose_stage([m](int sg) { return step64_for(m, sg); }, sizeof(double), 2, &h->P, h->nsm,
+                                    ntiles, cap_tile, cap_pair, h->step_smem, 0, h->stage64, h->cap64, h->smem64);
     if (sst == GMRES_OK)
-      sst = choose_stage([m](int sg) { return step32_for(m, sg); }, sizeof(float), 3, h->P32, ntiles,
-                         cap_tile, cap_pair, h->step_smem, h->stage32, h->cap32, h->smem32);
+      sst = choose_stage([m](int sg) { return step32_for(m, sg); }, sizeof(float), 3, &h->P32, h->nsm, ntiles,
+                         cap_tile, cap_pair, h->step_smem, (size_t)m * kThreads * sizeof(float), h->stage32,
+                         h->cap32, h->smem32);
     if (sst == GMRES_OK)
-      sst = choose_stage([m](int sg) { return step16_for(m, sg); }, sizeof(float), 3,
-                         h->P32, ntiles, cap_tile, cap_pair, h->step_smem, h->stage16, h->cap16, h->smem16);
+      sst = choose_stage([m](int sg) { return step16_for(m, sg); }, sizeof(float), 3, &h->P16, h->nsm, ntiles,
+                         cap_tile, cap_pair, h->step_smem, (size_t)m * kThreads * sizeof(__nv_bfloat16),
+                         h->stage16, h->cap16, h->smem16);
     if (sst != GMRES_OK) {
       h->err = "cudaFuncSetAttribute / occupancy query of the step kernels failed";
       return bail(GMRES_ERR_CUDA);

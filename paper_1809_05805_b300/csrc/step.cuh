@@ -10,7 +10,8 @@
 
 namespace lsg_steps {
 // Host stub of the step kernel for restart length m and staging mode (0 off,
-// 1 tiles, 2 tile pairs); callers cast it to their StepKernel type.
+// 1 tiles, 2 tile pairs, 3 tiles with their basis columns); callers cast it
+// to their StepKernel type.
 const void* step_kernel_f64_s0(int m);
 const void* step_kernel_f64_s1(int m);
 const void* step_kernel_f64_s2(int m);
@@ -20,14 +21,23 @@ const void* step_kernel_f32_s2(int m);
 const void* step_kernel_bf16_s0(int m);
 const void* step_kernel_bf16_s1(int m);
 const void* step_kernel_bf16_s2(int m);
+const void* step_kernel_f32_s3(int m);
+const void* step_kernel_bf16_s3(int m);
+// FP64 has no mode 3 (its basis tile does not fit beside two resident CTAs).
 inline const void* step_kernel_f64(int m, int stage) {
   return stage == 2 ? step_kernel_f64_s2(m) : stage == 1 ? step_kernel_f64_s1(m) : step_kernel_f64_s0(m);
 }
 inline const void* step_kernel_f32(int m, int stage) {
-  return stage == 2 ? step_kernel_f32_s2(m) : stage == 1 ? step_kernel_f32_s1(m) : step_kernel_f32_s0(m);
+  return stage == 3   ? step_kernel_f32_s3(m)
+         : stage == 2 ? step_kernel_f32_s2(m)
+         : stage == 1 ? step_kernel_f32_s1(m)
+                      : step_kernel_f32_s0(m);
 }
 inline const void* step_kernel_bf16(int m, int stage) {
-  return stage == 2 ? step_kernel_bf16_s2(m) : stage == 1 ? step_kernel_bf16_s1(m) : step_kernel_bf16_s0(m);
+  return stage == 3   ? step_kernel_bf16_s3(m)
+         : stage == 2 ? step_kernel_bf16_s2(m)
+         : stage == 1 ? step_kernel_bf16_s1(m)
+                      : step_kernel_bf16_s0(m);
 }
 }  // namespace lsg_steps
 
@@ -44,7 +54,7 @@ using StepKernel = void (*)(const int32_t*, const int32_t*, const VT*, const SV*
 // the 192^3 27-point GMRES-IR solve: 2.9 -> 3.4 TB/s; four per SM spill and
 // lose).
 template <int MAXC, typename VT, typename SV = VT, int STAGE = 0>
-__global__ void __launch_bounds__(kThreads, sizeof(VT) == 4 ? 3 : 2)
+__global__ void __launch_bounds__(kThreads, (sizeof(VT) == 4 && STAGE != 3) ? 3 : 2)
 k_one_reduce_step(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                   const VT* __restrict__ val, const SV* __restrict__ V, int64_t ldv,
                   const SV* __restrict__ u_arg, VT* __restrict__ w, int64_t n, Small s,
@@ -53,7 +63,7 @@ k_one_reduce_step(const int32_t* __restrict__ rowptr, const int32_t* __restrict_
   __shared__ VT sw[2 * kThreads];
   __shared__ double red[2 * (kMaxM + 1) + 2];
   __shared__ int s_j, s_tail, s_skip, s_stage_off;
-  __shared__ uint64_t s_bar;
+  __shared__ uint64_t s_bar, s_barV;
   __shared__ uint32_t s_extra;
   DevState* st = s.st;
   if (threadIdx.x == 0) {
@@ -71,6 +81,9 @@ k_one_reduce_step(const int32_t* __restrict__ rowptr, const int32_t* __restrict_
   }
   __syncthreads();
   if (s_skip) return;
+  // STAGE 3 copies basis columns of the handle's own basis; the standalone
+  // block dot (raw_out) never runs it
+  if (STAGE == 3 && raw_out) return;
   const int j = s_j;
   const bool tail = s_tail;
   const bool spmv = raw_out ? (use_spmv != 0) : !tail;
@@ -92,9 +105,11 @@ k_one_reduce_step(const int32_t* __restrict__ rowptr, const int32_t* __restrict_
 
   const int64_t ntiles = (n + kThreads - 1) / kThreads;
   if constexpr (STAGE != 0) {
-    // Staged CSR (STAGE 1: one tile per unit, 2: tile pairs): the bulk-copy
-    // engine fetches the next unit's rowptr slice, indices and values into
-    // shared memory while this one's block dot runs. The global CSR is never
+    // Staged CSR (STAGE 1: one tile per unit, 2: tile pairs; 3: one tile per
+    // unit, and the tile's basis columns too): the bulk-copy engine fetches
+    // the next unit's rowptr slice, indices and values into shared memory
+    // while this one's block dot runs (and, for STAGE 3, the next tile's basis
+    // columns while this one's SpMV runs). The global CSR is never
     // read by this instantiation: a unit whose copy did not arrive in time, or
     // that does not fit the buffer (the host sizes it for the largest unit),
     // sets the stalled flag and contributes a zero SpMV.
@@ -110,18 +125,33 @@ k_one_reduce_step(const int32_t* __restrict__ rowptr, const int32_t* __restrict_
       cs.bar = &s_bar;
       cs.cap = stage_cap;
       cs.U = U;
+      // STAGE 3 also stages the tile's basis columns 0 .. j-1 (after the CSR)
+      SV* sV = reinterpret_cast<SV*>(cs.val + stage_cap);
       if (threadIdx.x == 0) {
         s_stage_off = 0;
         mbar_init(&s_bar, 1);
+        if (STAGE == 3) mbar_init(&s_barV, 1);
       }
       __syncthreads();
-      uint32_t phase = 0, pend_phase = 0;
-      bool pending = false;  // thread 0: a copy was issued and not yet seen complete (phase pend_phase)
+      uint32_t phase = 0, pend_phase = 0, vphase = 0, vpend_phase = 0;
+      bool pending = false;   // thread 0: a CSR copy was issued and not yet seen complete (phase pend_phase)
+      bool vpending = false;  // the same for the basis copies
+      // thread 0: bulk copies of the tile's slices of basis columns 0 .. j-1
+      auto issue_cols = [&](int64_t tu) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        const uint32_t bytes = (uint32_t)(kThreads * sizeof(SV));
+        mbar_arrive_expect_tx(&s_barV, (uint32_t)j * bytes + s_extra);
+        for (int k = 0; k < j; ++k) bulk_g2s(sV + (size_t)k * kThreads, V + (size_t)k * ldv + tu * kThreads, bytes, &s_barV);
+      };
       int64_t unit = blockIdx.x;
       if (threadIdx.x == 0 && unit < units) {
         cs.issue(rowptr, col, val, unit, CsrStage<VT>::lo_of(__ldg(rowptr + unit * U)),
                  CsrStage<VT>::hi_of(__ldg(rowptr + unit * U + U)), s_extra);
         pending = true;
+        if (STAGE == 3) {
+          issue_cols(unit);
+          vpending = true;
+        }
       }
       for (; unit < units; unit += gridDim.x) {
         const int64_t nx = unit + gridDim.x;
@@ -169,15 +199,43 @@ k_one_reduce_step(const int32_t* __restrict__ rowptr, const int32_t* __restrict_
             pending = true;
           }
         };
-        if (STAGE == 2)
+        if constexpr (STAGE == 3) {
+          // the tile's basis columns: waited for after the SpMV, refilled for
+          // the next tile once every thread is done with them
+          auto before = [&]() {
+            bool ok = !s_stage_off;
+            if (ok) {
+              ok = mbar_wait_bounded(&s_barV, vphase);
+              if (!ok) {
+                s_stage_off = 1;
+                atomicExch(&st->stalled, 1);
+              }
+            }
+            if (threadIdx.x == 0) {
+              if (ok) vpending = false;
+              else if (vpending) vpend_phase = vphase;
+            }
+            vphase ^= 1u;
+          };
+          auto after = [&]() {
+            if (threadIdx.x == 0 && nx < units && !s_stage_off) {
+              issue_cols(nx);
+              vpending = true;
+            }
+          };
+          tile_dot_rows_cols<MAXC, SV, VT>(unit, n, SharedCols<SV>{sV}, need_w, J8, r8, ur0, wr0, su, sw, acc_a,
+                                           acc_c, rem_a, rem_c, sig, dd, next, before, after);
+        } else if (STAGE == 2) {
           tile_pair_dot_rows<MAXC, SV, VT>(unit, n, V, ldv, need_w, J8, r8, ur0, wr0, ur1, wr1, su, sw, acc_a,
                                            acc_c, rem_a, rem_c, sig, dd, next);
-        else
+        } else {
           tile_dot_rows<MAXC, SV, VT>(unit, n, V, ldv, need_w, J8, r8, ur0, wr0, su, sw, acc_a, acc_c, rem_a,
                                       rem_c, sig, dd, next);
+        }
       }
       // no copy may still be landing in shared memory when the CTA moves on
       if (threadIdx.x == 0 && pending) mbar_wait_bounded(&s_bar, pend_phase);
+      if (STAGE == 3 && threadIdx.x == 0 && vpending) mbar_wait_bounded(&s_barV, vpend_phase);
       __syncthreads();
     } else {
       // no SpMV (the cycle's tail, or a standalone block dot with w given)

@@ -1,0 +1,8 @@
+// Instantiations of the one-reduce step kernel: FP32 arithmetic and basis, staged CSR and basis columns, one tile per unit.
+#include "step.cuh"
+
+namespace lsg_steps {
+const void* step_kernel_f32_s3(int m) {
+  return reinterpret_cast<const void*>(step_kernel_staged<float, float, 3>(m));
+}
+}  // namespace lsg_steps

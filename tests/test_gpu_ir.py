@@ -2,8 +2,11 @@
 the oracle's GMRES-IR and against its FP64 one-reduce GMRES.
 
 Tolerances: both IR solves stop at a true relative residual <= tol = 1e-10, so
-their solutions differ by at most ~kappa(A) * 2 tol (kappa of these test
-problems is below 1e3): 1e-8 relative. The cycle counts must agree exactly.
+their solutions differ by at most ~kappa(A) * 2 tol: 1e-8 relative for the
+small cases (kappa below 1e3), 1e-6 at 69^3 (kappa of the 27-point operator
+grows like (N+1)^2: 90, 273 and 397 at N = 12, 24 and 32 by Lanczos, so about
+1.7e3 at 69^3). The step and cycle counts must
+agree exactly below 1e5 rows, and within 1% (at least 3 steps) above.
 Residual estimates inside the first cycle are compared to 2e-2 relative: they
 come from FP32 arithmetic on both sides (the oracle's FP32 sums are sequential,
 with relative error up to n * 2^-24 ~ 1e-4 per sum at these sizes, amplified
@@ -20,7 +23,21 @@ CASES = {
     "aniso27_12cubed": (lambda: P.aniso_27pt(12), 40),
     "convdiff7_16cubed": (lambda: P.conv_diff_7pt(16), 30),
     "aniso27_24cubed": (lambda: P.aniso_27pt(24), 40),
+    # 328,509 rows (1,284 tiles, a ragged last one): large enough that the FP32
+    # step kernel stages the basis columns of each tile too (at least 4 tiles
+    # per CTA at two CTAs per SM)
+    "aniso27_69cubed": (lambda: P.aniso_27pt(69), 40),
 }
+
+_ORACLE = {}
+
+
+def _oracle(orc, name, cases, variant, A, b, m, tol, max_iter):
+    """The oracle's solve of a case (computed once per module run)."""
+    key = (name, variant)
+    if key not in _ORACLE:
+        _ORACLE[key] = orc.gmres(A, b, variant=variant, m=m, tol=tol, max_iter=max_iter)
+    return _ORACLE[key]
 
 
 @pytest.fixture(scope="module")
@@ -43,8 +60,8 @@ def test_ir_solve_matches_oracle(torch_cuda, orc, name, use_stream):
     xt, b = P.rhs(A, seed=0)
     n = len(b)
     tol = 1e-10
-    rir = orc.gmres(A, b, variant=2, m=m, tol=tol, max_iter=3000)
-    r64 = orc.gmres(A, b, variant=1, m=m, tol=tol, max_iter=3000)
+    rir = _oracle(orc, name, CASES, 2, A, b, m, tol, 3000)
+    r64 = _oracle(orc, name, CASES, 1, A, b, m, tol, 3000)
     s = lsgmres.Solver(A, m=m, tol=tol, prec="ir_fp32", max_iter=3000,
                        stream=torch.cuda.Stream() if use_stream else None)
     x = torch.zeros(n, dtype=torch.float64, device="cuda")
@@ -53,12 +70,23 @@ def test_ir_solve_matches_oracle(torch_cuda, orc, name, use_stream):
     h = s.history()
     xg = x.cpu().numpy()
     assert info.status == 0 and rir.status == 0
-    assert info.iters == rir.iters and info.restarts == rir.restarts
+    if n < 100_000:
+        assert info.iters == rir.iters and info.restarts == rir.restarts
+    else:
+        # FP32 sums of n ~ 3e5 terms: sequential (oracle) and tree (GPU) orders
+        # differ by up to ~n 2^-24 relative, which can move the step at which
+        # the last cycle's estimate crosses tol by a few steps
+        assert abs(info.iters - rir.iters) <= max(3, rir.iters // 100), (info.iters, rir.iters)
+        assert abs(info.restarts - rir.restarts) <= 1
     true = np.linalg.norm(b - P.to_scipy(A) @ xg) / np.linalg.norm(b)
     assert true <= tol
-    assert np.linalg.norm(xg - rir.x) <= 1e-8 * np.linalg.norm(rir.x)
-    assert np.linalg.norm(xg - r64.x) <= 1e-8 * np.linalg.norm(r64.x)
-    k = min(m, len(h))
+    xbar = 1e-8 if n < 100_000 else 1e-6
+    assert np.linalg.norm(xg - rir.x) <= xbar * np.linalg.norm(rir.x)
+    assert np.linalg.norm(xg - r64.x) <= xbar * np.linalg.norm(r64.x)
+    # the first cycle's estimates agree at FP32 level; above 1e5 rows the two
+    # FP32 Krylov processes drift apart later in the cycle (11% by step 40 at
+    # 69^3, with the same solution), so only its first 10 steps are compared
+    k = min(m, len(h), 10 if n >= 100_000 else m)
     assert np.all(np.abs(h[:k] - rir.history[:k]) <= 2e-2 * rir.history[:k])
 
 
@@ -93,6 +121,7 @@ BF16_CASES = {
     "aniso27_12cubed": (lambda: P.aniso_27pt(12), 40),
     "convdiff7_16cubed": (lambda: P.conv_diff_7pt(16), 30),
     "aniso27_23cubed": (lambda: P.aniso_27pt(23), 40),  # ragged: 12167 rows
+    "aniso27_69cubed": (lambda: P.aniso_27pt(69), 40),  # basis columns staged too (as above)
 }
 
 
@@ -116,8 +145,8 @@ def test_ir_bf16_solve(torch_cuda, orc, name, use_stream):
     _, b = P.rhs(A, seed=0)
     n = len(b)
     tol = 1e-10
-    r16 = orc.gmres(A, b, variant=5, m=m, tol=tol, max_iter=4000)
-    r64 = orc.gmres(A, b, variant=1, m=m, tol=tol, max_iter=4000)
+    r16 = _oracle(orc, "bf16:" + name, BF16_CASES, 5, A, b, m, tol, 4000)
+    r64 = _oracle(orc, "bf16:" + name, BF16_CASES, 1, A, b, m, tol, 4000)
     s = lsgmres.Solver(A, m=m, tol=tol, prec="ir_bf16", max_iter=4000,
                        stream=torch.cuda.Stream() if use_stream else None)
     x = torch.zeros(n, dtype=torch.float64, device="cuda")
@@ -128,7 +157,8 @@ def test_ir_bf16_solve(torch_cuda, orc, name, use_stream):
     assert info.status == 0 and r16.status == 0
     true = np.linalg.norm(b - P.to_scipy(A) @ xg) / np.linalg.norm(b)
     assert true <= tol
-    assert np.linalg.norm(xg - r16.x) <= 1e-8 * np.linalg.norm(r16.x)
-    assert np.linalg.norm(xg - r64.x) <= 1e-8 * np.linalg.norm(r64.x)
+    xbar = 1e-8 if n < 100_000 else 1e-6  # kappa * 2 tol, as in the FP32 test
+    assert np.linalg.norm(xg - r16.x) <= xbar * np.linalg.norm(r16.x)
+    assert np.linalg.norm(xg - r64.x) <= xbar * np.linalg.norm(r64.x)
     assert abs(info.iters - r16.iters) <= 0.25 * r16.iters, (info.iters, r16.iters)
     assert np.all(np.abs(h[:4] - r16.history[:4]) <= 1e-2 * r16.history[:4])
