@@ -1,9 +1,10 @@
-// Device code shared by the single-system solver (lsgmres.cu) and the batched
-// engine (batch.cu): constants, the per-system state, CSR rows, the fused
-// tile block dot, the deterministic grid reduction, and the small dense
-// epilogues of one-reduce MGS-GMRES (Algorithm 7 on Algorithm 4, Sections II-IV
-// of Swirydowicz et al., arXiv:1809.05805). Internal linkage: each translation
-// unit gets its own copy.
+// Device code shared by the single-system solver (lsgmres.cu, step.cuh) and the
+// batched engine (batch.cu, engine_step.cuh): constants, the per-system state,
+// CSR rows (from global memory, or staged in shared memory by bulk copies
+// with mbarrier completion), the fused tile block dot, the deterministic grid
+// reduction, and the small dense epilogues of one-reduce MGS-GMRES (Algorithm 7
+// on Algorithm 4, Sections II-IV of Swirydowicz et al., arXiv:1809.05805).
+// Internal linkage: each translation unit gets its own copy.
 #pragma once
 
 #include <cuda_bf16.h>

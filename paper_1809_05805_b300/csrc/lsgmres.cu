@@ -16,9 +16,15 @@
 //    so v_k = scale[k] * u_k is never written. Scales are folded into the
 //    coefficients of the dot products and of the MAXPY.
 //  * One grid-wide reduction per kernel: per-CTA partial sums go to global
-//    memory, an atomic ticket elects the last CTA, which sums the partials in
+//    memory, an atomic ticket elects the last CTA (of each group of 16 CTAs,
+//    then of the groups, when the sum is long), which sums the partials in
 //    CTA order (deterministic) and runs the small dense epilogue (lagged norm,
 //    Givens rotation, T row, T s, MAXPY coefficients) in shared memory.
+//  * The step kernel's CSR reaches the SpMV through shared memory: the
+//    bulk-copy engine brings each tile's rowptr slice, indices and values in
+//    while the previous tile is computed (mbarrier completion, bounded waits);
+//    FP32 cycles stage the tile's basis columns the same way. The instantiations
+//    of the step kernel live in step.cuh and the step_*.cu units.
 //  * Kernels read the step index and the stop flag from device state, so a
 //    cycle is a fixed launch sequence; once the epilogue marks the cycle done,
 //    the remaining kernels of the cycle return immediately.
