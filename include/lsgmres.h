@@ -59,7 +59,7 @@ typedef enum {
   GMRES_ERR_CUDA = -2,       /* a CUDA runtime call failed */
   GMRES_ERR_NONFINITE = -3,  /* NaN or Inf in b, x0 or a reduction */
   GMRES_ERR_OOM = -4,        /* device or pinned-host allocation failed */
-  GMRES_ERR_TIMEOUT = -5     /* reserved for bounded device-side waits */
+  GMRES_ERR_TIMEOUT = -5     /* a bounded device-side wait gave up, or a host wait timed out */
 } gmres_status;
 
 typedef enum { GMRES_MGS = 0, GMRES_ONE_REDUCE_MGS = 1, GMRES_CGS2_LVL2 = 2, GMRES_ONE_REDUCE_PIPE2 = 3 } gmres_ortho;
@@ -138,7 +138,10 @@ gmres_status gmres_set_stream(gmres_handle h, void* cuda_stream);
  * ||b - A x|| / ||b|| <= tol (GMRES_OK) or after max_iter steps
  * (GMRES_MAXITER). b = 0 gives x = 0. info may be NULL. Synchronizes the stream.
  * Errors: GMRES_ERR_ARG (NULL or misaligned pointer: b and x must be 8-byte
- * aligned), GMRES_ERR_NONFINITE, GMRES_ERR_CUDA. */
+ * aligned), GMRES_ERR_NONFINITE, GMRES_ERR_CUDA, GMRES_ERR_TIMEOUT (a bounded
+ * wait of the step kernel for the bulk copies that stage its CSR and basis
+ * tiles in shared memory gave up after about a second; see
+ * gmres_test_stall_staging). */
 gmres_status gmres_solve(gmres_handle h, const double* b, double* x, gmres_info* info);
 
 /* As gmres_solve with b and x in host memory: copies b and x0 to the device,

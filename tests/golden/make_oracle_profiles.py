@@ -1,4 +1,4 @@
-"""Write tests/golden/oracle_profile_<name>.txt by running the FP64 oracle (only).
+"""Write tests/golden/oracle_profile_<name>.txt by running the oracle (only).
 
 For each benchmark workload the file records the oracle's iteration count,
 restart count, reduction count, final true residual and its per-step residual
@@ -6,8 +6,8 @@ history. The GPU solve of the same seeded inputs is compared against these
 files, and bench.py's reference arm scales its bounded oracle sample by the
 recorded step profile. Nothing here touches the CUDA library.
 
-Usage:  python tests/golden/make_oracle_profiles.py [c1] [c2_one_reduce] [c2_mgs]
-(c2 runs the full 256^3 solve single-threaded: tens of minutes.)
+Usage:  python tests/golden/make_oracle_profiles.py [c1] [c2_one_reduce] [c2_mgs] [c3_ir]
+(c2 and c3 run the full 256^3 / 192^3 solves single-threaded: tens of minutes.)
 """
 import os
 import sys
@@ -27,22 +27,26 @@ WORKLOADS = {
     "c1_mgs": dict(N=32, m=30, tol=1e-8, max_iter=300, variant=oracle.MGS),
     "c2_one_reduce": dict(N=256, m=50, tol=1e-8, max_iter=3000, variant=oracle.ONE_REDUCE),
     "c2_mgs": dict(N=256, m=50, tol=1e-8, max_iter=3000, variant=oracle.MGS),
+    # GMRES-IR (FP32 cycles inside FP64 restarts) on the 192^3 27-point problem
+    "c3_ir": dict(N=192, m=40, tol=1e-10, max_iter=5000, variant=2, stencil="27pt"),
 }
+VARIANT_NAMES = {0: "mgs", 1: "one_reduce", 2: "ir_fp32"}
 
 
 def run(name):
     w = WORKLOADS[name]
-    A = P.conv_diff_7pt(w["N"])
+    A = P.aniso_27pt(w["N"]) if w.get("stencil") == "27pt" else P.conv_diff_7pt(w["N"])
     _, b = P.rhs(A, seed=0)
     t0 = time.time()
     r = oracle.get().gmres(A, b, variant=w["variant"], m=w["m"], tol=w["tol"], max_iter=w["max_iter"])
     dt = time.time() - t0
     path = os.path.join(HERE, f"oracle_profile_{name}.txt")
     with open(path, "w") as f:
-        f.write(f"# written by tests/golden/make_oracle_profiles.py from the FP64 oracle only\n")
-        f.write(f"# workload: 7-point convection-diffusion N={w['N']} (n={w['N'] ** 3}), x_true ~ U[-1,1] "
+        f.write(f"# written by tests/golden/make_oracle_profiles.py from the oracle only\n")
+        stencil = "27-point anisotropic diffusion" if w.get("stencil") == "27pt" else "7-point convection-diffusion"
+        f.write(f"# workload: {stencil} N={w['N']} (n={w['N'] ** 3}), x_true ~ U[-1,1] "
                 f"PCG64(0), b = A x_true, x0 = 0, GMRES(m={w['m']}), tol={w['tol']}, "
-                f"variant={'one_reduce' if w['variant'] else 'mgs'}\n")
+                f"variant={VARIANT_NAMES[w['variant']]}\n")
         f.write(f"# oracle wall time {dt:.1f} s (1 thread)\n")
         f.write(f"status {r.status}\niters {r.iters}\nrestarts {r.restarts}\nreductions {r.reductions}\n")
         f.write(f"rel_resid_true {r.rel_resid_true!r}\n")
