@@ -43,6 +43,7 @@
 #include <mutex>
 #include <string>
 #include <thread>
+#include <utility>
 #include <vector>
 
 #include "lsgmres.h"
@@ -309,6 +310,25 @@ EngStepKernel<float> eng_step_for<float>(int m, bool pairs) {
 // ==========================================================================
 // host side
 // ==========================================================================
+
+// Raise (never lower) a kernel's dynamic shared-memory limit. The attribute
+// belongs to the function and the device, process-wide, and handles of
+// different shapes launch the same kernels with different amounts: lowering it
+// for one handle would make another's launches fail.
+cudaError_t raise_smem_limit(const void* f, size_t bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, size_t> cur;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(mu);
+  size_t& c = cur[{dev, f}];
+  if (bytes <= c) return cudaSuccess;
+  e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) c = bytes;
+  return e;
+}
+
 
 // First-fit allocator of unit ranges [0, cap) (free ranges kept merged).
 class RangeAlloc {
@@ -579,7 +599,7 @@ struct Engine {
           const void* f = ir() ? reinterpret_cast<const void*>(eng_step_for<float>(m, pr))
                                : reinterpret_cast<const void*>(eng_step_for<double>(m, pr));
           int nb = 0;
-          if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need) != cudaSuccess ||
+          if (raise_smem_limit(f, need) != cudaSuccess ||
               cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, kThreads, need) != cudaSuccess || nb < per_sm)
             ok = false;
         }
@@ -591,8 +611,7 @@ struct Engine {
       (void)cudaGetLastError();  // sizes above the per-block limit were refused; that is not an error here
       if (stage_cap == 0) return fail(GMRES_ERR_CUDA, "no shared-memory size keeps the step kernel resident");
     }
-    ETRY(cudaFuncSetAttribute(reinterpret_cast<const void*>(ke_lsq), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)lsq_smem));
+    ETRY(raise_smem_limit(reinterpret_cast<const void*>(ke_lsq), lsq_smem));
     P = (ir() ? 3 : 2) * nsm;  // resident CTAs per SM of the step kernel
     pairs = true;
     return GMRES_OK;

@@ -36,9 +36,11 @@
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
 #include <type_traits>
+#include <utility>
 #include <vector>
 
 #include "lsgmres.h"
@@ -536,6 +538,27 @@ StepKernel<float, __nv_bfloat16> step16_for(int m, int stage = 0) {
 // ==========================================================================
 // host side
 // ==========================================================================
+namespace {
+// Raise (never lower) a kernel's dynamic shared-memory limit. The attribute
+// belongs to the function and the device, process-wide, and handles of
+// different shapes launch the same kernels with different amounts: lowering it
+// for one handle would make another's launches fail.
+cudaError_t raise_smem_limit(const void* f, size_t bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, size_t> cur;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(mu);
+  size_t& c = cur[{dev, f}];
+  if (bytes <= c) return cudaSuccess;
+  e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) c = bytes;
+  return e;
+}
+
+}  // namespace
+
 struct gmres_ctx {
   int64_t n = 0, nnz = 0;
   int m = 0;
@@ -1021,7 +1044,7 @@ static gmres_status choose_stage(KernelFor kernel_for, size_t vb, int per_sm, in
         std::max(t_smem, (size_t)(U + 4) * 4 + (size_t)c * (4 + vb) + (cand == 3 ? v3_bytes : 0));
     if (need > 200 * 1024) continue;
     const void* k = reinterpret_cast<const void*>(kernel_for(cand));
-    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need) != cudaSuccess)
+    if (raise_smem_limit(k, need) != cudaSuccess)
       return GMRES_ERR_CUDA;
     int nb = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, kThreads, need) != cudaSuccess) return GMRES_ERR_CUDA;
@@ -1036,8 +1059,7 @@ static gmres_status choose_stage(KernelFor kernel_for, size_t vb, int per_sm, in
   mode = 0;
   cap = 0;
   smem = t_smem;
-  if (cudaFuncSetAttribute(reinterpret_cast<const void*>(kernel_for(0)), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)t_smem) != cudaSuccess)
+  if (raise_smem_limit(reinterpret_cast<const void*>(kernel_for(0)), t_smem) != cudaSuccess)
     return GMRES_ERR_CUDA;
   return GMRES_OK;
 }
@@ -1152,8 +1174,7 @@ gmres_status gmres_create(const gmres_csr* A, int m_restart, double tol, gmres_h
     h->step32 = step32_for(m, h->stage32);
     h->step16 = step16_for(m, h->stage16);
   }
-  CREATE_TRY(cudaFuncSetAttribute(reinterpret_cast<const void*>(k_lsq),
-                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)h->lsq_smem));
+  CREATE_TRY(raise_smem_limit(reinterpret_cast<const void*>(k_lsq), h->lsq_smem));
 #undef CREATE_TRY
   *out = h;
   return GMRES_OK;

@@ -224,12 +224,15 @@ def test_zero_and_nonfinite_rhs(torch_cuda, lsg):
     assert e.value.status == lsg.ERR_NONFINITE
 
 
-def test_deterministic(torch_cuda, lsg):
-    """Fixed-order reductions: two solves give bitwise identical x and history."""
+@pytest.mark.parametrize("N,m,prec", [(20, 20, "fp64"), (32, 30, "fp64"), (69, 40, "ir_fp32")])
+def test_deterministic(torch_cuda, lsg, N, m, prec):
+    """Fixed-order reductions: two solves give bitwise identical x and history
+    (20^3: one-level grid sums; 32^3: two-level; 69^3 GMRES-IR: CSR and basis
+    tiles staged in shared memory)."""
     torch = torch_cuda
-    A = P.conv_diff_7pt(20)
+    A = P.conv_diff_7pt(N)
     _, b = P.rhs(A, 5)
-    s = lsg.Solver(A, m=20, tol=1e-9)
+    s = lsg.Solver(A, m=m, tol=1e-9, prec=prec, max_iter=3000)
     bd = dev(torch, b)
     outs = []
     for _ in range(2):

@@ -98,3 +98,27 @@ def test_staging_wait_runs_out_and_reports_timeout(torch_cuda, lsg, graph):
     info = s.solve(bd, x)
     assert info.status == 0
     assert np.linalg.norm(b - P.to_scipy(A) @ x.cpu().numpy()) <= 1e-8 * np.linalg.norm(b)
+
+
+def test_handles_of_different_shapes_interleave(torch_cuda, lsg):
+    """Kernels are shared by all handles and their shared-memory limit is a
+    process-wide attribute: a handle whose step kernel stages a large tile
+    (27-point GMRES-IR at 69^3, basis columns staged too) must still solve
+    after handles with smaller tiles (and a smaller restart length) were made."""
+    torch = torch_cuda
+    big = P.aniso_27pt(69)
+    _, bb = P.rhs(big, seed=3)
+    s1 = lsg.Solver(big, m=40, tol=1e-8, prec="ir_fp32", max_iter=2000)
+    # the same step kernel (restart 40, basis staged) with a 7-point tile: less shared memory
+    seven = P.conv_diff_7pt(69)
+    _, b7 = P.rhs(seven, seed=4)
+    s2 = lsg.Solver(seven, m=40, tol=1e-8, prec="ir_fp32", max_iter=2000)
+    # a shorter restart: the least-squares kernel needs less shared memory
+    small = P.conv_diff_7pt(12)
+    _, bs = P.rhs(small, seed=5)
+    s3 = lsg.Solver(small, m=10, tol=1e-8, max_iter=2000)
+    for s, A, b in ((s2, seven, b7), (s3, small, bs), (s1, big, bb), (s2, seven, b7), (s1, big, bb)):
+        x = torch.zeros(len(b), dtype=torch.float64, device="cuda")
+        info = s.solve(torch.from_numpy(b).cuda(), x)
+        assert info.status == 0
+        assert np.linalg.norm(b - P.to_scipy(A) @ x.cpu().numpy()) <= 1e-8 * np.linalg.norm(b)
