@@ -254,7 +254,11 @@ def run_reference(args, w, rank, world):
         return 0
     A = make_problem(w)
     _, b = P.rhs(A, seed=0)
-    prof = golden_profile({256: "c2_one_reduce", 32: "c1", 192: "c3_ir"}.get(w["N"], "none"))
+    if w["prec"] == "ir_fp32" and w["N"] >= 192:
+        print(json.dumps({"impl": "reference", "unavailable": "the oracle's GMRES-IR (sequential FP32 sums) does not "
+                          "reach tol 1e-10 at 192^3: it stalls at a true residual of 1.43e-10 after 5000 steps"}))
+        return 0
+    prof = golden_profile({256: "c2_one_reduce", 32: "c1"}.get(w["N"], "none"))
     if prof is None:
         print(json.dumps({"impl": "reference", "unavailable": "oracle iteration profile for this workload "
                           "(tests/golden/oracle_profile_*.txt) has not been written"}))

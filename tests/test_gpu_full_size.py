@@ -63,35 +63,24 @@ def test_256cubed_solve_matches_oracle_run():
         assert np.all(np.abs(xs[idx] - g["x_sample"]) <= 1e-9)
 
 
-GOLDEN_IR = os.path.join(os.path.dirname(__file__), "golden", "oracle_profile_c3_ir.txt")
-
-
-@pytest.mark.skipif(not os.path.exists(GOLDEN_IR), reason="the oracle's 192^3 GMRES-IR run has not been written")
-def test_192cubed_ir_solve_matches_oracle_run():
+def test_192cubed_ir_solve_properties():
     """The 192^3 27-point GMRES-IR benchmark solve (FP32 cycles, the bench's launch
-    configuration: a non-default stream, staging mode 3) against the oracle's
-    complete GMRES-IR run of the same system (tests/golden/oracle_profile_c3_ir.txt).
-    Both cycles run in FP32, whose sums over n = 7.1e6 terms differ between the
-    oracle's sequential order and the GPU's trees by up to ~n 2^-24 relative, so
-    the step count may differ by a few steps (1%), the first cycle's estimates
-    agree to FP32 level over its first steps (2e-2), and the solutions agree to
-    the conditioning bound of two solves stopped at tol = 1e-10: kappa ~ 0.36
-    (N+1)^2 ~ 1.3e4 (the growth measured by Lanczos up to N = 32), so x within
-    3e-6 of max |x| per sampled entry."""
+    configuration: a non-default stream, staging mode 3), checked through
+    properties that hold at any size (the oracle's own GMRES-IR, with its
+    sequential FP32 sums over 7.1e6 terms, stagnates at a true residual of
+    1.43e-10 after 5,000 steps and 125 restarts at this size, so it cannot
+    serve as the reference here): the solve converges to a true residual
+    <= 1e-10; its solution agrees with the FP64 one-reduce solve of the same
+    handle to the conditioning bound of two solves stopped at tol, kappa * 2 tol
+    with kappa ~ 0.36 (N+1)^2 ~ 1.3e4 (the growth measured by Lanczos up to
+    N = 32): 3e-6 relative; and the first residual estimates of the FP32 cycle
+    agree with the FP64 cycle's to FP32 level (2e-2 over the first 10 steps)."""
     import torch
 
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     from paper_1809_05805_b300 import lsgmres
 
-    g = {}
-    with open(GOLDEN_IR) as f:
-        for line in f:
-            if line.startswith("#") or not line.strip():
-                continue
-            k, v = line.split(" ", 1)
-            g[k] = np.array([float(t) for t in v.split()]) if k in ("history", "x_sample_idx", "x_sample") \
-                else float(v)
     A = P.aniso_27pt(192)
     _, b = P.rhs(A, seed=0)
     n = len(b)
@@ -101,14 +90,17 @@ def test_192cubed_ir_solve_matches_oracle_run():
     x = torch.zeros(n, dtype=torch.float64, device="cuda")
     torch.cuda.synchronize()
     info = s.solve(bd, x)
-    hist = s.history()
-    assert info.status == 0 and g["status"] == 0
-    assert abs(info.iters - int(g["iters"])) <= max(3, int(g["iters"]) // 100), (info.iters, g["iters"])
-    assert abs(info.restarts - int(g["restarts"])) <= 1
-    h = g["history"]
-    assert np.all(np.abs(hist[:10] - h[:10]) <= 2e-2 * h[:10])
-    xs = x.cpu().numpy()
-    true = np.linalg.norm(b - P.to_scipy(A) @ xs) / np.linalg.norm(b)
-    assert true <= 1e-10
-    idx = g["x_sample_idx"].astype(np.int64)
-    assert np.all(np.abs(xs[idx] - g["x_sample"]) <= 3e-6 * np.abs(xs).max())
+    h_ir = s.history()
+    x_ir = x.cpu().numpy()
+    s.set(ortho="one_reduce_mgs", prec="fp64", max_iter=5000)
+    x.zero_()
+    info64 = s.solve(bd, x)
+    h_64 = s.history()
+    x_64 = x.cpu().numpy()
+    S = P.to_scipy(A)
+    nb = np.linalg.norm(b)
+    assert info.status == 0 and info64.status == 0
+    assert np.linalg.norm(b - S @ x_ir) / nb <= 1e-10
+    assert np.linalg.norm(b - S @ x_64) / nb <= 1e-10
+    assert np.linalg.norm(x_ir - x_64) <= 3e-6 * np.linalg.norm(x_64)
+    assert np.all(np.abs(h_ir[:10] - h_64[:10]) <= 2e-2 * h_64[:10])
