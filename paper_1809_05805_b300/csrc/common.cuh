@@ -648,14 +648,14 @@ __device__ __forceinline__ void tile_dot_rows(int64_t t, int64_t n, const SV* __
 }
 
 // The block-dot half of the tile pair pp (rows 512 pp .. 512 pp + 511, two
-// per thread: row0 = 512 pp + tid and row1 = row0 + 256), as tile_dot_rows.
-// su, sw hold 512 values.
-template <int MAXC, typename SV, typename VT, typename Hook>
-__device__ __forceinline__ void tile_pair_dot_rows(int64_t pp, int64_t n, const SV* __restrict__ V, int64_t ldv,
-                                                   bool need_w, int J8, int r8, VT ur0, VT wr0, VT ur1, VT wr1,
-                                                   VT* su, VT* sw, VT (&acc_a)[MAXC], VT (&acc_c)[MAXC],
-                                                   VT (&rem_a)[kWarps - 1], VT (&rem_c)[kWarps - 1], VT& sig,
-                                                   VT& dd, Hook hook) {
+// per thread: row0 = 512 pp + tid and row1 = row0 + 256), as tile_dot_rows_cols;
+// cols.ld(k, i) reads row 512 pp + i of column k. su, sw hold 512 values.
+template <int MAXC, typename SV, typename VT, typename Cols, typename Hook, typename After>
+__device__ __forceinline__ void tile_pair_dot_rows_cols(int64_t pp, int64_t n, Cols cols, bool need_w, int J8,
+                                                        int r8, VT ur0, VT wr0, VT ur1, VT wr1, VT* su, VT* sw,
+                                                        VT (&acc_a)[MAXC], VT (&acc_c)[MAXC],
+                                                        VT (&rem_a)[kWarps - 1], VT (&rem_c)[kWarps - 1], VT& sig,
+                                                        VT& dd, Hook hook, After after) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int64_t row0 = pp * (2 * kThreads) + threadIdx.x, row1 = row0 + kThreads;
   sig = fma(ur0, ur0, sig);
@@ -681,10 +681,10 @@ __device__ __forceinline__ void tile_pair_dot_rows(int64_t pp, int64_t n, const 
     for (int c = 0; c < MAXC; ++c) {
       if (c < J8) {  // warp-uniform
         const int k = wid + c * kWarps;
-        const SV* vk = V + (size_t)k * ldv + base;
         VT x[kRowsPerLane];
 #pragma unroll
-        for (int q = 0; q < kRowsPerLane; ++q) x[q] = (base + 32 * q < n) ? ld_as<VT>(vk + 32 * q) : VT(0);
+        for (int q = 0; q < kRowsPerLane; ++q)
+          x[q] = (base + 32 * q < n) ? cols.template ld<VT>(k, h * kThreads + lane + 32 * q) : VT(0);
 #pragma unroll
         for (int q = 0; q < kRowsPerLane; ++q) acc_a[c] = fma(x[q], ru[q], acc_a[c]);
         if (need_w) {  // the cycle's tail needs only V^T u
@@ -702,9 +702,8 @@ __device__ __forceinline__ void tile_pair_dot_rows(int64_t pp, int64_t n, const 
 #pragma unroll
       for (int b = 0; b < kRemBatch; ++b) {
         const int c = c0 + b;
-        const SV* vk = V + (size_t)(J8 * kWarps + c) * ldv;
-        x0[b] = (c < r8 && row0 < n) ? ld_as<VT>(vk + row0) : VT(0);
-        x1[b] = (c < r8 && row1 < n) ? ld_as<VT>(vk + row1) : VT(0);
+        x0[b] = (c < r8 && row0 < n) ? cols.template ld<VT>(J8 * kWarps + c, (int)threadIdx.x) : VT(0);
+        x1[b] = (c < r8 && row1 < n) ? cols.template ld<VT>(J8 * kWarps + c, kThreads + (int)threadIdx.x) : VT(0);
       }
 #pragma unroll
       for (int b = 0; b < kRemBatch; ++b) {
@@ -721,6 +720,18 @@ __device__ __forceinline__ void tile_pair_dot_rows(int64_t pp, int64_t n, const 
     }
   }
   __syncthreads();
+  after();
+}
+
+// The tile pair with the basis read from global memory.
+template <int MAXC, typename SV, typename VT, typename Hook>
+__device__ __forceinline__ void tile_pair_dot_rows(int64_t pp, int64_t n, const SV* __restrict__ V, int64_t ldv,
+                                                   bool need_w, int J8, int r8, VT ur0, VT wr0, VT ur1, VT wr1,
+                                                   VT* su, VT* sw, VT (&acc_a)[MAXC], VT (&acc_c)[MAXC],
+                                                   VT (&rem_a)[kWarps - 1], VT (&rem_c)[kWarps - 1], VT& sig,
+                                                   VT& dd, Hook hook) {
+  tile_pair_dot_rows_cols<MAXC, SV, VT>(pp, n, GlobalCols<SV>{V, ldv, pp * (2 * kThreads)}, need_w, J8, r8, ur0,
+                                        wr0, ur1, wr1, su, sw, acc_a, acc_c, rem_a, rem_c, sig, dd, hook, NoHook{});
 }
 
 // One 256-row tile t of the fused SpMV + block dot (one row per thread in the
