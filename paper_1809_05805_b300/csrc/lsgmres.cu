@@ -23,7 +23,7 @@
 //  * The step kernel's CSR reaches the SpMV through shared memory: the
 //    bulk-copy engine brings each tile's rowptr slice, indices and values in
 //    while the previous tile is computed (mbarrier completion, bounded waits);
-//    FP32 cycles stage the tile's basis columns the same way. The instantiations
+//    cycles with a BF16 basis stage the tile's basis columns the same way. The instantiations
 //    of the step kernel live in step.cuh and the step_*.cu units.
 //  * Kernels read the step index and the stop flag from device state, so a
 //    cycle is a fixed launch sequence; once the epilogue marks the cycle done,
@@ -569,8 +569,8 @@ struct gmres_ctx {
   int device = 0;
   int nsm = 0;
   int P = 0;          // CTAs of reduction kernels
-  int P32 = 0;        // CTAs of the FP32-cycle step kernel (3 resident per SM; 2 in staging mode 3)
-  int P16 = 0;        // the same for the BF16-basis step kernel
+  int P32 = 0;        // CTAs of the FP32-cycle step kernel (3 resident per SM)
+  int P16 = 0;        // CTAs of the BF16-basis step kernel (3 per SM; 2 in staging mode 3)
   int grid_stream = 0;// CTAs of streaming kernels
   int32_t* rowptr = nullptr;
   int32_t* col = nullptr;
@@ -1024,8 +1024,8 @@ static void csr_stage_caps(const std::vector<int32_t>& rp, int64_t n, int& cap_t
 // Staging of a step kernel with values of vb bytes, launched on P CTAs of
 // which `per_sm` must stay resident per SM: tile pairs when the unstaged kernel
 // would take pairs (ntiles >= 4 P) and their buffer fits, else single tiles if
-// theirs fits, else off. With v3_bytes > 0 (the basis columns of a tile, FP32
-// cycles), mode 3 (single tiles with their basis columns staged too, two CTAs
+// theirs fits, else off. With v3_bytes > 0 (the basis columns of a tile, BF16
+// basis), mode 3 (single tiles with their basis columns staged too, two CTAs
 // per SM) is tried first; *P is then lowered to two CTAs per SM. kernel_for(stage)
 // gives the kernel of a mode; the dynamic shared memory is the larger of the
 // epilogue's (t_smem) and the staging buffer's. Sets the kernel's
@@ -1159,9 +1159,11 @@ gmres_status gmres_create(const gmres_csr* A, int m_restart, double tol, gmres_h
     gmres_status sst = choose_stage([m](int sg) { return step64_for(m, sg); }, sizeof(double), 2, &h->P, h->nsm,
                                     ntiles, cap_tile, cap_pair, h->step_smem, 0, h->stage64, h->cap64, h->smem64);
     if (sst == GMRES_OK)
+      // FP32 basis: no mode 3 (measured: equal at 192^3 27-point, 16% slower at 256^3
+      // 7-point than three CTAs per SM reading the basis themselves); the BF16
+      // basis, whose 2-byte loads use sectors poorly, gains from it (31% at 192^3)
       sst = choose_stage([m](int sg) { return step32_for(m, sg); }, sizeof(float), 3, &h->P32, h->nsm, ntiles,
-                         cap_tile, cap_pair, h->step_smem, (size_t)m * kThreads * sizeof(float), h->stage32,
-                         h->cap32, h->smem32);
+                         cap_tile, cap_pair, h->step_smem, 0, h->stage32, h->cap32, h->smem32);
     if (sst == GMRES_OK)
       sst = choose_stage([m](int sg) { return step16_for(m, sg); }, sizeof(float), 3, &h->P16, h->nsm, ntiles,
                          cap_tile, cap_pair, h->step_smem, (size_t)m * kThreads * sizeof(__nv_bfloat16),

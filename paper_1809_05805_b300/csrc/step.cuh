@@ -10,8 +10,8 @@
 
 namespace lsg_steps {
 // Host stub of the step kernel for restart length m and staging mode (0 off,
-// 1 tiles, 2 tile pairs, 3 tiles with their basis columns); callers cast it
-// to their StepKernel type.
+// 1 tiles, 2 tile pairs, 3 tiles with their basis columns, BF16 basis only);
+// callers cast it to their StepKernel type.
 const void* step_kernel_f64_s0(int m);
 const void* step_kernel_f64_s1(int m);
 const void* step_kernel_f64_s2(int m);
@@ -21,17 +21,15 @@ const void* step_kernel_f32_s2(int m);
 const void* step_kernel_bf16_s0(int m);
 const void* step_kernel_bf16_s1(int m);
 const void* step_kernel_bf16_s2(int m);
-const void* step_kernel_f32_s3(int m);
 const void* step_kernel_bf16_s3(int m);
-// FP64 has no mode 3 (its basis tile does not fit beside two resident CTAs).
+// Mode 3 is built for the BF16 basis only: the FP64 basis tile does not fit
+// beside two resident CTAs, and FP32 cycles ran faster at three CTAs per SM
+// reading the basis themselves than at two with it staged.
 inline const void* step_kernel_f64(int m, int stage) {
   return stage == 2 ? step_kernel_f64_s2(m) : stage == 1 ? step_kernel_f64_s1(m) : step_kernel_f64_s0(m);
 }
 inline const void* step_kernel_f32(int m, int stage) {
-  return stage == 3   ? step_kernel_f32_s3(m)
-         : stage == 2 ? step_kernel_f32_s2(m)
-         : stage == 1 ? step_kernel_f32_s1(m)
-                      : step_kernel_f32_s0(m);
+  return stage == 2 ? step_kernel_f32_s2(m) : stage == 1 ? step_kernel_f32_s1(m) : step_kernel_f32_s0(m);
 }
 inline const void* step_kernel_bf16(int m, int stage) {
   return stage == 3   ? step_kernel_bf16_s3(m)

@@ -65,7 +65,7 @@ def test_256cubed_solve_matches_oracle_run():
 
 def test_192cubed_ir_solve_properties():
     """The 192^3 27-point GMRES-IR benchmark solve (FP32 cycles, the bench's launch
-    configuration: a non-default stream, staging mode 3), checked through
+    configuration: a non-default stream, staged CSR), checked through
     properties that hold at any size (the oracle's own GMRES-IR, with its
     sequential FP32 sums over 7.1e6 terms, stagnates at a true residual of
     1.43e-10 after 5,000 steps and 125 restarts at this size, so it cannot

@@ -23,9 +23,9 @@ CASES = {
     "aniso27_12cubed": (lambda: P.aniso_27pt(12), 40),
     "convdiff7_16cubed": (lambda: P.conv_diff_7pt(16), 30),
     "aniso27_24cubed": (lambda: P.aniso_27pt(24), 40),
-    # 328,509 rows (1,284 tiles, a ragged last one): large enough that the FP32
-    # step kernel stages the basis columns of each tile too (at least 4 tiles
-    # per CTA at two CTAs per SM)
+    # 328,509 rows (1,284 tiles, a ragged last one): large enough that the
+    # BF16-basis step kernel (below) stages the basis columns of each tile too
+    # (at least 4 tiles per CTA at two CTAs per SM); the FP32 step stages the CSR
     "aniso27_69cubed": (lambda: P.aniso_27pt(69), 40),
 }
 

@@ -224,11 +224,11 @@ def test_zero_and_nonfinite_rhs(torch_cuda, lsg):
     assert e.value.status == lsg.ERR_NONFINITE
 
 
-@pytest.mark.parametrize("N,m,prec", [(20, 20, "fp64"), (32, 30, "fp64"), (69, 40, "ir_fp32")])
+@pytest.mark.parametrize("N,m,prec", [(20, 20, "fp64"), (32, 30, "fp64"), (69, 40, "ir_fp32"), (69, 40, "ir_bf16")])
 def test_deterministic(torch_cuda, lsg, N, m, prec):
     """Fixed-order reductions: two solves give bitwise identical x and history
-    (20^3: one-level grid sums; 32^3: two-level; 69^3 GMRES-IR: CSR and basis
-    tiles staged in shared memory)."""
+    (20^3: one-level grid sums; 32^3: two-level; 69^3 GMRES-IR: CSR tiles
+    staged in shared memory, and with a BF16 basis its basis tiles too)."""
     torch = torch_cuda
     A = P.conv_diff_7pt(N)
     _, b = P.rhs(A, 5)

@@ -103,13 +103,13 @@ def test_staging_wait_runs_out_and_reports_timeout(torch_cuda, lsg, graph):
 def test_handles_of_different_shapes_interleave(torch_cuda, lsg):
     """Kernels are shared by all handles and their shared-memory limit is a
     process-wide attribute: a handle whose step kernel stages a large tile
-    (27-point GMRES-IR at 69^3, basis columns staged too) must still solve
+    (27-point GMRES-IR at 69^3, the largest staged CSR tile) must still solve
     after handles with smaller tiles (and a smaller restart length) were made."""
     torch = torch_cuda
     big = P.aniso_27pt(69)
     _, bb = P.rhs(big, seed=3)
     s1 = lsg.Solver(big, m=40, tol=1e-8, prec="ir_fp32", max_iter=2000)
-    # the same step kernel (restart 40, basis staged) with a 7-point tile: less shared memory
+    # the same step kernel (restart 40, staged single tiles) with a 7-point tile: less shared memory
     seven = P.conv_diff_7pt(69)
     _, b7 = P.rhs(seven, seed=4)
     s2 = lsg.Solver(seven, m=40, tol=1e-8, prec="ir_fp32", max_iter=2000)
