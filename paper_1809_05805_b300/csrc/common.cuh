@@ -536,8 +536,8 @@ __device__ int finish_completed(Small s, int c, double h, bool tail) {
 // (use_spmv == 0), and the totals go to raw_out without the GMRES epilogue.
 // Where the block dot of a 256-row tile t reads basis column k: GlobalCols
 // reads the basis in global memory (row 256 t of column k at V + k ldv + r0);
-// SharedCols a copy of the tile's columns in shared memory (column k at
-// s + 256 k).
+// SharedCols a copy of the unit's columns in shared memory (column k at
+// s + ld_s k).
 // ld(k, i) reads entry i of the tile's slice of column k (global memory goes
 // through the read-only path, which takes global addresses only; shared
 // memory through plain loads).
@@ -554,12 +554,13 @@ struct GlobalCols {
 template <typename SV>
 struct SharedCols {
   const SV* s;
+  int ld_s;  // values per staged column slice (the unit's rows)
   template <typename VT>
   __device__ VT ld(int k, int i) const {
     if constexpr (std::is_same<SV, __nv_bfloat16>::value)
-      return __bfloat162float(s[(size_t)k * kThreads + i]);
+      return __bfloat162float(s[(size_t)k * ld_s + i]);
     else
-      return (VT)s[(size_t)k * kThreads + i];
+      return (VT)s[(size_t)k * ld_s + i];
   }
 };
 
@@ -650,12 +651,12 @@ __device__ __forceinline__ void tile_dot_rows(int64_t t, int64_t n, const SV* __
 // The block-dot half of the tile pair pp (rows 512 pp .. 512 pp + 511, two
 // per thread: row0 = 512 pp + tid and row1 = row0 + 256), as tile_dot_rows_cols;
 // cols.ld(k, i) reads row 512 pp + i of column k. su, sw hold 512 values.
-template <int MAXC, typename SV, typename VT, typename Cols, typename Hook, typename After>
+template <int MAXC, typename SV, typename VT, typename Cols, typename Hook, typename Before, typename After>
 __device__ __forceinline__ void tile_pair_dot_rows_cols(int64_t pp, int64_t n, Cols cols, bool need_w, int J8,
                                                         int r8, VT ur0, VT wr0, VT ur1, VT wr1, VT* su, VT* sw,
                                                         VT (&acc_a)[MAXC], VT (&acc_c)[MAXC],
                                                         VT (&rem_a)[kWarps - 1], VT (&rem_c)[kWarps - 1], VT& sig,
-                                                        VT& dd, Hook hook, After after) {
+                                                        VT& dd, Hook hook, Before before, After after) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int64_t row0 = pp * (2 * kThreads) + threadIdx.x, row1 = row0 + kThreads;
   sig = fma(ur0, ur0, sig);
@@ -668,6 +669,7 @@ __device__ __forceinline__ void tile_pair_dot_rows_cols(int64_t pp, int64_t n, C
   sw[kThreads + threadIdx.x] = wr1;
   __syncthreads();
   hook();
+  before();
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
     const int64_t base = pp * (2 * kThreads) + h * kThreads + lane;
@@ -731,7 +733,8 @@ __device__ __forceinline__ void tile_pair_dot_rows(int64_t pp, int64_t n, const 
                                                    VT (&rem_a)[kWarps - 1], VT (&rem_c)[kWarps - 1], VT& sig,
                                                    VT& dd, Hook hook) {
   tile_pair_dot_rows_cols<MAXC, SV, VT>(pp, n, GlobalCols<SV>{V, ldv, pp * (2 * kThreads)}, need_w, J8, r8, ur0,
-                                        wr0, ur1, wr1, su, sw, acc_a, acc_c, rem_a, rem_c, sig, dd, hook, NoHook{});
+                                        wr0, ur1, wr1, su, sw, acc_a, acc_c, rem_a, rem_c, sig, dd, hook, NoHook{},
+                                        NoHook{});
 }
 
 // One 256-row tile t of the fused SpMV + block dot (one row per thread in the

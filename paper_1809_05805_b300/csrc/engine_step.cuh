@@ -87,6 +87,7 @@ ke_step(const VT* __restrict__ V, int64_t ldv, VT* __restrict__ w, EngDev e, int
   };
   uint32_t phase = 0, pend_phase = 0;
   bool pending = false;  // thread 0: a copy was issued and not yet seen complete (phase pend_phase)
+  bool held = false;     // thread 0: pend_phase is that of the copy left in flight by a failed wait
   if (threadIdx.x == 0 && lo < hi) {
     int64_t t0;
     int sy0;
@@ -153,8 +154,12 @@ ke_step(const VT* __restrict__ V, int64_t ldv, VT* __restrict__ w, EngDev e, int
       if (!staged) s_stage_off = 1;
     }
     if (threadIdx.x == 0) {
-      if (staged) pending = false;
-      else if (pending) pend_phase = phase;
+      if (staged) {
+        pending = false;
+      } else if (pending && !held) {  // no copy is issued after this one: keep its phase
+        pend_phase = phase;
+        held = true;
+      }
     }
     phase ^= 1u;
     // once every thread is past this unit's SpMV, the buffer takes the next unit

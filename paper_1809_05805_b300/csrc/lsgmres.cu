@@ -570,7 +570,7 @@ struct gmres_ctx {
   int nsm = 0;
   int P = 0;          // CTAs of reduction kernels
   int P32 = 0;        // CTAs of the FP32-cycle step kernel (3 resident per SM)
-  int P16 = 0;        // CTAs of the BF16-basis step kernel (3 per SM; 2 in staging mode 3)
+  int P16 = 0;        // CTAs of the BF16-basis step kernel (3 per SM; 2 in staging modes 3 and 4)
   int grid_stream = 0;// CTAs of streaming kernels
   int32_t* rowptr = nullptr;
   int32_t* col = nullptr;
@@ -1025,8 +1025,9 @@ static void csr_stage_caps(const std::vector<int32_t>& rp, int64_t n, int& cap_t
 // which `per_sm` must stay resident per SM: tile pairs when the unstaged kernel
 // would take pairs (ntiles >= 4 P) and their buffer fits, else single tiles if
 // theirs fits, else off. With v3_bytes > 0 (the basis columns of a tile, BF16
-// basis), mode 3 (single tiles with their basis columns staged too, two CTAs
-// per SM) is tried first; *P is then lowered to two CTAs per SM. kernel_for(stage)
+// basis), modes with the unit's basis columns staged too are tried first, at
+// two CTAs per SM: 4 (tile pairs: bulk copies of twice the size, half as
+// many), then 3 (single tiles); *P is then lowered to two CTAs per SM. kernel_for(stage)
 // gives the kernel of a mode; the dynamic shared memory is the larger of the
 // epilogue's (t_smem) and the staging buffer's. Sets the kernel's
 // shared-memory limit.
@@ -1035,24 +1036,26 @@ static gmres_status choose_stage(KernelFor kernel_for, size_t vb, int per_sm, in
                                  int cap_tile, int cap_pair, size_t t_smem, size_t v3_bytes, int& mode, int& cap,
                                  size_t& smem) {
   const bool pairs = ntiles >= 4 * (int64_t)*P;
-  for (int cand : {3, 2, 1}) {
-    if (cand == 3 && (v3_bytes == 0 || ntiles < 4 * 2 * (int64_t)nsm)) continue;
+  for (int cand : {4, 3, 2, 1}) {
+    // staged basis: at least 4 tiles per CTA at two CTAs per SM
+    if (cand >= 3 && (v3_bytes == 0 || ntiles < 4 * 2 * (int64_t)nsm)) continue;
     if (cand == 2 && !pairs) continue;
-    const int U = cand == 2 ? 2 * kThreads : kThreads;
-    const int c = cand == 2 ? cap_pair : cap_tile;
-    const size_t need =
-        std::max(t_smem, (size_t)(U + 4) * 4 + (size_t)c * (4 + vb) + (cand == 3 ? v3_bytes : 0));
+    const bool pr = cand == 2 || cand == 4;
+    const int U = pr ? 2 * kThreads : kThreads;
+    const int c = pr ? cap_pair : cap_tile;
+    const size_t need = std::max(t_smem, (size_t)(U + 4) * 4 + (size_t)c * (4 + vb) +
+                                             (cand >= 3 ? (pr ? 2 : 1) * v3_bytes : 0));
     if (need > 200 * 1024) continue;
     const void* k = reinterpret_cast<const void*>(kernel_for(cand));
     if (raise_smem_limit(k, need) != cudaSuccess)
       return GMRES_ERR_CUDA;
     int nb = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, kThreads, need) != cudaSuccess) return GMRES_ERR_CUDA;
-    if (nb >= (cand == 3 ? 2 : per_sm)) {
+    if (nb >= (cand >= 3 ? 2 : per_sm)) {
       mode = cand;
       cap = c;
       smem = need;
-      if (cand == 3) *P = (int)std::min<int64_t>(2 * (int64_t)nsm, ntiles);
+      if (cand >= 3) *P = (int)std::min<int64_t>(2 * (int64_t)nsm, cand == 4 ? (ntiles + 1) / 2 : ntiles);
       return GMRES_OK;
     }
   }

@@ -10,8 +10,9 @@
 
 namespace lsg_steps {
 // Host stub of the step kernel for restart length m and staging mode (0 off,
-// 1 tiles, 2 tile pairs, 3 tiles with their basis columns, BF16 basis only);
-// callers cast it to their StepKernel type.
+// 1 tiles, 2 tile pairs, 3 tiles with their basis columns, 4 tile pairs with
+// theirs; 3 and 4 for the BF16 basis only); callers cast it to their
+// StepKernel type.
 const void* step_kernel_f64_s0(int m);
 const void* step_kernel_f64_s1(int m);
 const void* step_kernel_f64_s2(int m);
@@ -22,7 +23,8 @@ const void* step_kernel_bf16_s0(int m);
 const void* step_kernel_bf16_s1(int m);
 const void* step_kernel_bf16_s2(int m);
 const void* step_kernel_bf16_s3(int m);
-// Mode 3 is built for the BF16 basis only: the FP64 basis tile does not fit
+const void* step_kernel_bf16_s4(int m);
+// Modes 3 and 4 are built for the BF16 basis only: the FP64 basis tile does not fit
 // beside two resident CTAs, and FP32 cycles ran faster at three CTAs per SM
 // reading the basis themselves than at two with it staged.
 inline const void* step_kernel_f64(int m, int stage) {
@@ -32,7 +34,8 @@ inline const void* step_kernel_f32(int m, int stage) {
   return stage == 2 ? step_kernel_f32_s2(m) : stage == 1 ? step_kernel_f32_s1(m) : step_kernel_f32_s0(m);
 }
 inline const void* step_kernel_bf16(int m, int stage) {
-  return stage == 3   ? step_kernel_bf16_s3(m)
+  return stage == 4   ? step_kernel_bf16_s4(m)
+         : stage == 3 ? step_kernel_bf16_s3(m)
          : stage == 2 ? step_kernel_bf16_s2(m)
          : stage == 1 ? step_kernel_bf16_s1(m)
                       : step_kernel_bf16_s0(m);
@@ -52,7 +55,7 @@ using StepKernel = void (*)(const int32_t*, const int32_t*, const VT*, const SV*
 // the 192^3 27-point GMRES-IR solve: 2.9 -> 3.4 TB/s; four per SM spill and
 // lose).
 template <int MAXC, typename VT, typename SV = VT, int STAGE = 0>
-__global__ void __launch_bounds__(kThreads, (sizeof(VT) == 4 && STAGE != 3) ? 3 : 2)
+__global__ void __launch_bounds__(kThreads, (sizeof(VT) == 4 && STAGE < 3) ? 3 : 2)
 k_one_reduce_step(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                   const VT* __restrict__ val, const SV* __restrict__ V, int64_t ldv,
                   const SV* __restrict__ u_arg, VT* __restrict__ w, int64_t n, Small s,
@@ -79,9 +82,9 @@ k_one_reduce_step(const int32_t* __restrict__ rowptr, const int32_t* __restrict_
   }
   __syncthreads();
   if (s_skip) return;
-  // STAGE 3 copies basis columns of the handle's own basis; the standalone
-  // block dot (raw_out) never runs it
-  if (STAGE == 3 && raw_out) return;
+  // STAGES 3 and 4 copy basis columns of the handle's own basis; the
+  // standalone block dot (raw_out) never runs them
+  if (STAGE >= 3 && raw_out) return;
   const int j = s_j;
   const bool tail = s_tail;
   const bool spmv = raw_out ? (use_spmv != 0) : !tail;
@@ -104,18 +107,21 @@ k_one_reduce_step(const int32_t* __restrict__ rowptr, const int32_t* __restrict_
   const int64_t ntiles = (n + kThreads - 1) / kThreads;
   if constexpr (STAGE != 0) {
     // Staged CSR (STAGE 1: one tile per unit, 2: tile pairs; 3: one tile per
-    // unit, and the tile's basis columns too): the bulk-copy engine fetches
-    // the next unit's rowptr slice, indices and values into shared memory
-    // while this one's block dot runs (and, for STAGE 3, the next tile's basis
-    // columns while this one's SpMV runs). The global CSR is never
+    // unit, and the tile's basis columns too; 4: tile pairs and their basis
+    // columns): the bulk-copy engine fetches the next unit's rowptr slice,
+    // indices and values into shared memory while this one's block dot runs
+    // (and, for STAGES 3 and 4, the next unit's basis columns while this
+    // one's SpMV runs). The global CSR is never
     // read by this instantiation: a unit whose copy did not arrive in time, or
     // that does not fit the buffer (the host sizes it for the largest unit),
     // sets the stalled flag and contributes a zero SpMV.
-    const int U = STAGE == 2 ? 2 * kThreads : kThreads;
+    constexpr bool kPairs = STAGE == 2 || STAGE == 4;  // units of two tiles
+    constexpr bool kStageV = STAGE >= 3;              // basis columns staged too
+    const int U = kPairs ? 2 * kThreads : kThreads;
     const int64_t units = (n + U - 1) / U;
     if (spmv) {
       extern __shared__ __align__(16) double dyn[];
-      constexpr int kWs = STAGE == 2 ? 8 : 14;  // gathers in flight per staged row
+      constexpr int kWs = kPairs ? 8 : 14;  // gathers in flight per staged row
       CsrStage<VT> cs;
       cs.rp = reinterpret_cast<int32_t*>(dyn);
       cs.col = cs.rp + (U + 4);
@@ -123,30 +129,36 @@ k_one_reduce_step(const int32_t* __restrict__ rowptr, const int32_t* __restrict_
       cs.bar = &s_bar;
       cs.cap = stage_cap;
       cs.U = U;
-      // STAGE 3 also stages the tile's basis columns 0 .. j-1 (after the CSR)
+      // STAGES 3 and 4 also stage the unit's basis columns 0 .. j-1 (after the
+      // CSR; U values each)
       SV* sV = reinterpret_cast<SV*>(cs.val + stage_cap);
       if (threadIdx.x == 0) {
         s_stage_off = 0;
         mbar_init(&s_bar, 1);
-        if (STAGE == 3) mbar_init(&s_barV, 1);
+        if (kStageV) mbar_init(&s_barV, 1);
       }
       __syncthreads();
       uint32_t phase = 0, pend_phase = 0, vphase = 0, vpend_phase = 0;
       bool pending = false;   // thread 0: a CSR copy was issued and not yet seen complete (phase pend_phase)
       bool vpending = false;  // the same for the basis copies
-      // thread 0: bulk copies of the tile's slices of basis columns 0 .. j-1
+      // thread 0: pend_phase (vpend_phase) is that of the copy a failed wait
+      // left in flight; no copy is issued after a failed wait, so the first
+      // one recorded is the last one
+      bool held = false, vheld = false;
+      // thread 0: bulk copies of unit tu's slices of basis columns 0 .. j-1
+      // (in bounds: ldv is a whole number of tile pairs)
       auto issue_cols = [&](int64_t tu) {
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        const uint32_t bytes = (uint32_t)(kThreads * sizeof(SV));
+        const uint32_t bytes = (uint32_t)(U * sizeof(SV));
         mbar_arrive_expect_tx(&s_barV, (uint32_t)j * bytes + s_extra);
-        for (int k = 0; k < j; ++k) bulk_g2s(sV + (size_t)k * kThreads, V + (size_t)k * ldv + tu * kThreads, bytes, &s_barV);
+        for (int k = 0; k < j; ++k) bulk_g2s(sV + (size_t)k * U, V + (size_t)k * ldv + tu * U, bytes, &s_barV);
       };
       int64_t unit = blockIdx.x;
       if (threadIdx.x == 0 && unit < units) {
         cs.issue(rowptr, col, val, unit, CsrStage<VT>::lo_of(__ldg(rowptr + unit * U)),
                  CsrStage<VT>::hi_of(__ldg(rowptr + unit * U + U)), s_extra);
         pending = true;
-        if (STAGE == 3) {
+        if (kStageV) {
           issue_cols(unit);
           vpending = true;
         }
@@ -161,15 +173,19 @@ k_one_reduce_step(const int32_t* __restrict__ rowptr, const int32_t* __restrict_
         const int64_t row0 = unit * U + threadIdx.x, row1 = row0 + kThreads;
         VT ur0 = VT(0), ur1 = VT(0), wr0 = VT(0), wr1 = VT(0);
         if (row0 < n) ur0 = ld_as<VT>(u + row0);
-        if (STAGE == 2 && row1 < n) ur1 = ld_as<VT>(u + row1);
+        if (kPairs && row1 < n) ur1 = ld_as<VT>(u + row1);
         bool staged = !s_stage_off;
         if (staged) {
           staged = mbar_wait_bounded(&s_bar, phase);
           if (!staged) s_stage_off = 1;
         }
         if (threadIdx.x == 0) {
-          if (staged) pending = false;
-          else if (pending) pend_phase = phase;
+          if (staged) {
+            pending = false;
+          } else if (pending && !held) {
+            pend_phase = phase;
+            held = true;
+          }
         }
         phase ^= 1u;
         int lo = 0;
@@ -178,7 +194,7 @@ k_one_reduce_step(const int32_t* __restrict__ rowptr, const int32_t* __restrict_
           staged = CsrStage<VT>::hi_of(cs.rp[U]) - lo <= stage_cap;
         }
         if (!staged) atomicExch(&st->stalled, 1);
-        if (STAGE == 2) {
+        if (kPairs) {
           if (staged)
             csr_row2_staged<kWs>(cs.col, cs.val, u, cs.rp[threadIdx.x] - lo, cs.rp[threadIdx.x + 1] - lo,
                                  cs.rp[kThreads + threadIdx.x] - lo, cs.rp[kThreads + threadIdx.x + 1] - lo, wr0,
@@ -197,9 +213,9 @@ k_one_reduce_step(const int32_t* __restrict__ rowptr, const int32_t* __restrict_
             pending = true;
           }
         };
-        if constexpr (STAGE == 3) {
-          // the tile's basis columns: waited for after the SpMV, refilled for
-          // the next tile once every thread is done with them
+        if constexpr (kStageV) {
+          // the unit's basis columns: waited for after the SpMV, refilled for
+          // the next unit once every thread is done with them
           auto before = [&]() {
             bool ok = !s_stage_off;
             if (ok) {
@@ -210,8 +226,12 @@ k_one_reduce_step(const int32_t* __restrict__ rowptr, const int32_t* __restrict_
               }
             }
             if (threadIdx.x == 0) {
-              if (ok) vpending = false;
-              else if (vpending) vpend_phase = vphase;
+              if (ok) {
+                vpending = false;
+              } else if (vpending && !vheld) {
+                vpend_phase = vphase;
+                vheld = true;
+              }
             }
             vphase ^= 1u;
           };
@@ -221,8 +241,13 @@ k_one_reduce_step(const int32_t* __restrict__ rowptr, const int32_t* __restrict_
               vpending = true;
             }
           };
-          tile_dot_rows_cols<MAXC, SV, VT>(unit, n, SharedCols<SV>{sV}, need_w, J8, r8, ur0, wr0, su, sw, acc_a,
-                                           acc_c, rem_a, rem_c, sig, dd, next, before, after);
+          if constexpr (kPairs)
+            tile_pair_dot_rows_cols<MAXC, SV, VT>(unit, n, SharedCols<SV>{sV, U}, need_w, J8, r8, ur0, wr0, ur1,
+                                                  wr1, su, sw, acc_a, acc_c, rem_a, rem_c, sig, dd, next, before,
+                                                  after);
+          else
+            tile_dot_rows_cols<MAXC, SV, VT>(unit, n, SharedCols<SV>{sV, U}, need_w, J8, r8, ur0, wr0, su, sw,
+                                             acc_a, acc_c, rem_a, rem_c, sig, dd, next, before, after);
         } else if (STAGE == 2) {
           tile_pair_dot_rows<MAXC, SV, VT>(unit, n, V, ldv, need_w, J8, r8, ur0, wr0, ur1, wr1, su, sw, acc_a,
                                            acc_c, rem_a, rem_c, sig, dd, next);
@@ -233,7 +258,7 @@ k_one_reduce_step(const int32_t* __restrict__ rowptr, const int32_t* __restrict_
       }
       // no copy may still be landing in shared memory when the CTA moves on
       if (threadIdx.x == 0 && pending) mbar_wait_bounded(&s_bar, pend_phase);
-      if (STAGE == 3 && threadIdx.x == 0 && vpending) mbar_wait_bounded(&s_barV, vpend_phase);
+      if (kStageV && threadIdx.x == 0 && vpending) mbar_wait_bounded(&s_barV, vpend_phase);
       __syncthreads();
     } else {
       // no SpMV (the cycle's tail, or a standalone block dot with w given)
@@ -244,11 +269,11 @@ k_one_reduce_step(const int32_t* __restrict__ rowptr, const int32_t* __restrict_
           ur0 = ld_as<VT>(u + row0);
           if (need_w) wr0 = w[row0];
         }
-        if (STAGE == 2 && row1 < n) {
+        if (kPairs && row1 < n) {
           ur1 = ld_as<VT>(u + row1);
           if (need_w) wr1 = w[row1];
         }
-        if (STAGE == 2)
+        if (kPairs)
           tile_pair_dot_rows<MAXC, SV, VT>(unit, n, V, ldv, need_w, J8, r8, ur0, wr0, ur1, wr1, su, sw, acc_a,
                                            acc_c, rem_a, rem_c, sig, dd, NoHook{});
         else

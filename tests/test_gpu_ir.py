@@ -121,7 +121,11 @@ BF16_CASES = {
     "aniso27_12cubed": (lambda: P.aniso_27pt(12), 40),
     "convdiff7_16cubed": (lambda: P.conv_diff_7pt(16), 30),
     "aniso27_23cubed": (lambda: P.aniso_27pt(23), 40),  # ragged: 12167 rows
-    "aniso27_69cubed": (lambda: P.aniso_27pt(69), 40),  # basis columns staged too (as above)
+    # 328,509 rows: the basis columns of each unit are staged too, at two CTAs
+    # per SM; the 27-point case stages single tiles (staging mode 3), the
+    # 7-point one, whose CSR is smaller, tile pairs (mode 4)
+    "aniso27_69cubed": (lambda: P.aniso_27pt(69), 40),
+    "convdiff7_69cubed": (lambda: P.conv_diff_7pt(69), 40),
 }
 
 
