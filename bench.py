@@ -53,6 +53,7 @@ WORKLOADS = {
     144: dict(N=144, m=40, tol=1e-10, max_iter=5000, stencil="27pt", prec="ir_fp32", compare="fp64"),  # profiling
     # the 256^3 7-point problem of the headline, solved by GMRES-IR (FP32 cycles)
     "256ir": dict(N=256, m=50, tol=1e-8, max_iter=3000, stencil="7pt", prec="ir_fp32", compare="fp64"),
+    "128ir": dict(N=128, m=50, tol=1e-8, max_iter=3000, stencil="7pt", prec="ir_fp32", compare="fp64"),  # profiling
 }
 # batched uneven solves: 2D 9-point variable-coefficient convection-diffusion
 # systems, grid side log-uniform in `side`, all solved together
@@ -72,7 +73,7 @@ SERVE_WORKLOADS = {
 }
 METRIC_SERVE = "solves/s at 2000 req/s offered (1e-8 rel. resid each), continuous-batching serving loop; p50/p99 latency"
 METRIC = "time-to-solve (1e-8 rel. resid), one-reduce MGS-GMRES"
-METRIC_IR = "time-to-solve (1e-10 rel. resid), GMRES-IR: one-reduce cycles in FP32, FP64 restarts"
+METRIC_IR = "time-to-solve ({tol} rel. resid), GMRES-IR: one-reduce cycles in FP32, FP64 restarts"
 
 
 def make_problem(w):
@@ -82,8 +83,10 @@ FP64_DFMA_PER_CLK_SM = 2  # B300: 1.25 TFLOP/s nominal FP64 = 148 SMs x 2 DFMA/c
 # step kernels (dram__bytes_read.sum + dram__bytes_write.sum over the launch's
 # algorithmic bytes): the FP64 kernel with staged tile pairs on the 128^3
 # 7-point workload at j = 8 and 9, the FP32 kernel with staged tiles on the
-# 144^3 27-point GMRES-IR workload at j = 18 and 19. Valid only for the kernel
-# builds those captures measured; set to None when a kernel changes.
+# 144^3 27-point GMRES-IR workload at j = 18 and 19 (the single-tile kernel
+# the 27-point workloads run; the 7-point ones take tile pairs, uncaptured).
+# Valid only for the kernel builds those captures measured; set to None when a
+# kernel changes.
 STEP_TRAFFIC_RATIO = 1.049
 STEP32_TRAFFIC_RATIO = 1.016
 
@@ -260,9 +263,9 @@ def run_reference(args, w, rank, world):
     A = make_problem(w)
     _, b = P.rhs(A, seed=0)
     if w["prec"] == "ir_fp32" and w["N"] >= 192:
-        print(json.dumps({"impl": "reference", "unavailable": "no complete run of the oracle's GMRES-IR at this size: "
-                          "its sequential FP32 sums stall it (192^3 27-point: true residual 1.43e-10 after 5000 "
-                          "steps, tol 1e-10)"}))
+        print(json.dumps({"impl": "reference", "unavailable": "no complete run of the oracle's GMRES-IR at this size "
+                          "to scale a sample by (at 192^3 27-point its sequential FP32 sums stall it: true residual "
+                          "1.43e-10 after 5000 steps, tol 1e-10)"}))
         return 0
     prof = golden_profile({256: "c2_one_reduce", 32: "c1"}.get(w["N"], "none"))
     if prof is None:
@@ -279,7 +282,7 @@ def run_reference(args, w, rank, world):
     v = float(np.mean([c["value"] for c in vals]))
     cores = 1
     line = {
-        "impl": "reference", "metric": METRIC_IR if w["prec"] == "ir_fp32" else METRIC, "value": v, "unit": "s", "n_gpus": args.gpus,
+        "impl": "reference", "metric": METRIC_IR.format(tol=("%.0e" % w["tol"]).replace("e-0", "e-")) if w["prec"] == "ir_fp32" else METRIC, "value": v, "unit": "s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * v, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": workload_name(w), "m": w["m"], "tol": w["tol"]},
@@ -443,7 +446,7 @@ def run_ours(args, w, rank, world, dist):
             "frac": step_gbs / hbm if step_gbs else None,
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy bandwidth, of measured)",
             "traffic": ((STEP32_TRAFFIC_RATIO * st["bytes"] / max(st["launches"], 1))
-                        if STEP32_TRAFFIC_RATIO and w["prec"] == "ir_fp32" else None),
+                        if STEP32_TRAFFIC_RATIO and w["prec"] == "ir_fp32" and w["stencil"] == "27pt" else None),
             "traffic_source": "ncu dram bytes / algorithmic bytes of the FP32 step at 144^3 (same kernel build), "
                               "times this run's algorithmic bytes per launch",
             "launch_avg_ms": step_avg_ms, "launches": st["launches"],
@@ -481,7 +484,7 @@ def run_ours(args, w, rank, world, dist):
         cpu = cpu_baseline(A, b, w, ks, sample)
 
     line = {
-        "metric": METRIC_IR if ir else METRIC, "value": ms / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
+        "metric": METRIC_IR.format(tol=("%.0e" % w["tol"]).replace("e-0", "e-")) if ir else METRIC, "value": ms / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32 cycles / f64 restarts" if ir else "f64",
         "data": "synthetic (seeded stencil, x_true ~ U[-1,1])",
