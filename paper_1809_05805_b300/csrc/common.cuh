@@ -200,6 +200,18 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
                "l"(src), "r"(bytes), "r"(smem_u32(bar))
                : "memory");
 }
+// Per-thread asynchronous 16-byte copy global -> shared through L2; bytes
+// past src_bytes (0..16) are zero-filled and not read. Completion is per
+// thread: commit groups, then wait until at most N of them are pending.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, int src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src), "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
@@ -723,6 +735,113 @@ __device__ __forceinline__ void tile_pair_dot_rows_cols(int64_t pp, int64_t n, C
   }
   __syncthreads();
   after();
+}
+
+// The tile pair pp with an FP32 basis read from global memory through a
+// per-warp ring of kPfStages column slices in shared memory, filled by
+// per-thread asynchronous copies kPfStages - 1 columns ahead of use: the
+// loads in flight cost shared memory instead of registers, so a warp keeps
+// two 1 KB slices in flight beside the one in use. Each lane
+// copies and reads only its own rows (half h: rows 256 h + 128 q + 4 lane +
+// e, q < 2, e < 4), so no barrier orders the ring; a slot is refilled only
+// after the FMAs that consumed it were issued. Rows >= n are zero-filled.
+// Same sums as tile_pair_dot_rows in another row order; the remainder
+// columns are read directly as there. ring: kWarps * kPfStages * 256 floats.
+constexpr int kPfStages = 3;
+template <int MAXC, typename Hook>
+__device__ __forceinline__ void tile_pair_dot_rows_pf(int64_t pp, int64_t n, const float* __restrict__ V,
+                                                      int64_t ldv, bool need_w, int J8, int r8, float ur0,
+                                                      float wr0, float ur1, float wr1, float* su, float* sw,
+                                                      float* ring, float (&acc_a)[MAXC], float (&acc_c)[MAXC],
+                                                      float (&rem_a)[kWarps - 1], float (&rem_c)[kWarps - 1],
+                                                      float& sig, float& dd, Hook hook) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t row0 = pp * (2 * kThreads) + threadIdx.x, row1 = row0 + kThreads;
+  sig = fmaf(ur0, ur0, sig);
+  dd = fmaf(ur0, wr0, dd);
+  sig = fmaf(ur1, ur1, sig);
+  dd = fmaf(ur1, wr1, dd);
+  su[threadIdx.x] = ur0;
+  sw[threadIdx.x] = wr0;
+  su[kThreads + threadIdx.x] = ur1;
+  sw[kThreads + threadIdx.x] = wr1;
+  __syncthreads();
+  hook();
+  float* wring = ring + wid * (kPfStages * kThreads);
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int64_t hb = pp * (2 * kThreads) + h * kThreads;  // first row of the half
+    float ru[8], rw[8];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const float4 a = *reinterpret_cast<const float4*>(su + h * kThreads + 128 * q + 4 * lane);
+      const float4 b = *reinterpret_cast<const float4*>(sw + h * kThreads + 128 * q + 4 * lane);
+      ru[4 * q] = a.x, ru[4 * q + 1] = a.y, ru[4 * q + 2] = a.z, ru[4 * q + 3] = a.w;
+      rw[4 * q] = b.x, rw[4 * q + 1] = b.y, rw[4 * q + 2] = b.z, rw[4 * q + 3] = b.w;
+    }
+    // this lane's 8 rows of column wid + 8 c into ring slot `slot`
+    auto issue = [&](int c, int slot) {
+      const float* colp = V + (size_t)(wid + c * kWarps) * ldv;
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const int64_t r = hb + 128 * q + 4 * lane;
+        const int64_t left = n - r;
+        const int bytes = left >= 4 ? 16 : (left > 0 ? (int)left * 4 : 0);
+        cp_async16(wring + slot * kThreads + 128 * q + 4 * lane, colp + (bytes ? r : 0), bytes);
+      }
+    };
+#pragma unroll
+    for (int c = 0; c < kPfStages - 1; ++c) {
+      if (c < J8) issue(c, c);  // warp-uniform
+      cp_async_commit();
+    }
+#pragma unroll
+    for (int c = 0; c < MAXC; ++c) {
+      if (c < J8) {  // warp-uniform
+        if (c + kPfStages - 1 < J8) issue(c + kPfStages - 1, (c + kPfStages - 1) % kPfStages);
+        cp_async_commit();
+        cp_async_wait<kPfStages - 1>();  // column c's copies are done
+        const float* sl = wring + (c % kPfStages) * kThreads;
+        const float4 x0 = *reinterpret_cast<const float4*>(sl + 4 * lane);
+        const float4 x1 = *reinterpret_cast<const float4*>(sl + 128 + 4 * lane);
+        const float x[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+#pragma unroll
+        for (int i = 0; i < 8; ++i) acc_a[c] = fmaf(x[i], ru[i], acc_a[c]);
+        if (need_w) {
+#pragma unroll
+          for (int i = 0; i < 8; ++i) acc_c[c] = fmaf(x[i], rw[i], acc_c[c]);
+        }
+      }
+    }
+    cp_async_wait<0>();
+  }
+  // The r8 remainder columns, four at a time (loads issued together).
+#pragma unroll
+  for (int c0 = 0; c0 < kWarps - 1; c0 += kRemBatch) {
+    if (c0 < r8) {  // block-uniform
+      float x0[kRemBatch], x1[kRemBatch];
+#pragma unroll
+      for (int b = 0; b < kRemBatch; ++b) {
+        const int c = c0 + b;
+        const float* colp = V + (size_t)(J8 * kWarps + c) * ldv;
+        x0[b] = (c < r8 && row0 < n) ? __ldg(colp + row0) : 0.f;
+        x1[b] = (c < r8 && row1 < n) ? __ldg(colp + row1) : 0.f;
+      }
+#pragma unroll
+      for (int b = 0; b < kRemBatch; ++b) {
+        const int c = c0 + b;
+        if (c < kWarps - 1 && c < r8) {
+          rem_a[c] = fmaf(x0[b], ur0, rem_a[c]);
+          rem_a[c] = fmaf(x1[b], ur1, rem_a[c]);
+          if (need_w) {
+            rem_c[c] = fmaf(x0[b], wr0, rem_c[c]);
+            rem_c[c] = fmaf(x1[b], wr1, rem_c[c]);
+          }
+        }
+      }
+    }
+  }
+  __syncthreads();
 }
 
 // The tile pair with the basis read from global memory.

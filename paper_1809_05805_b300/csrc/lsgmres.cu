@@ -1029,12 +1029,13 @@ static void csr_stage_caps(const std::vector<int32_t>& rp, int64_t n, int& cap_t
 // two CTAs per SM: 4 (tile pairs: bulk copies of twice the size, half as
 // many), then 3 (single tiles); *P is then lowered to two CTAs per SM. kernel_for(stage)
 // gives the kernel of a mode; the dynamic shared memory is the larger of the
-// epilogue's (t_smem) and the staging buffer's. Sets the kernel's
+// epilogue's (t_smem) and the staging buffer's (plus pair_extra bytes behind
+// a tile pair's CSR in mode 2: the FP32 kernel's column ring). Sets the kernel's
 // shared-memory limit.
 template <typename KernelFor>
 static gmres_status choose_stage(KernelFor kernel_for, size_t vb, int per_sm, int* P, int nsm, int64_t ntiles,
-                                 int cap_tile, int cap_pair, size_t t_smem, size_t v3_bytes, int& mode, int& cap,
-                                 size_t& smem) {
+                                 int cap_tile, int cap_pair, size_t t_smem, size_t v3_bytes, size_t pair_extra,
+                                 int& mode, int& cap, size_t& smem) {
   const bool pairs = ntiles >= 4 * (int64_t)*P;
   for (int cand : {4, 3, 2, 1}) {
     // staged basis: at least 4 tiles per CTA at two CTAs per SM
@@ -1044,7 +1045,7 @@ static gmres_status choose_stage(KernelFor kernel_for, size_t vb, int per_sm, in
     const int U = pr ? 2 * kThreads : kThreads;
     const int c = pr ? cap_pair : cap_tile;
     const size_t need = std::max(t_smem, (size_t)(U + 4) * 4 + (size_t)c * (4 + vb) +
-                                             (cand >= 3 ? (pr ? 2 : 1) * v3_bytes : 0));
+                                             (cand >= 3 ? (pr ? 2 : 1) * v3_bytes : 0) + (cand == 2 ? pair_extra : 0));
     if (need > 200 * 1024) continue;
     const void* k = reinterpret_cast<const void*>(kernel_for(cand));
     if (raise_smem_limit(k, need) != cudaSuccess)
@@ -1160,16 +1161,17 @@ gmres_status gmres_create(const gmres_csr* A, int m_restart, double tol, gmres_h
     csr_stage_caps(rp, n, cap_tile, cap_pair);
     const int m = m_restart;
     gmres_status sst = choose_stage([m](int sg) { return step64_for(m, sg); }, sizeof(double), 2, &h->P, h->nsm,
-                                    ntiles, cap_tile, cap_pair, h->step_smem, 0, h->stage64, h->cap64, h->smem64);
+                                    ntiles, cap_tile, cap_pair, h->step_smem, 0, 0, h->stage64, h->cap64, h->smem64);
     if (sst == GMRES_OK)
       // FP32 basis: no mode 3 (measured: equal at 192^3 27-point, 16% slower at 256^3
       // 7-point than three CTAs per SM reading the basis themselves); the BF16
       // basis, whose 2-byte loads use sectors poorly, gains from it (31% at 192^3)
       sst = choose_stage([m](int sg) { return step32_for(m, sg); }, sizeof(float), 3, &h->P32, h->nsm, ntiles,
-                         cap_tile, cap_pair, h->step_smem, 0, h->stage32, h->cap32, h->smem32);
+                         cap_tile, cap_pair, h->step_smem, 0, sizeof(float) * kWarps * kPfStages * kThreads,
+                         h->stage32, h->cap32, h->smem32);
     if (sst == GMRES_OK)
       sst = choose_stage([m](int sg) { return step16_for(m, sg); }, sizeof(float), 3, &h->P16, h->nsm, ntiles,
-                         cap_tile, cap_pair, h->step_smem, (size_t)m * kThreads * sizeof(__nv_bfloat16),
+                         cap_tile, cap_pair, h->step_smem, (size_t)m * kThreads * sizeof(__nv_bfloat16), 0,
                          h->stage16, h->cap16, h->smem16);
     if (sst != GMRES_OK) {
       h->err = "cudaFuncSetAttribute / occupancy query of the step kernels failed";

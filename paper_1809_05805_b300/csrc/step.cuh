@@ -60,8 +60,8 @@ k_one_reduce_step(const int32_t* __restrict__ rowptr, const int32_t* __restrict_
                   const VT* __restrict__ val, const SV* __restrict__ V, int64_t ldv,
                   const SV* __restrict__ u_arg, VT* __restrict__ w, int64_t n, Small s,
                   int j_arg, int use_spmv, double* raw_out, int stage, int stage_cap) {
-  __shared__ VT su[2 * kThreads];
-  __shared__ VT sw[2 * kThreads];
+  __shared__ __align__(16) VT su[2 * kThreads];
+  __shared__ __align__(16) VT sw[2 * kThreads];
   __shared__ double red[2 * (kMaxM + 1) + 2];
   __shared__ int s_j, s_tail, s_skip, s_stage_off;
   __shared__ uint64_t s_bar, s_barV;
@@ -249,8 +249,15 @@ k_one_reduce_step(const int32_t* __restrict__ rowptr, const int32_t* __restrict_
             tile_dot_rows_cols<MAXC, SV, VT>(unit, n, SharedCols<SV>{sV, U}, need_w, J8, r8, ur0, wr0, su, sw,
                                              acc_a, acc_c, rem_a, rem_c, sig, dd, next, before, after);
         } else if (STAGE == 2) {
-          tile_pair_dot_rows<MAXC, SV, VT>(unit, n, V, ldv, need_w, J8, r8, ur0, wr0, ur1, wr1, su, sw, acc_a,
-                                           acc_c, rem_a, rem_c, sig, dd, next);
+          if constexpr (std::is_same<SV, float>::value && std::is_same<VT, float>::value)
+            // FP32 basis: the column slices stream through a per-warp ring
+            // behind the CSR buffer
+            tile_pair_dot_rows_pf<MAXC>(unit, n, V, ldv, need_w, J8, r8, ur0, wr0, ur1, wr1, su, sw,
+                                        reinterpret_cast<float*>(cs.val + stage_cap), acc_a, acc_c, rem_a, rem_c,
+                                        sig, dd, next);
+          else
+            tile_pair_dot_rows<MAXC, SV, VT>(unit, n, V, ldv, need_w, J8, r8, ur0, wr0, ur1, wr1, su, sw, acc_a,
+                                             acc_c, rem_a, rem_c, sig, dd, next);
         } else {
           tile_dot_rows<MAXC, SV, VT>(unit, n, V, ldv, need_w, J8, r8, ur0, wr0, su, sw, acc_a, acc_c, rem_a,
                                       rem_c, sig, dd, next);
