@@ -737,24 +737,31 @@ __device__ __forceinline__ void tile_pair_dot_rows_cols(int64_t pp, int64_t n, C
   after();
 }
 
-// The tile pair pp with an FP32 basis read from global memory through a
-// per-warp ring of kPfStages column slices in shared memory, filled by
-// per-thread asynchronous copies kPfStages - 1 columns ahead of use: the
-// loads in flight cost shared memory instead of registers, so a warp keeps
-// two 1 KB slices in flight beside the one in use. Each lane
-// copies and reads only its own rows (half h: rows 256 h + 128 q + 4 lane +
-// e, q < 2, e < 4), so no barrier orders the ring; a slot is refilled only
-// after the FMAs that consumed it were issued. Rows >= n are zero-filled.
-// Same sums as tile_pair_dot_rows in another row order; the remainder
-// columns are read directly as there. ring: kWarps * kPfStages * 256 floats.
-constexpr int kPfStages = 3;
-template <int MAXC, typename Hook>
-__device__ __forceinline__ void tile_pair_dot_rows_pf(int64_t pp, int64_t n, const float* __restrict__ V,
+// The tile pair pp with the basis (FP32 or BF16) read from global memory
+// through a per-warp ring of pf_stages<SV>() column slices in shared memory,
+// filled by per-thread asynchronous 16-byte copies pf_stages - 1 columns ahead
+// of use: the bytes in flight cost shared memory instead of registers (with
+// register loads a lane kept one column's 8 loads in flight). Each lane
+// copies and reads only its own rows (half h: rows 256 h + 32 R q + R lane +
+// e, R = 16 / sizeof(SV) rows per copy, q < 8 / R, e < R), so no barrier
+// orders the ring; a slot is refilled only after the FMAs that consumed it
+// were issued. Rows >= n are zero-filled. Same sums as tile_pair_dot_rows in
+// another row order; the remainder columns are read directly as there.
+// ring: kWarps * pf_stages<SV>() * 256 values of SV (24 KB either way).
+template <typename SV>
+__host__ __device__ constexpr int pf_stages() { return sizeof(SV) == 4 ? 3 : 6; }
+template <typename SV>
+__host__ __device__ constexpr size_t pf_ring_bytes() { return (size_t)kWarps * pf_stages<SV>() * kThreads * sizeof(SV); }
+template <int MAXC, typename SV, typename Hook>
+__device__ __forceinline__ void tile_pair_dot_rows_pf(int64_t pp, int64_t n, const SV* __restrict__ V,
                                                       int64_t ldv, bool need_w, int J8, int r8, float ur0,
                                                       float wr0, float ur1, float wr1, float* su, float* sw,
-                                                      float* ring, float (&acc_a)[MAXC], float (&acc_c)[MAXC],
+                                                      SV* ring, float (&acc_a)[MAXC], float (&acc_c)[MAXC],
                                                       float (&rem_a)[kWarps - 1], float (&rem_c)[kWarps - 1],
                                                       float& sig, float& dd, Hook hook) {
+  constexpr int S = pf_stages<SV>();
+  constexpr int R = 16 / (int)sizeof(SV);  // rows per 16-byte copy
+  constexpr int NQ = kRowsPerLane / R;     // copies per lane per column half
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int64_t row0 = pp * (2 * kThreads) + threadIdx.x, row1 = row0 + kThreads;
   sig = fmaf(ur0, ur0, sig);
@@ -767,49 +774,65 @@ __device__ __forceinline__ void tile_pair_dot_rows_pf(int64_t pp, int64_t n, con
   sw[kThreads + threadIdx.x] = wr1;
   __syncthreads();
   hook();
-  float* wring = ring + wid * (kPfStages * kThreads);
+  SV* wring = ring + wid * (S * kThreads);
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
     const int64_t hb = pp * (2 * kThreads) + h * kThreads;  // first row of the half
-    float ru[8], rw[8];
+    float ru[kRowsPerLane], rw[kRowsPerLane];
 #pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      const float4 a = *reinterpret_cast<const float4*>(su + h * kThreads + 128 * q + 4 * lane);
-      const float4 b = *reinterpret_cast<const float4*>(sw + h * kThreads + 128 * q + 4 * lane);
-      ru[4 * q] = a.x, ru[4 * q + 1] = a.y, ru[4 * q + 2] = a.z, ru[4 * q + 3] = a.w;
-      rw[4 * q] = b.x, rw[4 * q + 1] = b.y, rw[4 * q + 2] = b.z, rw[4 * q + 3] = b.w;
-    }
-    // this lane's 8 rows of column wid + 8 c into ring slot `slot`
+    for (int q = 0; q < NQ; ++q)
+#pragma unroll
+      for (int e = 0; e < R; e += 4) {
+        const int o = h * kThreads + 32 * R * q + R * lane + e;
+        const float4 a = *reinterpret_cast<const float4*>(su + o);
+        const float4 b = *reinterpret_cast<const float4*>(sw + o);
+        ru[R * q + e] = a.x, ru[R * q + e + 1] = a.y, ru[R * q + e + 2] = a.z, ru[R * q + e + 3] = a.w;
+        rw[R * q + e] = b.x, rw[R * q + e + 1] = b.y, rw[R * q + e + 2] = b.z, rw[R * q + e + 3] = b.w;
+      }
+    // this lane's rows of column wid + 8 c into ring slot `slot`
     auto issue = [&](int c, int slot) {
-      const float* colp = V + (size_t)(wid + c * kWarps) * ldv;
+      const SV* colp = V + (size_t)(wid + c * kWarps) * ldv;
 #pragma unroll
-      for (int q = 0; q < 2; ++q) {
-        const int64_t r = hb + 128 * q + 4 * lane;
+      for (int q = 0; q < NQ; ++q) {
+        const int64_t r = hb + 32 * R * q + R * lane;
         const int64_t left = n - r;
-        const int bytes = left >= 4 ? 16 : (left > 0 ? (int)left * 4 : 0);
-        cp_async16(wring + slot * kThreads + 128 * q + 4 * lane, colp + (bytes ? r : 0), bytes);
+        const int bytes = left >= R ? 16 : (left > 0 ? (int)left * (int)sizeof(SV) : 0);
+        cp_async16(wring + slot * kThreads + 32 * R * q + R * lane, colp + (bytes ? r : 0), bytes);
       }
     };
 #pragma unroll
-    for (int c = 0; c < kPfStages - 1; ++c) {
+    for (int c = 0; c < S - 1; ++c) {
       if (c < J8) issue(c, c);  // warp-uniform
       cp_async_commit();
     }
 #pragma unroll
     for (int c = 0; c < MAXC; ++c) {
       if (c < J8) {  // warp-uniform
-        if (c + kPfStages - 1 < J8) issue(c + kPfStages - 1, (c + kPfStages - 1) % kPfStages);
+        if (c + S - 1 < J8) issue(c + S - 1, (c + S - 1) % S);
         cp_async_commit();
-        cp_async_wait<kPfStages - 1>();  // column c's copies are done
-        const float* sl = wring + (c % kPfStages) * kThreads;
-        const float4 x0 = *reinterpret_cast<const float4*>(sl + 4 * lane);
-        const float4 x1 = *reinterpret_cast<const float4*>(sl + 128 + 4 * lane);
-        const float x[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+        cp_async_wait<S - 1>();  // column c's copies are done
+        const SV* sl = wring + (c % S) * kThreads;
+        float x[kRowsPerLane];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) acc_a[c] = fmaf(x[i], ru[i], acc_a[c]);
+        for (int q = 0; q < NQ; ++q) {
+          const uint4 v = *reinterpret_cast<const uint4*>(sl + 32 * R * q + R * lane);
+          if constexpr (sizeof(SV) == 4) {
+            x[R * q] = __uint_as_float(v.x), x[R * q + 1] = __uint_as_float(v.y);
+            x[R * q + 2] = __uint_as_float(v.z), x[R * q + 3] = __uint_as_float(v.w);
+          } else {  // BF16 widened exactly: its bits are the high half of the FP32 value
+            const uint32_t wds[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+              x[R * q + 2 * t] = __uint_as_float(wds[t] << 16);
+              x[R * q + 2 * t + 1] = __uint_as_float(wds[t] & 0xffff0000u);
+            }
+          }
+        }
+#pragma unroll
+        for (int i = 0; i < kRowsPerLane; ++i) acc_a[c] = fmaf(x[i], ru[i], acc_a[c]);
         if (need_w) {
 #pragma unroll
-          for (int i = 0; i < 8; ++i) acc_c[c] = fmaf(x[i], rw[i], acc_c[c]);
+          for (int i = 0; i < kRowsPerLane; ++i) acc_c[c] = fmaf(x[i], rw[i], acc_c[c]);
         }
       }
     }
@@ -823,9 +846,9 @@ __device__ __forceinline__ void tile_pair_dot_rows_pf(int64_t pp, int64_t n, con
 #pragma unroll
       for (int b = 0; b < kRemBatch; ++b) {
         const int c = c0 + b;
-        const float* colp = V + (size_t)(J8 * kWarps + c) * ldv;
-        x0[b] = (c < r8 && row0 < n) ? __ldg(colp + row0) : 0.f;
-        x1[b] = (c < r8 && row1 < n) ? __ldg(colp + row1) : 0.f;
+        const SV* colp = V + (size_t)(J8 * kWarps + c) * ldv;
+        x0[b] = (c < r8 && row0 < n) ? ld_as<float>(colp + row0) : 0.f;
+        x1[b] = (c < r8 && row1 < n) ? ld_as<float>(colp + row1) : 0.f;
       }
 #pragma unroll
       for (int b = 0; b < kRemBatch; ++b) {

@@ -1025,9 +1025,10 @@ static void csr_stage_caps(const std::vector<int32_t>& rp, int64_t n, int& cap_t
 // which `per_sm` must stay resident per SM: tile pairs when the unstaged kernel
 // would take pairs (ntiles >= 4 P) and their buffer fits, else single tiles if
 // theirs fits, else off. With v3_bytes > 0 (the basis columns of a tile, BF16
-// basis), modes with the unit's basis columns staged too are tried first, at
-// two CTAs per SM: 4 (tile pairs: bulk copies of twice the size, half as
-// many), then 3 (single tiles); *P is then lowered to two CTAs per SM. kernel_for(stage)
+// basis), modes with the unit's basis columns staged too are tried next (first
+// when the kernel has no column ring), at two CTAs per SM: 4 (tile pairs: bulk
+// copies of twice the size, half as many), then 3 (single tiles); *P is then
+// lowered to two CTAs per SM. kernel_for(stage)
 // gives the kernel of a mode; the dynamic shared memory is the larger of the
 // epilogue's (t_smem) and the staging buffer's (plus pair_extra bytes behind
 // a tile pair's CSR in mode 2: the FP32 kernel's column ring). Sets the kernel's
@@ -1037,7 +1038,11 @@ static gmres_status choose_stage(KernelFor kernel_for, size_t vb, int per_sm, in
                                  int cap_tile, int cap_pair, size_t t_smem, size_t v3_bytes, size_t pair_extra,
                                  int& mode, int& cap, size_t& smem) {
   const bool pairs = ntiles >= 4 * (int64_t)*P;
-  for (int cand : {4, 3, 2, 1}) {
+  // a kernel with the column ring (pair_extra > 0) takes tile pairs at per_sm
+  // CTAs per SM first: at 256^3 7-point the BF16 basis streamed through the
+  // ring (0.523 s) beat its bulk-copy staging (mode 4, 0.583 s)
+  const int order_ring[4] = {2, 4, 3, 1}, order_bulk[4] = {4, 3, 2, 1};
+  for (int cand : (pair_extra > 0 ? order_ring : order_bulk)) {
     // staged basis: at least 4 tiles per CTA at two CTAs per SM
     if (cand >= 3 && (v3_bytes == 0 || ntiles < 4 * 2 * (int64_t)nsm)) continue;
     if (cand == 2 && !pairs) continue;
@@ -1167,11 +1172,12 @@ gmres_status gmres_create(const gmres_csr* A, int m_restart, double tol, gmres_h
       // 7-point than three CTAs per SM reading the basis themselves); the BF16
       // basis, whose 2-byte loads use sectors poorly, gains from it (31% at 192^3)
       sst = choose_stage([m](int sg) { return step32_for(m, sg); }, sizeof(float), 3, &h->P32, h->nsm, ntiles,
-                         cap_tile, cap_pair, h->step_smem, 0, sizeof(float) * kWarps * kPfStages * kThreads,
+                         cap_tile, cap_pair, h->step_smem, 0, pf_ring_bytes<float>(),
                          h->stage32, h->cap32, h->smem32);
     if (sst == GMRES_OK)
       sst = choose_stage([m](int sg) { return step16_for(m, sg); }, sizeof(float), 3, &h->P16, h->nsm, ntiles,
-                         cap_tile, cap_pair, h->step_smem, (size_t)m * kThreads * sizeof(__nv_bfloat16), 0,
+                         cap_tile, cap_pair, h->step_smem, (size_t)m * kThreads * sizeof(__nv_bfloat16),
+                         pf_ring_bytes<__nv_bfloat16>(),
                          h->stage16, h->cap16, h->smem16);
     if (sst != GMRES_OK) {
       h->err = "cudaFuncSetAttribute / occupancy query of the step kernels failed";
