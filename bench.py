@@ -82,13 +82,13 @@ FP64_DFMA_PER_CLK_SM = 2  # B300: 1.25 TFLOP/s nominal FP64 = 148 SMs x 2 DFMA/c
 # DRAM bytes per step launch / algorithmic bytes, from ncu captures of the
 # step kernels (dram__bytes_read.sum + dram__bytes_write.sum over the launch's
 # algorithmic bytes): the FP64 kernel with staged tile pairs on the 128^3
-# 7-point workload at j = 8 and 9, the FP32 kernel with staged tiles on the
-# 144^3 27-point GMRES-IR workload at j = 18 and 19 (the single-tile kernel
-# the 27-point workloads run; the 7-point ones take tile pairs, uncaptured).
-# Valid only for the kernel builds those captures measured; set to None when a
-# kernel changes.
+# 7-point workload at j = 8 and 9; the FP32 kernels, per stencil: single
+# tiles on the 144^3 27-point GMRES-IR workload at j = 18 and 19, tile pairs
+# with the column ring on the 128^3 7-point one at j = 20 and 21. Valid only
+# for the kernel builds those captures measured; set to None when a kernel
+# changes.
 STEP_TRAFFIC_RATIO = 1.049
-STEP32_TRAFFIC_RATIO = 1.016
+STEP32_TRAFFIC_RATIO = {"27pt": 1.016, "7pt": 1.005}
 
 
 def _rank_device(dist):
@@ -445,10 +445,12 @@ def run_ours(args, w, rank, world, dist):
             "bound": "hbm", "achieved": step_gbs, "peak": hbm, "unit": "GB/s",
             "frac": step_gbs / hbm if step_gbs else None,
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy bandwidth, of measured)",
-            "traffic": ((STEP32_TRAFFIC_RATIO * st["bytes"] / max(st["launches"], 1))
-                        if STEP32_TRAFFIC_RATIO and w["prec"] == "ir_fp32" and w["stencil"] == "27pt" else None),
-            "traffic_source": "ncu dram bytes / algorithmic bytes of the FP32 step at 144^3 (same kernel build), "
-                              "times this run's algorithmic bytes per launch",
+            "traffic": ((STEP32_TRAFFIC_RATIO[w["stencil"]] * st["bytes"] / max(st["launches"], 1))
+                        if STEP32_TRAFFIC_RATIO and w["prec"] == "ir_fp32" else None),
+            "traffic_source": ("ncu dram bytes / algorithmic bytes of the FP32 step "
+                               + ("(single tiles) at 144^3 27-point" if w["stencil"] == "27pt"
+                                  else "(tile pairs, column ring) at 128^3 7-point")
+                               + " (same kernel build), times this run's algorithmic bytes per launch"),
             "launch_avg_ms": step_avg_ms, "launches": st["launches"],
             "alg_bytes_per_launch": st["bytes"] / max(st["launches"], 1),
             "fp32_tflops": step_tflops,
