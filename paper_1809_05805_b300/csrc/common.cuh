@@ -737,7 +737,7 @@ __device__ __forceinline__ void tile_pair_dot_rows_cols(int64_t pp, int64_t n, C
   after();
 }
 
-// The tile pair pp with the basis (FP32 or BF16) read from global memory
+// The tile pair pp with the basis (FP64, FP32 or BF16) read from global memory
 // through a per-warp ring of pf_stages<SV>() column slices in shared memory,
 // filled by per-thread asynchronous 16-byte copies pf_stages - 1 columns ahead
 // of use: the bytes in flight cost shared memory instead of registers (with
@@ -747,27 +747,28 @@ __device__ __forceinline__ void tile_pair_dot_rows_cols(int64_t pp, int64_t n, C
 // orders the ring; a slot is refilled only after the FMAs that consumed it
 // were issued. Rows >= n are zero-filled. Same sums as tile_pair_dot_rows in
 // another row order; the remainder columns are read directly as there.
-// ring: kWarps * pf_stages<SV>() * 256 values of SV (24 KB either way).
+// ring: kWarps * pf_stages<SV>() * 256 values of SV (24 KB for FP32 and BF16,
+// 48 KB for FP64).
 template <typename SV>
-__host__ __device__ constexpr int pf_stages() { return sizeof(SV) == 4 ? 3 : 6; }
+__host__ __device__ constexpr int pf_stages() { return sizeof(SV) == 2 ? 6 : 3; }
 template <typename SV>
 __host__ __device__ constexpr size_t pf_ring_bytes() { return (size_t)kWarps * pf_stages<SV>() * kThreads * sizeof(SV); }
-template <int MAXC, typename SV, typename Hook>
+template <int MAXC, typename SV, typename VT, typename Hook>
 __device__ __forceinline__ void tile_pair_dot_rows_pf(int64_t pp, int64_t n, const SV* __restrict__ V,
-                                                      int64_t ldv, bool need_w, int J8, int r8, float ur0,
-                                                      float wr0, float ur1, float wr1, float* su, float* sw,
-                                                      SV* ring, float (&acc_a)[MAXC], float (&acc_c)[MAXC],
-                                                      float (&rem_a)[kWarps - 1], float (&rem_c)[kWarps - 1],
-                                                      float& sig, float& dd, Hook hook) {
+                                                      int64_t ldv, bool need_w, int J8, int r8, VT ur0, VT wr0,
+                                                      VT ur1, VT wr1, VT* su, VT* sw, SV* ring,
+                                                      VT (&acc_a)[MAXC], VT (&acc_c)[MAXC],
+                                                      VT (&rem_a)[kWarps - 1], VT (&rem_c)[kWarps - 1], VT& sig,
+                                                      VT& dd, Hook hook) {
   constexpr int S = pf_stages<SV>();
   constexpr int R = 16 / (int)sizeof(SV);  // rows per 16-byte copy
   constexpr int NQ = kRowsPerLane / R;     // copies per lane per column half
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int64_t row0 = pp * (2 * kThreads) + threadIdx.x, row1 = row0 + kThreads;
-  sig = fmaf(ur0, ur0, sig);
-  dd = fmaf(ur0, wr0, dd);
-  sig = fmaf(ur1, ur1, sig);
-  dd = fmaf(ur1, wr1, dd);
+  sig = fma(ur0, ur0, sig);
+  dd = fma(ur0, wr0, dd);
+  sig = fma(ur1, ur1, sig);
+  dd = fma(ur1, wr1, dd);
   su[threadIdx.x] = ur0;
   sw[threadIdx.x] = wr0;
   su[kThreads + threadIdx.x] = ur1;
@@ -778,17 +779,26 @@ __device__ __forceinline__ void tile_pair_dot_rows_pf(int64_t pp, int64_t n, con
 #pragma unroll
   for (int h = 0; h < 2; ++h) {
     const int64_t hb = pp * (2 * kThreads) + h * kThreads;  // first row of the half
-    float ru[kRowsPerLane], rw[kRowsPerLane];
+    VT ru[kRowsPerLane], rw[kRowsPerLane];
 #pragma unroll
-    for (int q = 0; q < NQ; ++q)
+    for (int q = 0; q < NQ; ++q) {
+      if constexpr (sizeof(VT) == 4) {
 #pragma unroll
-      for (int e = 0; e < R; e += 4) {
-        const int o = h * kThreads + 32 * R * q + R * lane + e;
-        const float4 a = *reinterpret_cast<const float4*>(su + o);
-        const float4 b = *reinterpret_cast<const float4*>(sw + o);
-        ru[R * q + e] = a.x, ru[R * q + e + 1] = a.y, ru[R * q + e + 2] = a.z, ru[R * q + e + 3] = a.w;
-        rw[R * q + e] = b.x, rw[R * q + e + 1] = b.y, rw[R * q + e + 2] = b.z, rw[R * q + e + 3] = b.w;
+        for (int e = 0; e < R; e += 4) {
+          const int o = h * kThreads + 32 * R * q + R * lane + e;
+          const float4 a = *reinterpret_cast<const float4*>(su + o);
+          const float4 b = *reinterpret_cast<const float4*>(sw + o);
+          ru[R * q + e] = a.x, ru[R * q + e + 1] = a.y, ru[R * q + e + 2] = a.z, ru[R * q + e + 3] = a.w;
+          rw[R * q + e] = b.x, rw[R * q + e + 1] = b.y, rw[R * q + e + 2] = b.z, rw[R * q + e + 3] = b.w;
+        }
+      } else {  // FP64: two rows per copy
+        const int o = h * kThreads + 32 * R * q + R * lane;
+        const double2 a = *reinterpret_cast<const double2*>(su + o);
+        const double2 b = *reinterpret_cast<const double2*>(sw + o);
+        ru[R * q] = a.x, ru[R * q + 1] = a.y;
+        rw[R * q] = b.x, rw[R * q + 1] = b.y;
       }
+    }
     // this lane's rows of column wid + 8 c into ring slot `slot`
     auto issue = [&](int c, int slot) {
       const SV* colp = V + (size_t)(wid + c * kWarps) * ldv;
@@ -812,11 +822,14 @@ __device__ __forceinline__ void tile_pair_dot_rows_pf(int64_t pp, int64_t n, con
         cp_async_commit();
         cp_async_wait<S - 1>();  // column c's copies are done
         const SV* sl = wring + (c % S) * kThreads;
-        float x[kRowsPerLane];
+        VT x[kRowsPerLane];
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
           const uint4 v = *reinterpret_cast<const uint4*>(sl + 32 * R * q + R * lane);
-          if constexpr (sizeof(SV) == 4) {
+          if constexpr (sizeof(SV) == 8) {
+            x[R * q] = __hiloint2double((int)v.y, (int)v.x);
+            x[R * q + 1] = __hiloint2double((int)v.w, (int)v.z);
+          } else if constexpr (sizeof(SV) == 4) {
             x[R * q] = __uint_as_float(v.x), x[R * q + 1] = __uint_as_float(v.y);
             x[R * q + 2] = __uint_as_float(v.z), x[R * q + 3] = __uint_as_float(v.w);
           } else {  // BF16 widened exactly: its bits are the high half of the FP32 value
@@ -829,10 +842,10 @@ __device__ __forceinline__ void tile_pair_dot_rows_pf(int64_t pp, int64_t n, con
           }
         }
 #pragma unroll
-        for (int i = 0; i < kRowsPerLane; ++i) acc_a[c] = fmaf(x[i], ru[i], acc_a[c]);
+        for (int i = 0; i < kRowsPerLane; ++i) acc_a[c] = fma(x[i], ru[i], acc_a[c]);
         if (need_w) {
 #pragma unroll
-          for (int i = 0; i < kRowsPerLane; ++i) acc_c[c] = fmaf(x[i], rw[i], acc_c[c]);
+          for (int i = 0; i < kRowsPerLane; ++i) acc_c[c] = fma(x[i], rw[i], acc_c[c]);
         }
       }
     }
@@ -842,23 +855,23 @@ __device__ __forceinline__ void tile_pair_dot_rows_pf(int64_t pp, int64_t n, con
 #pragma unroll
   for (int c0 = 0; c0 < kWarps - 1; c0 += kRemBatch) {
     if (c0 < r8) {  // block-uniform
-      float x0[kRemBatch], x1[kRemBatch];
+      VT x0[kRemBatch], x1[kRemBatch];
 #pragma unroll
       for (int b = 0; b < kRemBatch; ++b) {
         const int c = c0 + b;
         const SV* colp = V + (size_t)(J8 * kWarps + c) * ldv;
-        x0[b] = (c < r8 && row0 < n) ? ld_as<float>(colp + row0) : 0.f;
-        x1[b] = (c < r8 && row1 < n) ? ld_as<float>(colp + row1) : 0.f;
+        x0[b] = (c < r8 && row0 < n) ? ld_as<VT>(colp + row0) : VT(0);
+        x1[b] = (c < r8 && row1 < n) ? ld_as<VT>(colp + row1) : VT(0);
       }
 #pragma unroll
       for (int b = 0; b < kRemBatch; ++b) {
         const int c = c0 + b;
         if (c < kWarps - 1 && c < r8) {
-          rem_a[c] = fmaf(x0[b], ur0, rem_a[c]);
-          rem_a[c] = fmaf(x1[b], ur1, rem_a[c]);
+          rem_a[c] = fma(x0[b], ur0, rem_a[c]);
+          rem_a[c] = fma(x1[b], ur1, rem_a[c]);
           if (need_w) {
-            rem_c[c] = fmaf(x0[b], wr0, rem_c[c]);
-            rem_c[c] = fmaf(x1[b], wr1, rem_c[c]);
+            rem_c[c] = fma(x0[b], wr0, rem_c[c]);
+            rem_c[c] = fma(x1[b], wr1, rem_c[c]);
           }
         }
       }

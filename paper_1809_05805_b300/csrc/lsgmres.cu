@@ -1166,7 +1166,8 @@ gmres_status gmres_create(const gmres_csr* A, int m_restart, double tol, gmres_h
     csr_stage_caps(rp, n, cap_tile, cap_pair);
     const int m = m_restart;
     gmres_status sst = choose_stage([m](int sg) { return step64_for(m, sg); }, sizeof(double), 2, &h->P, h->nsm,
-                                    ntiles, cap_tile, cap_pair, h->step_smem, 0, 0, h->stage64, h->cap64, h->smem64);
+                                    ntiles, cap_tile, cap_pair, h->step_smem, 0, pf_ring_bytes<double>(), h->stage64,
+                                    h->cap64, h->smem64);
     if (sst == GMRES_OK)
       // FP32 basis: no mode 3 (measured: equal at 192^3 27-point, 16% slower at 256^3
       // 7-point than three CTAs per SM reading the basis themselves); the BF16

@@ -249,9 +249,9 @@ k_one_reduce_step(const int32_t* __restrict__ rowptr, const int32_t* __restrict_
             tile_dot_rows_cols<MAXC, SV, VT>(unit, n, SharedCols<SV>{sV, U}, need_w, J8, r8, ur0, wr0, su, sw,
                                              acc_a, acc_c, rem_a, rem_c, sig, dd, next, before, after);
         } else if (STAGE == 2) {
-          if constexpr (std::is_same<VT, float>::value)
-            // FP32 or BF16 basis: the column slices stream through a per-warp
-            // ring behind the CSR buffer
+          if constexpr (true)
+            // the column slices stream through a per-warp ring behind the
+            // CSR buffer
             tile_pair_dot_rows_pf<MAXC, SV>(unit, n, V, ldv, need_w, J8, r8, ur0, wr0, ur1, wr1, su, sw,
                                             reinterpret_cast<SV*>(cs.val + stage_cap), acc_a, acc_c, rem_a, rem_c,
                                             sig, dd, next);
