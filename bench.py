@@ -87,7 +87,7 @@ FP64_DFMA_PER_CLK_SM = 2  # B300: 1.25 TFLOP/s nominal FP64 = 148 SMs x 2 DFMA/c
 # with the column ring on the 128^3 7-point one at j = 20 and 21. Valid only
 # for the kernel builds those captures measured; set to None when a kernel
 # changes.
-STEP_TRAFFIC_RATIO = None
+STEP_TRAFFIC_RATIO = 1.048
 STEP32_TRAFFIC_RATIO = {"27pt": 1.014, "7pt": 1.005}
 
 
