@@ -1031,7 +1031,8 @@ static void csr_stage_caps(const std::vector<int32_t>& rp, int64_t n, int& cap_t
 // lowered to two CTAs per SM. kernel_for(stage)
 // gives the kernel of a mode; the dynamic shared memory is the larger of the
 // epilogue's (t_smem) and the staging buffer's (plus pair_extra bytes behind
-// a tile pair's CSR in mode 2: the FP32 kernel's column ring). Sets the kernel's
+// a tile pair's CSR in mode 2: the kernel's column ring; mode 5 is the same
+// tile-pair kernel without it). Sets the kernel's
 // shared-memory limit.
 template <typename KernelFor>
 static gmres_status choose_stage(KernelFor kernel_for, size_t vb, int per_sm, int* P, int nsm, int64_t ntiles,
@@ -1039,29 +1040,32 @@ static gmres_status choose_stage(KernelFor kernel_for, size_t vb, int per_sm, in
                                  int& mode, int& cap, size_t& smem) {
   const bool pairs = ntiles >= 4 * (int64_t)*P;
   // a kernel with the column ring (pair_extra > 0) takes tile pairs at per_sm
-  // CTAs per SM first: at 256^3 7-point the BF16 basis streamed through the
-  // ring (0.523 s) beat its bulk-copy staging (mode 4, 0.583 s)
-  const int order_ring[4] = {2, 4, 3, 1}, order_bulk[4] = {4, 3, 2, 1};
+  // CTAs per SM first (at 256^3 7-point the BF16 basis streamed through the
+  // ring, 0.523 s, beat its bulk-copy staging, mode 4, 0.583 s), then tile
+  // pairs without the ring (mode 5: where the pair CSR leaves no room for it)
+  const int order_ring[5] = {2, 5, 4, 3, 1}, order_bulk[5] = {4, 3, 2, 1, 0};
   for (int cand : (pair_extra > 0 ? order_ring : order_bulk)) {
+    if (cand == 0) continue;
+    const bool sv = cand == 3 || cand == 4;  // basis columns staged too
     // staged basis: at least 4 tiles per CTA at two CTAs per SM
-    if (cand >= 3 && (v3_bytes == 0 || ntiles < 4 * 2 * (int64_t)nsm)) continue;
-    if (cand == 2 && !pairs) continue;
-    const bool pr = cand == 2 || cand == 4;
+    if (sv && (v3_bytes == 0 || ntiles < 4 * 2 * (int64_t)nsm)) continue;
+    if ((cand == 2 || cand == 5) && !pairs) continue;
+    const bool pr = cand == 2 || cand == 4 || cand == 5;
     const int U = pr ? 2 * kThreads : kThreads;
     const int c = pr ? cap_pair : cap_tile;
     const size_t need = std::max(t_smem, (size_t)(U + 4) * 4 + (size_t)c * (4 + vb) +
-                                             (cand >= 3 ? (pr ? 2 : 1) * v3_bytes : 0) + (cand == 2 ? pair_extra : 0));
+                                             (sv ? (pr ? 2 : 1) * v3_bytes : 0) + (cand == 2 ? pair_extra : 0));
     if (need > 200 * 1024) continue;
     const void* k = reinterpret_cast<const void*>(kernel_for(cand));
     if (raise_smem_limit(k, need) != cudaSuccess)
       return GMRES_ERR_CUDA;
     int nb = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, kThreads, need) != cudaSuccess) return GMRES_ERR_CUDA;
-    if (nb >= (cand >= 3 ? 2 : per_sm)) {
+    if (nb >= (sv ? 2 : per_sm)) {
       mode = cand;
       cap = c;
       smem = need;
-      if (cand >= 3) *P = (int)std::min<int64_t>(2 * (int64_t)nsm, cand == 4 ? (ntiles + 1) / 2 : ntiles);
+      if (sv) *P = (int)std::min<int64_t>(2 * (int64_t)nsm, cand == 4 ? (ntiles + 1) / 2 : ntiles);
       return GMRES_OK;
     }
   }

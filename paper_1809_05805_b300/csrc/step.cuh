@@ -10,31 +10,41 @@
 
 namespace lsg_steps {
 // Host stub of the step kernel for restart length m and staging mode (0 off,
-// 1 tiles, 2 tile pairs, 3 tiles with their basis columns, 4 tile pairs with
-// theirs; 3 and 4 for the BF16 basis only); callers cast it to their
-// StepKernel type.
+// 1 tiles, 2 tile pairs with the block dot's column ring, 3 tiles with their
+// basis columns, 4 tile pairs with theirs, 5 tile pairs without the ring; 3
+// and 4 for the BF16 basis only); callers cast it to their StepKernel type.
 const void* step_kernel_f64_s0(int m);
 const void* step_kernel_f64_s1(int m);
 const void* step_kernel_f64_s2(int m);
+const void* step_kernel_f64_s5(int m);
 const void* step_kernel_f32_s0(int m);
 const void* step_kernel_f32_s1(int m);
 const void* step_kernel_f32_s2(int m);
+const void* step_kernel_f32_s5(int m);
 const void* step_kernel_bf16_s0(int m);
 const void* step_kernel_bf16_s1(int m);
 const void* step_kernel_bf16_s2(int m);
+const void* step_kernel_bf16_s5(int m);
 const void* step_kernel_bf16_s3(int m);
 const void* step_kernel_bf16_s4(int m);
 // Modes 3 and 4 are built for the BF16 basis only: the FP64 basis tile does not fit
 // beside two resident CTAs, and FP32 cycles ran faster at three CTAs per SM
 // reading the basis themselves than at two with it staged.
 inline const void* step_kernel_f64(int m, int stage) {
-  return stage == 2 ? step_kernel_f64_s2(m) : stage == 1 ? step_kernel_f64_s1(m) : step_kernel_f64_s0(m);
+  return stage == 5   ? step_kernel_f64_s5(m)
+         : stage == 2 ? step_kernel_f64_s2(m)
+         : stage == 1 ? step_kernel_f64_s1(m)
+                      : step_kernel_f64_s0(m);
 }
 inline const void* step_kernel_f32(int m, int stage) {
-  return stage == 2 ? step_kernel_f32_s2(m) : stage == 1 ? step_kernel_f32_s1(m) : step_kernel_f32_s0(m);
+  return stage == 5   ? step_kernel_f32_s5(m)
+         : stage == 2 ? step_kernel_f32_s2(m)
+         : stage == 1 ? step_kernel_f32_s1(m)
+                      : step_kernel_f32_s0(m);
 }
 inline const void* step_kernel_bf16(int m, int stage) {
-  return stage == 4   ? step_kernel_bf16_s4(m)
+  return stage == 5   ? step_kernel_bf16_s5(m)
+         : stage == 4 ? step_kernel_bf16_s4(m)
          : stage == 3 ? step_kernel_bf16_s3(m)
          : stage == 2 ? step_kernel_bf16_s2(m)
          : stage == 1 ? step_kernel_bf16_s1(m)
@@ -55,7 +65,7 @@ using StepKernel = void (*)(const int32_t*, const int32_t*, const VT*, const SV*
 // the 192^3 27-point GMRES-IR solve: 2.9 -> 3.4 TB/s; four per SM spill and
 // lose).
 template <int MAXC, typename VT, typename SV = VT, int STAGE = 0>
-__global__ void __launch_bounds__(kThreads, (sizeof(VT) == 4 && STAGE < 3) ? 3 : 2)
+__global__ void __launch_bounds__(kThreads, (sizeof(VT) == 4 && STAGE != 3 && STAGE != 4) ? 3 : 2)
 k_one_reduce_step(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                   const VT* __restrict__ val, const SV* __restrict__ V, int64_t ldv,
                   const SV* __restrict__ u_arg, VT* __restrict__ w, int64_t n, Small s,
@@ -84,7 +94,7 @@ k_one_reduce_step(const int32_t* __restrict__ rowptr, const int32_t* __restrict_
   if (s_skip) return;
   // STAGES 3 and 4 copy basis columns of the handle's own basis; the
   // standalone block dot (raw_out) never runs them
-  if (STAGE >= 3 && raw_out) return;
+  if ((STAGE == 3 || STAGE == 4) && raw_out) return;
   const int j = s_j;
   const bool tail = s_tail;
   const bool spmv = raw_out ? (use_spmv != 0) : !tail;
@@ -106,17 +116,17 @@ k_one_reduce_step(const int32_t* __restrict__ rowptr, const int32_t* __restrict_
 
   const int64_t ntiles = (n + kThreads - 1) / kThreads;
   if constexpr (STAGE != 0) {
-    // Staged CSR (STAGE 1: one tile per unit, 2: tile pairs; 3: one tile per
-    // unit, and the tile's basis columns too; 4: tile pairs and their basis
-    // columns): the bulk-copy engine fetches the next unit's rowptr slice,
+    // Staged CSR (STAGE 1: one tile per unit, 2: tile pairs, 5: the same
+    // without the block dot's column ring; 3: one tile per unit, and the
+    // tile's basis columns too; 4: tile pairs and their basis columns): the bulk-copy engine fetches the next unit's rowptr slice,
     // indices and values into shared memory while this one's block dot runs
     // (and, for STAGES 3 and 4, the next unit's basis columns while this
     // one's SpMV runs). The global CSR is never
     // read by this instantiation: a unit whose copy did not arrive in time, or
     // that does not fit the buffer (the host sizes it for the largest unit),
     // sets the stalled flag and contributes a zero SpMV.
-    constexpr bool kPairs = STAGE == 2 || STAGE == 4;  // units of two tiles
-    constexpr bool kStageV = STAGE >= 3;              // basis columns staged too
+    constexpr bool kPairs = STAGE == 2 || STAGE == 4 || STAGE == 5;  // units of two tiles
+    constexpr bool kStageV = STAGE == 3 || STAGE == 4;               // basis columns staged too
     const int U = kPairs ? 2 * kThreads : kThreads;
     const int64_t units = (n + U - 1) / U;
     if (spmv) {
@@ -248,8 +258,8 @@ k_one_reduce_step(const int32_t* __restrict__ rowptr, const int32_t* __restrict_
           else
             tile_dot_rows_cols<MAXC, SV, VT>(unit, n, SharedCols<SV>{sV, U}, need_w, J8, r8, ur0, wr0, su, sw,
                                              acc_a, acc_c, rem_a, rem_c, sig, dd, next, before, after);
-        } else if (STAGE == 2) {
-          if constexpr (true)
+        } else if (kPairs) {
+          if constexpr (STAGE == 2)
             // the column slices stream through a per-warp ring behind the
             // CSR buffer
             tile_pair_dot_rows_pf<MAXC, SV>(unit, n, V, ldv, need_w, J8, r8, ur0, wr0, ur1, wr1, su, sw,

@@ -122,3 +122,26 @@ def test_handles_of_different_shapes_interleave(torch_cuda, lsg):
         info = s.solve(torch.from_numpy(b).cuda(), x)
         assert info.status == 0
         assert np.linalg.norm(b - P.to_scipy(A) @ x.cpu().numpy()) <= 1e-8 * np.linalg.norm(b)
+
+
+def test_dense_row_pairs_without_ring_match_oracle(torch_cuda, lsg, orc):
+    """A 2D 9-point problem of 360,000 rows (1,407 tiles, enough for tile pairs
+    at two CTAs per SM): its tile pair's CSR (4,608 entries, 57 KB in FP64)
+    leaves no room beside it for the 48 KB column ring at two CTAs per SM, so
+    the FP64 step kernel takes tile pairs without the ring (staging mode 5).
+    Two cycles of GMRES(30) against the oracle, step by step."""
+    torch = torch_cuda
+    N = 600
+    kc = np.exp(np.random.default_rng(7).uniform(np.log(0.1), np.log(10.0), (N + 1, N + 1)))
+    A = P.conv_diff_9pt_2d(N, kc, 0.7, 1.0)
+    n = N * N
+    _, b = P.rhs(A, seed=3)
+    s = lsg.Solver(A, m=30, tol=1e-14, max_iter=60)
+    assert s.test_stall_staging(False)  # the FP64 step kernel stages this matrix
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    info = s.solve(torch.from_numpy(b).cuda(), x)
+    r = orc.gmres(A, b, variant=1, m=30, tol=1e-14, max_iter=60)
+    assert info.status == r.status and info.iters == r.iters == 60
+    hist = s.history()
+    assert np.all(np.abs(hist[:60] - r.history[:60]) <= 1e-8 * r.history[:60] + 1e-15)
+    assert np.linalg.norm(x.cpu().numpy() - r.x) <= 1e-9 * np.linalg.norm(r.x)
