@@ -26,7 +26,8 @@
  *                         convergence test after every second column.
  *
  * All schemes run on the same kernels (CSR SpMV, multi-column dot, MAXPY) on
- * one GPU. All arithmetic on the solve path is FP64 (except GMRES_IR_FP32).
+ * one GPU. All arithmetic on the solve path is FP64, except in the GMRES-IR
+ * precisions (GMRES_IR_FP32, GMRES_IR_BF16), whose restart cycles run in FP32.
  *
  * Conventions for every entry point:
  *   - Every call returns a gmres_status; no call aborts or exits. After an
@@ -157,8 +158,11 @@ gmres_status gmres_history(gmres_handle h, double* host_buf, int cap, int* len);
 /* Release all device and host memory of h. NULL is accepted. */
 gmres_status gmres_destroy(gmres_handle h);
 
-/* Description of the last error on h (or of the last failed gmres_create when
- * h is NULL). The string is owned by the library. */
+/* Description of the last error on h. With h = NULL: the last error of a call
+ * that has no handle (a failed gmres_create, lsg_block_dot_noalloc) made by
+ * the calling host thread; each host thread has its own such message. The
+ * string is owned by the library and stays valid until the next failing call
+ * on the same handle (or, for NULL, by the same thread). */
 const char* gmres_last_error(gmres_handle h);
 
 /* Per-kernel timing. With on = 1, later solves bracket every kernel launch
@@ -276,7 +280,8 @@ gmres_status gmres_batch_history(gmres_batch bt, int i, double* host_buf, int ca
 
 gmres_status gmres_batch_destroy(gmres_batch bt);
 
-/* Description of the last error on bt (or of the last failed gmres_batch_create when NULL). */
+/* Description of the last error on bt (or, with NULL, of the calling host
+ * thread's last failed gmres_batch_create). */
 const char* gmres_batch_last_error(gmres_batch bt);
 
 /* ------------------------------------------------------------------------
@@ -371,6 +376,8 @@ gmres_status gmres_server_latencies(gmres_server sv, double* buf, int cap, int* 
  * admitted run to completion first. */
 gmres_status gmres_server_destroy(gmres_server sv);
 
+/* Description of the last error on sv (or, with NULL, of the calling host
+ * thread's last failed gmres_server_create). */
 const char* gmres_server_last_error(gmres_server sv);
 
 /* ------------------------------------------------------------------------
@@ -434,6 +441,48 @@ gmres_status lsg_maxpy(gmres_handle h, const double* V, int64_t ldv, int K, cons
  * number of columns completed (< k only after a breakdown). */
 gmres_status gmres_arnoldi(gmres_handle h, const double* r0, int k, double* V_out,
                            double* H_out, double* T_out, int* k_done);
+
+/* ------------------------------------------------------------------------
+ * Instruction-throughput probe (measurement only).
+ * ------------------------------------------------------------------------
+ * The paper has no counterpart. On B300 the FP64 Arnoldi step is bound by the
+ * FP64 pipe rather than by HBM, so the roofline it is reported against is a
+ * measured instruction rate; these calls measure it, and the rates of the
+ * integer and conversion instructions an FP64 product can be emulated with.
+ * lsg_probe_pipe launches ctas_per_sm x (SM count) CTAs of 256 threads on the
+ * current device (legacy default stream; it synchronizes), each thread
+ * running 8 independent chains of `iters` x 4 instructions of kind `op` and
+ * nothing else, and reports per-SM and whole-GPU rates. It allocates and
+ * frees a few KB of device memory per call. 1 <= ctas_per_sm <= 8,
+ * 1 <= iters <= 2^24. Errors: GMRES_ERR_ARG, GMRES_ERR_CUDA, described by
+ * lsg_probe_last_error() (per host thread). */
+typedef enum {
+  LSG_PROBE_DFMA = 0,        /* fma.rn.f64 */
+  LSG_PROBE_DADD = 1,        /* add.rn.f64 */
+  LSG_PROBE_FFMA = 2,        /* fma.rn.f32 */
+  LSG_PROBE_IMAD = 3,        /* mad.lo.u32 */
+  LSG_PROBE_IMAD_WIDE = 4,   /* mad.wide.u32: 32 x 32 + 64 -> 64 bits */
+  LSG_PROBE_IMAD_HI = 5,     /* mad.hi.u32 */
+  LSG_PROBE_IADD = 6,        /* add.u32 */
+  LSG_PROBE_LOP3 = 7,        /* lop3.b32 */
+  LSG_PROBE_SHF = 8,         /* shf.l.wrap.b32 (funnel shift) */
+  LSG_PROBE_I2F_F64 = 9,     /* cvt.rn.f64.s64 */
+  LSG_PROBE_F2I_F64 = 10,    /* cvt.rni.s64.f64 */
+  LSG_PROBE_F2F_F32_F64 = 11,/* cvt.rn.f32.f64 */
+  LSG_PROBE_I2F_F32 = 12,    /* cvt.rn.f32.s32 */
+  LSG_PROBE_FLO = 13         /* clz.b32 */
+} lsg_probe_op;
+
+typedef struct {
+  double ops_per_clk_per_sm; /* thread instructions retired per SM clock (from clock64 stamps) */
+  double ops_per_s;          /* thread instructions per second, whole GPU (CUDA events) */
+  double sm_mhz;             /* SM clock during the run: clock64 cycles / event time */
+  double seconds;            /* device time of the timed launch */
+  int sms;                   /* SM count */
+} lsg_probe_result;
+
+gmres_status lsg_probe_pipe(int op, int ctas_per_sm, int iters, lsg_probe_result* out);
+const char* lsg_probe_last_error(void);
 
 #ifdef __cplusplus
 }

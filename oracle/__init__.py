@@ -29,9 +29,14 @@ MGS, ONE_REDUCE, IR_FP32, CGS2, PIPE2, IR_BF16 = 0, 1, 2, 3, 4, 5
 CFLAGS = ["-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-std=c99"]
 
 
+_LIB_OMP = os.path.join(_HERE, "liboracle_omp.so")
+OMP_FLAGS = ["-fopenmp", "-DORC_OMP"]
+
+
 def build(src: str = _SRC, out: str = _LIB, extra: list[str] | None = None) -> str:
     """Compile oracle.c into a shared library (idempotent; rebuilds when stale)."""
-    if os.path.exists(out) and os.path.getmtime(out) >= os.path.getmtime(src) and not extra:
+    fresh = os.path.exists(out) and os.path.getmtime(out) >= os.path.getmtime(src)
+    if fresh and (not extra or out == _LIB_OMP):
         return out
     cmd = ["gcc", *CFLAGS, *(extra or []), src, "-o", out + ".tmp", "-lm"]
     subprocess.run(cmd, check=True, capture_output=True, text=True)
@@ -82,6 +87,9 @@ class Oracle:
             ctypes.POINTER(ctypes.c_int),
         ]
         lib.orc_gmres.restype = ctypes.c_int
+        lib.orc_threads.argtypes = []
+        lib.orc_threads.restype = ctypes.c_int
+        self.threads = lib.orc_threads()
         lib.orc_round_bf16.argtypes = [ctypes.c_float]
         lib.orc_round_bf16.restype = ctypes.c_float
         self.lib = lib
@@ -217,3 +225,16 @@ def get() -> Oracle:
     if _DEFAULT is None:
         _DEFAULT = Oracle()
     return _DEFAULT
+
+
+_OMP = None
+
+
+def get_omp() -> Oracle:
+    """The same oracle.c built with OpenMP (-DORC_OMP -fopenmp): its vector
+    loops run on all host cores (OMP_NUM_THREADS, default all). For timing the
+    CPU baseline only; its sums are reordered, so it is never the checker."""
+    global _OMP
+    if _OMP is None:
+        _OMP = Oracle(build(out=_LIB_OMP, extra=OMP_FLAGS))
+    return _OMP

@@ -76,6 +76,29 @@
 #define ORC_VARIANT_PIPE2 4
 #define ORC_VARIANT_IR_BF16 5
 
+/* Timing build only: compiled with -DORC_OMP -fopenmp, the plain vector loops
+ * below are shared out over the host's cores (each sum by an OpenMP
+ * reduction, so its order changes), to time the oracle on all cores for the
+ * CPU baseline. The checker is built without ORC_OMP: these macros are then
+ * empty and every loop stays sequential. */
+#ifdef ORC_OMP
+#include <omp.h>
+#define ORC_PAR_FOR _Pragma("omp parallel for schedule(static)")
+#define ORC_PAR_SUM_S _Pragma("omp parallel for schedule(static) reduction(+ : s)")
+#else
+#define ORC_PAR_FOR
+#define ORC_PAR_SUM_S
+#endif
+
+/* Host threads the vector loops use (1 unless built with ORC_OMP). */
+int orc_threads(void) {
+#ifdef ORC_OMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
 /* Breakdown threshold factor [A6]: the new direction is declared exhausted
  * when its norm is below BREAKDOWN_FACTOR * eps * ||Hbar(:, j)||. */
 #define BREAKDOWN_FACTOR 16.0
@@ -87,6 +110,7 @@
 /* y = A x, A in compressed-sparse-row form (rowptr[n+1], col[nnz], val[nnz]). */
 void orc_spmv(int64_t n, const int32_t* rowptr, const int32_t* col, const double* val,
               const double* x, double* y) {
+  ORC_PAR_FOR
   for (int64_t i = 0; i < n; ++i) {
     double s = 0.0;
     for (int64_t p = rowptr[i]; p < rowptr[i + 1]; ++p) s += val[p] * x[col[p]];
@@ -96,6 +120,7 @@ void orc_spmv(int64_t n, const int32_t* rowptr, const int32_t* col, const double
 
 static double dot(int64_t n, const double* x, const double* y) {
   double s = 0.0;
+  ORC_PAR_SUM_S
   for (int64_t i = 0; i < n; ++i) s += x[i] * y[i];
   return s;
 }
@@ -110,6 +135,7 @@ double orc_dot(int64_t n, const double* x, const double* y) { return dot(n, x, y
  * with leading dimension ldv, written term by term in column order. */
 void orc_maxpy(int64_t n, int K, const double* V, int64_t ldv, const double* c, double alpha,
                const double* y_in, double* y_out) {
+  ORC_PAR_FOR
   for (int64_t i = 0; i < n; ++i) {
     double t = alpha * y_in[i];
     for (int k = 0; k < K; ++k) t += c[k] * V[i + (size_t)k * ldv];
@@ -119,11 +145,13 @@ void orc_maxpy(int64_t n, int K, const double* V, int64_t ldv, const double* c, 
 
 /* y = y + alpha x */
 static void axpy(int64_t n, double alpha, const double* x, double* y) {
+  ORC_PAR_FOR
   for (int64_t i = 0; i < n; ++i) y[i] += alpha * x[i];
 }
 
 /* x = alpha x */
 static void scal(int64_t n, double alpha, double* x) {
+  ORC_PAR_FOR
   for (int64_t i = 0; i < n; ++i) x[i] *= alpha;
 }
 
@@ -604,6 +632,7 @@ static cycle_out cycle_one_reduce(cycle_ws* ws, int kmax, double beta0, double b
 
 static void spmv_f32(int64_t n, const int32_t* rowptr, const int32_t* col, const float* val32,
                      const float* x, float* y) {
+  ORC_PAR_FOR
   for (int64_t i = 0; i < n; ++i) {
     float s = 0.0f;
     for (int64_t p = rowptr[i]; p < rowptr[i + 1]; ++p) s += val32[p] * x[col[p]];
@@ -613,6 +642,7 @@ static void spmv_f32(int64_t n, const int32_t* rowptr, const int32_t* col, const
 
 static float dot_f32(int64_t n, const float* x, const float* y) {
   float s = 0.0f;
+  ORC_PAR_SUM_S
   for (int64_t i = 0; i < n; ++i) s += x[i] * y[i];
   return s;
 }

@@ -1226,7 +1226,7 @@ struct gmres_batch_ctx {
 
 namespace {
 
-std::string g_batch_err;
+thread_local std::string g_batch_err;  // handle-less errors, one string per host thread
 
 gmres_status bfail(gmres_batch_ctx* b, gmres_status st, const std::string& msg) {
   if (b)
@@ -1492,7 +1492,7 @@ struct gmres_server_ctx {
 
 namespace {
 
-std::string g_server_err;
+thread_local std::string g_server_err;  // handle-less errors, one string per host thread
 
 gmres_status sfail(gmres_server_ctx* sv, gmres_status st, const std::string& m) {
   if (sv)

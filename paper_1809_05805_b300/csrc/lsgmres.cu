@@ -640,7 +640,9 @@ struct gmres_ctx {
 
 namespace {
 
-std::string g_create_err;
+// Handle-less errors (failed create, the no-alloc entry point): one string per
+// host thread, so concurrent callers never share or tear it.
+thread_local std::string g_create_err;
 
 // Device address of g_noalloc_scratch, looked up once per device (the host
 // symbol is only a stand-in and must never be passed to a kernel).

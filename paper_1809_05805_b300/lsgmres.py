@@ -63,6 +63,15 @@ class _ServerCounters(ctypes.Structure):
                 ("wall_seconds", ctypes.c_double)]
 
 
+class _ProbeResult(ctypes.Structure):
+    _fields_ = [("ops_per_clk_per_sm", ctypes.c_double), ("ops_per_s", ctypes.c_double), ("sm_mhz", ctypes.c_double),
+                ("seconds", ctypes.c_double), ("sms", ctypes.c_int)]
+
+
+PROBE_OPS = ["dfma", "dadd", "ffma", "imad", "imad_wide", "imad_hi", "iadd", "lop3", "shf", "i2f_f64", "f2i_f64",
+             "f2f_f32_f64", "i2f_f32", "flo"]
+
+
 @dataclass
 class SolveInfo:
     status: int
@@ -86,7 +95,8 @@ EXPORTS = ["gmres_create", "gmres_set", "gmres_set_tol", "gmres_set_stream", "gm
            "gmres_batch_history", "gmres_batch_destroy", "gmres_batch_last_error", "gmres_server_create",
            "gmres_server_submit", "gmres_server_poll", "gmres_server_wait", "gmres_server_drain",
            "gmres_server_release", "gmres_server_stats", "gmres_server_latencies", "gmres_server_destroy",
-           "gmres_server_last_error", "gmres_server_set_profile", "gmres_server_profile"]
+           "gmres_server_last_error", "gmres_server_set_profile", "gmres_server_profile", "lsg_probe_pipe",
+           "lsg_probe_last_error"]
 
 PROFILE_CLASSES = ["one_reduce_step", "arnoldi_maxpy", "mgs_spmv_dot", "mgs_axpy_dot", "residual",
                    "least_squares", "x_update", "noop", "reorth_dot", "reorth_maxpy"]
@@ -150,6 +160,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "gmres_server_set_profile": ([P, I], I),
         "gmres_server_profile": ([P, I, I, ctypes.POINTER(D), ctypes.POINTER(I64), ctypes.POINTER(D),
                                   ctypes.POINTER(D)], I),
+        "lsg_probe_pipe": ([I, I, I, ctypes.POINTER(_ProbeResult)], I),
+        "lsg_probe_last_error": ([], ctypes.c_char_p),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -311,6 +323,18 @@ def block_dot_noalloc(A_dev, n: int, V, ldv: int, j: int, u, w, X, use_spmv: boo
                                    int(use_spmv), _ptr(X), None if stream is None else int(stream.cuda_stream))
     if st != OK:
         raise GmresError(st, lib.gmres_last_error(None).decode())
+
+
+def probe_pipe(op: str, ctas_per_sm: int = 2, iters: int = 4096) -> dict:
+    """lsg_probe_pipe: measured rate of one instruction kind on the current
+    device (thread instructions per SM clock and per second, the SM clock)."""
+    lib = load()
+    r = _ProbeResult()
+    st = lib.lsg_probe_pipe(PROBE_OPS.index(op), ctas_per_sm, iters, ctypes.byref(r))
+    if st != OK:
+        raise GmresError(st, lib.lsg_probe_last_error().decode())
+    return {"op": op, "ops_per_clk_per_sm": r.ops_per_clk_per_sm, "ops_per_s": r.ops_per_s, "sm_mhz": r.sm_mhz,
+            "seconds": r.seconds, "sms": r.sms}
 
 
 class BatchSolver:

@@ -6,7 +6,7 @@ history. The GPU solve of the same seeded inputs is compared against these
 files, and bench.py's reference arm scales its bounded oracle sample by the
 recorded step profile. Nothing here touches the CUDA library.
 
-Usage:  python tests/golden/make_oracle_profiles.py [c1] [c2_one_reduce] [c2_mgs] [c3_ir]
+Usage:  python tests/golden/make_oracle_profiles.py [c1] [c2_one_reduce] [c2_mgs] [c3_ir] [c3_fp64]
 (c2 and c3 run the full 256^3 / 192^3 solves single-threaded: tens of minutes.)
 """
 import os
@@ -29,6 +29,9 @@ WORKLOADS = {
     "c2_mgs": dict(N=256, m=50, tol=1e-8, max_iter=3000, variant=oracle.MGS),
     # GMRES-IR (FP32 cycles inside FP64 restarts) on the 192^3 27-point problem
     "c3_ir": dict(N=192, m=40, tol=1e-10, max_iter=5000, variant=2, stencil="27pt"),
+    # the same 192^3 27-point system solved by FP64 one-reduce MGS-GMRES (Algorithm 7):
+    # the fixed point against which the GMRES-IR solutions' error is stated
+    "c3_fp64": dict(N=192, m=40, tol=1e-10, max_iter=5000, variant=oracle.ONE_REDUCE, stencil="27pt"),
 }
 VARIANT_NAMES = {0: "mgs", 1: "one_reduce", 2: "ir_fp32"}
 
