@@ -22,6 +22,17 @@ GMRES-IR, each to 1e-8) served by one continuous-batching server; reports
 solves/s and p50/p99 latency, a run at half the measured capacity, and the
 same requests one at a time on the single-system solver.
 
+The default run (256^3, one GPU) then measures the other configurations in the
+same process and reports each under "legs", with its own timing, roofline,
+clocks and CPU baseline: 32^3 GMRES(30) (latency-bound), the 192^3 27-point
+GMRES-IR solve (FP32 and BF16 basis, FP64 one-reduce beside them, errors
+against the FP64 oracle's stored solve), batch512, and the serving loop with a
+sweep of sustained arrival rates (--no-legs skips them).
+
+The FP64 kernels' roofline is the FP64 pipe's rate measured by the library's
+instruction-throughput probe (lsg_probe_pipe) in the same run; the CPU
+baselines time the oracle on one host thread and on all host cores.
+
 Prints one JSON line (rank 0). With N > 1 (torchrun) every rank solves its own
 replica of the system (no data-path collective); the time is the maximum
 over ranks. The reference arm (--impl reference) times the FP64 CPU oracle on
@@ -50,7 +61,8 @@ WORKLOADS = {
     128: dict(N=128, m=50, tol=1e-8, max_iter=3000, stencil="7pt", prec="fp64", compare="mgs"),  # profiling size
     32: dict(N=32, m=30, tol=1e-8, max_iter=300, stencil="7pt", prec="fp64", compare="mgs"),
     # 27-point anisotropic diffusion, GMRES-IR (FP32 cycles) against FP64 one-reduce
-    192: dict(N=192, m=40, tol=1e-10, max_iter=5000, stencil="27pt", prec="ir_fp32", compare="fp64"),
+    192: dict(N=192, m=40, tol=1e-10, max_iter=5000, stencil="27pt", prec="ir_fp32", compare="fp64",
+              golden_fp64="c3_fp64"),
     144: dict(N=144, m=40, tol=1e-10, max_iter=5000, stencil="27pt", prec="ir_fp32", compare="fp64"),  # profiling
     # the 256^3 7-point problem of the headline, solved by GMRES-IR (FP32 cycles)
     "256ir": dict(N=256, m=50, tol=1e-8, max_iter=3000, stencil="7pt", prec="ir_fp32", compare="fp64"),
@@ -68,9 +80,11 @@ METRIC_BATCH = "time-to-solve (1e-8 rel. resid) of a batch of uneven systems, ba
 # 70% FP64 / 30% GMRES-IR, each to 1e-8, one continuous-batching server
 SERVE_WORKLOADS = {
     "serve": dict(rate=2000.0, requests=256, n_range=(4096, 2_000_000), sides=16, ir_frac=0.3, m=30, tol=1e-8,
-                  max_iter=3000, budget=64 << 30, max_requests=256, seed=0),
+                  max_iter=3000, budget=64 << 30, max_requests=256, seed=0,
+                  sweep=(0.25, 0.5, 0.75, 1.0, 1.25), sweep_s=10.0),
     "serve_small": dict(rate=2000.0, requests=48, n_range=(4096, 262_144), sides=8, ir_frac=0.3, m=30, tol=1e-8,
-                        max_iter=3000, budget=16 << 30, max_requests=64, seed=0),  # profiling size
+                        max_iter=3000, budget=16 << 30, max_requests=64, seed=0,
+                        sweep=(0.5, 1.0), sweep_s=2.0),  # profiling size
 }
 METRIC_SERVE = "solves/s at 2000 req/s offered (1e-8 rel. resid each), continuous-batching serving loop; p50/p99 latency"
 METRIC = "time-to-solve (1e-8 rel. resid), one-reduce MGS-GMRES"
@@ -194,6 +208,33 @@ def load_peaks():
         return {}
 
 
+_FP64_PEAK = None
+
+
+def fp64_peak():
+    """The FP64 pipe's measured rate on this device (lsg_probe_pipe: DFMA chains
+    on every SM, nothing else issued; the best of a few launch shapes), as
+    TFLOP/s (2 flops per DFMA), with the derived nominal figure beside it."""
+    global _FP64_PEAK
+    if _FP64_PEAK is None:
+        from paper_1809_05805_b300 import lsgmres
+
+        best = None
+        for cps in (2, 4):
+            r = lsgmres.probe_pipe("dfma", ctas_per_sm=cps, iters=4096)
+            if best is None or r["ops_per_s"] > best["ops_per_s"]:
+                best = r
+        peaks = load_peaks()
+        _FP64_PEAK = {
+            "tflops": 2 * best["ops_per_s"] / 1e12, "dfma_per_clk_per_sm": best["ops_per_clk_per_sm"],
+            "probe_sm_mhz": best["sm_mhz"],
+            "nominal_tflops": best["sms"] * FP64_DFMA_PER_CLK_SM * 2 * float(peaks.get("sm_max_mhz", 2032.0)) / 1e6,
+            "source": "measured: lsg_probe_pipe DFMA (independent fma.rn.f64 chains on every SM, CUDA events; "
+                      "best of 2 and 4 CTAs/SM); nominal = SMs x 2 DFMA/clk x 2 flop x max SM clock",
+        }
+    return _FP64_PEAK
+
+
 def cycle_profile(total_iters, m):
     """Columns per cycle of a solve with `total_iters` steps and restart m (all cycles full but the last)."""
     ks = [m] * (total_iters // m)
@@ -227,19 +268,51 @@ def cpu_baseline(A, b, w, ks_full, sample_iters):
     import oracle
 
     n, nnz = len(A[0]) - 1, len(A[1])
-    o = oracle.get()
-    t0 = time.perf_counter()
     variant = oracle.IR_FP32 if w["prec"] == "ir_fp32" else oracle.ONE_REDUCE
-    r = o.gmres(A, b, variant=variant, m=w["m"], tol=0.0, max_iter=sample_iters)
-    dt = time.perf_counter() - t0
-    est = dt * oracle_solve_bytes(n, nnz, ks_full) / oracle_solve_bytes(n, nnz, [r.iters])
-    return {"value": est, "unit": "s", "cores": 1, "kind": "oracle",
-            "sample": (f"first {r.iters} Arnoldi steps (+ tail, residual, update) of "
-                       f"{'GMRES-IR' if w['prec'] == 'ir_fp32' else 'one-reduce GMRES'}({w['m']}) "
-                       f"on the same {w['N']}^3 system, FP64 C oracle on 1 host thread, {dt:.2f} s, scaled to the "
-                       f"full solve ({sum(ks_full)} steps, {len(ks_full)} cycles) by a model of the oracle's "
-                       f"memory traffic"),
-            "sample_seconds": dt}
+    scale = oracle_solve_bytes(n, nnz, ks_full) / oracle_solve_bytes(n, nnz, [min(sample_iters, sum(ks_full))])
+    out = None
+    for o in (oracle.get(), oracle.get_omp()):
+        t0 = time.perf_counter()
+        r = o.gmres(A, b, variant=variant, m=w["m"], tol=0.0, max_iter=sample_iters)
+        dt = time.perf_counter() - t0
+        entry = {"value": dt * scale, "unit": "s", "cores": o.threads, "kind": "oracle",
+                 "sample": (f"first {r.iters} Arnoldi steps (+ tail, residual, update) of "
+                            f"{'GMRES-IR' if w['prec'] == 'ir_fp32' else 'one-reduce GMRES'}({w['m']}) "
+                            f"on the same {w['N']}^3 system, FP64 C oracle on {o.threads} host thread(s), "
+                            f"{dt:.2f} s, scaled to the full solve ({sum(ks_full)} steps, {len(ks_full)} cycles) "
+                            f"by a model of the oracle's memory traffic"),
+                 "sample_seconds": dt}
+        if out is None:
+            out = entry
+        else:
+            entry["build"] = "oracle.c with -DORC_OMP -fopenmp (its vector loops on all host cores; timing only)"
+            out["all_cores"] = entry
+    return out
+
+
+def _oracle_solve_job(job):
+    """Worker of the all-core CPU baseline: one complete oracle solve (1 thread)."""
+    from oracle import Oracle
+
+    A, b, variant, m, tol, max_iter = job
+    r = Oracle().gmres(A, b, variant=variant, m=m, tol=tol, max_iter=max_iter)
+    return r.iters
+
+
+def pool_oracle_solves(jobs):
+    """Wall time of the independent oracle solves `jobs` run on all host cores
+    (one spawned process per core, each solve on one thread; spawn, so no
+    process forks after the CUDA context exists). Returns (seconds, cores)."""
+    import multiprocessing as mp
+
+    cores = os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        pool.map(_oracle_solve_job, jobs[:1])  # workers started and warm before timing
+        t0 = time.perf_counter()
+        pool.map(_oracle_solve_job, jobs, chunksize=1)
+        dt = time.perf_counter() - t0
+    return dt, cores
 
 
 def golden_profile(name):
@@ -256,41 +329,105 @@ def golden_profile(name):
     return out
 
 
+def golden_vectors(name):
+    """All entries of an oracle profile, vectors (history, x samples) as arrays; None if absent."""
+    path = os.path.join(ROOT, "tests", "golden", f"oracle_profile_{name}.txt")
+    if not os.path.exists(path):
+        return None
+    out = {}
+    with open(path) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            k, v = line.split(" ", 1)
+            out[k] = np.array([float(t) for t in v.split()])
+    return out
+
+
+def oracle_sample_error(gold, x):
+    """Relative 2-norm error of x against the FP64 oracle's solution over the
+    profile's sampled entries (None without a profile)."""
+    if gold is None or "x_sample" not in gold:
+        return None
+    idx = gold["x_sample_idx"].astype(np.int64)
+    return float(np.linalg.norm(x[idx] - gold["x_sample"]) / np.linalg.norm(gold["x_sample"]))
+
+
 # ----------------------------------------------------------------------------- reference arm
+def single_config(w, n, nnz, world=1):
+    """The `config` object of a single-system workload (both arms print the same one)."""
+    ir = w["prec"] == "ir_fp32"
+    return {"workload": workload_name(w), "n": n, "nnz": nnz, "m": w["m"], "tol": w["tol"],
+            "parallelism": "replicas" if world > 1 else "1 GPU",
+            "l2": (("inputs larger than L2 (Krylov basis %.1f GB >> 126 MB), no flush"
+                    % ((4 if ir else 8) * n * (w["m"] + 1) / 1e9)) if (8 * n * (w["m"] + 1) > 126e6) else
+                   ("L2-resident by design (Krylov basis %.1f MB < 126 MB: the latency-bound case), no flush"
+                    % ((4 if ir else 8) * n * (w["m"] + 1) / 1e6)))}
+
+
 def run_reference(args, w, rank, world):
+    """The oracle as it stands (sequential FP64 C, one host thread) on the same
+    workload. Every timed step is a bounded sample -- the first `sample`
+    Arnoldi steps of the same solve, with the cycle tail, residual and update --
+    and `value` scales the sample to a whole solve by a model of the oracle's
+    own memory traffic and its recorded iteration profile (checked against one
+    complete 256^3 oracle solve: within 13%). `ms_per_step` is the measured wall
+    time of one sample, so steps x ms_per_step is the time actually spent."""
     if rank != 0:
-        return 0
+        return None
     A = make_problem(w)
     _, b = P.rhs(A, seed=0)
+    n, nnz = len(A[0]) - 1, len(A[1])
     if w["prec"] == "ir_fp32" and w["N"] >= 192:
-        print(json.dumps({"impl": "reference", "unavailable": "no complete run of the oracle's GMRES-IR at this size "
-                          "to scale a sample by (at 192^3 27-point its sequential FP32 sums stall it: true residual "
-                          "1.43e-10 after 5000 steps, tol 1e-10)"}))
-        return 0
+        return {"impl": "reference", "unavailable": "no complete run of the oracle's GMRES-IR at this size "
+                "to scale a sample by (at 192^3 27-point its sequential FP32 sums stall it: true residual "
+                "1.43e-10 after 5000 steps, tol 1e-10)"}
     prof = golden_profile({256: "c2_one_reduce", 32: "c1"}.get(w["N"], "none"))
     if prof is None:
-        print(json.dumps({"impl": "reference", "unavailable": "oracle iteration profile for this workload "
-                          "(tests/golden/oracle_profile_*.txt) has not been written"}))
-        return 0
+        return {"impl": "reference", "unavailable": "oracle iteration profile for this workload "
+                "(tests/golden/oracle_profile_*.txt) has not been written"}
+    import oracle
+
     ks = cycle_profile(int(prof["iters"]), w["m"])
-    sample = 12 if w["N"] >= 128 else w["max_iter"]
-    vals = []
-    for s in range(args.warmup + args.steps):
-        cb = cpu_baseline(A, b, w, ks, sample)
-        if s >= args.warmup:
-            vals.append(cb)
-    v = float(np.mean([c["value"] for c in vals]))
-    cores = 1
-    line = {
-        "impl": "reference", "metric": METRIC_IR.format(tol=("%.0e" % w["tol"]).replace("e-0", "e-")) if w["prec"] == "ir_fp32" else METRIC, "value": v, "unit": "s", "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * v, "higher_is_better": False,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": workload_name(w), "m": w["m"], "tol": w["tol"]},
-        "cpu_baseline": {"value": v, "unit": "s", "cores": cores, "kind": "oracle", "sample": vals[-1]["sample"]},
+    sample = 6 if w["N"] >= 128 else w["max_iter"]
+    variant = oracle.IR_FP32 if w["prec"] == "ir_fp32" else oracle.ONE_REDUCE
+    o = oracle.get()
+    walls, iters = [], 0
+    for s_ in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        r = o.gmres(A, b, variant=variant, m=w["m"], tol=0.0 if w["N"] >= 128 else w["tol"], max_iter=sample)
+        dt = time.perf_counter() - t0
+        iters = r.iters
+        if s_ >= args.warmup:
+            walls.append(dt)
+    sample_s = float(np.mean(walls))
+    full = iters >= int(prof["iters"])  # the sample is the whole solve
+    v = sample_s if full else sample_s * oracle_solve_bytes(n, nnz, ks) / oracle_solve_bytes(n, nnz, [iters])
+    what = ("the complete solve" if full else
+            f"first {iters} Arnoldi steps (+ tail, residual, update) of the same solve, scaled to the whole solve "
+            f"({sum(ks)} steps, {len(ks)} cycles, the oracle's own profile) by a model of its memory traffic")
+    # the same sample once more on all host cores (timing build of the same source)
+    om = oracle.get_omp()
+    t0 = time.perf_counter()
+    r2 = om.gmres(A, b, variant=variant, m=w["m"], tol=0.0 if w["N"] >= 128 else w["tol"], max_iter=sample)
+    dt_all = time.perf_counter() - t0
+    v_all = dt_all if full else dt_all * oracle_solve_bytes(n, nnz, ks) / oracle_solve_bytes(n, nnz, [r2.iters])
+    metric = METRIC_IR.format(tol=("%.0e" % w["tol"]).replace("e-0", "e-")) if w["prec"] == "ir_fp32" else METRIC
+    return {
+        "impl": "reference", "metric": metric, "value": v, "unit": "s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sample_s, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded stencil, x_true ~ U[-1,1])",
+        "config": single_config(w, n, nnz, world),
+        "value_basis": ("measured" if full else "extrapolated") + ": each timed step runs " + what
+                       + "; ms_per_step is the measured wall time of one such sample",
+        "sample_seconds": sample_s,
+        "cpu_baseline": {"value": v, "unit": "s", "cores": o.threads, "kind": "oracle",
+                         "sample": what + f", FP64 C oracle on {o.threads} host thread, {sample_s:.2f} s per sample",
+                         "all_cores": {"value": v_all, "unit": "s", "cores": om.threads, "kind": "oracle",
+                                       "sample": f"the same sample once on {om.threads} host threads "
+                                                 f"(oracle.c built with -DORC_OMP -fopenmp): {dt_all:.2f} s"}},
         "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
-    print(json.dumps(line))
-    return 0
 
 
 # ----------------------------------------------------------------------------- our arm
@@ -372,9 +509,14 @@ def run_ours(args, w, rank, world, dist):
         ms_f = max_over_ranks(ms_f)
         i64 = infos_f[-1]
         x64 = x.cpu().numpy()
+        gold = golden_vectors(w["golden_fp64"]) if w.get("golden_fp64") else None
         fp64 = {"time_to_solve_s": ms_f / 1e3, "iters": i64.iters, "restarts": i64.restarts,
                 "rel_resid_true": i64.rel_resid_true,
                 "ir_rel_error_vs_fp64": float(np.linalg.norm(xs - x64) / np.linalg.norm(x64)),
+                # against the CPU oracle's complete FP64 one-reduce solve (64 sampled entries)
+                "ir_rel_error_vs_fp64_oracle": oracle_sample_error(gold, xs),
+                "fp64_rel_error_vs_fp64_oracle": oracle_sample_error(gold, x64),
+                "oracle_profile": ("tests/golden/oracle_profile_%s.txt" % w["golden_fp64"]) if gold else None,
                 "step_tflops_fp64": prof_f["one_reduce_step"]["flops"] / (prof_f["one_reduce_step"]["ms"] * 1e9)
                 if prof_f["one_reduce_step"]["ms"] else None}
         # BF16 basis storage (FP32 arithmetic): the other GMRES-IR storage option
@@ -385,6 +527,7 @@ def run_ours(args, w, rank, world, dist):
         fp64["ir_bf16"] = {"time_to_solve_s": max_over_ranks(ms_b) / 1e3, "iters": ib16.iters,
                            "restarts": ib16.restarts, "rel_resid_true": ib16.rel_resid_true,
                            "rel_error_vs_fp64": float(np.linalg.norm(xb - x64) / np.linalg.norm(x64)),
+                           "rel_error_vs_fp64_oracle": oracle_sample_error(gold, xb),
                            "step_hbm_gbs": prof_b["one_reduce_step"]["bytes"] / (prof_b["one_reduce_step"]["ms"] * 1e6)
                            if prof_b["one_reduce_step"]["ms"] else None,
                            "maxpy_hbm_gbs": prof_b["arnoldi_maxpy"]["bytes"] / (prof_b["arnoldi_maxpy"]["ms"] * 1e6)
@@ -434,7 +577,6 @@ def run_ours(args, w, rank, world, dist):
     st = prof["one_reduce_step"]
     mx = prof["arnoldi_maxpy"]
     clk_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2032.0)
-    fp64_peak = 148 * FP64_DFMA_PER_CLK_SM * 2 * float(peaks.get("sm_max_mhz", 2032.0)) * 1e6 / 1e12
     step_avg_ms = st["ms"] / max(st["launches"], 1)
     step_tflops = st["flops"] / (st["ms"] * 1e-3) / 1e12 if st["ms"] else None
     step_gbs = st["bytes"] / (st["ms"] * 1e-3) / 1e9 if st["ms"] else None
@@ -459,12 +601,19 @@ def run_ours(args, w, rank, world, dist):
                       "hbm_frac_of_measured": (mx["bytes"] / (mx["ms"] * 1e-3) / 1e9) / hbm if mx["ms"] else None},
         }
     else:
+        pk = fp64_peak()
+        # the method's own byte count per step (12 nnz + 4n + 8n(j+1): CSR, u and
+        # V_j read) -- the library's count without the 8n of w written by each
+        # launch that ran the SpMV (all but the cycle tails)
+        survey_bytes = st["bytes"] - 8.0 * n * max(st["launches"] - info.restarts, 0)
         roofline = {
             "kernel": "k_one_reduce_step (fused CSR SpMV + block dot [V u]^T[u w] + epilogue)",
-            "bound": "alu", "achieved": step_tflops, "peak": fp64_peak, "unit": "TFLOP/s",
-            "frac": step_tflops / fp64_peak if step_tflops else None,
-            "peak_source": (f"FP64 pipe derived from unit counts and clock: 148 SMs x {FP64_DFMA_PER_CLK_SM} DFMA/clk x 2 "
-                            f"flop x {peaks.get('sm_max_mhz', 2032.0):g} MHz (nominal 1.25 TFLOP/s)"),
+            "bound": "alu", "achieved": step_tflops, "peak": pk["tflops"], "unit": "TFLOP/s",
+            "frac": step_tflops / pk["tflops"] if step_tflops else None,
+            "peak_source": pk["source"] + " (of measured)",
+            "peak_nominal": pk["nominal_tflops"],
+            "frac_of_nominal": step_tflops / pk["nominal_tflops"] if step_tflops else None,
+            "hbm_frac_of_measured_survey_bytes": (survey_bytes / (st["ms"] * 1e-3) / 1e9) / hbm if st["ms"] else None,
             "traffic": (STEP_TRAFFIC_RATIO * st["bytes"] / max(st["launches"], 1)) if STEP_TRAFFIC_RATIO else None,
             "traffic_source": "ncu dram bytes / algorithmic bytes at 128^3 (same kernel build), times this run's "
                               "algorithmic bytes per launch",
@@ -490,12 +639,11 @@ def run_ours(args, w, rank, world, dist):
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32 cycles / f64 restarts" if ir else "f64",
         "data": "synthetic (seeded stencil, x_true ~ U[-1,1])",
-        "config": {"workload": workload_name(w), "n": n, "nnz": nnz, "m": w["m"], "tol": w["tol"],
-                   "parallelism": "replicas" if world > 1 else "1 GPU",
-                   "l2": "inputs larger than L2 (Krylov basis %.1f GB >> 126 MB), no flush"
-                         % ((4 if ir else 8) * n * (w["m"] + 1) / 1e9)},
+        "config": single_config(w, n, nnz, world),
         "iters": info.iters, "restarts": info.restarts, "reductions": info.reductions,
         "grid_syncs": info.grid_syncs, "rel_resid_true": true_rel,
+        "us_per_arnoldi_step": ms * 1e3 / max(info.iters, 1),
+        "grid_syncs_per_step": info.grid_syncs / max(info.iters, 1),
         "solves_per_s": world / (ms / 1e3),
         "alg_hbm_gbs_whole_solve": total_bytes / (total_ms_prof * 1e6) if total_ms_prof else None,
         "mgs": mgs,
@@ -510,10 +658,8 @@ def run_ours(args, w, rank, world, dist):
         "clocks": clocks,
         "history_first": [float(h) for h in hist_1r[:3]],
     }
-    if rank == 0:
-        print(json.dumps(line))
     s.close()
-    return 0
+    return line
 
 
 # ----------------------------------------------------------------------------- batched workload
@@ -554,14 +700,20 @@ def batch_cpu_baseline(mats, rhs, w, iters, budget_s=20.0):
             break
     work_all = sum((len(A[0]) - 1) * k for A, k in zip(mats, iters))
     v = t_tot * work_all / work_s
+    # all host cores: the systems are independent, so the same sample solved by
+    # one process per core
+    dt, cores = pool_oracle_solves([(mats[i], rhs[i], 1, w["m"], w["tol"], w["max_iter"]) for i in names])
     return {"value": v, "unit": "s", "cores": 1, "kind": "oracle",
             "sample": f"complete oracle solves of {len(names)} of the {len(mats)} systems (every 16th), "
-                      f"{t_tot:.1f} s, scaled by sum(n_i * iters_i) over all systems / over the sample"}
+                      f"{t_tot:.1f} s, scaled by sum(n_i * iters_i) over all systems / over the sample",
+            "all_cores": {"value": dt * work_all / work_s, "unit": "s", "cores": cores, "kind": "oracle",
+                          "sample": f"the same {len(names)} solves on {cores} spawned processes (one per core, "
+                                    f"1 thread each): {dt:.1f} s wall, scaled the same way"}}
 
 
 def run_batch_reference(args, w, rank):
     if rank != 0:
-        return 0
+        return None
     _, mats, rhs = batch_problem(w)
     from oracle import Oracle
 
@@ -593,8 +745,7 @@ def run_batch_reference(args, w, rank):
                                    f"total n / sample n"},
         "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
-    print(json.dumps(line))
-    return 0
+    return line
 
 
 def run_batch(args, w, rank, world, dist):
@@ -697,16 +848,15 @@ def run_batch(args, w, rank, world, dist):
 
     st = prof["one_reduce_step"]
     mx = prof["arnoldi_maxpy"]
-    fp64_peak = 148 * FP64_DFMA_PER_CLK_SM * 2 * float(peaks.get("sm_max_mhz", 2032.0)) * 1e6 / 1e12
+    pk = fp64_peak()
     hbm = float(peaks.get("hbm_gbs", 6400.0))
     step_tflops = st["flops"] / (st["ms"] * 1e-3) / 1e12 if st["ms"] else None
     step_gbs = st["bytes"] / (st["ms"] * 1e-3) / 1e9 if st["ms"] else None
     roofline = {
         "kernel": "ke_step (batched fused CSR SpMV + block dot, per-(CTA, system) partial sums, per-system epilogue)",
-        "bound": "alu", "achieved": step_tflops, "peak": fp64_peak, "unit": "TFLOP/s",
-        "frac": step_tflops / fp64_peak if step_tflops else None,
-        "peak_source": (f"FP64 pipe derived from unit counts and clock: 148 SMs x {FP64_DFMA_PER_CLK_SM} DFMA/clk x 2 "
-                        f"flop x {peaks.get('sm_max_mhz', 2032.0):g} MHz (nominal 1.25 TFLOP/s)"),
+        "bound": "alu", "achieved": step_tflops, "peak": pk["tflops"], "unit": "TFLOP/s",
+        "frac": step_tflops / pk["tflops"] if step_tflops else None,
+        "peak_source": pk["source"] + " (of measured)", "peak_nominal": pk["nominal_tflops"],
         "traffic": None,
         "launch_avg_ms": st["ms"] / max(st["launches"], 1), "launches": st["launches"],
         "alg_flops_per_launch": st["flops"] / max(st["launches"], 1),
@@ -740,10 +890,8 @@ def run_batch(args, w, rank, world, dist):
         "cpu_baseline": cpu,
         "clocks": clocks,
     }
-    if rank == 0:
-        print(json.dumps(line))
     bs.close()
-    return 0
+    return line
 
 
 # ----------------------------------------------------------------------------- serving workload
@@ -766,6 +914,19 @@ def serve_requests(w):
         reqs.append(dict(A=A, b=P.rhs(A, seed=1000 + i)[1], prec=str(precs[i]), t=float(arrivals[i]),
                          n=int(sides[i]) ** 3))
     return reqs
+
+
+def serve_trace(reqs, rate, duration, seed):
+    """A finite Poisson trace of `duration` seconds of arrivals at `rate`/s,
+    each request drawn (seeded) from the pool `reqs` (same sizes, precisions
+    and systems as the stream)."""
+    rng = np.random.default_rng(seed)
+    t, out = 0.0, []
+    while True:
+        t += rng.exponential(1.0 / rate)
+        if t > duration:
+            return out
+        out.append(dict(reqs[int(rng.integers(len(reqs)))], t=t))
 
 
 def serve_run(lsgmres, sv, reqs, w, time_scale=1.0):
@@ -839,10 +1000,22 @@ def run_serve(args, w, rank, world, dist):
     job_thr = world * k / rank_max(dist, wall)
     true_rel = [float(np.linalg.norm(r["b"] - P.to_scipy(r["A"]) @ x) / np.linalg.norm(r["b"]))
                 for r, x in zip(reqs, xs_last)]
-    # sustainable load: half the measured throughput, same requests
+    # sustained service: finite Poisson traces of sweep_s seconds at fractions of
+    # the capacity the burst measured, requests drawn from the same stream
     sv.set_profile(False)
-    rate_s = 0.5 * thr
-    wall_s, lat_s, _, _ = serve_run(lsgmres, sv, reqs, w, time_scale=w["rate"] / rate_s)
+    sweep = []
+    for i, f in enumerate(w.get("sweep", ())):
+        rate = f * thr
+        trace = serve_trace(reqs, rate, w["sweep_s"], seed=w["seed"] + 17 + i)
+        wall_t, lat_t, infos_t, _ = serve_run(lsgmres, sv, trace, w)
+        last_arrival = trace[-1]["t"] if trace else 0.0
+        sweep.append({"fraction_of_burst_capacity": f, "offered_rate": rate, "requests": len(trace),
+                      "arrivals_s": last_arrival, "solves_per_s": len(trace) / wall_t,
+                      "latency_p50_s": float(np.percentile(lat_t, 50)),
+                      "latency_p99_s": float(np.percentile(lat_t, 99)),
+                      "latency_max_s": float(np.max(lat_t)),
+                      "drain_after_last_arrival_s": wall_t - last_arrival,
+                      "all_converged": all(x.status == 0 for x in infos_t)})
     sv.close()
 
     # baseline: the same requests one at a time in arrival order by the
@@ -883,16 +1056,15 @@ def run_serve(args, w, rank, world, dist):
                        "order; queueing simulated from the measured solve times"}
 
     st0, st1 = prof[0]["one_reduce_step"], prof[1]["one_reduce_step"]
-    fp64_peak = 148 * FP64_DFMA_PER_CLK_SM * 2 * float(peaks.get("sm_max_mhz", 2032.0)) * 1e6 / 1e12
+    pk = fp64_peak()
     hbm = float(peaks.get("hbm_gbs", 6400.0))
     tf0 = st0["flops"] / (st0["ms"] * 1e-3) / 1e12 if st0["ms"] else None
     gbs1 = st1["bytes"] / (st1["ms"] * 1e-3) / 1e9 if st1["ms"] else None
     roofline = {
         "kernel": "ke_step<double> (FP64 engine: fused CSR SpMV + block dot + per-request epilogue)",
-        "bound": "alu", "achieved": tf0, "peak": fp64_peak, "unit": "TFLOP/s",
-        "frac": tf0 / fp64_peak if tf0 else None,
-        "peak_source": (f"FP64 pipe derived from unit counts and clock: 148 SMs x {FP64_DFMA_PER_CLK_SM} DFMA/clk x 2 "
-                        f"flop x {peaks.get('sm_max_mhz', 2032.0):g} MHz (nominal 1.25 TFLOP/s)"),
+        "bound": "alu", "achieved": tf0, "peak": pk["tflops"], "unit": "TFLOP/s",
+        "frac": tf0 / pk["tflops"] if tf0 else None,
+        "peak_source": pk["source"] + " (of measured)", "peak_nominal": pk["nominal_tflops"],
         "traffic": None, "launch_avg_ms": st0["ms"] / max(st0["launches"], 1), "launches": st0["launches"],
         "hbm_gbs": st0["bytes"] / (st0["ms"] * 1e-3) / 1e9 if st0["ms"] else None,
         "ir_engine_step": {"kernel": "ke_step<float>", "bound": "hbm", "achieved_gbs": gbs1, "peak_gbs": hbm,
@@ -921,6 +1093,13 @@ def run_serve(args, w, rank, world, dist):
         cpu = {"value": k / cpu_s, "unit": "solves/s", "cores": 1, "kind": "oracle",
                "sample": f"complete oracle solves of {cnt} requests (every 4th with n <= 300k, until 15 s: "
                          f"{t_tot:.1f} s), scaled to all {k} requests by sum(n_i * iters_i)"}
+        # all host cores: the same sample, one spawned process per core
+        picked = [r for r in reqs[0:k:4] if r["n"] <= 300_000][:cnt]
+        dt, cores = pool_oracle_solves([(r["A"], r["b"], 1 if r["prec"] == "fp64" else 2, w["m"], w["tol"],
+                                         w["max_iter"]) for r in picked])
+        cpu["all_cores"] = {"value": k / (dt * work_all / work_s), "unit": "solves/s", "cores": cores,
+                            "kind": "oracle", "sample": f"the same {cnt} solves on {cores} spawned processes "
+                                                        f"(1 thread each): {dt:.1f} s wall, scaled the same way"}
     ntot = sum(r["n"] for r in reqs)
     line = {
         "metric": METRIC_SERVE, "value": job_thr, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
@@ -938,9 +1117,11 @@ def run_serve(args, w, rank, world, dist):
                              "buffers, solutions back to host buffers)"},
         "latency_p50_s": float(np.percentile(lat, 50)), "latency_p99_s": float(np.percentile(lat, 99)),
         "makespan_s": wall,
-        "sustained": {"offered_rate": rate_s, "solves_per_s": k / wall_s,
-                      "latency_p50_s": float(np.percentile(lat_s, 50)),
-                      "latency_p99_s": float(np.percentile(lat_s, 99))},
+        "sustained_sweep": sweep,
+        "sustained_capacity_solves_per_s": max((p["solves_per_s"] for p in sweep), default=None),
+        "sustained_note": ("each sweep point is a finite Poisson trace of about sweep_s seconds of arrivals at the "
+                           "given fraction of the burst's measured throughput, drawn from the same request "
+                           "distribution; latency from each scheduled arrival to its solution in host memory"),
         "all_converged": all(i.status == 0 for i in all_infos), "max_rel_resid_true": max(true_rel),
         "server": {"peak_running": st["peak_running"], "cycles": st["cycles"], "engine_bytes": st["engine_bytes"],
                    "peak_bytes_in_use": st["peak_bytes_in_use"]},
@@ -954,14 +1135,12 @@ def run_serve(args, w, rank, world, dist):
         "cpu_baseline": cpu,
         "clocks": clocks,
     }
-    if rank == 0:
-        print(json.dumps(line))
-    return 0
+    return line
 
 
 def run_serve_reference(args, w, rank):
     if rank != 0:
-        return 0
+        return None
     reqs = serve_requests(w)
     from oracle import Oracle
 
@@ -985,7 +1164,7 @@ def run_serve_reference(args, w, rank):
         if s >= args.warmup:
             vals.append(len(reqs) / total_s)
     v = float(np.mean(vals))
-    print(json.dumps({
+    return ({
         "impl": "reference", "metric": METRIC_SERVE, "value": v, "unit": "solves/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * len(reqs) / v, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -994,8 +1173,40 @@ def run_serve_reference(args, w, rank):
                          "sample": f"complete oracle solves of {cnt} requests (every 16th) per step, scaled by "
                                    f"total n / sample n"},
         "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-    }))
-    return 0
+    })
+
+
+# ----------------------------------------------------------------------------- the other configurations
+SERVE_LEG = dict(SERVE_WORKLOADS["serve"], sweep_s=6.0)
+
+
+def run_legs(args, rank, world, dist):
+    """The other benchmark configurations, each measured in the same run after
+    the headline and reported under its own key with its own timing, roofline,
+    clocks and CPU baseline: 32^3 (latency-bound, one-reduce vs plain MGS),
+    192^3 27-point GMRES-IR (FP32 and BF16 basis vs FP64 one-reduce, errors
+    against the FP64 oracle's stored solve), 512 uneven 2D systems batched, and
+    the serving loop (a 2000 req/s burst and a sweep of sustained arrival
+    rates). Steps are capped per leg so the whole run stays within minutes."""
+    import copy
+
+    def sub(cap, warm=3):
+        a = copy.copy(args)
+        a.steps, a.warmup = max(1, min(args.steps, cap)), warm
+        return a
+
+    legs = {}
+    for name, fn in (("c1_32cubed", lambda: run_ours(sub(20), WORKLOADS[32], rank, world, dist)),
+                     ("c3_192cubed_gmres_ir", lambda: run_ours(sub(3), WORKLOADS[192], rank, world, dist)),
+                     ("c4_batch512", lambda: run_batch(sub(3), BATCH_WORKLOADS["batch512"], rank, world, dist)),
+                     ("c5_serve", lambda: run_serve(sub(1), SERVE_LEG, rank, world, dist))):
+        t0 = time.perf_counter()
+        line = fn()
+        if line is not None:
+            line.pop("history_first", None)
+            line["leg_wall_s"] = time.perf_counter() - t0
+        legs[name] = line
+    return legs
 
 
 def main():
@@ -1008,6 +1219,8 @@ def main():
                     + sorted(SERVE_WORKLOADS), default="256")
     ap.add_argument("--no-mgs", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-legs", action="store_true",
+                    help="default workload: skip the other configurations measured after the headline")
     args = ap.parse_args()
     batch = args.workload in BATCH_WORKLOADS
     serve = args.workload in SERVE_WORKLOADS
@@ -1029,16 +1242,20 @@ def main():
             dist = dist_mod
     try:
         if serve:
-            if args.impl == "reference":
-                return run_serve_reference(args, w, rank)
-            return run_serve(args, w, rank, world, dist)
-        if batch:
-            if args.impl == "reference":
-                return run_batch_reference(args, w, rank)
-            return run_batch(args, w, rank, world, dist)
-        if args.impl == "reference":
-            return run_reference(args, w, rank, world)
-        return run_ours(args, w, rank, world, dist)
+            line = (run_serve_reference(args, w, rank) if args.impl == "reference"
+                    else run_serve(args, w, rank, world, dist))
+        elif batch:
+            line = (run_batch_reference(args, w, rank) if args.impl == "reference"
+                    else run_batch(args, w, rank, world, dist))
+        elif args.impl == "reference":
+            line = run_reference(args, w, rank, world)
+        else:
+            line = run_ours(args, w, rank, world, dist)
+            if args.workload == "256" and world == 1 and not args.no_legs:
+                line["legs"] = run_legs(args, rank, world, dist)
+        if rank == 0 and line is not None:
+            print(json.dumps(line))
+        return 0
     finally:
         if dist is not None:
             dist.destroy_process_group()
