@@ -103,6 +103,9 @@ FP64_DFMA_PER_CLK_SM = 2  # B300: 1.25 TFLOP/s nominal FP64 = 148 SMs x 2 DFMA/c
 # for the kernel builds those captures measured; set to None when a kernel
 # changes.
 STEP_TRAFFIC_RATIO = 1.048
+# The same ratio for the FP64 step with fixed-point products (staging mode 6),
+# None until an ncu capture of that kernel build gives it.
+STEP6_TRAFFIC_RATIO = None
 STEP32_TRAFFIC_RATIO = {"27pt": 1.014, "7pt": 1.005}
 
 
@@ -487,6 +490,9 @@ def run_ours(args, w, rank, world, dist):
     x = torch.zeros(n, dtype=torch.float64, device="cuda")
     s = lsgmres.Solver(A, m=w["m"], tol=w["tol"], ortho="one_reduce_mgs", max_iter=w["max_iter"], stream=stream,
                        prec=w["prec"])
+    # FP64 cycles: the block dot and MAXPY products on the integer pipes (the
+    # library's default where the tile-pair ring kernel runs)
+    fx = s.set_block_dot(True)
 
     barrier()
     with ClockSampler(local) as clk:
@@ -545,6 +551,20 @@ def run_ours(args, w, rank, world, dist):
                if prof_m else None}
         s.set(ortho="one_reduce_mgs", max_iter=w["max_iter"])
 
+    # the same solve with every FP64 product on the FP64 pipe (FMAs), for comparison
+    dfma = None
+    if fx and not ir and not args.no_mgs:
+        s.set_block_dot(False)
+        ms_d, infos_d, prof_d = timed_solves(torch, s, bd, x, max(1, min(args.steps, 2)), 1, stream)
+        idd = infos_d[-1]
+        std = prof_d["one_reduce_step"]
+        dfma = {"time_to_solve_s": max_over_ranks(ms_d) / 1e3, "iters": idd.iters, "restarts": idd.restarts,
+                "rel_resid_true": idd.rel_resid_true,
+                "step_launch_avg_ms": std["ms"] / max(std["launches"], 1),
+                "step_tflops": std["flops"] / (std["ms"] * 1e9) if std["ms"] else None,
+                "maxpy_launch_avg_ms": prof_d["arnoldi_maxpy"]["ms"] / max(prof_d["arnoldi_maxpy"]["launches"], 1)}
+        s.set_block_dot(True)
+
     # the paper's sibling schemes on the same kernels (Algorithm 5: two reductions
     # per step; Algorithm 8: Givens rotations on column pairs)
     siblings = None
@@ -600,6 +620,28 @@ def run_ours(args, w, rank, world, dist):
                       "hbm_gbs": mx["bytes"] / (mx["ms"] * 1e-3) / 1e9 if mx["ms"] else None,
                       "hbm_frac_of_measured": (mx["bytes"] / (mx["ms"] * 1e-3) / 1e9) / hbm if mx["ms"] else None},
         }
+    elif fx:  # FP64 cycles with fixed-point products: HBM is the bound again
+        pk = fp64_peak()
+        survey_bytes = st["bytes"] - 8.0 * n * max(st["launches"] - info.restarts, 0)
+        roofline = {
+            "kernel": "k_one_reduce_step<., double, double, 6> (fused CSR SpMV + block dot [V u]^T[u w] with the "
+                      "basis columns' products as exact fixed-point integers + epilogue)",
+            "bound": "hbm", "achieved": step_gbs, "peak": hbm, "unit": "GB/s",
+            "frac": step_gbs / hbm if step_gbs else None,
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy bandwidth, of measured)",
+            "alg_bytes_formula": "4(n+1) + 12 nnz + 8n(j+1) + 8n (CSR, u and V_j read, w written)",
+            "hbm_frac_of_measured_survey_bytes": (survey_bytes / (st["ms"] * 1e-3) / 1e9) / hbm if st["ms"] else None,
+            "traffic": (STEP6_TRAFFIC_RATIO * st["bytes"] / max(st["launches"], 1)) if STEP6_TRAFFIC_RATIO else None,
+            "traffic_source": "ncu dram bytes / algorithmic bytes of the fixed-point step at 128^3 (same kernel build), "
+                              "times this run's algorithmic bytes per launch",
+            "launch_avg_ms": step_avg_ms, "launches": st["launches"],
+            "alg_bytes_per_launch": st["bytes"] / max(st["launches"], 1),
+            "fp64_method_tflops": step_tflops,
+            "fp64_pipe_peak_tflops": pk["tflops"], "fp64_pipe_peak_source": pk["source"],
+            "maxpy": {"kernel": "k_maxpy_fx", "launch_avg_ms": mx["ms"] / max(mx["launches"], 1),
+                      "hbm_gbs": mx["bytes"] / (mx["ms"] * 1e-3) / 1e9 if mx["ms"] else None,
+                      "hbm_frac_of_measured": (mx["bytes"] / (mx["ms"] * 1e-3) / 1e9) / hbm if mx["ms"] else None},
+        }
     else:
         pk = fp64_peak()
         # the method's own byte count per step (12 nnz + 4n + 8n(j+1): CSR, u and
@@ -640,6 +682,7 @@ def run_ours(args, w, rank, world, dist):
         "vs_baseline": None, "dtype": "f32 cycles / f64 restarts" if ir else "f64",
         "data": "synthetic (seeded stencil, x_true ~ U[-1,1])",
         "config": single_config(w, n, nnz, world),
+        "fixed_point_products": bool(fx) and not ir,
         "iters": info.iters, "restarts": info.restarts, "reductions": info.reductions,
         "grid_syncs": info.grid_syncs, "rel_resid_true": true_rel,
         "us_per_arnoldi_step": ms * 1e3 / max(info.iters, 1),
@@ -648,6 +691,8 @@ def run_ours(args, w, rank, world, dist):
         "alg_hbm_gbs_whole_solve": total_bytes / (total_ms_prof * 1e6) if total_ms_prof else None,
         "mgs": mgs,
         "speedup_vs_mgs": (mgs["time_to_solve_s"] / (ms / 1e3)) if mgs else None,
+        "fma_products": dfma,
+        "speedup_vs_fma_products": (dfma["time_to_solve_s"] / (ms / 1e3)) if dfma else None,
         "siblings": siblings,
         "fp64_one_reduce": fp64,
         "speedup_vs_fp64": (fp64["time_to_solve_s"] / (ms / 1e3)) if fp64 else None,

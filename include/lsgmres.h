@@ -181,6 +181,27 @@ gmres_status gmres_set_profile(gmres_handle h, int on);
 gmres_status gmres_profile(gmres_handle h, int cls, double* total_ms, int64_t* launches,
                            double* alg_bytes, double* alg_flops);
 
+/* Arithmetic of the FP64 block inner product [V_{j-1} u_j]^T [u_j  A u_j] of
+ * the one-reduce step (Algorithm 4's single reduction; Section IV's mass inner
+ * product). fixed_point = 1 (the default): where the step kernel stages tile
+ * pairs with its column ring, the products of the basis columns run on the
+ * integer pipes as exact fixed-point products -- each FP64 value rescaled by
+ * a power of two to a 58-bit integer (relative to its column's largest
+ * exponent, or its tile pair's for u and w), split in two 29-bit limbs,
+ * multiplied and summed exactly in 64-bit integers over each tile pair, then
+ * converted to FP64 once -- while the slow FP64 pipe of this GPU is spent on
+ * the SpMV, the norms and the few remainder columns only. Each product's
+ * inputs are exact to 2^-58 of their vector's largest entry and the integer
+ * sums are exact, so a sum x^T y is off by at most about 2^-57 (max|x| sum|y_i|
+ * + max|y| sum|x_i|) before its last FP64 roundings: below FP64 summation's
+ * classical bound gamma_n sum|x_i y_i| unless the largest entries of one
+ * vector sit where the other is many orders of magnitude smaller. fixed_point = 0: FP64 fused
+ * multiply-adds throughout. *active (may be NULL) receives whether this
+ * handle's step kernel uses the fixed-point form (it needs staging mode 2:
+ * large enough matrices whose tile-pair CSR fits the shared memory). The
+ * choice changes rounding only. Never errors on a valid handle. */
+gmres_status gmres_set_block_dot(gmres_handle h, int fixed_point, int* active);
+
 /* Testing the bounded waits of the CSR staging. The step kernel brings each
  * tile's CSR into shared memory with bulk copies whose completion it waits for
  * on an mbarrier, for at most ~2^31 SM clocks (about one second); a wait that

@@ -26,7 +26,7 @@ ROOT = os.path.dirname(HERE)
 SRCS = [os.path.join(HERE, "csrc", f) for f in (
     "lsgmres.cu", *(f"step_{t}_s{s}.cu" for t in ("f64", "f32", "bf16") for s in (0, 1, 2)),
     "step_bf16_s3.cu", "step_bf16_s4.cu",
-    *(f"step_{t}_s5.cu" for t in ("f64", "f32", "bf16")),
+    *(f"step_{t}_s5.cu" for t in ("f64", "f32", "bf16")), "step_f64_s6.cu",
     "batch.cu", "engine_step_f64.cu", "engine_step_f32.cu", "probe.cu")]
 OBJ_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblsgmres.so")

@@ -74,6 +74,10 @@ struct Small {
   double* hist;     // hist_cap
   double* partials; // P x nvmax
   double* raw;      // nvmax: standalone block-dot output
+  // m + 2: per basis column, the largest (hi word & 0x7FF00000) its writer
+  // stored (atomicMax; cleared at each cycle start): the bound of the
+  // fixed-point block dot. Unused (may be NULL) elsewhere.
+  unsigned int* ecol;
   int m;
   int ldh;          // m + 1
   int nvmax;        // 2 (m + 1) + 2
@@ -862,6 +866,219 @@ __device__ __forceinline__ void tile_pair_dot_rows_pf(int64_t pp, int64_t n, con
         const SV* colp = V + (size_t)(J8 * kWarps + c) * ldv;
         x0[b] = (c < r8 && row0 < n) ? ld_as<VT>(colp + row0) : VT(0);
         x1[b] = (c < r8 && row1 < n) ? ld_as<VT>(colp + row1) : VT(0);
+      }
+#pragma unroll
+      for (int b = 0; b < kRemBatch; ++b) {
+        const int c = c0 + b;
+        if (c < kWarps - 1 && c < r8) {
+          rem_a[c] = fma(x0[b], ur0, rem_a[c]);
+          rem_a[c] = fma(x1[b], ur1, rem_a[c]);
+          if (need_w) {
+            rem_c[c] = fma(x0[b], wr0, rem_c[c]);
+            rem_c[c] = fma(x1[b], wr1, rem_c[c]);
+          }
+        }
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// FP64 block dot on the integer pipes (exact fixed-point products).
+// ---------------------------------------------------------------------------
+// On B300 an SM retires about 1.8 DFMA per clock but 64 IMAD/LOP3/SHF and 25
+// 32x32->64-bit IMAD.WIDE, so the FP64 block dot, at 2 DFMA per basis element,
+// is bound by the FP64 pipe at ~40% of HBM bandwidth. Here the products of the
+// full columns run as integer arithmetic instead, at FP64 accuracy:
+//  * each value x of a vector with bound |x| < 2^(f - 1022) (f: a biased
+//    exponent at least that of its largest entry) becomes the integer
+//    X = trunc(x 2^(58 - f + 1022)), |X| < 2^58, split into two signed 29-bit
+//    limbs X = Xh 2^29 + Xl (the truncation error is below 2^-58 of the bound,
+//    32 times finer than FP64 rounding of the largest entry);
+//  * X Y = Xh Yh 2^58 + (Xh Yl + Xl Yh) 2^29 + Xl Yl: the first two parts are
+//    summed exactly in 64-bit integers (three mad.wide.s32 per product), the
+//    last (below 2^-58 of the largest product) is dropped;
+//  * each lane sums the 16 products of one column over one tile pair exactly,
+//    then converts the sum to FP64 once and adds it to its FP64 accumulator.
+// The bounds: basis columns carry the largest exponent their writer stored
+// (Small::ecol, kept by the residual and MAXPY kernels); u and w get theirs
+// per tile pair from the CTA's own rows. The sums differ from FP64 DFMA sums
+// only by rounding, within the same classical bounds.
+// Record the largest exponent field among the values a warp stored into
+// column k (per thread: emax = max over its values of the hi word & 0x7FF00000).
+__device__ __forceinline__ void fx_note_max(unsigned int* ecol, int k, uint32_t emax) {
+  emax = __reduce_max_sync(0xffffffffu, emax);
+  if (ecol && (threadIdx.x & 31) == 0 && emax) atomicMax(ecol + k, emax);
+}
+__device__ __forceinline__ uint32_t fx_hi_field(double x) { return (uint32_t)__double2hiint(x) & 0x7FF00000u; }
+
+constexpr uint32_t kFxMinField = 64;  // bounds below 2^-958 are raised to it (values that small count as 0)
+
+__device__ __forceinline__ uint32_t fx_field(double x) {
+  return ((uint32_t)__double2hiint(x) >> 20) & 0x7FFu;
+}
+
+// x -> (Xh, Xl) for the bound of biased exponent f, given kf = 5 + f (the
+// right shift that takes x's 63-bit aligned significand to X).
+__device__ __forceinline__ int2 fx_split(double x, int kf) {
+  const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
+  const int sh = kf - (int)((hi >> 20) & 0x7FFu);  // >= 5 in bound; >= 69 for zero and subnormals
+  const uint32_t mh = (__funnelshift_l(lo, hi, 10) & 0x3FFFFFFFu) | 0x40000000u;
+  const unsigned long long M = ((unsigned long long)mh << 32) | (unsigned long long)(lo << 10);
+  unsigned long long X;
+  asm("shr.b64 %0, %1, %2;" : "=l"(X) : "l"(M), "r"(sh));  // shifts past 64 give 0
+  const int sg = (int)hi >> 31;
+  const int xh = (int)(X >> 29), xl = (int)((uint32_t)X & 0x1FFFFFFFu);
+  return make_int2((xh ^ sg) - sg, (xl ^ sg) - sg);
+}
+
+__device__ __forceinline__ long long fx_madw(int a, int b, long long c) {
+  long long d;
+  asm("mad.wide.s32 %0, %1, %2, %3;" : "=l"(d) : "r"(a), "r"(b), "l"(c));
+  return d;
+}
+
+// t * 2^e2 rounded to the nearest FP64 value (ties away from zero), |t| < 2^63,
+// assembled from the binary64 layout with integer instructions (the FP64
+// conversion instructions run at the FP64 pipe's rate on this part). Results
+// below the normal range flush to zero, above it give infinity.
+__device__ __forceinline__ double fx_to_double(long long t, int e2) {
+  if (t == 0) return 0.0;
+  const unsigned long long sgn = (unsigned long long)t & 0x8000000000000000ull;
+  unsigned long long a = t < 0 ? 0ull - (unsigned long long)t : (unsigned long long)t;
+  const int lz = __clzll((long long)a);
+  a <<= lz;                                                    // leading one at bit 63
+  const unsigned long long m = (a >> 11) + ((a >> 10) & 1ull);  // 53 bits, rounded; 2^53 carries into the exponent
+  const int ef = 1022 + 63 - lz + e2;                           // biased exponent - 1 (the significand adds 1)
+  if (ef < 0) return __longlong_as_double((long long)sgn);
+  if (ef >= 2046) return __longlong_as_double((long long)(0x7ff0000000000000ull | sgn));
+  return __longlong_as_double((long long)((((unsigned long long)ef) << 52) + m | sgn));
+}
+
+// The FP64 block dot of tile pair pp as tile_pair_dot_rows_pf (the same
+// ring of column slices, the same remainder columns in FP64), with the full
+// columns' products on the integer pipes. Loop order: column by column, both
+// halves of the tile pair in turn (the ring streams (column, half) slices),
+// so that each column's 16 products per lane are summed exactly before one
+// conversion. kf[c] = 5 + f of column wid + 8 c (its stored bound). The u and
+// w values of the pair are replaced in su, sw by their limbs (int2 per row)
+// relative to the pair's own bounds; s_ex holds 2 kWarps words.
+template <int MAXC, typename Hook>
+__device__ __forceinline__ void tile_pair_dot_rows_fx(int64_t pp, int64_t n, const double* __restrict__ V,
+                                                      int64_t ldv, bool need_w, int J8, int r8, double ur0,
+                                                      double wr0, double ur1, double wr1, double* su, double* sw,
+                                                      double* ring, const int (&kf)[MAXC], double (&acc_a)[MAXC],
+                                                      double (&acc_c)[MAXC], double (&rem_a)[kWarps - 1],
+                                                      double (&rem_c)[kWarps - 1], double& sig, double& dd,
+                                                      uint32_t* s_ex, Hook hook) {
+  constexpr int S = pf_stages<double>();  // ring slices per warp
+  constexpr int R = 2;                    // rows per 16-byte copy
+  constexpr int NQ = kRowsPerLane / R;    // copies per lane per slice
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t row0 = pp * (2 * kThreads) + threadIdx.x, row1 = row0 + kThreads;
+  sig = fma(ur0, ur0, sig);
+  dd = fma(ur0, wr0, dd);
+  sig = fma(ur1, ur1, sig);
+  dd = fma(ur1, wr1, dd);
+  // the pair's bounds for u and w: largest exponent field over its 512 rows
+  uint32_t eu = max(fx_field(ur0), fx_field(ur1)), ew = max(fx_field(wr0), fx_field(wr1));
+  eu = __reduce_max_sync(0xffffffffu, eu);
+  ew = __reduce_max_sync(0xffffffffu, ew);
+  if (lane == 0) {
+    s_ex[wid] = eu;
+    s_ex[kWarps + wid] = ew;
+  }
+  __syncthreads();
+  hook();
+  uint32_t fu = kFxMinField, fw = kFxMinField;
+#pragma unroll
+  for (int q = 0; q < kWarps; ++q) {
+    fu = max(fu, s_ex[q]);
+    fw = max(fw, s_ex[kWarps + q]);
+  }
+  int2* lu = reinterpret_cast<int2*>(su);
+  int2* lw = reinterpret_cast<int2*>(sw);
+  lu[threadIdx.x] = fx_split(ur0, 5 + (int)fu);
+  lu[kThreads + threadIdx.x] = fx_split(ur1, 5 + (int)fu);
+  lw[threadIdx.x] = fx_split(wr0, 5 + (int)fw);
+  lw[kThreads + threadIdx.x] = fx_split(wr1, 5 + (int)fw);
+  __syncthreads();
+  const bool bad = fu == 0x7FFu || fw == 0x7FFu;  // NaN or Inf among the pair's u, w
+  // x u = Xh Uh 2^(f_x + f_u - 2044 - 58) + ...: the flush scales
+  const int ea = (int)fu - 2102, ec = (int)fw - 2102;
+  double* wring = ring + wid * (S * kThreads);
+  const int nsl = 2 * J8;  // (column, half) slices this warp streams
+  auto issue = [&](int sl, int slot) {
+    const int c = sl >> 1, h = sl & 1;
+    const double* colp = V + (size_t)(wid + c * kWarps) * ldv;
+    const int64_t hb = pp * (2 * kThreads) + h * kThreads;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      const int64_t r = hb + 32 * R * q + R * lane;
+      const int64_t left = n - r;
+      const int bytes = left >= R ? 16 : (left > 0 ? (int)left * 8 : 0);
+      cp_async16(wring + slot * kThreads + 32 * R * q + R * lane, colp + (bytes ? r : 0), bytes);
+    }
+  };
+#pragma unroll
+  for (int sl = 0; sl < S - 1; ++sl) {
+    if (sl < nsl) issue(sl, sl);  // warp-uniform
+    cp_async_commit();
+  }
+#pragma unroll
+  for (int c = 0; c < MAXC; ++c) {
+    if (c < J8) {  // warp-uniform
+      long long ah = 0, am = 0, ch = 0, cm = 0;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int sl = 2 * c + h;
+        if (sl + S - 1 < nsl) issue(sl + S - 1, (sl + S - 1) % S);
+        cp_async_commit();
+        cp_async_wait<S - 1>();  // slice sl's copies are done
+        const double* slp = wring + (sl % S) * kThreads;
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+          const double2 xv = *reinterpret_cast<const double2*>(slp + 32 * R * q + R * lane);
+          const int r = h * kThreads + 32 * R * q + R * lane;  // row within the pair
+          const int4 uu = *reinterpret_cast<const int4*>(lu + r);  // limbs of rows r, r + 1
+          const int2 x0 = fx_split(xv.x, kf[c]), x1 = fx_split(xv.y, kf[c]);
+          ah = fx_madw(x0.x, uu.x, ah);
+          am = fx_madw(x0.x, uu.y, am);
+          am = fx_madw(x0.y, uu.x, am);
+          ah = fx_madw(x1.x, uu.z, ah);
+          am = fx_madw(x1.x, uu.w, am);
+          am = fx_madw(x1.y, uu.z, am);
+          if (need_w) {
+            const int4 ww = *reinterpret_cast<const int4*>(lw + r);
+            ch = fx_madw(x0.x, ww.x, ch);
+            cm = fx_madw(x0.x, ww.y, cm);
+            cm = fx_madw(x0.y, ww.x, cm);
+            ch = fx_madw(x1.x, ww.z, ch);
+            cm = fx_madw(x1.x, ww.w, cm);
+            cm = fx_madw(x1.y, ww.z, cm);
+          }
+        }
+      }
+      const int fx = kf[c] - 5;
+      const bool nan = bad || fx == 0x7FF;
+      acc_a[c] += nan ? __longlong_as_double(0x7ff8000000000000ll) : fx_to_double(ah + (am >> 29), ea + fx);
+      if (need_w)
+        acc_c[c] += nan ? __longlong_as_double(0x7ff8000000000000ll) : fx_to_double(ch + (cm >> 29), ec + fx);
+    }
+  }
+  cp_async_wait<0>();
+  // The r8 remainder columns in FP64, four at a time (loads issued together).
+#pragma unroll
+  for (int c0 = 0; c0 < kWarps - 1; c0 += kRemBatch) {
+    if (c0 < r8) {  // block-uniform
+      double x0[kRemBatch], x1[kRemBatch];
+#pragma unroll
+      for (int b = 0; b < kRemBatch; ++b) {
+        const int c = c0 + b;
+        const double* colp = V + (size_t)(J8 * kWarps + c) * ldv;
+        x0[b] = (c < r8 && row0 < n) ? __ldg(colp + row0) : 0.0;
+        x1[b] = (c < r8 && row1 < n) ? __ldg(colp + row1) : 0.0;
       }
 #pragma unroll
       for (int b = 0; b < kRemBatch; ++b) {

@@ -133,17 +133,20 @@ k_maxpy(const VT* __restrict__ V, int64_t ldv, const YT* y_in, YT* y_out, int64_
         int K_arg) {
   __shared__ double sc[kMaxM + 3];
   __shared__ CT scc[kMaxM + 3];
-  __shared__ int sK, s_skip;
+  __shared__ int sK, s_skip, s_colk;
   __shared__ YT* s_out;
   DevState* st = s.st;
   if (threadIdx.x == 0) {
     s_skip = 0;
     s_out = y_out;
+    s_colk = -1;
     if (mode == MAXPY_ARNOLDI || mode == MAXPY_REORTH) {
       s_skip = __ldcg(&st->done);
       sK = __ldcg(&st->maxpy_k);
-      if constexpr (std::is_same<VT, YT>::value)
-        s_out = const_cast<VT*>(V) + (size_t)__ldcg(&st->step) * ldv;
+      if constexpr (std::is_same<VT, YT>::value) {
+        s_colk = __ldcg(&st->step);
+        s_out = const_cast<VT*>(V) + (size_t)s_colk * ldv;
+      }
     } else if (mode == MAXPY_XUPDATE) {
       sK = __ldcg(&st->k);
     } else {
@@ -175,6 +178,9 @@ k_maxpy(const VT* __restrict__ V, int64_t ldv, const YT* y_in, YT* y_out, int64_
   }
   const int ndata = gridDim.x - (mode == MAXPY_ARNOLDI ? 1 : 0);  // CTAs that stream
   YT* out = s_out;
+  // FP64 basis column written: its exponent bound for the fixed-point block dot
+  constexpr bool kNote = std::is_same<VT, double>::value && std::is_same<YT, double>::value;
+  uint32_t emax = 0;
   if (mode == MAXPY_REORTH) y_in = out;  // in place: each element is read, then written, by one thread
   const CT alpha = scc[0];
   const int64_t stride = (int64_t)ndata * blockDim.x;
@@ -215,7 +221,10 @@ k_maxpy(const VT* __restrict__ V, int64_t ldv, const YT* y_in, YT* y_out, int64_
         }
         U o;
 #pragma unroll
-        for (int e = 0; e < E; ++e) o.e[e] = (VT)a[e];
+        for (int e = 0; e < E; ++e) {
+          o.e[e] = (VT)a[e];
+          if constexpr (kNote) emax = max(emax, fx_hi_field(o.e[e]));
+        }
         reinterpret_cast<V16*>(out)[i] = o.v;
       }
       done_rows = nE * E;
@@ -223,7 +232,10 @@ k_maxpy(const VT* __restrict__ V, int64_t ldv, const YT* y_in, YT* y_out, int64_
         CT a0 = alpha * (CT)y_in[i];
         for (int k = 0; k < K; ++k) a0 = fma(scc[1 + k], (CT)V[(size_t)k * ldv + i], a0);
         out[i] = (YT)a0;
+        if constexpr (kNote) emax = max(emax, fx_hi_field(a0));
       }
+      if constexpr (kNote)
+        if (s_colk >= 0) fx_note_max(s.ecol, s_colk, emax);
       return;
     }
   }
@@ -231,7 +243,154 @@ k_maxpy(const VT* __restrict__ V, int64_t ldv, const YT* y_in, YT* y_out, int64_
     CT a0 = alpha * (CT)y_in[i];
     for (int k = 0; k < K; ++k) a0 = fma(scc[1 + k], (CT)V[(size_t)k * ldv + i], a0);
     out[i] = (YT)a0;
+    if constexpr (kNote) emax = max(emax, fx_hi_field((double)a0));
   }
+  if constexpr (kNote)
+    if (s_colk >= 0) fx_note_max(s.ecol, s_colk, emax);
+}
+
+// Arnoldi MAXPY of FP64 cycles with the column products on the integer
+// pipes: u_{j+1} = alpha w + sum_{k<K} c_k u_k (Section IV's MAXPY; the
+// coefficients fold the lagged normalization and T s of Algorithm 4). The
+// sum over the basis columns is formed exactly in integers and rounded to
+// FP64 once per row, then alpha w is added with one FMA:
+//  * each basis value becomes X = trunc(u 2^(58 - E_k)) from its column's
+//    stored bound (Small::ecol), split in 29-bit limbs (fx_split);
+//  * each coefficient becomes an integer C_k = round(c_k 2^e_k) scaled so
+//    that every product C_k X_k shares one scale and |C_k| < 2^57 (2^56 past
+//    64 columns), split in C_k = Ch 2^29 + Cl;
+//  * per row, hh = sum Ch Xh and mid = sum (Ch Xl + Cl Xh) in 64-bit integers
+//    (mid folded into hh every 16 columns), Cl Xl (below 2^-56 of the
+//    largest product) dropped.
+// The last CTA finishes column j-1 of H meanwhile, as in k_maxpy.
+__global__ void __launch_bounds__(kThreads, 4)
+k_maxpy_fx(const double* __restrict__ V, int64_t ldv, const double* __restrict__ w, int64_t n, Small s) {
+  __shared__ int4 sC[kMaxM + 1];  // (Ch, Cl, 5 + column bound field, 0) per column
+  __shared__ uint32_t s_p[kWarps];
+  __shared__ int sK, s_skip, s_colk, s_bad, s_ps;
+  __shared__ double s_alpha;
+  DevState* st = s.st;
+  if (threadIdx.x == 0) {
+    s_skip = __ldcg(&st->done);
+    sK = __ldcg(&st->maxpy_k);
+    s_colk = __ldcg(&st->step);
+    s_alpha = __ldcg(s.coef);
+    s_bad = 0;
+  }
+  __syncthreads();
+  if (s_skip) return;
+  const int K = sK;
+  if (blockIdx.x == gridDim.x - 1) {
+    // column j-1 of H: Givens, residual estimate, stop decision
+    const int j = s_colk - 1;
+    if (j >= 1) {
+      const double h = __ldcg(&s.H[(size_t)(j - 1) * s.ldh + j]);
+      const int stop = finish_completed(s, j - 1, h, false);
+      if (threadIdx.x == 0) {
+        st->grid_syncs += 1;
+        if (stop) st->done = 1;
+      }
+    }
+    return;
+  }
+  // the coefficients' common scale: P = max_k (field(c_k) + field bound of column k)
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  double ck = 0.0;
+  int fk = (int)kFxMinField, pk = 0;
+  if ((int)threadIdx.x < K) {
+    ck = __ldcg(s.coef + 1 + threadIdx.x);
+    fk = (int)max(kFxMinField, __ldcg(s.ecol + threadIdx.x) >> 20);
+    const int gk = (int)fx_field(ck);
+    if (gk == 0x7FF || fk == 0x7FF) s_bad = 1;  // NaN or Inf among the inputs
+    pk = (ck != 0.0) ? gk + fk : 0;
+  }
+  uint32_t pm = __reduce_max_sync(0xffffffffu, (uint32_t)pk);
+  if (lane == 0) s_p[wid] = pm;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t q = 0;
+    for (int v = 0; v < kWarps; ++v) q = max(q, s_p[v]);
+    s_ps = (int)q;
+  }
+  __syncthreads();
+  const int P = s_ps;
+  const int cbits = K > 64 ? 56 : 57;
+  if ((int)threadIdx.x < K) {
+    long long C = 0;
+    if (ck != 0.0 && P > 0) {
+      // |c_k| 2^e < 2^(cbits + field(c_k) + f_k - P) <= 2^cbits
+      const int e = cbits + 1022 - P + fk;
+      C = __double2ll_rn(scalbn(ck, e));
+    }
+    sC[threadIdx.x] = make_int4((int)(C >> 29), (int)(C & 0x1FFFFFFFll), 5 + fk, 0);
+  }
+  __syncthreads();
+  const bool bad = s_bad != 0;
+  const double alpha = s_alpha;
+  double* out = const_cast<double*>(V) + (size_t)s_colk * ldv;
+  const int ndata = gridDim.x - 1;
+  const int64_t stride = (int64_t)ndata * blockDim.x;
+  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int e2 = P - 2044 - cbits;  // sum = (hh + mid / 2^29) 2^(P - 2044 - cbits)
+  uint32_t emax = 0;
+  const int64_t nE = n / 2;
+  // two rows per thread (16-byte loads); ldv is even and the columns 16-byte aligned
+  for (int64_t i = gid; i < nE; i += stride) {
+    long long hh0 = 0, md0 = 0, hh1 = 0, md1 = 0;
+    int k = 0;
+    for (; k < K; k += 4) {
+      double2 x[4];
+#pragma unroll
+      for (int u2 = 0; u2 < 4; ++u2)
+        x[u2] = (k + u2 < K) ? __ldg(reinterpret_cast<const double2*>(V + (size_t)(k + u2) * ldv) + i)
+                             : make_double2(0.0, 0.0);
+#pragma unroll
+      for (int u2 = 0; u2 < 4; ++u2) {
+        if (k + u2 < K) {
+          const int4 c = sC[k + u2];
+          const int2 a = fx_split(x[u2].x, c.z), b = fx_split(x[u2].y, c.z);
+          hh0 = fx_madw(c.x, a.x, hh0);
+          md0 = fx_madw(c.x, a.y, md0);
+          md0 = fx_madw(c.y, a.x, md0);
+          hh1 = fx_madw(c.x, b.x, hh1);
+          md1 = fx_madw(c.x, b.y, md1);
+          md1 = fx_madw(c.y, b.x, md1);
+        }
+      }
+      if ((k & 15) == 12) {  // every 16 columns: carry mid's high part into hh
+        hh0 += md0 >> 29;
+        md0 &= 0x1FFFFFFFll;
+        hh1 += md1 >> 29;
+        md1 &= 0x1FFFFFFFll;
+      }
+    }
+    const double2 wv = __ldg(reinterpret_cast<const double2*>(w) + i);
+    double2 o;
+    o.x = fma(alpha, wv.x, fx_to_double(hh0 + (md0 >> 29), e2));
+    o.y = fma(alpha, wv.y, fx_to_double(hh1 + (md1 >> 29), e2));
+    if (bad) o.x = o.y = __longlong_as_double(0x7ff8000000000000ll);
+    reinterpret_cast<double2*>(out)[i] = o;
+    emax = max(emax, max(fx_hi_field(o.x), fx_hi_field(o.y)));
+  }
+  for (int64_t i = 2 * nE + gid; i < n; i += stride) {  // odd last row
+    long long hh = 0, md = 0;
+    for (int k = 0; k < K; ++k) {
+      const int4 c = sC[k];
+      const int2 a = fx_split(V[(size_t)k * ldv + i], c.z);
+      hh = fx_madw(c.x, a.x, hh);
+      md = fx_madw(c.x, a.y, md);
+      md = fx_madw(c.y, a.x, md);
+      if ((k & 15) == 15) {
+        hh += md >> 29;
+        md &= 0x1FFFFFFFll;
+      }
+    }
+    double o = fma(alpha, w[i], fx_to_double(hh + (md >> 29), e2));
+    if (bad) o = __longlong_as_double(0x7ff8000000000000ll);
+    out[i] = o;
+    emax = max(emax, fx_hi_field(o));
+  }
+  fx_note_max(s.ecol, s_colk, emax);
 }
 
 // Arnoldi MAXPY of GMRES-IR with BF16 basis storage: u_{j+1} = alpha w +
@@ -417,6 +576,18 @@ k_mgs_axpy_dot(double* __restrict__ V, int64_t ldv, int64_t n, Small s) {
   }
 }
 
+// Exponent bounds of the first j columns of a caller's basis (the standalone
+// block dot): ecol[k] = largest (hi word & 0x7FF00000) in column k; ecol
+// cleared before. Grid: (x, j).
+__global__ void k_col_fields(const double* __restrict__ V, int64_t ldv, int64_t n, unsigned int* ecol) {
+  const int k = blockIdx.y;
+  uint32_t emax = 0;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+    emax = max(emax, fx_hi_field(V[(size_t)k * ldv + i]));
+  fx_note_max(ecol, k, emax);
+}
+
 // mode RES_BNORM:    ||b|| -> st->bnorm
 // mode RES_RESIDUAL: r = b - A x -> column 0, ||r|| -> st->rnorm, and the
 //                    cycle state is reset (x == nullptr means x = 0).
@@ -428,13 +599,18 @@ k_residual(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
   __shared__ double sbuf[kWarps];
   __shared__ double red[2];
   double acc = 0.0;
+  uint32_t emax = 0;  // exponent bound of column 0 for the fixed-point block dot
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride) {
     double v = b[r];
     if (mode == RES_RESIDUAL && x) v -= csr_row(rowptr, col, val, x, r);
-    if (mode != RES_BNORM) V0[r] = v;
+    if (mode != RES_BNORM) {
+      V0[r] = v;
+      emax = max(emax, fx_hi_field(v));
+    }
     acc = fma(v, v, acc);
   }
+  if (mode != RES_BNORM) fx_note_max(s.ecol, 0, emax);
   const double tot = block_sum(acc, sbuf);
   if (threadIdx.x == 0) red[0] = tot;
   __syncthreads();
@@ -526,6 +702,9 @@ ReorthKernel reorth_kernel_for(int m) {
 StepKernel<double> step64_for(int m, int stage = 0) {
   return reinterpret_cast<StepKernel<double>>(const_cast<void*>(lsg_steps::step_kernel_f64(m, stage)));
 }
+// The FP64 step kernel of a handle: staging mode 2 runs as mode 6 (the same
+// kernel with the fixed-point block dot) unless the handle turned that off.
+int fx_stage(int stage, int dot_fx) { return (dot_fx && stage == 2) ? 6 : stage; }
 StepKernel<float> step32_for(int m, int stage = 0) {
   return reinterpret_cast<StepKernel<float>>(const_cast<void*>(lsg_steps::step_kernel_f32(m, stage)));
 }
@@ -598,6 +777,9 @@ struct gmres_ctx {
   // 1 tiles, 2 tile pairs; entry capacity; dynamic shared memory at launch.
   int stage64 = 0, cap64 = 0, stage32 = 0, cap32 = 0, stage16 = 0, cap16 = 0;
   int stall_test = 0;  // gmres_test_stall_staging
+  // FP64 block dot of staging mode 2 on the integer pipes (mode 6; on by
+  // default, gmres_set_block_dot)
+  int dot_fx = 1;
   size_t smem64 = 0, smem32 = 0, smem16 = 0;
   size_t lsq_smem = 0;   // dynamic shared memory of k_lsq (rotated Hessenberg)
   std::vector<double> hist;
@@ -705,6 +887,7 @@ gmres_status alloc_small(gmres_ctx* h) {
   const int Pmax = std::max({h->P, h->P32, h->P16});  // rows: one per CTA, then one per group of 16 CTAs
   const size_t o_pa = take(sizeof(double) * (size_t)(Pmax + (Pmax + kGridGroup - 1) / kGridGroup) * nvmax);
   const size_t o_raw = take(sizeof(double) * nvmax);
+  const size_t o_ec = take(sizeof(unsigned int) * (m + 2));
   if (h->small) cudaFree(h->small);
   h->small = nullptr;
   CUDA_TRY(h, cudaMalloc(&h->small, off));
@@ -723,6 +906,7 @@ gmres_status alloc_small(gmres_ctx* h) {
   h->s.hist = reinterpret_cast<double*>(b + o_hi);
   h->s.partials = reinterpret_cast<double*>(b + o_pa);
   h->s.raw = reinterpret_cast<double*>(b + o_raw);
+  h->s.ecol = reinterpret_cast<unsigned int*>(b + o_ec);
   h->hist.assign(h->s.hist_cap, 0.0);
   return GMRES_OK;
 }
@@ -768,6 +952,8 @@ gmres_status launch_cycle(gmres_ctx* h, int kmax) {
               h->V32, h->ldv, h->w32, nullptr, h->n, h->s, MAXPY_ARNOLDI, 0);
         else if (h->prec == GMRES_IR_BF16)
           k_maxpy_bf16<<<h->grid_stream + 1, kThreads, 0, h->stream>>>(h->V16, h->ldv, h->w32, h->n, h->s);
+        else if (fx_stage(h->stage64, h->dot_fx) == 6)  // large systems: the fixed-point form with the step's
+          k_maxpy_fx<<<h->grid_stream + 1, kThreads, 0, h->stream>>>(h->V, h->ldv, h->w, h->n, h->s);
         else
           k_maxpy<double, double, double><<<h->grid_stream + 1, kThreads, 0, h->stream>>>(
               h->V, h->ldv, h->w, nullptr, h->n, h->s, MAXPY_ARNOLDI, 0);
@@ -1190,7 +1376,13 @@ gmres_status gmres_create(const gmres_csr* A, int m_restart, double tol, gmres_h
       h->err = "cudaFuncSetAttribute / occupancy query of the step kernels failed";
       return bail(GMRES_ERR_CUDA);
     }
-    h->step = step64_for(m, h->stage64);
+    if ((h->stage64 == 2 &&
+         raise_smem_limit(reinterpret_cast<const void*>(step64_for(m, 6)), h->smem64) != cudaSuccess) ||
+        raise_smem_limit(reinterpret_cast<const void*>(step64_for(m, 0)), h->step_smem) != cudaSuccess) {
+      h->err = "cudaFuncSetAttribute of the fixed-point or unstaged step kernel failed";
+      return bail(GMRES_ERR_CUDA);
+    }
+    h->step = step64_for(m, fx_stage(h->stage64, h->dot_fx));
     h->step32 = step32_for(m, h->stage32);
     h->step16 = step16_for(m, h->stage16);
   }
@@ -1291,6 +1483,8 @@ gmres_status gmres_solve(gmres_handle h, const double* b, double* x, gmres_info*
     int prev_total = 0, cycles = 0;
     for (;;) {
       pr = prof_begin(h, PC_RES, 1, 0);
+      // a new cycle rewrites every basis column: clear their exponent bounds
+      CUDA_TRY(h, cudaMemsetAsync(h->s.ecol, 0, sizeof(unsigned int) * (h->m + 2), h->stream));
       k_residual<<<P, kThreads, 0, h->stream>>>(h->rowptr, h->col, h->val, b, x,
                                                  h->prec != GMRES_FP64 ? h->r64 : h->V, h->n, h->s,
                                                  RES_RESIDUAL, 0);
@@ -1427,6 +1621,18 @@ gmres_status gmres_destroy(gmres_handle h) {
 
 const char* gmres_last_error(gmres_handle h) { return h ? h->err.c_str() : g_create_err.c_str(); }
 
+gmres_status gmres_set_block_dot(gmres_handle h, int fixed_point, int* active) {
+  if (!h) return GMRES_ERR_ARG;
+  h->dot_fx = fixed_point ? 1 : 0;
+  auto k = step64_for(h->m, fx_stage(h->stage64, h->dot_fx));
+  if (k != h->step) {
+    destroy_graphs(h);  // captured cycles hold the other kernel
+    h->step = k;
+  }
+  if (active) *active = fx_stage(h->stage64, h->dot_fx) == 6;
+  return GMRES_OK;
+}
+
 gmres_status gmres_test_stall_staging(gmres_handle h, int on, int* staged) {
   if (!h) return GMRES_ERR_ARG;
   h->stall_test = on ? 1 : 0;
@@ -1468,8 +1674,24 @@ gmres_status lsg_block_dot(gmres_handle h, const double* V, int64_t ldv, int j, 
   if (!h) return GMRES_ERR_ARG;
   if (j < 0 || j > h->m) return fail(h, GMRES_ERR_ARG, "j must be in [0, m]");
   if ((j > 0 && (!V || ldv < h->n)) || !u || !w || !X) return fail(h, GMRES_ERR_ARG, "bad pointer or ldv");
-  h->step<<<h->P, kThreads, h->smem64, h->stream>>>(h->rowptr, h->col, h->val, V, ldv, u, w, h->n, h->s, j,
-                                                     use_spmv, h->s.raw, h->stage64, h->cap64);
+  CUDA_TRY(h, cudaSetDevice(h->device));
+  if (j > 0) {  // the caller's columns carry no stored exponent bounds: measure them
+    CUDA_TRY(h, cudaMemsetAsync(h->s.ecol, 0, sizeof(unsigned int) * (h->m + 2), h->stream));
+    k_col_fields<<<dim3((unsigned)std::max(1, h->grid_stream / std::max(1, j)), (unsigned)j), kThreads, 0,
+                   h->stream>>>(V, ldv, h->n, h->s.ecol);
+    LAUNCH_CHECK(h);
+  }
+  // The staged kernels copy basis slices with 16-byte asynchronous copies,
+  // which need 16-byte aligned columns: a caller's basis with an odd leading
+  // dimension or an unaligned base goes through the kernel that loads the
+  // basis with plain loads (staging mode 0, FP64 products).
+  const bool aligned = ((reinterpret_cast<uintptr_t>(V) & 15) == 0 && (ldv & 1) == 0) || j == 0;
+  if (aligned)
+    h->step<<<h->P, kThreads, h->smem64, h->stream>>>(h->rowptr, h->col, h->val, V, ldv, u, w, h->n, h->s, j,
+                                                       use_spmv, h->s.raw, h->stage64, h->cap64);
+  else
+    step64_for(h->m, 0)<<<h->P, kThreads, h->step_smem, h->stream>>>(h->rowptr, h->col, h->val, V, ldv, u, w, h->n,
+                                                                     h->s, j, use_spmv, h->s.raw, 0, 0);
   LAUNCH_CHECK(h);
   CUDA_TRY(h, cudaMemcpyAsync(X, h->s.raw, sizeof(double) * (2 * j + 2), cudaMemcpyDeviceToHost, h->stream));
   CUDA_TRY(h, cudaStreamSynchronize(h->stream));
@@ -1555,6 +1777,7 @@ gmres_status gmres_arnoldi(gmres_handle h, const double* r0, int k, double* V_ou
   if ((st = write_state(h)) != GMRES_OK) return st;
   CUDA_TRY(h, cudaMemsetAsync(h->s.H, 0, sizeof(double) * h->s.ldh * h->m, h->stream));
   CUDA_TRY(h, cudaMemsetAsync(h->s.T, 0, sizeof(double) * h->s.ldh * h->s.ldh, h->stream));
+  CUDA_TRY(h, cudaMemsetAsync(h->s.ecol, 0, sizeof(unsigned int) * (h->m + 2), h->stream));
   k_residual<<<h->P, kThreads, 0, h->stream>>>(h->rowptr, h->col, h->val, r0, nullptr, h->V, h->n, h->s, RES_START, k);
   LAUNCH_CHECK(h);
   if ((st = launch_cycle(h, k)) != GMRES_OK) return st;

@@ -11,12 +11,14 @@
 namespace lsg_steps {
 // Host stub of the step kernel for restart length m and staging mode (0 off,
 // 1 tiles, 2 tile pairs with the block dot's column ring, 3 tiles with their
-// basis columns, 4 tile pairs with theirs, 5 tile pairs without the ring; 3
-// and 4 for the BF16 basis only); callers cast it to their StepKernel type.
+// basis columns, 4 tile pairs with theirs, 5 tile pairs without the ring, 6
+// mode 2 with the fixed-point block dot; 3 and 4 for the BF16 basis only, 6
+// for FP64 only); callers cast it to their StepKernel type.
 const void* step_kernel_f64_s0(int m);
 const void* step_kernel_f64_s1(int m);
 const void* step_kernel_f64_s2(int m);
 const void* step_kernel_f64_s5(int m);
+const void* step_kernel_f64_s6(int m);
 const void* step_kernel_f32_s0(int m);
 const void* step_kernel_f32_s1(int m);
 const void* step_kernel_f32_s2(int m);
@@ -29,9 +31,12 @@ const void* step_kernel_bf16_s3(int m);
 const void* step_kernel_bf16_s4(int m);
 // Modes 3 and 4 are built for the BF16 basis only: the FP64 basis tile does not fit
 // beside two resident CTAs, and FP32 cycles ran faster at three CTAs per SM
-// reading the basis themselves than at two with it staged.
+// reading the basis themselves than at two with it staged. Mode 6 is FP64
+// only: mode 2 with the block dot's full columns on the integer pipes
+// (exact fixed-point products, tile_pair_dot_rows_fx).
 inline const void* step_kernel_f64(int m, int stage) {
-  return stage == 5   ? step_kernel_f64_s5(m)
+  return stage == 6   ? step_kernel_f64_s6(m)
+         : stage == 5 ? step_kernel_f64_s5(m)
          : stage == 2 ? step_kernel_f64_s2(m)
          : stage == 1 ? step_kernel_f64_s1(m)
                       : step_kernel_f64_s0(m);
@@ -76,6 +81,7 @@ k_one_reduce_step(const int32_t* __restrict__ rowptr, const int32_t* __restrict_
   __shared__ int s_j, s_tail, s_skip, s_stage_off;
   __shared__ uint64_t s_bar, s_barV;
   __shared__ uint32_t s_extra;
+  __shared__ uint32_t s_ex[2 * kWarps];  // STAGE 6: per-warp exponent maxima of u and w
   DevState* st = s.st;
   if (threadIdx.x == 0) {
     if (raw_out) {
@@ -113,11 +119,22 @@ k_one_reduce_step(const int32_t* __restrict__ rowptr, const int32_t* __restrict_
 #pragma unroll
   for (int c = 0; c < kWarps - 1; ++c) rem_a[c] = rem_c[c] = VT(0);
   VT sig = VT(0), dd = VT(0);
+  // STAGE 6: 5 + the stored exponent bound of each full column this warp owns
+  int kf[MAXC];
+#pragma unroll
+  for (int c = 0; c < MAXC; ++c) {
+    kf[c] = 5 + (int)kFxMinField;
+    if constexpr (STAGE == 6) {
+      const int k = (threadIdx.x >> 5) + c * kWarps;
+      if (c < J8) kf[c] = 5 + (int)max(kFxMinField, __ldcg(s.ecol + k) >> 20);
+    }
+  }
 
   const int64_t ntiles = (n + kThreads - 1) / kThreads;
   if constexpr (STAGE != 0) {
     // Staged CSR (STAGE 1: one tile per unit, 2: tile pairs, 5: the same
-    // without the block dot's column ring; 3: one tile per unit, and the
+    // without the block dot's column ring, 6: STAGE 2 with the full columns'
+    // products in exact fixed point on the integer pipes; 3: one tile per unit, and the
     // tile's basis columns too; 4: tile pairs and their basis columns): the bulk-copy engine fetches the next unit's rowptr slice,
     // indices and values into shared memory while this one's block dot runs
     // (and, for STAGES 3 and 4, the next unit's basis columns while this
@@ -125,7 +142,7 @@ k_one_reduce_step(const int32_t* __restrict__ rowptr, const int32_t* __restrict_
     // read by this instantiation: a unit whose copy did not arrive in time, or
     // that does not fit the buffer (the host sizes it for the largest unit),
     // sets the stalled flag and contributes a zero SpMV.
-    constexpr bool kPairs = STAGE == 2 || STAGE == 4 || STAGE == 5;  // units of two tiles
+    constexpr bool kPairs = STAGE == 2 || STAGE == 4 || STAGE == 5 || STAGE == 6;  // units of two tiles
     constexpr bool kStageV = STAGE == 3 || STAGE == 4;               // basis columns staged too
     const int U = kPairs ? 2 * kThreads : kThreads;
     const int64_t units = (n + U - 1) / U;
@@ -265,6 +282,11 @@ k_one_reduce_step(const int32_t* __restrict__ rowptr, const int32_t* __restrict_
             tile_pair_dot_rows_pf<MAXC, SV>(unit, n, V, ldv, need_w, J8, r8, ur0, wr0, ur1, wr1, su, sw,
                                             reinterpret_cast<SV*>(cs.val + stage_cap), acc_a, acc_c, rem_a, rem_c,
                                             sig, dd, next);
+          else if constexpr (STAGE == 6)
+            // the same ring; the full columns' products on the integer pipes
+            tile_pair_dot_rows_fx<MAXC>(unit, n, V, ldv, need_w, J8, r8, ur0, wr0, ur1, wr1, su, sw,
+                                        reinterpret_cast<double*>(cs.val + stage_cap), kf, acc_a, acc_c, rem_a,
+                                        rem_c, sig, dd, s_ex, next);
           else
             tile_pair_dot_rows<MAXC, SV, VT>(unit, n, V, ldv, need_w, J8, r8, ur0, wr0, ur1, wr1, su, sw, acc_a,
                                              acc_c, rem_a, rem_c, sig, dd, next);

@@ -88,7 +88,7 @@ class SolveInfo:
 
 EXPORTS = ["gmres_create", "gmres_set", "gmres_set_tol", "gmres_set_stream", "gmres_solve",
            "gmres_solve_host", "gmres_history", "gmres_destroy", "gmres_last_error", "lsg_spmv",
-           "lsg_block_dot", "lsg_maxpy", "gmres_arnoldi", "gmres_set_profile", "gmres_profile", "gmres_test_stall_staging",
+           "lsg_block_dot", "lsg_maxpy", "gmres_arnoldi", "gmres_set_profile", "gmres_profile", "gmres_test_stall_staging", "gmres_set_block_dot",
            "lsg_block_dot_noalloc", "gmres_batch_create", "gmres_batch_set_grid", "gmres_batch_get_grid",
            "gmres_batch_set_rows_per_thread", "gmres_batch_get_rows_per_thread", "gmres_batch_set_stream", "gmres_batch_solve",
            "gmres_batch_solve_host", "gmres_batch_set_profile", "gmres_batch_profile", "gmres_batch_launch_log",
@@ -129,6 +129,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "gmres_arnoldi": ([P, P, I, P, P, P, ctypes.POINTER(I)], I),
         "gmres_set_profile": ([P, I], I),
         "gmres_test_stall_staging": ([P, I, ctypes.POINTER(I)], I),
+        "gmres_set_block_dot": ([P, I, ctypes.POINTER(I)], I),
         "lsg_block_dot_noalloc": ([P, P, P, I64, P, I64, I, P, P, I, P, P], I),
         "gmres_profile": ([P, I, ctypes.POINTER(D), ctypes.POINTER(I64), ctypes.POINTER(D),
                            ctypes.POINTER(D)], I),
@@ -282,6 +283,14 @@ class Solver:
 
     def set_profile(self, on: bool):
         self._check(self.lib.gmres_set_profile(self.h, int(on)))
+
+    def set_block_dot(self, fixed_point: bool) -> bool:
+        """gmres_set_block_dot: FP64 block dot with exact fixed-point products on
+        the integer pipes (True, the default) or FP64 FMAs; returns whether the
+        handle's step kernel uses the fixed-point form."""
+        active = ctypes.c_int(0)
+        self._check(self.lib.gmres_set_block_dot(self.h, int(fixed_point), ctypes.byref(active)))
+        return bool(active.value)
 
     def test_stall_staging(self, on: bool) -> bool:
         """Make the bounded waits of the CSR staging run out (testing); returns
