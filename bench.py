@@ -103,9 +103,9 @@ FP64_DFMA_PER_CLK_SM = 2  # B300: 1.25 TFLOP/s nominal FP64 = 148 SMs x 2 DFMA/c
 # for the kernel builds those captures measured; set to None when a kernel
 # changes.
 STEP_TRAFFIC_RATIO = 1.048
-# The same ratio for the FP64 step with fixed-point products (staging mode 6),
-# None until an ncu capture of that kernel build gives it.
-STEP6_TRAFFIC_RATIO = None
+# The same ratio for the FP64 step with fixed-point products (staging mode 6):
+# 128^3 7-point at j = 10 and 11.
+STEP6_TRAFFIC_RATIO = 1.003
 STEP32_TRAFFIC_RATIO = {"27pt": 1.014, "7pt": 1.005}
 
 
