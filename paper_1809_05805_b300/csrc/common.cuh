@@ -956,27 +956,32 @@ __device__ __forceinline__ double fx_to_double(long long t, int e2) {
   return __longlong_as_double((long long)((((unsigned long long)ef) << 52) + m | sgn));
 }
 
-// The FP64 block dot of tile pair pp as tile_pair_dot_rows_pf (the same
-// ring of column slices, the same remainder columns in FP64), with the full
-// columns' products on the integer pipes. Loop order: column by column, both
-// halves of the tile pair in turn (the ring streams (column, half) slices),
-// so that each column's 16 products per lane are summed exactly before one
-// conversion. kf[c] = 5 + f of column wid + 8 c (its stored bound). The u and
-// w values of the pair are replaced in su, sw by their limbs (int2 per row)
-// relative to the pair's own bounds; s_ex holds 2 kWarps words.
+// The FP64 block dot of tile pair pp on the integer pipes, with the same ring
+// of column slices as tile_pair_dot_rows_pf. The ring streams half-column
+// slices (256 rows of one column): warp w takes both halves of its full
+// columns w + 8 c (c < J8) and the remainder half-columns r = w and r = w + 8
+// of the r8 = j mod 8 last columns (half-column r: column 8 J8 + r / 2, half
+// r mod 2), so that no warp does more than half a column more than another.
+// Each lane sums a column's 16 products (8 for a remainder half-column)
+// exactly, then converts the sum to FP64 once (one FP64 add per column and
+// tile pair). kf[c] = 5 + f of column w + 8 c, kfr[q] of remainder slot q
+// (f: its stored exponent bound). The u and w values of the pair are replaced
+// in su, sw by their limbs (int2 per row) relative to the pair's own bounds;
+// s_ex holds 2 kWarps words. w may be absent (need_w false: the cycle's tail,
+// which needs only V^T u); then wr0 = wr1 = 0.
 template <int MAXC, typename Hook>
-__device__ __forceinline__ void tile_pair_dot_rows_fx(int64_t pp, int64_t n, const double* __restrict__ V,
-                                                      int64_t ldv, bool need_w, int J8, int r8, double ur0,
-                                                      double wr0, double ur1, double wr1, double* su, double* sw,
-                                                      double* ring, const int (&kf)[MAXC], double (&acc_a)[MAXC],
-                                                      double (&acc_c)[MAXC], double (&rem_a)[kWarps - 1],
-                                                      double (&rem_c)[kWarps - 1], double& sig, double& dd,
-                                                      uint32_t* s_ex, Hook hook) {
+__device__ __forceinline__ void tile_pair_dot_rows_fx(int64_t pp, int64_t n,
+                                                      const double* __restrict__ V, int64_t ldv, bool need_w, int J8,
+                                                      int r8, double ur0, double wr0, double ur1, double wr1,
+                                                      double* su, double* sw, double* ring, const int (&kf)[MAXC],
+                                                      const int (&kfr)[2], double (&acc_a)[MAXC],
+                                                      double (&acc_c)[MAXC], double (&rem_a)[2],
+                                                      double (&rem_c)[2], double& sig, double& dd, uint32_t* s_ex,
+                                                      Hook hook) {
   constexpr int S = pf_stages<double>();  // ring slices per warp
   constexpr int R = 2;                    // rows per 16-byte copy
   constexpr int NQ = kRowsPerLane / R;    // copies per lane per slice
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int64_t row0 = pp * (2 * kThreads) + threadIdx.x, row1 = row0 + kThreads;
   sig = fma(ur0, ur0, sig);
   dd = fma(ur0, wr0, dd);
   sig = fma(ur1, ur1, sig);
@@ -1005,13 +1010,26 @@ __device__ __forceinline__ void tile_pair_dot_rows_fx(int64_t pp, int64_t n, con
   lw[kThreads + threadIdx.x] = fx_split(wr1, 5 + (int)fw);
   __syncthreads();
   const bool bad = fu == 0x7FFu || fw == 0x7FFu;  // NaN or Inf among the pair's u, w
-  // x u = Xh Uh 2^(f_x + f_u - 2044 - 58) + ...: the flush scales
+  // x u = (Xh Uh + (Xh Ul + Xl Uh) / 2^29) 2^(f_x + f_u - 2102): the flush scales
   const int ea = (int)fu - 2102, ec = (int)fw - 2102;
   double* wring = ring + wid * (S * kThreads);
-  const int nsl = 2 * J8;  // (column, half) slices this warp streams
+  const int nr = (wid < 2 * r8 ? 1 : 0) + (wid + kWarps < 2 * r8 ? 1 : 0);  // remainder half-columns of this warp
+  const int nsl = 2 * J8 + nr;  // slices this warp streams
+  // column and half of this warp's slice sl
+  auto locate = [&](int sl, int& col, int& h) {
+    if (sl < 2 * J8) {
+      col = wid + (sl >> 1) * kWarps;
+      h = sl & 1;
+    } else {
+      const int r = wid + (sl - 2 * J8) * kWarps;
+      col = J8 * kWarps + (r >> 1);
+      h = r & 1;
+    }
+  };
   auto issue = [&](int sl, int slot) {
-    const int c = sl >> 1, h = sl & 1;
-    const double* colp = V + (size_t)(wid + c * kWarps) * ldv;
+    int col, h;
+    locate(sl, col, h);
+    const double* colp = V + (size_t)col * ldv;
     const int64_t hb = pp * (2 * kThreads) + h * kThreads;
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
@@ -1020,6 +1038,43 @@ __device__ __forceinline__ void tile_pair_dot_rows_fx(int64_t pp, int64_t n, con
       const int bytes = left >= R ? 16 : (left > 0 ? (int)left * 8 : 0);
       cp_async16(wring + slot * kThreads + 32 * R * q + R * lane, colp + (bytes ? r : 0), bytes);
     }
+  };
+  // the products of slice sl (half h of a column with shift kfc) into the
+  // exact sums ah, am (x u) and ch, cm (x w)
+  auto slice = [&](int sl, int h, int kfc, long long& ah, long long& am, long long& ch, long long& cm) {
+    if (sl + S - 1 < nsl) issue(sl + S - 1, (sl + S - 1) % S);
+    cp_async_commit();
+    cp_async_wait<S - 1>();  // slice sl's copies are done
+    const double* slp = wring + (sl % S) * kThreads;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      const double2 xv = *reinterpret_cast<const double2*>(slp + 32 * R * q + R * lane);
+      const int r = h * kThreads + 32 * R * q + R * lane;       // row within the pair
+      const int4 uu = *reinterpret_cast<const int4*>(lu + r);  // limbs of rows r, r + 1
+      const int2 x0 = fx_split(xv.x, kfc), x1 = fx_split(xv.y, kfc);
+      ah = fx_madw(x0.x, uu.x, ah);
+      am = fx_madw(x0.x, uu.y, am);
+      am = fx_madw(x0.y, uu.x, am);
+      ah = fx_madw(x1.x, uu.z, ah);
+      am = fx_madw(x1.x, uu.w, am);
+      am = fx_madw(x1.y, uu.z, am);
+      if (need_w) {
+        const int4 ww = *reinterpret_cast<const int4*>(lw + r);
+        ch = fx_madw(x0.x, ww.x, ch);
+        cm = fx_madw(x0.x, ww.y, cm);
+        cm = fx_madw(x0.y, ww.x, cm);
+        ch = fx_madw(x1.x, ww.z, ch);
+        cm = fx_madw(x1.x, ww.w, cm);
+        cm = fx_madw(x1.y, ww.z, cm);
+      }
+    }
+  };
+  auto flush = [&](int kfc, long long ah, long long am, long long ch, long long cm, double& a, double& c) {
+    const int fx = kfc - 5;
+    const bool nan = bad || fx == 0x7FF;
+    const double qnan = __longlong_as_double(0x7ff8000000000000ll);
+    a += nan ? qnan : fx_to_double(ah + (am >> 29), ea + fx);
+    if (need_w) c += nan ? qnan : fx_to_double(ch + (cm >> 29), ec + fx);
   };
 #pragma unroll
   for (int sl = 0; sl < S - 1; ++sl) {
@@ -1030,69 +1085,77 @@ __device__ __forceinline__ void tile_pair_dot_rows_fx(int64_t pp, int64_t n, con
   for (int c = 0; c < MAXC; ++c) {
     if (c < J8) {  // warp-uniform
       long long ah = 0, am = 0, ch = 0, cm = 0;
+      slice(2 * c, 0, kf[c], ah, am, ch, cm);
+      slice(2 * c + 1, 1, kf[c], ah, am, ch, cm);
+      flush(kf[c], ah, am, ch, cm, acc_a[c], acc_c[c]);
+    }
+  }
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int sl = 2 * c + h;
-        if (sl + S - 1 < nsl) issue(sl + S - 1, (sl + S - 1) % S);
-        cp_async_commit();
-        cp_async_wait<S - 1>();  // slice sl's copies are done
-        const double* slp = wring + (sl % S) * kThreads;
-#pragma unroll
-        for (int q = 0; q < NQ; ++q) {
-          const double2 xv = *reinterpret_cast<const double2*>(slp + 32 * R * q + R * lane);
-          const int r = h * kThreads + 32 * R * q + R * lane;  // row within the pair
-          const int4 uu = *reinterpret_cast<const int4*>(lu + r);  // limbs of rows r, r + 1
-          const int2 x0 = fx_split(xv.x, kf[c]), x1 = fx_split(xv.y, kf[c]);
-          ah = fx_madw(x0.x, uu.x, ah);
-          am = fx_madw(x0.x, uu.y, am);
-          am = fx_madw(x0.y, uu.x, am);
-          ah = fx_madw(x1.x, uu.z, ah);
-          am = fx_madw(x1.x, uu.w, am);
-          am = fx_madw(x1.y, uu.z, am);
-          if (need_w) {
-            const int4 ww = *reinterpret_cast<const int4*>(lw + r);
-            ch = fx_madw(x0.x, ww.x, ch);
-            cm = fx_madw(x0.x, ww.y, cm);
-            cm = fx_madw(x0.y, ww.x, cm);
-            ch = fx_madw(x1.x, ww.z, ch);
-            cm = fx_madw(x1.x, ww.w, cm);
-            cm = fx_madw(x1.y, ww.z, cm);
-          }
-        }
-      }
-      const int fx = kf[c] - 5;
-      const bool nan = bad || fx == 0x7FF;
-      acc_a[c] += nan ? __longlong_as_double(0x7ff8000000000000ll) : fx_to_double(ah + (am >> 29), ea + fx);
-      if (need_w)
-        acc_c[c] += nan ? __longlong_as_double(0x7ff8000000000000ll) : fx_to_double(ch + (cm >> 29), ec + fx);
+  for (int q = 0; q < 2; ++q) {
+    if (q < nr) {  // warp-uniform
+      const int r = wid + q * kWarps;
+      long long ah = 0, am = 0, ch = 0, cm = 0;
+      slice(2 * J8 + q, r & 1, kfr[q], ah, am, ch, cm);
+      flush(kfr[q], ah, am, ch, cm, rem_a[q], rem_c[q]);
     }
   }
   cp_async_wait<0>();
-  // The r8 remainder columns in FP64, four at a time (loads issued together).
+  __syncthreads();
+}
+
+// The CTA's partial sums of the fixed-point block dot (tile_pair_dot_rows_fx):
+// red[0:j] = a, red[j:2j] = c, red[2j] = sigma, red[2j+1] = d. Full column
+// wid + 8 c comes from warp wid alone; remainder column 8 J8 + q from the two
+// warps holding its halves (half-columns 2q and 2q + 1: warps 2q mod 8 and
+// 2q + 1 mod 8, slot q / 4), added in that order. Warp totals by the
+// butterfly reduce-scatter; fixed order throughout.
+template <int MAXC>
+__device__ __forceinline__ void cta_partials_fx(double (&acc_a)[MAXC], double (&acc_c)[MAXC], double (&rem_a)[2],
+                                                double (&rem_c)[2], double sig, double dd, int j, int J8, int r8,
+                                                double* red) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  constexpr int kSlots = 2 * MAXC + 4 + 2;
+  constexpr int kChunks = (kSlots + 31) / 32;
+  double v[kChunks * 32];
 #pragma unroll
-  for (int c0 = 0; c0 < kWarps - 1; c0 += kRemBatch) {
-    if (c0 < r8) {  // block-uniform
-      double x0[kRemBatch], x1[kRemBatch];
+  for (int i = 0; i < kChunks * 32; ++i) v[i] = 0.0;
 #pragma unroll
-      for (int b = 0; b < kRemBatch; ++b) {
-        const int c = c0 + b;
-        const double* colp = V + (size_t)(J8 * kWarps + c) * ldv;
-        x0[b] = (c < r8 && row0 < n) ? __ldg(colp + row0) : 0.0;
-        x1[b] = (c < r8 && row1 < n) ? __ldg(colp + row1) : 0.0;
-      }
+  for (int c = 0; c < MAXC; ++c) {
+    v[c] = acc_a[c];
+    v[MAXC + c] = acc_c[c];
+  }
+  v[2 * MAXC] = rem_a[0];
+  v[2 * MAXC + 1] = rem_a[1];
+  v[2 * MAXC + 2] = rem_c[0];
+  v[2 * MAXC + 3] = rem_c[1];
+  v[kSlots - 2] = sig;
+  v[kSlots - 1] = dd;
+  __shared__ double sx[6][kWarps];  // per warp: rem_a[0..1], rem_c[0..1], sigma, d
 #pragma unroll
-      for (int b = 0; b < kRemBatch; ++b) {
-        const int c = c0 + b;
-        if (c < kWarps - 1 && c < r8) {
-          rem_a[c] = fma(x0[b], ur0, rem_a[c]);
-          rem_a[c] = fma(x1[b], ur1, rem_a[c]);
-          if (need_w) {
-            rem_c[c] = fma(x0[b], wr0, rem_c[c]);
-            rem_c[c] = fma(x1[b], wr1, rem_c[c]);
-          }
-        }
-      }
+  for (int ch = 0; ch < kChunks; ++ch) {
+    const double tot = warp_reduce_scatter32(v + 32 * ch);
+    const int slot = 32 * ch + lane;
+    if (slot < MAXC) {
+      if (slot < J8) red[wid + slot * kWarps] = tot;  // column wid + 8 slot belongs to this warp
+    } else if (slot < 2 * MAXC) {
+      if (slot - MAXC < J8) red[j + wid + (slot - MAXC) * kWarps] = tot;
+    } else if (slot < kSlots) {
+      sx[slot - 2 * MAXC][wid] = tot;
     }
+  }
+  __syncthreads();
+  const int t = threadIdx.x;
+  if (t < 2 * r8) {  // remainder column q = t mod r8, a (t < r8) or c
+    const int q = t < r8 ? t : t - r8;
+    const int base = t < r8 ? 0 : 2;  // rem_a or rem_c slots
+    const int h0 = 2 * q, h1 = 2 * q + 1;  // its half-columns
+    const double x0 = sx[base + h0 / kWarps][h0 % kWarps], x1 = sx[base + h1 / kWarps][h1 % kWarps];
+    red[(t < r8 ? 0 : j) + J8 * kWarps + q] = x0 + x1;
+  } else if (t == 2 * r8 || t == 2 * r8 + 1) {  // sigma, d: the 8 warps in warp order
+    const int k = 4 + (t - 2 * r8);
+    double s2 = 0.0;
+    for (int w2 = 0; w2 < kWarps; ++w2) s2 += sx[k][w2];
+    red[2 * j + (t - 2 * r8)] = s2;
   }
   __syncthreads();
 }

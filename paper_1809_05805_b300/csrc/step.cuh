@@ -120,13 +120,24 @@ k_one_reduce_step(const int32_t* __restrict__ rowptr, const int32_t* __restrict_
   for (int c = 0; c < kWarps - 1; ++c) rem_a[c] = rem_c[c] = VT(0);
   VT sig = VT(0), dd = VT(0);
   // STAGE 6: 5 + the stored exponent bound of each full column this warp owns
-  int kf[MAXC];
+  // and of its remainder half-columns (slots q = 0, 1: half-column wid + 8 q of
+  // columns 8 J8 ..), and their FP64 sums
+  int kf[MAXC], kfr[2];
+  double fr_a[2] = {0.0, 0.0}, fr_c[2] = {0.0, 0.0};
 #pragma unroll
   for (int c = 0; c < MAXC; ++c) {
     kf[c] = 5 + (int)kFxMinField;
     if constexpr (STAGE == 6) {
       const int k = (threadIdx.x >> 5) + c * kWarps;
       if (c < J8) kf[c] = 5 + (int)max(kFxMinField, __ldcg(s.ecol + k) >> 20);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    kfr[q] = 5 + (int)kFxMinField;
+    if constexpr (STAGE == 6) {
+      const int r = (threadIdx.x >> 5) + q * kWarps;
+      if (r < 2 * r8) kfr[q] = 5 + (int)max(kFxMinField, __ldcg(s.ecol + J8 * kWarps + (r >> 1)) >> 20);
     }
   }
 
@@ -283,10 +294,10 @@ k_one_reduce_step(const int32_t* __restrict__ rowptr, const int32_t* __restrict_
                                             reinterpret_cast<SV*>(cs.val + stage_cap), acc_a, acc_c, rem_a, rem_c,
                                             sig, dd, next);
           else if constexpr (STAGE == 6)
-            // the same ring; the full columns' products on the integer pipes
-            tile_pair_dot_rows_fx<MAXC>(unit, n, V, ldv, need_w, J8, r8, ur0, wr0, ur1, wr1, su, sw,
-                                        reinterpret_cast<double*>(cs.val + stage_cap), kf, acc_a, acc_c, rem_a,
-                                        rem_c, sig, dd, s_ex, next);
+            // the same ring; every column's products on the integer pipes
+            tile_pair_dot_rows_fx<MAXC>(unit, n, V, ldv, need_w, J8, r8, ur0, wr0, ur1, wr1,
+                                        su, sw, reinterpret_cast<double*>(cs.val + stage_cap), kf, kfr, acc_a,
+                                        acc_c, fr_a, fr_c, sig, dd, s_ex, next);
           else
             tile_pair_dot_rows<MAXC, SV, VT>(unit, n, V, ldv, need_w, J8, r8, ur0, wr0, ur1, wr1, su, sw, acc_a,
                                              acc_c, rem_a, rem_c, sig, dd, next);
@@ -312,7 +323,15 @@ k_one_reduce_step(const int32_t* __restrict__ rowptr, const int32_t* __restrict_
           ur1 = ld_as<VT>(u + row1);
           if (need_w) wr1 = w[row1];
         }
-        if (kPairs)
+        if constexpr (STAGE == 6) {
+          // the ring sits where the SpMV launches keep it, behind the CSR buffer
+          extern __shared__ __align__(16) double dyn6[];
+          double* ring = reinterpret_cast<double*>(reinterpret_cast<int32_t*>(dyn6) + (U + 4) + stage_cap) +
+                         stage_cap;
+          tile_pair_dot_rows_fx<MAXC>(unit, n, V, ldv, need_w,
+                                      J8, r8, ur0, wr0, ur1, wr1, su, sw, ring, kf, kfr, acc_a, acc_c, fr_a, fr_c,
+                                      sig, dd, s_ex, NoHook{});
+        } else if (kPairs)
           tile_pair_dot_rows<MAXC, SV, VT>(unit, n, V, ldv, need_w, J8, r8, ur0, wr0, ur1, wr1, su, sw, acc_a,
                                            acc_c, rem_a, rem_c, sig, dd, NoHook{});
         else
@@ -334,7 +353,10 @@ k_one_reduce_step(const int32_t* __restrict__ rowptr, const int32_t* __restrict_
                                    acc_c, rem_a, rem_c, sig, dd);
   }
 
-  cta_partials<MAXC, VT>(acc_a, acc_c, rem_a, rem_c, sig, dd, j, J8, r8, red);
+  if constexpr (STAGE == 6)
+    cta_partials_fx<MAXC>(acc_a, acc_c, fr_a, fr_c, sig, dd, j, J8, r8, red);
+  else
+    cta_partials<MAXC, VT>(acc_a, acc_c, rem_a, rem_c, sig, dd, j, J8, r8, red);
   const int nv = 2 * j + 2;
   if (!grid_reduce_last(s, red, nv)) return;
 
