@@ -491,8 +491,10 @@ def run_ours(args, w, rank, world, dist):
     s = lsgmres.Solver(A, m=w["m"], tol=w["tol"], ortho="one_reduce_mgs", max_iter=w["max_iter"], stream=stream,
                        prec=w["prec"])
     # FP64 cycles: the block dot and MAXPY products on the integer pipes (the
-    # library's default where the tile-pair ring kernel runs)
+    # library's default where the tile-pair ring kernel runs); small systems run
+    # each restart cycle in one launch (the library's default where it applies)
     fx = s.set_block_dot(True)
+    persistent = s.set_persistent(-1)
 
     barrier()
     with ClockSampler(local) as clk:
@@ -551,6 +553,17 @@ def run_ours(args, w, rank, world, dist):
                if prof_m else None}
         s.set(ortho="one_reduce_mgs", max_iter=w["max_iter"])
 
+    # small systems: the same solve with one launch per step and MAXPY, for comparison
+    per_step = None
+    if persistent and not args.no_mgs:
+        s.set_persistent(0)
+        ms_p, infos_p, _ = timed_solves(torch, s, bd, x, max(1, min(args.steps, 10)), 3, stream)
+        ip = infos_p[-1]
+        per_step = {"time_to_solve_s": max_over_ranks(ms_p) / 1e3, "iters": ip.iters,
+                    "us_per_arnoldi_step": ms_p * 1e3 / max(ip.iters, 1), "kernel_launches": ip.kernel_launches,
+                    "rel_resid_true": ip.rel_resid_true}
+        s.set_persistent(-1)
+
     # the same solve with every FP64 product on the FP64 pipe (FMAs), for comparison
     dfma = None
     if fx and not ir and not args.no_mgs:
@@ -601,7 +614,23 @@ def run_ours(args, w, rank, world, dist):
     step_tflops = st["flops"] / (st["ms"] * 1e-3) / 1e12 if st["ms"] else None
     step_gbs = st["bytes"] / (st["ms"] * 1e-3) / 1e9 if st["ms"] else None
     hbm = float(peaks.get("hbm_gbs", 6400.0))
-    if ir:  # FP32 cycles: the step kernel streams at FP32 rates, HBM is the bound
+    if persistent and not ir:  # one launch per cycle: the cycle kernel is the only one that matters
+        cy = prof["persistent_cycle"]
+        cy_gbs = cy["bytes"] / (cy["ms"] * 1e-3) / 1e9 if cy["ms"] else None
+        roofline = {
+            "kernel": "k_cycle_persistent (every Arnoldi step of a restart cycle in one cooperative launch)",
+            "bound": "hbm", "achieved": cy_gbs, "peak": hbm, "unit": "GB/s",
+            "frac": cy_gbs / hbm if cy_gbs else None,
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy bandwidth, of measured)",
+            "note": "latency-bound by design: the working set (%.1f MB) is L2-resident, so the fraction of HBM "
+                    "bandwidth is low; us_per_arnoldi_step and grid_syncs_per_step are the figures of merit"
+                    % ((8 * n * (w["m"] + 2) + 12 * nnz) / 1e6),
+            "traffic": None,
+            "launch_avg_ms": cy["ms"] / max(cy["launches"], 1), "launches": cy["launches"],
+            "alg_bytes_per_launch": cy["bytes"] / max(cy["launches"], 1),
+            "fp64_tflops": cy["flops"] / (cy["ms"] * 1e9) if cy["ms"] else None,
+        }
+    elif ir:  # FP32 cycles: the step kernel streams at FP32 rates, HBM is the bound
         roofline = {
             "kernel": "k_one_reduce_step<float> (fused FP32 CSR SpMV + block dot + epilogue)",
             "bound": "hbm", "achieved": step_gbs, "peak": hbm, "unit": "GB/s",
@@ -691,6 +720,9 @@ def run_ours(args, w, rank, world, dist):
         "alg_hbm_gbs_whole_solve": total_bytes / (total_ms_prof * 1e6) if total_ms_prof else None,
         "mgs": mgs,
         "speedup_vs_mgs": (mgs["time_to_solve_s"] / (ms / 1e3)) if mgs else None,
+        "one_launch_per_cycle": bool(persistent),
+        "per_step_launches": per_step,
+        "speedup_vs_per_step_launches": (per_step["time_to_solve_s"] / (ms / 1e3)) if per_step else None,
         "fma_products": dfma,
         "speedup_vs_fma_products": (dfma["time_to_solve_s"] / (ms / 1e3)) if dfma else None,
         "siblings": siblings,

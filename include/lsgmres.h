@@ -175,8 +175,9 @@ const char* gmres_last_error(gmres_handle h);
  * MAXPY, 2 MGS SpMV + first dot, 3 MGS axpy + next dot, 4 residual / norm,
  * 5 least squares, 6 solution update (MAXPY), 7 launches that did no work,
  * 8 second (re-orthogonalizing) block reduction of GMRES_CGS2_LVL2, 9 its
- * in-place MAXPY. */
-#define GMRES_PROFILE_CLASSES 10
+ * in-place MAXPY, 10 whole cycles in one launch (gmres_set_persistent; their
+ * bytes and flops are the cycle's steps and MAXPYs). */
+#define GMRES_PROFILE_CLASSES 11
 gmres_status gmres_set_profile(gmres_handle h, int on);
 gmres_status gmres_profile(gmres_handle h, int cls, double* total_ms, int64_t* launches,
                            double* alg_bytes, double* alg_flops);
@@ -201,6 +202,31 @@ gmres_status gmres_profile(gmres_handle h, int cls, double* total_ms, int64_t* l
  * large enough matrices whose tile-pair CSR fits the shared memory). The
  * choice changes rounding only. Never errors on a valid handle. */
 gmres_status gmres_set_block_dot(gmres_handle h, int fixed_point, int* active);
+
+/* One launch per restart cycle, for small systems whose steps are bound by
+ * launch and synchronization latency rather than by memory or arithmetic.
+ * The kernel keeps every CTA resident (a cooperative launch) and runs all
+ * Arnoldi steps of the cycle (Algorithm 7): per step the fused SpMV + block
+ * dot with its single grid reduction and the epilogue in the last CTA, a
+ * software grid barrier, the MAXPY beside the Givens rotation of the previous
+ * column, and a second barrier -- the same two grid-wide synchronizations per
+ * step as the per-step launches, without their kernel boundaries. Arithmetic
+ * as the per-step launches of the unstaged kernel (FP64 fused multiply-adds).
+ * mode = 1: use it whenever it applies (FP64, GMRES_ONE_REDUCE_MGS or
+ * GMRES_ONE_REDUCE_PIPE2, and the grid fits on the device at once); 0: never;
+ * -1 (the default): when it applies and the system has at most one 256-row
+ * tile per CTA of the reduction grid (n <= 2 x SMs x 256). *active (may be
+ * NULL) receives whether the handle's next solve uses it. Every wait of its
+ * grid barrier is bounded (about one second of SM clocks); a wait that gives up
+ * ends the cycle and the solve returns GMRES_ERR_TIMEOUT. Never errors on a
+ * valid handle. */
+gmres_status gmres_set_persistent(gmres_handle h, int mode, int* active);
+
+/* Testing the bounded waits of the persistent cycle's grid barrier: with
+ * on = 1 the barrier waits for one CTA more than the grid has, so its first
+ * wait runs out (no fault, no hang: about one second), the kernel returns and
+ * the solve reports GMRES_ERR_TIMEOUT; on = 0 restores normal operation. */
+gmres_status gmres_test_stall_barrier(gmres_handle h, int on);
 
 /* Testing the bounded waits of the CSR staging. The step kernel brings each
  * tile's CSR into shared memory with bulk copies whose completion it waits for

@@ -424,8 +424,8 @@ __device__ bool publish_and_reduce(double* partials, int nvmax, int64_t slot, in
 // consecutive CTAs sums its group's slots into row P + group, and the last
 // group sums the group rows. Both levels sum in a fixed order (deterministic
 // for a given grid). Needs P + ceil(P / 16) rows of partials.
-__device__ bool grid_reduce_last(Small s, double* red, int nv) {
-  const int P = gridDim.x;
+__device__ bool grid_reduce_last(Small s, double* red, int nv, int nctas = 0) {
+  const int P = nctas > 0 ? nctas : (int)gridDim.x;  // CTAs taking part (the first nctas of the grid)
   int S = 1;
   while (2 * S * nv <= (int)blockDim.x && S < (int)blockDim.x) S *= 2;
   const int NG = (P + kGridGroup - 1) / kGridGroup;
@@ -437,7 +437,7 @@ __device__ bool grid_reduce_last(Small s, double* red, int nv) {
     if (!publish_and_reduce(s.partials, s.nvmax, blockIdx.x, g0, gn, &s.st->gticket[g], red, nv)) return false;
     if (!publish_and_reduce(s.partials, s.nvmax, P + g, P, NG, &s.st->ticket, red, nv)) return false;
   }
-  if (threadIdx.x == 0) s.st->reductions += 1;
+  if (threadIdx.x == 0) atomicAdd(reinterpret_cast<unsigned long long*>(&s.st->reductions), 1ull);
   return true;
 }
 
@@ -451,10 +451,12 @@ __device__ int finish_column(Small s, int j, double h, bool last_allowed) {
   __shared__ double sh_col[kMaxM + 2], sh_c[kMaxM + 1], sh_s[kMaxM + 1];
   __shared__ int s_res;
   const int ld = s.ldh;
-  for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) sh_col[i] = s.H[(size_t)j * ld + i];
+  // state written by other CTAs of the same launch (the one-launch cycle) is
+  // read through L2 (__ldcg): their writes are not visible in this SM's L1
+  for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) sh_col[i] = __ldcg(&s.H[(size_t)j * ld + i]);
   for (int i = threadIdx.x; i < j; i += blockDim.x) {
-    sh_c[i] = s.cs[i];
-    sh_s[i] = s.sn[i];
+    sh_c[i] = __ldcg(&s.cs[i]);
+    sh_s[i] = __ldcg(&s.sn[i]);
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -480,11 +482,11 @@ __device__ int finish_column(Small s, int j, double h, bool last_allowed) {
     for (int i = 0; i <= j + 1; ++i) Rg[i] = R[i];
     s.cs[j] = c;
     s.sn[j] = sn;
-    const double gj = s.g[j];
+    const double gj = __ldcg(&s.g[j]);
     s.g[j + 1] = -sn * gj;
     s.g[j] = c * gj;
-    const double est = fabs(sn * gj) * st->cycle_scale * st->inv_bnorm;
-    const int it = st->total_iters + j;
+    const double est = fabs(sn * gj) * __ldcg(&st->cycle_scale) * __ldcg(&st->inv_bnorm);
+    const int it = __ldcg(&st->total_iters) + j;
     if (it < s.hist_cap) s.hist[it] = est;
     st->k = j + 1;
     st->est = est;
@@ -495,7 +497,88 @@ __device__ int finish_column(Small s, int j, double h, bool last_allowed) {
     } else if (h <= kBreakdownFactor * kEps * sqrt(hn2)) {
       st->breakdown = 1;
       stop = 1;
-    } else if (est <= st->tol) {
+    } else if (est <= __ldcg(&st->tol)) {
+      st->converged = 1;
+      stop = 1;
+    } else if (last_allowed) {
+      stop = 1;
+    }
+    s_res = stop;
+  }
+  __syncthreads();
+  return s_res;
+}
+
+// finish_column in two parts, for a caller that knows column c's first c+1
+// entries one step before its last one (the one-launch cycle): prerotate_column
+// applies the stored rotations 0 .. c-1 to H(0:c, c) and keeps the result in
+// Rg(:, c) (rows 0 .. c, row c not yet final) and the column's squared norm
+// in *hn2_out; finish_prerotated then forms rotation c from Rg(c, c) and
+// h = H(c+1, c), as finish_column does, with the same operations in the same
+// order (bitwise the same results). Thread 0 works; the whole CTA calls both.
+__device__ void prerotate_column(Small s, int c, double* hn2_out) {
+  __shared__ double sh_col[kMaxM + 2], sh_c[kMaxM + 1], sh_s[kMaxM + 1];
+  const int ld = s.ldh;
+  for (int i = threadIdx.x; i <= c; i += blockDim.x) sh_col[i] = __ldcg(&s.H[(size_t)c * ld + i]);
+  for (int i = threadIdx.x; i < c; i += blockDim.x) {
+    sh_c[i] = __ldcg(&s.cs[i]);
+    sh_s[i] = __ldcg(&s.sn[i]);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double hn2 = 0.0;
+    for (int i = 0; i <= c; ++i) hn2 += sh_col[i] * sh_col[i];
+    *hn2_out = hn2;
+    double* R = sh_col;
+    for (int i = 0; i < c; ++i) {
+      const double cc = sh_c[i], sn = sh_s[i];
+      const double t = cc * R[i] + sn * R[i + 1];
+      R[i + 1] = -sn * R[i] + cc * R[i + 1];
+      R[i] = t;
+    }
+    double* Rg = s.Rg + (size_t)c * ld;
+    for (int i = 0; i <= c; ++i) Rg[i] = R[i];
+  }
+  __syncthreads();
+}
+
+// Rg(c, c) rotated by rotations 0 .. c-1 is in Rg; hn2 = ||H(0:c, c)||^2 (from
+// prerotate_column, the same thread 0); h = H(c+1, c). Returns the stop
+// decision in every thread, as finish_column.
+__device__ int finish_prerotated(Small s, int c, double h, double hn2_partial, bool last_allowed) {
+  __shared__ int s_res;
+  if (threadIdx.x == 0) {
+    DevState* st = s.st;
+    const int ld = s.ldh;
+    double* Rg = s.Rg + (size_t)c * ld;
+    const double hn2 = hn2_partial + h * h;
+    double R0 = __ldcg(&Rg[c]), R1 = h;
+    double cc = 1.0, sn = 0.0;
+    if (R1 != 0.0) {
+      const double irho = 1.0 / hypot(R0, R1);
+      cc = R0 * irho;
+      sn = R1 * irho;
+    }
+    Rg[c] = cc * R0 + sn * R1;
+    Rg[c + 1] = 0.0;
+    s.cs[c] = cc;
+    s.sn[c] = sn;
+    const double gj = __ldcg(&s.g[c]);
+    s.g[c + 1] = -sn * gj;
+    s.g[c] = cc * gj;
+    const double est = fabs(sn * gj) * __ldcg(&st->cycle_scale) * __ldcg(&st->inv_bnorm);
+    const int it = __ldcg(&st->total_iters) + c;
+    if (it < s.hist_cap) s.hist[it] = est;
+    st->k = c + 1;
+    st->est = est;
+    int stop = 0;
+    if (!isfinite(est)) {
+      st->nonfinite = 1;
+      stop = 1;
+    } else if (h <= kBreakdownFactor * kEps * sqrt(hn2)) {
+      st->breakdown = 1;
+      stop = 1;
+    } else if (est <= __ldcg(&st->tol)) {
       st->converged = 1;
       stop = 1;
     } else if (last_allowed) {
@@ -521,14 +604,14 @@ __device__ int finish_completed(Small s, int c, double h, bool tail) {
   __shared__ int s_rot, s_first;
   double v = 0.0;
   for (int i = threadIdx.x; i <= c + 1; i += blockDim.x) {
-    const double x = (i == c + 1) ? h : s.H[(size_t)c * s.ldh + i];
+    const double x = (i == c + 1) ? h : __ldcg(&s.H[(size_t)c * s.ldh + i]);
     v = fma(x, x, v);
   }
   const double hn2 = block_sum(v, sbuf);
   if (threadIdx.x == 0) {
     const bool brk = h <= kBreakdownFactor * kEps * sqrt(hn2);
     s_rot = (c == 0 || (c & 1) == 0 || tail || brk);
-    s_first = st->k;  // columns rotated so far in this cycle
+    s_first = __ldcg(&st->k);  // columns rotated so far in this cycle
   }
   __syncthreads();
   if (!s_rot) return 0;
@@ -1307,11 +1390,11 @@ __device__ void epilogue_one_reduce(Small s, double* red, int j, bool tail, size
   __shared__ int s_stop;
   for (int e = threadIdx.x; e < j * j; e += blockDim.x) {
     const int k = e / j, i = e % j;  // column k, row i
-    if (i >= k) sT[(size_t)k * ld + i] = s.T[(size_t)k * ld + i];
+    if (i >= k) sT[(size_t)k * ld + i] = __ldcg(&s.T[(size_t)k * ld + i]);
   }
-  for (int i = threadIdx.x; i < j; i += blockDim.x) sScale[i] = s.scale[i];
+  for (int i = threadIdx.x; i < j; i += blockDim.x) sScale[i] = __ldcg(&s.scale[i]);
   if (threadIdx.x == 0) {
-    st->grid_syncs += 1;
+    atomicAdd(reinterpret_cast<unsigned long long*>(&st->grid_syncs), 1ull);
     const double beta = sqrt(red[2 * j]);
     int stop = 0;
     if (!isfinite(beta)) {
@@ -1479,7 +1562,7 @@ __device__ void lsq_system(Small s) {
 
 // Kernel classes of the per-launch profiles (gmres_profile, gmres_batch_profile).
 enum { PC_STEP = 0, PC_MAXPY = 1, PC_MGS_SPMV = 2, PC_MGS_AXPY = 3, PC_RES = 4, PC_LSQ = 5, PC_XUPD = 6,
-       PC_NOOP = 7, PC_REORTH = 8, PC_REORTH_MAXPY = 9 };
+       PC_NOOP = 7, PC_REORTH = 8, PC_REORTH_MAXPY = 9, PC_CYCLE = 10 };
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 

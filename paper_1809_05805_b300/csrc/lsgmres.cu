@@ -576,6 +576,202 @@ k_mgs_axpy_dot(double* __restrict__ V, int64_t ldv, int64_t n, Small s) {
   }
 }
 
+// --------------------------------------------------------------------------
+// One whole restart cycle in one launch (small systems: latency-bound)
+// --------------------------------------------------------------------------
+// A software grid barrier for a cooperative launch (every CTA resident):
+// bar[0] counts arrivals, bar[1] is the generation. Thread 0 of each CTA reads
+// the generation, arrives, and the last arrival resets the count and advances
+// the generation; the others wait for it to advance. Every wait is bounded
+// (about one second of SM clocks, as the staging waits): a CTA that gives up,
+// or sees that another gave up, marks the state stalled and returns false, so
+// every CTA leaves the kernel within a few seconds and the solve reports
+// GMRES_ERR_TIMEOUT. `extra` (testing) raises the arrival count the barrier
+// waits for, so that it never completes.
+__device__ bool grid_barrier(unsigned int* bar, unsigned int nblocks, unsigned int extra, DevState* st) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned int* vgen = bar + 1;
+    const unsigned int g = *vgen;
+    __threadfence();
+    int ok = 1;
+    if (atomicAdd(bar, 1u) == nblocks + extra - 1) {
+      bar[0] = 0u;
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      const long long t0 = clock64();
+      while (*vgen == g) {
+        if (*reinterpret_cast<volatile int*>(&st->stalled)) {
+          ok = 0;
+          break;
+        }
+        if (clock64() - t0 > (1ll << 31)) {
+          atomicExch(&st->stalled, 1);
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+      __threadfence();
+    }
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// Basis reads of the one-launch cycle go through L2 (__ldcg): the columns are
+// written during the launch by other CTAs, so neither the read-only path nor
+// a possibly stale L1 line may serve them.
+struct CoherentCols {
+  const double* V;
+  int64_t ldv;
+  int64_t r0;
+  template <typename VT>
+  __device__ VT ld(int k, int i) const {
+    return __ldcg(V + (size_t)k * ldv + r0 + i);
+  }
+};
+
+// Row i of A times x (FMA chain in column order, as csr_row), x through L2.
+__device__ __forceinline__ double csr_row_cg(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                                             const double* __restrict__ val, const double* x, int64_t i) {
+  double acc = 0.0;
+  for (int p = __ldg(rowptr + i), e = __ldg(rowptr + i + 1); p < e; ++p)
+    acc = fma(__ldg(val + p), __ldcg(x + __ldg(col + p)), acc);
+  return acc;
+}
+
+// Every Arnoldi step of a cycle (Algorithm 7 on Algorithm 4), with the same
+// arithmetic and device functions as the per-step launches (the fused SpMV +
+// block dot on single tiles, the last-CTA grid reduction and epilogue, the
+// Arnoldi MAXPY, the Givens rotations). The grid is Pw work CTAs and one
+// Givens CTA (the last). Per step j:
+//   phase A: the work CTAs run the fused SpMV + block dot over their tiles
+//            and publish their partial sums; the last to arrive sums them and
+//            runs the epilogue (lagged norm, T row, r = T s, MAXPY
+//            coefficients). Meanwhile the Givens CTA applies the stored
+//            rotations to column j-1, whose first j entries the previous
+//            step's epilogue wrote (the lagged H(j, j-1) is still to come);
+//   barrier 1;
+//   phase B: the work CTAs run the MAXPY over their rows; the Givens CTA forms
+//            rotation j-1 from the new H(j, j-1) and takes the convergence
+//            decision (in the L = 2 pipeline: the rotations of Algorithm 8's
+//            column pairs, as the per-step launches do);
+//   barrier 2 (the next SpMV reads the new column everywhere).
+// Two grid-wide synchronizations per step, as with two launches per step, but
+// without a kernel boundary, and with the Givens chain off the critical path.
+// Needs a cooperative launch (every CTA resident) and (m+1)^2 + (m+1) doubles
+// of dynamic shared memory for the epilogue.
+template <int MAXC>
+__global__ void __launch_bounds__(kThreads, 2)
+k_cycle_persistent(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                   const double* __restrict__ val, double* V, int64_t ldv, double* w, int64_t n, Small s,
+                   unsigned int* bar, unsigned int bar_extra) {
+  __shared__ double su[kThreads];
+  __shared__ double sw[kThreads];
+  __shared__ double red[2 * (kMaxM + 1) + 2];
+  __shared__ double scf[kMaxM + 3];
+  __shared__ double s_hn2;
+  __shared__ int s_j, s_tail, s_done, s_K, s_out, s_pipe2;
+  DevState* st = s.st;
+  const unsigned int P = gridDim.x;
+  const int Pw = (int)P - 1;  // work CTAs; CTA Pw rotates
+  const bool givens = (int)blockIdx.x == Pw;
+  const int64_t ntiles = (n + kThreads - 1) / kThreads;
+  if (threadIdx.x == 0) s_pipe2 = __ldcg(&st->pipe2);
+  for (;;) {
+    if (threadIdx.x == 0) {
+      s_done = __ldcg(&st->done) | __ldcg(&st->stalled);
+      s_j = __ldcg(&st->step);
+      s_tail = (s_j == __ldcg(&st->kmax));
+    }
+    __syncthreads();
+    if (s_done) return;
+    const int j = s_j;
+    const bool tail = s_tail;
+    const double* u = V + (size_t)j * ldv;
+    // ---- phase A ----
+    if (givens) {
+      if (j >= 1 && !tail && !s_pipe2) prerotate_column(s, j - 1, &s_hn2);
+    } else {
+      const int J8 = j / kWarps, r8 = j % kWarps;
+      double acc_a[MAXC], acc_c[MAXC], rem_a[kWarps - 1], rem_c[kWarps - 1];
+#pragma unroll
+      for (int c = 0; c < MAXC; ++c) acc_a[c] = acc_c[c] = 0.0;
+#pragma unroll
+      for (int c = 0; c < kWarps - 1; ++c) rem_a[c] = rem_c[c] = 0.0;
+      double sig = 0.0, dd = 0.0;
+      for (int64_t t = blockIdx.x; t < ntiles; t += Pw) {
+        const int64_t row = t * kThreads + threadIdx.x;
+        double ur = 0.0, wr = 0.0;
+        if (row < n) {
+          ur = __ldcg(u + row);
+          if (!tail) {
+            wr = csr_row_cg(rowptr, col, val, u, row);
+            w[row] = wr;
+          }
+        }
+        tile_dot_rows_cols<MAXC, double, double>(t, n, CoherentCols{V, ldv, t * kThreads}, !tail, J8, r8, ur, wr,
+                                                 su, sw, acc_a, acc_c, rem_a, rem_c, sig, dd, NoHook{}, NoHook{},
+                                                 NoHook{});
+      }
+      cta_partials<MAXC, double>(acc_a, acc_c, rem_a, rem_c, sig, dd, j, J8, r8, red);
+      if (grid_reduce_last(s, red, 2 * j + 2, Pw)) epilogue_one_reduce(s, red, j, tail);
+    }
+    if (!grid_barrier(bar, P, bar_extra, st)) return;
+    if (threadIdx.x == 0) {
+      s_done = __ldcg(&st->done);
+      s_K = __ldcg(&st->maxpy_k);
+      s_out = __ldcg(&st->step);
+    }
+    __syncthreads();
+    if (s_done) return;
+    // ---- phase B ----
+    if (givens) {
+      if (j >= 1) {
+        const double h = __ldcg(&s.H[(size_t)(j - 1) * s.ldh + j]);
+        const int stop = s_pipe2 ? finish_completed(s, j - 1, h, false)
+                                 : finish_prerotated(s, j - 1, h, s_hn2, false);
+        if (threadIdx.x == 0) {
+          atomicAdd(reinterpret_cast<unsigned long long*>(&st->grid_syncs), 1ull);
+          if (stop) st->done = 1;
+        }
+      }
+    } else {
+      const int K = s_K;
+      for (int i = threadIdx.x; i <= K; i += blockDim.x) scf[i] = __ldcg(s.coef + i);
+      __syncthreads();
+      double* out = V + (size_t)s_out * ldv;
+      for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)Pw * blockDim.x) {
+        double a0 = scf[0] * __ldcg(w + i);
+        for (int k = 0; k < K; ++k) a0 = fma(scf[1 + k], __ldcg(V + (size_t)k * ldv + i), a0);
+        out[i] = a0;
+      }
+    }
+    if (!grid_barrier(bar, P, bar_extra, st)) return;
+  }
+}
+
+using CycleKernel = void (*)(const int32_t*, const int32_t*, const double*, double*, int64_t, double*, int64_t,
+                             Small, unsigned int*, unsigned int);
+CycleKernel cycle_kernel_for(int m) {
+  switch (std::max(1, m / kWarps)) {
+    case 1: return k_cycle_persistent<1>;
+    case 2: return k_cycle_persistent<2>;
+    case 3: return k_cycle_persistent<3>;
+    case 4: return k_cycle_persistent<4>;
+    case 5: return k_cycle_persistent<5>;
+    case 6: return k_cycle_persistent<6>;
+    case 7: return k_cycle_persistent<7>;
+    case 8: return k_cycle_persistent<8>;
+    case 9: case 10: case 11: case 12: return k_cycle_persistent<12>;
+    default: return k_cycle_persistent<16>;
+  }
+}
+
 // Exponent bounds of the first j columns of a caller's basis (the standalone
 // block dot): ecol[k] = largest (hi word & 0x7FF00000) in column k; ecol
 // cleared before. Grid: (x, j).
@@ -780,6 +976,14 @@ struct gmres_ctx {
   // FP64 block dot of staging mode 2 on the integer pipes (mode 6; on by
   // default, gmres_set_block_dot)
   int dot_fx = 1;
+  // whole cycles in one cooperative launch (gmres_set_persistent): -1 auto,
+  // 0 off, 1 on; the kernel, whether it fits the device at once, its grid
+  // barrier words (in the small block) and the barrier test switch
+  int persist = -1;
+  CycleKernel cyc = nullptr;
+  bool cyc_ok = false;
+  unsigned int* bar = nullptr;
+  unsigned int bar_extra = 0;
   size_t smem64 = 0, smem32 = 0, smem16 = 0;
   size_t lsq_smem = 0;   // dynamic shared memory of k_lsq (rotated Hessenberg)
   std::vector<double> hist;
@@ -888,6 +1092,7 @@ gmres_status alloc_small(gmres_ctx* h) {
   const size_t o_pa = take(sizeof(double) * (size_t)(Pmax + (Pmax + kGridGroup - 1) / kGridGroup) * nvmax);
   const size_t o_raw = take(sizeof(double) * nvmax);
   const size_t o_ec = take(sizeof(unsigned int) * (m + 2));
+  const size_t o_bar = take(sizeof(unsigned int) * 2);
   if (h->small) cudaFree(h->small);
   h->small = nullptr;
   CUDA_TRY(h, cudaMalloc(&h->small, off));
@@ -907,6 +1112,7 @@ gmres_status alloc_small(gmres_ctx* h) {
   h->s.partials = reinterpret_cast<double*>(b + o_pa);
   h->s.raw = reinterpret_cast<double*>(b + o_raw);
   h->s.ecol = reinterpret_cast<unsigned int*>(b + o_ec);
+  h->bar = reinterpret_cast<unsigned int*>(b + o_bar);
   h->hist.assign(h->s.hist_cap, 0.0);
   return GMRES_OK;
 }
@@ -1042,7 +1248,36 @@ gmres_status launch_cycle(gmres_ctx* h, int kmax);
 // mode) and replayed; kernels read their step index from device state, so the
 // same graph serves every cycle. On the legacy default stream (which cannot be
 // captured) the kernels are launched one by one.
+// Whether the next cycle runs as one cooperative launch (gmres_set_persistent).
+// CTAs of the one-launch cycle: up to two per SM of work CTAs (the reduction
+// grid, one fewer) and the Givens CTA.
+int persistent_grid(const gmres_ctx* h) {
+  const int64_t ntiles = (h->n + kThreads - 1) / kThreads;
+  return (int)std::min<int64_t>(2 * (int64_t)h->nsm - 1, ntiles) + 1;
+}
+
+bool use_persistent(const gmres_ctx* h) {
+  if (!h->cyc_ok || h->prec != GMRES_FP64 || h->persist == 0) return false;
+  if (h->ortho != GMRES_ONE_REDUCE_MGS && h->ortho != GMRES_ONE_REDUCE_PIPE2) return false;
+  const int64_t ntiles = (h->n + kThreads - 1) / kThreads;
+  return h->persist == 1 || ntiles < 2 * (int64_t)h->nsm;
+}
+
+// One cycle of kmax steps in one cooperative launch (k_cycle_persistent).
+gmres_status launch_persistent(gmres_ctx* h, int kmax) {
+  CUDA_TRY(h, cudaMemsetAsync(h->bar, 0, 2 * sizeof(unsigned int), h->stream));
+  const int pr = prof_begin(h, PC_CYCLE, 0, kmax);
+  void* args[] = {&h->rowptr, &h->col, &h->val, &h->V, &h->ldv, &h->w, &h->n, &h->s, &h->bar, &h->bar_extra};
+  CUDA_TRY(h, cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(h->cyc), dim3(persistent_grid(h)),
+                                          dim3(kThreads), args, h->step_smem, h->stream));
+  prof_end(h, pr);
+  ++h->launches;
+  LAUNCH_CHECK(h);
+  return GMRES_OK;
+}
+
 gmres_status run_cycle(gmres_ctx* h, int kmax) {
+  if (use_persistent(h)) return launch_persistent(h, kmax);
   if (h->stream == nullptr || (h->prof_on && !h->graph_prof_ok)) return launch_cycle(h, kmax);
   gmres_ctx::CycleGraph* g = nullptr;
   for (auto& c : h->graphs)
@@ -1120,6 +1355,21 @@ void alg_model(const gmres_ctx* h, const gmres_ctx::ProfRec& r, int kx, double* 
         *flops = 2.0 * nnz + 2.0 * n * (2.0 * r.j + 2.0);
       }
       break;
+    case PC_CYCLE: {  // every step and MAXPY of a cycle that completed k columns (tail at kmax)
+      double by = 0.0, fl = 0.0;
+      for (int jj = 0; jj <= std::min(kx, r.i); ++jj) {
+        const bool tl = (jj == r.i);
+        by += tl ? vb * n * (jj + 1) : csr + vb * n * (jj + 1) + wb * n;
+        fl += tl ? 2.0 * n * (jj + 1) : 2.0 * nnz + 2.0 * n * (2.0 * jj + 2.0);
+        if (jj < kx && jj < r.i) {
+          by += wb * n + vb * n * (jj + 2);
+          fl += 2.0 * n * (jj + 1) + n;
+        }
+      }
+      *bytes = by;
+      *flops = fl;
+      break;
+    }
     case PC_MAXPY:  // w and j+1 columns read, one column written
       *bytes = wb * n + vb * n * (r.j + 2);
       *flops = 2.0 * n * (r.j + 1) + n;
@@ -1386,6 +1636,15 @@ gmres_status gmres_create(const gmres_csr* A, int m_restart, double tol, gmres_h
     h->step32 = step32_for(m, h->stage32);
     h->step16 = step16_for(m, h->stage16);
   }
+  {  // whole cycles in one launch: needs cooperative launches and the grid resident at once
+    h->cyc = cycle_kernel_for(h->m);
+    int coop = 0, nb = 0;
+    if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, h->device) == cudaSuccess && coop &&
+        raise_smem_limit(reinterpret_cast<const void*>(h->cyc), h->step_smem) == cudaSuccess &&
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, h->cyc, kThreads, h->step_smem) == cudaSuccess)
+      h->cyc_ok = (int64_t)nb * h->nsm >= (int64_t)persistent_grid(h);
+    cudaGetLastError();
+  }
   CREATE_TRY(raise_smem_limit(reinterpret_cast<const void*>(k_lsq), h->lsq_smem));
 #undef CREATE_TRY
   *out = h;
@@ -1494,6 +1753,12 @@ gmres_status gmres_solve(gmres_handle h, const double* b, double* x, gmres_info*
       if ((st = read_state(h)) != GMRES_OK) return st;
       const DevState& hs = *h->h_st;
       prof_settle(h, hs.total_iters - prev_total);
+      if (hs.stalled) {  // (a cycle that gave up waiting may have completed no column)
+        result = GMRES_ERR_TIMEOUT;
+        fail(h, result, "a bounded device-side wait (staged CSR data or the one-launch cycle's grid barrier) "
+                        "gave up");
+        break;
+      }
       if (cycles > 0 && hs.total_iters == prev_total) {  // every cycle completes >= 1 column
         result = GMRES_ERR_CUDA;
         fail(h, result, "internal: a cycle completed no column");
@@ -1501,11 +1766,6 @@ gmres_status gmres_solve(gmres_handle h, const double* b, double* x, gmres_info*
       }
       prev_total = hs.total_iters;
       ++cycles;
-      if (hs.stalled) {
-        result = GMRES_ERR_TIMEOUT;
-        fail(h, result, "a bounded device-side wait for staged CSR data gave up");
-        break;
-      }
       if (!std::isfinite(hs.rnorm) || hs.nonfinite) {
         result = GMRES_ERR_NONFINITE;
         fail(h, result, "non-finite residual (NaN or Inf in x0 or the iteration)");
@@ -1620,6 +1880,19 @@ gmres_status gmres_destroy(gmres_handle h) {
 }
 
 const char* gmres_last_error(gmres_handle h) { return h ? h->err.c_str() : g_create_err.c_str(); }
+
+gmres_status gmres_set_persistent(gmres_handle h, int mode, int* active) {
+  if (!h) return GMRES_ERR_ARG;
+  h->persist = mode < 0 ? -1 : (mode ? 1 : 0);
+  if (active) *active = use_persistent(h);
+  return GMRES_OK;
+}
+
+gmres_status gmres_test_stall_barrier(gmres_handle h, int on) {
+  if (!h) return GMRES_ERR_ARG;
+  h->bar_extra = on ? 1u : 0u;
+  return GMRES_OK;
+}
 
 gmres_status gmres_set_block_dot(gmres_handle h, int fixed_point, int* active) {
   if (!h) return GMRES_ERR_ARG;

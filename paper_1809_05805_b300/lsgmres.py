@@ -88,7 +88,8 @@ class SolveInfo:
 
 EXPORTS = ["gmres_create", "gmres_set", "gmres_set_tol", "gmres_set_stream", "gmres_solve",
            "gmres_solve_host", "gmres_history", "gmres_destroy", "gmres_last_error", "lsg_spmv",
-           "lsg_block_dot", "lsg_maxpy", "gmres_arnoldi", "gmres_set_profile", "gmres_profile", "gmres_test_stall_staging", "gmres_set_block_dot",
+           "lsg_block_dot", "lsg_maxpy", "gmres_arnoldi", "gmres_set_profile", "gmres_profile", "gmres_test_stall_staging", "gmres_set_block_dot", "gmres_set_persistent",
+           "gmres_test_stall_barrier",
            "lsg_block_dot_noalloc", "gmres_batch_create", "gmres_batch_set_grid", "gmres_batch_get_grid",
            "gmres_batch_set_rows_per_thread", "gmres_batch_get_rows_per_thread", "gmres_batch_set_stream", "gmres_batch_solve",
            "gmres_batch_solve_host", "gmres_batch_set_profile", "gmres_batch_profile", "gmres_batch_launch_log",
@@ -99,7 +100,7 @@ EXPORTS = ["gmres_create", "gmres_set", "gmres_set_tol", "gmres_set_stream", "gm
            "lsg_probe_last_error"]
 
 PROFILE_CLASSES = ["one_reduce_step", "arnoldi_maxpy", "mgs_spmv_dot", "mgs_axpy_dot", "residual",
-                   "least_squares", "x_update", "noop", "reorth_dot", "reorth_maxpy"]
+                   "least_squares", "x_update", "noop", "reorth_dot", "reorth_maxpy", "persistent_cycle"]
 
 _lib = None
 
@@ -130,6 +131,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "gmres_set_profile": ([P, I], I),
         "gmres_test_stall_staging": ([P, I, ctypes.POINTER(I)], I),
         "gmres_set_block_dot": ([P, I, ctypes.POINTER(I)], I),
+        "gmres_set_persistent": ([P, I, ctypes.POINTER(I)], I),
+        "gmres_test_stall_barrier": ([P, I], I),
         "lsg_block_dot_noalloc": ([P, P, P, I64, P, I64, I, P, P, I, P, P], I),
         "gmres_profile": ([P, I, ctypes.POINTER(D), ctypes.POINTER(I64), ctypes.POINTER(D),
                            ctypes.POINTER(D)], I),
@@ -291,6 +294,19 @@ class Solver:
         active = ctypes.c_int(0)
         self._check(self.lib.gmres_set_block_dot(self.h, int(fixed_point), ctypes.byref(active)))
         return bool(active.value)
+
+    def set_persistent(self, mode: int) -> bool:
+        """gmres_set_persistent: one launch per restart cycle (1), per-step
+        launches (0) or automatic (-1, the default); returns whether the next
+        solve runs whole cycles in one launch."""
+        active = ctypes.c_int(0)
+        self._check(self.lib.gmres_set_persistent(self.h, int(mode), ctypes.byref(active)))
+        return bool(active.value)
+
+    def test_stall_barrier(self, on: bool):
+        """Make the persistent cycle's grid barrier wait for a CTA that never
+        arrives (testing): the solve returns GMRES_ERR_TIMEOUT after ~1 s."""
+        self._check(self.lib.gmres_test_stall_barrier(self.h, int(on)))
 
     def test_stall_staging(self, on: bool) -> bool:
         """Make the bounded waits of the CSR staging run out (testing); returns

@@ -277,6 +277,7 @@ def test_stream_graph_path(torch_cuda, lsg, orc, ortho):
     outs = []
     for use_stream in (False, True):
         s = lsg.Solver(A, m=30, tol=1e-12, ortho=ortho, max_iter=70)
+        s.set_persistent(0)  # per-step launches (graphs on the stream)
         stream = torch.cuda.Stream() if use_stream else None
         if stream is not None:
             s.set_stream(stream)
@@ -298,6 +299,7 @@ def test_stream_graph_replay_twice(torch_cuda, lsg):
     A = P.conv_diff_7pt(16)
     _, b = P.rhs(A, seed=12)
     s = lsg.Solver(A, m=20, tol=1e-10)
+    s.set_persistent(0)  # per-step launches, so that the cycles run as replayed graphs
     stream = torch.cuda.Stream()
     s.set_stream(stream)
     bd = dev(torch, b)

@@ -67,6 +67,7 @@ def test_staged_ragged_rows_match_oracle(torch_cuda, lsg, orc, n):
     A = _ragged(n, seed=n)
     b = np.random.default_rng(1).standard_normal(n)
     s = lsg.Solver(A, m=20, tol=1e-10, max_iter=400)
+    s.set_persistent(0)  # per-step launches: the staged step kernel (small systems default to one launch per cycle)
     assert s.test_stall_staging(False)  # the FP64 step kernel stages this matrix
     x = torch.zeros(n, dtype=torch.float64, device="cuda")
     info = s.solve(torch.from_numpy(b).cuda(), x)
@@ -86,6 +87,7 @@ def test_staging_wait_runs_out_and_reports_timeout(torch_cuda, lsg, graph):
     _, b = P.rhs(A, seed=2)
     bd = torch.from_numpy(b).cuda()
     s = lsg.Solver(A, m=6, tol=1e-8, max_iter=300, stream=torch.cuda.Stream() if graph else None)
+    s.set_persistent(0)  # per-step launches: the staged step kernel
     assert s.test_stall_staging(True)
     x = torch.zeros(n, dtype=torch.float64, device="cuda")
     t0 = time.time()
