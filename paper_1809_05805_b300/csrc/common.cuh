@@ -54,6 +54,7 @@ struct DevState {
   int pipe2;           // Givens rotations on column pairs (the L = 2 pipeline)
   int stalled;         // a bounded device-side wait for staged CSR data gave up
   int stall_test;      // testing: staged copies announce 16 bytes more than they bring
+  unsigned int unit_ctr;  // step kernel (mode 6): units handed out beyond the first per CTA; 0 between launches
   long long reductions;
   long long grid_syncs;
   double mgs_coef;     // MGS: coefficient of the pending axpy

@@ -82,6 +82,7 @@ k_one_reduce_step(const int32_t* __restrict__ rowptr, const int32_t* __restrict_
   __shared__ uint64_t s_bar, s_barV;
   __shared__ uint32_t s_extra;
   __shared__ uint32_t s_ex[2 * kWarps];  // STAGE 6: per-warp exponent maxima of u and w
+  __shared__ int64_t s_nx[2];            // STAGE 6: the CTA's next unit (by iteration parity)
   DevState* st = s.st;
   if (threadIdx.x == 0) {
     if (raw_out) {
@@ -201,8 +202,19 @@ k_one_reduce_step(const int32_t* __restrict__ rowptr, const int32_t* __restrict_
           vpending = true;
         }
       }
-      for (; unit < units; unit += gridDim.x) {
-        const int64_t nx = unit + gridDim.x;
+      int par = 0;
+      for (; unit < units; par ^= 1) {
+        // The next unit: fixed stride, or (STAGE 6) the next one not yet taken,
+        // from a counter (CTAs that run faster take more units, so the launch
+        // does not wait for the slowest one's last units); the counter is
+        // reset by the CTA that completes the grid reduction.
+        int64_t nx = unit + gridDim.x;
+        if constexpr (STAGE == 6) {
+          if (threadIdx.x == 0) {
+            nx = (int64_t)gridDim.x + (int64_t)atomicAdd(&st->unit_ctr, 1u);
+            s_nx[par] = nx;
+          }
+        }
         int nlo = 0, nhi = 0;  // thread 0: the next unit's entry range, loaded ahead of its use
         if (threadIdx.x == 0 && nx < units) {
           nlo = CsrStage<VT>::lo_of(__ldg(rowptr + nx * U));
@@ -305,6 +317,10 @@ k_one_reduce_step(const int32_t* __restrict__ rowptr, const int32_t* __restrict_
           tile_dot_rows<MAXC, SV, VT>(unit, n, V, ldv, need_w, J8, r8, ur0, wr0, su, sw, acc_a, acc_c, rem_a,
                                       rem_c, sig, dd, next);
         }
+        if constexpr (STAGE == 6)
+          unit = s_nx[par];  // written by thread 0 before this unit's barriers
+        else
+          unit += gridDim.x;
       }
       // no copy may still be landing in shared memory when the CTA moves on
       if (threadIdx.x == 0 && pending) mbar_wait_bounded(&s_bar, pend_phase);
@@ -359,6 +375,7 @@ k_one_reduce_step(const int32_t* __restrict__ rowptr, const int32_t* __restrict_
     cta_partials<MAXC, VT>(acc_a, acc_c, rem_a, rem_c, sig, dd, j, J8, r8, red);
   const int nv = 2 * j + 2;
   if (!grid_reduce_last(s, red, nv)) return;
+  if (STAGE == 6 && threadIdx.x == 0) st->unit_ctr = 0u;  // every CTA has taken its last unit
 
   if (raw_out) {
     for (int v = threadIdx.x; v < nv; v += blockDim.x) raw_out[v] = red[v];
