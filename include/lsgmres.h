@@ -291,6 +291,19 @@ gmres_status gmres_batch_get_grid(gmres_batch bt, int* ctas);
 gmres_status gmres_batch_set_rows_per_thread(gmres_batch bt, int rows);
 gmres_status gmres_batch_get_rows_per_thread(gmres_batch bt, int* rows);
 
+/* FP64 products of the batched block dot [V_{j-1} u_j]^T [u_j  A u_j] and of
+ * the Arnoldi MAXPY as exact fixed-point integers on the integer pipes, as
+ * gmres_set_block_dot for one system: each basis value becomes a 58-bit
+ * integer relative to its system's column exponent bound (kept per system by
+ * the kernels that write the column), u and w relative to their tile pair's
+ * largest entry; products are summed exactly per tile pair (per row in the
+ * MAXPY) and rounded to FP64 once. fixed_point = 1 (the default) uses them
+ * for FP64 batches with two rows per thread; 0 uses FP64 fused multiply-adds.
+ * *active (may be NULL) receives whether the next solve uses them. The choice
+ * changes rounding only (bound as gmres_set_block_dot states). Never errors
+ * on a valid handle. */
+gmres_status gmres_batch_set_block_dot(gmres_batch bt, int fixed_point, int* active);
+
 /* Solve all systems: b[i] and x[i] are device pointers (host array of `count`
  * pointers) to system i's right-hand side and its x0 / solution. info may be
  * NULL or a host array of `count` entries (per system). Returns GMRES_OK if

@@ -162,6 +162,138 @@ ke_maxpy(VT* __restrict__ V, int64_t ldv, const VT* __restrict__ w, EngDev e, in
   }
 }
 
+// Arnoldi MAXPY of FP64 cycles for every listed system with the column
+// products on the integer pipes (the single-system k_maxpy_fx, per run of one
+// system's tiles): the system's coefficients become integers C_k on one
+// common scale chosen from its basis exponent bounds (Small::ecol), each basis
+// value a 58-bit integer relative to its column's bound; per row the sum over
+// the columns is exact in 64-bit integers (hi-hi and mid limb products, the
+// low-low product dropped) and rounded to FP64 once, then alpha w is added by
+// one FMA. Rows of the run past the system's last row (its last tile's
+// padding) are stored as zeros. The writers note column j+1's exponent bound.
+// CTA ndata + i rotates column j-1 of the i-th listed system, as in ke_maxpy.
+__global__ void __launch_bounds__(kThreads, 4)
+ke_maxpy_fx(double* __restrict__ V, int64_t ldv, const double* __restrict__ w, EngDev e, int j, int ndata) {
+  __shared__ int4 sC[kMaxM + 1];  // (Ch, Cl, 5 + column bound field, 0) per column
+  __shared__ uint32_t s_p[kWarps];
+  __shared__ int sK, s_on, s_bad;
+  __shared__ double s_alpha;
+  __shared__ int64_t s_end;
+  __shared__ const double* s_coef;
+  __shared__ unsigned int* s_ecol;
+  if ((int)blockIdx.x >= ndata) {
+    const int i = (int)blockIdx.x - ndata;
+    if (i >= *e.n_slots) return;
+    const Small sm = e.smalls[__ldg(e.act_slots + i)];
+    if (threadIdx.x == 0) s_on = !__ldcg(&sm.st->done) && j >= 1 && j < __ldcg(&sm.st->kmax);
+    __syncthreads();
+    if (s_on) {
+      const double h = __ldcg(&sm.H[(size_t)(j - 1) * sm.ldh + j]);
+      const int stop = finish_column(sm, j - 1, h, false);
+      if (threadIdx.x == 0) {
+        sm.st->grid_syncs += 1;
+        if (stop) sm.st->done = 1;
+      }
+    }
+    return;
+  }
+  int64_t lo, hi;
+  if (!cta_tile_range(e, ndata, lo, hi)) return;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  double2* out2 = reinterpret_cast<double2*>(V + (size_t)(j + 1) * ldv);
+  const double2* w2 = reinterpret_cast<const double2*>(w);
+  for (int64_t it = lo; it < hi;) {
+    int sy;
+    const int64_t run = tile_run(e, it, hi, &sy);
+    const int64_t t0 = __ldg(e.act_tiles + it);
+    __syncthreads();  // every warp is done with the previous run's flags and coefficients
+    if (threadIdx.x == 0) {
+      const Small sm = e.smalls[sy];
+      s_on = !__ldcg(&sm.st->done) && j < __ldcg(&sm.st->kmax);
+      sK = __ldcg(&sm.st->maxpy_k);
+      s_coef = sm.coef;
+      s_ecol = sm.ecol;
+      s_alpha = __ldcg(sm.coef);
+      s_bad = 0;
+      s_end = e.desc[sy].row0 + e.desc[sy].n;
+    }
+    __syncthreads();
+    it += run;
+    if (!s_on) continue;
+    const int K = sK;
+    // the coefficients' common scale: P = max_k (field(c_k) + field bound of column k)
+    double ck = 0.0;
+    int fk = (int)kFxMinField, pk = 0;
+    if ((int)threadIdx.x < K) {
+      ck = __ldcg(s_coef + 1 + threadIdx.x);
+      fk = (int)max(kFxMinField, __ldcg(s_ecol + threadIdx.x) >> 20);
+      const int gk = (int)fx_field(ck);
+      if (gk == 0x7FF || fk == 0x7FF) s_bad = 1;  // NaN or Inf among the inputs
+      pk = (ck != 0.0) ? gk + fk : 0;
+    }
+    const uint32_t pm = __reduce_max_sync(0xffffffffu, (uint32_t)pk);
+    if (lane == 0) s_p[wid] = pm;
+    __syncthreads();
+    uint32_t q = 0;
+#pragma unroll
+    for (int v = 0; v < kWarps; ++v) q = max(q, s_p[v]);
+    const int P = (int)q;
+    const int cbits = K > 64 ? 56 : 57;
+    if ((int)threadIdx.x < K) {
+      long long C = 0;
+      if (ck != 0.0 && P > 0) C = __double2ll_rn(scalbn(ck, cbits + 1022 - P + fk));  // |C| < 2^cbits
+      sC[threadIdx.x] = make_int4((int)(C >> 29), (int)(C & 0x1FFFFFFFll), 5 + fk, 0);
+    }
+    __syncthreads();
+    const bool bad = s_bad != 0;
+    const double alpha = s_alpha;
+    const int e2 = P - 2044 - cbits;  // sum = (hh + mid / 2^29) 2^(P - 2044 - cbits)
+    const int64_t end = s_end;
+    uint32_t emax = 0;
+    // two rows per thread (16-byte loads): arena rows are even-aligned and ldv is a multiple of 512
+    const int64_t q1 = (t0 + run) * (kThreads / 2);
+    for (int64_t i = t0 * (kThreads / 2) + threadIdx.x; i < q1; i += blockDim.x) {
+      long long hh0 = 0, md0 = 0, hh1 = 0, md1 = 0;
+      for (int k = 0; k < K; k += 4) {
+        double2 x[4];
+#pragma unroll
+        for (int u2 = 0; u2 < 4; ++u2)
+          x[u2] = (k + u2 < K) ? __ldg(reinterpret_cast<const double2*>(V + (size_t)(k + u2) * ldv) + i)
+                               : make_double2(0.0, 0.0);
+#pragma unroll
+        for (int u2 = 0; u2 < 4; ++u2) {
+          if (k + u2 < K) {
+            const int4 c = sC[k + u2];
+            const int2 a = fx_split(x[u2].x, c.z), b = fx_split(x[u2].y, c.z);
+            hh0 = fx_madw(c.x, a.x, hh0);
+            md0 = fx_madw(c.x, a.y, md0);
+            md0 = fx_madw(c.y, a.x, md0);
+            hh1 = fx_madw(c.x, b.x, hh1);
+            md1 = fx_madw(c.x, b.y, md1);
+            md1 = fx_madw(c.y, b.x, md1);
+          }
+        }
+        if ((k & 15) == 12) {  // every 16 columns: carry mid's high part into hh
+          hh0 += md0 >> 29;
+          md0 &= 0x1FFFFFFFll;
+          hh1 += md1 >> 29;
+          md1 &= 0x1FFFFFFFll;
+        }
+      }
+      const double2 wv = __ldg(w2 + i);
+      double2 o;
+      o.x = fma(alpha, wv.x, fx_to_double(hh0 + (md0 >> 29), e2));
+      o.y = fma(alpha, wv.y, fx_to_double(hh1 + (md1 >> 29), e2));
+      if (bad) o.x = o.y = __longlong_as_double(0x7ff8000000000000ll);
+      if (2 * i >= end) o.x = 0.0;
+      if (2 * i + 1 >= end) o.y = 0.0;
+      out2[i] = o;
+      emax = max(emax, max(fx_hi_field(o.x), fx_hi_field(o.y)));
+    }
+    fx_note_max(s_ecol, j + 1, emax);
+  }
+}
+
 // Cycle start of every listed system: r = b - A x over its rows (FP64, local
 // CSR), written to out (basis column 0 for FP64 cycles, the FP64 residual
 // vector for FP32 cycles), with the sums of r^2 and b^2; the CTA completing a
@@ -177,11 +309,13 @@ ke_residual(const double* __restrict__ b, const double* __restrict__ x, double* 
   if (!cta_tile_range(e, (int)gridDim.x, lo, hi)) return;
   int cur = -1;
   double rr = 0.0, bb = 0.0;
+  uint32_t emax = 0;  // exponent bound of basis column 0 (FP64 cycles; Small::ecol is null otherwise)
   for (int64_t it = lo; it <= hi; ++it) {
     const int64_t t = (it < hi) ? __ldg(e.act_tiles + it) : -1;
     const int snext = (it < hi) ? __ldg(e.act_sys + it) : -1;
     if (snext != cur) {  // CTA-uniform
       if (cur >= 0 && s_on) {
+        fx_note_max(e.smalls[cur].ecol, 0, emax);
         const double trr = block_sum(rr, sbuf);
         const double tbb = block_sum(bb, sbuf);
         if (threadIdx.x == 0) {
@@ -203,6 +337,7 @@ ke_residual(const double* __restrict__ b, const double* __restrict__ x, double* 
       if (snext < 0) break;
       cur = snext;
       rr = bb = 0.0;
+      emax = 0;
       __syncthreads();
       if (threadIdx.x == 0) {
         s_on = __ldcg(&e.smalls[cur].st->kmax) >= 0;  // a retired system is left untouched
@@ -216,6 +351,7 @@ ke_residual(const double* __restrict__ b, const double* __restrict__ x, double* 
       const double bv = b[row];
       const double v = bv - csr_row(s_d.rowptr - s_d.row0, s_d.col, s_d.val, x + s_d.row0, row);
       out[row] = v;
+      emax = max(emax, fx_hi_field(v));
       rr = fma(v, v, rr);
       bb = fma(bv, bv, bb);
     }
@@ -297,14 +433,14 @@ __global__ void ke_to_float(const double* __restrict__ a, float* __restrict__ ou
 
 // Engine step kernels (instantiated in engine_step_f64.cu and engine_step_f32.cu).
 template <typename VT>
-EngStepKernel<VT> eng_step_for(int m, bool pairs);
+EngStepKernel<VT> eng_step_for(int m, bool pairs, bool fx);
 template <>
-EngStepKernel<double> eng_step_for<double>(int m, bool pairs) {
-  return reinterpret_cast<EngStepKernel<double>>(const_cast<void*>(lsg_engine::eng_step_f64(m, pairs)));
+EngStepKernel<double> eng_step_for<double>(int m, bool pairs, bool fx) {
+  return reinterpret_cast<EngStepKernel<double>>(const_cast<void*>(lsg_engine::eng_step_f64(m, pairs, fx)));
 }
 template <>
-EngStepKernel<float> eng_step_for<float>(int m, bool pairs) {
-  return reinterpret_cast<EngStepKernel<float>>(const_cast<void*>(lsg_engine::eng_step_f32(m, pairs)));
+EngStepKernel<float> eng_step_for<float>(int m, bool pairs, bool fx) {
+  return reinterpret_cast<EngStepKernel<float>>(const_cast<void*>(lsg_engine::eng_step_f32(m, pairs, fx)));
 }
 
 // ==========================================================================
@@ -394,6 +530,7 @@ struct Engine {
   std::string err;
   int device = 0, nsm = 0, P = 0, nvmax = 0, hist_cap = 0;
   bool pairs = true;
+  bool fx = true;  // FP64 tile pairs: block dot and MAXPY products on the integer pipes
   int64_t R = 0, ldv = 0;
   size_t vb = 8;
   // arena
@@ -409,6 +546,7 @@ struct Engine {
   DevState* d_states = nullptr;
   char* d_blk = nullptr;
   unsigned int* d_tickets = nullptr;
+  unsigned int* d_ecol = nullptr;  // FP64 cycles: basis exponent bounds, m + 2 per slot
   // listing
   int32_t* d_tiles = nullptr;  // act_tiles (R / 256) | act_sys (R / 256)
   int32_t* d_act = nullptr;    // act_slots (S) | sys_b0 (S) | sys_nslot (S) | sys_slot0 (S) | n_slots
@@ -551,6 +689,10 @@ struct Engine {
     ETRY(cudaMemset(d_blk, 0, off * S));
     ETRY(cudaMalloc(&d_states, sizeof(DevState) * S));
     ETRY(cudaMemset(d_states, 0, sizeof(DevState) * S));
+    if (!ir()) {
+      ETRY(cudaMalloc(&d_ecol, sizeof(unsigned int) * (size_t)(m + 2) * S));
+      ETRY(cudaMemset(d_ecol, 0, sizeof(unsigned int) * (size_t)(m + 2) * S));
+    }
     ETRY(cudaMallocHost(&h_states, sizeof(DevState) * S));
     std::memset(h_states, 0, sizeof(DevState) * S);
     smalls.resize(S);
@@ -568,6 +710,7 @@ struct Engine {
       sm.coef = reinterpret_cast<double*>(base + ocf);
       sm.coefx = reinterpret_cast<double*>(base + ocx);
       sm.hist = reinterpret_cast<double*>(base + ohi);
+      sm.ecol = d_ecol ? d_ecol + (size_t)(m + 2) * i : nullptr;
       sm.partials = nullptr;
       sm.raw = nullptr;
       sm.m = m;
@@ -595,9 +738,10 @@ struct Engine {
       for (int cap = 16384; cap >= 256 && stage_cap == 0; cap -= 256) {
         const size_t need = (size_t)(2 * kThreads + 4) * 4 + (size_t)cap * (4 + vb) + epi;
         bool ok = true;
-        for (bool pr : {false, true}) {
-          const void* f = ir() ? reinterpret_cast<const void*>(eng_step_for<float>(m, pr))
-                               : reinterpret_cast<const void*>(eng_step_for<double>(m, pr));
+        for (int v = 0; v < 3; ++v) {  // one row per thread, tile pairs, tile pairs with fixed-point products
+          const bool pr = v > 0, fv = v == 2;
+          const void* f = ir() ? reinterpret_cast<const void*>(eng_step_for<float>(m, pr, fv))
+                               : reinterpret_cast<const void*>(eng_step_for<double>(m, pr, fv));
           int nb = 0;
           if (raise_smem_limit(f, need) != cudaSuccess ||
               cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, kThreads, need) != cudaSuccess || nb < per_sm)
@@ -620,8 +764,8 @@ struct Engine {
   void release() {
     drop_graphs();
     for (void* p : {V, w, (void*)bv, (void*)xv, (void*)r64, (void*)csr_pool, (void*)d_desc, (void*)d_smalls,
-                    (void*)d_states, (void*)d_blk, (void*)d_tickets, (void*)d_tiles, (void*)d_act, (void*)d_nact,
-                    (void*)d_partials})
+                    (void*)d_states, (void*)d_blk, (void*)d_tickets, (void*)d_ecol, (void*)d_tiles, (void*)d_act,
+                    (void*)d_nact, (void*)d_partials})
       if (p) cudaFree(p);
     for (void* p : {(void*)h_states, (void*)h_tiles, (void*)h_act, (void*)h_nact, (void*)h_desc})
       if (p) cudaFreeHost(p);
@@ -635,6 +779,7 @@ struct Engine {
     d_states = nullptr;
     d_blk = nullptr;
     d_tickets = nullptr;
+    d_ecol = nullptr;
     d_tiles = d_act = nullptr;
     d_nact = nullptr;
     d_partials = nullptr;
@@ -934,10 +1079,10 @@ struct Engine {
     for (int j = 0; j <= KM; ++j) {
       int pr = prof_begin(PC_STEP, j);
       if (ir())
-        eng_step_for<float>(cfg.m, pairs)<<<P, kThreads, step_smem, stream>>>(
+        eng_step_for<float>(cfg.m, pairs, false)<<<P, kThreads, step_smem, stream>>>(
             static_cast<const float*>(V), ldv, static_cast<float*>(w), d, j, stage_cap);
       else
-        eng_step_for<double>(cfg.m, pairs)<<<P, kThreads, step_smem, stream>>>(
+        eng_step_for<double>(cfg.m, pairs, fx)<<<P, kThreads, step_smem, stream>>>(
             static_cast<const double*>(V), ldv, static_cast<double*>(w), d, j, stage_cap);
       prof_end(pr);
       if (j < KM) {
@@ -945,6 +1090,9 @@ struct Engine {
         if (ir())
           ke_maxpy<float><<<nd + S, kThreads, 0, stream>>>(static_cast<float*>(V), ldv, static_cast<const float*>(w),
                                                            d, j, nd);
+        else if (fx_active())
+          ke_maxpy_fx<<<nd + S, kThreads, 0, stream>>>(static_cast<double*>(V), ldv, static_cast<const double*>(w), d,
+                                                       j, nd);
         else
           ke_maxpy<double><<<nd + S, kThreads, 0, stream>>>(static_cast<double*>(V), ldv,
                                                             static_cast<const double*>(w), d, j, nd);
@@ -1014,6 +1162,8 @@ struct Engine {
       rby += 4.0 * (n + 1) + 12.0 * nnz + 24.0 * n;
       rfl += 2.0 * nnz + 5.0 * n;
     }
+    if (d_ecol)  // the new cycle's basis bounds start from column 0, noted by the residual pass
+      ETRY(cudaMemsetAsync(d_ecol, 0, sizeof(unsigned int) * (size_t)(cfg.m + 2) * slot.size(), stream));
     int pr = prof_begin(PC_RES, 1, rby, rfl);
     ke_residual<<<P, kThreads, 0, stream>>>(bv, xv, ir() ? r64 : static_cast<double*>(V), d);
     prof_end(pr);
@@ -1156,10 +1306,10 @@ struct Engine {
           if (e == cudaSuccess) e = cudaEventRecord(e0, stream);
           if (e == cudaSuccess) {
             if (ir())
-              eng_step_for<float>(cfg.m, pr == 1)<<<Pc, kThreads, step_smem, stream>>>(
+              eng_step_for<float>(cfg.m, pr == 1, false)<<<Pc, kThreads, step_smem, stream>>>(
                   static_cast<const float*>(V), ldv, static_cast<float*>(w), dev(), j, stage_cap);
             else
-              eng_step_for<double>(cfg.m, pr == 1)<<<Pc, kThreads, step_smem, stream>>>(
+              eng_step_for<double>(cfg.m, pr == 1, fx)<<<Pc, kThreads, step_smem, stream>>>(
                   static_cast<const double*>(V), ldv, static_cast<double*>(w), dev(), j, stage_cap);
             e = cudaGetLastError();
           }
@@ -1187,6 +1337,9 @@ struct Engine {
     set_shape(bestP, bestPairs);
     return GMRES_OK;
   }
+
+  // FP64 tile pairs with fixed-point block-dot and MAXPY products
+  bool fx_active() const { return fx && pairs && !ir(); }
 
   void set_shape(int ctas, bool pr) {
     P = ctas;
@@ -1367,6 +1520,14 @@ gmres_status gmres_batch_set_rows_per_thread(gmres_batch b, int rows) {
   if (!b) return GMRES_ERR_ARG;
   if (rows != 1 && rows != 2) return bfail(b, GMRES_ERR_ARG, "rows per thread must be 1 or 2");
   b->eng.set_shape(b->eng.P, rows == 2);
+  return GMRES_OK;
+}
+
+gmres_status gmres_batch_set_block_dot(gmres_batch b, int fixed_point, int* active) {
+  if (!b) return GMRES_ERR_ARG;
+  b->eng.fx = fixed_point != 0;
+  b->eng.drop_graphs();
+  if (active) *active = b->eng.fx_active() ? 1 : 0;
   return GMRES_OK;
 }
 

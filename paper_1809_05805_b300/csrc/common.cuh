@@ -1053,7 +1053,12 @@ __device__ __forceinline__ double fx_to_double(long long t, int e2) {
 // in su, sw by their limbs (int2 per row) relative to the pair's own bounds;
 // s_ex holds 2 kWarps words. w may be absent (need_w false: the cycle's tail,
 // which needs only V^T u); then wr0 = wr1 = 0.
-template <int MAXC, typename Hook>
+//
+// RING = false (the batched engine, which has no room for the ring): each lane
+// loads its two rows of a slice directly (16-byte loads through the read-only
+// path), and only pair rows in [rlo, rhi) (relative to the pair's first row)
+// take part: a unit that is one tile of a pair, or a system's ragged end.
+template <int MAXC, bool RING = true, typename Hook>
 __device__ __forceinline__ void tile_pair_dot_rows_fx(int64_t pp, int64_t n,
                                                       const double* __restrict__ V, int64_t ldv, bool need_w, int J8,
                                                       int r8, double ur0, double wr0, double ur1, double wr1,
@@ -1061,7 +1066,7 @@ __device__ __forceinline__ void tile_pair_dot_rows_fx(int64_t pp, int64_t n,
                                                       const int (&kfr)[2], double (&acc_a)[MAXC],
                                                       double (&acc_c)[MAXC], double (&rem_a)[2],
                                                       double (&rem_c)[2], double& sig, double& dd, uint32_t* s_ex,
-                                                      Hook hook) {
+                                                      Hook hook, int rlo = 0, int rhi = 2 * kThreads) {
   constexpr int S = pf_stages<double>();  // ring slices per warp
   constexpr int R = 2;                    // rows per 16-byte copy
   constexpr int NQ = kRowsPerLane / R;    // copies per lane per slice
@@ -1096,7 +1101,7 @@ __device__ __forceinline__ void tile_pair_dot_rows_fx(int64_t pp, int64_t n,
   const bool bad = fu == 0x7FFu || fw == 0x7FFu;  // NaN or Inf among the pair's u, w
   // x u = (Xh Uh + (Xh Ul + Xl Uh) / 2^29) 2^(f_x + f_u - 2102): the flush scales
   const int ea = (int)fu - 2102, ec = (int)fw - 2102;
-  double* wring = ring + wid * (S * kThreads);
+  double* wring = RING ? ring + wid * (S * kThreads) : nullptr;  // this warp's ring slices
   const int nr = (wid < 2 * r8 ? 1 : 0) + (wid + kWarps < 2 * r8 ? 1 : 0);  // remainder half-columns of this warp
   const int nsl = 2 * J8 + nr;  // slices this warp streams
   // column and half of this warp's slice sl
@@ -1126,14 +1131,28 @@ __device__ __forceinline__ void tile_pair_dot_rows_fx(int64_t pp, int64_t n,
   // the products of slice sl (half h of a column with shift kfc) into the
   // exact sums ah, am (x u) and ch, cm (x w)
   auto slice = [&](int sl, int h, int kfc, long long& ah, long long& am, long long& ch, long long& cm) {
-    if (sl + S - 1 < nsl) issue(sl + S - 1, (sl + S - 1) % S);
-    cp_async_commit();
-    cp_async_wait<S - 1>();  // slice sl's copies are done
-    const double* slp = wring + (sl % S) * kThreads;
+    const double* slp = nullptr;
+    const double* colg = nullptr;
+    if constexpr (RING) {
+      if (sl + S - 1 < nsl) issue(sl + S - 1, (sl + S - 1) % S);
+      cp_async_commit();
+      cp_async_wait<S - 1>();  // slice sl's copies are done
+      slp = wring + (sl % S) * kThreads;
+    } else {
+      int col, hh;
+      locate(sl, col, hh);
+      colg = V + (size_t)col * ldv + pp * (2 * kThreads);
+    }
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
-      const double2 xv = *reinterpret_cast<const double2*>(slp + 32 * R * q + R * lane);
       const int r = h * kThreads + 32 * R * q + R * lane;       // row within the pair
+      double2 xv;
+      if constexpr (RING) {
+        xv = *reinterpret_cast<const double2*>(slp + 32 * R * q + R * lane);
+      } else {
+        xv = (r >= rlo && r + 1 < rhi) ? __ldg(reinterpret_cast<const double2*>(colg + r)) : make_double2(0.0, 0.0);
+        if (r >= rlo && r < rhi && r + 1 >= rhi) xv.x = __ldg(colg + r);  // the range's last row, alone
+      }
       const int4 uu = *reinterpret_cast<const int4*>(lu + r);  // limbs of rows r, r + 1
       const int2 x0 = fx_split(xv.x, kfc), x1 = fx_split(xv.y, kfc);
       ah = fx_madw(x0.x, uu.x, ah);
@@ -1160,10 +1179,12 @@ __device__ __forceinline__ void tile_pair_dot_rows_fx(int64_t pp, int64_t n,
     a += nan ? qnan : fx_to_double(ah + (am >> 29), ea + fx);
     if (need_w) c += nan ? qnan : fx_to_double(ch + (cm >> 29), ec + fx);
   };
+  if constexpr (RING) {
 #pragma unroll
-  for (int sl = 0; sl < S - 1; ++sl) {
-    if (sl < nsl) issue(sl, sl);  // warp-uniform
-    cp_async_commit();
+    for (int sl = 0; sl < S - 1; ++sl) {
+      if (sl < nsl) issue(sl, sl);  // warp-uniform
+      cp_async_commit();
+    }
   }
 #pragma unroll
   for (int c = 0; c < MAXC; ++c) {
@@ -1183,7 +1204,7 @@ __device__ __forceinline__ void tile_pair_dot_rows_fx(int64_t pp, int64_t n,
       flush(kfr[q], ah, am, ch, cm, rem_a[q], rem_c[q]);
     }
   }
-  cp_async_wait<0>();
+  if constexpr (RING) cp_async_wait<0>();
   __syncthreads();
 }
 

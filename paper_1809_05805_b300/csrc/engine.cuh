@@ -9,9 +9,10 @@
 
 namespace lsg_engine {
 // Host stub of the engine step kernel for restart length m, with or without
-// tile pairs; callers cast it to their EngStepKernel type.
-const void* eng_step_f64(int m, bool pairs);
-const void* eng_step_f32(int m, bool pairs);
+// tile pairs, with or without fixed-point block-dot products (FP64 tile pairs
+// only; ignored otherwise); callers cast it to their EngStepKernel type.
+const void* eng_step_f64(int m, bool pairs, bool fx);
+const void* eng_step_f32(int m, bool pairs, bool fx);
 }  // namespace lsg_engine
 
 namespace {

@@ -37,11 +37,18 @@ __device__ __noinline__ VT csr_row_plain(const int32_t* __restrict__ rowptr, con
 // step kernel); the epilogue's shared memory follows the staging buffer
 // (cap entries), since a system's epilogue can run while the next unit lands.
 // Each system's rowptr is padded with nnz to whole tile pairs + 8.
-template <int MAXC, bool PAIRS, typename VT>
+// FP64 cycles on tile pairs (FX): the block dot's products as exact
+// fixed-point integers on the integer pipes (tile_pair_dot_rows_fx without the
+// column ring, the system's basis exponent bounds from its Small::ecol), as
+// the single-system solver's staging mode 6; a unit that is one tile of a pair
+// runs as that pair with the other tile's rows masked.
+template <int MAXC, bool PAIRS, typename VT, bool FX>
 __global__ void __launch_bounds__(kThreads, sizeof(VT) == 4 ? 3 : 2)
 ke_step(const VT* __restrict__ V, int64_t ldv, VT* __restrict__ w, EngDev e, int j, int cap) {
-  __shared__ VT su[PAIRS ? 2 * kThreads : kThreads];
-  __shared__ VT sw[PAIRS ? 2 * kThreads : kThreads];
+  static_assert(!FX || (PAIRS && std::is_same<VT, double>::value), "fixed-point products need FP64 tile pairs");
+  __shared__ __align__(16) VT su[PAIRS ? 2 * kThreads : kThreads];
+  __shared__ __align__(16) VT sw[PAIRS ? 2 * kThreads : kThreads];
+  __shared__ uint32_t s_ex[2 * kWarps];
   __shared__ double red[2 * (kMaxM + 1) + 2];
   __shared__ int s_active, s_tail, s_stage_off;
   __shared__ SysDesc s_d;
@@ -99,6 +106,8 @@ ke_step(const VT* __restrict__ V, int64_t ldv, VT* __restrict__ w, EngDev e, int
   }
   VT acc_a[MAXC], acc_c[MAXC], rem_a[kWarps - 1], rem_c[kWarps - 1];
   VT sig = VT(0), dd = VT(0);
+  double fr_a[2] = {0.0, 0.0}, fr_c[2] = {0.0, 0.0};  // FX: remainder half-columns
+  int kf[MAXC], kfr[2];                               // FX: 5 + the current system's column bounds
   int cur = -1;
   for (int64_t it = lo; it <= hi;) {
     const int64_t t = (it < hi) ? __ldg(e.act_tiles + it) : -1;
@@ -109,7 +118,10 @@ ke_step(const VT* __restrict__ V, int64_t ldv, VT* __restrict__ w, EngDev e, int
         __syncthreads();
       }
       if (cur >= 0 && s_active) {  // done with system cur: publish its sums
-        cta_partials<MAXC, VT>(acc_a, acc_c, rem_a, rem_c, sig, dd, j, J8, r8, red);
+        if constexpr (FX)
+          cta_partials_fx<MAXC>(acc_a, acc_c, fr_a, fr_c, sig, dd, j, J8, r8, red);
+        else
+          cta_partials<MAXC, VT>(acc_a, acc_c, rem_a, rem_c, sig, dd, j, J8, r8, red);
         if (sys_publish(e, cur, red, 2 * j + 2)) {
           const Small sm = e.smalls[cur];
           if (threadIdx.x == 0) sm.st->reductions += 1;
@@ -132,6 +144,19 @@ ke_step(const VT* __restrict__ V, int64_t ldv, VT* __restrict__ w, EngDev e, int
 #pragma unroll
       for (int c = 0; c < kWarps - 1; ++c) rem_a[c] = rem_c[c] = VT(0);
       sig = dd = VT(0);
+      if constexpr (FX) {
+        fr_a[0] = fr_a[1] = fr_c[0] = fr_c[1] = 0.0;
+        const unsigned int* ec = e.smalls[cur].ecol;
+        const int wid = threadIdx.x >> 5;
+#pragma unroll
+        for (int c = 0; c < MAXC; ++c)
+          kf[c] = 5 + (int)max(kFxMinField, c < J8 ? __ldcg(ec + wid + c * kWarps) >> 20 : 0u);
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const int r = wid + q * kWarps;
+          kfr[q] = 5 + (int)max(kFxMinField, r < 2 * r8 ? __ldcg(ec + J8 * kWarps + (r >> 1)) >> 20 : 0u);
+        }
+      }
     }
     const bool tail = s_tail;
     // a system's tiles are consecutive in the list and in the arena (its
@@ -203,7 +228,19 @@ ke_step(const VT* __restrict__ V, int64_t ldv, VT* __restrict__ w, EngDev e, int
           w[row0] = wr0;
         }
       }
-      if (pair)
+      if constexpr (FX) {
+        // the pair t / 2: both tiles, or (a single tile) the one this unit holds
+        const int64_t pb = (t >> 1) * (2 * kThreads);  // the pair's first arena row
+        const bool second = !pair && (t & 1);
+        const int rlo = (int)(max(s_d.row0, second ? pb + kThreads : pb) - pb);
+        const int rhi = (int)(min(lim, pair || second ? pb + 2 * kThreads : pb + kThreads) - pb);
+        if (second)
+          tile_pair_dot_rows_fx<MAXC, false>(t >> 1, lim, V, ldv, !tail, J8, r8, 0.0, 0.0, ur0, wr0, su, sw, nullptr,
+                                              kf, kfr, acc_a, acc_c, fr_a, fr_c, sig, dd, s_ex, next, rlo, rhi);
+        else
+          tile_pair_dot_rows_fx<MAXC, false>(t >> 1, lim, V, ldv, !tail, J8, r8, ur0, wr0, ur1, wr1, su, sw, nullptr,
+                                              kf, kfr, acc_a, acc_c, fr_a, fr_c, sig, dd, s_ex, next, rlo, rhi);
+      } else if (pair)
         tile_pair_dot_rows<MAXC, VT, VT>(t >> 1, lim, V, ldv, !tail, J8, r8, ur0, wr0, ur1, wr1, su, sw, acc_a, acc_c,
                                          rem_a, rem_c, sig, dd, next);
       else
@@ -217,25 +254,29 @@ ke_step(const VT* __restrict__ V, int64_t ldv, VT* __restrict__ w, EngDev e, int
   }
 }
 
-template <bool PAIRS, typename VT>
+template <bool PAIRS, typename VT, bool FX>
 EngStepKernel<VT> eng_step_sel(int m) {
   switch (std::max(1, m / kWarps)) {
-    case 1: return ke_step<1, PAIRS, VT>;
-    case 2: return ke_step<2, PAIRS, VT>;
-    case 3: return ke_step<3, PAIRS, VT>;
-    case 4: return ke_step<4, PAIRS, VT>;
-    case 5: return ke_step<5, PAIRS, VT>;
-    case 6: return ke_step<6, PAIRS, VT>;
-    case 7: return ke_step<7, PAIRS, VT>;
-    case 8: return ke_step<8, PAIRS, VT>;
-    case 9: case 10: case 11: case 12: return ke_step<12, PAIRS, VT>;
-    default: return ke_step<16, PAIRS, VT>;
+    case 1: return ke_step<1, PAIRS, VT, FX>;
+    case 2: return ke_step<2, PAIRS, VT, FX>;
+    case 3: return ke_step<3, PAIRS, VT, FX>;
+    case 4: return ke_step<4, PAIRS, VT, FX>;
+    case 5: return ke_step<5, PAIRS, VT, FX>;
+    case 6: return ke_step<6, PAIRS, VT, FX>;
+    case 7: return ke_step<7, PAIRS, VT, FX>;
+    case 8: return ke_step<8, PAIRS, VT, FX>;
+    case 9: case 10: case 11: case 12: return ke_step<12, PAIRS, VT, FX>;
+    default: return ke_step<16, PAIRS, VT, FX>;
   }
 }
 
+// The step kernel for restart length m, one or two rows per thread, and (FP64
+// tile pairs only) fixed-point block-dot products.
 template <typename VT>
-EngStepKernel<VT> eng_step_table(int m, bool pairs) {
-  return pairs ? eng_step_sel<true, VT>(m) : eng_step_sel<false, VT>(m);
+EngStepKernel<VT> eng_step_table(int m, bool pairs, bool fx) {
+  if constexpr (std::is_same<VT, double>::value)
+    if (pairs && fx) return eng_step_sel<true, VT, true>(m);
+  return pairs ? eng_step_sel<true, VT, false>(m) : eng_step_sel<false, VT, false>(m);
 }
 
 }  // namespace

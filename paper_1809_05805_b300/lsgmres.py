@@ -91,7 +91,8 @@ EXPORTS = ["gmres_create", "gmres_set", "gmres_set_tol", "gmres_set_stream", "gm
            "lsg_block_dot", "lsg_maxpy", "gmres_arnoldi", "gmres_set_profile", "gmres_profile", "gmres_test_stall_staging", "gmres_set_block_dot", "gmres_set_persistent",
            "gmres_test_stall_barrier",
            "lsg_block_dot_noalloc", "gmres_batch_create", "gmres_batch_set_grid", "gmres_batch_get_grid",
-           "gmres_batch_set_rows_per_thread", "gmres_batch_get_rows_per_thread", "gmres_batch_set_stream", "gmres_batch_solve",
+           "gmres_batch_set_rows_per_thread", "gmres_batch_get_rows_per_thread", "gmres_batch_set_block_dot",
+           "gmres_batch_set_stream", "gmres_batch_solve",
            "gmres_batch_solve_host", "gmres_batch_set_profile", "gmres_batch_profile", "gmres_batch_launch_log",
            "gmres_batch_history", "gmres_batch_destroy", "gmres_batch_last_error", "gmres_server_create",
            "gmres_server_submit", "gmres_server_poll", "gmres_server_wait", "gmres_server_drain",
@@ -142,6 +143,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "gmres_batch_get_grid": ([P, ctypes.POINTER(I)], I),
         "gmres_batch_set_rows_per_thread": ([P, I], I),
         "gmres_batch_get_rows_per_thread": ([P, ctypes.POINTER(I)], I),
+        "gmres_batch_set_block_dot": ([P, I, ctypes.POINTER(I)], I),
         "gmres_batch_solve": ([P, P, P, ctypes.POINTER(_Info)], I),
         "gmres_batch_history": ([P, I, P, I, ctypes.POINTER(I)], I),
         "gmres_batch_solve_host": ([P, P, P, ctypes.POINTER(_Info)], I),
@@ -417,6 +419,14 @@ class BatchSolver:
 
     def set_rows_per_thread(self, rows: int):
         self._check(self.lib.gmres_batch_set_rows_per_thread(self.h, int(rows)))
+
+    def set_block_dot(self, fixed_point: bool) -> bool:
+        """gmres_batch_set_block_dot: fixed-point block-dot and MAXPY products
+        (True, the default) or FP64 FMAs; returns whether the next solve uses
+        the fixed-point form (FP64 batches with two rows per thread)."""
+        active = ctypes.c_int(0)
+        self._check(self.lib.gmres_batch_set_block_dot(self.h, int(fixed_point), ctypes.byref(active)))
+        return bool(active.value)
 
     def solve(self, bs, xs, *, allow=(OK, MAXITER)) -> list[SolveInfo]:
         """bs, xs: lists of float64 CUDA tensors (xs hold x0 on entry, solutions on exit)."""

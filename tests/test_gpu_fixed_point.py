@@ -185,3 +185,71 @@ def test_nonfinite_reaches_the_sums(torch_cuda, lsg):
                     torch.zeros(n, dtype=torch.float64, device="cuda"), True)
     assert np.all(np.isnan(X[:16])) and np.isnan(X[32])
     s.close()
+
+
+def _batch_systems(count, seed, side):
+    mats, rhs = [], []
+    for i, par in enumerate(P.batch_2d_params(count, seed=seed, side=side)):
+        A = P.batch_2d_system(par)
+        _, b = P.rhs(A, seed=seed * 1000 + i)
+        mats.append(A)
+        rhs.append(b)
+    return mats, rhs
+
+
+@pytest.mark.parametrize("fixed_point", [True, False])
+@pytest.mark.parametrize("grid", [None, 5, "tiles"])
+def test_batch_matches_oracle(torch_cuda, lsg, orc, fixed_point, grid):
+    """Batched FP64 solves with two rows per thread, with either form of the
+    block-dot and MAXPY products (gmres_batch_set_block_dot), each system held
+    to the single-solve bar against the oracle. Two systems are rescaled (the
+    matrix by 2^-200 and the right-hand side by 2^300, and the right-hand side
+    by 2^-400) so that their stored exponent bounds sit far from 1 and from
+    each other's. grid = 'tiles' gives one tile per CTA: every unit is a single
+    tile, the first or the second of its pair (masked rows in the fixed-point
+    kernel); grid 5 cuts pairs at CTA boundaries."""
+    torch = torch_cuda
+    mats, rhs = _batch_systems(8, seed=41, side=(9, 70))
+    A = mats[2]
+    mats[2] = (A[0], A[1], A[2] * 2.0 ** -200)
+    rhs[2] = P.rhs(mats[2], seed=7)[1] * 2.0 ** 300
+    rhs[5] = rhs[5] * 2.0 ** -400
+    ntiles = sum((len(A[0]) - 1 + 255) // 256 for A in mats)
+    bs = lsg.BatchSolver(mats, m=20, tol=1e-8, max_iter=3000)
+    if grid is not None:
+        bs.set_grid(ntiles if grid == "tiles" else grid)
+    bs.set_rows_per_thread(2)
+    assert bs.set_block_dot(fixed_point) == fixed_point
+    bd = [torch.from_numpy(b).cuda() for b in rhs]
+    xd = [torch.zeros(len(b), dtype=torch.float64, device="cuda") for b in rhs]
+    infos = bs.solve(bd, xd)
+    for i, (A, b, info) in enumerate(zip(mats, rhs, infos)):
+        r = orc.gmres(A, b, variant=1, m=20, tol=1e-8, max_iter=3000)
+        assert info.status == r.status == 0
+        assert info.iters == r.iters and info.restarts == r.restarts
+        hist = bs.history(i)
+        assert len(hist) == len(r.history)
+        k = min(20, len(hist))
+        assert np.all(np.abs(hist[:k] - r.history[:k]) <= 1e-8 * r.history[:k] + 1e-15 * r.history[0])
+        x = xd[i].cpu().numpy()
+        assert np.linalg.norm(x - r.x) <= 1e-9 * np.linalg.norm(r.x)
+    # switching the form back on the same handle changes rounding only
+    assert bs.set_block_dot(not fixed_point) == (not fixed_point)
+    for x in xd:
+        x.zero_()
+    infos2 = bs.solve(bd, xd)
+    for info, info2 in zip(infos, infos2):
+        assert info2.iters == info.iters
+    bs.close()
+
+
+def test_batch_fixed_point_off_for_single_rows(torch_cuda, lsg):
+    """The fixed-point form needs two rows per thread: with one it reports
+    itself inactive."""
+    mats, rhs = _batch_systems(3, seed=43, side=(9, 30))
+    bs = lsg.BatchSolver(mats, m=10, tol=1e-8, max_iter=500)
+    bs.set_rows_per_thread(1)
+    assert not bs.set_block_dot(True)
+    bs.set_rows_per_thread(2)
+    assert bs.set_block_dot(True)
+    bs.close()
