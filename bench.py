@@ -931,7 +931,8 @@ def run_batch(args, w, rank, world, dist):
     step_tflops = st["flops"] / (st["ms"] * 1e-3) / 1e12 if st["ms"] else None
     step_gbs = st["bytes"] / (st["ms"] * 1e-3) / 1e9 if st["ms"] else None
     kname = ("ke_step (batched fused CSR SpMV + block dot, per-(CTA, system) partial sums, per-system epilogue"
-             + ("; tile pairs, the basis products as exact fixed-point integers)" if fx else ")"))
+             + ("; tile pairs, the basis products as exact fixed-point integers"
+                + (", basis streamed through the per-warp cp.async column ring)" if fx == 2 else ")") if fx else ")"))
     if fx:  # the FP64 pipe no longer bounds it: HBM does
         bound = {"bound": "hbm", "achieved": step_gbs, "peak": hbm, "unit": "GB/s",
                  "frac": step_gbs / hbm if step_gbs else None,
@@ -943,7 +944,7 @@ def run_batch(args, w, rank, world, dist):
                  "peak_source": pk["source"] + " (of measured)", "peak_nominal": pk["nominal_tflops"]}
     roofline = {
         "kernel": kname, **bound,
-        "fixed_point_products": fx,
+        "fixed_point_products": bool(fx), "column_ring": fx == 2,
         "traffic": None,
         "launch_avg_ms": st["ms"] / max(st["launches"], 1), "launches": st["launches"],
         "alg_flops_per_launch": st["flops"] / max(st["launches"], 1),

@@ -203,6 +203,18 @@ gmres_status gmres_profile(gmres_handle h, int cls, double* total_ms, int64_t* l
  * choice changes rounding only. Never errors on a valid handle. */
 gmres_status gmres_set_block_dot(gmres_handle h, int fixed_point, int* active);
 
+/* Run-to-run reproducibility of the fixed-point step kernel (the one
+ * gmres_set_block_dot reports active). By default (on = 0) its CTAs take the
+ * 512-row tile pairs from a counter, so that CTAs that run faster take more;
+ * which CTA sums which pair, and so the order of the FP64 additions of the
+ * pairs' exact sums, then varies from run to run, and results can differ in
+ * the last bits between identical solves (each within the same bounds). on = 1
+ * assigns pair p to CTA p mod P (P the reduction grid): every sum in a fixed
+ * order, results bitwise reproducible for a given device and grid, about 6%
+ * slower per step at 256^3. Every other kernel of the library sums in a fixed
+ * order always. Never errors on a valid handle. */
+gmres_status gmres_set_reproducible(gmres_handle h, int on);
+
 /* One launch per restart cycle, for small systems whose steps are bound by
  * launch and synchronization latency rather than by memory or arithmetic.
  * The kernel keeps every CTA resident (a cooperative launch) and runs all
@@ -298,10 +310,15 @@ gmres_status gmres_batch_get_rows_per_thread(gmres_batch bt, int* rows);
  * the kernels that write the column), u and w relative to their tile pair's
  * largest entry; products are summed exactly per tile pair (per row in the
  * MAXPY) and rounded to FP64 once. fixed_point = 1 (the default) uses them
- * for FP64 batches with two rows per thread; 0 uses FP64 fused multiply-adds.
- * *active (may be NULL) receives whether the next solve uses them. The choice
- * changes rounding only (bound as gmres_set_block_dot states). Never errors
- * on a valid handle. */
+ * for FP64 batches with two rows per thread, the step kernel streaming the
+ * basis through a per-warp ring of column slices in shared memory when the
+ * listed systems' tile-pair CSR fits the staging capacity left beside the
+ * ring, else loading it directly; -1 uses them with direct loads always; 0
+ * uses FP64 fused multiply-adds. *active (may be NULL) receives the form the
+ * next solve uses for the systems listed now: 0 FP64 FMAs, 1 fixed point
+ * with direct loads, 2 fixed point with the ring. The choice changes rounding
+ * only (bound as gmres_set_block_dot states). Never errors on a valid
+ * handle. */
 gmres_status gmres_batch_set_block_dot(gmres_batch bt, int fixed_point, int* active);
 
 /* Solve all systems: b[i] and x[i] are device pointers (host array of `count`

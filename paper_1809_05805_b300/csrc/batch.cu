@@ -433,13 +433,13 @@ __global__ void ke_to_float(const double* __restrict__ a, float* __restrict__ ou
 
 // Engine step kernels (instantiated in engine_step_f64.cu and engine_step_f32.cu).
 template <typename VT>
-EngStepKernel<VT> eng_step_for(int m, bool pairs, bool fx);
+EngStepKernel<VT> eng_step_for(int m, bool pairs, int fx);
 template <>
-EngStepKernel<double> eng_step_for<double>(int m, bool pairs, bool fx) {
+EngStepKernel<double> eng_step_for<double>(int m, bool pairs, int fx) {
   return reinterpret_cast<EngStepKernel<double>>(const_cast<void*>(lsg_engine::eng_step_f64(m, pairs, fx)));
 }
 template <>
-EngStepKernel<float> eng_step_for<float>(int m, bool pairs, bool fx) {
+EngStepKernel<float> eng_step_for<float>(int m, bool pairs, int fx) {
   return reinterpret_cast<EngStepKernel<float>>(const_cast<void*>(lsg_engine::eng_step_f32(m, pairs, fx)));
 }
 
@@ -531,6 +531,13 @@ struct Engine {
   int device = 0, nsm = 0, P = 0, nvmax = 0, hist_cap = 0;
   bool pairs = true;
   bool fx = true;  // FP64 tile pairs: block dot and MAXPY products on the integer pipes
+  // the fixed-point step kernel with its column ring (over the epilogue's
+  // shared memory): its CSR staging capacity and dynamic shared memory, and
+  // whether the listed systems' tile pairs fit that capacity
+  int ring_cap = 0;
+  size_t ring_smem = 0;
+  bool ring_ok = false;
+  bool no_ring = false;  // gmres_batch_set_block_dot(-1): fixed point with direct basis loads
   int64_t R = 0, ldv = 0;
   size_t vb = 8;
   // arena
@@ -581,6 +588,7 @@ struct Engine {
   struct G {
     int kmax;
     bool prof;
+    int fxm;  // the step kernel's fixed-point mode when captured
     cudaGraphExec_t exec;
     std::vector<cudaEvent_t> events;
     std::vector<int> rec_cls, rec_j;
@@ -739,7 +747,8 @@ struct Engine {
         const size_t need = (size_t)(2 * kThreads + 4) * 4 + (size_t)cap * (4 + vb) + epi;
         bool ok = true;
         for (int v = 0; v < 3; ++v) {  // one row per thread, tile pairs, tile pairs with fixed-point products
-          const bool pr = v > 0, fv = v == 2;
+          const bool pr = v > 0;
+          const int fv = v == 2 ? 1 : 0;
           const void* f = ir() ? reinterpret_cast<const void*>(eng_step_for<float>(m, pr, fv))
                                : reinterpret_cast<const void*>(eng_step_for<double>(m, pr, fv));
           int nb = 0;
@@ -750,6 +759,19 @@ struct Engine {
         if (ok) {
           stage_cap = cap;
           step_smem = need;
+        }
+      }
+      // the ring variant: the ring shares the epilogue's region (it is live only inside a unit's block dot)
+      if (!ir()) {
+        const void* f = reinterpret_cast<const void*>(eng_step_for<double>(m, true, 2));
+        for (int cap = 16384; cap >= 256 && ring_cap == 0; cap -= 256) {
+          const size_t need = (size_t)(2 * kThreads + 4) * 4 + (size_t)cap * (4 + vb) + std::max(epi, kEngRingBytes);
+          int nb = 0;
+          if (raise_smem_limit(f, need) == cudaSuccess &&
+              cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, kThreads, need) == cudaSuccess && nb >= per_sm) {
+            ring_cap = cap;
+            ring_smem = need;
+          }
         }
       }
       (void)cudaGetLastError();  // sizes above the per-block limit were refused; that is not an error here
@@ -967,6 +989,16 @@ struct Engine {
       tot += ns[s];
     }
     if (tot > slot_cap) return fail(GMRES_ERR_ARG, "internal: slot capacity");
+    // the ring variant keeps the tile pairs' CSR staged when a pair's entries
+    // (estimated from each system's mean row length, with 5% and the copies'
+    // 16-byte rounding to spare) fit its smaller staging capacity
+    bool fits = ring_cap > 0;
+    for (int s : ls) {
+      const Slot& sl = slot[s];
+      const double per_pair = (double)kPairRows * (double)sl.nnz / (double)std::max<int64_t>(sl.n, 1);
+      if (per_pair * 1.05 + 16.0 > (double)ring_cap) fits = false;
+    }
+    ring_ok = fits;
     act[4 * S] = (int32_t)ls.size();  // n_slots
     *h_nact = Ta;
     if (Ta > 0) {
@@ -1074,16 +1106,17 @@ struct Engine {
   // ---- launches
   gmres_status launch_cycle(int KM) {
     const EngDev d = dev();
+    const int fxm = fx_mode();
     const int nd = stream_grid();
     const int S = (int)slot.size();
     for (int j = 0; j <= KM; ++j) {
       int pr = prof_begin(PC_STEP, j);
       if (ir())
-        eng_step_for<float>(cfg.m, pairs, false)<<<P, kThreads, step_smem, stream>>>(
+        eng_step_for<float>(cfg.m, pairs, 0)<<<P, kThreads, step_smem, stream>>>(
             static_cast<const float*>(V), ldv, static_cast<float*>(w), d, j, stage_cap);
       else
-        eng_step_for<double>(cfg.m, pairs, fx)<<<P, kThreads, step_smem, stream>>>(
-            static_cast<const double*>(V), ldv, static_cast<double*>(w), d, j, stage_cap);
+        eng_step_for<double>(cfg.m, pairs, fxm)<<<P, kThreads, fxm == 2 ? ring_smem : step_smem, stream>>>(
+            static_cast<const double*>(V), ldv, static_cast<double*>(w), d, j, fxm == 2 ? ring_cap : stage_cap);
       prof_end(pr);
       if (j < KM) {
         pr = prof_begin(PC_MAXPY, j);
@@ -1109,9 +1142,9 @@ struct Engine {
     if (stream == nullptr) return launch_cycle(KM);
     G* hit = nullptr;
     for (auto& g : graphs)
-      if (g.kmax == KM && g.prof == prof_on) hit = &g;
+      if (g.kmax == KM && g.prof == prof_on && g.fxm == fx_mode()) hit = &g;
     if (!hit) {
-      G g{KM, prof_on, nullptr, {}, {}, {}};
+      G g{KM, prof_on, fx_mode(), nullptr, {}, {}, {}};
       if (prof_on) {
         g.events.resize(2 * (2 * (size_t)KM + 1));
         for (auto& ev : g.events) ETRY(cudaEventCreate(&ev));
@@ -1286,6 +1319,7 @@ struct Engine {
     float best = 1e30f;
     int bestP = (ir() ? 3 : 2) * nsm;
     bool bestPairs = true;
+    const bool pairs0 = pairs;
     st = GMRES_OK;
     for (int pr = 0; pr < 2 && st == GMRES_OK; ++pr)
       for (int k = 1; k <= 3 && st == GMRES_OK; ++k) {
@@ -1305,12 +1339,16 @@ struct Engine {
                                           stream);
           if (e == cudaSuccess) e = cudaEventRecord(e0, stream);
           if (e == cudaSuccess) {
-            if (ir())
-              eng_step_for<float>(cfg.m, pr == 1, false)<<<Pc, kThreads, step_smem, stream>>>(
+            if (ir()) {
+              eng_step_for<float>(cfg.m, pr == 1, 0)<<<Pc, kThreads, step_smem, stream>>>(
                   static_cast<const float*>(V), ldv, static_cast<float*>(w), dev(), j, stage_cap);
-            else
-              eng_step_for<double>(cfg.m, pr == 1, fx)<<<Pc, kThreads, step_smem, stream>>>(
-                  static_cast<const double*>(V), ldv, static_cast<double*>(w), dev(), j, stage_cap);
+            } else {
+              pairs = pr == 1;  // fx_mode() follows the shape being timed
+              const int fxm = fx_mode();
+              eng_step_for<double>(cfg.m, pairs, fxm)<<<Pc, kThreads, fxm == 2 ? ring_smem : step_smem, stream>>>(
+                  static_cast<const double*>(V), ldv, static_cast<double*>(w), dev(), j,
+                  fxm == 2 ? ring_cap : stage_cap);
+            }
             e = cudaGetLastError();
           }
           if (e == cudaSuccess) e = cudaEventRecord(e1, stream);
@@ -1333,13 +1371,18 @@ struct Engine {
     cudaEventDestroy(e1);
     for (int s : all) std::memset(&h_states[s], 0, sizeof(DevState));
     cudaMemcpy(d_states, h_states, sizeof(DevState) * slot.size(), cudaMemcpyHostToDevice);
-    if (st != GMRES_OK) return st;
+    if (st != GMRES_OK) {
+      pairs = pairs0;
+      return st;
+    }
     set_shape(bestP, bestPairs);
     return GMRES_OK;
   }
 
   // FP64 tile pairs with fixed-point block-dot and MAXPY products
   bool fx_active() const { return fx && pairs && !ir(); }
+  // the step kernel's fixed-point mode: 0 none, 1 direct basis loads, 2 the column ring
+  int fx_mode() const { return !fx_active() ? 0 : (ring_ok && !no_ring) ? 2 : 1; }
 
   void set_shape(int ctas, bool pr) {
     P = ctas;
@@ -1526,8 +1569,9 @@ gmres_status gmres_batch_set_rows_per_thread(gmres_batch b, int rows) {
 gmres_status gmres_batch_set_block_dot(gmres_batch b, int fixed_point, int* active) {
   if (!b) return GMRES_ERR_ARG;
   b->eng.fx = fixed_point != 0;
+  b->eng.no_ring = fixed_point < 0;
   b->eng.drop_graphs();
-  if (active) *active = b->eng.fx_active() ? 1 : 0;
+  if (active) *active = b->eng.fx_mode();
   return GMRES_OK;
 }
 

@@ -79,6 +79,9 @@ struct Small {
   // stored (atomicMax; cleared at each cycle start): the bound of the
   // fixed-point block dot. Unused (may be NULL) elsewhere.
   unsigned int* ecol;
+  // Staging mode 6: 1 assigns tile pairs to CTAs by a fixed stride (results
+  // bitwise reproducible for a given grid), 0 hands them out by a counter.
+  int fixed_order;
   int m;
   int ldh;          // m + 1
   int nvmax;        // 2 (m + 1) + 2
@@ -1054,11 +1057,13 @@ __device__ __forceinline__ double fx_to_double(long long t, int e2) {
 // s_ex holds 2 kWarps words. w may be absent (need_w false: the cycle's tail,
 // which needs only V^T u); then wr0 = wr1 = 0.
 //
-// RING = false (the batched engine, which has no room for the ring): each lane
-// loads its two rows of a slice directly (16-byte loads through the read-only
-// path), and only pair rows in [rlo, rhi) (relative to the pair's first row)
-// take part: a unit that is one tile of a pair, or a system's ragged end.
-template <int MAXC, bool RING = true, typename Hook>
+// S: ring slices per warp (S - 1 slices in flight ahead of use). RING = false
+// (no room for a ring): each lane loads its two rows of a slice directly
+// (16-byte loads through the read-only path), and only pair rows in
+// [rlo, rhi) (relative to the pair's first row) take part: a unit that is one
+// tile of a pair, or a system's ragged end. With the ring, rows past n read as
+// zeros and a caller masks rows below n by passing zero u and w there.
+template <int MAXC, bool RING = true, int S = pf_stages<double>(), typename Hook>
 __device__ __forceinline__ void tile_pair_dot_rows_fx(int64_t pp, int64_t n,
                                                       const double* __restrict__ V, int64_t ldv, bool need_w, int J8,
                                                       int r8, double ur0, double wr0, double ur1, double wr1,
@@ -1067,7 +1072,7 @@ __device__ __forceinline__ void tile_pair_dot_rows_fx(int64_t pp, int64_t n,
                                                       double (&acc_c)[MAXC], double (&rem_a)[2],
                                                       double (&rem_c)[2], double& sig, double& dd, uint32_t* s_ex,
                                                       Hook hook, int rlo = 0, int rhi = 2 * kThreads) {
-  constexpr int S = pf_stages<double>();  // ring slices per warp
+  static_assert(S >= 2, "the ring needs a slice in flight beside the one in use");
   constexpr int R = 2;                    // rows per 16-byte copy
   constexpr int NQ = kRowsPerLane / R;    // copies per lane per slice
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;

@@ -9,16 +9,19 @@
 
 namespace lsg_engine {
 // Host stub of the engine step kernel for restart length m, with or without
-// tile pairs, with or without fixed-point block-dot products (FP64 tile pairs
-// only; ignored otherwise); callers cast it to their EngStepKernel type.
-const void* eng_step_f64(int m, bool pairs, bool fx);
-const void* eng_step_f32(int m, bool pairs, bool fx);
+// tile pairs, with fixed-point block-dot products (FP64 tile pairs only;
+// ignored otherwise: fx = 1 direct basis loads, 2 the column ring) or not
+// (fx = 0); callers cast it to their EngStepKernel type.
+const void* eng_step_f64(int m, bool pairs, int fx);
+const void* eng_step_f32(int m, bool pairs, int fx);
 }  // namespace lsg_engine
 
 namespace {
 
 constexpr int kPairRows = 2 * kThreads;  // arena regions are whole tile pairs
 constexpr int kMaxGridPerSm = 8;         // largest grid of any engine kernel, per SM
+constexpr int kEngRing = 2;              // half-column slices per warp in the step kernel's column ring
+constexpr size_t kEngRingBytes = (size_t)kWarps * kEngRing * kThreads * sizeof(double);
 
 // Where one system lives.
 struct SysDesc {

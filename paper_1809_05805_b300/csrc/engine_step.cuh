@@ -37,14 +37,19 @@ __device__ __noinline__ VT csr_row_plain(const int32_t* __restrict__ rowptr, con
 // step kernel); the epilogue's shared memory follows the staging buffer
 // (cap entries), since a system's epilogue can run while the next unit lands.
 // Each system's rowptr is padded with nnz to whole tile pairs + 8.
-// FP64 cycles on tile pairs (FX): the block dot's products as exact
-// fixed-point integers on the integer pipes (tile_pair_dot_rows_fx without the
-// column ring, the system's basis exponent bounds from its Small::ecol), as
-// the single-system solver's staging mode 6; a unit that is one tile of a pair
-// runs as that pair with the other tile's rows masked.
-template <int MAXC, bool PAIRS, typename VT, bool FX>
+// FP64 cycles on tile pairs with FXM > 0: the block dot's products as exact
+// fixed-point integers on the integer pipes (tile_pair_dot_rows_fx, the
+// system's basis exponent bounds from its Small::ecol), as the single-system
+// solver's staging mode 6; a unit that is one tile of a pair runs as that pair
+// with the other tile's rows masked. FXM = 1 loads the basis directly;
+// FXM = 2 streams it through a per-warp ring of kEngRing half-column slices
+// filled by cp.async, placed over the epilogue's shared memory (the epilogue
+// runs between units, the ring only inside a unit's block dot, which waits
+// for all of its copies before it returns).
+template <int MAXC, bool PAIRS, typename VT, int FXM>
 __global__ void __launch_bounds__(kThreads, sizeof(VT) == 4 ? 3 : 2)
 ke_step(const VT* __restrict__ V, int64_t ldv, VT* __restrict__ w, EngDev e, int j, int cap) {
+  constexpr bool FX = FXM > 0;
   static_assert(!FX || (PAIRS && std::is_same<VT, double>::value), "fixed-point products need FP64 tile pairs");
   __shared__ __align__(16) VT su[PAIRS ? 2 * kThreads : kThreads];
   __shared__ __align__(16) VT sw[PAIRS ? 2 * kThreads : kThreads];
@@ -234,12 +239,15 @@ ke_step(const VT* __restrict__ V, int64_t ldv, VT* __restrict__ w, EngDev e, int
         const bool second = !pair && (t & 1);
         const int rlo = (int)(max(s_d.row0, second ? pb + kThreads : pb) - pb);
         const int rhi = (int)(min(lim, pair || second ? pb + 2 * kThreads : pb + kThreads) - pb);
+        double* ring = FXM == 2 ? reinterpret_cast<double*>(reinterpret_cast<char*>(dyn) + epi_off) : nullptr;
         if (second)
-          tile_pair_dot_rows_fx<MAXC, false>(t >> 1, lim, V, ldv, !tail, J8, r8, 0.0, 0.0, ur0, wr0, su, sw, nullptr,
-                                              kf, kfr, acc_a, acc_c, fr_a, fr_c, sig, dd, s_ex, next, rlo, rhi);
+          tile_pair_dot_rows_fx<MAXC, FXM == 2, kEngRing>(t >> 1, lim, V, ldv, !tail, J8, r8, 0.0, 0.0, ur0, wr0, su,
+                                                          sw, ring, kf, kfr, acc_a, acc_c, fr_a, fr_c, sig, dd, s_ex,
+                                                          next, rlo, rhi);
         else
-          tile_pair_dot_rows_fx<MAXC, false>(t >> 1, lim, V, ldv, !tail, J8, r8, ur0, wr0, ur1, wr1, su, sw, nullptr,
-                                              kf, kfr, acc_a, acc_c, fr_a, fr_c, sig, dd, s_ex, next, rlo, rhi);
+          tile_pair_dot_rows_fx<MAXC, FXM == 2, kEngRing>(t >> 1, lim, V, ldv, !tail, J8, r8, ur0, wr0, ur1, wr1, su,
+                                                          sw, ring, kf, kfr, acc_a, acc_c, fr_a, fr_c, sig, dd, s_ex,
+                                                          next, rlo, rhi);
       } else if (pair)
         tile_pair_dot_rows<MAXC, VT, VT>(t >> 1, lim, V, ldv, !tail, J8, r8, ur0, wr0, ur1, wr1, su, sw, acc_a, acc_c,
                                          rem_a, rem_c, sig, dd, next);
@@ -254,7 +262,7 @@ ke_step(const VT* __restrict__ V, int64_t ldv, VT* __restrict__ w, EngDev e, int
   }
 }
 
-template <bool PAIRS, typename VT, bool FX>
+template <bool PAIRS, typename VT, int FX>
 EngStepKernel<VT> eng_step_sel(int m) {
   switch (std::max(1, m / kWarps)) {
     case 1: return ke_step<1, PAIRS, VT, FX>;
@@ -271,12 +279,15 @@ EngStepKernel<VT> eng_step_sel(int m) {
 }
 
 // The step kernel for restart length m, one or two rows per thread, and (FP64
-// tile pairs only) fixed-point block-dot products.
+// tile pairs only) fixed-point block-dot products: fx = 1 direct basis loads,
+// fx = 2 the column ring.
 template <typename VT>
-EngStepKernel<VT> eng_step_table(int m, bool pairs, bool fx) {
-  if constexpr (std::is_same<VT, double>::value)
-    if (pairs && fx) return eng_step_sel<true, VT, true>(m);
-  return pairs ? eng_step_sel<true, VT, false>(m) : eng_step_sel<false, VT, false>(m);
+EngStepKernel<VT> eng_step_table(int m, bool pairs, int fx) {
+  if constexpr (std::is_same<VT, double>::value) {
+    if (pairs && fx == 1) return eng_step_sel<true, VT, 1>(m);
+    if (pairs && fx == 2) return eng_step_sel<true, VT, 2>(m);
+  }
+  return pairs ? eng_step_sel<true, VT, 0>(m) : eng_step_sel<false, VT, 0>(m);
 }
 
 }  // namespace

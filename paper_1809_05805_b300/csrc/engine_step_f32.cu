@@ -2,7 +2,7 @@
 #include "engine_step.cuh"
 
 namespace lsg_engine {
-const void* eng_step_f32(int m, bool pairs, bool fx) {
+const void* eng_step_f32(int m, bool pairs, int fx) {
   return reinterpret_cast<const void*>(eng_step_table<float>(m, pairs, fx));
 }
 }  // namespace lsg_engine

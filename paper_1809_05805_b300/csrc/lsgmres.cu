@@ -1906,6 +1906,16 @@ gmres_status gmres_set_block_dot(gmres_handle h, int fixed_point, int* active) {
   return GMRES_OK;
 }
 
+gmres_status gmres_set_reproducible(gmres_handle h, int on) {
+  if (!h) return GMRES_ERR_ARG;
+  const int v = on ? 1 : 0;
+  if (h->s.fixed_order != v) {
+    destroy_graphs(h);  // captured cycles hold the kernels' Small by value
+    h->s.fixed_order = v;
+  }
+  return GMRES_OK;
+}
+
 gmres_status gmres_test_stall_staging(gmres_handle h, int on, int* staged) {
   if (!h) return GMRES_ERR_ARG;
   h->stall_test = on ? 1 : 0;

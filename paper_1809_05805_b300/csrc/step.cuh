@@ -204,14 +204,15 @@ k_one_reduce_step(const int32_t* __restrict__ rowptr, const int32_t* __restrict_
       }
       int par = 0;
       for (; unit < units; par ^= 1) {
-        // The next unit: fixed stride, or (STAGE 6) the next one not yet taken,
-        // from a counter (CTAs that run faster take more units, so the launch
-        // does not wait for the slowest one's last units); the counter is
-        // reset by the CTA that completes the grid reduction.
+        // The next unit: fixed stride, or (STAGE 6 unless s.fixed_order) the
+        // next one not yet taken, from a counter (CTAs that run faster take
+        // more units, so the launch does not wait for the slowest one's last
+        // units; which CTA sums which unit then varies from run to run); the
+        // counter is reset by the CTA that completes the grid reduction.
         int64_t nx = unit + gridDim.x;
         if constexpr (STAGE == 6) {
           if (threadIdx.x == 0) {
-            nx = (int64_t)gridDim.x + (int64_t)atomicAdd(&st->unit_ctr, 1u);
+            if (!s.fixed_order) nx = (int64_t)gridDim.x + (int64_t)atomicAdd(&st->unit_ctr, 1u);
             s_nx[par] = nx;
           }
         }

@@ -88,7 +88,7 @@ class SolveInfo:
 
 EXPORTS = ["gmres_create", "gmres_set", "gmres_set_tol", "gmres_set_stream", "gmres_solve",
            "gmres_solve_host", "gmres_history", "gmres_destroy", "gmres_last_error", "lsg_spmv",
-           "lsg_block_dot", "lsg_maxpy", "gmres_arnoldi", "gmres_set_profile", "gmres_profile", "gmres_test_stall_staging", "gmres_set_block_dot", "gmres_set_persistent",
+           "lsg_block_dot", "lsg_maxpy", "gmres_arnoldi", "gmres_set_profile", "gmres_profile", "gmres_test_stall_staging", "gmres_set_block_dot", "gmres_set_reproducible", "gmres_set_persistent",
            "gmres_test_stall_barrier",
            "lsg_block_dot_noalloc", "gmres_batch_create", "gmres_batch_set_grid", "gmres_batch_get_grid",
            "gmres_batch_set_rows_per_thread", "gmres_batch_get_rows_per_thread", "gmres_batch_set_block_dot",
@@ -132,6 +132,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "gmres_set_profile": ([P, I], I),
         "gmres_test_stall_staging": ([P, I, ctypes.POINTER(I)], I),
         "gmres_set_block_dot": ([P, I, ctypes.POINTER(I)], I),
+        "gmres_set_reproducible": ([P, I], I),
         "gmres_set_persistent": ([P, I, ctypes.POINTER(I)], I),
         "gmres_test_stall_barrier": ([P, I], I),
         "lsg_block_dot_noalloc": ([P, P, P, I64, P, I64, I, P, P, I, P, P], I),
@@ -297,6 +298,11 @@ class Solver:
         self._check(self.lib.gmres_set_block_dot(self.h, int(fixed_point), ctypes.byref(active)))
         return bool(active.value)
 
+    def set_reproducible(self, on: bool):
+        """gmres_set_reproducible: tile pairs of the fixed-point step kernel by a
+        fixed stride (bitwise reproducible results) instead of from a counter."""
+        self._check(self.lib.gmres_set_reproducible(self.h, int(bool(on))))
+
     def set_persistent(self, mode: int) -> bool:
         """gmres_set_persistent: one launch per restart cycle (1), per-step
         launches (0) or automatic (-1, the default); returns whether the next
@@ -420,13 +426,15 @@ class BatchSolver:
     def set_rows_per_thread(self, rows: int):
         self._check(self.lib.gmres_batch_set_rows_per_thread(self.h, int(rows)))
 
-    def set_block_dot(self, fixed_point: bool) -> bool:
+    def set_block_dot(self, fixed_point) -> int:
         """gmres_batch_set_block_dot: fixed-point block-dot and MAXPY products
-        (True, the default) or FP64 FMAs; returns whether the next solve uses
-        the fixed-point form (FP64 batches with two rows per thread)."""
+        (True / 1, the default; -1: without the column ring) or FP64 FMAs
+        (False / 0); returns the form the next solve uses: 0 FP64 FMAs, 1 fixed
+        point with direct basis loads, 2 fixed point with the column ring
+        (FP64 batches with two rows per thread)."""
         active = ctypes.c_int(0)
         self._check(self.lib.gmres_batch_set_block_dot(self.h, int(fixed_point), ctypes.byref(active)))
-        return bool(active.value)
+        return active.value
 
     def solve(self, bs, xs, *, allow=(OK, MAXITER)) -> list[SolveInfo]:
         """bs, xs: lists of float64 CUDA tensors (xs hold x0 on entry, solutions on exit)."""

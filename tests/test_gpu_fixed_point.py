@@ -197,12 +197,14 @@ def _batch_systems(count, seed, side):
     return mats, rhs
 
 
-@pytest.mark.parametrize("fixed_point", [True, False])
+@pytest.mark.parametrize("fixed_point,form", [(1, 2), (-1, 1), (0, 0)])
 @pytest.mark.parametrize("grid", [None, 5, "tiles"])
-def test_batch_matches_oracle(torch_cuda, lsg, orc, fixed_point, grid):
-    """Batched FP64 solves with two rows per thread, with either form of the
-    block-dot and MAXPY products (gmres_batch_set_block_dot), each system held
-    to the single-solve bar against the oracle. Two systems are rescaled (the
+def test_batch_matches_oracle(torch_cuda, lsg, orc, fixed_point, form, grid):
+    """Batched FP64 solves with two rows per thread, with each form of the
+    block-dot and MAXPY products (gmres_batch_set_block_dot: fixed point with
+    the basis streamed through the column ring, which these 9-point systems'
+    tile-pair CSR leaves room for; fixed point with direct basis loads; FP64
+    FMAs), each system held to the single-solve bar against the oracle. Two systems are rescaled (the
     matrix by 2^-200 and the right-hand side by 2^300, and the right-hand side
     by 2^-400) so that their stored exponent bounds sit far from 1 and from
     each other's. grid = 'tiles' gives one tile per CTA: every unit is a single
@@ -219,7 +221,7 @@ def test_batch_matches_oracle(torch_cuda, lsg, orc, fixed_point, grid):
     if grid is not None:
         bs.set_grid(ntiles if grid == "tiles" else grid)
     bs.set_rows_per_thread(2)
-    assert bs.set_block_dot(fixed_point) == fixed_point
+    assert bs.set_block_dot(fixed_point) == form
     bd = [torch.from_numpy(b).cuda() for b in rhs]
     xd = [torch.zeros(len(b), dtype=torch.float64, device="cuda") for b in rhs]
     infos = bs.solve(bd, xd)
@@ -233,8 +235,8 @@ def test_batch_matches_oracle(torch_cuda, lsg, orc, fixed_point, grid):
         assert np.all(np.abs(hist[:k] - r.history[:k]) <= 1e-8 * r.history[:k] + 1e-15 * r.history[0])
         x = xd[i].cpu().numpy()
         assert np.linalg.norm(x - r.x) <= 1e-9 * np.linalg.norm(r.x)
-    # switching the form back on the same handle changes rounding only
-    assert bs.set_block_dot(not fixed_point) == (not fixed_point)
+    # switching the form on the same handle changes rounding only
+    assert bs.set_block_dot(0 if fixed_point else 1) == (0 if fixed_point else 2)
     for x in xd:
         x.zero_()
     infos2 = bs.solve(bd, xd)
@@ -249,7 +251,31 @@ def test_batch_fixed_point_off_for_single_rows(torch_cuda, lsg):
     mats, rhs = _batch_systems(3, seed=43, side=(9, 30))
     bs = lsg.BatchSolver(mats, m=10, tol=1e-8, max_iter=500)
     bs.set_rows_per_thread(1)
-    assert not bs.set_block_dot(True)
+    assert bs.set_block_dot(True) == 0
     bs.set_rows_per_thread(2)
-    assert bs.set_block_dot(True)
+    assert bs.set_block_dot(True) == 2
+    assert bs.set_block_dot(-1) == 1
     bs.close()
+
+
+def test_reproducible_fixed_order(torch_cuda, lsg):
+    """gmres_set_reproducible(1): the fixed-point step kernel takes its tile
+    pairs by a fixed stride, so two solves on one handle, and a solve on a
+    second handle whose cycles replay as CUDA graphs, give bitwise identical x
+    and residual histories."""
+    torch = torch_cuda
+    A = P.conv_diff_7pt(72)
+    _, b = P.rhs(A, seed=9)
+    bd = torch.from_numpy(b).cuda()
+    outs = []
+    for stream in (None, None, torch.cuda.Stream()):
+        s = lsg.Solver(A, m=40, tol=1e-9, max_iter=2000, stream=stream)
+        assert s.set_block_dot(True)
+        s.set_reproducible(True)
+        x = torch.zeros(len(b), dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        s.solve(bd, x)
+        outs.append((x.cpu().numpy(), s.history()))
+        s.close()
+    for o in outs[1:]:
+        assert np.array_equal(outs[0][0], o[0]) and np.array_equal(outs[0][1], o[1])
