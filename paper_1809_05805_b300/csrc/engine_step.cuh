@@ -168,14 +168,29 @@ ke_step(const VT* __restrict__ V, int64_t ldv, VT* __restrict__ w, EngDev e, int
     // region starts on a tile pair): tiles t, t + 1 form the pair t / 2
     const bool pair = PAIRS && (t & 1) == 0 && it + 1 < hi && __ldg(e.act_sys + it + 1) == cur;
     const int64_t it_next = it + (pair ? 2 : 1);
-    if (threadIdx.x == 0) {  // the next unit's copies, described ahead of their issue (kept in shared memory)
+    // thread 0: the next unit's copies, described ahead of their issue (kept
+    // in shared memory). A unit of the current system takes its descriptor
+    // from s_d (no loads); the two rowptr bounds are loaded here and first
+    // used when the copies are issued, after this unit's SpMV, which hides
+    // their latency.
+    int nlo_raw = 0, nhi_raw = 0;
+    if (threadIdx.x == 0) {
       s_nc.nrows = 0;
       if (it_next < hi) {
         int64_t t1;
         int sy1;
         bool pr1;
         unit_at(it_next, t1, sy1, pr1);
-        s_nc = copy_of(t1, sy1, pr1);
+        const SysDesc* d = sy1 == cur ? &s_d : e.desc + sy1;
+        StageCopy<VT> c;
+        c.rp = d->rowptr + (t1 * kThreads - d->row0);
+        c.col = d->col;
+        c.val = desc_val<VT>(*d);
+        c.nrows = pr1 ? 2 * kThreads : kThreads;
+        c.lo = c.hi = 0;  // set from nlo_raw, nhi_raw at the issue
+        nlo_raw = __ldg(c.rp);
+        nhi_raw = __ldg(c.rp + c.nrows);
+        s_nc = c;
       }
     }
     bool staged = !s_stage_off;
@@ -195,7 +210,8 @@ ke_step(const VT* __restrict__ V, int64_t ldv, VT* __restrict__ w, EngDev e, int
     // once every thread is past this unit's SpMV, the buffer takes the next unit
     auto next = [&]() {
       if (threadIdx.x == 0 && s_nc.nrows > 0 && !s_stage_off) {
-        cs.issue_at(s_nc.rp, s_nc.col, s_nc.val, s_nc.nrows, s_nc.lo, s_nc.hi);
+        cs.issue_at(s_nc.rp, s_nc.col, s_nc.val, s_nc.nrows, CsrStage<VT>::lo_of(nlo_raw),
+                    CsrStage<VT>::hi_of(nhi_raw));
         pending = true;
       }
     };
