@@ -556,10 +556,11 @@ struct Engine {
   unsigned int* d_ecol = nullptr;  // FP64 cycles: basis exponent bounds, m + 2 per slot
   // listing
   int32_t* d_tiles = nullptr;  // act_tiles (R / 256) | act_sys (R / 256)
-  int32_t* d_act = nullptr;    // act_slots (S) | sys_b0 (S) | sys_nslot (S) | sys_slot0 (S) | n_slots
+  int32_t* d_act = nullptr;    // act_slots (S) | sys_b0 (S) | sys_nslot (S) | sys_slot0 (S) | n_slots | bounds (act_len - 4 S - 1)
   int64_t* d_nact = nullptr;
   double* d_partials = nullptr;
   int64_t tile_cap = 0, slot_cap = 0;
+  size_t act_len = 0;  // entries of d_act / h_act
   // pinned host mirrors
   DevState* h_states = nullptr;
   int32_t* h_tiles = nullptr;
@@ -667,11 +668,12 @@ struct Engine {
     slot_cap = (int64_t)kMaxGridPerSm * nsm + S + 1;
     nvmax = 2 * (m + 1) + 2;
     ETRY(cudaMalloc(&d_tiles, sizeof(int32_t) * 2 * (size_t)tile_cap));
-    ETRY(cudaMalloc(&d_act, sizeof(int32_t) * (4 * (size_t)S + 1)));
+    act_len = 4 * (size_t)S + 1 + (size_t)kMaxGridPerSm * nsm + 2;
+    ETRY(cudaMalloc(&d_act, sizeof(int32_t) * act_len));
     ETRY(cudaMalloc(&d_nact, sizeof(int64_t)));
     ETRY(cudaMalloc(&d_partials, sizeof(double) * (size_t)slot_cap * nvmax));
     ETRY(cudaMallocHost(&h_tiles, sizeof(int32_t) * 2 * (size_t)tile_cap));
-    ETRY(cudaMallocHost(&h_act, sizeof(int32_t) * (4 * (size_t)S + 1)));
+    ETRY(cudaMallocHost(&h_act, sizeof(int32_t) * act_len));
     ETRY(cudaMallocHost(&h_nact, sizeof(int64_t)));
     *h_nact = 0;
     ETRY(cudaMalloc(&d_tickets, sizeof(unsigned int) * S));
@@ -832,6 +834,8 @@ struct Engine {
     d.sys_nslot = d_act + 2 * S;
     d.sys_slot0 = d_act + 3 * S;
     d.n_slots = d_act + 4 * S;
+    d.bounds = d_act + 4 * S + 1;
+    d.nb = P;
     d.partials = d_partials;
     d.tickets = d_tickets;
     d.nvmax = nvmax;
@@ -973,9 +977,37 @@ struct Engine {
       ns[s] = 0;
     }
     const int Pe = (int)std::min<int64_t>(P, Ta);
+    // The reduction grid's ranges, balanced by estimated cost: a tile costs 1,
+    // and a system costs kSysCost more (its switch, publish and, in the CTA
+    // that completes it, its epilogue: measured at 3-4 tiles' time), charged
+    // at its first tile. Boundary c goes where the cumulative cost first
+    // reaches c / Pe of the total, moved one tile on so that it does not split
+    // a tile pair where it can, and kept strictly increasing (every range
+    // non-empty).
+    int32_t* bnd = h_act + 4 * S + 1;
+    {
+      constexpr double kSysCost = 3.5;
+      std::vector<double> cum((size_t)Ta + 1, 0.0);
+      for (int64_t i = 0; i < Ta; ++i)
+        cum[i + 1] = cum[i] + 1.0 + ((i == 0 || as[i] != as[i - 1]) ? kSysCost : 0.0);
+      bnd[0] = Pe;
+      bnd[1] = 0;
+      int64_t prev = 0;
+      for (int c = 1; c < Pe; ++c) {
+        const double target = cum[Ta] * c / Pe;
+        int64_t b = std::lower_bound(cum.begin(), cum.end(), target) - cum.begin();
+        // odd tile with its pair partner just before it in the same system: cut after it instead
+        if (b < Ta && b > 0 && (at[b] & 1) && as[b - 1] == as[b]) ++b;
+        b = std::max<int64_t>(b, prev + 1);
+        b = std::min<int64_t>(b, Ta - (Pe - c));
+        bnd[1 + c] = (int32_t)b;
+        prev = b;
+      }
+      bnd[1 + Pe] = (int32_t)Ta;
+    }
     std::vector<int32_t> b1(S, -1);
     for (int c = 0; c < Pe; ++c) {
-      const int64_t lo = (int64_t)c * Ta / Pe, hi = ((int64_t)c + 1) * Ta / Pe;
+      const int64_t lo = bnd[1 + c], hi = bnd[2 + c];
       for (int64_t it = lo; it < hi; ++it) {
         const int s = as[it];
         b0[s] = std::min(b0[s], c);
@@ -1005,7 +1037,8 @@ struct Engine {
       ETRY(cudaMemcpyAsync(d_tiles, at, sizeof(int32_t) * Ta, cudaMemcpyHostToDevice, stream));
       ETRY(cudaMemcpyAsync(d_tiles + tile_cap, as, sizeof(int32_t) * Ta, cudaMemcpyHostToDevice, stream));
     }
-    ETRY(cudaMemcpyAsync(d_act, h_act, sizeof(int32_t) * (4 * (size_t)S + 1), cudaMemcpyHostToDevice, stream));
+    ETRY(cudaMemcpyAsync(d_act, h_act, sizeof(int32_t) * (4 * (size_t)S + 2 + (size_t)Pe + 1), cudaMemcpyHostToDevice,
+                         stream));
     ETRY(cudaMemcpyAsync(d_nact, h_nact, sizeof(int64_t), cudaMemcpyHostToDevice, stream));
     listed = ls;
     listing_dirty = false;

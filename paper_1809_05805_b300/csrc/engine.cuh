@@ -46,14 +46,29 @@ struct EngDev {
   const int32_t* sys_slot0;  // per slot: its first partial-sum slot
   double* partials;          // one row of nvmax per (CTA, system) pair
   unsigned int* tickets;     // per slot
+  // The reduction grid's ranges of the listing: bounds[0] = Pe (CTAs with a
+  // range), CTA c < Pe takes [bounds[1 + c], bounds[2 + c]); built by the host
+  // with the listing for a grid of nb CTAs.
+  const int32_t* bounds;
+  int nb;
   int nvmax;
 };
 
-// This CTA's range [lo, hi) of the listed tiles when `grid` CTAs share them:
-// the first Pe = min(grid, Ta) CTAs split the list evenly (every range
-// non-empty, so the CTAs touching a system are consecutive); the others get
-// none.
+// This CTA's range [lo, hi) of the listed tiles when `grid` CTAs share them.
+// For the reduction grid (grid == nb) the ranges are the host's (balanced by
+// estimated cost: each tile, plus a fixed charge for each system whose first
+// tile the range holds, for its switch and epilogue); otherwise the first
+// Pe = min(grid, Ta) CTAs split the list evenly. Either way every range is
+// non-empty (so the CTAs touching a system are consecutive) and the other
+// CTAs get none.
 __device__ __forceinline__ bool cta_tile_range(const EngDev& e, int grid, int64_t& lo, int64_t& hi) {
+  if (grid == e.nb) {
+    const int pe = __ldg(e.bounds);
+    if ((int)blockIdx.x >= pe) return false;
+    lo = __ldg(e.bounds + 1 + blockIdx.x);
+    hi = __ldg(e.bounds + 2 + blockIdx.x);
+    return true;
+  }
   const int64_t Ta = *e.n_act;
   const int64_t Pe = Ta < (int64_t)grid ? Ta : (int64_t)grid;
   if ((int64_t)blockIdx.x >= Pe) return false;

@@ -114,9 +114,20 @@ ke_step(const VT* __restrict__ V, int64_t ldv, VT* __restrict__ w, EngDev e, int
   double fr_a[2] = {0.0, 0.0}, fr_c[2] = {0.0, 0.0};  // FX: remainder half-columns
   int kf[MAXC], kfr[2];                               // FX: 5 + the current system's column bounds
   int cur = -1;
+  // Within a system the listing is the system's tiles in order, so the next
+  // unit's tile follows from the current one (t_next) while it is at most the
+  // system's last tile (t_last); the listing is read only where a system starts.
+  int64_t t_next = -1, t_last = -1;
   for (int64_t it = lo; it <= hi;) {
-    const int64_t t = (it < hi) ? __ldg(e.act_tiles + it) : -1;
-    const int snext = (it < hi) ? __ldg(e.act_sys + it) : -1;
+    int64_t t;
+    int snext;
+    if (it < hi && cur >= 0 && t_next <= t_last) {  // CTA-uniform
+      t = t_next;
+      snext = cur;
+    } else {
+      t = (it < hi) ? __ldg(e.act_tiles + it) : -1;
+      snext = (it < hi) ? __ldg(e.act_sys + it) : -1;
+    }
     if (snext != cur) {  // CTA-uniform
       if (snext < 0) {   // end of the range: no copy may still land in the buffer
         if (threadIdx.x == 0 && pending) mbar_wait_bounded(&s_bar, pend_phase);
@@ -144,6 +155,7 @@ ke_step(const VT* __restrict__ V, int64_t ldv, VT* __restrict__ w, EngDev e, int
         s_d = e.desc[cur];
       }
       __syncthreads();
+      t_last = (s_d.row0 + s_d.n - 1) / kThreads;
 #pragma unroll
       for (int c = 0; c < MAXC; ++c) acc_a[c] = acc_c[c] = VT(0);
 #pragma unroll
@@ -166,8 +178,9 @@ ke_step(const VT* __restrict__ V, int64_t ldv, VT* __restrict__ w, EngDev e, int
     const bool tail = s_tail;
     // a system's tiles are consecutive in the list and in the arena (its
     // region starts on a tile pair): tiles t, t + 1 form the pair t / 2
-    const bool pair = PAIRS && (t & 1) == 0 && it + 1 < hi && __ldg(e.act_sys + it + 1) == cur;
+    const bool pair = PAIRS && (t & 1) == 0 && it + 1 < hi && t + 1 <= t_last;
     const int64_t it_next = it + (pair ? 2 : 1);
+    t_next = t + (pair ? 2 : 1);
     // thread 0: the next unit's copies, described ahead of their issue (kept
     // in shared memory). A unit of the current system takes its descriptor
     // from s_d (no loads); the two rowptr bounds are loaded here and first
@@ -180,7 +193,13 @@ ke_step(const VT* __restrict__ V, int64_t ldv, VT* __restrict__ w, EngDev e, int
         int64_t t1;
         int sy1;
         bool pr1;
-        unit_at(it_next, t1, sy1, pr1);
+        if (t_next <= t_last) {  // the current system's next tile: no listing loads
+          t1 = t_next;
+          sy1 = cur;
+          pr1 = PAIRS && (t1 & 1) == 0 && it_next + 1 < hi && t1 + 1 <= t_last;
+        } else {
+          unit_at(it_next, t1, sy1, pr1);
+        }
         const SysDesc* d = sy1 == cur ? &s_d : e.desc + sy1;
         StageCopy<VT> c;
         c.rp = d->rowptr + (t1 * kThreads - d->row0);
