@@ -465,6 +465,11 @@ __device__ int finish_column(Small s, int j, double h, bool last_allowed) {
   __syncthreads();
   if (threadIdx.x == 0) {
     DevState* st = s.st;
+    // every global input first: the stores below may alias them, so a load
+    // placed after a store would wait for it
+    const double gj = __ldcg(&s.g[j]);
+    const double cyc_scale = __ldcg(&st->cycle_scale), inv_bnorm = __ldcg(&st->inv_bnorm), tol = __ldcg(&st->tol);
+    const int it0 = __ldcg(&st->total_iters);
     double hn2 = 0.0;  // ||Hbar(0:j+1, j)||^2 for the breakdown test
     for (int i = 0; i <= j + 1; ++i) hn2 += sh_col[i] * sh_col[i];
     double* R = sh_col;
@@ -486,11 +491,10 @@ __device__ int finish_column(Small s, int j, double h, bool last_allowed) {
     for (int i = 0; i <= j + 1; ++i) Rg[i] = R[i];
     s.cs[j] = c;
     s.sn[j] = sn;
-    const double gj = __ldcg(&s.g[j]);
     s.g[j + 1] = -sn * gj;
     s.g[j] = c * gj;
-    const double est = fabs(sn * gj) * __ldcg(&st->cycle_scale) * __ldcg(&st->inv_bnorm);
-    const int it = __ldcg(&st->total_iters) + j;
+    const double est = fabs(sn * gj) * cyc_scale * inv_bnorm;
+    const int it = it0 + j;
     if (it < s.hist_cap) s.hist[it] = est;
     st->k = j + 1;
     st->est = est;
@@ -501,7 +505,7 @@ __device__ int finish_column(Small s, int j, double h, bool last_allowed) {
     } else if (h <= kBreakdownFactor * kEps * sqrt(hn2)) {
       st->breakdown = 1;
       stop = 1;
-    } else if (est <= __ldcg(&st->tol)) {
+    } else if (est <= tol) {
       st->converged = 1;
       stop = 1;
     } else if (last_allowed) {
@@ -513,14 +517,24 @@ __device__ int finish_column(Small s, int j, double h, bool last_allowed) {
   return s_res;
 }
 
+// What prerotate_column leaves for finish_prerotated (in the caller's shared
+// memory): the column's squared norm so far, rotated entry c, and the scalars
+// the finish reads (fixed for the rest of the cycle), so that the finish
+// itself reads nothing but h from global memory.
+struct PreRot {
+  double hn2, rc, gj, cyc_scale, inv_bnorm, tol;
+  int it0;
+};
+
 // finish_column in two parts, for a caller that knows column c's first c+1
 // entries one step before its last one (the one-launch cycle): prerotate_column
 // applies the stored rotations 0 .. c-1 to H(0:c, c) and keeps the result in
-// Rg(:, c) (rows 0 .. c, row c not yet final) and the column's squared norm
-// in *hn2_out; finish_prerotated then forms rotation c from Rg(c, c) and
-// h = H(c+1, c), as finish_column does, with the same operations in the same
-// order (bitwise the same results). Thread 0 works; the whole CTA calls both.
-__device__ void prerotate_column(Small s, int c, double* hn2_out) {
+// Rg(:, c) (rows 0 .. c, row c not yet final), and the column's squared norm
+// and rotated entry c in *pr; finish_prerotated then forms rotation c from
+// that entry and h = H(c+1, c), as finish_column does, with the same
+// operations in the same order (bitwise the same results). Thread 0 works; the
+// whole CTA calls both.
+__device__ void prerotate_column(Small s, int c, PreRot* pr) {
   __shared__ double sh_col[kMaxM + 2], sh_c[kMaxM + 1], sh_s[kMaxM + 1];
   const int ld = s.ldh;
   for (int i = threadIdx.x; i <= c; i += blockDim.x) sh_col[i] = __ldcg(&s.H[(size_t)c * ld + i]);
@@ -530,9 +544,15 @@ __device__ void prerotate_column(Small s, int c, double* hn2_out) {
   }
   __syncthreads();
   if (threadIdx.x == 0) {
+    DevState* st = s.st;
+    pr->gj = __ldcg(&s.g[c]);  // g(c) is final once rotation c-1 is
+    pr->cyc_scale = __ldcg(&st->cycle_scale);
+    pr->inv_bnorm = __ldcg(&st->inv_bnorm);
+    pr->tol = __ldcg(&st->tol);
+    pr->it0 = __ldcg(&st->total_iters);
     double hn2 = 0.0;
     for (int i = 0; i <= c; ++i) hn2 += sh_col[i] * sh_col[i];
-    *hn2_out = hn2;
+    pr->hn2 = hn2;
     double* R = sh_col;
     for (int i = 0; i < c; ++i) {
       const double cc = sh_c[i], sn = sh_s[i];
@@ -542,21 +562,22 @@ __device__ void prerotate_column(Small s, int c, double* hn2_out) {
     }
     double* Rg = s.Rg + (size_t)c * ld;
     for (int i = 0; i <= c; ++i) Rg[i] = R[i];
+    pr->rc = R[c];
   }
   __syncthreads();
 }
 
-// Rg(c, c) rotated by rotations 0 .. c-1 is in Rg; hn2 = ||H(0:c, c)||^2 (from
-// prerotate_column, the same thread 0); h = H(c+1, c). Returns the stop
-// decision in every thread, as finish_column.
-__device__ int finish_prerotated(Small s, int c, double h, double hn2_partial, bool last_allowed) {
+// *pr from prerotate_column (the same thread 0); h = H(c+1, c). Returns the
+// stop decision in every thread, as finish_column.
+__device__ int finish_prerotated(Small s, int c, double h, const PreRot* pr, bool last_allowed) {
   __shared__ int s_res;
   if (threadIdx.x == 0) {
     DevState* st = s.st;
     const int ld = s.ldh;
     double* Rg = s.Rg + (size_t)c * ld;
-    const double hn2 = hn2_partial + h * h;
-    double R0 = __ldcg(&Rg[c]), R1 = h;
+    const double hn2 = pr->hn2 + h * h;
+    const double gj = pr->gj;
+    double R0 = pr->rc, R1 = h;
     double cc = 1.0, sn = 0.0;
     if (R1 != 0.0) {
       const double irho = 1.0 / hypot(R0, R1);
@@ -567,11 +588,10 @@ __device__ int finish_prerotated(Small s, int c, double h, double hn2_partial, b
     Rg[c + 1] = 0.0;
     s.cs[c] = cc;
     s.sn[c] = sn;
-    const double gj = __ldcg(&s.g[c]);
     s.g[c + 1] = -sn * gj;
     s.g[c] = cc * gj;
-    const double est = fabs(sn * gj) * __ldcg(&st->cycle_scale) * __ldcg(&st->inv_bnorm);
-    const int it = __ldcg(&st->total_iters) + c;
+    const double est = fabs(sn * gj) * pr->cyc_scale * pr->inv_bnorm;
+    const int it = pr->it0 + c;
     if (it < s.hist_cap) s.hist[it] = est;
     st->k = c + 1;
     st->est = est;
@@ -582,7 +602,7 @@ __device__ int finish_prerotated(Small s, int c, double h, double hn2_partial, b
     } else if (h <= kBreakdownFactor * kEps * sqrt(hn2)) {
       st->breakdown = 1;
       stop = 1;
-    } else if (est <= __ldcg(&st->tol)) {
+    } else if (est <= pr->tol) {
       st->converged = 1;
       stop = 1;
     } else if (last_allowed) {

@@ -674,7 +674,7 @@ k_cycle_persistent(const int32_t* __restrict__ rowptr, const int32_t* __restrict
   __shared__ double sw[kThreads];
   __shared__ double red[2 * (kMaxM + 1) + 2];
   __shared__ double scf[kMaxM + 3];
-  __shared__ double s_hn2;
+  __shared__ PreRot s_pr;
   __shared__ int s_j, s_tail, s_done, s_K, s_out, s_pipe2;
   DevState* st = s.st;
   const unsigned int P = gridDim.x;
@@ -695,7 +695,7 @@ k_cycle_persistent(const int32_t* __restrict__ rowptr, const int32_t* __restrict
     const double* u = V + (size_t)j * ldv;
     // ---- phase A ----
     if (givens) {
-      if (j >= 1 && !tail && !s_pipe2) prerotate_column(s, j - 1, &s_hn2);
+      if (j >= 1 && !tail && !s_pipe2) prerotate_column(s, j - 1, &s_pr);
     } else {
       const int J8 = j / kWarps, r8 = j % kWarps;
       double acc_a[MAXC], acc_c[MAXC], rem_a[kWarps - 1], rem_c[kWarps - 1];
@@ -734,7 +734,7 @@ k_cycle_persistent(const int32_t* __restrict__ rowptr, const int32_t* __restrict
       if (j >= 1) {
         const double h = __ldcg(&s.H[(size_t)(j - 1) * s.ldh + j]);
         const int stop = s_pipe2 ? finish_completed(s, j - 1, h, false)
-                                 : finish_prerotated(s, j - 1, h, s_hn2, false);
+                                 : finish_prerotated(s, j - 1, h, &s_pr, false);
         if (threadIdx.x == 0) {
           atomicAdd(reinterpret_cast<unsigned long long*>(&st->grid_syncs), 1ull);
           if (stop) st->done = 1;
