@@ -1229,8 +1229,12 @@ __device__ __forceinline__ void tile_pair_dot_rows_fx(int64_t pp, int64_t n,
       flush(kfr[q], ah, am, ch, cm, rem_a[q], rem_c[q]);
     }
   }
+  // No closing barrier: each thread's ring copies are complete here; the
+  // limbs in su, sw and the bounds in s_ex are next written after the next
+  // pair's first barrier, which no warp passes before every warp has left
+  // this pair's column loop; a caller's own shared state after the call is
+  // ordered by its own barriers.
   if constexpr (RING) cp_async_wait<0>();
-  __syncthreads();
 }
 
 // The CTA's partial sums of the fixed-point block dot (tile_pair_dot_rows_fx):
