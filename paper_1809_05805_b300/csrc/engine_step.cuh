@@ -118,6 +118,11 @@ ke_step(const VT* __restrict__ V, int64_t ldv, VT* __restrict__ w, EngDev e, int
   // unit's tile follows from the current one (t_next) while it is at most the
   // system's last tile (t_last); the listing is read only where a system starts.
   int64_t t_next = -1, t_last = -1;
+  // the current system's CSR (registers: the next unit's description reads no memory)
+  const int32_t* cur_rp = nullptr;
+  const int32_t* cur_col = nullptr;
+  const VT* cur_val = nullptr;
+  int64_t cur_row0 = 0;
   for (int64_t it = lo; it <= hi;) {
     int64_t t;
     int snext;
@@ -156,6 +161,10 @@ ke_step(const VT* __restrict__ V, int64_t ldv, VT* __restrict__ w, EngDev e, int
       }
       __syncthreads();
       t_last = (s_d.row0 + s_d.n - 1) / kThreads;
+      cur_rp = s_d.rowptr;
+      cur_col = s_d.col;
+      cur_val = desc_val<VT>(s_d);
+      cur_row0 = s_d.row0;
 #pragma unroll
       for (int c = 0; c < MAXC; ++c) acc_a[c] = acc_c[c] = VT(0);
 #pragma unroll
@@ -189,18 +198,22 @@ ke_step(const VT* __restrict__ V, int64_t ldv, VT* __restrict__ w, EngDev e, int
     int nlo_raw = 0, nhi_raw = 0;
     if (threadIdx.x == 0) {
       s_nc.nrows = 0;
-      if (it_next < hi) {
+      if (it_next < hi && t_next <= t_last) {  // the current system's next tile
+        const int nr = (PAIRS && (t_next & 1) == 0 && it_next + 1 < hi && t_next + 1 <= t_last) ? 2 * kThreads
+                                                                                               : kThreads;
+        const int32_t* rp = cur_rp + (t_next * kThreads - cur_row0);
+        nlo_raw = __ldg(rp);
+        nhi_raw = __ldg(rp + nr);
+        s_nc.rp = rp;
+        s_nc.col = cur_col;
+        s_nc.val = cur_val;
+        s_nc.nrows = nr;
+      } else if (it_next < hi) {  // the first tile of the next system
         int64_t t1;
         int sy1;
         bool pr1;
-        if (t_next <= t_last) {  // the current system's next tile: no listing loads
-          t1 = t_next;
-          sy1 = cur;
-          pr1 = PAIRS && (t1 & 1) == 0 && it_next + 1 < hi && t1 + 1 <= t_last;
-        } else {
-          unit_at(it_next, t1, sy1, pr1);
-        }
-        const SysDesc* d = sy1 == cur ? &s_d : e.desc + sy1;
+        unit_at(it_next, t1, sy1, pr1);
+        const SysDesc* d = e.desc + sy1;
         StageCopy<VT> c;
         c.rp = d->rowptr + (t1 * kThreads - d->row0);
         c.col = d->col;
