@@ -162,9 +162,10 @@ k_maxpy(const VT* __restrict__ V, int64_t ldv, const YT* y_in, YT* y_out, int64_
     scc[i] = (CT)sc[i];
   }
   __syncthreads();
-  if (mode == MAXPY_ARNOLDI && blockIdx.x == gridDim.x - 1) {
-    // The last CTA of an Arnoldi MAXPY finishes column j-1 of H (Givens,
-    // residual estimate, stop decision) while the other CTAs stream.
+  if (mode == MAXPY_ARNOLDI && blockIdx.x == 0) {
+    // The first CTA of an Arnoldi MAXPY finishes column j-1 of H (Givens,
+    // residual estimate, stop decision) while the other CTAs stream (first,
+    // so that it starts with them rather than after the first wave).
     const int j = __ldcg(&st->step) - 1;
     if (j >= 1) {
       const double h = __ldcg(&s.H[(size_t)(j - 1) * s.ldh + j]);
@@ -177,6 +178,7 @@ k_maxpy(const VT* __restrict__ V, int64_t ldv, const YT* y_in, YT* y_out, int64_
     return;
   }
   const int ndata = gridDim.x - (mode == MAXPY_ARNOLDI ? 1 : 0);  // CTAs that stream
+  const int bdata = (int)blockIdx.x - (mode == MAXPY_ARNOLDI ? 1 : 0);  // this CTA among them
   YT* out = s_out;
   // FP64 basis column written: its exponent bound for the fixed-point block dot
   constexpr bool kNote = std::is_same<VT, double>::value && std::is_same<YT, double>::value;
@@ -184,7 +186,7 @@ k_maxpy(const VT* __restrict__ V, int64_t ldv, const YT* y_in, YT* y_out, int64_
   if (mode == MAXPY_REORTH) y_in = out;  // in place: each element is read, then written, by one thread
   const CT alpha = scc[0];
   const int64_t stride = (int64_t)ndata * blockDim.x;
-  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t gid = (int64_t)bdata * blockDim.x + threadIdx.x;
   int64_t done_rows = 0;
   if constexpr (std::is_same<VT, YT>::value) {
     constexpr int E = 16 / (int)sizeof(VT);
@@ -262,7 +264,7 @@ k_maxpy(const VT* __restrict__ V, int64_t ldv, const YT* y_in, YT* y_out, int64_
 //  * per row, hh = sum Ch Xh and mid = sum (Ch Xl + Cl Xh) in 64-bit integers
 //    (mid folded into hh every 16 columns), Cl Xl (below 2^-56 of the
 //    largest product) dropped.
-// The last CTA finishes column j-1 of H meanwhile, as in k_maxpy.
+// The first CTA finishes column j-1 of H meanwhile, as in k_maxpy.
 __global__ void __launch_bounds__(kThreads, 4)
 k_maxpy_fx(const double* __restrict__ V, int64_t ldv, const double* __restrict__ w, int64_t n, Small s) {
   __shared__ int4 sC[kMaxM + 1];  // (Ch, Cl, 5 + column bound field, 0) per column
@@ -280,8 +282,9 @@ k_maxpy_fx(const double* __restrict__ V, int64_t ldv, const double* __restrict__
   __syncthreads();
   if (s_skip) return;
   const int K = sK;
-  if (blockIdx.x == gridDim.x - 1) {
-    // column j-1 of H: Givens, residual estimate, stop decision
+  if (blockIdx.x == 0) {
+    // column j-1 of H: Givens, residual estimate, stop decision (the first
+    // CTA, so that it starts with the streaming ones)
     const int j = s_colk - 1;
     if (j >= 1) {
       const double h = __ldcg(&s.H[(size_t)(j - 1) * s.ldh + j]);
@@ -330,7 +333,7 @@ k_maxpy_fx(const double* __restrict__ V, int64_t ldv, const double* __restrict__
   double* out = const_cast<double*>(V) + (size_t)s_colk * ldv;
   const int ndata = gridDim.x - 1;
   const int64_t stride = (int64_t)ndata * blockDim.x;
-  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t gid = (int64_t)(blockIdx.x - 1) * blockDim.x + threadIdx.x;
   const int e2 = P - 2044 - cbits;  // sum = (hh + mid / 2^29) 2^(P - 2044 - cbits)
   uint32_t emax = 0;
   const int64_t nE = n / 2;
@@ -396,7 +399,7 @@ k_maxpy_fx(const double* __restrict__ V, int64_t ldv, const double* __restrict__
 // Arnoldi MAXPY of GMRES-IR with BF16 basis storage: u_{j+1} = alpha w +
 // sum_k c_k u_k computed in FP32 (w in FP32, the basis widened from BF16, the
 // coefficients rounded to FP32) and rounded to BF16 (nearest, ties to even)
-// as it is stored; eight BF16 values per 16-byte access. The last CTA
+// as it is stored; eight BF16 values per 16-byte access. The first CTA
 // finishes column j-1 of H as in k_maxpy.
 __global__ void __launch_bounds__(kThreads, 4)
 k_maxpy_bf16(__nv_bfloat16* __restrict__ V, int64_t ldv, const float* __restrict__ w, int64_t n, Small s) {
@@ -413,7 +416,7 @@ k_maxpy_bf16(__nv_bfloat16* __restrict__ V, int64_t ldv, const float* __restrict
   const int K = sK;
   for (int i = threadIdx.x; i <= K; i += blockDim.x) scc[i] = (float)__ldcg(s.coef + i);
   __syncthreads();
-  if (blockIdx.x == gridDim.x - 1) {
+  if (blockIdx.x == 0) {  // column j-1 of H, beside the streaming CTAs
     const int j = s_step - 1;
     if (j >= 1) {
       const double h = __ldcg(&s.H[(size_t)(j - 1) * s.ldh + j]);
@@ -428,7 +431,7 @@ k_maxpy_bf16(__nv_bfloat16* __restrict__ V, int64_t ldv, const float* __restrict
   __nv_bfloat16* out = V + (size_t)s_step * ldv;
   const int ndata = gridDim.x - 1;
   const int64_t stride = (int64_t)ndata * blockDim.x;
-  const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t gid = (int64_t)(blockIdx.x - 1) * blockDim.x + threadIdx.x;
   const float alpha = scc[0];
   const int64_t n8 = n / 8;  // columns start on 16-byte boundaries (ldv is a multiple of 32)
   for (int64_t i = gid; i < n8; i += stride) {
