@@ -851,6 +851,10 @@ def run_batch(args, w, rank, world, dist):
     bd = [torch.from_numpy(b).cuda() for b in rhs]
     xd = [torch.zeros(len(b), dtype=torch.float64, device="cuda") for b in rhs]
     bs.set_profile(False)  # timed without per-launch timing nodes; profiled after
+    if getattr(args, "batch_shape", None):
+        ctas, rows = (int(v) for v in args.batch_shape.split(","))
+        bs.set_grid(ctas)
+        bs.set_rows_per_thread(rows)
     fx = bs.set_block_dot(True)  # the default: fixed-point products on FP64 tile pairs (autotuned rows per thread)
 
     def one_solve():
@@ -1310,6 +1314,9 @@ def main():
                     + sorted(SERVE_WORKLOADS), default="256")
     ap.add_argument("--no-mgs", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch-shape", default=None, metavar="CTAS,ROWS",
+                    help="batch workloads: pin the launch shape (grid CTAs, rows per thread) instead of the "
+                         "autotuner's choice, e.g. to profile the shape a plain run chose")
     ap.add_argument("--no-legs", action="store_true",
                     help="default workload: skip the other configurations measured after the headline")
     args = ap.parse_args()
