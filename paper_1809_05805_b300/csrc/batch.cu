@@ -531,9 +531,10 @@ struct Engine {
   int device = 0, nsm = 0, P = 0, nvmax = 0, hist_cap = 0;
   bool pairs = true;
   bool fx = true;  // FP64 tile pairs: block dot and MAXPY products on the integer pipes
-  // the fixed-point step kernel with its column ring (over the epilogue's
-  // shared memory): its CSR staging capacity and dynamic shared memory, and
-  // whether the listed systems' tile pairs fit that capacity
+  // the step kernel with the column ring over the epilogue's shared memory
+  // (FP64: fixed-point products; FP32: FMA products): its CSR staging
+  // capacity and dynamic shared memory, and whether the listed systems' tile
+  // pairs fit that capacity
   int ring_cap = 0;
   size_t ring_smem = 0;
   bool ring_ok = false;
@@ -764,10 +765,12 @@ struct Engine {
         }
       }
       // the ring variant: the ring shares the epilogue's region (it is live only inside a unit's block dot)
-      if (!ir()) {
-        const void* f = reinterpret_cast<const void*>(eng_step_for<double>(m, true, 2));
+      {
+        const void* f = ir() ? reinterpret_cast<const void*>(eng_step_for<float>(m, true, 3))
+                             : reinterpret_cast<const void*>(eng_step_for<double>(m, true, 2));
+        const size_t ring = ir() ? pf_ring_bytes<float>() : kEngRingBytes;
         for (int cap = 16384; cap >= 256 && ring_cap == 0; cap -= 256) {
-          const size_t need = (size_t)(2 * kThreads + 4) * 4 + (size_t)cap * (4 + vb) + std::max(epi, kEngRingBytes);
+          const size_t need = (size_t)(2 * kThreads + 4) * 4 + (size_t)cap * (4 + vb) + std::max(epi, ring);
           int nb = 0;
           if (raise_smem_limit(f, need) == cudaSuccess &&
               cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, kThreads, need) == cudaSuccess && nb >= per_sm) {
@@ -1145,8 +1148,8 @@ struct Engine {
     for (int j = 0; j <= KM; ++j) {
       int pr = prof_begin(PC_STEP, j);
       if (ir())
-        eng_step_for<float>(cfg.m, pairs, 0)<<<P, kThreads, step_smem, stream>>>(
-            static_cast<const float*>(V), ldv, static_cast<float*>(w), d, j, stage_cap);
+        eng_step_for<float>(cfg.m, pairs, fxm)<<<P, kThreads, fxm == 3 ? ring_smem : step_smem, stream>>>(
+            static_cast<const float*>(V), ldv, static_cast<float*>(w), d, j, fxm == 3 ? ring_cap : stage_cap);
       else
         eng_step_for<double>(cfg.m, pairs, fxm)<<<P, kThreads, fxm == 2 ? ring_smem : step_smem, stream>>>(
             static_cast<const double*>(V), ldv, static_cast<double*>(w), d, j, fxm == 2 ? ring_cap : stage_cap);
@@ -1373,8 +1376,11 @@ struct Engine {
           if (e == cudaSuccess) e = cudaEventRecord(e0, stream);
           if (e == cudaSuccess) {
             if (ir()) {
-              eng_step_for<float>(cfg.m, pr == 1, 0)<<<Pc, kThreads, step_smem, stream>>>(
-                  static_cast<const float*>(V), ldv, static_cast<float*>(w), dev(), j, stage_cap);
+              pairs = pr == 1;
+              const int fxm = fx_mode();
+              eng_step_for<float>(cfg.m, pairs, fxm)<<<Pc, kThreads, fxm == 3 ? ring_smem : step_smem, stream>>>(
+                  static_cast<const float*>(V), ldv, static_cast<float*>(w), dev(), j,
+                  fxm == 3 ? ring_cap : stage_cap);
             } else {
               pairs = pr == 1;  // fx_mode() follows the shape being timed
               const int fxm = fx_mode();
@@ -1415,7 +1421,11 @@ struct Engine {
   // FP64 tile pairs with fixed-point block-dot and MAXPY products
   bool fx_active() const { return fx && pairs && !ir(); }
   // the step kernel's fixed-point mode: 0 none, 1 direct basis loads, 2 the column ring
-  int fx_mode() const { return !fx_active() ? 0 : (ring_ok && !no_ring) ? 2 : 1; }
+  // (FP32 cycles: 3 with the column ring, else 0)
+  int fx_mode() const {
+    if (ir()) return (pairs && ring_ok && !no_ring) ? 3 : 0;
+    return !fx_active() ? 0 : (ring_ok && !no_ring) ? 2 : 1;
+  }
 
   void set_shape(int ctas, bool pr) {
     P = ctas;

@@ -37,7 +37,7 @@ __device__ __noinline__ VT csr_row_plain(const int32_t* __restrict__ rowptr, con
 // step kernel); the epilogue's shared memory follows the staging buffer
 // (cap entries), since a system's epilogue can run while the next unit lands.
 // Each system's rowptr is padded with nnz to whole tile pairs + 8.
-// FP64 cycles on tile pairs with FXM > 0: the block dot's products as exact
+// FP64 cycles on tile pairs with FXM = 1 or 2: the block dot's products as exact
 // fixed-point integers on the integer pipes (tile_pair_dot_rows_fx, the
 // system's basis exponent bounds from its Small::ecol), as the single-system
 // solver's staging mode 6; a unit that is one tile of a pair runs as that pair
@@ -45,12 +45,16 @@ __device__ __noinline__ VT csr_row_plain(const int32_t* __restrict__ rowptr, con
 // FXM = 2 streams it through a per-warp ring of kEngRing half-column slices
 // filled by cp.async, placed over the epilogue's shared memory (the epilogue
 // runs between units, the ring only inside a unit's block dot, which waits
-// for all of its copies before it returns).
+// for all of its copies before it returns). FP32 cycles on tile pairs with
+// FXM = 3: FMA products with the basis through the single-system kernels'
+// column ring (tile_pair_dot_rows_pf, pf_stages<float>() column slices per
+// warp), laid over the epilogue's shared memory in the same way.
 template <int MAXC, bool PAIRS, typename VT, int FXM>
 __global__ void __launch_bounds__(kThreads, sizeof(VT) == 4 ? 3 : 2)
 ke_step(const VT* __restrict__ V, int64_t ldv, VT* __restrict__ w, EngDev e, int j, int cap) {
-  constexpr bool FX = FXM > 0;
+  constexpr bool FX = FXM == 1 || FXM == 2;
   static_assert(!FX || (PAIRS && std::is_same<VT, double>::value), "fixed-point products need FP64 tile pairs");
+  static_assert(FXM != 3 || (PAIRS && std::is_same<VT, float>::value), "the FP32 ring variant is for FP32 tile pairs");
   __shared__ __align__(16) VT su[PAIRS ? 2 * kThreads : kThreads];
   __shared__ __align__(16) VT sw[PAIRS ? 2 * kThreads : kThreads];
   __shared__ uint32_t s_ex[2 * kWarps];
@@ -296,6 +300,17 @@ ke_step(const VT* __restrict__ V, int64_t ldv, VT* __restrict__ w, EngDev e, int
           tile_pair_dot_rows_fx<MAXC, FXM == 2, kEngRing>(t >> 1, lim, V, ldv, !tail, J8, r8, ur0, wr0, ur1, wr1, su,
                                                           sw, ring, kf, kfr, acc_a, acc_c, fr_a, fr_c, sig, dd, s_ex,
                                                           next, rlo, rhi);
+      } else if constexpr (FXM == 3) {
+        // FP32 tile pairs with the basis through the per-warp cp.async ring
+        // (over the epilogue's shared memory); a single tile runs as its pair
+        // with the absent tile's u and w zero
+        VT* ring = reinterpret_cast<VT*>(reinterpret_cast<char*>(dyn) + epi_off);
+        if (!pair && (t & 1))
+          tile_pair_dot_rows_pf<MAXC, VT, VT>(t >> 1, lim, V, ldv, !tail, J8, r8, VT(0), VT(0), ur0, wr0, su, sw,
+                                              ring, acc_a, acc_c, rem_a, rem_c, sig, dd, next);
+        else
+          tile_pair_dot_rows_pf<MAXC, VT, VT>(t >> 1, lim, V, ldv, !tail, J8, r8, ur0, wr0, ur1, wr1, su, sw, ring,
+                                              acc_a, acc_c, rem_a, rem_c, sig, dd, next);
       } else if (pair)
         tile_pair_dot_rows<MAXC, VT, VT>(t >> 1, lim, V, ldv, !tail, J8, r8, ur0, wr0, ur1, wr1, su, sw, acc_a, acc_c,
                                          rem_a, rem_c, sig, dd, next);
@@ -328,12 +343,14 @@ EngStepKernel<VT> eng_step_sel(int m) {
 
 // The step kernel for restart length m, one or two rows per thread, and (FP64
 // tile pairs only) fixed-point block-dot products: fx = 1 direct basis loads,
-// fx = 2 the column ring.
+// fx = 2 the column ring; (FP32 tile pairs only) fx = 3 the column ring.
 template <typename VT>
 EngStepKernel<VT> eng_step_table(int m, bool pairs, int fx) {
   if constexpr (std::is_same<VT, double>::value) {
     if (pairs && fx == 1) return eng_step_sel<true, VT, 1>(m);
     if (pairs && fx == 2) return eng_step_sel<true, VT, 2>(m);
+  } else {
+    if (pairs && fx == 3) return eng_step_sel<true, VT, 3>(m);
   }
   return pairs ? eng_step_sel<true, VT, 0>(m) : eng_step_sel<false, VT, 0>(m);
 }
