@@ -625,6 +625,39 @@ __device__ bool grid_barrier(unsigned int* bar, unsigned int nblocks, unsigned i
   return s_ok != 0;
 }
 
+// The one-launch cycle's wait for a step's epilogue: bar[2] counts the
+// epilogues published in this launch; every CTA waits until it reaches
+// `epoch` (bounded as grid_barrier's waits). The CTA that ran the epilogue has
+// made its writes visible (__threadfence) before raising the count, so after
+// the wait its coefficients and state may be read through L2. This replaces a
+// grid barrier: every CTA's arrival is already implied by the grid reduction
+// that elected the epilogue's CTA.
+__device__ bool wait_epilogue(unsigned int* bar, unsigned int epoch, DevState* st) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned int* vf = bar + 2;
+    int ok = 1;
+    const long long t0 = clock64();
+    while (*vf < epoch) {
+      if (*reinterpret_cast<volatile int*>(&st->stalled)) {
+        ok = 0;
+        break;
+      }
+      if (clock64() - t0 > (1ll << 31)) {
+        atomicExch(&st->stalled, 1);
+        ok = 0;
+        break;
+      }
+      __nanosleep(32);
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
 // Basis reads of the one-launch cycle go through L2 (__ldcg): the columns are
 // written during the launch by other CTAs, so neither the read-only path nor
 // a possibly stale L1 line may serve them.
@@ -658,14 +691,15 @@ __device__ __forceinline__ double csr_row_cg(const int32_t* __restrict__ rowptr,
 //            coefficients). Meanwhile the Givens CTA applies the stored
 //            rotations to column j-1, whose first j entries the previous
 //            step's epilogue wrote (the lagged H(j, j-1) is still to come);
-//   barrier 1;
+//   wait for the epilogue (wait_epilogue: a count the epilogue's CTA raises;
+//            every CTA's arrival is implied by the grid reduction);
 //   phase B: the work CTAs run the MAXPY over their rows; the Givens CTA forms
 //            rotation j-1 from the new H(j, j-1) and takes the convergence
 //            decision (in the L = 2 pipeline: the rotations of Algorithm 8's
 //            column pairs, as the per-step launches do);
 //   barrier 2 (the next SpMV reads the new column everywhere).
-// Two grid-wide synchronizations per step, as with two launches per step, but
-// without a kernel boundary, and with the Givens chain off the critical path.
+// One grid reduction and one grid barrier per step (two launches per step
+// would synchronize twice), and the Givens chain off the critical path.
 // Needs a cooperative launch (every CTA resident) and (m+1)^2 + (m+1) doubles
 // of dynamic shared memory for the epilogue.
 template <int MAXC>
@@ -685,6 +719,7 @@ k_cycle_persistent(const int32_t* __restrict__ rowptr, const int32_t* __restrict
   const bool givens = (int)blockIdx.x == Pw;
   const int64_t ntiles = (n + kThreads - 1) / kThreads;
   if (threadIdx.x == 0) s_pipe2 = __ldcg(&st->pipe2);
+  unsigned int epoch = 0;  // steps of this launch whose epilogue has been waited for
   for (;;) {
     if (threadIdx.x == 0) {
       s_done = __ldcg(&st->done) | __ldcg(&st->stalled);
@@ -722,9 +757,17 @@ k_cycle_persistent(const int32_t* __restrict__ rowptr, const int32_t* __restrict
                                                  NoHook{});
       }
       cta_partials<MAXC, double>(acc_a, acc_c, rem_a, rem_c, sig, dd, j, J8, r8, red);
-      if (grid_reduce_last(s, red, 2 * j + 2, Pw)) epilogue_one_reduce(s, red, j, tail);
+      if (grid_reduce_last(s, red, 2 * j + 2, Pw)) {
+        epilogue_one_reduce(s, red, j, tail);
+        __syncthreads();  // every thread's epilogue writes are issued
+        if (threadIdx.x == 0) {
+          __threadfence();
+          atomicAdd(bar + 2, 1u);
+        }
+      }
     }
-    if (!grid_barrier(bar, P, bar_extra, st)) return;
+    ++epoch;
+    if (!wait_epilogue(bar, epoch, st)) return;
     if (threadIdx.x == 0) {
       s_done = __ldcg(&st->done);
       s_K = __ldcg(&st->maxpy_k);
@@ -1095,7 +1138,7 @@ gmres_status alloc_small(gmres_ctx* h) {
   const size_t o_pa = take(sizeof(double) * (size_t)(Pmax + (Pmax + kGridGroup - 1) / kGridGroup) * nvmax);
   const size_t o_raw = take(sizeof(double) * nvmax);
   const size_t o_ec = take(sizeof(unsigned int) * (m + 2));
-  const size_t o_bar = take(sizeof(unsigned int) * 2);
+  const size_t o_bar = take(sizeof(unsigned int) * 3);
   if (h->small) cudaFree(h->small);
   h->small = nullptr;
   CUDA_TRY(h, cudaMalloc(&h->small, off));
@@ -1268,7 +1311,7 @@ bool use_persistent(const gmres_ctx* h) {
 
 // One cycle of kmax steps in one cooperative launch (k_cycle_persistent).
 gmres_status launch_persistent(gmres_ctx* h, int kmax) {
-  CUDA_TRY(h, cudaMemsetAsync(h->bar, 0, 2 * sizeof(unsigned int), h->stream));
+  CUDA_TRY(h, cudaMemsetAsync(h->bar, 0, 3 * sizeof(unsigned int), h->stream));
   const int pr = prof_begin(h, PC_CYCLE, 0, kmax);
   void* args[] = {&h->rowptr, &h->col, &h->val, &h->V, &h->ldv, &h->w, &h->n, &h->s, &h->bar, &h->bar_extra};
   CUDA_TRY(h, cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(h->cyc), dim3(persistent_grid(h)),
