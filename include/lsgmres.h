@@ -234,10 +234,12 @@ gmres_status gmres_set_reproducible(gmres_handle h, int on);
  * valid handle. */
 gmres_status gmres_set_persistent(gmres_handle h, int mode, int* active);
 
-/* Testing the bounded waits of the persistent cycle's grid barrier: with
- * on = 1 the barrier waits for one CTA more than the grid has, so its first
- * wait runs out (no fault, no hang: about one second), the kernel returns and
- * the solve reports GMRES_ERR_TIMEOUT; on = 0 restores normal operation. */
+/* Testing the bounded waits of the persistent cycle: with on = 1 its grid
+ * barrier waits for one CTA more than the grid has; with on = 2 the wait for
+ * each step's epilogue waits for one epilogue more than there is. Either way
+ * the first such wait runs out (no fault, no hang: about one second), the
+ * kernel returns and the solve reports GMRES_ERR_TIMEOUT; on = 0 restores
+ * normal operation. Other values: GMRES_ERR_ARG. */
 gmres_status gmres_test_stall_barrier(gmres_handle h, int on);
 
 /* Testing the bounded waits of the CSR staging. The step kernel brings each

@@ -767,7 +767,7 @@ k_cycle_persistent(const int32_t* __restrict__ rowptr, const int32_t* __restrict
       }
     }
     ++epoch;
-    if (!wait_epilogue(bar, epoch, st)) return;
+    if (!wait_epilogue(bar, epoch + (bar_extra >> 1), st)) return;
     if (threadIdx.x == 0) {
       s_done = __ldcg(&st->done);
       s_K = __ldcg(&st->maxpy_k);
@@ -797,7 +797,7 @@ k_cycle_persistent(const int32_t* __restrict__ rowptr, const int32_t* __restrict
         out[i] = a0;
       }
     }
-    if (!grid_barrier(bar, P, bar_extra, st)) return;
+    if (!grid_barrier(bar, P, bar_extra & 1u, st)) return;
   }
 }
 
@@ -1936,7 +1936,8 @@ gmres_status gmres_set_persistent(gmres_handle h, int mode, int* active) {
 
 gmres_status gmres_test_stall_barrier(gmres_handle h, int on) {
   if (!h) return GMRES_ERR_ARG;
-  h->bar_extra = on ? 1u : 0u;
+  if (on < 0 || on > 2) return fail(h, GMRES_ERR_ARG, "stall test mode must be 0, 1 or 2");
+  h->bar_extra = (unsigned int)on;  // bit 0: the grid barrier; bit 1: the epilogue wait
   return GMRES_OK;
 }
 

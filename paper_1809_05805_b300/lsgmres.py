@@ -311,9 +311,11 @@ class Solver:
         self._check(self.lib.gmres_set_persistent(self.h, int(mode), ctypes.byref(active)))
         return bool(active.value)
 
-    def test_stall_barrier(self, on: bool):
-        """Make the persistent cycle's grid barrier wait for a CTA that never
-        arrives (testing): the solve returns GMRES_ERR_TIMEOUT after ~1 s."""
+    def test_stall_barrier(self, on):
+        """Make a wait of the persistent cycle run out (testing): on = 1 (or
+        True) its grid barrier waits for a CTA that never arrives, on = 2 its
+        epilogue wait for an epilogue that never comes; the solve returns
+        GMRES_ERR_TIMEOUT after ~1 s. 0 (False) restores normal operation."""
         self._check(self.lib.gmres_test_stall_barrier(self.h, int(on)))
 
     def test_stall_staging(self, on: bool) -> bool:

@@ -109,15 +109,16 @@ def test_persistent_edge_cases(torch_cuda, lsg, orc, case):
     s.close()
 
 
-@pytest.mark.parametrize("use_stream", [False, True])
-def test_persistent_barrier_wait_runs_out(torch_cuda, lsg, use_stream):
+@pytest.mark.parametrize("use_stream,which", [(False, 1), (True, 1), (False, 2), (True, 2)])
+def test_persistent_barrier_wait_runs_out(torch_cuda, lsg, use_stream, which):
+    """which = 1: the grid barrier's wait; 2: the wait for a step's epilogue."""
     torch = torch_cuda
     A = P.conv_diff_7pt(16)
     _, b = P.rhs(A, seed=2)
     bd = torch.from_numpy(b).cuda()
     s = lsg.Solver(A, m=10, tol=1e-8, max_iter=300, stream=torch.cuda.Stream() if use_stream else None)
     assert s.set_persistent(1)
-    s.test_stall_barrier(True)
+    s.test_stall_barrier(which)
     x = torch.zeros(len(b), dtype=torch.float64, device="cuda")
     t0 = time.time()
     with pytest.raises(lsg.GmresError) as e:
