@@ -382,8 +382,23 @@ __device__ void reduce_slots(const double* partials, int64_t slot0, int nslot, i
     const int v = t / S, seg = t % S;
     double acc = 0.0;
     if (v < nv) {
-#pragma unroll 8
-      for (int b = seg; b < nslot; b += S) acc += __ldcg(partials + (size_t)(slot0 + b) * nvmax + v);
+      // this thread's slots seg, seg + S, ... in chunks of 16: the chunk's
+      // loads issued together, then summed as a fixed pairwise tree (four
+      // dependent FP64 adds instead of sixteen), the chunks in order
+      constexpr int C = 16;
+      for (int b0 = seg; b0 < nslot; b0 += C * S) {
+        double x[C];
+#pragma unroll
+        for (int i = 0; i < C; ++i) {
+          const int b = b0 + i * S;
+          x[i] = b < nslot ? __ldcg(partials + (size_t)(slot0 + b) * nvmax + v) : 0.0;
+        }
+#pragma unroll
+        for (int h = C / 2; h > 0; h >>= 1)
+#pragma unroll
+          for (int i = 0; i < h; ++i) x[i] += x[i + h];
+        acc += x[0];
+      }
     }
     for (int o = Sw >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (S > 32) {  // one pass only (S * nv <= blockDim): combine the warps of each value
@@ -422,9 +437,9 @@ __device__ bool publish_and_reduce(double* partials, int nvmax, int64_t slot, in
 
 // Grid-wide form: every CTA of the grid publishes one slot (its block index).
 // The last CTA sums the slots with S threads per value; when that leaves more
-// than 8 slots per thread (many CTAs and many values: each thread's loads come
-// in dependent rounds of 8, and the sums are one dependent FP64 chain), the
-// reduction takes two levels instead: the last CTA of each group of 16
+// than 64 slots per thread (many CTAs and many values: each thread's loads
+// come in rounds of 16, one round per chunk sum), the reduction takes two
+// levels instead: the last CTA of each group of 16
 // consecutive CTAs sums its group's slots into row P + group, and the last
 // group sums the group rows. Both levels sum in a fixed order (deterministic
 // for a given grid). Needs P + ceil(P / 16) rows of partials.
@@ -433,7 +448,7 @@ __device__ bool grid_reduce_last(Small s, double* red, int nv, int nctas = 0) {
   int S = 1;
   while (2 * S * nv <= (int)blockDim.x && S < (int)blockDim.x) S *= 2;
   const int NG = (P + kGridGroup - 1) / kGridGroup;
-  if ((P + S - 1) / S <= 8 || NG > kGridGroupsMax) {
+  if ((P + S - 1) / S <= 64 || NG > kGridGroupsMax) {
     if (!publish_and_reduce(s.partials, s.nvmax, blockIdx.x, 0, P, &s.st->ticket, red, nv)) return false;
   } else {
     const int g = (int)blockIdx.x / kGridGroup, g0 = g * kGridGroup;
