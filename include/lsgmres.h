@@ -210,8 +210,8 @@ gmres_status gmres_set_block_dot(gmres_handle h, int fixed_point, int* active);
  * pairs' exact sums, then varies from run to run, and results can differ in
  * the last bits between identical solves (each within the same bounds). on = 1
  * assigns pair p to CTA p mod P (P the reduction grid): every sum in a fixed
- * order, results bitwise reproducible for a given device and grid, about 6%
- * slower per step at 256^3. Every other kernel of the library sums in a fixed
+ * order, results bitwise reproducible for a given device and grid, about 2%
+ * slower at 256^3. Every other kernel of the library sums in a fixed
  * order always. Never errors on a valid handle. */
 gmres_status gmres_set_reproducible(gmres_handle h, int on);
 
@@ -219,17 +219,17 @@ gmres_status gmres_set_reproducible(gmres_handle h, int on);
  * launch and synchronization latency rather than by memory or arithmetic.
  * The kernel keeps every CTA resident (a cooperative launch) and runs all
  * Arnoldi steps of the cycle (Algorithm 7): per step the fused SpMV + block
- * dot with its single grid reduction and the epilogue in the last CTA, a
- * software grid barrier, the MAXPY beside the Givens rotation of the previous
- * column, and a second barrier -- the same two grid-wide synchronizations per
- * step as the per-step launches, without their kernel boundaries. Arithmetic
- * as the per-step launches of the unstaged kernel (FP64 fused multiply-adds).
+ * dot with its single grid reduction and the epilogue in the last CTA, a wait
+ * for that epilogue, the MAXPY beside the Givens rotation of the previous
+ * column, and a software grid barrier -- one grid reduction and one barrier
+ * per step, without kernel boundaries. Arithmetic as the per-step launches of
+ * the unstaged kernel (FP64 fused multiply-adds).
  * mode = 1: use it whenever it applies (FP64, GMRES_ONE_REDUCE_MGS or
  * GMRES_ONE_REDUCE_PIPE2, and the grid fits on the device at once); 0: never;
  * -1 (the default): when it applies and the system has at most one 256-row
  * tile per CTA of the reduction grid (n <= 2 x SMs x 256). *active (may be
- * NULL) receives whether the handle's next solve uses it. Every wait of its
- * grid barrier is bounded (about one second of SM clocks); a wait that gives up
+ * NULL) receives whether the handle's next solve uses it. Every wait of the
+ * launch is bounded (about one second of SM clocks); a wait that gives up
  * ends the cycle and the solve returns GMRES_ERR_TIMEOUT. Never errors on a
  * valid handle. */
 gmres_status gmres_set_persistent(gmres_handle h, int mode, int* active);
