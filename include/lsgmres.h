@@ -512,7 +512,10 @@ gmres_status lsg_maxpy(gmres_handle h, const double* V, int64_t ldv, int K, cons
                        double alpha, const double* y_in, double* y_out);
 
 /* Run one GMRES cycle of k Arnoldi steps (1 <= k <= m) from the device vector
- * r0, with no convergence test, using the selected scheme. Returns the
+ * r0, with no convergence test, using the selected scheme and precision (a
+ * GMRES-IR handle runs one inner cycle from r0 / ||r0|| rounded to its basis
+ * type, as gmres_solve does; its basis is exported widened to FP64 and its
+ * Hessenberg is that of the unit right-hand side). Returns the
  * normalized basis V_out (device, n x (k+1), leading dimension n), the
  * unrotated Hessenberg H_out (host, (k+1) x k, column-major) and, for the
  * one-reduce scheme, T_out = (I + L)^{-1} (host, (k+1) x (k+1), lower;

@@ -883,14 +883,19 @@ __global__ void k_to_float(const double* __restrict__ a, float* __restrict__ out
 
 __global__ void k_lsq(Small s) { lsq_system(s); }
 
-// V_out[:, k] = scale[k] * V[:, k] for k <= kk (normalized basis export).
-__global__ void k_export_basis(const double* __restrict__ V, int64_t ldv, double* __restrict__ Vo,
+// V_out[:, k] = scale[k] * V[:, k] for k <= kk (normalized basis export; an
+// FP32 or BF16 basis is widened exactly before the scaling).
+template <typename SV>
+__global__ void k_export_basis(const SV* __restrict__ V, int64_t ldv, double* __restrict__ Vo,
                                int64_t n, int kk, Small s) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int k = 0; k <= kk; ++k) {
     const double sc = s.scale[k];
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride)
-      Vo[(size_t)k * n + r] = sc * V[(size_t)k * ldv + r];
+      if constexpr (std::is_same<SV, double>::value)
+        Vo[(size_t)k * n + r] = sc * V[(size_t)k * ldv + r];
+      else
+        Vo[(size_t)k * n + r] = sc * (double)ld_as<float>(V + (size_t)k * ldv + r);
   }
 }
 
@@ -2098,7 +2103,6 @@ gmres_status gmres_arnoldi(gmres_handle h, const double* r0, int k, double* V_ou
   gmres_status st;
   if ((st = check_ptr(h, r0, "r0")) != GMRES_OK) return st;
   if (k < 1 || k > h->m) return fail(h, GMRES_ERR_ARG, "k must be in [1, m]");
-  if (h->prec != GMRES_FP64) return fail(h, GMRES_ERR_ARG, "gmres_arnoldi runs the FP64 cycle only");
   CUDA_TRY(h, cudaSetDevice(h->device));
   std::memset(h->h_st, 0, sizeof(DevState));
   h->h_st->tol = 0.0;
@@ -2108,7 +2112,14 @@ gmres_status gmres_arnoldi(gmres_handle h, const double* r0, int k, double* V_ou
   CUDA_TRY(h, cudaMemsetAsync(h->s.H, 0, sizeof(double) * h->s.ldh * h->m, h->stream));
   CUDA_TRY(h, cudaMemsetAsync(h->s.T, 0, sizeof(double) * h->s.ldh * h->s.ldh, h->stream));
   CUDA_TRY(h, cudaMemsetAsync(h->s.ecol, 0, sizeof(unsigned int) * (h->m + 2), h->stream));
-  k_residual<<<h->P, kThreads, 0, h->stream>>>(h->rowptr, h->col, h->val, r0, nullptr, h->V, h->n, h->s, RES_START, k);
+  k_residual<<<h->P, kThreads, 0, h->stream>>>(h->rowptr, h->col, h->val, r0, nullptr,
+                                               h->prec != GMRES_FP64 ? h->r64 : h->V, h->n, h->s, RES_START, k);
+  LAUNCH_CHECK(h);
+  // a GMRES-IR cycle starts from r0 / ||r0|| rounded to its basis type, as in gmres_solve
+  if (h->prec == GMRES_IR_BF16)
+    k_round_scaled<<<h->grid_stream, kThreads, 0, h->stream>>>(h->r64, h->V16, h->n, h->s);
+  else if (h->prec == GMRES_IR_FP32)
+    k_round_scaled<<<h->grid_stream, kThreads, 0, h->stream>>>(h->r64, h->V32, h->n, h->s);
   LAUNCH_CHECK(h);
   if ((st = launch_cycle(h, k)) != GMRES_OK) return st;
   if ((st = read_state(h)) != GMRES_OK) return st;
@@ -2117,7 +2128,12 @@ gmres_status gmres_arnoldi(gmres_handle h, const double* r0, int k, double* V_ou
   if (h->h_st->nonfinite) return fail(h, GMRES_ERR_NONFINITE, "non-finite value in the Arnoldi process");
   if (k_done) *k_done = kk;
   if (V_out) {
-    k_export_basis<<<h->grid_stream, kThreads, 0, h->stream>>>(h->V, h->ldv, V_out, h->n, kk, h->s);
+    if (h->prec == GMRES_IR_BF16)
+      k_export_basis<<<h->grid_stream, kThreads, 0, h->stream>>>(h->V16, h->ldv, V_out, h->n, kk, h->s);
+    else if (h->prec == GMRES_IR_FP32)
+      k_export_basis<<<h->grid_stream, kThreads, 0, h->stream>>>(h->V32, h->ldv, V_out, h->n, kk, h->s);
+    else
+      k_export_basis<<<h->grid_stream, kThreads, 0, h->stream>>>(h->V, h->ldv, V_out, h->n, kk, h->s);
     LAUNCH_CHECK(h);
   }
   const int ld = h->s.ldh;

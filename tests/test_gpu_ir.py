@@ -176,3 +176,54 @@ def test_ir_bf16_solve(torch_cuda, orc, name, use_stream):
     assert np.linalg.norm(xg - r64.x) <= xbar * np.linalg.norm(r64.x)
     assert abs(info.iters - r16.iters) <= 0.25 * r16.iters, (info.iters, r16.iters)
     assert np.all(np.abs(h[:4] - r16.history[:4]) <= 1e-2 * r16.history[:4])
+
+
+@pytest.mark.parametrize("name", ["aniso27_12cubed", "aniso27_69cubed", "convdiff7_80cubed"])
+@pytest.mark.parametrize("prec", ["ir_fp32", "ir_bf16"])
+def test_ir_inner_cycle_arnoldi(torch_cuda, orc, name, prec):
+    """One GMRES-IR inner cycle (gmres_arnoldi on an IR handle), its basis
+    widened exactly to FP64. Properties that hold at any size, checked on
+    every column: the Arnoldi relation A V_k = V_{k+1} H holds to the
+    rounding of the FP32 arithmetic (the SpMV with A's values in FP32, the
+    MAXPY, the coefficients rounded to FP32) and, for BF16 storage, of the new
+    column's rounding to BF16:
+      ||(A V - V H)[:, j]|| <= 2^-24 ((r + 1) || |A| |v_j| || + (j + 3)(||A v_j|| + sum_i |H_ij|))
+                               [+ 2^-8 H(j+1, j)]   (r: the longest row).
+    The relation is blind to wrong inner products (H and the MAXPY would carry
+    the same coefficients), so at the large sizes, where the cycle stays far
+    from convergence, the basis must also stay orthogonal to the storage type's
+    level (max |I - V^T V| <= 1e-3 FP32, 3e-2 BF16; measured 3e-5..2e-4 and
+    5e-4..7e-3: a block-dot error of 1% shows as about 1e-2 at once), and the
+    first five columns of H must match the oracle's FP32 cycle to FP32
+    summation's level (1e-2 of max |H|: the oracle's sequential FP32 sums of
+    n <= 5e5 terms carry relative errors up to ~n 2^-24)."""
+    torch = torch_cuda
+    from paper_1809_05805_b300 import lsgmres
+
+    make, m = CASES[name]
+    A = make()
+    _, b = P.rhs(A, seed=0)
+    n = len(b)
+    s = lsgmres.Solver(A, m=m, tol=1e-10, prec=prec)
+    V, H, _, kk = s.arnoldi(torch.from_numpy(b).cuda(), m)
+    s.close()
+    assert kk == m
+    Vg = V.cpu().numpy()
+    As = P.to_scipy(A)
+    absA = abs(As)
+    r = int(np.diff(A[0]).max())
+    R = As @ Vg[:, :kk] - Vg @ H
+    for j in range(kk):
+        Av = As @ Vg[:, j]
+        bound = 2.0 ** -24 * ((r + 1) * np.linalg.norm(absA @ np.abs(Vg[:, j]))
+                              + (j + 3) * (np.linalg.norm(Av) + np.abs(H[:, j]).sum()))
+        if prec == "ir_bf16":
+            bound += 2.0 ** -8 * abs(H[j + 1, j])
+        assert np.linalg.norm(R[:, j]) <= bound, (j, np.linalg.norm(R[:, j]), bound)
+    if n >= 100_000:
+        orth = np.abs(Vg.T @ Vg - np.eye(kk + 1)).max()
+        assert orth <= (1e-3 if prec == "ir_fp32" else 3e-2), orth
+        ro = orc.gmres(A, b, variant=2 if prec == "ir_fp32" else 5, m=m, tol=0.0, max_iter=m, capture=True)
+        assert ro.k == kk
+        k5 = 5
+        assert np.abs(H[:, :k5] - ro.H[:, :k5]).max() <= 1e-2 * np.abs(ro.H[:, :k5]).max()
