@@ -114,6 +114,25 @@ __device__ __forceinline__ T warp_reduce_scatter32(T* v) {
   return v[0];
 }
 
+// The same over 16 slots: four halving levels on lane bits 3..0, then one add
+// across bit 4 (16 adds instead of 31); lanes l and l + 16 both return the
+// warp total of slot l mod 16. Fixed order: bitwise reproducible.
+template <typename T>
+__device__ __forceinline__ T warp_reduce_scatter16(T* v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 8; o >= 1; o >>= 1) {
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int i = 0; i < o; ++i) {
+      const T send = up ? v[i] : v[i + o];
+      const T keep = up ? v[i + o] : v[i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
+  }
+  return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 16);
+}
+
 // Sum one value over the CTA (fixed order); result valid in thread 0.
 __device__ __forceinline__ double block_sum(double v, double* sbuf /* kWarps */) {
   v = warp_sum(v);
@@ -1399,38 +1418,55 @@ __device__ __forceinline__ void cta_partials(VT (&acc_a)[MAXC], VT (&acc_c)[MAXC
     v[c] = acc_a[c];
     v[MAXC + c] = acc_c[c];
   }
+  // cross-warp slots q = slot - 2 MAXC: sigma, d, then remainder columns a, c
+  // interleaved (so that few remainder columns leave the high slots empty)
+  v[2 * MAXC] = sig;
+  v[2 * MAXC + 1] = dd;
 #pragma unroll
   for (int c = 0; c < kWarps - 1; ++c) {
-    v[2 * MAXC + c] = rem_a[c];
-    v[2 * MAXC + kWarps - 1 + c] = rem_c[c];
+    v[2 * MAXC + 2 + 2 * c] = rem_a[c];
+    v[2 * MAXC + 3 + 2 * c] = rem_c[c];
   }
-  v[kSlots - 2] = sig;
-  v[kSlots - 1] = dd;
   __shared__ VT scross[kSlots - 2 * MAXC][kWarps];  // slots summed across warps
+  // all used slots below 16: a 16-slot reduce-scatter (16 FP64 adds instead of 31)
+  const bool short16 = kSlots > 16 && 2 * MAXC + 2 + 2 * r8 <= 16;
+  if (short16) {
+    const VT tot = warp_reduce_scatter16(v);
+    const int slot = lane;
+    if (lane < 16) {
+      if (slot < MAXC) {
+        if (slot < J8) red[wid + slot * kWarps] = tot;
+      } else if (slot < 2 * MAXC) {
+        if (slot - MAXC < J8) red[j + wid + (slot - MAXC) * kWarps] = tot;
+      } else {
+        scross[slot - 2 * MAXC][wid] = tot;
+      }
+    }
+  } else {
 #pragma unroll
-  for (int ch = 0; ch < kChunks; ++ch) {
-    const VT tot = warp_reduce_scatter32(v + 32 * ch);
-    const int slot = 32 * ch + lane;
-    if (slot < MAXC) {
-      if (slot < J8) red[wid + slot * kWarps] = tot;  // column wid + 8 slot belongs to this warp
-    } else if (slot < 2 * MAXC) {
-      if (slot - MAXC < J8) red[j + wid + (slot - MAXC) * kWarps] = tot;
-    } else if (slot < kSlots) {
-      scross[slot - 2 * MAXC][wid] = tot;
+    for (int ch = 0; ch < kChunks; ++ch) {
+      const VT tot = warp_reduce_scatter32(v + 32 * ch);
+      const int slot = 32 * ch + lane;
+      if (slot < MAXC) {
+        if (slot < J8) red[wid + slot * kWarps] = tot;  // column wid + 8 slot belongs to this warp
+      } else if (slot < 2 * MAXC) {
+        if (slot - MAXC < J8) red[j + wid + (slot - MAXC) * kWarps] = tot;
+      } else if (slot < kSlots) {
+        scross[slot - 2 * MAXC][wid] = tot;
+      }
     }
   }
   __syncthreads();
   // remainder columns and the two norms: sum the 8 warps in warp order
-  if ((int)threadIdx.x < kSlots - 2 * MAXC) {
+  if ((int)threadIdx.x < 2 + 2 * r8) {
     const int q = threadIdx.x;
     double t2 = 0.0;
     for (int w2 = 0; w2 < kWarps; ++w2) t2 += scross[q][w2];
-    if (q < kWarps - 1) {
-      if (q < r8) red[J8 * kWarps + q] = t2;
-    } else if (q < 2 * (kWarps - 1)) {
-      if (q - (kWarps - 1) < r8) red[j + J8 * kWarps + q - (kWarps - 1)] = t2;
+    if (q < 2) {
+      red[2 * j + q] = t2;
     } else {
-      red[2 * j + (q - 2 * (kWarps - 1))] = t2;
+      const int c = (q - 2) >> 1;
+      red[((q - 2) & 1 ? j : 0) + J8 * kWarps + c] = t2;
     }
   }
   __syncthreads();
