@@ -238,7 +238,9 @@ ke_maxpy_fx(double* __restrict__ V, int64_t ldv, const double* __restrict__ w, E
 #pragma unroll
     for (int v = 0; v < kWarps; ++v) q = max(q, s_p[v]);
     const int P = (int)q;
-    const int cbits = K > 64 ? 56 : 57;
+    // |C| <= 2^cbits and |Xh| <= 2^29: the high sum gathers K products of at most
+    // 2^cbits, below 2^63 for K < 2^(63 - cbits)
+    const int cbits = K < 64 ? 57 : (K < 128 ? 56 : 55);
     if ((int)threadIdx.x < K) {
       long long C = 0;
       if (ck != 0.0 && P > 0) C = __double2ll_rn(scalbn(ck, cbits + 1022 - P + fk));  // |C| < 2^cbits

@@ -79,6 +79,13 @@ struct Small {
   // stored (atomicMax; cleared at each cycle start): the bound of the
   // fixed-point block dot. Unused (may be NULL) elsewhere.
   unsigned int* ecol;
+  // Staging mode 6: the basis columns as fixed-point limbs (fx_split against
+  // the column's stored bound ecol[k]), m + 1 columns of leading dimension
+  // ldl. The step kernel writes column j when it is the step's u; later steps'
+  // block dots read the limbs instead of splitting the FP64 values again.
+  // NULL (and unused) elsewhere.
+  int2* VL;
+  int64_t ldl;
   // Staging mode 6: 1 assigns tile pairs to CTAs by a fixed stride (results
   // bitwise reproducible for a given grid), 0 hands them out by a counter.
   int fixed_order;
@@ -1033,10 +1040,10 @@ __device__ __forceinline__ void tile_pair_dot_rows_pf(int64_t pp, int64_t n, con
 // is bound by the FP64 pipe at ~40% of HBM bandwidth. Here the products of the
 // full columns run as integer arithmetic instead, at FP64 accuracy:
 //  * each value x of a vector with bound |x| < 2^(f - 1022) (f: a biased
-//    exponent at least that of its largest entry) becomes the integer
-//    X = trunc(x 2^(58 - f + 1022)), |X| < 2^58, split into two signed 29-bit
-//    limbs X = Xh 2^29 + Xl (the truncation error is below 2^-58 of the bound,
-//    32 times finer than FP64 rounding of the largest entry);
+//    exponent at least that of its largest entry) becomes an integer X within
+//    one unit of x 2^(58 - f + 1022), |X| <= 2^58, split into two 29-bit limbs
+//    X = Xh 2^29 + Xl, Xh signed, Xl >= 0 (the error is at most 2^-58 of the
+//    bound, 32 times finer than FP64 rounding of the largest entry);
 //  * X Y = Xh Yh 2^58 + (Xh Yl + Xl Yh) 2^29 + Xl Yl: the first two parts are
 //    summed exactly in 64-bit integers (three mad.wide.s32 per product), the
 //    last (below 2^-58 of the largest product) is dropped;
@@ -1065,13 +1072,17 @@ __device__ __forceinline__ uint32_t fx_field(double x) {
 __device__ __forceinline__ int2 fx_split(double x, int kf) {
   const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
   const int sh = kf - (int)((hi >> 20) & 0x7FFu);  // >= 5 in bound; >= 69 for zero and subnormals
-  const uint32_t mh = (__funnelshift_l(lo, hi, 10) & 0x3FFFFFFFu) | 0x40000000u;
-  const unsigned long long M = ((unsigned long long)mh << 32) | (unsigned long long)(lo << 10);
-  unsigned long long X;
-  asm("shr.b64 %0, %1, %2;" : "=l"(X) : "l"(M), "r"(sh));  // shifts past 64 give 0
-  const int sg = (int)hi >> 31;
-  const int xh = (int)(X >> 29), xl = (int)((uint32_t)X & 0x1FFFFFFFu);
-  return make_int2((xh ^ sg) - sg, (xl ^ sg) - sg);
+  // M: the significand with its leading one at bit 62, or, for negative x,
+  // its ones' complement ~M = -M - 1; the arithmetic shift then gives
+  // floor(M / 2^sh) or -floor(M / 2^sh) - 1, within one unit of x 2^(58 - f + 1022)
+  // either way (shifts past 64 give 0 or -1)
+  const uint32_t sg = (uint32_t)((int)hi >> 31);
+  const uint32_t mh = ((__funnelshift_l(lo, hi, 10) & 0x3FFFFFFFu) | 0x40000000u) ^ sg;
+  const long long M = (long long)(((unsigned long long)mh << 32) | (unsigned long long)((lo << 10) ^ sg));
+  long long X;
+  asm("shr.s64 %0, %1, %2;" : "=l"(X) : "l"(M), "r"(sh));
+  // X = Xh 2^29 + Xl with Xh = floor(X / 2^29) in [-2^29, 2^29) and Xl in [0, 2^29)
+  return make_int2((int)(X >> 29), (int)((uint32_t)X & 0x1FFFFFFFu));
 }
 
 __device__ __forceinline__ long long fx_madw(int a, int b, long long c) {
@@ -1117,7 +1128,11 @@ __device__ __forceinline__ double fx_to_double(long long t, int e2) {
 // [rlo, rhi) (relative to the pair's first row) take part: a unit that is one
 // tile of a pair, or a system's ragged end. With the ring, rows past n read as
 // zeros and a caller masks rows below n by passing zero u and w there.
-template <int MAXC, bool RING = true, int S = pf_stages<double>(), typename Hook>
+//
+// LIMBS: V holds each column's limbs already (int2 per row, (Xh, Xl) as
+// fx_split gives them against the column's bound; Small::VL), read through the
+// same 8-byte-per-row copies, so the per-value split drops out of the loop.
+template <int MAXC, bool RING = true, int S = pf_stages<double>(), bool LIMBS = false, typename Hook>
 __device__ __forceinline__ void tile_pair_dot_rows_fx(int64_t pp, int64_t n,
                                                       const double* __restrict__ V, int64_t ldv, bool need_w, int J8,
                                                       int r8, double ur0, double wr0, double ur1, double wr1,
@@ -1213,7 +1228,14 @@ __device__ __forceinline__ void tile_pair_dot_rows_fx(int64_t pp, int64_t n,
         if (r >= rlo && r < rhi && r + 1 >= rhi) xv.x = __ldg(colg + r);  // the range's last row, alone
       }
       const int4 uu = *reinterpret_cast<const int4*>(lu + r);  // limbs of rows r, r + 1
-      const int2 x0 = fx_split(xv.x, kfc), x1 = fx_split(xv.y, kfc);
+      int2 x0, x1;
+      if constexpr (LIMBS) {  // the stored (Xh, Xl) of rows r, r + 1
+        x0 = make_int2(__double2loint(xv.x), __double2hiint(xv.x));
+        x1 = make_int2(__double2loint(xv.y), __double2hiint(xv.y));
+      } else {
+        x0 = fx_split(xv.x, kfc);
+        x1 = fx_split(xv.y, kfc);
+      }
       ah = fx_madw(x0.x, uu.x, ah);
       am = fx_madw(x0.x, uu.y, am);
       am = fx_madw(x0.y, uu.x, am);
@@ -1407,7 +1429,8 @@ __device__ __forceinline__ void cta_partials(VT (&acc_a)[MAXC], VT (&acc_c)[MAXC
   // CTA partials: red[0:j] = a, red[j:2j] = c, red[2j] = sigma, red[2j+1] = d.
   // Each lane's accumulators are packed into 32-slot chunks and reduced across
   // the warp by a butterfly reduce-scatter (31 adds per chunk instead of 5 per
-  // value): lane l then holds the warp total of slot l.
+  // value): lane l then holds the warp total of slot l. When every used slot
+  // lies below 16, a 16-slot reduce-scatter takes the place of the 32-slot one.
   constexpr int kSlots = 2 * MAXC + 2 * (kWarps - 1) + 2;
   constexpr int kChunks = (kSlots + 31) / 32;
   VT v[kChunks * 32];

@@ -317,7 +317,9 @@ k_maxpy_fx(const double* __restrict__ V, int64_t ldv, const double* __restrict__
   }
   __syncthreads();
   const int P = s_ps;
-  const int cbits = K > 64 ? 56 : 57;
+  // |C| <= 2^cbits and |Xh| <= 2^29: the high sum gathers K products of at most
+  // 2^cbits, below 2^63 for K < 2^(63 - cbits)
+  const int cbits = K < 64 ? 57 : (K < 128 ? 56 : 55);
   if ((int)threadIdx.x < K) {
     long long C = 0;
     if (ck != 0.0 && P > 0) {
@@ -830,6 +832,18 @@ __global__ void k_col_fields(const double* __restrict__ V, int64_t ldv, int64_t 
   fx_note_max(ecol, k, emax);
 }
 
+// The first j columns of a caller's basis as fixed-point limbs (fx_split
+// against the bounds k_col_fields measured) into VL, for the standalone block
+// dot of staging mode 6. Grid: (x, j).
+__global__ void k_col_limbs(const double* __restrict__ V, int64_t ldv, int64_t n, const unsigned int* ecol,
+                            int2* __restrict__ VL, int64_t ldl) {
+  const int k = blockIdx.y;
+  const int kf = 5 + (int)max(kFxMinField, ecol[k] >> 20);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+    VL[(size_t)k * ldl + i] = fx_split(V[(size_t)k * ldv + i], kf);
+}
+
 // mode RES_BNORM:    ||b|| -> st->bnorm
 // mode RES_RESIDUAL: r = b - A x -> column 0, ||r|| -> st->rnorm, and the
 //                    cycle state is reset (x == nullptr means x = 0).
@@ -952,6 +966,7 @@ StepKernel<double> step64_for(int m, int stage = 0) {
 // The FP64 step kernel of a handle: staging mode 2 runs as mode 6 (the same
 // kernel with the fixed-point block dot) unless the handle turned that off.
 int fx_stage(int stage, int dot_fx) { return (dot_fx && stage == 2) ? 6 : stage; }
+
 StepKernel<float> step32_for(int m, int stage = 0) {
   return reinterpret_cast<StepKernel<float>>(const_cast<void*>(lsg_steps::step_kernel_f32(m, stage)));
 }
@@ -1002,6 +1017,7 @@ struct gmres_ctx {
   int32_t* col = nullptr;
   double* val = nullptr;
   double* V = nullptr;
+  int2* VL = nullptr;  // the basis as fixed-point limbs (Small::VL; staging mode 6 only)
   int64_t ldv = 0;
   double* w = nullptr;
   char* small = nullptr;
@@ -1113,6 +1129,24 @@ gmres_status fail(gmres_ctx* h, gmres_status st, const std::string& msg) {
 
 
 void destroy_graphs(gmres_ctx* h);
+
+// Staging mode 6 keeps the basis a second time as fixed-point limbs
+// (Small::VL, 8 bytes per entry, m + 1 columns): allocated when the mode is
+// first chosen.
+cudaError_t ensure_limbs(gmres_ctx* h) {
+  if (fx_stage(h->stage64, h->dot_fx) != 6 || h->VL) return cudaSuccess;
+  const size_t bytes = sizeof(int2) * (size_t)h->ldv * (h->m + 1);
+  cudaError_t e = cudaMalloc(&h->VL, bytes);
+  if (e == cudaSuccess) e = cudaMemset(h->VL, 0, bytes);
+  if (e != cudaSuccess) {
+    cudaFree(h->VL);
+    h->VL = nullptr;
+    return e;
+  }
+  h->s.VL = h->VL;
+  h->s.ldl = h->ldv;
+  return cudaSuccess;
+}
 
 gmres_status alloc_small(gmres_ctx* h) {
   destroy_graphs(h);  // captured graphs hold pointers into the old block
@@ -1684,6 +1718,7 @@ gmres_status gmres_create(const gmres_csr* A, int m_restart, double tol, gmres_h
       return bail(GMRES_ERR_CUDA);
     }
     h->step = step64_for(m, fx_stage(h->stage64, h->dot_fx));
+    CREATE_TRY(ensure_limbs(h));
     h->step32 = step32_for(m, h->stage32);
     h->step16 = step16_for(m, h->stage16);
   }
@@ -1914,6 +1949,7 @@ gmres_status gmres_destroy(gmres_handle h) {
   cudaFree(h->col);
   cudaFree(h->val);
   cudaFree(h->V);
+  cudaFree(h->VL);
   cudaFree(h->w);
   cudaFree(h->small);
   cudaFree(h->d_b);
@@ -1949,6 +1985,12 @@ gmres_status gmres_test_stall_barrier(gmres_handle h, int on) {
 gmres_status gmres_set_block_dot(gmres_handle h, int fixed_point, int* active) {
   if (!h) return GMRES_ERR_ARG;
   h->dot_fx = fixed_point ? 1 : 0;
+  CUDA_TRY(h, cudaSetDevice(h->device));
+  if (cudaError_t e = ensure_limbs(h); e != cudaSuccess) {
+    h->dot_fx = 0;  // the kernel in use stays the FP64 one
+    return fail(h, e == cudaErrorMemoryAllocation ? GMRES_ERR_OOM : GMRES_ERR_CUDA,
+                std::string("limb basis: ") + cudaGetErrorString(e));
+  }
   auto k = step64_for(h->m, fx_stage(h->stage64, h->dot_fx));
   if (k != h->step) {
     destroy_graphs(h);  // captured cycles hold the other kernel
@@ -2021,6 +2063,12 @@ gmres_status lsg_block_dot(gmres_handle h, const double* V, int64_t ldv, int j, 
   // dimension or an unaligned base goes through the kernel that loads the
   // basis with plain loads (staging mode 0, FP64 products).
   const bool aligned = ((reinterpret_cast<uintptr_t>(V) & 15) == 0 && (ldv & 1) == 0) || j == 0;
+  if (aligned && j > 0 && use_spmv && fx_stage(h->stage64, h->dot_fx) == 6) {
+    // mode 6 reads the columns as limbs: split the caller's columns once
+    k_col_limbs<<<dim3((unsigned)std::max(1, h->grid_stream / std::max(1, j)), (unsigned)j), kThreads, 0,
+                  h->stream>>>(V, ldv, h->n, h->s.ecol, h->VL, h->ldv);
+    LAUNCH_CHECK(h);
+  }
   if (aligned)
     h->step<<<h->P, kThreads, h->smem64, h->stream>>>(h->rowptr, h->col, h->val, V, ldv, u, w, h->n, h->s, j,
                                                        use_spmv, h->s.raw, h->stage64, h->cap64);

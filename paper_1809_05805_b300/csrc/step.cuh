@@ -125,6 +125,11 @@ k_one_reduce_step(const int32_t* __restrict__ rowptr, const int32_t* __restrict_
   // columns 8 J8 ..), and their FP64 sums
   int kf[MAXC], kfr[2];
   double fr_a[2] = {0.0, 0.0}, fr_c[2] = {0.0, 0.0};
+  // STAGE 6: u's limbs go to Small::VL column j against u's stored bound (not
+  // for the standalone block dot, whose u is the caller's, nor at the tail,
+  // whose column no later step reads)
+  const bool put_limbs = STAGE == 6 && !raw_out && !tail;
+  const int kf_u = put_limbs ? 5 + (int)max(kFxMinField, __ldcg(s.ecol + j) >> 20) : 0;
 #pragma unroll
   for (int c = 0; c < MAXC; ++c) {
     kf[c] = 5 + (int)kFxMinField;
@@ -225,6 +230,15 @@ k_one_reduce_step(const int32_t* __restrict__ rowptr, const int32_t* __restrict_
         VT ur0 = VT(0), ur1 = VT(0), wr0 = VT(0), wr1 = VT(0);
         if (row0 < n) ur0 = ld_as<VT>(u + row0);
         if (kPairs && row1 < n) ur1 = ld_as<VT>(u + row1);
+        if constexpr (STAGE == 6) {
+          // u is basis column j: its limbs, for the block dots of the
+          // cycle's later steps (rows past n stay zero)
+          if (put_limbs) {
+            int2* vl = s.VL + (size_t)j * s.ldl;
+            if (row0 < n) vl[row0] = fx_split((double)ur0, kf_u);
+            if (row1 < n) vl[row1] = fx_split((double)ur1, kf_u);
+          }
+        }
         bool staged = !s_stage_off;
         if (staged) {
           staged = mbar_wait_bounded(&s_bar, phase);
@@ -307,10 +321,12 @@ k_one_reduce_step(const int32_t* __restrict__ rowptr, const int32_t* __restrict_
                                             reinterpret_cast<SV*>(cs.val + stage_cap), acc_a, acc_c, rem_a, rem_c,
                                             sig, dd, next);
           else if constexpr (STAGE == 6)
-            // the same ring; every column's products on the integer pipes
-            tile_pair_dot_rows_fx<MAXC>(unit, n, V, ldv, need_w, J8, r8, ur0, wr0, ur1, wr1,
-                                        su, sw, reinterpret_cast<double*>(cs.val + stage_cap), kf, kfr, acc_a,
-                                        acc_c, fr_a, fr_c, sig, dd, s_ex, next);
+            // the same ring over the columns' stored limbs; every column's
+            // products on the integer pipes
+            tile_pair_dot_rows_fx<MAXC, true, pf_stages<double>(), true>(
+                unit, n, reinterpret_cast<const double*>(s.VL), s.ldl, need_w, J8, r8, ur0, wr0, ur1, wr1, su, sw,
+                reinterpret_cast<double*>(cs.val + stage_cap), kf, kfr, acc_a, acc_c, fr_a, fr_c, sig, dd, s_ex,
+                next);
           else
             tile_pair_dot_rows<MAXC, SV, VT>(unit, n, V, ldv, need_w, J8, r8, ur0, wr0, ur1, wr1, su, sw, acc_a,
                                              acc_c, rem_a, rem_c, sig, dd, next);

@@ -122,21 +122,29 @@ def test_block_dot_matches_oracle(torch_cuda, lsg, orc, fixed_point, j, pad, spr
     s.close()
 
 
-@pytest.mark.parametrize("fixed_point", [True, False])
-def test_solve_matches_oracle(torch_cuda, lsg, orc, fixed_point):
+ORACLE_VARIANT = {"one_reduce_mgs": 1, "cgs2_lvl2": 3, "one_reduce_pipe2": 4}
+
+
+@pytest.mark.parametrize("fixed_point,ortho", [(True, "one_reduce_mgs"), (False, "one_reduce_mgs"),
+                                               (True, "cgs2_lvl2"), (True, "one_reduce_pipe2")])
+def test_solve_matches_oracle(torch_cuda, lsg, orc, fixed_point, ortho):
+    """72^3 (tile pairs, staging mode 6 when the fixed-point form is on): the
+    one-reduce scheme and its two siblings, whose basis columns (and their
+    stored limbs) are written by other kernels in between, at the
+    single-solve bar."""
     torch = torch_cuda
     N = 72
     A = P.conv_diff_7pt(N)
     _, b = P.rhs(A, seed=3)
     n = len(b)
     stream = torch.cuda.Stream()
-    s = lsg.Solver(A, m=40, tol=1e-9, max_iter=2000, stream=stream)
+    s = lsg.Solver(A, m=40, tol=1e-9, max_iter=2000, stream=stream, ortho=ortho)
     assert s.set_block_dot(fixed_point) == fixed_point
     x = torch.zeros(n, dtype=torch.float64, device="cuda")
     bd = torch.from_numpy(b).cuda()
     torch.cuda.synchronize()
     info = s.solve(bd, x)
-    r = orc.gmres(A, b, variant=1, m=40, tol=1e-9, max_iter=2000)
+    r = orc.gmres(A, b, variant=ORACLE_VARIANT[ortho], m=40, tol=1e-9, max_iter=2000)
     assert info.status == r.status == 0
     assert info.iters == r.iters and info.restarts == r.restarts and info.reductions == r.reductions
     hist = s.history()
