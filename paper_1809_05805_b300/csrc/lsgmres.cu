@@ -256,11 +256,12 @@ k_maxpy(const VT* __restrict__ V, int64_t ldv, const YT* y_in, YT* y_out, int64_
 // coefficients fold the lagged normalization and T s of Algorithm 4). The
 // sum over the basis columns is formed exactly in integers and rounded to
 // FP64 once per row, then alpha w is added with one FMA:
-//  * each basis value becomes X = trunc(u 2^(58 - E_k)) from its column's
-//    stored bound (Small::ecol), split in 29-bit limbs (fx_split);
+//  * each basis value is the integer X within one unit of u 2^(58 - E_k)
+//    from its column's stored bound (Small::ecol), in 29-bit limbs, as the
+//    step kernel stored them (Small::VL, fx_split);
 //  * each coefficient becomes an integer C_k = round(c_k 2^e_k) scaled so
-//    that every product C_k X_k shares one scale and |C_k| < 2^57 (2^56 past
-//    64 columns), split in C_k = Ch 2^29 + Cl;
+//    that every product C_k X_k shares one scale and |C_k| <= 2^57 (2^56 from
+//    64 columns, 2^55 from 128), split in C_k = Ch 2^29 + Cl;
 //  * per row, hh = sum Ch Xh and mid = sum (Ch Xl + Cl Xh) in 64-bit integers
 //    (mid folded into hh every 16 columns), Cl Xl (below 2^-56 of the
 //    largest product) dropped.
@@ -344,16 +345,16 @@ k_maxpy_fx(const double* __restrict__ V, int64_t ldv, const double* __restrict__
     long long hh0 = 0, md0 = 0, hh1 = 0, md1 = 0;
     int k = 0;
     for (; k < K; k += 4) {
-      double2 x[4];
+      int4 x[4];  // the stored limbs of rows 2i, 2i + 1 of columns k .. k + 3
 #pragma unroll
       for (int u2 = 0; u2 < 4; ++u2)
-        x[u2] = (k + u2 < K) ? __ldg(reinterpret_cast<const double2*>(V + (size_t)(k + u2) * ldv) + i)
-                             : make_double2(0.0, 0.0);
+        x[u2] = (k + u2 < K) ? __ldg(reinterpret_cast<const int4*>(s.VL + (size_t)(k + u2) * s.ldl) + i)
+                             : make_int4(0, 0, 0, 0);
 #pragma unroll
       for (int u2 = 0; u2 < 4; ++u2) {
         if (k + u2 < K) {
           const int4 c = sC[k + u2];
-          const int2 a = fx_split(x[u2].x, c.z), b = fx_split(x[u2].y, c.z);
+          const int2 a = make_int2(x[u2].x, x[u2].y), b = make_int2(x[u2].z, x[u2].w);
           hh0 = fx_madw(c.x, a.x, hh0);
           md0 = fx_madw(c.x, a.y, md0);
           md0 = fx_madw(c.y, a.x, md0);
@@ -381,7 +382,7 @@ k_maxpy_fx(const double* __restrict__ V, int64_t ldv, const double* __restrict__
     long long hh = 0, md = 0;
     for (int k = 0; k < K; ++k) {
       const int4 c = sC[k];
-      const int2 a = fx_split(V[(size_t)k * ldv + i], c.z);
+      const int2 a = __ldg(s.VL + (size_t)k * s.ldl + i);
       hh = fx_madw(c.x, a.x, hh);
       md = fx_madw(c.x, a.y, md);
       md = fx_madw(c.y, a.x, md);
