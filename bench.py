@@ -103,9 +103,10 @@ FP64_DFMA_PER_CLK_SM = 2  # B300: 1.25 TFLOP/s nominal FP64 = 148 SMs x 2 DFMA/c
 # for the kernel builds those captures measured; set to None when a kernel
 # changes.
 STEP_TRAFFIC_RATIO = 1.048
-# The same ratio for the FP64 step with fixed-point products (staging mode 6):
+# The same ratio for the FP64 step with fixed-point products (staging mode 6,
+# the basis read as stored limbs; the limbs of u, 8n bytes, written on top):
 # 128^3 7-point at j = 10 and 11.
-STEP6_TRAFFIC_RATIO = 1.003
+STEP6_TRAFFIC_RATIO = 1.035
 STEP32_TRAFFIC_RATIO = {"27pt": 1.014, "7pt": 1.005}
 
 
@@ -658,7 +659,9 @@ def run_ours(args, w, rank, world, dist):
             "bound": "hbm", "achieved": step_gbs, "peak": hbm, "unit": "GB/s",
             "frac": step_gbs / hbm if step_gbs else None,
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy bandwidth, of measured)",
-            "alg_bytes_formula": "4(n+1) + 12 nnz + 8n(j+1) + 8n (CSR, u and V_j read, w written)",
+            "alg_bytes_formula": "4(n+1) + 12 nnz + 8n(j+1) + 8n (CSR, u and V_j read, w written; the basis "
+                                 "is read as stored limbs, 8 bytes per entry, and the limbs of u, 8n, written "
+                                 "on top are not counted)",
             "hbm_frac_of_measured_survey_bytes": (survey_bytes / (st["ms"] * 1e-3) / 1e9) / hbm if st["ms"] else None,
             "traffic": (STEP6_TRAFFIC_RATIO * st["bytes"] / max(st["launches"], 1)) if STEP6_TRAFFIC_RATIO else None,
             "traffic_source": "ncu dram bytes / algorithmic bytes of the fixed-point step at 128^3 (same kernel build), "
