@@ -166,7 +166,9 @@ ke_maxpy(VT* __restrict__ V, int64_t ldv, const VT* __restrict__ w, EngDev e, in
 // products on the integer pipes (the single-system k_maxpy_fx, per run of one
 // system's tiles): the system's coefficients become integers C_k on one
 // common scale chosen from its basis exponent bounds (Small::ecol), each basis
-// value a 58-bit integer relative to its column's bound; per row the sum over
+// value a 58-bit integer relative to its column's bound, read as the limbs the
+// step kernel stored (EngDev::VL; rows past a system's end hold limbs of
+// whatever the arena held, their outputs are zeroed); per row the sum over
 // the columns is exact in 64-bit integers (hi-hi and mid limb products, the
 // low-low product dropped) and rounded to FP64 once, then alpha w is added by
 // one FMA. Rows of the run past the system's last row (its last tile's
@@ -257,16 +259,16 @@ ke_maxpy_fx(double* __restrict__ V, int64_t ldv, const double* __restrict__ w, E
     for (int64_t i = t0 * (kThreads / 2) + threadIdx.x; i < q1; i += blockDim.x) {
       long long hh0 = 0, md0 = 0, hh1 = 0, md1 = 0;
       for (int k = 0; k < K; k += 4) {
-        double2 x[4];
+        int4 x[4];  // the stored limbs of rows 2i, 2i + 1 of columns k .. k + 3
 #pragma unroll
         for (int u2 = 0; u2 < 4; ++u2)
-          x[u2] = (k + u2 < K) ? __ldg(reinterpret_cast<const double2*>(V + (size_t)(k + u2) * ldv) + i)
-                               : make_double2(0.0, 0.0);
+          x[u2] = (k + u2 < K) ? __ldg(reinterpret_cast<const int4*>(e.VL + (size_t)(k + u2) * ldv) + i)
+                               : make_int4(0, 0, 0, 0);
 #pragma unroll
         for (int u2 = 0; u2 < 4; ++u2) {
           if (k + u2 < K) {
             const int4 c = sC[k + u2];
-            const int2 a = fx_split(x[u2].x, c.z), b = fx_split(x[u2].y, c.z);
+            const int2 a = make_int2(x[u2].x, x[u2].y), b = make_int2(x[u2].z, x[u2].w);
             hh0 = fx_madw(c.x, a.x, hh0);
             md0 = fx_madw(c.x, a.y, md0);
             md0 = fx_madw(c.y, a.x, md0);
@@ -545,6 +547,7 @@ struct Engine {
   size_t vb = 8;
   // arena
   void* V = nullptr;
+  int2* VL = nullptr;  // FP64 cycles: the basis as fixed-point limbs (EngDev::VL)
   void* w = nullptr;
   double* bv = nullptr;
   double* xv = nullptr;
@@ -640,12 +643,14 @@ struct Engine {
 
   bool ir() const { return cfg.prec == GMRES_IR_FP32; }
 
-  // Device bytes the engine holds for `rows` arena rows and `csr_bytes` of CSR.
-  static size_t footprint(const EngineConfig& c) {
+  // Device bytes per arena row: the basis (m + 1 columns) and w, b and x;
+  // FP32 cycles add the FP64 residual, FP64 cycles the basis limbs.
+  static size_t row_bytes(const EngineConfig& c) {
     const size_t vbytes = c.prec == GMRES_IR_FP32 ? 4 : 8;
-    const size_t per_row = vbytes * (c.m + 2) + 16 + (c.prec == GMRES_IR_FP32 ? 8 : 0);
-    return per_row * (size_t)c.rows + (size_t)c.csr_bytes;
+    return vbytes * (c.m + 2) + 16 + (c.prec == GMRES_IR_FP32 ? 8 : 8 * (size_t)(c.m + 1));
   }
+  // Device bytes the engine holds for `rows` arena rows and `csr_bytes` of CSR.
+  static size_t footprint(const EngineConfig& c) { return row_bytes(c) * (size_t)c.rows + (size_t)c.csr_bytes; }
 
   gmres_status init(const EngineConfig& c) {
     cfg = c;
@@ -657,6 +662,10 @@ struct Engine {
     ldv = R;
     const int m = cfg.m, ld = m + 1, S = std::max(1, cfg.max_systems);
     ETRY(cudaMalloc(&V, vb * (size_t)R * (m + 1)));
+    if (!ir()) {  // rows no system has written read as zero limbs
+      ETRY(cudaMalloc(&VL, sizeof(int2) * (size_t)R * (m + 1)));
+      ETRY(cudaMemset(VL, 0, sizeof(int2) * (size_t)R * (m + 1)));
+    }
     ETRY(cudaMalloc(&w, vb * (size_t)R));
     ETRY(cudaMalloc(&bv, 8 * (size_t)R));
     ETRY(cudaMalloc(&xv, 8 * (size_t)R));
@@ -792,7 +801,7 @@ struct Engine {
 
   void release() {
     drop_graphs();
-    for (void* p : {V, w, (void*)bv, (void*)xv, (void*)r64, (void*)csr_pool, (void*)d_desc, (void*)d_smalls,
+    for (void* p : {V, (void*)VL, w, (void*)bv, (void*)xv, (void*)r64, (void*)csr_pool, (void*)d_desc, (void*)d_smalls,
                     (void*)d_states, (void*)d_blk, (void*)d_tickets, (void*)d_ecol, (void*)d_tiles, (void*)d_act,
                     (void*)d_nact, (void*)d_partials})
       if (p) cudaFree(p);
@@ -844,6 +853,7 @@ struct Engine {
     d.partials = d_partials;
     d.tickets = d_tickets;
     d.nvmax = nvmax;
+    d.VL = VL;
     return d;
   }
 
@@ -1907,8 +1917,7 @@ gmres_status gmres_server_create(const gmres_server_config* cfg, gmres_server* o
     // fixed per-slot state, then rows and CSR in proportion to a row's needs
     const int ld = c.m + 1;
     const int64_t per_slot = 8 * (int64_t)(2 * ld * c.m + ld * ld + 6 * ld + c.max_iter_cap + ld) + 256 * 12;
-    const int64_t vb = k == 0 ? 8 : 4;
-    const int64_t per_row = vb * (c.m + 2) + 16 + (k == 1 ? 8 : 0);
+    const int64_t per_row = (int64_t)Engine::row_bytes(c);
     const int64_t csr_row = 4 + cfg->nnz_per_row_hint * (12 + (k == 1 ? 4 : 0));
     // reduction slots: (largest grid + slots) rows of 2 (m+1) + 2 partial sums
     const int64_t partials = 8 * ((int64_t)kMaxGridPerSm * nsm + c.max_systems + 1) * (2 * ld + 2);
@@ -2039,7 +2048,7 @@ gmres_status gmres_server_stats(gmres_server sv, gmres_server_counters* st) {
     st->cycles[k] = W.cycles;
     st->busy_seconds[k] = W.busy_s;
     st->kernel_launches[k] = e.launches;
-    const int64_t row_bytes = (int64_t)e.vb * (e.cfg.m + 2) + 16 + (k == 1 ? 8 : 0);
+    const int64_t row_bytes = (int64_t)Engine::row_bytes(e.cfg);
     st->engine_bytes[k] = e.R > 0 ? (int64_t)Engine::footprint(e.cfg) : 0;
     st->peak_bytes_in_use[k] = W.peak_rows * kPairRows * row_bytes + W.peak_csr_units * 256;
     st->arena_rows[k] = e.R;

@@ -52,6 +52,11 @@ struct EngDev {
   const int32_t* bounds;
   int nb;
   int nvmax;
+  // FP64 cycles: the arena's basis a second time as fixed-point limbs (same
+  // rows and leading dimension; each system's column j written by the step
+  // kernel when it is the step's u, read by later steps' block dots and by
+  // the MAXPY); null for FP32 cycles
+  int2* VL;
 };
 
 // This CTA's range [lo, hi) of the listed tiles when `grid` CTAs share them.

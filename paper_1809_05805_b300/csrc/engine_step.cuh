@@ -40,7 +40,8 @@ __device__ __noinline__ VT csr_row_plain(const int32_t* __restrict__ rowptr, con
 // FP64 cycles on tile pairs with FXM = 1 or 2: the block dot's products as exact
 // fixed-point integers on the integer pipes (tile_pair_dot_rows_fx, the
 // system's basis exponent bounds from its Small::ecol), as the single-system
-// solver's staging mode 6; a unit that is one tile of a pair runs as that pair
+// solver's staging mode 6, on the limbs each basis column got at the step
+// whose u it was (EngDev::VL); a unit that is one tile of a pair runs as that pair
 // with the other tile's rows masked. FXM = 1 loads the basis directly;
 // FXM = 2 streams it through a per-warp ring of kEngRing half-column slices
 // filled by cp.async, placed over the epilogue's shared memory (the epilogue
@@ -117,6 +118,7 @@ ke_step(const VT* __restrict__ V, int64_t ldv, VT* __restrict__ w, EngDev e, int
   VT sig = VT(0), dd = VT(0);
   double fr_a[2] = {0.0, 0.0}, fr_c[2] = {0.0, 0.0};  // FX: remainder half-columns
   int kf[MAXC], kfr[2];                               // FX: 5 + the current system's column bounds
+  int kf_u = 0;                                       // FX: 5 + the bound of its column j (u)
   int cur = -1;
   // Within a system the listing is the system's tiles in order, so the next
   // unit's tile follows from the current one (t_next) while it is at most the
@@ -186,6 +188,7 @@ ke_step(const VT* __restrict__ V, int64_t ldv, VT* __restrict__ w, EngDev e, int
           const int r = wid + q * kWarps;
           kfr[q] = 5 + (int)max(kFxMinField, r < 2 * r8 ? __ldcg(ec + J8 * kWarps + (r >> 1)) >> 20 : 0u);
         }
+        kf_u = 5 + (int)max(kFxMinField, __ldcg(ec + j) >> 20);
       }
     }
     const bool tail = s_tail;
@@ -266,6 +269,16 @@ ke_step(const VT* __restrict__ V, int64_t ldv, VT* __restrict__ w, EngDev e, int
       VT ur0 = VT(0), ur1 = VT(0), wr0 = VT(0), wr1 = VT(0);
       if (row0 < lim) ur0 = ld_as<VT>(u + row0);
       if (pair && row1 < lim) ur1 = ld_as<VT>(u + row1);
+      if constexpr (FX) {
+        // u is the system's basis column j: its limbs, for the block dots of
+        // the cycle's later steps and the MAXPY (not at the tail, whose
+        // column nothing reads again)
+        if (!tail) {
+          int2* vl = e.VL + (size_t)j * ldv;
+          if (row0 < lim) vl[row0] = fx_split((double)ur0, kf_u);
+          if (pair && row1 < lim) vl[row1] = fx_split((double)ur1, kf_u);
+        }
+      }
       if (!tail) {
         if (pair) {
           if (staged)
@@ -292,14 +305,16 @@ ke_step(const VT* __restrict__ V, int64_t ldv, VT* __restrict__ w, EngDev e, int
         const int rlo = (int)(max(s_d.row0, second ? pb + kThreads : pb) - pb);
         const int rhi = (int)(min(lim, pair || second ? pb + 2 * kThreads : pb + kThreads) - pb);
         double* ring = FXM == 2 ? reinterpret_cast<double*>(reinterpret_cast<char*>(dyn) + epi_off) : nullptr;
+        // the basis columns as the limbs stored at their own steps
+        const double* VLd = reinterpret_cast<const double*>(e.VL);
         if (second)
-          tile_pair_dot_rows_fx<MAXC, FXM == 2, kEngRing>(t >> 1, lim, V, ldv, !tail, J8, r8, 0.0, 0.0, ur0, wr0, su,
-                                                          sw, ring, kf, kfr, acc_a, acc_c, fr_a, fr_c, sig, dd, s_ex,
-                                                          next, rlo, rhi);
+          tile_pair_dot_rows_fx<MAXC, FXM == 2, kEngRing, true>(t >> 1, lim, VLd, ldv, !tail, J8, r8, 0.0, 0.0, ur0,
+                                                                wr0, su, sw, ring, kf, kfr, acc_a, acc_c, fr_a, fr_c,
+                                                                sig, dd, s_ex, next, rlo, rhi);
         else
-          tile_pair_dot_rows_fx<MAXC, FXM == 2, kEngRing>(t >> 1, lim, V, ldv, !tail, J8, r8, ur0, wr0, ur1, wr1, su,
-                                                          sw, ring, kf, kfr, acc_a, acc_c, fr_a, fr_c, sig, dd, s_ex,
-                                                          next, rlo, rhi);
+          tile_pair_dot_rows_fx<MAXC, FXM == 2, kEngRing, true>(t >> 1, lim, VLd, ldv, !tail, J8, r8, ur0, wr0, ur1,
+                                                                wr1, su, sw, ring, kf, kfr, acc_a, acc_c, fr_a, fr_c,
+                                                                sig, dd, s_ex, next, rlo, rhi);
       } else if constexpr (FXM == 3) {
         // FP32 tile pairs with the basis through the per-warp cp.async ring
         // (over the epilogue's shared memory); a single tile runs as its pair

@@ -102,7 +102,7 @@ def test_server_admission_by_budget(torch_cuda, lsg):
     and are admitted as earlier ones complete; the bytes occupied never exceed
     the engine's allocation; every request completes and converges."""
     reqs = [(A, b, "fp64") for A, b, _ in _requests(10, seed=5, sides=(24, 28))]
-    # FP64 engine: ~18 MB -> room for about three 24^3..28^3 requests (m = 20)
+    # FP64 engine: ~18 MB (basis, its limbs, CSR) -> room for one or two 24^3..28^3 requests (m = 20)
     sv, infos, xs = _serve(lsg, reqs, 1e-8, budget=int(18e6 / 0.6), max_requests=8, gap_s=0.0)
     st = sv.stats()
     sv.close()
