@@ -115,7 +115,11 @@ typedef struct {
 /* Create a solver for A with restart length m_restart (1 <= m <= 128) and
  * relative tolerance tol >= 0. Validates A on the host (structure above; n > 0;
  * nnz < 2^31), copies it to the device and allocates the Krylov basis
- * ((m+1) columns of n doubles) and the small dense state. Defaults:
+ * ((m+1) columns of n doubles) and the small dense state; when the fixed-point
+ * block dot is active (gmres_set_block_dot; the default for matrices that take
+ * the tile-pair kernel) also a second copy of the basis as fixed-point limbs
+ * (8 bytes per entry), written once per column and read by the later steps'
+ * block dots and MAXPYs. Defaults:
  * GMRES_ONE_REDUCE_MGS, GMRES_FP64, max_iter = 10 * m, legacy default stream.
  * Errors: GMRES_ERR_ARG, GMRES_ERR_OOM, GMRES_ERR_CUDA; *out is NULL then. */
 gmres_status gmres_create(const gmres_csr* A, int m_restart, double tol, gmres_handle* out);
@@ -200,7 +204,9 @@ gmres_status gmres_profile(gmres_handle h, int cls, double* total_ms, int64_t* l
  * multiply-adds throughout. *active (may be NULL) receives whether this
  * handle's step kernel uses the fixed-point form (it needs staging mode 2:
  * large enough matrices whose tile-pair CSR fits the shared memory). The
- * choice changes rounding only. Never errors on a valid handle. */
+ * choice changes rounding only. Turning the form on allocates the limb copy of
+ * the basis (see gmres_create) if the handle has none; GMRES_ERR_OOM or
+ * GMRES_ERR_CUDA if that fails, and the FP64 form stays in use. */
 gmres_status gmres_set_block_dot(gmres_handle h, int fixed_point, int* active);
 
 /* Run-to-run reproducibility of the fixed-point step kernel (the one
@@ -371,7 +377,8 @@ const char* gmres_batch_last_error(gmres_batch bt);
  * cycles inside FP64 restarts (GMRES_IR_FP32), exactly as a batch would.
  * A server owns two batched engines, one per precision, each with its own
  * CUDA stream and host worker thread, so their launches overlap on the
- * device. Each engine's device memory (Krylov bases and vectors for a fixed
+ * device. Each engine's device memory (Krylov bases, for FP64 also as
+ * fixed-point limbs, and vectors for a fixed
  * number of arena rows, a CSR pool, per-request state) is allocated once at
  * create from its share of hbm_budget_bytes. A worker runs lock-step restart
  * cycles over its iterating requests; at every cycle boundary it completes
