@@ -17,6 +17,8 @@ That changes rounding only, so:
   single-solve bar (identical counts, history 1e-8 over the first 50 steps, x
   1e-9), on a system large enough for the tile-pair ring kernel that carries
   the fixed-point form;
+* the limb copy of the basis those kernels read is rewritten by every user
+  (standalone block dots on different columns, a solve in between);
 * NaN in u reaches the sums.
 """
 import numpy as np
@@ -119,6 +121,46 @@ def test_block_dot_matches_oracle(torch_cuda, lsg, orc, fixed_point, j, pad, spr
     assert np.all(np.abs(X - ref) <= bound)
     if j > 3:  # the zero column gives exact zeros
         assert X[2] == 0.0 and X[j + 2] == 0.0
+    s.close()
+
+
+def _block_dot_checked(torch, s, orc, A, n, ldv, j, seed):
+    """One standalone fused SpMV + block dot on fresh columns against the
+    oracle's sums at the classical bound (entries within 2^(+-3))."""
+    rng = np.random.default_rng(seed)
+    V = _columns(rng, j, n, ldv, 3)
+    u = rng.standard_normal(n) * np.exp2(rng.uniform(-3, 3, n))
+    wd = torch.zeros(n, dtype=torch.float64, device="cuda")
+    X = s.block_dot(torch.from_numpy(V).cuda(), ldv, j, torch.from_numpy(u).cuda(), wd, True)
+    w = wd.cpu().numpy()
+    cols = [V[k, :n] for k in range(j)]
+    ref = np.array([orc.dot(c, u) for c in cols] + [orc.dot(c, w) for c in cols] + [orc.dot(u, u), orc.dot(u, w)])
+    terms = np.array([np.abs(c * u).sum() for c in cols] + [np.abs(c * w).sum() for c in cols] +
+                     [np.abs(u * u).sum(), np.abs(u * w).sum()])
+    assert np.all(np.abs(X - ref) <= 2 * gamma(n) * terms)
+
+
+def test_limb_copy_rewritten_by_each_user(torch_cuda, lsg, orc):
+    """The fixed-point kernels read the basis as the limb copy (written once per
+    column): two standalone block dots with different columns on one handle
+    (each splits its caller's columns into the copy), then a solve (its steps
+    rewrite the columns they use), then a block dot again, each against the
+    oracle."""
+    torch = torch_cuda
+    A = P.conv_diff_7pt(70)
+    n = len(A[0]) - 1
+    ldv = n + 6  # even, so the columns stay 16-byte aligned for the ring kernel
+    s = lsg.Solver(A, m=30, tol=1e-8, max_iter=1500)
+    assert s.set_block_dot(True)
+    _block_dot_checked(torch, s, orc, A, n, ldv, 21, seed=1)
+    _block_dot_checked(torch, s, orc, A, n, ldv, 13, seed=2)
+    _, b = P.rhs(A, seed=4)
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    info = s.solve(torch.from_numpy(b).cuda(), x)
+    r = orc.gmres(A, b, variant=1, m=30, tol=1e-8, max_iter=1500)
+    assert info.status == r.status == 0 and info.iters == r.iters and info.restarts == r.restarts
+    assert np.linalg.norm(x.cpu().numpy() - r.x) <= 1e-9 * np.linalg.norm(r.x)
+    _block_dot_checked(torch, s, orc, A, n, ldv, 30, seed=3)
     s.close()
 
 
