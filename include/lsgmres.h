@@ -119,7 +119,8 @@ typedef struct {
  * block dot is active (gmres_set_block_dot; the default for matrices that take
  * the tile-pair kernel) also a second copy of the basis as fixed-point limbs
  * (8 bytes per entry), written once per column and read by the later steps'
- * block dots and MAXPYs. Defaults:
+ * block dots and MAXPYs; when that copy does not fit, the handle starts with
+ * FP64 products instead (see gmres_set_block_dot). Defaults:
  * GMRES_ONE_REDUCE_MGS, GMRES_FP64, max_iter = 10 * m, legacy default stream.
  * Errors: GMRES_ERR_ARG, GMRES_ERR_OOM, GMRES_ERR_CUDA; *out is NULL then. */
 gmres_status gmres_create(const gmres_csr* A, int m_restart, double tol, gmres_handle* out);

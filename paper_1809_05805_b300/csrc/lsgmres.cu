@@ -1718,8 +1718,16 @@ gmres_status gmres_create(const gmres_csr* A, int m_restart, double tol, gmres_h
       h->err = "cudaFuncSetAttribute of the fixed-point or unstaged step kernel failed";
       return bail(GMRES_ERR_CUDA);
     }
+    if (cudaError_t e = ensure_limbs(h); e == cudaErrorMemoryAllocation) {
+      // no room for the limb copy beside the basis: the handle starts with
+      // FP64 products (gmres_set_block_dot reports which form is active)
+      cudaGetLastError();
+      h->dot_fx = 0;
+    } else if (e != cudaSuccess) {
+      h->err = std::string("limb copy of the basis: ") + cudaGetErrorString(e);
+      return bail(GMRES_ERR_CUDA);
+    }
     h->step = step64_for(m, fx_stage(h->stage64, h->dot_fx));
-    CREATE_TRY(ensure_limbs(h));
     h->step32 = step32_for(m, h->stage32);
     h->step16 = step16_for(m, h->stage16);
   }
