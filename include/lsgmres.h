@@ -287,7 +287,9 @@ typedef struct gmres_batch_ctx* gmres_batch;
 
 /* Create a batch from `count` >= 1 host CSR matrices (A[i].on_device must be
  * 0; the arrays are copied), restart length 1 <= m <= 128, tol >= 0,
- * max_iter >= 0 steps per system. Errors: GMRES_ERR_ARG, GMRES_ERR_OOM,
+ * max_iter >= 0 steps per system. The row arena holds the m + 1 basis columns
+ * twice, as FP64 values and as the fixed-point limbs the engine's block dot
+ * and MAXPY read (8 bytes per entry each). Errors: GMRES_ERR_ARG, GMRES_ERR_OOM,
  * GMRES_ERR_CUDA (details in gmres_batch_last_error(NULL)). */
 gmres_status gmres_batch_create(const gmres_csr* A, int count, int m_restart, double tol, int max_iter,
                                 gmres_batch* out);
