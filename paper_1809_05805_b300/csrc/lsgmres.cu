@@ -344,14 +344,14 @@ k_maxpy_fx(const double* __restrict__ V, int64_t ldv, const double* __restrict__
   for (int64_t i = gid; i < nE; i += stride) {
     long long hh0 = 0, md0 = 0, hh1 = 0, md1 = 0;
     int k = 0;
-    for (; k < K; k += 4) {
-      int4 x[4];  // the stored limbs of rows 2i, 2i + 1 of columns k .. k + 3
+    for (; k < K; k += 8) {
+      int4 x[8];  // the stored limbs of rows 2i, 2i + 1 of columns k .. k + 7
 #pragma unroll
-      for (int u2 = 0; u2 < 4; ++u2)
+      for (int u2 = 0; u2 < 8; ++u2)
         x[u2] = (k + u2 < K) ? __ldg(reinterpret_cast<const int4*>(s.VL + (size_t)(k + u2) * s.ldl) + i)
                              : make_int4(0, 0, 0, 0);
 #pragma unroll
-      for (int u2 = 0; u2 < 4; ++u2) {
+      for (int u2 = 0; u2 < 8; ++u2) {
         if (k + u2 < K) {
           const int4 c = sC[k + u2];
           const int2 a = make_int2(x[u2].x, x[u2].y), b = make_int2(x[u2].z, x[u2].w);
@@ -363,7 +363,7 @@ k_maxpy_fx(const double* __restrict__ V, int64_t ldv, const double* __restrict__
           md1 = fx_madw(c.y, b.x, md1);
         }
       }
-      if ((k & 15) == 12) {  // every 16 columns: carry mid's high part into hh
+      if ((k & 15) == 8) {  // every 16 columns: carry mid's high part into hh
         hh0 += md0 >> 29;
         md0 &= 0x1FFFFFFFll;
         hh1 += md1 >> 29;
