@@ -266,24 +266,30 @@ k_maxpy(const VT* __restrict__ V, int64_t ldv, const YT* y_in, YT* y_out, int64_
 //    (mid folded into hh every 16 columns), Cl Xl (below 2^-56 of the
 //    largest product) dropped.
 // The first CTA finishes column j-1 of H meanwhile, as in k_maxpy.
+// mode MAXPY_XUPDATE: the cycle's solution update x += sum_{k<K} c_k u_k the
+// same way (K = the cycle's steps, c from Small::coefx, w = xout = x, in
+// place: each element is read, then written, by one thread; no Givens CTA).
 __global__ void __launch_bounds__(kThreads, 4)
-k_maxpy_fx(const double* __restrict__ V, int64_t ldv, const double* __restrict__ w, int64_t n, Small s) {
+k_maxpy_fx(const double* __restrict__ V, int64_t ldv, const double* w, int64_t n, Small s, int mode,
+           double* xout) {
   __shared__ int4 sC[kMaxM + 1];  // (Ch, Cl, 5 + column bound field, 0) per column
   __shared__ uint32_t s_p[kWarps];
   __shared__ int sK, s_skip, s_colk, s_bad, s_ps;
   __shared__ double s_alpha;
   DevState* st = s.st;
+  const bool arn = mode == MAXPY_ARNOLDI;
+  const double* cf = arn ? s.coef : s.coefx;
   if (threadIdx.x == 0) {
-    s_skip = __ldcg(&st->done);
-    sK = __ldcg(&st->maxpy_k);
-    s_colk = __ldcg(&st->step);
-    s_alpha = __ldcg(s.coef);
+    s_skip = arn ? __ldcg(&st->done) : 0;
+    sK = __ldcg(arn ? &st->maxpy_k : &st->k);
+    s_colk = arn ? __ldcg(&st->step) : -1;
+    s_alpha = __ldcg(cf);
     s_bad = 0;
   }
   __syncthreads();
   if (s_skip) return;
   const int K = sK;
-  if (blockIdx.x == 0) {
+  if (arn && blockIdx.x == 0) {
     // column j-1 of H: Givens, residual estimate, stop decision (the first
     // CTA, so that it starts with the streaming ones)
     const int j = s_colk - 1;
@@ -302,7 +308,7 @@ k_maxpy_fx(const double* __restrict__ V, int64_t ldv, const double* __restrict__
   double ck = 0.0;
   int fk = (int)kFxMinField, pk = 0;
   if ((int)threadIdx.x < K) {
-    ck = __ldcg(s.coef + 1 + threadIdx.x);
+    ck = __ldcg(cf + 1 + threadIdx.x);
     fk = (int)max(kFxMinField, __ldcg(s.ecol + threadIdx.x) >> 20);
     const int gk = (int)fx_field(ck);
     if (gk == 0x7FF || fk == 0x7FF) s_bad = 1;  // NaN or Inf among the inputs
@@ -333,10 +339,10 @@ k_maxpy_fx(const double* __restrict__ V, int64_t ldv, const double* __restrict__
   __syncthreads();
   const bool bad = s_bad != 0;
   const double alpha = s_alpha;
-  double* out = const_cast<double*>(V) + (size_t)s_colk * ldv;
-  const int ndata = gridDim.x - 1;
+  double* out = arn ? const_cast<double*>(V) + (size_t)s_colk * ldv : xout;
+  const int ndata = gridDim.x - (arn ? 1 : 0);
   const int64_t stride = (int64_t)ndata * blockDim.x;
-  const int64_t gid = (int64_t)(blockIdx.x - 1) * blockDim.x + threadIdx.x;
+  const int64_t gid = (int64_t)(blockIdx.x - (arn ? 1 : 0)) * blockDim.x + threadIdx.x;
   const int e2 = P - 2044 - cbits;  // sum = (hh + mid / 2^29) 2^(P - 2044 - cbits)
   uint32_t emax = 0;
   const int64_t nE = n / 2;
@@ -396,7 +402,7 @@ k_maxpy_fx(const double* __restrict__ V, int64_t ldv, const double* __restrict__
     out[i] = o;
     emax = max(emax, fx_hi_field(o));
   }
-  fx_note_max(s.ecol, s_colk, emax);
+  if (s_colk >= 0) fx_note_max(s.ecol, s_colk, emax);
 }
 
 // Arnoldi MAXPY of GMRES-IR with BF16 basis storage: u_{j+1} = alpha w +
@@ -1245,7 +1251,8 @@ gmres_status launch_cycle(gmres_ctx* h, int kmax) {
         else if (h->prec == GMRES_IR_BF16)
           k_maxpy_bf16<<<h->grid_stream + 1, kThreads, 0, h->stream>>>(h->V16, h->ldv, h->w32, h->n, h->s);
         else if (fx_stage(h->stage64, h->dot_fx) == 6)  // large systems: the fixed-point form with the step's
-          k_maxpy_fx<<<h->grid_stream + 1, kThreads, 0, h->stream>>>(h->V, h->ldv, h->w, h->n, h->s);
+          k_maxpy_fx<<<h->grid_stream + 1, kThreads, 0, h->stream>>>(h->V, h->ldv, h->w, h->n, h->s,
+                                                                     MAXPY_ARNOLDI, nullptr);
         else
           k_maxpy<double, double, double><<<h->grid_stream + 1, kThreads, 0, h->stream>>>(
               h->V, h->ldv, h->w, nullptr, h->n, h->s, MAXPY_ARNOLDI, 0);
@@ -1347,6 +1354,15 @@ bool use_persistent(const gmres_ctx* h) {
   if (h->ortho != GMRES_ONE_REDUCE_MGS && h->ortho != GMRES_ONE_REDUCE_PIPE2) return false;
   const int64_t ntiles = (h->n + kThreads - 1) / kThreads;
   return h->persist == 1 || ntiles < 2 * (int64_t)h->nsm;
+}
+
+// Whether the solution update of an FP64 cycle can run in fixed point on the
+// basis limbs: the cycle ran the mode-6 step kernel (which stores the limbs of
+// every column it uses; the persistent cycle and plain MGS do not), and x is
+// 16-byte aligned for the kernel's two-row loads and stores.
+bool xupdate_fx(const gmres_ctx* h, const double* x) {
+  return h->prec == GMRES_FP64 && h->ortho != GMRES_MGS && fx_stage(h->stage64, h->dot_fx) == 6 &&
+         !use_persistent(h) && (reinterpret_cast<uintptr_t>(x) & 15) == 0;
 }
 
 // One cycle of kmax steps in one cooperative launch (k_cycle_persistent).
@@ -1899,6 +1915,8 @@ gmres_status gmres_solve(gmres_handle h, const double* b, double* x, gmres_info*
       else if (h->prec == GMRES_IR_FP32)
         k_maxpy<float, double, double><<<h->grid_stream, kThreads, 0, h->stream>>>(h->V32, h->ldv, x, x, h->n, h->s,
                                                                                   MAXPY_XUPDATE, 0);
+      else if (xupdate_fx(h, x))  // the cycle stored the limbs of every column it used
+        k_maxpy_fx<<<h->grid_stream, kThreads, 0, h->stream>>>(h->V, h->ldv, x, h->n, h->s, MAXPY_XUPDATE, x);
       else
         k_maxpy<double, double, double><<<h->grid_stream, kThreads, 0, h->stream>>>(h->V, h->ldv, x, x, h->n, h->s,
                                                                                    MAXPY_XUPDATE, 0);
